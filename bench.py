@@ -1,0 +1,499 @@
+#!/usr/bin/env python3
+"""Benchmark of the taches-algorithm convolution on GB300.
+
+Workload (one step): 64 independent streams x 10 s at 48 kHz (480000 float32
+samples each, uniform [-1, 1]). Each stream has its own IR of L = 48000 taps
+(exp-decayed Gaussian, tau = 14400), and the IR is replaced by a new seeded
+one every 24000 samples. Odd swaps fall inside a 128-sample block, and each
+swap takes effect at its exact sample. Block size is 128. Every input is
+pushed through the C ABI, followed by the L-1 sample flush. Useful work:
+64 * 480000 * 48000 tap multiply-adds.
+
+  value    tap-MAC/s with inputs (x and every IR version) resident in device
+           memory (device-pointer pushes of P samples per launch)
+  e2e      the same step through the C ABI with host buffers (host->device
+           copies of x and IRs and device->host copy of y inside the timed region)
+  roofline K1 (FP32 gather) useful FLOP/s over its CUDA-event time, against the
+           FP32 FMA peak 152 SM x 128 FMA/clk x 2 FLOP x 2.07 GHz
+  latency  p50/p99 of one 128-sample block for all 64 streams (host buffers)
+           against the real-time deadline 128/48000 s
+  cpu_baseline  the FP64 oracle (buffer algorithm) on the host cores, on a
+           bounded sample of the same workload
+
+Under torchrun each rank runs its own 64 streams (weak scaling, no collective
+on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2401_01607_gb300 import synth  # noqa: E402  (no CUDA at import)
+
+C_STREAMS = 64
+N_SAMPLES = 480_000
+L_TAPS = 48_000
+BLOCK = 128
+SWAP = 24_000
+FS = synth.FS
+SM_COUNT = 152
+FMA_PER_CLK = 128
+SM_MAX_MHZ = 2070.0
+METRIC = "tap-MAC/s and concurrent 48 kHz real-time streams per GB300; p99 block latency"
+
+
+def fp32_peak_tflops(mhz: float) -> float:
+    return SM_COUNT * FMA_PER_CLK * 2 * mhz * 1e6 / 1e12
+
+
+def workload_config(P: int) -> dict:
+    return {
+        "workload": "64 independent streams x 10 s @ 48 kHz, own IRs L=48000 swapped every 24000 samples, block 128",
+        "streams": C_STREAMS, "samples_per_stream": N_SAMPLES, "L": L_TAPS, "block": BLOCK,
+        "ir_swap_every": SWAP, "push_samples": P,
+        "l2": "inputs larger than L2 (x 123 MB + 20 IR versions x 64 streams 246 MB resident)",
+    }
+
+
+# ---------------------------------------------------------------------------
+# Clocks sampled with nvidia-smi during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.device)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(self.NAMES, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on the host cores (spawned workers)
+# ---------------------------------------------------------------------------
+def _oracle_worker(args):
+    stream, nsamp = args
+    sys.path.insert(0, ROOT)
+    import oracle
+    from paper_2401_01607_gb300 import synth as sy
+    x = sy.audio(nsamp, sy.x_seed(2, stream))
+    nver = max(1, math.ceil(nsamp / SWAP))
+    H = np.stack([sy.decayed_ir(L_TAPS, 0.3 * L_TAPS, sy.ir_seed(stream, v)) for v in range(nver)])
+    vs = np.arange(nver, dtype=np.int64) * SWAP
+    o = oracle.Oracle()
+    t0 = time.perf_counter()
+    o.buffer(x, H, vs, BLOCK)
+    return time.perf_counter() - t0
+
+
+def oracle_baseline(cores: int, nsamp: int) -> dict:
+    import oracle
+    oracle.build()
+    ctx = mp.get_context("spawn")
+    jobs = [(s, nsamp) for s in range(cores)]
+    with ctx.Pool(cores) as pool:
+        t0 = time.perf_counter()
+        times = pool.map(_oracle_worker, jobs)
+        wall = time.perf_counter() - t0
+    slowest = max(times)
+    macs = cores * nsamp * L_TAPS
+    return {"value": macs / slowest, "unit": "tap-MAC/s", "cores": cores, "kind": "oracle",
+            "sample": f"{cores} of the 64 streams, first {nsamp} samples each (IR swaps included), "
+                      f"FP64 buffer algorithm, one stream per core; time = slowest worker "
+                      f"({slowest:.2f} s, pool wall {wall:.2f} s)",
+            "cpu_seconds": float(sum(times))}
+
+
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for ln in out.splitlines():
+            if "Model name" in ln:
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+# ---------------------------------------------------------------------------
+# Distributed plumbing (torchrun): barrier and max over ranks on the host
+# ---------------------------------------------------------------------------
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("gloo")
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, v: float) -> float:
+        if not self.pg:
+            return v
+        import torch
+        t = torch.tensor([v], dtype=torch.float64)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# The GPU step
+# ---------------------------------------------------------------------------
+class Runner:
+    def __init__(self, P: int, w, torch):
+        from paper_2401_01607_gb300 import capi
+        self.capi = capi
+        self.torch = torch
+        self.P = P
+        self.w = w
+        self.npush = math.ceil(N_SAMPLES / P)
+        # Input laid out push-major: push i is one contiguous [stream][n] slab
+        # (n = P except for the last push, which is stored packed as [stream][n]).
+        xp = np.zeros((self.npush, C_STREAMS, P), np.float32)
+        for i in range(self.npush):
+            seg = w.x[:, i * P:(i + 1) * P]
+            xp[i].reshape(-1)[:seg.size] = seg.reshape(-1)
+        self.x_host_push = xp
+        self.H_vmajor = np.ascontiguousarray(np.transpose(w.H, (1, 0, 2)))  # [nver][C][L]
+        self.x_d = torch.from_numpy(xp).cuda()
+        self.H_d = torch.from_numpy(self.H_vmajor).cuda()
+        self.y_d = torch.empty((self.npush, C_STREAMS, P), device="cuda")
+        self.tail_d = torch.empty((C_STREAMS, L_TAPS - 1), device="cuda")
+        self.ts = torch.cuda.Stream()
+        self.s = capi.tc_open_group(C_STREAMS, L_TAPS, BLOCK, False, capi.TC_FP32, P)
+        capi.tc_set_cuda_stream(self.s, self.ts)
+        self.vstart = [int(v) for v in w.vstart]
+
+    def step_device(self):
+        c = self.capi
+        c.tc_reset(self.s)
+        v = 0
+        for i in range(self.npush):
+            pos = i * self.P
+            n = min(self.P, N_SAMPLES - pos)
+            while v < len(self.vstart) and self.vstart[v] < pos + n:
+                c.tc_set_ir_rows(self.s, int(self.H_d[v].data_ptr()), L_TAPS, self.vstart[v], on_device=True)
+                v += 1
+            c.tc_push(self.s, int(self.x_d[i].data_ptr()), n, int(self.y_d[i].data_ptr()), on_device=True)
+        c.tc_flush_dev(self.s, int(self.tail_d.data_ptr()))
+
+    def step_host(self, y_host, tail_host):
+        c = self.capi
+        c.tc_reset(self.s)
+        v = 0
+        for i in range(self.npush):
+            pos = i * self.P
+            n = min(self.P, N_SAMPLES - pos)
+            while v < len(self.vstart) and self.vstart[v] < pos + n:
+                c.tc_set_ir_rows(self.s, self.H_vmajor[v], L_TAPS, self.vstart[v])
+                v += 1
+            xb = self.x_host_push[i].reshape(-1)[:C_STREAMS * n]
+            yb = y_host[i].reshape(-1)[:C_STREAMS * n]
+            c.tc_push(self.s, xb, n, yb)
+        c.tc_flush(self.s, tail_host, L_TAPS - 1)
+
+    def close(self):
+        self.capi.tc_close(self.s)
+
+
+def check_sampled(runner, n_check=64) -> dict:
+    """Sampled outputs of the last device step against Eq. (4) computed one by one (FP64 oracle)."""
+    import oracle
+    w = runner.w
+    y = runner.y_d.cpu().numpy()
+    tail = runner.tail_d.cpu().numpy()
+    rng = np.random.default_rng(123)
+    got, ref = [], []
+    for _ in range(n_check):
+        c = int(rng.integers(C_STREAMS))
+        m = int(rng.integers(N_SAMPLES + L_TAPS - 1))
+        if m < N_SAMPLES:
+            i, j = divmod(m, runner.P)
+            n = min(runner.P, N_SAMPLES - i * runner.P)
+            got.append(y[i].reshape(-1)[c * n + j])
+        else:
+            got.append(tail[c, m - N_SAMPLES])
+        ref.append(oracle.direct_at(w.x[c], w.H[c], w.vstart, m))
+    got = np.array(got, np.float64)
+    ref = np.array(ref)
+    return {"sampled_outputs": n_check, "rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+            "max_abs": float(np.max(np.abs(got - ref)))}
+
+
+def traffic_from_profile(kernel_src: str) -> float | None:
+    """Per-launch DRAM bytes of K1 from the committed ncu summary, if it matches the current kernel source."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k1_gather_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    digest = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    for ln in open(path):
+        parts = ln.split()
+        if len(parts) >= 3 and parts[0] == "traffic_bytes_per_launch" and parts[2] == digest:
+            return float(parts[1])
+    return None
+
+
+def run_reference(args, dist: Dist) -> None:
+    if dist.rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    nsamp = args.ref_samples
+    times = []
+    for i in range(args.warmup + args.steps):
+        r = oracle_baseline(cores, nsamp)
+        if i >= args.warmup:
+            times.append(r)
+    value = float(np.median([t["value"] for t in times]))
+    ms = float(np.median([cores * nsamp * L_TAPS / t["value"] for t in times])) * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "tap-MAC/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args.push),
+            "cpu_baseline": {"value": value, "unit": "tap-MAC/s", "cores": cores, "kind": "oracle",
+                             "sample": times[-1]["sample"], "cpu_model": cpu_model()},
+            "e2e": {"value": value, "unit": "tap-MAC/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--push", type=int, default=0, help="samples per push (0: autotune)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-latency", action="store_true")
+    ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--cpu-samples", type=int, default=30_000)
+    ap.add_argument("--ref-samples", type=int, default=6_000)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+
+    dist = Dist()
+    if args.impl == "reference":
+        run_reference(args, dist)
+        dist.close()
+        return
+
+    # CPU baseline first: the spawned oracle workers start before any CUDA call.
+    cpu = None
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu:
+        cpu = oracle_baseline(os.cpu_count() or 1, args.cpu_samples)
+        cpu["cpu_model"] = cpu_model()
+
+    import torch
+    import paper_2401_01607_gb300 as pkg
+    from paper_2401_01607_gb300 import capi
+    pkg.build()
+    torch.cuda.set_device(dist.local)
+    dev = torch.cuda.current_device()
+
+    w = synth.multi(C=C_STREAMS, N=N_SAMPLES, L=L_TAPS, block=BLOCK, swap_every=SWAP,
+                    stream0=dist.rank * C_STREAMS)
+
+    # Blocks per launch: pick the fastest push size on a short segment.
+    P = args.push
+    tune = {}
+    if P == 0:
+        for cand in (1024, 2048, 4096, 8192):
+            r = Runner(cand, w, torch)
+            c = r.capi
+            c.tc_reset(r.s)
+            c.tc_set_ir_rows(r.s, int(r.H_d[0].data_ptr()), L_TAPS, 0, on_device=True)
+            pushes = max(2, 16384 // cand)
+            for rep in range(2):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(r.ts)
+                for i in range(pushes):
+                    c.tc_push(r.s, int(r.x_d[i].data_ptr()), cand, int(r.y_d[i].data_ptr()), on_device=True)
+                e1.record(r.ts)
+                e1.synchronize()
+            tune[cand] = e0.elapsed_time(e1) / (pushes * cand)
+            r.close()
+            del r
+            torch.cuda.empty_cache()
+        P = min(tune, key=tune.get)
+
+    runner = Runner(P, w, torch)
+    for _ in range(args.warmup):
+        runner.step_device()
+    torch.cuda.synchronize()
+
+    launches0 = capi.tc_kernel_launches()
+    capi.tc_profile(runner.s, True)
+    clocks = ClockSampler(dev)
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e_start.record(runner.ts)
+    for _ in range(args.steps):
+        runner.step_device()
+    e_end.record(runner.ts)
+    e_end.synchronize()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    dist.barrier()
+    launches = capi.tc_kernel_launches() - launches0
+    k_ms, k_launches, k_macs = capi.tc_profile_read(runner.s)
+    capi.tc_profile(runner.s, False)
+    t_ms = e_start.elapsed_time(e_end)
+    t_ms_max = dist.max(t_ms)
+    macs_step = C_STREAMS * N_SAMPLES * L_TAPS
+    value = macs_step * dist.world * args.steps / (t_ms_max / 1e3)
+    ms_per_step = t_ms_max / args.steps
+
+    check = None if args.no_check else check_sampled(runner)
+
+    # Roofline of K1: useful FLOPs per launch over its average event time.
+    k1_flops_per_launch = 2.0 * k_macs / max(k_launches, 1)
+    k1_avg_s = (k_ms / max(k_launches, 1)) / 1e3
+    achieved = k1_flops_per_launch / k1_avg_s / 1e12 if k1_avg_s > 0 else 0.0
+    peak = fp32_peak_tflops(SM_MAX_MHZ)
+    traffic = traffic_from_profile(os.path.join(ROOT, "paper_2401_01607_gb300", "csrc", "k1_gather.cu"))
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": "k1_gather (FP32 FMA gather)",
+                "peak_basis": "152 SM x 128 FP32 FMA/clk x 2 FLOP x 2070 MHz (max SM clock)",
+                "k1_launches": k_launches, "k1_avg_ms": k1_avg_s * 1e3,
+                "k1_share_of_step": (k_ms / args.steps) / ms_per_step if ms_per_step > 0 else None}
+    if clk:
+        roofline["frac_at_measured_clock"] = achieved / fp32_peak_tflops(clk["sm_mhz"])
+
+    e2e = None
+    if not args.no_e2e:
+        y_host = np.empty((runner.npush, C_STREAMS, P), np.float32)
+        tail_host = np.empty((C_STREAMS, L_TAPS - 1), np.float32)
+        runner.step_host(y_host, tail_host)  # warm
+        reps = min(args.steps, 2)
+        dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            runner.step_host(y_host, tail_host)
+        dt = dist.max(time.perf_counter() - t0) / reps
+        nver = len(runner.vstart)
+        h2d = C_STREAMS * N_SAMPLES * 4 + nver * C_STREAMS * L_TAPS * 4
+        d2h = C_STREAMS * (N_SAMPLES + L_TAPS - 1) * 4
+        e2e = {"value": macs_step * dist.world / dt, "unit": "tap-MAC/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3,
+               "path": "tc_set_ir_rows / tc_push / tc_flush with host buffers"}
+
+    latency = None
+    if not args.no_latency:
+        # Real-time block latency: one 128-sample block per stream per call, host buffers.
+        s2 = capi.tc_open_group(C_STREAMS, L_TAPS, BLOCK, False, capi.TC_FP32, BLOCK)
+        try:
+            capi.tc_set_ir_rows(s2, runner.H_vmajor[0], L_TAPS, 0)
+            xb = np.ascontiguousarray(runner.w.x[:, :BLOCK])
+            yb = np.empty((C_STREAMS, BLOCK), np.float32)
+            # Fill the history to a full window first.
+            for _ in range(L_TAPS // BLOCK + 2):
+                capi.tc_push_block(s2, xb, yb)
+            lat = []
+            for _ in range(400):
+                t0 = time.perf_counter()
+                capi.tc_push_block(s2, xb, yb)
+                lat.append(time.perf_counter() - t0)
+        finally:
+            capi.tc_close(s2)
+        lat = np.array(lat) * 1e3
+        deadline = BLOCK / FS * 1e3
+        latency = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                   "max_ms": float(lat.max()), "deadline_ms": deadline,
+                   "misses": int(np.sum(lat > deadline)), "blocks": int(lat.size),
+                   "mode": "64 streams, one 128-sample block per tc_push_block call, host buffers"}
+
+    runner.close()
+    if dist.rank == 0:
+        per_stream_rt = FS * L_TAPS  # tap-MAC/s one real-time stream needs
+        line = {"metric": METRIC, "value": value, "unit": "tap-MAC/s", "n_gpus": dist.world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic", "config": workload_config(P),
+                "realtime_streams_48k": value / per_stream_rt,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "gpu_launches": int(launches), "latency": latency, "check": check,
+                "autotune_push_ms_per_sample": {str(k): v for k, v in tune.items()} or None}
+        print(json.dumps(line), flush=True)
+    dist.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,229 @@
+/*
+ * taches.h -- C ABI of a GB300 (sm_103a) library for the taches-algorithm:
+ * streaming, block-by-block time-domain convolution with an impulse response
+ * (IR) that may change between input samples.
+ *
+ * Method: L. Millot and G. Pele, "An alternative approach for the convolution
+ * in time-domain: the taches-algorithms", AES 125th Convention, 2008.
+ *   - Every input sample x[n] spawns a "tache" x[n] * h[0..L-1] that is added
+ *     to the output from sample n on (Sec. 3.2, Eq. 4):
+ *         y[m] = sum_n x[n] * h_{v(n)}[m - n].
+ *   - The IR used by sample n, h_{v(n)}, is the one in force when n arrived.
+ *     Replacing the IR affects only later samples, even one sample apart
+ *     (abstract and Sec. 6).
+ *   - The input comes in blocks of Nb samples and each pushed block yields
+ *     the output block of the same sample range at once (buffer algorithm,
+ *     Sec. 4.2). A shorter last block is allowed.
+ *   - The output is L-1 samples longer than the input. This "temporal
+ *     overflow" (Sec. 4.1) is delivered by tc_flush.
+ *
+ * The GPU computes each output block as an output-side gather,
+ *     y[t0+i] = sum_k h_{v(t0+i-k)}[k] * x[t0+i-k],
+ * over the resident input history. This gives the same values as the
+ * paper's scatter into a ring accumulator, up to float rounding.
+ *
+ * Conventions (all entry points):
+ *   - Every call returns a tc_status. Nothing throws or aborts across the
+ *     ABI. On error, tc_last_error() returns a message for the calling thread.
+ *   - The library owns all device memory that it allocates. The caller owns
+ *     the x, y and h buffers that it passes, and the library keeps no pointer
+ *     to them after the call returns (device-pointer calls: after the
+ *     enqueued work has run).
+ *   - Samples are float32. A group with C channels takes x as [C][n] and
+ *     returns y as [C][n], row-major with rows of exactly n floats.
+ *   - Host-pointer calls are synchronous: they return once y holds the
+ *     result. Device-pointer calls (the *_dev functions, or on_device = 1)
+ *     enqueue work on the stream's CUDA stream and return at once.
+ *   - Use one tc_stream from one thread at a time. Different tc_streams may
+ *     be used from different threads.
+ */
+#ifndef TACHES_H
+#define TACHES_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tc_stream tc_stream; /* opaque, owned by the library */
+
+typedef enum tc_status {
+    TC_OK = 0,
+    TC_EINVAL = 1,       /* bad argument: NULL pointer, zero size, n > max_push, IR longer than L, ... */
+    TC_ENOMEM = 2,       /* device or pinned allocation failed, or every IR slot is still in use */
+    TC_ESTATE = 3,       /* call not allowed now: push before any IR, push after the last (short) block or after flush */
+    TC_ECUDA = 4,        /* a CUDA call or kernel launch failed; tc_last_error() has the CUDA message */
+    TC_ETIMEOUT = 5,     /* a bounded device-side wait gave up; the results of that call are invalid */
+    TC_EUNSUPPORTED = 6  /* the option is not available for this kind of stream */
+} tc_status;
+
+typedef enum tc_precision {
+    TC_FP32 = 0,         /* FP32 FMA on CUDA cores (any stream kind) */
+    TC_BF16 = 1,         /* BF16 tensor cores, FP32 accumulate (shared-IR groups and MIMO only) */
+    TC_BF16_SPLIT = 2    /* BF16 hi/lo split of both operands, 3 tensor products, FP32 accumulate */
+} tc_precision;
+
+/* Describes a stream; filled by tc_get_info. */
+typedef struct tc_info {
+    size_t channels;     /* rows of x per push (MIMO: inputs) */
+    size_t outputs;      /* rows of y per push (MIMO: outputs; otherwise = channels) */
+    size_t L;            /* IR length (taps) */
+    size_t block;        /* nominal block size Nb */
+    size_t max_push;     /* largest n accepted by one push */
+    uint64_t pushed;     /* input samples pushed so far, per channel */
+    int shared_ir;       /* 1: one IR for every channel */
+    int precision;       /* tc_precision */
+    int state;           /* 0 open, 1 ended (short block pushed), 2 flushed */
+    int max_versions;    /* IR versions that can be live at once, per IR set */
+} tc_info;
+
+/* ---------------------------------------------------------------------- */
+/* Opening and closing                                                     */
+/* ---------------------------------------------------------------------- */
+
+/* One mono stream, FP32, IR length L taps, block Nb = block samples.
+ * Allocates the stream's device state on the current CUDA device. That
+ * state is the input history, the IR slots and the scratch for the split
+ * tap sums.
+ * Errors: TC_EINVAL if L == 0, block == 0 or out == NULL; TC_ENOMEM; TC_ECUDA. */
+tc_status tc_open_stream(size_t L, size_t block, tc_stream **out);
+
+/* A group of `channels` streams pushed together: the multichannel use of
+ * Sec. 5.1 and Sec. 6. With shared_ir = 1 all channels use one IR. The
+ * BF16 modes then run on the tensor cores as a Toeplitz(h) x X contraction.
+ * With shared_ir = 0 each channel has its own IR and its own IR versions
+ * (FP32 only). max_push >= block is the largest n of one push. A push of
+ * several blocks gives the same values as pushing them one at a time,
+ * since Nb affects only timing (Sec. 5.2, Table 2). max_push = 0 means block.
+ * Errors: TC_EINVAL (sizes 0, max_push < block); TC_EUNSUPPORTED (BF16
+ * with per-channel IRs); TC_ENOMEM; TC_ECUDA. */
+tc_status tc_open_group(size_t channels, size_t L, size_t block, int shared_ir,
+                        tc_precision precision, size_t max_push, tc_stream **out);
+
+/* nin inputs and nout outputs. Output o is sum_i h_{o,i} * x_i. The IR set
+ * is [nout][nin][L]. Pushes take x as [nin][n] and return y as [nout][n].
+ * Errors as tc_open_group. */
+tc_status tc_open_mimo(size_t nin, size_t nout, size_t L, size_t block,
+                       tc_precision precision, size_t max_push, tc_stream **out);
+
+/* Frees everything the stream owns (after its device work has finished).
+ * NULL is accepted. */
+tc_status tc_close(tc_stream *s);
+
+/* Back to the state right after open: no IR, nothing pushed, the history
+ * zeroed. Keeps all allocations. */
+tc_status tc_reset(tc_stream *s);
+
+/* Maximum number of IR versions live at once per IR set (default 4). A
+ * version stays live while a future output still needs a sample that spawned
+ * its tache with it, that is until L-1 samples after the next version
+ * starts. Only allowed before the first tc_set_ir*. Reallocates the IR slots. */
+tc_status tc_set_max_versions(tc_stream *s, int max_versions);
+
+/* Use this CUDA stream (a cudaStream_t passed as void*; NULL = the library's
+ * own stream) for all of this tc_stream's later device work. */
+tc_status tc_set_cuda_stream(tc_stream *s, void *cuda_stream);
+
+tc_status tc_get_info(const tc_stream *s, tc_info *info);
+
+/* ---------------------------------------------------------------------- */
+/* IR versions (abstract, Sec. 6: update the IR "for next samples")        */
+/* ---------------------------------------------------------------------- */
+
+/* Sets the IR h[0..n-1], n <= L (zero-padded to L), for every channel. It
+ * takes effect from the next input sample to be pushed. Taches already
+ * spawned keep their IR. h is a host pointer and is copied before the call
+ * returns. Errors: TC_EINVAL (n == 0 or n > L, h NULL); TC_ENOMEM (no free
+ * IR slot: too many versions still live); TC_ECUDA. */
+tc_status tc_set_ir(tc_stream *s, const float *h, size_t n);
+
+/* As tc_set_ir, but the IR is used from input sample index `sample` on (0 =
+ * first sample of the stream). This gives the exact per-sample switch of
+ * Sec. 6: the switch may fall inside a block. sample must be >= the number
+ * of samples already pushed, and >= the start of the latest version. A
+ * version set at the same sample replaces it. */
+tc_status tc_set_ir_at(tc_stream *s, const float *h, size_t n, uint64_t sample);
+
+/* One IR per IR set, all taking effect at `sample`. h is [sets][n]. sets is
+ * 1 for a shared-IR group, channels for a per-channel group, and nout*nin
+ * ([nout][nin][n]) for MIMO. h_on_device = 1: h is a device pointer; the copy
+ * is enqueued on the stream and h must stay valid until it has run.
+ * Errors as tc_set_ir_at. */
+tc_status tc_set_ir_rows(tc_stream *s, const float *h, size_t n, uint64_t sample, int h_on_device);
+
+/* ---------------------------------------------------------------------- */
+/* Pushing input, receiving output (buffer algorithm, Sec. 4.2)            */
+/* ---------------------------------------------------------------------- */
+
+/* Pushes n <= block samples per channel (host x [channels][n]). Receives
+ * the n output samples of the same sample range (host y [outputs][n]).
+ * n < block marks the last block (Sec. 4.2, Nb <- min(Nb, size(pe))); only
+ * tc_flush is allowed after it.
+ * Errors: TC_EINVAL (NULL, n == 0, n > block); TC_ESTATE (no IR covers
+ * the next sample, or stream ended); TC_ECUDA; TC_ETIMEOUT. */
+tc_status tc_push_block(tc_stream *s, const float *x, size_t n, float *y);
+
+/* As tc_push_block, for n <= max_push samples. n should be a multiple of
+ * block; otherwise this is the last push. on_device = 1: x and y are device
+ * pointers, and the call enqueues the work on the stream's CUDA stream and
+ * returns without waiting (check with tc_sync). */
+tc_status tc_push(tc_stream *s, const float *x, size_t n, float *y, int on_device);
+
+/* Temporal overflow (Sec. 4.1): the last L-1 output samples per output row,
+ * as if L-1 zeros were pushed. Host y holds [outputs][cap], and row o gets
+ * min(cap, L-1) samples. *n_out (optional) receives L-1. After this, only
+ * tc_reset or tc_close is allowed.
+ * Errors: TC_EINVAL (y NULL, cap < L-1); TC_ESTATE (already flushed). */
+tc_status tc_flush(tc_stream *s, float *y, size_t cap, size_t *n_out);
+
+/* Device version of tc_flush: y is a device [outputs][L-1] buffer.
+ * Asynchronous. */
+tc_status tc_flush_dev(tc_stream *s, float *y, size_t *n_out);
+
+/* Waits for the stream's enqueued device work. Returns TC_ETIMEOUT if a
+ * kernel reported a bounded-wait failure, TC_ECUDA on a CUDA error. */
+tc_status tc_sync(tc_stream *s);
+
+/* ---------------------------------------------------------------------- */
+/* One-shot convolution (off-line use, Sec. 3.2)                           */
+/* ---------------------------------------------------------------------- */
+
+/* y[0..N+L-2] = x[0..N-1] * h[0..L-1], all device pointers, FP32. Runs on
+ * cuda_stream (a cudaStream_t as void*; NULL = default stream) and waits
+ * for it before returning. Allocates its working memory, which is freed
+ * before return. Errors: TC_EINVAL (NULL or zero sizes); TC_ENOMEM; TC_ECUDA;
+ * TC_ETIMEOUT. */
+tc_status tc_convolve(const float *x, size_t N, const float *h, size_t L, float *y, void *cuda_stream);
+
+/* ---------------------------------------------------------------------- */
+/* Diagnostics                                                             */
+/* ---------------------------------------------------------------------- */
+
+/* Message of the calling thread's last failed call ("" if none). Valid until
+ * that thread's next call into the library. */
+const char *tc_last_error(void);
+
+/* Static name of a status code. */
+const char *tc_status_str(tc_status st);
+
+/* Number of kernel launches this library has issued in this process. Counts
+ * every launch, on every stream. */
+uint64_t tc_kernel_launches(void);
+
+/* Kernel timing (tracing aid). With enable = 1, each later convolution kernel
+ * launch of this stream is bracketed by CUDA events on the stream that runs
+ * it. tc_profile_read waits for the stream, then returns the summed event
+ * time in ms, the number of timed launches and the useful multiply-adds they
+ * did. The useful multiply-adds count one per (output sample, in-range tap,
+ * input row). It then clears the totals. Timing adds a little overhead per
+ * launch. */
+tc_status tc_profile(tc_stream *s, int enable);
+tc_status tc_profile_read(tc_stream *s, double *ms, uint64_t *launches, double *useful_macs);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TACHES_H */

@@ -1,0 +1,258 @@
+"""Python binding of the C ABI in include/taches.h (argument marshalling only).
+
+Every function has the name of its C entry point and does no computing of its
+own: it converts arguments (numpy arrays for host buffers, torch CUDA tensors
+or raw integers for device buffers), calls libtaches.so and raises TcError on
+a non-zero tc_status. Out-parameters become return values.
+
+The library is loaded on first use. If libtaches.so is missing or fails to
+load, the call raises at once: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+TC_FP32, TC_BF16, TC_BF16_SPLIT = 0, 1, 2
+STATUS = {0: "TC_OK", 1: "TC_EINVAL", 2: "TC_ENOMEM", 3: "TC_ESTATE", 4: "TC_ECUDA", 5: "TC_ETIMEOUT",
+          6: "TC_EUNSUPPORTED"}
+PRECISIONS = {"fp32": TC_FP32, "bf16": TC_BF16, "bf16split": TC_BF16_SPLIT}
+
+
+class TcError(RuntimeError):
+    def __init__(self, status: int, fn: str, msg: str):
+        self.status = status
+        self.code = STATUS.get(status, str(status))
+        super().__init__(f"{fn}: {self.code}: {msg}")
+
+
+class TcInfo(ctypes.Structure):
+    _fields_ = [("channels", ctypes.c_size_t), ("outputs", ctypes.c_size_t), ("L", ctypes.c_size_t),
+                ("block", ctypes.c_size_t), ("max_push", ctypes.c_size_t), ("pushed", ctypes.c_uint64),
+                ("shared_ir", ctypes.c_int), ("precision", ctypes.c_int), ("state", ctypes.c_int),
+                ("max_versions", ctypes.c_int)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+_vp = ctypes.c_void_p
+_sz = ctypes.c_size_t
+_u64 = ctypes.c_uint64
+_int = ctypes.c_int
+_SIGS = {
+    "tc_open_stream": [_sz, _sz, ctypes.POINTER(_vp)],
+    "tc_open_group": [_sz, _sz, _sz, _int, _int, _sz, ctypes.POINTER(_vp)],
+    "tc_open_mimo": [_sz, _sz, _sz, _sz, _int, _sz, ctypes.POINTER(_vp)],
+    "tc_close": [_vp],
+    "tc_reset": [_vp],
+    "tc_set_max_versions": [_vp, _int],
+    "tc_set_cuda_stream": [_vp, _vp],
+    "tc_get_info": [_vp, ctypes.POINTER(TcInfo)],
+    "tc_set_ir": [_vp, _vp, _sz],
+    "tc_set_ir_at": [_vp, _vp, _sz, _u64],
+    "tc_set_ir_rows": [_vp, _vp, _sz, _u64, _int],
+    "tc_push_block": [_vp, _vp, _sz, _vp],
+    "tc_push": [_vp, _vp, _sz, _vp, _int],
+    "tc_flush": [_vp, _vp, _sz, ctypes.POINTER(_sz)],
+    "tc_flush_dev": [_vp, _vp, ctypes.POINTER(_sz)],
+    "tc_sync": [_vp],
+    "tc_convolve": [_vp, _sz, _vp, _sz, _vp, _vp],
+    "tc_profile": [_vp, _int],
+    "tc_profile_read": [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_u64), ctypes.POINTER(ctypes.c_double)],
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load() -> ctypes.CDLL:
+    """Loads libtaches.so (raising if it is absent)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is not built: run __graft_entry__.build() (needs nvcc)")
+        lib = ctypes.CDLL(path)
+        for name, args in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        lib.tc_last_error.argtypes = []
+        lib.tc_last_error.restype = ctypes.c_char_p
+        lib.tc_status_str.argtypes = [ctypes.c_int]
+        lib.tc_status_str.restype = ctypes.c_char_p
+        lib.tc_kernel_launches.argtypes = []
+        lib.tc_kernel_launches.restype = ctypes.c_uint64
+        _lib = lib
+        return lib
+
+
+def _call(name: str, *args) -> None:
+    lib = load()
+    st = getattr(lib, name)(*args)
+    if st != 0:
+        raise TcError(st, name, lib.tc_last_error().decode(errors="replace"))
+
+
+def _host_f32(a, writable=False):
+    if not isinstance(a, np.ndarray) or a.dtype != np.float32 or not a.flags.c_contiguous:
+        if writable:
+            raise TypeError("host output must be a C-contiguous float32 numpy array")
+        a = np.ascontiguousarray(a, dtype=np.float32)
+    return a, a.ctypes.data_as(_vp)
+
+
+def _dev_ptr(t) -> int:
+    """Device address of a torch CUDA tensor (float32, contiguous) or a raw integer address."""
+    if isinstance(t, int):
+        return t
+    if getattr(t, "is_cuda", False):
+        if not t.is_contiguous():
+            raise ValueError("device tensor must be contiguous")
+        if str(t.dtype) != "torch.float32":
+            raise TypeError("device tensor must be float32")
+        return int(t.data_ptr())
+    raise TypeError("expected a torch CUDA tensor or an integer device address")
+
+
+# ---------------------------------------------------------------------------
+# Entry points (same names as include/taches.h)
+# ---------------------------------------------------------------------------
+
+def tc_open_stream(L: int, block: int) -> int:
+    h = _vp()
+    _call("tc_open_stream", L, block, ctypes.byref(h))
+    return h.value
+
+
+def tc_open_group(channels: int, L: int, block: int, shared_ir: bool, precision: int = TC_FP32,
+                  max_push: int = 0) -> int:
+    h = _vp()
+    _call("tc_open_group", channels, L, block, int(bool(shared_ir)), int(precision), max_push, ctypes.byref(h))
+    return h.value
+
+
+def tc_open_mimo(nin: int, nout: int, L: int, block: int, precision: int = TC_FP32, max_push: int = 0) -> int:
+    h = _vp()
+    _call("tc_open_mimo", nin, nout, L, block, int(precision), max_push, ctypes.byref(h))
+    return h.value
+
+
+def tc_close(s: int) -> None:
+    _call("tc_close", s)
+
+
+def tc_reset(s: int) -> None:
+    _call("tc_reset", s)
+
+
+def tc_set_max_versions(s: int, max_versions: int) -> None:
+    _call("tc_set_max_versions", s, max_versions)
+
+
+def tc_set_cuda_stream(s: int, cuda_stream) -> None:
+    """cuda_stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None."""
+    if cuda_stream is None:
+        ptr = None
+    elif isinstance(cuda_stream, int):
+        ptr = cuda_stream
+    else:
+        ptr = int(cuda_stream.cuda_stream)
+    _call("tc_set_cuda_stream", s, ptr)
+
+
+def tc_get_info(s: int) -> TcInfo:
+    info = TcInfo()
+    _call("tc_get_info", s, ctypes.byref(info))
+    return info
+
+
+def tc_set_ir(s: int, h) -> None:
+    h, p = _host_f32(h)
+    _call("tc_set_ir", s, p, h.size)
+
+
+def tc_set_ir_at(s: int, h, sample: int) -> None:
+    h, p = _host_f32(h)
+    _call("tc_set_ir_at", s, p, h.size, int(sample))
+
+
+def tc_set_ir_rows(s: int, h, n: int, sample: int, on_device: bool = False) -> None:
+    """h: [sets][n] float32 (host numpy, or device tensor when on_device)."""
+    if on_device:
+        _call("tc_set_ir_rows", s, _dev_ptr(h), n, int(sample), 1)
+    else:
+        h, p = _host_f32(h)
+        _call("tc_set_ir_rows", s, p, n, int(sample), 0)
+
+
+def tc_push_block(s: int, x, y) -> None:
+    """x: host [channels][n] float32; y: host [outputs][n] float32, written in place."""
+    x, px = _host_f32(x)
+    y, py = _host_f32(y, writable=True)
+    n = x.shape[-1]
+    _call("tc_push_block", s, px, n, py)
+
+
+def tc_push(s: int, x, n: int, y, on_device: bool = False) -> None:
+    if on_device:
+        _call("tc_push", s, _dev_ptr(x), n, _dev_ptr(y), 1)
+    else:
+        x, px = _host_f32(x)
+        y, py = _host_f32(y, writable=True)
+        _call("tc_push", s, px, n, py, 0)
+
+
+def tc_flush(s: int, y, cap: int) -> int:
+    y, py = _host_f32(y, writable=True)
+    n = _sz()
+    _call("tc_flush", s, py, cap, ctypes.byref(n))
+    return n.value
+
+
+def tc_flush_dev(s: int, y) -> int:
+    n = _sz()
+    _call("tc_flush_dev", s, _dev_ptr(y), ctypes.byref(n))
+    return n.value
+
+
+def tc_sync(s: int) -> None:
+    _call("tc_sync", s)
+
+
+def tc_convolve(x, N: int, h, L: int, y, cuda_stream=None) -> None:
+    cs = None if cuda_stream is None else (cuda_stream if isinstance(cuda_stream, int) else
+                                           int(cuda_stream.cuda_stream))
+    _call("tc_convolve", _dev_ptr(x), N, _dev_ptr(h), L, _dev_ptr(y), cs)
+
+
+def tc_profile(s: int, enable: bool = True) -> None:
+    _call("tc_profile", s, int(bool(enable)))
+
+
+def tc_profile_read(s: int) -> tuple[float, int, float]:
+    """Returns (kernel ms, timed launches, useful multiply-adds) and clears them."""
+    ms, n, macs = ctypes.c_double(), _u64(), ctypes.c_double()
+    _call("tc_profile_read", s, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(macs))
+    return ms.value, int(n.value), macs.value
+
+
+def tc_last_error() -> str:
+    return load().tc_last_error().decode(errors="replace")
+
+
+def tc_status_str(st: int) -> str:
+    return load().tc_status_str(st).decode()
+
+
+def tc_kernel_launches() -> int:
+    return int(load().tc_kernel_launches())

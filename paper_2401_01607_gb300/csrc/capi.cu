@@ -1,0 +1,883 @@
+// capi.cu -- implementation of the C ABI in include/taches.h (host code).
+//
+// Device state of a stream:
+//   hist     input history, one row per input channel, float32, row pitch
+//            `cap`. Sample n of a row lives at column n - base. The row keeps at
+//            least `keep` samples behind the next push, which is L plus one tap
+//            chunk. When a push would run past the row end, the kept tail is
+//            copied to the row start (one 2-D copy, source and destination
+//            disjoint) and base moves.
+//   ir       IR slots [slot][set][4 shifted copies][Lpad] for K1.
+//   vt       version table: (first sample, slot) per live IR version
+//            (abstract, Sec. 6: a new IR is used for the next samples).
+//   partial  K1 scratch for tap-chunk partial sums, plus ticket counters.
+// Everything runs on one CUDA stream per tc_stream, in call order, so a slot
+// or table entry is never overwritten while an earlier kernel may read it.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/taches.h"
+#include "tc_internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+tc_status fail(tc_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define TC_CU(call)                                                                                   \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess)                                                                        \
+            return fail(e_ == cudaErrorMemoryAllocation ? TC_ENOMEM : TC_ECUDA, "%s: %s", #call,     \
+                        cudaGetErrorString(e_));                                                      \
+    } while (0)
+
+#define TC_TRY(expr)                 \
+    do {                             \
+        tc_status st_ = (expr);      \
+        if (st_ != TC_OK)            \
+            return st_;              \
+    } while (0)
+
+long long round_up(long long a, long long m) { return (a + m - 1) / m * m; }
+long long floor4(long long a) { return a >= 0 ? (a & ~3LL) : -(((-a) + 3) & ~3LL); }
+
+constexpr int kMaxVersions = 16;
+
+struct Version {
+    long long start;
+    int slot;
+};
+
+// Device copy of the version table.
+struct DevTable {
+    long long vstart[kMaxVersions];
+    int vslot[kMaxVersions];
+    int nver;
+};
+
+enum Kind { KIND_GROUP = 0, KIND_MIMO = 1 };
+enum State { ST_OPEN = 0, ST_ENDED = 1, ST_FLUSHED = 2 };
+
+}  // namespace
+
+struct tc_stream {
+    // Shape.
+    int kind = KIND_GROUP;
+    size_t rows = 1;   // history rows (channels, or MIMO inputs)
+    size_t items = 1;  // output rows (channels, or MIMO outputs)
+    size_t nin = 1;    // inputs summed per output row
+    size_t nsets = 1;  // IR rows per version
+    size_t L = 0, block = 0, max_push = 0;
+    int shared_ir = 0;
+    tc_precision prec = TC_FP32;
+    int device = 0;
+
+    cudaStream_t own_cs = nullptr;
+    cudaStream_t cs = nullptr;
+
+    // Stream state.
+    long long pos = 0;
+    long long base = 0;
+    int state = ST_OPEN;
+    long long pos_end_hint = -1;  // number of real input samples (set at flush), for MAC counting
+
+    // History.
+    float *hist = nullptr;
+    long long cap = 0;
+    long long keep = 0;
+
+    // IR slots.
+    int nslots = 4;
+    long long Lpad = 0;
+    float *ir = nullptr;
+    float *ir_stage = nullptr;  // device staging for host IR uploads [nsets][L]
+    float *pin_ir = nullptr;    // pinned staging [nsets][L]
+    cudaEvent_t ev_ir = nullptr;
+    bool ir_ever_set = false;
+
+    // Versions.
+    std::vector<Version> vt;
+    std::vector<char> slot_used;
+    DevTable *d_vt = nullptr;
+    DevTable *pin_vt = nullptr;
+    cudaEvent_t ev_vt = nullptr;
+    bool vt_dirty = false;
+
+    // Host-pointer staging.
+    float *pin_x = nullptr;   // [rows][max_push]
+    float *pin_y = nullptr;   // [items][max_push]
+    float *d_y = nullptr;     // [items][max_push]
+    cudaEvent_t ev_x = nullptr;
+    int *pin_err = nullptr;
+
+    // K1 scratch.
+    float *partial = nullptr;
+    size_t partial_floats = 0;
+    unsigned *counter = nullptr;
+    size_t counter_n = 0;
+    int *d_err = nullptr;
+    int k1_variant_fixed = -1;  // -1: chosen per launch
+
+    // Kernel timing (tc_profile).
+    bool profile = false;
+    std::vector<cudaEvent_t> ev_pool;   // pairs (start, stop)
+    size_t ev_used = 0;                 // events in use, even
+    double prof_macs = 0.0;
+    uint64_t prof_launches = 0;
+};
+
+namespace {
+
+tc_status check_stream(const tc_stream *s)
+{
+    if (!s)
+        return fail(TC_EINVAL, "stream is NULL");
+    return TC_OK;
+}
+
+tc_status use_device(const tc_stream *s)
+{
+    int cur = -1;
+    TC_CU(cudaGetDevice(&cur));
+    if (cur != s->device)
+        TC_CU(cudaSetDevice(s->device));
+    return TC_OK;
+}
+
+// Tap chunk variant for a launch: the largest S that still fills the GPU with
+// a few waves of CTAs and keeps at most K1_MAX_CHUNKS partials per tile.
+int pick_variant(const tc_stream *s, long long ntile, int e)
+{
+    if (s->k1_variant_fixed >= 0)
+        return s->k1_variant_fixed;
+    static const int order[] = {tc::K1_S260, tc::K1_S100, tc::K1_S60, tc::K1_S20};
+    int fallback = -1;
+    for (int v : order) {
+        const long long kc = tc::k1_chunk_taps(v);
+        const long long nchunk = (s->L + e + kc - 1) / kc;
+        const long long ctot = nchunk * (long long)s->nin;
+        if (ctot > tc::K1_MAX_CHUNKS)
+            continue;
+        const long long ctas = ctot * ntile * (long long)s->items;
+        fallback = v;
+        if (ctas >= 8LL * 152)
+            return v;
+    }
+    return fallback;
+}
+
+long long max_ctot(const tc_stream *s)
+{
+    long long m = 0;
+    for (int v = 0; v < tc::K1_NVARIANTS; ++v) {
+        const long long kc = tc::k1_chunk_taps(v);
+        const long long ctot = ((long long)s->L + 3 + kc - 1) / kc * (long long)s->nin;
+        if (ctot <= tc::K1_MAX_CHUNKS)
+            m = std::max(m, ctot);
+    }
+    return m;
+}
+
+void free_all(tc_stream *s)
+{
+    if (s->cs)
+        cudaStreamSynchronize(s->cs);
+    cudaFree(s->hist);
+    cudaFree(s->ir);
+    cudaFree(s->ir_stage);
+    cudaFree(s->d_vt);
+    cudaFree(s->d_y);
+    cudaFree(s->partial);
+    cudaFree(s->counter);
+    cudaFree(s->d_err);
+    cudaFreeHost(s->pin_ir);
+    cudaFreeHost(s->pin_vt);
+    cudaFreeHost(s->pin_x);
+    cudaFreeHost(s->pin_y);
+    cudaFreeHost(s->pin_err);
+    if (s->ev_ir)
+        cudaEventDestroy(s->ev_ir);
+    if (s->ev_vt)
+        cudaEventDestroy(s->ev_vt);
+    if (s->ev_x)
+        cudaEventDestroy(s->ev_x);
+    for (cudaEvent_t e : s->ev_pool)
+        cudaEventDestroy(e);
+    if (s->own_cs)
+        cudaStreamDestroy(s->own_cs);
+}
+
+tc_status alloc_ir(tc_stream *s)
+{
+    if (s->ir) {
+        TC_CU(cudaStreamSynchronize(s->cs));
+        TC_CU(cudaFree(s->ir));
+        s->ir = nullptr;
+    }
+    const size_t floats = (size_t)s->nslots * s->nsets * 4 * (size_t)s->Lpad;
+    TC_CU(cudaMalloc(&s->ir, floats * sizeof(float)));
+    TC_CU(cudaMemsetAsync(s->ir, 0, floats * sizeof(float), s->cs));
+    s->slot_used.assign((size_t)s->nslots, 0);
+    return TC_OK;
+}
+
+tc_status clear_state(tc_stream *s)
+{
+    s->pos = 0;
+    s->base = -s->keep;
+    s->state = ST_OPEN;
+    s->pos_end_hint = -1;
+    s->vt.clear();
+    std::fill(s->slot_used.begin(), s->slot_used.end(), 0);
+    s->vt_dirty = true;
+    s->ir_ever_set = false;
+    TC_CU(cudaMemsetAsync(s->hist, 0, (size_t)s->rows * s->cap * sizeof(float), s->cs));
+    TC_CU(cudaMemsetAsync(s->counter, 0, s->counter_n * sizeof(unsigned), s->cs));
+    TC_CU(cudaMemsetAsync(s->d_err, 0, sizeof(int), s->cs));
+    return TC_OK;
+}
+
+tc_status open_common(tc_stream *s)
+{
+    TC_CU(cudaGetDevice(&s->device));
+    TC_CU(cudaStreamCreateWithFlags(&s->own_cs, cudaStreamNonBlocking));
+    s->cs = s->own_cs;
+    TC_CU(cudaEventCreateWithFlags(&s->ev_ir, cudaEventDisableTiming));
+    TC_CU(cudaEventCreateWithFlags(&s->ev_vt, cudaEventDisableTiming));
+    TC_CU(cudaEventCreateWithFlags(&s->ev_x, cudaEventDisableTiming));
+
+    // History row: `keep` samples behind the next push (L taps plus the
+    // largest tap chunk and alignment), the push itself, and one output tile
+    // of overrun. Doubled so that a compaction copy never overlaps itself.
+    s->keep = round_up((long long)s->L + tc::K1_KC_MAX + 8, 4);
+    s->cap = round_up(2 * s->keep + (long long)s->max_push + tc::K1_MO + 160, 64);
+    TC_CU(cudaMalloc(&s->hist, (size_t)s->rows * s->cap * sizeof(float)));
+
+    s->Lpad = round_up((long long)s->L + 4 + tc::K1_KC_MAX, 4);
+    TC_TRY(alloc_ir(s));
+    TC_CU(cudaMalloc(&s->ir_stage, s->nsets * s->L * sizeof(float)));
+    TC_CU(cudaHostAlloc(&s->pin_ir, s->nsets * s->L * sizeof(float), cudaHostAllocDefault));
+
+    TC_CU(cudaMalloc(&s->d_vt, sizeof(DevTable)));
+    TC_CU(cudaHostAlloc(&s->pin_vt, sizeof(DevTable), cudaHostAllocDefault));
+    std::memset(s->pin_vt, 0, sizeof(DevTable));
+
+    TC_CU(cudaHostAlloc(&s->pin_x, s->rows * s->max_push * sizeof(float), cudaHostAllocDefault));
+    TC_CU(cudaHostAlloc(&s->pin_y, s->items * s->max_push * sizeof(float), cudaHostAllocDefault));
+    TC_CU(cudaMalloc(&s->d_y, s->items * s->max_push * sizeof(float)));
+    TC_CU(cudaHostAlloc(&s->pin_err, sizeof(int), cudaHostAllocDefault));
+    *s->pin_err = 0;
+
+    const long long ntile = (long long)((s->max_push + tc::K1_MO - 1) / tc::K1_MO);
+    s->counter_n = (size_t)(ntile * (long long)s->items);
+    s->partial_floats = (size_t)(ntile * (long long)s->items * max_ctot(s) * tc::K1_MO);
+    TC_CU(cudaMalloc(&s->partial, std::max<size_t>(s->partial_floats, 1) * sizeof(float)));
+    TC_CU(cudaMalloc(&s->counter, s->counter_n * sizeof(unsigned)));
+    TC_CU(cudaMalloc(&s->d_err, sizeof(int)));
+    TC_TRY(clear_state(s));
+    TC_CU(cudaStreamSynchronize(s->cs));
+    return TC_OK;
+}
+
+tc_status open_any(int kind, size_t rows, size_t items, size_t nin, size_t nsets, size_t L, size_t block,
+                   int shared_ir, tc_precision prec, size_t max_push, tc_stream **out)
+{
+    if (!out)
+        return fail(TC_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (L == 0 || block == 0 || rows == 0 || items == 0)
+        return fail(TC_EINVAL, "L, block and channel counts must be > 0");
+    if (max_push == 0)
+        max_push = block;
+    if (max_push < block)
+        return fail(TC_EINVAL, "max_push (%zu) < block (%zu)", max_push, block);
+    if (L > (size_t)1 << 30 || max_push > (size_t)1 << 28 || rows > (size_t)1 << 20)
+        return fail(TC_EINVAL, "size out of range");
+    if (prec != TC_FP32 && prec != TC_BF16 && prec != TC_BF16_SPLIT)
+        return fail(TC_EINVAL, "unknown precision %d", (int)prec);
+    if (prec != TC_FP32)
+        return fail(TC_EUNSUPPORTED, "BF16 tensor-core path is not available for this stream kind");
+    tc_stream *s = new (std::nothrow) tc_stream();
+    if (!s)
+        return fail(TC_ENOMEM, "host allocation failed");
+    s->kind = kind;
+    s->rows = rows;
+    s->items = items;
+    s->nin = nin;
+    s->nsets = nsets;
+    s->L = L;
+    s->block = block;
+    s->max_push = max_push;
+    s->shared_ir = shared_ir;
+    s->prec = prec;
+    tc_status st = open_common(s);
+    if (st != TC_OK) {
+        std::string msg = g_err;
+        free_all(s);
+        delete s;
+        g_err = msg;
+        return st;
+    }
+    *out = s;
+    return TC_OK;
+}
+
+// Drops versions whose samples can no longer reach a future output: version v
+// is dead once the next version starts at or before pos - L + 1.
+void retire_versions(tc_stream *s)
+{
+    const long long oldest_needed = s->pos - (long long)s->L + 1;
+    size_t drop = 0;
+    while (drop + 1 < s->vt.size() && s->vt[drop + 1].start <= oldest_needed)
+        ++drop;
+    for (size_t i = 0; i < drop; ++i)
+        s->slot_used[(size_t)s->vt[i].slot] = 0;
+    if (drop) {
+        s->vt.erase(s->vt.begin(), s->vt.begin() + (long)drop);
+        s->vt_dirty = true;
+    }
+}
+
+tc_status upload_table(tc_stream *s)
+{
+    if (!s->vt_dirty)
+        return TC_OK;
+    TC_CU(cudaEventSynchronize(s->ev_vt));  // the previous upload has read the mirror
+    DevTable &t = *s->pin_vt;
+    std::memset(&t, 0, sizeof t);
+    t.nver = (int)s->vt.size();
+    for (size_t i = 0; i < s->vt.size(); ++i) {
+        t.vstart[i] = s->vt[i].start;
+        t.vslot[i] = s->vt[i].slot;
+    }
+    TC_CU(cudaMemcpyAsync(s->d_vt, &t, sizeof t, cudaMemcpyHostToDevice, s->cs));
+    TC_CU(cudaEventRecord(s->ev_vt, s->cs));
+    s->vt_dirty = false;
+    return TC_OK;
+}
+
+tc_status set_ir_impl(tc_stream *s, const float *h, size_t n, long long sample, bool rows_given,
+                      bool on_device)
+{
+    TC_TRY(check_stream(s));
+    if (!h)
+        return fail(TC_EINVAL, "h is NULL");
+    if (n == 0 || n > s->L)
+        return fail(TC_EINVAL, "IR length %zu not in [1, L=%zu]", n, s->L);
+    if (s->state != ST_OPEN)
+        return fail(TC_ESTATE, "stream has ended; reset it first");
+    if (sample < s->pos)
+        return fail(TC_EINVAL, "IR switch at sample %lld is before the next sample to push (%lld)", sample,
+                    s->pos);
+    if (!s->vt.empty() && sample < s->vt.back().start)
+        return fail(TC_EINVAL, "IR switch at sample %lld is before the latest version (%lld)", sample,
+                    s->vt.back().start);
+    TC_TRY(use_device(s));
+    retire_versions(s);
+
+    int slot = -1;
+    const bool replace = !s->vt.empty() && s->vt.back().start == sample;
+    if (replace) {
+        slot = s->vt.back().slot;
+    } else {
+        for (int i = 0; i < s->nslots; ++i)
+            if (!s->slot_used[(size_t)i]) {
+                slot = i;
+                break;
+            }
+        if (slot < 0)
+            return fail(TC_ENOMEM,
+                        "all %d IR slots hold live versions (a version stays live until L-1 samples after the "
+                        "next one starts); raise tc_set_max_versions",
+                        s->nslots);
+    }
+
+    // Source rows: [nsets][n]. A single host IR is replicated to every set.
+    const size_t sets = s->nsets;
+    const float *src = h;
+    long long src_pitch = (long long)n;
+    if (!on_device) {
+        TC_CU(cudaEventSynchronize(s->ev_ir));
+        if (rows_given) {
+            std::memcpy(s->pin_ir, h, sets * n * sizeof(float));
+            TC_CU(cudaMemcpyAsync(s->ir_stage, s->pin_ir, sets * n * sizeof(float), cudaMemcpyHostToDevice,
+                                  s->cs));
+        } else {
+            std::memcpy(s->pin_ir, h, n * sizeof(float));
+            TC_CU(cudaMemcpyAsync(s->ir_stage, s->pin_ir, n * sizeof(float), cudaMemcpyHostToDevice, s->cs));
+            src_pitch = 0;  // every set reads row 0
+        }
+        TC_CU(cudaEventRecord(s->ev_ir, s->cs));
+        src = s->ir_stage;
+    }
+    float *dst = s->ir + (size_t)slot * sets * 4 * (size_t)s->Lpad;
+    TC_CU(tc::ir_prep_launch(src, src_pitch, (long long)n, (int)sets, dst, 4 * s->Lpad, s->Lpad, s->Lpad, s->cs));
+
+    if (!replace) {
+        s->vt.push_back(Version{sample, slot});
+        s->slot_used[(size_t)slot] = 1;
+    }
+    s->vt_dirty = true;
+    s->ir_ever_set = true;
+    return TC_OK;
+}
+
+// Makes room in the history rows for n more samples (plus tile overrun).
+tc_status ensure_room(tc_stream *s, long long n)
+{
+    if (s->pos + n + tc::K1_MO + 8 <= s->base + s->cap)
+        return TC_OK;
+    const long long nb = floor4(s->pos - s->keep);
+    const long long len = s->pos - nb;
+    const long long shift = nb - s->base;
+    if (shift < len || len + n + tc::K1_MO + 8 > s->cap)
+        return fail(TC_EINVAL, "internal: history compaction would overlap");
+    TC_CU(cudaMemcpy2DAsync(s->hist, (size_t)s->cap * sizeof(float), s->hist + shift,
+                            (size_t)s->cap * sizeof(float), (size_t)len * sizeof(float), s->rows,
+                            cudaMemcpyDeviceToDevice, s->cs));
+    s->base = nb;
+    return TC_OK;
+}
+
+tc_status launch_k1(tc_stream *s, long long t0, long long nout, float *y, long long y_pitch)
+{
+    tc::K1Params p{};
+    p.hist = s->hist;
+    p.pitch = s->cap;
+    p.base = s->base;
+    const bool mimo = s->kind == KIND_MIMO;
+    p.x_item_rows = mimo ? 0 : 1;
+    p.x_in_rows = mimo ? 1 : 0;
+    p.ir = s->ir;
+    p.ir_slot = (long long)s->nsets * 4 * s->Lpad;
+    p.ir_item = s->shared_ir ? 0 : (mimo ? (long long)s->nin * 4 * s->Lpad : 4 * s->Lpad);
+    p.ir_in = mimo ? 4 * s->Lpad : 0;
+    p.ir_phase = s->Lpad;
+    p.L = (int)s->L;
+    p.vstart = s->d_vt->vstart;
+    p.vslot = s->d_vt->vslot;
+    p.nver = &s->d_vt->nver;
+    p.vt_item = 0;
+    p.nitems = (int)s->items;
+    p.nin = (int)s->nin;
+    p.t0 = t0;
+    p.nout = (int)nout;
+    p.ntile = (int)((nout + tc::K1_MO - 1) / tc::K1_MO);
+    p.e = tc::k1_shift_e(t0, s->base);
+    const int variant = pick_variant(s, p.ntile, p.e);
+    if (variant < 0)
+        return fail(TC_EUNSUPPORTED, "IR too long for the FP32 gather (more than %d tap chunks per tile)",
+                    tc::K1_MAX_CHUNKS);
+    const long long kc = tc::k1_chunk_taps(variant);
+    p.nchunk = (int)(((long long)s->L + p.e + kc - 1) / kc);
+    p.y = y;
+    p.y_pitch = y_pitch;
+    p.partial = s->partial;
+    p.counter = s->counter;
+    p.err = s->d_err;
+    const size_t need = (size_t)p.ntile * s->items * (size_t)(p.nin * p.nchunk) * tc::K1_MO;
+    if ((size_t)p.ntile * s->items > s->counter_n || (p.nin * p.nchunk > 1 && need > s->partial_floats))
+        return fail(TC_EINVAL, "internal: K1 scratch too small");
+    cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+    if (s->profile) {
+        while (s->ev_pool.size() < s->ev_used + 2) {
+            cudaEvent_t e;
+            TC_CU(cudaEventCreate(&e));
+            s->ev_pool.push_back(e);
+        }
+        ev_a = s->ev_pool[s->ev_used];
+        ev_b = s->ev_pool[s->ev_used + 1];
+        s->ev_used += 2;
+        TC_CU(cudaEventRecord(ev_a, s->cs));
+    }
+    TC_CU(tc::k1_launch(p, variant, s->cs));
+    if (s->profile) {
+        TC_CU(cudaEventRecord(ev_b, s->cs));
+        // Useful multiply-adds: output m sees the taps k < L with 0 <= m - k < n_end,
+        // where n_end is the number of real input samples (all pushed samples
+        // before a flush, the end of the input during one).
+        const long long n_end = s->pos_end_hint >= 0 ? s->pos_end_hint : t0 + nout;
+        double macs = 0.0;
+        for (long long m = t0; m < t0 + nout; ++m) {
+            const long long hi = std::min<long long>(m, (long long)s->L - 1);
+            const long long lo = std::max<long long>(0, m - n_end + 1);
+            if (hi >= lo)
+                macs += (double)(hi - lo + 1);
+        }
+        s->prof_macs += macs * (double)s->items * (double)s->nin;
+        s->prof_launches += 1;
+    }
+    return TC_OK;
+}
+
+tc_status check_err_word(tc_stream *s)
+{
+    if (*s->pin_err) {
+        const int w = *s->pin_err;
+        *s->pin_err = 0;
+        cudaMemsetAsync(s->d_err, 0, sizeof(int), s->cs);
+        cudaMemsetAsync(s->counter, 0, s->counter_n * sizeof(unsigned), s->cs);
+        return fail(TC_ETIMEOUT, "a kernel's bounded wait gave up (device error word 0x%x)", w);
+    }
+    return TC_OK;
+}
+
+tc_status push_impl(tc_stream *s, const float *x, size_t n, float *y, bool on_device, size_t limit)
+{
+    TC_TRY(check_stream(s));
+    if (!x || !y)
+        return fail(TC_EINVAL, "x or y is NULL");
+    if (n == 0 || n > limit)
+        return fail(TC_EINVAL, "n = %zu not in [1, %zu]", n, limit);
+    if (s->state != ST_OPEN)
+        return fail(TC_ESTATE, "stream has ended (short last block or flush); reset it first");
+    if (s->vt.empty() || s->vt.front().start > s->pos)
+        return fail(TC_ESTATE, "no IR covers input sample %lld; call tc_set_ir first", s->pos);
+    TC_TRY(use_device(s));
+    retire_versions(s);
+    TC_TRY(ensure_room(s, (long long)n));
+
+    float *hist_at = s->hist + (s->pos - s->base);
+    const size_t pitch_b = (size_t)s->cap * sizeof(float);
+    const size_t row_b = n * sizeof(float);
+    if (on_device) {
+        TC_CU(cudaMemcpy2DAsync(hist_at, pitch_b, x, row_b, row_b, s->rows, cudaMemcpyDeviceToDevice, s->cs));
+    } else {
+        TC_CU(cudaEventSynchronize(s->ev_x));
+        std::memcpy(s->pin_x, x, s->rows * row_b);
+        TC_CU(cudaMemcpy2DAsync(hist_at, pitch_b, s->pin_x, row_b, row_b, s->rows, cudaMemcpyHostToDevice, s->cs));
+        TC_CU(cudaEventRecord(s->ev_x, s->cs));
+    }
+    TC_TRY(upload_table(s));
+    float *ydst = on_device ? y : s->d_y;
+    TC_TRY(launch_k1(s, s->pos, (long long)n, ydst, (long long)n));
+    s->pos += (long long)n;
+    if (n % s->block != 0)
+        s->state = ST_ENDED;
+    if (!on_device) {
+        TC_CU(cudaMemcpyAsync(s->pin_y, s->d_y, s->items * row_b, cudaMemcpyDeviceToHost, s->cs));
+        TC_CU(cudaMemcpyAsync(s->pin_err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->cs));
+        TC_CU(cudaStreamSynchronize(s->cs));
+        TC_TRY(check_err_word(s));
+        std::memcpy(y, s->pin_y, s->items * row_b);
+    }
+    return TC_OK;
+}
+
+// Emits the L-1 tail into device rows y (pitch y_pitch floats) by pushing
+// zeros through the gather in pieces of at most max_push samples.
+tc_status flush_to_device(tc_stream *s, float *y, long long y_pitch)
+{
+    const long long tail = (long long)s->L - 1;
+    s->pos_end_hint = s->pos;
+    for (long long off = 0; off < tail;) {
+        const long long piece = std::min<long long>(tail - off, (long long)s->max_push);
+        TC_TRY(ensure_room(s, piece));
+        TC_CU(cudaMemset2DAsync(s->hist + (s->pos - s->base), (size_t)s->cap * sizeof(float), 0,
+                                (size_t)piece * sizeof(float), s->rows, s->cs));
+        TC_TRY(upload_table(s));
+        TC_TRY(launch_k1(s, s->pos, piece, y + off, y_pitch));
+        s->pos += piece;
+        off += piece;
+    }
+    s->state = ST_FLUSHED;
+    return TC_OK;
+}
+
+tc_status flush_checks(tc_stream *s)
+{
+    TC_TRY(check_stream(s));
+    if (s->state == ST_FLUSHED)
+        return fail(TC_ESTATE, "stream already flushed; reset it first");
+    if (!s->ir_ever_set)
+        return fail(TC_ESTATE, "no IR was set");
+    return TC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tc_status tc_open_stream(size_t L, size_t block, tc_stream **out)
+{
+    return open_any(KIND_GROUP, 1, 1, 1, 1, L, block, 1, TC_FP32, block, out);
+}
+
+tc_status tc_open_group(size_t channels, size_t L, size_t block, int shared_ir, tc_precision precision,
+                        size_t max_push, tc_stream **out)
+{
+    const size_t sets = shared_ir ? 1 : channels;
+    return open_any(KIND_GROUP, channels, channels, 1, sets, L, block, shared_ir ? 1 : 0, precision, max_push,
+                    out);
+}
+
+tc_status tc_open_mimo(size_t nin, size_t nout, size_t L, size_t block, tc_precision precision, size_t max_push,
+                       tc_stream **out)
+{
+    return open_any(KIND_MIMO, nin, nout, nin, nin * nout, L, block, 0, precision, max_push, out);
+}
+
+tc_status tc_close(tc_stream *s)
+{
+    if (!s)
+        return TC_OK;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    const int dev = s->device;
+    if (cur != dev)
+        cudaSetDevice(dev);
+    free_all(s);
+    delete s;
+    if (cur >= 0 && cur != dev)
+        cudaSetDevice(cur);
+    return TC_OK;
+}
+
+tc_status tc_reset(tc_stream *s)
+{
+    TC_TRY(check_stream(s));
+    TC_TRY(use_device(s));
+    // Stream-ordered: the memsets run after the stream's earlier work.
+    TC_TRY(clear_state(s));
+    return TC_OK;
+}
+
+tc_status tc_set_max_versions(tc_stream *s, int max_versions)
+{
+    TC_TRY(check_stream(s));
+    if (max_versions < 2 || max_versions > kMaxVersions)
+        return fail(TC_EINVAL, "max_versions must be in [2, %d]", kMaxVersions);
+    if (s->ir_ever_set)
+        return fail(TC_ESTATE, "max_versions can only change before the first IR is set");
+    TC_TRY(use_device(s));
+    s->nslots = max_versions;
+    return alloc_ir(s);
+}
+
+tc_status tc_set_cuda_stream(tc_stream *s, void *cuda_stream)
+{
+    TC_TRY(check_stream(s));
+    TC_TRY(use_device(s));
+    cudaStream_t next = cuda_stream ? (cudaStream_t)cuda_stream : s->own_cs;
+    if (next != s->cs) {
+        // Order the new stream after everything already enqueued on the old one.
+        TC_CU(cudaStreamSynchronize(s->cs));
+        s->cs = next;
+    }
+    return TC_OK;
+}
+
+tc_status tc_get_info(const tc_stream *s, tc_info *info)
+{
+    TC_TRY(check_stream(s));
+    if (!info)
+        return fail(TC_EINVAL, "info is NULL");
+    info->channels = s->rows;
+    info->outputs = s->items;
+    info->L = s->L;
+    info->block = s->block;
+    info->max_push = s->max_push;
+    info->pushed = (uint64_t)s->pos;
+    info->shared_ir = s->shared_ir;
+    info->precision = (int)s->prec;
+    info->state = s->state;
+    info->max_versions = s->nslots;
+    return TC_OK;
+}
+
+tc_status tc_set_ir(tc_stream *s, const float *h, size_t n)
+{
+    if (!s)
+        return fail(TC_EINVAL, "stream is NULL");
+    return set_ir_impl(s, h, n, s->pos, false, false);
+}
+
+tc_status tc_set_ir_at(tc_stream *s, const float *h, size_t n, uint64_t sample)
+{
+    if (sample > (uint64_t)1 << 62)
+        return fail(TC_EINVAL, "sample out of range");
+    return set_ir_impl(s, h, n, (long long)sample, false, false);
+}
+
+tc_status tc_set_ir_rows(tc_stream *s, const float *h, size_t n, uint64_t sample, int h_on_device)
+{
+    if (sample > (uint64_t)1 << 62)
+        return fail(TC_EINVAL, "sample out of range");
+    return set_ir_impl(s, h, n, (long long)sample, true, h_on_device != 0);
+}
+
+tc_status tc_push_block(tc_stream *s, const float *x, size_t n, float *y)
+{
+    if (!s)
+        return fail(TC_EINVAL, "stream is NULL");
+    return push_impl(s, x, n, y, false, s->block);
+}
+
+tc_status tc_push(tc_stream *s, const float *x, size_t n, float *y, int on_device)
+{
+    if (!s)
+        return fail(TC_EINVAL, "stream is NULL");
+    return push_impl(s, x, n, y, on_device != 0, s->max_push);
+}
+
+tc_status tc_flush(tc_stream *s, float *y, size_t cap, size_t *n_out)
+{
+    TC_TRY(flush_checks(s));
+    if (!y)
+        return fail(TC_EINVAL, "y is NULL");
+    const size_t tail = s->L - 1;
+    if (cap < tail)
+        return fail(TC_EINVAL, "cap %zu < L-1 = %zu", cap, tail);
+    TC_TRY(use_device(s));
+    if (n_out)
+        *n_out = tail;
+    if (tail == 0) {
+        s->state = ST_FLUSHED;
+        return TC_OK;
+    }
+    float *d = nullptr;
+    TC_CU(cudaMalloc(&d, s->items * tail * sizeof(float)));
+    tc_status st = flush_to_device(s, d, (long long)tail);
+    if (st == TC_OK) {
+        cudaError_t e = cudaMemcpy2DAsync(y, cap * sizeof(float), d, tail * sizeof(float), tail * sizeof(float),
+                                          s->items, cudaMemcpyDeviceToHost, s->cs);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(s->pin_err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->cs);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(s->cs);
+        if (e != cudaSuccess)
+            st = fail(TC_ECUDA, "flush copy: %s", cudaGetErrorString(e));
+        else
+            st = check_err_word(s);
+    }
+    cudaFree(d);
+    return st;
+}
+
+tc_status tc_flush_dev(tc_stream *s, float *y, size_t *n_out)
+{
+    TC_TRY(flush_checks(s));
+    if (!y)
+        return fail(TC_EINVAL, "y is NULL");
+    TC_TRY(use_device(s));
+    const size_t tail = s->L - 1;
+    if (n_out)
+        *n_out = tail;
+    if (tail == 0) {
+        s->state = ST_FLUSHED;
+        return TC_OK;
+    }
+    return flush_to_device(s, y, (long long)tail);
+}
+
+tc_status tc_sync(tc_stream *s)
+{
+    TC_TRY(check_stream(s));
+    TC_TRY(use_device(s));
+    TC_CU(cudaMemcpyAsync(s->pin_err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->cs));
+    TC_CU(cudaStreamSynchronize(s->cs));
+    return check_err_word(s);
+}
+
+tc_status tc_convolve(const float *x, size_t N, const float *h, size_t L, float *y, void *cuda_stream)
+{
+    if (!x || !h || !y)
+        return fail(TC_EINVAL, "x, h or y is NULL");
+    if (N == 0 || L == 0)
+        return fail(TC_EINVAL, "N and L must be > 0");
+    const size_t chunk = std::min<size_t>(N, (size_t)1 << 20);
+    tc_stream *s = nullptr;
+    TC_TRY(open_any(KIND_GROUP, 1, 1, 1, 1, L, chunk, 1, TC_FP32, chunk, &s));
+    tc_status st = TC_OK;
+    cudaStream_t cs = (cudaStream_t)cuda_stream;
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+        st = fail(TC_ECUDA, "event create failed");
+    // Start after the caller's stream has produced x and h.
+    if (st == TC_OK && (cudaEventRecord(ev, cs) != cudaSuccess || cudaStreamWaitEvent(s->cs, ev, 0) != cudaSuccess))
+        st = fail(TC_ECUDA, "stream ordering failed");
+    if (st == TC_OK)
+        st = set_ir_impl(s, h, L, 0, true, true);
+    for (size_t off = 0; st == TC_OK && off < N; off += chunk) {
+        const size_t n = std::min(chunk, N - off);
+        // A partial chunk may only come last; the stream block is `chunk`.
+        st = push_impl(s, x + off, n, y + off, true, chunk);
+    }
+    if (st == TC_OK && L > 1)
+        st = flush_to_device(s, y + N, (long long)(L - 1));
+    if (st == TC_OK)
+        st = tc_sync(s);
+    if (st == TC_OK && (cudaEventRecord(ev, s->cs) != cudaSuccess || cudaStreamWaitEvent(cs, ev, 0) != cudaSuccess))
+        st = fail(TC_ECUDA, "stream ordering failed");
+    std::string msg = g_err;
+    if (ev)
+        cudaEventDestroy(ev);
+    tc_close(s);
+    g_err = msg;
+    return st;
+}
+
+const char *tc_last_error(void) { return g_err.c_str(); }
+
+const char *tc_status_str(tc_status st)
+{
+    switch (st) {
+    case TC_OK: return "TC_OK";
+    case TC_EINVAL: return "TC_EINVAL";
+    case TC_ENOMEM: return "TC_ENOMEM";
+    case TC_ESTATE: return "TC_ESTATE";
+    case TC_ECUDA: return "TC_ECUDA";
+    case TC_ETIMEOUT: return "TC_ETIMEOUT";
+    case TC_EUNSUPPORTED: return "TC_EUNSUPPORTED";
+    default: return "TC_UNKNOWN";
+    }
+}
+
+uint64_t tc_kernel_launches(void) { return tc::launches(); }
+
+tc_status tc_profile(tc_stream *s, int enable)
+{
+    TC_TRY(check_stream(s));
+    s->profile = enable != 0;
+    return TC_OK;
+}
+
+tc_status tc_profile_read(tc_stream *s, double *ms, uint64_t *launches, double *useful_macs)
+{
+    TC_TRY(check_stream(s));
+    TC_TRY(use_device(s));
+    TC_CU(cudaStreamSynchronize(s->cs));
+    double tot = 0.0;
+    for (size_t i = 0; i + 1 < s->ev_used; i += 2) {
+        float e = 0.f;
+        TC_CU(cudaEventElapsedTime(&e, s->ev_pool[i], s->ev_pool[i + 1]));
+        tot += e;
+    }
+    if (ms)
+        *ms = tot;
+    if (launches)
+        *launches = s->prof_launches;
+    if (useful_macs)
+        *useful_macs = s->prof_macs;
+    s->ev_used = 0;
+    s->prof_launches = 0;
+    s->prof_macs = 0.0;
+    return TC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,56 @@
+// k_prep.cu -- IR preparation for K1: four copies of each IR row, shifted by
+// e = 0..3 taps and zero-padded, so that every tap chunk that K1 stages
+// starts on a 16-byte boundary whatever the output alignment.
+#include <atomic>
+
+#include "tc_internal.h"
+
+namespace tc {
+
+namespace {
+
+std::atomic<uint64_t> g_launches{0};
+
+__global__ void ir_prep_kernel(const float *__restrict__ src, long long src_pitch, long long n, int rows,
+                               float *__restrict__ dst, long long row_stride, long long phase, long long Lpad)
+{
+    // One float4 of one shifted copy per thread iteration.
+    const long long per_row = 4 * (Lpad / 4);
+    const long long total = (long long)rows * 4 * per_row;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const long long r = q / (4 * per_row);
+        const long long rem = q % (4 * per_row);
+        const int e = (int)(rem / per_row);
+        const long long j0 = 4 * (rem % per_row);
+        const float *s = src + r * src_pitch;
+        float v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const long long k = j0 + u - e;
+            v[u] = (k >= 0 && k < n) ? s[k] : 0.f;
+        }
+        *reinterpret_cast<float4 *>(dst + r * row_stride + e * phase + j0) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+}
+
+}  // namespace
+
+cudaError_t ir_prep_launch(const float *src, long long src_pitch, long long n, int rows, float *dst,
+                           long long row_stride, long long phase, long long Lpad, cudaStream_t st)
+{
+    if ((Lpad & 3) || (phase & 3) || (row_stride & 3) || rows < 1 || n < 1 || n > Lpad)
+        return cudaErrorInvalidValue;
+    const long long work = (long long)rows * Lpad;  // float4 items
+    long long blocks = (work + 255) / 256;
+    if (blocks > 4096)
+        blocks = 4096;
+    ir_prep_kernel<<<(unsigned)blocks, 256, 0, st>>>(src, src_pitch, n, rows, dst, row_stride, phase, Lpad);
+    count_launch();
+    return cudaGetLastError();
+}
+
+void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+uint64_t launches() { return g_launches.load(std::memory_order_relaxed); }
+
+}  // namespace tc

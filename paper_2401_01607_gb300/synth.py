@@ -99,15 +99,16 @@ def mono(N: int = 48_000, L: int = 4096, block: int = 64, tau: float = 800.0) ->
 
 
 def multi(C: int = 64, N: int = 480_000, L: int = 48_000, block: int = 128,
-          swap_every: int = 24_000, tau: float | None = None) -> Workload:
-    """Independent streams with their own IRs, each replaced every swap_every samples (workload 2)."""
+          swap_every: int = 24_000, tau: float | None = None, stream0: int = 0) -> Workload:
+    """Independent streams with their own IRs, each replaced every swap_every samples (workload 2).
+    Streams are numbered from stream0 (a shard of a larger set uses its own seeds)."""
     tau = 0.3 * L if tau is None else tau
     nver = max(1, -(-N // swap_every)) if swap_every else 1
-    x = audio_block(C, N, x_seed(2, 0))
+    x = audio_block(C, N, x_seed(2, stream0))
     H = np.empty((C, nver, L), dtype=np.float32)
     for s in range(C):
         for v in range(nver):
-            H[s, v] = decayed_ir(L, tau, ir_seed(s, v))
+            H[s, v] = decayed_ir(L, tau, ir_seed(stream0 + s, v))
     vstart = (np.arange(nver, dtype=np.int64) * swap_every) if swap_every else np.zeros(1, np.int64)
     return Workload("multi", x, H, vstart, L, block)
 

@@ -1,0 +1,211 @@
+"""FP32 gather (K1) through the C ABI against the FP64 oracle, element by element.
+
+Tolerance: relative L2 <= 1e-6 (FP32 path); max-abs is reported beside it.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_helpers import TOL, max_abs, rel_l2, stream_host
+from paper_2401_01607_gb300 import capi, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import paper_2401_01607_gb300 as pkg
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pkg.build()
+    capi.load()
+
+
+def _ref(x, H, vstart, block):
+    return oracle.buffer(x, H, np.asarray(vstart, np.int64), block)
+
+
+def test_mono_workload_full_size():
+    """Mono workload (48000 samples, L=4096, block 64), block by block, every output checked."""
+    w = synth.mono()
+    y = stream_host(w.x, w.H[0], w.vstart, w.L, w.block)
+    ref = _ref(w.x[0], w.H[0], w.vstart, w.block)
+    assert y.shape == (1, 48000 + 4096 - 1)
+    err = rel_l2(y[0], ref)
+    print(f"mono rel_l2={err:.3g} max_abs={max_abs(y[0], ref):.3g}")
+    assert err <= TOL["fp32"]
+
+
+def test_unit_impulse_is_exact():
+    L, B = 5000, 64
+    h = synth.decayed_ir(L, 1000.0, 7)
+    for n0 in (0, 37, 700):
+        x = np.zeros(1000, np.float32)
+        x[n0] = 1.0
+        y = stream_host(x, h[None], [0], L, B)[0]
+        ref = np.zeros(1000 + L - 1, np.float32)
+        ref[n0:n0 + L] = h
+        assert np.array_equal(y, ref), n0
+
+
+@pytest.mark.parametrize("N,L,B", [(1000, 1, 64), (777, 3, 5), (100, 257, 64), (333, 4096, 37), (64, 64, 64),
+                                   (5000, 700, 256), (129, 9000, 128), (2000, 31, 2000)])
+def test_ragged_shapes(N, L, B):
+    rng = np.random.default_rng(N * 7 + L)
+    x = rng.uniform(-1, 1, N).astype(np.float32)
+    h = synth.decayed_ir(L, max(1.0, 0.3 * L), N + L)
+    y = stream_host(x, h[None], [0], L, B)[0]
+    ref = _ref(x, h[None], [0], B)
+    assert y.shape == ref.shape
+    assert rel_l2(y, ref) <= TOL["fp32"], rel_l2(y, ref)
+
+
+@pytest.mark.parametrize("switches", [[0, 96], [0, 100], [0, 1, 2, 3], [0, 500, 501, 1500, 2900]])
+def test_ir_switch_per_sample(switches):
+    """IR replaced at exact samples, inside blocks and on block edges (abstract, Sec. 6)."""
+    N, L, B = 3000, 1500, 64
+    x = synth.audio(N, 11)
+    H = np.stack([synth.decayed_ir(L, 400.0, 100 + v) for v in range(len(switches))])
+    y = stream_host(x, H, switches, L, B)[0]
+    ref = _ref(x, H, switches, B)
+    assert rel_l2(y, ref) <= TOL["fp32"], rel_l2(y, ref)
+
+
+def test_multi_stream_group_with_swaps():
+    """Workload-2 recipe, shrunk: 8 streams, own IRs, swap every 3000 samples (odd swaps mid-block)."""
+    w = synth.multi(C=8, N=20_000, L=6_000, block=128, swap_every=3_000)
+    y = stream_host(w.x, w.H, w.vstart, w.L, w.block, max_push=1024)
+    for c in range(w.C):
+        ref = _ref(w.x[c], w.H[c], w.vstart, w.block)
+        assert rel_l2(y[c], ref) <= TOL["fp32"], (c, rel_l2(y[c], ref))
+
+
+def test_multi_block_push_matches_block_by_block():
+    """Nb and the push size change only timing (Sec. 5.2, Table 2)."""
+    N, L, B = 6000, 2500, 64
+    x = synth.audio(N, 5)
+    H = np.stack([synth.decayed_ir(L, 600.0, 40 + v) for v in range(2)])
+    vs = [0, 2222]
+    a = stream_host(x, H, vs, L, B)[0]
+    b = stream_host(x, H, vs, L, B, max_push=1024)[0]
+    c = stream_host(x, H, vs, L, B, pushes=[64, 128, 1024, 64, 640], max_push=1024)[0]
+    ref = _ref(x, H, vs, B)
+    for y in (a, b, c):
+        assert rel_l2(y, ref) <= TOL["fp32"]
+    assert rel_l2(a, b) <= 2 * TOL["fp32"]
+
+
+def test_long_ir_variant():
+    """L = 480000 taps (longest serving IR): sampled outputs against Eq. (4) one by one."""
+    N, L, B = 4096, 480_000, 256
+    x = synth.audio(N, 9)
+    h = synth.decayed_ir(L, 0.2 * L, 10)
+    y = stream_host(x, h[None], [0], L, B, max_push=4096)[0]
+    rng = np.random.default_rng(3)
+    idx = np.concatenate([rng.integers(0, N + L - 1, 64), [0, N - 1, N, N + L - 2]])
+    got = y[idx].astype(np.float64)
+    ref = np.array([oracle.direct_at(x, h[None], [0], int(m)) for m in idx])
+    assert rel_l2(got, ref) <= TOL["fp32"]
+
+
+def test_device_pointer_path_matches_host_path():
+    torch = pytest.importorskip("torch")
+    N, L, B, C = 4096, 3000, 128, 4
+    x = synth.audio_block(C, N, 77)
+    H = np.stack([synth.decayed_ir(L, 900.0, 300 + c) for c in range(C)])
+    host = stream_host(x, H[:, None], [0], L, B, max_push=512)
+    s = capi.tc_open_group(C, L, B, False, capi.TC_FP32, 512)
+    try:
+        capi.tc_set_ir_rows(s, torch.from_numpy(H).cuda(), L, 0, on_device=True)
+        xd = torch.from_numpy(x).cuda()
+        outs = []
+        for pos in range(0, N, 512):
+            xb = xd[:, pos:pos + 512].contiguous()
+            yb = torch.empty_like(xb)
+            capi.tc_push(s, xb, 512, yb, on_device=True)
+            outs.append(yb)
+        tail = torch.empty((C, L - 1), device="cuda")
+        capi.tc_flush_dev(s, tail)
+        capi.tc_sync(s)
+        dev = torch.cat(outs + [tail], dim=1).cpu().numpy()
+    finally:
+        capi.tc_close(s)
+    assert dev.shape == host.shape
+    assert rel_l2(dev, host) <= 1e-7
+
+
+def test_convolve_one_shot():
+    torch = pytest.importorskip("torch")
+    N, L = 10_000, 2_048
+    x = synth.audio(N, 1)
+    h = synth.decayed_ir(L, 500.0, 2)
+    y = torch.empty(N + L - 1, device="cuda")
+    capi.tc_convolve(torch.from_numpy(x).cuda(), N, torch.from_numpy(h).cuda(), L, y)
+    ref = oracle.buffer(x, h[None], None, 4096)
+    assert rel_l2(y.cpu().numpy(), ref) <= TOL["fp32"]
+
+
+def test_mimo_fp32():
+    nin, nout, N, L, B = 3, 2, 3000, 1000, 128
+    X = synth.audio_block(nin, N, 50)
+    H = np.stack([[synth.decayed_ir(L, 250.0, 60 + o * nin + i) for i in range(nin)] for o in range(nout)])
+    s = capi.tc_open_mimo(nin, nout, L, B, capi.TC_FP32, 512)
+    try:
+        capi.tc_set_ir_rows(s, np.ascontiguousarray(H), L, 0)
+        outs = []
+        for pos in range(0, N, 512):
+            n = min(512, N - pos)
+            y = np.empty((nout, n), np.float32)
+            capi.tc_push(s, np.ascontiguousarray(X[:, pos:pos + n]), n, y)
+            outs.append(y)
+        tail = np.empty((nout, L - 1), np.float32)
+        capi.tc_flush(s, tail, L - 1)
+        y = np.concatenate(outs + [tail], axis=1)
+    finally:
+        capi.tc_close(s)
+    ref = oracle.mimo(X, H, None, B)
+    assert rel_l2(y, ref) <= TOL["fp32"], rel_l2(y, ref)
+
+
+def test_errors_are_status_codes():
+    L, B = 100, 16
+    s = capi.tc_open_stream(L, B)
+    try:
+        x = np.zeros(B, np.float32)
+        y = np.empty(B, np.float32)
+        with pytest.raises(capi.TcError) as e:
+            capi.tc_push_block(s, x, y)           # no IR yet
+        assert e.value.code == "TC_ESTATE"
+        h = np.ones(L, np.float32)
+        with pytest.raises(capi.TcError) as e:
+            capi.tc_set_ir(s, np.ones(L + 1, np.float32))  # longer than L
+        assert e.value.code == "TC_EINVAL"
+        capi.tc_set_ir(s, h)
+        with pytest.raises(capi.TcError) as e:
+            capi.tc_push_block(s, np.zeros(B + 1, np.float32), np.empty(B + 1, np.float32))
+        assert e.value.code == "TC_EINVAL"
+        capi.tc_push_block(s, x, y)
+        with pytest.raises(capi.TcError) as e:
+            capi.tc_set_ir_at(s, h, 3)                # in the past
+        assert e.value.code == "TC_EINVAL"
+        for k in range(1, 4):
+            capi.tc_set_ir_at(s, h, B + k)
+        with pytest.raises(capi.TcError) as e:
+            capi.tc_set_ir_at(s, h, B + 9)            # 4 live versions already
+        assert e.value.code == "TC_ENOMEM"
+        capi.tc_push_block(s, x[:5], y[:5])          # short block ends the stream
+        with pytest.raises(capi.TcError) as e:
+            capi.tc_push_block(s, x, y)
+        assert e.value.code == "TC_ESTATE"
+        tail = np.empty(L - 1, np.float32)
+        capi.tc_flush(s, tail, L - 1)
+        with pytest.raises(capi.TcError) as e:
+            capi.tc_flush(s, tail, L - 1)
+        assert e.value.code == "TC_ESTATE"
+        capi.tc_reset(s)
+        capi.tc_set_ir(s, h)
+        capi.tc_push_block(s, np.ones(B, np.float32), y)
+        assert np.array_equal(y, np.arange(1, B + 1, dtype=np.float32))
+    finally:
+        capi.tc_close(s)

@@ -41,16 +41,20 @@ struct K1Cfg {
     static constexpr int MO = K1_MO;        // outputs per CTA
     static constexpr int KC = 32 * S;       // taps per CTA
     static constexpr int XS = KC + MO;      // staged input samples
-    static constexpr int PAD = 4;           // floats before xs[0]; the final window load reads xs[-4..-1]
-    static constexpr int STAGE = PAD + XS + KC;
+    static constexpr int PAD = 8;           // floats before xs[0]: the last prefetches read xs[-8..-1]
+    static constexpr int TAIL = 4;          // floats after hs: the last prefetch of h reads hs[KC..KC+3]
+    static constexpr int STAGE = PAD + XS + KC + TAIL;
     static constexpr int RED = 32 * MO;     // floats for one piece of the chunk reduction
     static constexpr int SMEM_FLOATS = STAGE > RED ? STAGE : RED;
 };
 
-// acc[r] += sum_{j < S} hp[j] * xp[3 + r - j - ...]: the thread's S taps for its
-// 16 outputs. xp points at xs[ia], the lowest input needed by the first 4 taps.
+// The thread's S taps for its 16 outputs: acc[r] += h[j] * x[m0 + r - j].
+// xp points at xs[ia], the lowest input sample needed by the first 4 taps.
 // Logical window at step q is w_q[i] = xp[i - 4q], i in [0, 20); tap 4q+u of
-// output r reads w_q[3 - u + r]. Physical register of w_q[i] is (i - 4q) mod 20.
+// output r reads w_q[3 - u + r]. The physical register of w_q[i] is
+// (i - 4q) mod 20, so the window slides without moves. The h and x loads of
+// step q+1 are issued before the FMAs of step q. The prefetch after the
+// last step reads padding.
 template <int S>
 __device__ __forceinline__ void k1_taps(const float *__restrict__ xp, const float *__restrict__ hp,
                                         float (&acc)[16])
@@ -64,13 +68,17 @@ __device__ __forceinline__ void k1_taps(const float *__restrict__ xp, const floa
         w[4 * i + 2] = t.z;
         w[4 * i + 3] = t.w;
     }
+    float4 h_nx = *reinterpret_cast<const float4 *>(hp);
+    float4 x_nx = *reinterpret_cast<const float4 *>(xp - 4);
 #pragma unroll 1
     for (int it = 0; it < S / 20; ++it) {
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
             const int j = it * 20 + 4 * q;
-            const float4 h4 = *reinterpret_cast<const float4 *>(hp + j);
-            const float4 xn = *reinterpret_cast<const float4 *>(xp - j - 4);
+            const float4 h4 = h_nx;
+            const float4 xn = x_nx;
+            h_nx = *reinterpret_cast<const float4 *>(hp + j + 4);
+            x_nx = *reinterpret_cast<const float4 *>(xp - j - 8);
             const float hv[4] = {h4.x, h4.y, h4.z, h4.w};
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -137,6 +145,9 @@ __global__ void __launch_bounds__(K1_THREADS, 3) k1_gather(const K1Params p)
     const int g = ((lane >> 2) & 1) | ((lane >> 3) << 1);
     const int s = warp * 4 + s_lo;
     const int ia = g * C::R - s * S + C::KC - 4;
+    // Input samples this thread reads (inclusive): outputs t0+16g .. +15, taps kc0+sS .. +S-1.
+    const long long th_hi = t0 + 16 * g + 15 - (kc0 + (long long)s * S);
+    const long long th_lo = th_hi - 15 - (S - 1);
 
     float acc[16];
 #pragma unroll
@@ -172,7 +183,8 @@ __global__ void __launch_bounds__(K1_THREADS, 3) k1_gather(const K1Params p)
             }
             __syncthreads();
         }
-        k1_taps<S>(xs + ia, hs + s * S, acc);
+        if (th_hi >= a && th_lo < b)  // only threads that see a tache of version v
+            k1_taps<S>(xs + ia, hs + s * S, acc);
         fence_proxy_async_smem();
         __syncthreads();
     }

@@ -14,8 +14,9 @@ std::atomic<uint64_t> g_launches{0};
 __global__ void ir_prep_kernel(const float *__restrict__ src, long long src_pitch, long long n, int rows,
                                float *__restrict__ dst, long long row_stride, long long phase, long long Lpad)
 {
-    // One float4 of one shifted copy per thread iteration.
-    const long long per_row = 4 * (Lpad / 4);
+    // One float4 of one shifted copy per thread iteration: Lpad / 4 float4s
+    // per copy, 4 copies per row.
+    const long long per_row = Lpad / 4;
     const long long total = (long long)rows * 4 * per_row;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
          q += (long long)gridDim.x * blockDim.x) {

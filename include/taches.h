@@ -198,6 +198,36 @@ tc_status tc_sync(tc_stream *s);
 tc_status tc_convolve(const float *x, size_t N, const float *h, size_t L, float *y, void *cuda_stream);
 
 /* ---------------------------------------------------------------------- */
+/* One-shot convolution without allocation                                 */
+/* ---------------------------------------------------------------------- */
+
+/* The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory where they call: a real-time audio callback
+ * (cudaMalloc may block for an unbounded time and miss the block deadline),
+ * or a host program whose own allocator owns the GPU's memory.
+ *
+ * Same result as tc_convolve, y[0..N+L-2] = x[0..N-1] * h[0..L-1] (device
+ * pointers, FP32), but it calls no cudaMalloc, cudaFree or allocating
+ * routine. Its working memory (input history with zero margins, shifted IR
+ * copies, split-sum partials, counters) lives in one fixed 32 MiB device
+ * array inside this library. Each GPU that loads the library holds that array
+ * until the process exits.
+ *   - Limit: the working set, about N + 13 L + 5e4 floats (N + 7 L + 5e4
+ *     for IRs over 70000 taps), must fit in 32 MiB = 8388608 floats: for
+ *     example N up to 8.2 million samples with L = 4096. A call beyond it
+ *     returns TC_EINVAL and names the size it would need.
+ *   - The first call on a device looks up the array's device address with
+ *     that device current. Make that first call before any CUDA stream
+ *     capture.
+ *   - Every call uses the same array and clears what must start at zero.
+ *     Calls that overlap on the GPU (different streams, or threads without
+ *     ordering) race and give wrong results, so serialise them.
+ * Runs on cuda_stream (NULL = default stream) and waits for it before
+ * returning. Errors: TC_EINVAL (NULL, zero or too large sizes); TC_ECUDA;
+ * TC_ETIMEOUT. */
+tc_status tc_convolve_noalloc(const float *x, size_t N, const float *h, size_t L, float *y, void *cuda_stream);
+
+/* ---------------------------------------------------------------------- */
 /* Diagnostics                                                             */
 /* ---------------------------------------------------------------------- */
 

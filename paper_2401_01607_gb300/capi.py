@@ -63,6 +63,7 @@ _SIGS = {
     "tc_flush_dev": [_vp, _vp, ctypes.POINTER(_sz)],
     "tc_sync": [_vp],
     "tc_convolve": [_vp, _sz, _vp, _sz, _vp, _vp],
+    "tc_convolve_noalloc": [_vp, _sz, _vp, _sz, _vp, _vp],
     "tc_profile": [_vp, _int],
     "tc_profile_read": [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_u64), ctypes.POINTER(ctypes.c_double)],
 }
@@ -244,6 +245,14 @@ def tc_profile_read(s: int) -> tuple[float, int, float]:
     ms, n, macs = ctypes.c_double(), _u64(), ctypes.c_double()
     _call("tc_profile_read", s, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(macs))
     return ms.value, int(n.value), macs.value
+
+
+def tc_convolve_noalloc(x, N: int, h, L: int, y, cuda_stream=None) -> None:
+    """As tc_convolve, for callers that cannot allocate: the working memory is a
+    fixed 32 MiB device array inside the library (calls must not overlap)."""
+    cs = None if cuda_stream is None else (cuda_stream if isinstance(cuda_stream, int) else
+                                           int(cuda_stream.cuda_stream))
+    _call("tc_convolve_noalloc", _dev_ptr(x), N, _dev_ptr(h), L, _dev_ptr(y), cs)
 
 
 def tc_last_error() -> str:

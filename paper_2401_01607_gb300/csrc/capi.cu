@@ -75,6 +75,11 @@ enum State { ST_OPEN = 0, ST_ENDED = 1, ST_FLUSHED = 2 };
 
 }  // namespace
 
+namespace tc {
+// Lets other translation units of the library report through tc_last_error().
+void set_last_error(const char *msg) { g_err = msg ? msg : ""; }
+}  // namespace tc
+
 struct tc_stream {
     // Shape.
     int kind = KIND_GROUP;

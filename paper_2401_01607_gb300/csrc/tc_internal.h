@@ -91,6 +91,9 @@ cudaError_t ir_prep_launch(const float *src, long long src_pitch, long long n, i
                            float *dst, long long row_stride, long long phase, long long Lpad,
                            cudaStream_t st);
 
+// Sets the calling thread's tc_last_error() message.
+void set_last_error(const char *msg);
+
 // Counts kernel launches issued by this library.
 void count_launch(int n = 1);
 uint64_t launches();

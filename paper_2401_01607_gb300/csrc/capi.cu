@@ -130,7 +130,7 @@ struct tc_stream {
     cudaEvent_t ev_x = nullptr;
     int *pin_err = nullptr;
 
-    // K1 scratch.
+    // K1 scratch: chunk sums of every tile and one ticket per tile.
     float *partial = nullptr;
     size_t partial_floats = 0;
     unsigned *counter = nullptr;
@@ -162,40 +162,6 @@ tc_status use_device(const tc_stream *s)
     if (cur != s->device)
         TC_CU(cudaSetDevice(s->device));
     return TC_OK;
-}
-
-// Tap chunk variant for a launch: the largest S that still fills the GPU with
-// a few waves of CTAs and keeps at most K1_MAX_CHUNKS partials per tile.
-int pick_variant(const tc_stream *s, long long ntile, int e)
-{
-    if (s->k1_variant_fixed >= 0)
-        return s->k1_variant_fixed;
-    static const int order[] = {tc::K1_S260, tc::K1_S100, tc::K1_S60, tc::K1_S20};
-    int fallback = -1;
-    for (int v : order) {
-        const long long kc = tc::k1_chunk_taps(v);
-        const long long nchunk = (s->L + e + kc - 1) / kc;
-        const long long ctot = nchunk * (long long)s->nin;
-        if (ctot > tc::K1_MAX_CHUNKS)
-            continue;
-        const long long ctas = ctot * ntile * (long long)s->items;
-        fallback = v;
-        if (ctas >= 8LL * 152)
-            return v;
-    }
-    return fallback;
-}
-
-long long max_ctot(const tc_stream *s)
-{
-    long long m = 0;
-    for (int v = 0; v < tc::K1_NVARIANTS; ++v) {
-        const long long kc = tc::k1_chunk_taps(v);
-        const long long ctot = ((long long)s->L + 3 + kc - 1) / kc * (long long)s->nin;
-        if (ctot <= tc::K1_MAX_CHUNKS)
-            m = std::max(m, ctot);
-    }
-    return m;
 }
 
 void free_all(tc_stream *s)
@@ -288,10 +254,11 @@ tc_status open_common(tc_stream *s)
     TC_CU(cudaHostAlloc(&s->pin_err, sizeof(int), cudaHostAllocDefault));
     *s->pin_err = 0;
 
-    const long long ntile = (long long)((s->max_push + tc::K1_MO - 1) / tc::K1_MO);
-    s->counter_n = (size_t)(ntile * (long long)s->items);
-    s->partial_floats = (size_t)(ntile * (long long)s->items * max_ctot(s) * tc::K1_MO);
-    TC_CU(cudaMalloc(&s->partial, std::max<size_t>(s->partial_floats, 1) * sizeof(float)));
+    // Chunk sums of every tile of the largest launch, one ticket per tile.
+    const long long max_tiles = (long long)s->items * (((long long)s->max_push + tc::K1_MO - 1) / tc::K1_MO);
+    s->counter_n = (size_t)max_tiles;
+    s->partial_floats = (size_t)tc::k1_partial_floats_max((long long)s->L, (int)s->nin, max_tiles);
+    TC_CU(cudaMalloc(&s->partial, s->partial_floats * sizeof(float)));
     TC_CU(cudaMalloc(&s->counter, s->counter_n * sizeof(unsigned)));
     TC_CU(cudaMalloc(&s->d_err, sizeof(int)));
     TC_TRY(clear_state(s));
@@ -484,19 +451,15 @@ tc_status launch_k1(tc_stream *s, long long t0, long long nout, float *y, long l
     p.nout = (int)nout;
     p.ntile = (int)((nout + tc::K1_MO - 1) / tc::K1_MO);
     p.e = tc::k1_shift_e(t0, s->base);
-    const int variant = pick_variant(s, p.ntile, p.e);
-    if (variant < 0)
-        return fail(TC_EUNSUPPORTED, "IR too long for the FP32 gather (more than %d tap chunks per tile)",
-                    tc::K1_MAX_CHUNKS);
-    const long long kc = tc::k1_chunk_taps(variant);
-    p.nchunk = (int)(((long long)s->L + p.e + kc - 1) / kc);
+    tc::K1Plan plan{};
+    TC_CU(tc::k1_plan((long long)s->L, p.e, p.nin, p.nitems, p.ntile, s->k1_variant_fixed, &plan));
     p.y = y;
     p.y_pitch = y_pitch;
     p.partial = s->partial;
     p.counter = s->counter;
     p.err = s->d_err;
-    const size_t need = (size_t)p.ntile * s->items * (size_t)(p.nin * p.nchunk) * tc::K1_MO;
-    if ((size_t)p.ntile * s->items > s->counter_n || (p.nin * p.nchunk > 1 && need > s->partial_floats))
+    if ((size_t)p.nitems * p.ntile > s->counter_n ||
+        (size_t)plan.ctas * tc::K1_MO > s->partial_floats)
         return fail(TC_EINVAL, "internal: K1 scratch too small");
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
     if (s->profile) {
@@ -510,7 +473,7 @@ tc_status launch_k1(tc_stream *s, long long t0, long long nout, float *y, long l
         s->ev_used += 2;
         TC_CU(cudaEventRecord(ev_a, s->cs));
     }
-    TC_CU(tc::k1_launch(p, variant, s->cs));
+    TC_CU(tc::k1_launch(p, plan, s->cs));
     if (s->profile) {
         TC_CU(cudaEventRecord(ev_b, s->cs));
         // Useful multiply-adds: output m sees the taps k < L with 0 <= m - k < n_end,

@@ -5,26 +5,33 @@
 // threads races. K1 computes the same sums from the output side instead:
 //     y[m] = sum_k h_{v(m-k)}[k] * x[m-k]              (Eq. 4, per-sample IR)
 // Each output is then written by exactly one thread, with no atomics on the
-// data. The per-sample IR version v(n) is kept as a version table. A CTA whose
-// input window straddles a version boundary runs once per version over a
-// masked copy of its window. This is the superposition of the taches of each
-// version.
+// data. The per-sample IR version v(n) is kept as a version table. A chunk
+// whose input window straddles a version boundary is computed once per
+// version over the samples that spawned their tache with that version: the
+// superposition of the taches of each version.
 //
-// CTA tile: 128 outputs x KC taps, 256 threads = 8 output groups (16
-// consecutive outputs each) x 32 tap sub-segments (S consecutive taps each,
-// KC = 32*S).
-//   * The input window (KC+128 samples) and the IR chunk (KC taps) are
-//     staged in shared memory by 1-D TMA bulk copies (cp.async.bulk) that
-//     complete on an mbarrier.
-//   * Each thread keeps 16 accumulators and a 20-register sliding window of
-//     the input. Per 4 taps it does one 128-bit load of h, one 128-bit load of
-//     the next 4 input samples and 64 FMAs. The window rotates through
-//     registers by compile-time renaming over 5 steps, so S is a multiple of
-//     20. S/4 is odd, which makes the 128-bit shared loads conflict-free.
-//   * Sub-segment sums are combined by a pairwise tree: warp shuffles, then
-//     shared memory. Chunk partials go to a scratch buffer. The last CTA of
-//     the tile (a ticket counter) adds them in a fixed pairwise tree and
-//     writes y. The result does not depend on CTA scheduling.
+// CTA = one output tile (128 samples of one item) x one tap chunk-task (KC =
+// 640 P taps of one input). 256 threads = 8 output groups (16 consecutive
+// outputs) x 32 tap sub-segments.
+//   * For each IR version that reaches the tile through the chunk, one thread
+//     issues two 1-D TMA bulk copies (cp.async.bulk) into shared memory: the
+//     input window (KC+128 samples) and the IR chunk (KC taps, from the
+//     shifted copy that makes it 16-byte aligned). They complete on an
+//     mbarrier, which that thread waits on (bounded); the others wait at the
+//     CTA barrier, which costs no issue slots.
+//   * In pass p a thread covers taps [20(32p+s), +20) of the chunk with 16
+//     accumulators and a 20-register input window. The window rotates by
+//     compile-time renaming inside the fully unrolled 20-tap pass, with
+//     128-bit shared loads (conflict-free: 20/4 is odd). When the window
+//     straddles a version boundary, the samples of other versions are zeroed
+//     in shared memory first; threads with no sample of the version skip the
+//     pass.
+//   * Epilogue: pairwise tree over the 32 sub-segments (warp shuffles, then
+//     shared memory). The chunk sum goes to scratch, then a ticket counter
+//     picks the tile's last CTA, which adds the chunk sums by a pairwise
+//     binary-counter stack per output column and writes y. The order is fixed
+//     by the decomposition, not by scheduling.
+#include <algorithm>
 #include <climits>
 
 #include "ptx.cuh"
@@ -34,29 +41,24 @@ namespace tc {
 
 namespace {
 
-template <int S>
+template <int P>
 struct K1Cfg {
-    static_assert(S % 20 == 0 && (S / 4) % 2 == 1, "S must be a multiple of 20 with S/4 odd");
-    static constexpr int R = 16;            // outputs per thread
-    static constexpr int MO = K1_MO;        // outputs per CTA
-    static constexpr int KC = 32 * S;       // taps per CTA
-    static constexpr int XS = KC + MO;      // staged input samples
-    static constexpr int PAD = 8;           // floats before xs[0]: the last prefetches read xs[-8..-1]
-    static constexpr int TAIL = 4;          // floats after hs: the last prefetch of h reads hs[KC..KC+3]
-    static constexpr int STAGE = PAD + XS + KC + TAIL;
-    static constexpr int RED = 32 * MO;     // floats for one piece of the chunk reduction
-    static constexpr int SMEM_FLOATS = STAGE > RED ? STAGE : RED;
+    static constexpr int MO = K1_MO;          // outputs per tile
+    static constexpr int SEG = K1_SEG;        // taps per thread per pass
+    static constexpr int KC = 32 * SEG * P;   // taps per chunk
+    static constexpr int XS = KC + MO;        // staged input samples
+    static constexpr int STAGE = XS + KC;     // window, then IR chunk
+    static constexpr int LEVELS = 12;         // pairwise stack depth: chunk-tasks per tile < 4096
+    static constexpr int RED = 8 * MO;
+    static constexpr int TAIL = RED + LEVELS * MO;  // reduction area, overlays the finished stage
+    static constexpr int SMEM_FLOATS = STAGE > TAIL ? STAGE : TAIL;
 };
 
-// The thread's S taps for its 16 outputs: acc[r] += h[j] * x[m0 + r - j].
-// xp points at xs[ia], the lowest input sample needed by the first 4 taps.
-// Logical window at step q is w_q[i] = xp[i - 4q], i in [0, 20); tap 4q+u of
-// output r reads w_q[3 - u + r]. The physical register of w_q[i] is
-// (i - 4q) mod 20, so the window slides without moves. The h and x loads of
-// step q+1 are issued before the FMAs of step q. The prefetch after the
-// last step reads padding.
-template <int S>
-__device__ __forceinline__ void k1_taps(const float *__restrict__ xp, const float *__restrict__ hp,
+// One pass: 20 taps for 16 outputs, fully unrolled. xp = xs + ia, the lowest
+// input sample read by the first 4 taps. Logical window w_q[i] = xp[i - 4q];
+// tap 4q+u of output r reads w_q[3-u+r]. Physical register of w_q[i] is
+// (i - 4q) mod 20, so the window slides without moves.
+__device__ __forceinline__ void k1_pass(const float *__restrict__ xp, const float *__restrict__ hp,
                                         float (&acc)[16])
 {
     float w[20];
@@ -68,24 +70,20 @@ __device__ __forceinline__ void k1_taps(const float *__restrict__ xp, const floa
         w[4 * i + 2] = t.z;
         w[4 * i + 3] = t.w;
     }
-    float4 h_nx = *reinterpret_cast<const float4 *>(hp);
-    float4 x_nx = *reinterpret_cast<const float4 *>(xp - 4);
-#pragma unroll 1
-    for (int it = 0; it < S / 20; ++it) {
 #pragma unroll
-        for (int q = 0; q < 5; ++q) {
-            const int j = it * 20 + 4 * q;
-            const float4 h4 = h_nx;
-            const float4 xn = x_nx;
-            h_nx = *reinterpret_cast<const float4 *>(hp + j + 4);
-            x_nx = *reinterpret_cast<const float4 *>(xp - j - 8);
-            const float hv[4] = {h4.x, h4.y, h4.z, h4.w};
+    for (int q = 0; q < 5; ++q) {
+        const float4 h4 = *reinterpret_cast<const float4 *>(hp + 4 * q);
+        float4 xn = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (q < 4)
+            xn = *reinterpret_cast<const float4 *>(xp - 4 * q - 4);
+        const float hv[4] = {h4.x, h4.y, h4.z, h4.w};
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < 4; ++u) {
 #pragma unroll
-                for (int r = 0; r < 16; ++r)
-                    acc[r] = fmaf(hv[u], w[(3 - u + r - 4 * q + 40) % 20], acc[r]);
-            }
+            for (int r = 0; r < 16; ++r)
+                acc[r] = fmaf(hv[u], w[(3 - u + r - 4 * q + 40) % 20], acc[r]);
+        }
+        if (q < 4) {
             w[(16 - 4 * q + 40) % 20] = xn.x;
             w[(17 - 4 * q + 40) % 20] = xn.y;
             w[(18 - 4 * q + 40) % 20] = xn.z;
@@ -94,15 +92,17 @@ __device__ __forceinline__ void k1_taps(const float *__restrict__ xp, const floa
     }
 }
 
-template <int S>
+template <int P>
 __global__ void __launch_bounds__(K1_THREADS, 3) k1_gather(const K1Params p)
 {
-    using C = K1Cfg<S>;
+    using C = K1Cfg<P>;
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ int s_last;
-    float *xs = smem + C::PAD;
-    float *hs = smem + C::PAD + C::XS;
+    float *const xs = smem;
+    float *const hs = smem + C::XS;
+    float *const red = smem;                  // [8 warps][16 r][8 g], after the last pass
+    float *const lv = red + C::RED;           // [LEVELS][128] pairwise stack of the last CTA
 
     const int tid = threadIdx.x;
     const int lane = tid & 31;
@@ -119,8 +119,8 @@ __global__ void __launch_bounds__(K1_THREADS, 3) k1_gather(const K1Params p)
     const int chunk = cidx % p.nchunk;
 
     const long long t0 = p.t0 + (long long)tile * C::MO;
-    const int kc0 = chunk * C::KC - p.e;             // first tap of the chunk; kc0 = t0 + 1 - base (mod 4)
-    const long long n_lo = t0 - kc0 - C::KC + 1;      // first staged input sample; n_lo = base (mod 4)
+    const int kc0 = chunk * C::KC - p.e;             // first tap; kc0 = t0 + 1 - base (mod 4)
+    const long long n_lo = t0 - kc0 - C::KC + 1;      // first staged sample; n_lo = base (mod 4)
     const long long n_end = n_lo + C::XS;
 
     const float *xsrc = p.hist + ((long long)item * p.x_item_rows + (long long)inp * p.x_in_rows) * p.pitch +
@@ -138,16 +138,12 @@ __global__ void __launch_bounds__(K1_THREADS, 3) k1_gather(const K1Params p)
     }
     __syncthreads();
 
-    // Thread roles: lane bits 0-1 pick the sub-segment within the warp, bit 2
-    // and bits 3-4 the output group, so each quarter-warp spans 2 groups x 4
-    // sub-segments (conflict-free 128-bit loads for S/4 odd).
+    // Lane bits 0-1: sub-segment within the warp; bit 2 and bits 3-4: output
+    // group. Each quarter-warp spans 2 groups x 4 sub-segments.
     const int s_lo = lane & 3;
     const int g = ((lane >> 2) & 1) | ((lane >> 3) << 1);
     const int s = warp * 4 + s_lo;
-    const int ia = g * C::R - s * S + C::KC - 4;
-    // Input samples this thread reads (inclusive): outputs t0+16g .. +15, taps kc0+sS .. +S-1.
-    const long long th_hi = t0 + 16 * g + 15 - (kc0 + (long long)s * S);
-    const long long th_lo = th_hi - 15 - (S - 1);
+    const long long out_hi = t0 + 16 * g + 15;  // last output of this thread
 
     float acc[16];
 #pragma unroll
@@ -155,41 +151,55 @@ __global__ void __launch_bounds__(K1_THREADS, 3) k1_gather(const K1Params p)
         acc[r] = 0.f;
 
     uint32_t parity = 0;
-    bool failed = false;
     for (int v = 0; v < nv; ++v) {
         const long long a = vst[v];
         const long long b = (v + 1 < nv) ? vst[v + 1] : LLONG_MAX;
         if (b <= n_lo || a >= n_end)
             continue;  // this version spawned no tache that reaches the tile through this chunk
+        bool ok = true;
         if (tid == 0) {
-            mbar_arrive_expect_tx(&bar, (uint32_t)((C::XS + C::KC) * sizeof(float)));
+            mbar_arrive_expect_tx(&bar, (uint32_t)(C::STAGE * sizeof(float)));
             bulk_g2s(xs, xsrc, (uint32_t)(C::XS * sizeof(float)), &bar);
             bulk_g2s(hs, hsrc + (long long)vsl[v] * p.ir_slot, (uint32_t)(C::KC * sizeof(float)), &bar);
+            ok = mbar_wait_bounded(&bar, parity, p.err, ERR_TIMEOUT_TMA);
         }
-        const bool ok = mbar_wait_bounded(&bar, parity, p.err, ERR_TIMEOUT_TMA);
         parity ^= 1u;
         if (!__syncthreads_and(ok)) {
             // Give the copies in flight a bounded chance to land before the CTA exits.
-            mbar_wait_bounded(&bar, parity ^ 1u, nullptr, 0);
-            failed = true;
-            break;
+            if (tid == 0)
+                mbar_wait_bounded(&bar, parity ^ 1u, nullptr, 0);
+            __syncthreads();
+            return;
         }
         if (a > n_lo || b < n_end) {
-            // Keep only the samples that spawned their tache with version v.
-            for (int i = tid; i < C::XS; i += K1_THREADS) {
-                const long long n = n_lo + i;
-                if (n < a || n >= b)
-                    xs[i] = 0.f;
-            }
+            // The window straddles a version boundary: keep only the samples
+            // that spawned their tache with this version by zeroing
+            // [n_lo, a) and [b, n_end) of the staged window.
+            const long long za = a - n_lo, zb = b - n_lo;
+            const int z0 = (za > 0) ? (za < C::XS ? (int)za : C::XS) : 0;
+            const int z1 = (b < n_end) ? (zb > 0 ? (int)zb : 0) : C::XS;
+            for (int i = tid; i < z0; i += K1_THREADS)
+                xs[i] = 0.f;
+            for (int i = z1 + tid; i < C::XS; i += K1_THREADS)
+                xs[i] = 0.f;
             __syncthreads();
         }
-        if (th_hi >= a && th_lo < b)  // only threads that see a tache of version v
-            k1_taps<S>(xs + ia, hs + s * S, acc);
+#pragma unroll 1
+        for (int pass = 0; pass < P; ++pass) {
+            const int seg = pass * 32 + s;
+            // Samples read by this pass: outputs - (kc0 + 20 seg + [0, 19]).
+            const long long th_hi = out_hi - (kc0 + (long long)seg * C::SEG);
+            const long long th_lo = th_hi - 15 - (C::SEG - 1);
+            if (th_hi < a || th_lo >= b)
+                continue;  // no tache of this version reaches these outputs here
+            if (kc0 + seg * C::SEG >= p.L)
+                continue;  // taps past the end of the IR (zero padding of the last chunk)
+            const int ia = g * 16 - seg * C::SEG + C::KC - 4;
+            k1_pass(xs + ia, hs + seg * C::SEG, acc);
+        }
         fence_proxy_async_smem();
         __syncthreads();
     }
-    if (failed)
-        return;
 
     // Pairwise tree over the 32 sub-segments: lanes (s, s^1), then (s, s^2)
     // inside the warp, then warps (0,1),(2,3).. through shared memory.
@@ -198,21 +208,18 @@ __global__ void __launch_bounds__(K1_THREADS, 3) k1_gather(const K1Params p)
         float v = acc[r];
         v += __shfl_xor_sync(0xffffffffu, v, 1);
         v += __shfl_xor_sync(0xffffffffu, v, 2);
-        acc[r] = v;
-    }
-    float *red = smem;  // [8 warps][128 outputs]; the stage is no longer read
-    if (s_lo == 0) {
-#pragma unroll
-        for (int r = 0; r < 16; ++r)
-            red[warp * C::MO + g * 16 + r] = acc[r];
+        if (s_lo == 0)
+            red[warp * C::MO + r * 8 + g] = v;  // the 8 writing lanes hit 8 banks
     }
     __syncthreads();
     float tot = 0.f;
+    const int o = tid;                        // output within the tile (threads < 128)
     if (tid < C::MO) {
-        const float w01 = red[0 * C::MO + tid] + red[1 * C::MO + tid];
-        const float w23 = red[2 * C::MO + tid] + red[3 * C::MO + tid];
-        const float w45 = red[4 * C::MO + tid] + red[5 * C::MO + tid];
-        const float w67 = red[6 * C::MO + tid] + red[7 * C::MO + tid];
+        const int ti = (o % 16) * 8 + o / 16;
+        const float w01 = red[0 * C::MO + ti] + red[1 * C::MO + ti];
+        const float w23 = red[2 * C::MO + ti] + red[3 * C::MO + ti];
+        const float w45 = red[4 * C::MO + ti] + red[5 * C::MO + ti];
+        const float w67 = red[6 * C::MO + ti] + red[7 * C::MO + ti];
         tot = (w01 + w23) + (w45 + w67);
     }
 
@@ -224,10 +231,10 @@ __global__ void __launch_bounds__(K1_THREADS, 3) k1_gather(const K1Params p)
         return;
     }
 
-    // Chunk partial -> scratch; the last CTA of the tile reduces.
+    // Chunk sum -> scratch; the last CTA of the tile reduces.
     float *part = p.partial + (((long long)item * p.ntile + tile) * ctot) * C::MO;
     if (tid < C::MO) {
-        __stcg(part + (long long)cidx * C::MO + tid, tot);
+        __stcg(part + (long long)cidx * C::MO + o, tot);
         __threadfence();
     }
     __syncthreads();
@@ -239,43 +246,30 @@ __global__ void __launch_bounds__(K1_THREADS, 3) k1_gather(const K1Params p)
     if (!s_last)
         return;
     __threadfence();
-
-    // Fixed pairwise tree over the ctot partials: pieces of 32 (adjacent
-    // pairs, zero-padded), then the piece sums (adjacent pairs).
-    const int npieces = (ctot + 31) / 32;  // <= 8 (ctot <= K1_MAX_CHUNKS)
-    float ps[8];
-#pragma unroll
-    for (int pc = 0; pc < 8; ++pc) {
-        ps[pc] = 0.f;
-        if (pc < npieces) {
-            __syncthreads();
-            const int c0 = pc * 32;
-            const int cn = min(32, ctot - c0);
-            for (int i = tid; i < 32 * C::MO; i += K1_THREADS) {
-                const int c = i / C::MO;
-                const int o = i % C::MO;
-                red[i] = (c < cn) ? __ldcg(part + (long long)(c0 + c) * C::MO + o) : 0.f;
+    if (tid < C::MO) {
+        // Fixed pairwise tree over the chunk sums, per output column: a
+        // binary-counter stack in this thread's column (older block on the left).
+        for (int c = 0; c < ctot; ++c) {
+            float carry = __ldcg(part + (long long)c * C::MO + o);
+            int cc = c, l = 0;
+            while (cc & 1) {
+                carry = lv[l * C::MO + o] + carry;
+                cc >>= 1;
+                ++l;
             }
-            __syncthreads();
-            if (tid < C::MO) {
-                float v[32];
-#pragma unroll
-                for (int c = 0; c < 32; ++c)
-                    v[c] = red[c * C::MO + tid];
-#pragma unroll
-                for (int wdt = 16; wdt >= 1; wdt >>= 1) {
-#pragma unroll
-                    for (int c = 0; c < wdt; ++c)
-                        v[c] = v[2 * c] + v[2 * c + 1];
-                }
-                ps[pc] = v[0];
+            lv[l * C::MO + o] = carry;
+        }
+        float y = 0.f;
+        bool first = true;
+        for (int l = 0; l < C::LEVELS; ++l) {
+            if ((ctot >> l) & 1) {
+                const float v = lv[l * C::MO + o];
+                y = first ? v : v + y;
+                first = false;
             }
         }
-    }
-    if (tid < C::MO) {
-        const float t = ((ps[0] + ps[1]) + (ps[2] + ps[3])) + ((ps[4] + ps[5]) + (ps[6] + ps[7]));
         if (tid < valid)
-            yrow[tid] = t;
+            yrow[tid] = y;
     }
     if (tid == 0)
         p.counter[(long long)item * p.ntile + tile] = 0u;
@@ -283,72 +277,151 @@ __global__ void __launch_bounds__(K1_THREADS, 3) k1_gather(const K1Params p)
 
 constexpr int kMaxDevices = 64;
 
-template <int S>
-cudaError_t launch_variant(const K1Params &p, cudaStream_t st)
+struct DevInfo {
+    bool ready = false;
+    int sms = 0;
+    int blocks_per_sm[K1_NVARIANTS] = {};
+};
+DevInfo g_dev[kMaxDevices];
+
+template <int P>
+size_t smem_bytes()
 {
-    using C = K1Cfg<S>;
-    static bool attr_set[kMaxDevices] = {};
-    const size_t smem = (size_t)C::SMEM_FLOATS * sizeof(float);
+    return (size_t)K1Cfg<P>::SMEM_FLOATS * sizeof(float);
+}
+
+template <int P>
+cudaError_t prepare_variant(int dev, int variant)
+{
+    const size_t smem = smem_bytes<P>();
+    cudaError_t e = cudaFuncSetAttribute(k1_gather<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    int n = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k1_gather<P>, K1_THREADS, smem);
+    if (e != cudaSuccess)
+        return e;
+    g_dev[dev].blocks_per_sm[variant] = n > 0 ? n : 1;
+    return cudaSuccess;
+}
+
+cudaError_t device_info(DevInfo **out)
+{
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess)
         return e;
     if (dev < 0 || dev >= kMaxDevices)
         return cudaErrorInvalidDevice;
-    if (!attr_set[dev]) {
-        e = cudaFuncSetAttribute(k1_gather<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    DevInfo &d = g_dev[dev];
+    if (!d.ready) {
+        e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = prepare_variant<1>(dev, K1_P1);
+        if (e == cudaSuccess)
+            e = prepare_variant<4>(dev, K1_P4);
+        if (e == cudaSuccess)
+            e = prepare_variant<13>(dev, K1_P13);
         if (e != cudaSuccess)
             return e;
-        attr_set[dev] = true;
+        d.ready = true;
     }
-    const long long grid = (long long)p.nitems * p.ntile * p.nin * p.nchunk;
-    if (grid <= 0)
-        return cudaSuccess;
-    if (grid > 0x7fffffffLL)
-        return cudaErrorInvalidConfiguration;
-    k1_gather<S><<<(unsigned)grid, K1_THREADS, smem, st>>>(p);
-    count_launch();
-    return cudaGetLastError();
+    *out = &d;
+    return cudaSuccess;
 }
 
 }  // namespace
 
-int k1_taps_per_thread(int variant)
+int k1_chunk_taps(int variant)
 {
     switch (variant) {
-    case K1_S20: return 20;
-    case K1_S60: return 60;
-    case K1_S100: return 100;
-    case K1_S260: return 260;
+    case K1_P1: return 32 * K1_SEG * 1;
+    case K1_P4: return 32 * K1_SEG * 4;
+    case K1_P13: return 32 * K1_SEG * 13;
     default: return 0;
     }
 }
 
-int k1_chunk_taps(int variant) { return 32 * k1_taps_per_thread(variant); }
-
-size_t k1_smem_bytes(int variant)
+cudaError_t k1_plan(long long L, int e, int nin, int nitems, int ntile, int forced_variant, K1Plan *plan)
 {
-    switch (variant) {
-    case K1_S20: return sizeof(float) * K1Cfg<20>::SMEM_FLOATS;
-    case K1_S60: return sizeof(float) * K1Cfg<60>::SMEM_FLOATS;
-    case K1_S100: return sizeof(float) * K1Cfg<100>::SMEM_FLOATS;
-    case K1_S260: return sizeof(float) * K1Cfg<260>::SMEM_FLOATS;
-    default: return 0;
-    }
-}
-
-cudaError_t k1_launch(const K1Params &p, int variant, cudaStream_t st)
-{
-    if (p.nin * p.nchunk > K1_MAX_CHUNKS || p.nin < 1 || p.nchunk < 1 || p.e < 0 || p.e > 3 ||
-        (p.base & 3) != 0 || (p.pitch & 3) != 0)
+    DevInfo *d = nullptr;
+    cudaError_t err = device_info(&d);
+    if (err != cudaSuccess)
+        return err;
+    if (L < 1 || nin < 1 || nitems < 1 || ntile < 1 || e < 0 || e > 3)
         return cudaErrorInvalidValue;
-    switch (variant) {
-    case K1_S20: return launch_variant<20>(p, st);
-    case K1_S60: return launch_variant<60>(p, st);
-    case K1_S100: return launch_variant<100>(p, st);
-    case K1_S260: return launch_variant<260>(p, st);
+    const long long tiles = (long long)nitems * ntile;
+    int chosen = -1;
+    if (forced_variant >= 0 && forced_variant < K1_NVARIANTS) {
+        chosen = forced_variant;
+    } else {
+        // The largest chunk that still gives about four waves of CTAs and
+        // wastes < 10 % on the padded last chunk; otherwise the smallest chunk
+        // whose chunk-task count fits the tile's pairwise stack.
+        static const int order[] = {K1_P13, K1_P4, K1_P1};
+        for (int v : order) {
+            const long long kc = k1_chunk_taps(v);
+            const long long nchunk = (L + e + kc - 1) / kc;
+            const long long ctas = tiles * nchunk * nin;
+            const long long waves = ctas / ((long long)d->blocks_per_sm[v] * d->sms);
+            const bool tight = nchunk * kc <= L + L / 10 + 64;
+            if (nchunk * nin <= K1_MAX_CHUNK_TASKS && waves >= 4 && tight) {
+                chosen = v;
+                break;
+            }
+        }
+        if (chosen < 0) {
+            static const int small_first[] = {K1_P1, K1_P4, K1_P13};
+            for (int v : small_first) {
+                const long long kc = k1_chunk_taps(v);
+                if ((L + e + kc - 1) / kc * nin <= K1_MAX_CHUNK_TASKS) {
+                    chosen = v;
+                    break;
+                }
+            }
+        }
+        if (chosen < 0)
+            return cudaErrorInvalidValue;
+    }
+    const long long kc = k1_chunk_taps(chosen);
+    const long long nchunk = (L + e + kc - 1) / kc;
+    if (nchunk * nin > K1_MAX_CHUNK_TASKS)
+        return cudaErrorInvalidValue;
+    plan->variant = chosen;
+    plan->nchunk = (int)nchunk;
+    plan->ctas = tiles * nchunk * nin;
+    return cudaSuccess;
+}
+
+long long k1_partial_floats_max(long long L, int nin, long long tiles)
+{
+    const long long kc = k1_chunk_taps(K1_P1);
+    const long long ctot = (L + 3 + kc - 1) / kc * nin;
+    return std::max<long long>(1, tiles * std::min<long long>(ctot, K1_MAX_CHUNK_TASKS)) * K1_MO;
+}
+
+cudaError_t k1_launch(K1Params &p, const K1Plan &plan, cudaStream_t st)
+{
+    if ((p.base & 3) != 0 || (p.pitch & 3) != 0 || p.e < 0 || p.e > 3)
+        return cudaErrorInvalidValue;
+    DevInfo *d = nullptr;
+    cudaError_t e = device_info(&d);
+    if (e != cudaSuccess)
+        return e;
+    p.nchunk = plan.nchunk;
+    if (plan.ctas <= 0)
+        return cudaSuccess;
+    if (plan.ctas > 0x7fffffffLL)
+        return cudaErrorInvalidConfiguration;
+    const unsigned grid = (unsigned)plan.ctas;
+    switch (plan.variant) {
+    case K1_P1: k1_gather<1><<<grid, K1_THREADS, smem_bytes<1>(), st>>>(p); break;
+    case K1_P4: k1_gather<4><<<grid, K1_THREADS, smem_bytes<4>(), st>>>(p); break;
+    case K1_P13: k1_gather<13><<<grid, K1_THREADS, smem_bytes<13>(), st>>>(p); break;
     default: return cudaErrorInvalidValue;
     }
+    count_launch();
+    return cudaGetLastError();
 }
 
 }  // namespace tc

@@ -32,7 +32,8 @@ namespace {
 constexpr size_t kNoAllocScratchBytes = 32u << 20;             // 32 MiB
 constexpr long long kScratchFloats = (long long)(kNoAllocScratchBytes / sizeof(float));
 constexpr long long kPiece = 4096;                              // outputs per K1 launch
-constexpr long long kPieceTiles = kPiece / tc::K1_MO;
+constexpr long long kPieceTiles = kPiece / tc::K1_MO;  // tickets needed per launch
+static_assert(kPieceTiles <= 64, "the ticket area holds 64 counters");
 constexpr int kMaxDev = 64;
 
 static __device__ __align__(256) float g_noalloc_scratch[kNoAllocScratchBytes / sizeof(float)];
@@ -84,22 +85,6 @@ tc_status setup(int dev, DevPtrs *out)
     return TC_OK;
 }
 
-int pick(long long L, long long ntile)
-{
-    static const int order[] = {tc::K1_S260, tc::K1_S100, tc::K1_S60, tc::K1_S20};
-    int fallback = -1;
-    for (int v : order) {
-        const long long kc = tc::k1_chunk_taps(v);
-        const long long ctot = (L + 3 + kc - 1) / kc;
-        if (ctot > tc::K1_MAX_CHUNKS)
-            continue;
-        fallback = v;
-        if (ctot * ntile >= 8LL * 152)
-            return v;
-    }
-    return fallback;
-}
-
 }  // namespace
 
 extern "C" tc_status tc_convolve_noalloc(const float *x, size_t N, const float *h, size_t L, float *y,
@@ -117,17 +102,14 @@ extern "C" tc_status tc_convolve_noalloc(const float *x, size_t N, const float *
     const long long Lpad = ru(Ll + 4 + tc::K1_KC_MAX, 4);
     const long long ny = Nl + Ll - 1;
     const long long cap = ru(keep + ny + tc::K1_MO + 160, 64);       // history row: zeros, x, zeros
-    const int variant = pick(Ll, kPieceTiles);
-    if (variant < 0)
-        return na_fail(TC_EINVAL, "tc_convolve_noalloc: IR too long for the FP32 gather");
-    const long long kc = tc::k1_chunk_taps(variant);
-    const long long ctot_max = (Ll + 3 + kc - 1) / kc;
-    const long long off_ctr = 0;
-    const long long off_ir = 64;
+    // Chunk sums: every tile of one piece (4096 outputs) with the most chunks
+    // any variant may use; one ticket per tile.
+    const long long off_ctr = 0;                                    // tickets, error word
+    const long long off_ir = 128;
     const long long off_hist = off_ir + ru(4 * Lpad, 64);
     const long long off_part = off_hist + cap;
-    const long long need = off_part + kPieceTiles * ctot_max * tc::K1_MO;
-    if (need > kScratchFloats || (long long)kPieceTiles + 1 > 64) {
+    const long long need = off_part + tc::k1_partial_floats_max(Ll, 1, kPieceTiles);
+    if (need > kScratchFloats) {
         char buf[256];
         snprintf(buf, sizeof buf,
                  "tc_convolve_noalloc: N=%zu, L=%zu need %.1f MiB of scratch; the fixed array holds %.0f MiB "
@@ -149,8 +131,8 @@ extern "C" tc_status tc_convolve_noalloc(const float *x, size_t N, const float *
 
     cudaStream_t cs = (cudaStream_t)cuda_stream;
     float *base = P.scratch;
-    unsigned *counters = reinterpret_cast<unsigned *>(base + off_ctr);
-    int *err = reinterpret_cast<int *>(base + off_ctr + kPieceTiles);
+    unsigned *counters = reinterpret_cast<unsigned *>(base + off_ctr);  // [kPieceTiles]
+    int *err = reinterpret_cast<int *>(base + off_ctr + 64);
     float *ir = base + off_ir;
     float *hist = base + off_hist;
     float *part = base + off_part;
@@ -164,7 +146,7 @@ extern "C" tc_status tc_convolve_noalloc(const float *x, size_t N, const float *
 
     // Clear what must start at zero: counters and error word, and the
     // history's zero margins before x[0] and after x[N-1].
-    NA_CU(cudaMemsetAsync(counters, 0, 64 * sizeof(float), cs));
+    NA_CU(cudaMemsetAsync(counters, 0, 128 * sizeof(float), cs));
     NA_CU(cudaMemsetAsync(hist, 0, (size_t)keep * sizeof(float), cs));
     NA_CU(cudaMemsetAsync(hist + keep + Nl, 0, (size_t)(cap - keep - Nl) * sizeof(float), cs));
     NA_CU(cudaMemcpyAsync(hist + keep, x, (size_t)Nl * sizeof(float), cudaMemcpyDeviceToDevice, cs));
@@ -197,10 +179,13 @@ extern "C" tc_status tc_convolve_noalloc(const float *x, size_t N, const float *
         p.nout = (int)n;
         p.ntile = (int)((n + tc::K1_MO - 1) / tc::K1_MO);
         p.e = tc::k1_shift_e(t0, p.base);
-        p.nchunk = (int)((Ll + p.e + kc - 1) / kc);
         p.y = y + t0;
         p.y_pitch = n;
-        NA_CU(tc::k1_launch(p, variant, cs));
+        tc::K1Plan plan{};
+        NA_CU(tc::k1_plan(Ll, p.e, 1, 1, p.ntile, -1, &plan));
+        if (plan.ctas * tc::K1_MO > tc::k1_partial_floats_max(Ll, 1, kPieceTiles))
+            return na_fail(TC_EINVAL, "tc_convolve_noalloc: internal: chunk-sum scratch too small");
+        NA_CU(tc::k1_launch(p, plan, cs));
     }
     int herr = 0;
     NA_CU(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, cs));

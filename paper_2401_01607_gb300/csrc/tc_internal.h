@@ -16,16 +16,16 @@ namespace tc {
 // where x_{c,i} is a row of the input history and v(n) the IR version of
 // input sample n (Eq. 4 with per-sample versions).
 //
-// Work split: output tiles of K1_MO = 128 samples x tap chunks of KC taps.
-// One CTA per (item, tile, input, chunk). A CTA sums its tap chunk in FP32
-// registers. Tap sub-segments are combined by a pairwise tree of warp
-// shuffles and shared memory, and the chunk partials by a pairwise tree run
-// by the last CTA of the tile.
+// Work split: output tiles of K1_MO = 128 samples x tap chunk-tasks of KC
+// taps (nin * nchunk per tile); one CTA per (item, tile, chunk-task). A CTA sums
+// its chunk in FP32 registers. Sub-segments are combined by a pairwise tree,
+// and the chunk sums of a tile by a pairwise tree run by the tile's last CTA.
 // ---------------------------------------------------------------------------
-constexpr int K1_MO = 128;         // outputs per tile
-constexpr int K1_THREADS = 256;    // 8 output groups of 16 x 32 tap sub-segments
-constexpr int K1_MAX_CHUNKS = 256; // nin * nchunk per tile, upper bound
-constexpr int K1_KC_MAX = 32 * 260;  // largest tap chunk of any variant
+constexpr int K1_MO = 128;           // outputs per tile
+constexpr int K1_THREADS = 256;      // 8 output groups of 16 x 32 tap sub-segments
+constexpr int K1_SEG = 20;           // taps per thread per pass
+constexpr int K1_KC_MAX = 32 * K1_SEG * 13;  // largest tap chunk of any variant
+constexpr int K1_MAX_CHUNK_TASKS = 4095;     // chunk-tasks per tile (12-level pairwise stack)
 
 struct K1Params {
     // Input history: sample n of history row r is hist[r * pitch + (n - base)].
@@ -55,23 +55,26 @@ struct K1Params {
     long long t0;            // first output sample of the launch
     int nout;                // outputs per item
     int ntile;               // ceil(nout / K1_MO)
-    int nchunk;              // tap chunks per input
     int e;                   // tap shift so that chunk starts are 16-byte aligned
+    int nchunk;              // tap chunks per input (filled by k1_launch)
 
     float *y;                // output of item c, sample t0 + j: y[c * y_pitch + j]
     long long y_pitch;
 
-    float *partial;          // [nitems][ntile][nin*nchunk][K1_MO]
+    float *partial;          // [nitems][ntile][nin*nchunk][K1_MO] chunk sums
     unsigned *counter;       // [nitems][ntile], zero between launches
     int *err;                // device error word
 };
 
-// Variants: taps per thread S (a multiple of 20 with S/4 odd, for the
-// register window rotation and conflict-free 128-bit shared loads).
-enum K1Variant { K1_S20 = 0, K1_S60 = 1, K1_S100 = 2, K1_S260 = 3, K1_NVARIANTS = 4 };
-int k1_taps_per_thread(int variant);
-int k1_chunk_taps(int variant);   // KC = 32 * S
-size_t k1_smem_bytes(int variant);
+// Variants: passes of K1_SEG taps per thread per chunk (KC = 32 * 20 * P).
+enum K1Variant { K1_P1 = 0, K1_P4 = 1, K1_P13 = 2, K1_NVARIANTS = 3 };
+int k1_chunk_taps(int variant);
+
+struct K1Plan {
+    int variant;
+    int nchunk;
+    long long ctas;
+};
 
 // Chunk alignment shift for a launch starting at output t0 with history base.
 inline int k1_shift_e(long long t0, long long base)
@@ -80,7 +83,15 @@ inline int k1_shift_e(long long t0, long long base)
     return (int)((4 - d) & 3);
 }
 
-cudaError_t k1_launch(const K1Params &p, int variant, cudaStream_t st);
+// Plans a launch: the largest chunk that still gives the GPU a few waves of
+// CTAs. forced_variant >= 0 picks one.
+cudaError_t k1_plan(long long L, int e, int nin, int nitems, int ntile, int forced_variant, K1Plan *plan);
+
+// Chunk-sum scratch (floats) a launch over `tiles` tiles may need with any variant.
+long long k1_partial_floats_max(long long L, int nin, long long tiles);
+
+// Launches K1 for plan on st (fills p.nchunk).
+cudaError_t k1_launch(K1Params &p, const K1Plan &plan, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // IR preparation: writes the four shifted copies of each IR row into a slot.

@@ -77,6 +77,9 @@ typedef struct tc_info {
     int precision;       /* tc_precision */
     int state;           /* 0 open, 1 ended (short block pushed), 2 flushed */
     int max_versions;    /* IR versions that can be live at once, per IR set */
+    uint64_t tensor_launches;  /* launches that ran on the tensor cores (BF16 modes) */
+    uint64_t fp32_fallbacks;   /* BF16-mode launches that ran on the FP32 gather because
+                                  their window straddled an IR switch */
 } tc_info;
 
 /* ---------------------------------------------------------------------- */

@@ -35,7 +35,8 @@ class TcInfo(ctypes.Structure):
     _fields_ = [("channels", ctypes.c_size_t), ("outputs", ctypes.c_size_t), ("L", ctypes.c_size_t),
                 ("block", ctypes.c_size_t), ("max_push", ctypes.c_size_t), ("pushed", ctypes.c_uint64),
                 ("shared_ir", ctypes.c_int), ("precision", ctypes.c_int), ("state", ctypes.c_int),
-                ("max_versions", ctypes.c_int)]
+                ("max_versions", ctypes.c_int), ("tensor_launches", ctypes.c_uint64),
+                ("fp32_fallbacks", ctypes.c_uint64)]
 
 
 _lib = None

@@ -14,6 +14,7 @@
 // Everything runs on one CUDA stream per tc_stream, in call order, so a slot
 // or table entry is never overwritten while an earlier kernel may read it.
 #include <algorithm>
+#include <array>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -54,7 +55,7 @@ tc_status fail(tc_status st, const char *fmt, ...)
     } while (0)
 
 long long round_up(long long a, long long m) { return (a + m - 1) / m * m; }
-long long floor4(long long a) { return a >= 0 ? (a & ~3LL) : -(((-a) + 3) & ~3LL); }
+long long floor8(long long a) { return a >= 0 ? (a & ~7LL) : -(((-a) + 7) & ~7LL); }
 
 constexpr int kMaxVersions = 16;
 
@@ -138,6 +139,22 @@ struct tc_stream {
     int *d_err = nullptr;
     int k1_variant_fixed = -1;  // -1: chosen per launch
 
+    // BF16 tensor-core path (shared-IR groups): bf16 hi/lo histories and, per
+    // IR slot and alignment shift delta, the materialised Toeplitz tiles.
+    void *hist_hi = nullptr;
+    void *hist_lo = nullptr;
+    CUtensorMap mx_hi{}, mx_lo{};
+    struct TSet {
+        bool ready = false;
+        long long nkb = 0;
+        void *thi = nullptr, *tlo = nullptr;
+        CUtensorMap mt_hi{}, mt_lo{};
+    };
+    std::vector<std::array<TSet, 8>> tsets;  // [slot][delta]
+    float *k2_partial = nullptr;
+    size_t k2_partial_floats = 0;
+    long long k2_launches = 0, k1_fallbacks = 0;
+
     // Kernel timing (tc_profile).
     bool profile = false;
     std::vector<cudaEvent_t> ev_pool;   // pairs (start, stop)
@@ -174,6 +191,14 @@ void free_all(tc_stream *s)
     cudaFree(s->d_vt);
     cudaFree(s->d_y);
     cudaFree(s->partial);
+    cudaFree(s->hist_hi);
+    cudaFree(s->hist_lo);
+    cudaFree(s->k2_partial);
+    for (auto &arr : s->tsets)
+        for (auto &t : arr) {
+            cudaFree(t.thi);
+            cudaFree(t.tlo);
+        }
     cudaFree(s->counter);
     cudaFree(s->d_err);
     cudaFreeHost(s->pin_ir);
@@ -204,6 +229,12 @@ tc_status alloc_ir(tc_stream *s)
     TC_CU(cudaMalloc(&s->ir, floats * sizeof(float)));
     TC_CU(cudaMemsetAsync(s->ir, 0, floats * sizeof(float), s->cs));
     s->slot_used.assign((size_t)s->nslots, 0);
+    for (auto &arr : s->tsets)
+        for (auto &t : arr) {
+            cudaFree(t.thi);
+            cudaFree(t.tlo);
+        }
+    s->tsets.assign((size_t)s->nslots, std::array<tc_stream::TSet, 8>{});
     return TC_OK;
 }
 
@@ -218,6 +249,13 @@ tc_status clear_state(tc_stream *s)
     s->vt_dirty = true;
     s->ir_ever_set = false;
     TC_CU(cudaMemsetAsync(s->hist, 0, (size_t)s->rows * s->cap * sizeof(float), s->cs));
+    if (s->hist_hi) {
+        TC_CU(cudaMemsetAsync(s->hist_hi, 0, (size_t)s->rows * s->cap * 2, s->cs));
+        TC_CU(cudaMemsetAsync(s->hist_lo, 0, (size_t)s->rows * s->cap * 2, s->cs));
+    }
+    for (auto &arr : s->tsets)
+        for (auto &t : arr)
+            t.ready = false;
     TC_CU(cudaMemsetAsync(s->counter, 0, s->counter_n * sizeof(unsigned), s->cs));
     TC_CU(cudaMemsetAsync(s->d_err, 0, sizeof(int), s->cs));
     return TC_OK;
@@ -235,8 +273,8 @@ tc_status open_common(tc_stream *s)
     // History row: `keep` samples behind the next push (L taps plus the
     // largest tap chunk and alignment), the push itself, and one output tile
     // of overrun. Doubled so that a compaction copy never overlaps itself.
-    s->keep = round_up((long long)s->L + tc::K1_KC_MAX + 8, 4);
-    s->cap = round_up(2 * s->keep + (long long)s->max_push + tc::K1_MO + 160, 64);
+    s->keep = round_up((long long)s->L + tc::K1_KC_MAX + 16, 8);
+    s->cap = round_up(2 * s->keep + (long long)s->max_push + 512 + 160, 64);
     TC_CU(cudaMalloc(&s->hist, (size_t)s->rows * s->cap * sizeof(float)));
 
     s->Lpad = round_up((long long)s->L + 4 + tc::K1_KC_MAX, 4);
@@ -261,6 +299,14 @@ tc_status open_common(tc_stream *s)
     TC_CU(cudaMalloc(&s->partial, s->partial_floats * sizeof(float)));
     TC_CU(cudaMalloc(&s->counter, s->counter_n * sizeof(unsigned)));
     TC_CU(cudaMalloc(&s->d_err, sizeof(int)));
+    if (s->prec != TC_FP32) {
+        TC_CU(cudaMalloc(&s->hist_hi, (size_t)s->rows * s->cap * 2));
+        TC_CU(cudaMalloc(&s->hist_lo, (size_t)s->rows * s->cap * 2));
+        TC_CU(tc::encode_bf16_2d(&s->mx_hi, s->hist_hi, (unsigned long long)s->cap, s->rows,
+                                 (unsigned long long)s->cap * 2, tc::k2_kblock(), tc::k2_tile_m()));
+        TC_CU(tc::encode_bf16_2d(&s->mx_lo, s->hist_lo, (unsigned long long)s->cap, s->rows,
+                                 (unsigned long long)s->cap * 2, tc::k2_kblock(), tc::k2_tile_m()));
+    }
     TC_TRY(clear_state(s));
     TC_CU(cudaStreamSynchronize(s->cs));
     return TC_OK;
@@ -282,8 +328,8 @@ tc_status open_any(int kind, size_t rows, size_t items, size_t nin, size_t nsets
         return fail(TC_EINVAL, "size out of range");
     if (prec != TC_FP32 && prec != TC_BF16 && prec != TC_BF16_SPLIT)
         return fail(TC_EINVAL, "unknown precision %d", (int)prec);
-    if (prec != TC_FP32)
-        return fail(TC_EUNSUPPORTED, "BF16 tensor-core path is not available for this stream kind");
+    if (prec != TC_FP32 && !(kind == KIND_GROUP && shared_ir))
+        return fail(TC_EUNSUPPORTED, "the BF16 tensor-core path needs one IR shared by all channels");
     tc_stream *s = new (std::nothrow) tc_stream();
     if (!s)
         return fail(TC_ENOMEM, "host allocation failed");
@@ -397,6 +443,8 @@ tc_status set_ir_impl(tc_stream *s, const float *h, size_t n, long long sample, 
         TC_CU(cudaEventRecord(s->ev_ir, s->cs));
         src = s->ir_stage;
     }
+    for (auto &t : s->tsets[(size_t)slot])
+        t.ready = false;  // the slot gets a new IR: its Toeplitz tiles are stale
     float *dst = s->ir + (size_t)slot * sets * 4 * (size_t)s->Lpad;
     TC_CU(tc::ir_prep_launch(src, src_pitch, (long long)n, (int)sets, dst, 4 * s->Lpad, s->Lpad, s->Lpad, s->cs));
 
@@ -414,7 +462,7 @@ tc_status ensure_room(tc_stream *s, long long n)
 {
     if (s->pos + n + tc::K1_MO + 8 <= s->base + s->cap)
         return TC_OK;
-    const long long nb = floor4(s->pos - s->keep);
+    const long long nb = floor8(s->pos - s->keep);
     const long long len = s->pos - nb;
     const long long shift = nb - s->base;
     if (shift < len || len + n + tc::K1_MO + 8 > s->cap)
@@ -422,7 +470,58 @@ tc_status ensure_room(tc_stream *s, long long n)
     TC_CU(cudaMemcpy2DAsync(s->hist, (size_t)s->cap * sizeof(float), s->hist + shift,
                             (size_t)s->cap * sizeof(float), (size_t)len * sizeof(float), s->rows,
                             cudaMemcpyDeviceToDevice, s->cs));
+    if (s->hist_hi) {
+        for (void *hb : {s->hist_hi, s->hist_lo}) {
+            char *b = static_cast<char *>(hb);
+            TC_CU(cudaMemcpy2DAsync(b, (size_t)s->cap * 2, b + shift * 2, (size_t)s->cap * 2, (size_t)len * 2,
+                                    s->rows, cudaMemcpyDeviceToDevice, s->cs));
+        }
+    }
     s->base = nb;
+    return TC_OK;
+}
+
+// bf16 hi/lo split of history columns [col0, col0 + n) (BF16 streams only).
+tc_status split_new(tc_stream *s, long long col0, long long n)
+{
+    if (!s->hist_hi)
+        return TC_OK;
+    TC_CU(tc::k2_split_launch(s->hist, s->cap, (int)s->rows, col0, n, s->hist_hi, s->hist_lo, s->cs));
+    return TC_OK;
+}
+
+tc_status prof_begin(tc_stream *s)
+{
+    if (!s->profile)
+        return TC_OK;
+    while (s->ev_pool.size() < s->ev_used + 2) {
+        cudaEvent_t e;
+        TC_CU(cudaEventCreate(&e));
+        s->ev_pool.push_back(e);
+    }
+    TC_CU(cudaEventRecord(s->ev_pool[s->ev_used], s->cs));
+    return TC_OK;
+}
+
+tc_status prof_end(tc_stream *s, long long t0, long long nout)
+{
+    if (!s->profile)
+        return TC_OK;
+    TC_CU(cudaEventRecord(s->ev_pool[s->ev_used + 1], s->cs));
+    s->ev_used += 2;
+    // Useful multiply-adds: output m sees the taps k < L with 0 <= m - k < n_end,
+    // where n_end is the number of real input samples (all pushed samples
+    // before a flush, the end of the input during one).
+    const long long n_end = s->pos_end_hint >= 0 ? s->pos_end_hint : t0 + nout;
+    double macs = 0.0;
+    for (long long m = t0; m < t0 + nout; ++m) {
+        const long long hi = std::min<long long>(m, (long long)s->L - 1);
+        const long long lo = std::max<long long>(0, m - n_end + 1);
+        if (hi >= lo)
+            macs += (double)(hi - lo + 1);
+    }
+    s->prof_macs += macs * (double)s->items * (double)s->nin;
+    s->prof_launches += 1;
     return TC_OK;
 }
 
@@ -461,36 +560,102 @@ tc_status launch_k1(tc_stream *s, long long t0, long long nout, float *y, long l
     if ((size_t)p.nitems * p.ntile > s->counter_n ||
         (size_t)plan.ctas * tc::K1_MO > s->partial_floats)
         return fail(TC_EINVAL, "internal: K1 scratch too small");
-    cudaEvent_t ev_a = nullptr, ev_b = nullptr;
-    if (s->profile) {
-        while (s->ev_pool.size() < s->ev_used + 2) {
-            cudaEvent_t e;
-            TC_CU(cudaEventCreate(&e));
-            s->ev_pool.push_back(e);
-        }
-        ev_a = s->ev_pool[s->ev_used];
-        ev_b = s->ev_pool[s->ev_used + 1];
-        s->ev_used += 2;
-        TC_CU(cudaEventRecord(ev_a, s->cs));
-    }
+    TC_TRY(prof_begin(s));
     TC_CU(tc::k1_launch(p, plan, s->cs));
-    if (s->profile) {
-        TC_CU(cudaEventRecord(ev_b, s->cs));
-        // Useful multiply-adds: output m sees the taps k < L with 0 <= m - k < n_end,
-        // where n_end is the number of real input samples (all pushed samples
-        // before a flush, the end of the input during one).
-        const long long n_end = s->pos_end_hint >= 0 ? s->pos_end_hint : t0 + nout;
-        double macs = 0.0;
-        for (long long m = t0; m < t0 + nout; ++m) {
-            const long long hi = std::min<long long>(m, (long long)s->L - 1);
-            const long long lo = std::max<long long>(0, m - n_end + 1);
-            if (hi >= lo)
-                macs += (double)(hi - lo + 1);
+    return prof_end(s, t0, nout);
+}
+
+// K2 on the tensor cores when every input sample of the launch's window
+// spawned its tache with the same IR version; false in *used otherwise.
+tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long long y_pitch, bool *used)
+{
+    *used = false;
+    const long long L = (long long)s->L;
+    const int delta = (int)((((t0 - L + 1 - s->base) % 8) + 8) % 8);
+    const long long w0 = t0 - L + 1 - delta;
+    const long long nkb = tc::k2_nkb(L, delta);
+    const int TN = tc::k2_tile_n(), TM = tc::k2_tile_m(), KB = tc::k2_kblock();
+    const long long ntile_o = (nout + TN - 1) / TN;
+    const long long hi = w0 + (ntile_o - 1) * TN + nkb * KB;  // past the last sample read
+    // Single version over [max(w0, first start), hi)?
+    int v = -1;
+    for (size_t i = 0; i < s->vt.size(); ++i)
+        if (s->vt[i].start <= std::max(w0, s->vt.front().start))
+            v = (int)i;
+    if (v < 0)
+        return TC_OK;
+    if ((size_t)v + 1 < s->vt.size() && s->vt[(size_t)v + 1].start < hi)
+        return TC_OK;
+    const int slot = s->vt[(size_t)v].slot;
+    tc_stream::TSet &ts = s->tsets[(size_t)slot][(size_t)delta];
+    if (!ts.ready) {
+        if (!ts.thi || ts.nkb < nkb) {
+            cudaFree(ts.thi);
+            cudaFree(ts.tlo);
+            ts.thi = ts.tlo = nullptr;
+            const size_t bytes = (size_t)nkb * TN * KB * 2;
+            TC_CU(cudaMalloc(&ts.thi, bytes));
+            TC_CU(cudaMalloc(&ts.tlo, bytes));
+            ts.nkb = nkb;
+            TC_CU(tc::encode_bf16_2d(&ts.mt_hi, ts.thi, (unsigned long long)KB, (unsigned long long)nkb * TN,
+                                     (unsigned long long)KB * 2, KB, TN));
+            TC_CU(tc::encode_bf16_2d(&ts.mt_lo, ts.tlo, (unsigned long long)KB, (unsigned long long)nkb * TN,
+                                     (unsigned long long)KB * 2, KB, TN));
         }
-        s->prof_macs += macs * (double)s->items * (double)s->nin;
-        s->prof_launches += 1;
+        // The slot's unshifted fp32 copy (shift e = 0) holds h[k] at index k.
+        const float *h = s->ir + (size_t)slot * s->nsets * 4 * (size_t)s->Lpad;
+        TC_CU(tc::k2_tprep_launch(h, (int)L, delta, (int)nkb, ts.thi, ts.tlo, s->cs));
+        ts.ready = true;
     }
+    tc::K2Params p{};
+    p.C = (int)s->rows;
+    p.nout = (int)nout;
+    p.ntile_c = (int)((s->rows + TM - 1) / TM);
+    p.ntile_o = (int)ntile_o;
+    p.x_col0 = w0 - s->base;
+    p.nkb = (int)nkb;
+    const long long tiles = (long long)p.ntile_c * p.ntile_o;
+    // K ranges: at most 256 blocks of serial accumulation, and about two waves.
+    long long nsplit = std::max<long long>((nkb + 255) / 256, (2 * 148 + tiles - 1) / tiles);
+    nsplit = std::min<long long>(std::min<long long>(nsplit, nkb), 64);
+    const long long kb_per = (nkb + nsplit - 1) / nsplit;
+    nsplit = (nkb + kb_per - 1) / kb_per;
+    p.nsplit = (int)nsplit;
+    p.kb_per = (int)kb_per;
+    p.y = y;
+    p.y_pitch = y_pitch;
+    p.err = s->d_err;
+    if (nsplit > 1) {
+        const size_t need = (size_t)(tiles * nsplit) * TM * TN;
+        if (need > s->k2_partial_floats) {
+            TC_CU(cudaStreamSynchronize(s->cs));
+            cudaFree(s->k2_partial);
+            s->k2_partial = nullptr;
+            TC_CU(cudaMalloc(&s->k2_partial, need * sizeof(float)));
+            s->k2_partial_floats = need;
+        }
+        p.partial = s->k2_partial;
+    }
+    tc_stream::TSet &t = ts;
+    TC_TRY(prof_begin(s));
+    TC_CU(tc::k2_launch(s->mx_hi, s->mx_lo, t.mt_hi, t.mt_lo, p, s->prec == TC_BF16 ? 1 : 3, s->cs));
+    TC_TRY(prof_end(s, t0, nout));
+    s->k2_launches++;
+    *used = true;
     return TC_OK;
+}
+
+// One convolution launch for outputs [t0, t0 + nout) of every row.
+tc_status launch_conv(tc_stream *s, long long t0, long long nout, float *y, long long y_pitch)
+{
+    if (s->prec != TC_FP32) {
+        bool used = false;
+        TC_TRY(launch_k2(s, t0, nout, y, y_pitch, &used));
+        if (used)
+            return TC_OK;
+        s->k1_fallbacks++;  // a window that straddles an IR switch runs on the FP32 gather
+    }
+    return launch_k1(s, t0, nout, y, y_pitch);
 }
 
 tc_status check_err_word(tc_stream *s)
@@ -531,9 +696,10 @@ tc_status push_impl(tc_stream *s, const float *x, size_t n, float *y, bool on_de
         TC_CU(cudaMemcpy2DAsync(hist_at, pitch_b, s->pin_x, row_b, row_b, s->rows, cudaMemcpyHostToDevice, s->cs));
         TC_CU(cudaEventRecord(s->ev_x, s->cs));
     }
+    TC_TRY(split_new(s, s->pos - s->base, (long long)n));
     TC_TRY(upload_table(s));
     float *ydst = on_device ? y : s->d_y;
-    TC_TRY(launch_k1(s, s->pos, (long long)n, ydst, (long long)n));
+    TC_TRY(launch_conv(s, s->pos, (long long)n, ydst, (long long)n));
     s->pos += (long long)n;
     if (n % s->block != 0)
         s->state = ST_ENDED;
@@ -558,8 +724,9 @@ tc_status flush_to_device(tc_stream *s, float *y, long long y_pitch)
         TC_TRY(ensure_room(s, piece));
         TC_CU(cudaMemset2DAsync(s->hist + (s->pos - s->base), (size_t)s->cap * sizeof(float), 0,
                                 (size_t)piece * sizeof(float), s->rows, s->cs));
+        TC_TRY(split_new(s, s->pos - s->base, piece));
         TC_TRY(upload_table(s));
-        TC_TRY(launch_k1(s, s->pos, piece, y + off, y_pitch));
+        TC_TRY(launch_conv(s, s->pos, piece, y + off, y_pitch));
         s->pos += piece;
         off += piece;
     }
@@ -665,6 +832,8 @@ tc_status tc_get_info(const tc_stream *s, tc_info *info)
     info->precision = (int)s->prec;
     info->state = s->state;
     info->max_versions = s->nslots;
+    info->tensor_launches = (uint64_t)s->k2_launches;
+    info->fp32_fallbacks = (uint64_t)s->k1_fallbacks;
     return TC_OK;
 }
 

@@ -1,0 +1,335 @@
+// k2_toeplitz_tc.cu -- K2: the shared-IR contraction on the tcgen05 tensor cores.
+//
+// When C channels share one IR h, a block of outputs of every channel is one
+// dense product (Sec. 4.2 suggests organising a channel's data "as a part of
+// a matrix" for GPUs):
+//     Y[c][t0+i] = sum_j X[c][w0+j] * T[i][j],   T[i][j] = h[t0 + i - w0 - j],
+// with X the input history and T a Toeplitz matrix of the IR. With the
+// window start w0 = t0 - L + 1 - delta on an 8-sample grid, T depends only on
+// delta and on j's block, not on t0. So its tiles are materialised once per IR
+// version (k2_tprep) and shared by every output tile of every push.
+//
+// Tile: M = 128 channels (TMEM lanes) x N = 256 outputs (TMEM columns), K in
+// blocks of 32 samples (64-byte swizzled rows). Warp roles: warp 0 lane 0 issues
+// TMA tensor loads of the X tile (bf16 history) and the T tile into a stage
+// ring; warp 1 lane 0 issues tcgen05.mma (kind::f16, BF16 in, FP32 accumulate
+// in TMEM) and commits each stage back to the producer; warp 2 owns the TMEM
+// allocation; all four warps read the accumulator out (tcgen05.ld) at the end.
+// Precision modes: plain BF16 (X_hi T_hi) and the hi/lo split (X_hi T_hi +
+// X_hi T_lo + X_lo T_hi), all into the same FP32 accumulator.
+//
+// Each CTA covers a bounded K range (a serial accumulation of at most
+// kb_per blocks); the ranges of a tile are added by k2_reduce in a fixed
+// pairwise tree. Every wait is an mbarrier wait bounded by %globaltimer.
+#include <algorithm>
+#include <cuda_bf16.h>
+
+#include "tc5.cuh"
+#include "tc_internal.h"
+
+namespace tc {
+
+namespace {
+
+constexpr int K2_M = 128;
+constexpr int K2_N = 256;
+constexpr int K2_KB = 32;
+constexpr int K2_THREADS = 128;
+constexpr int K2_XBYTES = K2_M * K2_KB * 2;  // 8 KB
+constexpr int K2_TBYTES = K2_N * K2_KB * 2;  // 16 KB
+
+template <int NPROD>
+struct K2Cfg {
+    static constexpr int NS = NPROD == 1 ? 8 : 4;  // stages
+    static constexpr int XOFF_LO = K2_XBYTES;       // X_lo after X_hi (split only)
+    static constexpr int TOFF = NPROD == 1 ? K2_XBYTES : 2 * K2_XBYTES;
+    static constexpr int STAGE = NPROD == 1 ? K2_XBYTES + K2_TBYTES : 2 * (K2_XBYTES + K2_TBYTES);
+    static constexpr int SMEM = NS * STAGE + 1024;  // + alignment slack
+};
+
+template <int NPROD>
+__global__ void __launch_bounds__(K2_THREADS, 1)
+    k2_toeplitz(const __grid_constant__ CUtensorMap mx_hi, const __grid_constant__ CUtensorMap mx_lo,
+                const __grid_constant__ CUtensorMap mt_hi, const __grid_constant__ CUtensorMap mt_lo, const K2Params p)
+{
+    using C = K2Cfg<NPROD>;
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full[C::NS];
+    __shared__ __align__(8) uint64_t empty[C::NS];
+    __shared__ __align__(8) uint64_t accbar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_fail;
+
+    // Swizzled tiles need 512-byte aligned stages.
+    uint8_t *const smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int lane = tid & 31;
+
+    long long u = blockIdx.x;
+    const int split = (int)(u % p.nsplit);
+    u /= p.nsplit;
+    const int tile_o = (int)(u % p.ntile_o);
+    const int tile_c = (int)(u / p.ntile_o);
+    const int kb0 = split * p.kb_per;
+    const int kb1 = min(kb0 + p.kb_per, p.nkb);
+    const int nk = kb1 - kb0;
+    const int c0 = tile_c * K2_M;
+    const long long xcol0 = p.x_col0 + (long long)tile_o * K2_N;  // history column of the tile's window start
+
+    if (tid == 0) {
+        for (int i = 0; i < C::NS; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        mbar_init(&accbar, 1);
+        s_fail = 0;
+        fence_mbar_init();
+    }
+    if (warp == 2)
+        tmem_alloc(&tmem_base, K2_N);
+    tc_fence_before_sync();
+    __syncthreads();
+    tc_fence_after_sync();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0 && lane == 0) {
+        // ---- producer ----
+        for (int i = 0; i < nk; ++i) {
+            const int st = i % C::NS;
+            const int use = i / C::NS;
+            if (use > 0 && !mbar_wait_bounded(&empty[st], (uint32_t)((use - 1) & 1), p.err, ERR_TIMEOUT_TMA)) {
+                s_fail = 1;
+                break;
+            }
+            uint8_t *sb = smem + st * C::STAGE;
+            const int kb = kb0 + i;
+            mbar_arrive_expect_tx(&full[st], (uint32_t)C::STAGE);
+            const int xc = (int)(xcol0 + (long long)kb * K2_KB);
+            tma_load_2d(sb, &mx_hi, xc, c0, &full[st]);
+            if (NPROD == 3)
+                tma_load_2d(sb + C::XOFF_LO, &mx_lo, xc, c0, &full[st]);
+            tma_load_2d(sb + C::TOFF, &mt_hi, 0, kb * K2_N, &full[st]);
+            if (NPROD == 3)
+                tma_load_2d(sb + C::TOFF + K2_TBYTES, &mt_lo, 0, kb * K2_N, &full[st]);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---- MMA issuer ----
+        const uint32_t idesc = umma_idesc_bf16(K2_M, K2_N);
+        bool ok = true;
+        for (int i = 0; i < nk; ++i) {
+            const int st = i % C::NS;
+            if (!mbar_wait_bounded(&full[st], (uint32_t)((i / C::NS) & 1), p.err, ERR_TIMEOUT_MMA)) {
+                ok = false;
+                s_fail = 1;
+                break;
+            }
+            tc_fence_after_sync();
+            const uint32_t sb = smem_u32(smem + st * C::STAGE);
+#pragma unroll
+            for (int kk = 0; kk < K2_KB / 16; ++kk) {
+                const uint32_t koff = kk * 32;  // 16 bf16 = 32 bytes along the swizzled row
+                const uint64_t xh = umma_desc_sw64(sb + koff);
+                const uint64_t th = umma_desc_sw64(sb + C::TOFF + koff);
+                umma_bf16(tmem, xh, th, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+                if (NPROD == 3) {
+                    const uint64_t xl = umma_desc_sw64(sb + C::XOFF_LO + koff);
+                    const uint64_t tl = umma_desc_sw64(sb + C::TOFF + K2_TBYTES + koff);
+                    umma_bf16(tmem, xh, tl, idesc, 1u);
+                    umma_bf16(tmem, xl, th, idesc, 1u);
+                }
+            }
+            umma_commit(&empty[st]);  // the stage is free once these MMAs are done
+        }
+        if (ok)
+            umma_commit(&accbar);
+        else
+            mbar_arrive(&accbar);  // release the epilogue; s_fail marks the result invalid
+    }
+
+    // ---- epilogue: all four warps ----
+    bool ok = true;
+    if (lane == 0)
+        ok = mbar_wait_bounded(&accbar, 0, p.err, ERR_TIMEOUT_MMA);
+    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+    if (ok)
+        mbar_try_wait(&accbar, 0);
+    tc_fence_after_sync();
+    __syncwarp();
+    const int ch = warp * 32 + lane;  // TMEM lane = channel within the tile
+    const int c = c0 + ch;
+    const bool fail = !ok || s_fail;
+    if (!fail) {
+        const uint32_t row = tmem + ((uint32_t)(warp * 32) << 16);
+        float *dst;
+        long long lim;
+        if (p.nsplit == 1) {
+            dst = p.y + (long long)c * p.y_pitch + (long long)tile_o * K2_N;
+            lim = p.nout - (long long)tile_o * K2_N;
+        } else {
+            dst = p.partial + ((((long long)tile_c * p.ntile_o + tile_o) * p.nsplit + split) * K2_M + ch) * K2_N;
+            lim = K2_N;
+        }
+#pragma unroll 1
+        for (int cc = 0; cc < K2_N / 32; ++cc) {
+            float v[32];
+            tmem_ld_32x32(row + cc * 32, v);
+            if (c < p.C) {
+                if (lim >= (cc + 1) * 32) {
+#pragma unroll
+                    for (int j = 0; j < 32; j += 4)
+                        *reinterpret_cast<float4 *>(dst + cc * 32 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (cc * 32 + j < lim)
+                            dst[cc * 32 + j] = v[j];
+                }
+            }
+        }
+    }
+    tc_fence_before_sync();
+    __syncthreads();
+    if (warp == 2) {
+        tc_fence_after_sync();
+        tmem_dealloc(tmem, K2_N);
+    }
+}
+
+// Adds the nsplit K-range partials of each (channel, output) by a fixed
+// pairwise tree (adjacent pairs, zero-padded to 64 leaves) and writes y.
+__global__ void k2_reduce(const float *__restrict__ partial, int nsplit, int C, int ntile_o, int nout, float *y,
+                          long long y_pitch)
+{
+    const long long total = (long long)C * nout;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(q / nout);
+        const int o = (int)(q % nout);
+        const int tc_ = c / K2_M, ch = c % K2_M, to = o / K2_N, oo = o % K2_N;
+        const float *src = partial + ((((long long)tc_ * ntile_o + to) * nsplit) * K2_M + ch) * K2_N + oo;
+        float v[64];
+#pragma unroll
+        for (int s = 0; s < 64; ++s)
+            v[s] = (s < nsplit) ? src[(long long)s * K2_M * K2_N] : 0.f;
+#pragma unroll
+        for (int w = 32; w >= 1; w >>= 1) {
+#pragma unroll
+            for (int s = 0; s < w; ++s)
+                v[s] = v[2 * s] + v[2 * s + 1];
+        }
+        y[(long long)c * y_pitch + o] = v[0];
+    }
+}
+
+// Materialises the Toeplitz tiles of one IR for alignment shift delta:
+//   T[kb][i][j] = h[L - 1 + delta + i - 32 kb - j]  (0 outside [0, L)),
+// as bf16 hi = bf16(h) and lo = bf16(h - hi), row-major [kb][256][32].
+__global__ void k2_tprep(const float *__restrict__ h, int L, int delta, int nkb, __nv_bfloat16 *thi,
+                         __nv_bfloat16 *tlo)
+{
+    const long long total = (long long)nkb * K2_N * K2_KB;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(q % K2_KB);
+        const long long r = q / K2_KB;
+        const int i = (int)(r % K2_N);
+        const long long kb = r / K2_N;
+        const long long k = (long long)L - 1 + delta + i - K2_KB * kb - j;
+        const float v = (k >= 0 && k < L) ? h[k] : 0.f;
+        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+        thi[q] = hi;
+        tlo[q] = __float2bfloat16_rn(v - __bfloat162float(hi));
+    }
+}
+
+// Splits new history samples into bf16 hi = bf16(x) and lo = bf16(x - hi):
+// rows r < rows, columns [col0, col0 + n) of pitch-`pitch` histories.
+__global__ void k2_split(const float *__restrict__ hist, long long pitch, int rows, long long col0, long long n,
+                         __nv_bfloat16 *hhi, __nv_bfloat16 *hlo)
+{
+    const long long total = (long long)rows * n;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const long long r = q / n;
+        const long long idx = r * pitch + col0 + q % n;
+        const float v = hist[idx];
+        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+        hhi[idx] = hi;
+        hlo[idx] = __float2bfloat16_rn(v - __bfloat162float(hi));
+    }
+}
+
+unsigned grid_for(long long work)
+{
+    long long b = (work + 255) / 256;
+    return (unsigned)std::max<long long>(1, std::min<long long>(b, 8192));
+}
+
+}  // namespace
+
+int k2_tile_m() { return K2_M; }
+int k2_tile_n() { return K2_N; }
+int k2_kblock() { return K2_KB; }
+
+long long k2_nkb(long long L, int delta) { return (L - 1 + delta + K2_N + K2_KB - 1) / K2_KB; }
+
+cudaError_t k2_tprep_launch(const float *h, int L, int delta, int nkb, void *thi, void *tlo, cudaStream_t st)
+{
+    const long long work = (long long)nkb * K2_N * K2_KB;
+    k2_tprep<<<grid_for(work), 256, 0, st>>>(h, L, delta, nkb, (__nv_bfloat16 *)thi, (__nv_bfloat16 *)tlo);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t k2_split_launch(const float *hist, long long pitch, int rows, long long col0, long long n, void *hhi,
+                            void *hlo, cudaStream_t st)
+{
+    if (n <= 0)
+        return cudaSuccess;
+    k2_split<<<grid_for((long long)rows * n), 256, 0, st>>>(hist, pitch, rows, col0, n, (__nv_bfloat16 *)hhi,
+                                                           (__nv_bfloat16 *)hlo);
+    count_launch();
+    return cudaGetLastError();
+}
+
+size_t k2_smem_bytes(int nprod) { return nprod == 1 ? K2Cfg<1>::SMEM : K2Cfg<3>::SMEM; }
+
+cudaError_t k2_launch(const CUtensorMap &mx_hi, const CUtensorMap &mx_lo, const CUtensorMap &mt_hi,
+                      const CUtensorMap &mt_lo, const K2Params &p, int nprod, cudaStream_t st)
+{
+    static bool attr[64][2] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    if (dev < 0 || dev >= 64 || (nprod != 1 && nprod != 3) || p.nsplit < 1 || p.nsplit > 64)
+        return cudaErrorInvalidValue;
+    const int vi = nprod == 1 ? 0 : 1;
+    const size_t smem = k2_smem_bytes(nprod);
+    if (!attr[dev][vi]) {
+        e = nprod == 1 ? cudaFuncSetAttribute(k2_toeplitz<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                       : cudaFuncSetAttribute(k2_toeplitz<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        attr[dev][vi] = true;
+    }
+    const long long units = (long long)p.ntile_c * p.ntile_o * p.nsplit;
+    if (units <= 0)
+        return cudaSuccess;
+    if (nprod == 1)
+        k2_toeplitz<1><<<(unsigned)units, K2_THREADS, smem, st>>>(mx_hi, mx_lo, mt_hi, mt_lo, p);
+    else
+        k2_toeplitz<3><<<(unsigned)units, K2_THREADS, smem, st>>>(mx_hi, mx_lo, mt_hi, mt_lo, p);
+    count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess || p.nsplit == 1)
+        return e;
+    const long long work = (long long)p.C * p.nout;
+    k2_reduce<<<grid_for(work), 256, 0, st>>>(p.partial, p.nsplit, p.C, p.ntile_o, p.nout, p.y, p.y_pitch);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace tc

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace tc {
@@ -101,6 +102,42 @@ cudaError_t k1_launch(K1Params &p, const K1Plan &plan, cudaStream_t st);
 cudaError_t ir_prep_launch(const float *src, long long src_pitch, long long n, int rows,
                            float *dst, long long row_stride, long long phase, long long Lpad,
                            cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// K2: shared-IR contraction on the tensor cores (k2_toeplitz_tc.cu).
+//   Y[c][t0+i] = sum_j X[c][w0+j] T[i][j],  T[i][j] = h[L - 1 + delta + i - j],
+//   w0 = t0 - L + 1 - delta on an 8-sample grid of the history.
+// Tiles: 128 channels x 256 outputs x K blocks of 32 samples.
+// ---------------------------------------------------------------------------
+struct K2Params {
+    int C;                   // channels (rows of the history)
+    int nout;                // outputs per channel in this launch
+    int ntile_c, ntile_o;    // ceil(C / 128), ceil(nout / 256)
+    long long x_col0;        // history column of w0 for output tile 0 (multiple of 8)
+    int nkb;                 // K blocks per output tile
+    int nsplit, kb_per;      // K ranges per tile and blocks per range
+    float *y;                // y[c * y_pitch + j], j < nout
+    long long y_pitch;
+    float *partial;          // [ntile_c][ntile_o][nsplit][128][256] (nsplit > 1)
+    int *err;
+};
+int k2_tile_m();
+int k2_tile_n();
+int k2_kblock();
+long long k2_nkb(long long L, int delta);
+size_t k2_smem_bytes(int nprod);
+// Toeplitz tiles of IR h (fp32, L taps) for shift delta: hi/lo bf16 [nkb][256][32].
+cudaError_t k2_tprep_launch(const float *h, int L, int delta, int nkb, void *thi, void *tlo, cudaStream_t st);
+// bf16 hi/lo split of history columns [col0, col0 + n) of `rows` rows.
+cudaError_t k2_split_launch(const float *hist, long long pitch, int rows, long long col0, long long n, void *hhi,
+                            void *hlo, cudaStream_t st);
+// nprod = 1 (BF16) or 3 (BF16 hi/lo split). Maps: X over the bf16 history
+// [rows][pitch], box 32 x 128; T over [nkb * 256][32], box 32 x 256; 64-byte swizzle.
+cudaError_t k2_launch(const CUtensorMap &mx_hi, const CUtensorMap &mx_lo, const CUtensorMap &mt_hi,
+                      const CUtensorMap &mt_lo, const K2Params &p, int nprod, cudaStream_t st);
+// Encodes a 2-D bf16 tensor map (inner dimension first), 64-byte swizzle.
+cudaError_t encode_bf16_2d(CUtensorMap *map, const void *base, unsigned long long dim0, unsigned long long dim1,
+                           unsigned long long stride1_bytes, unsigned box0, unsigned box1);
 
 // Sets the calling thread's tc_last_error() message.
 void set_last_error(const char *msg);

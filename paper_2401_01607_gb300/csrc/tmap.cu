@@ -1,0 +1,41 @@
+// tmap.cu -- tensor-map encoding through the runtime's driver entry point
+// (no link-time dependency on libcuda).
+#include <mutex>
+
+#include "tc_internal.h"
+
+namespace tc {
+
+namespace {
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+std::once_flag g_once;
+EncodeTiledFn g_encode = nullptr;
+cudaError_t g_encode_err = cudaSuccess;
+}  // namespace
+
+cudaError_t encode_bf16_2d(CUtensorMap *map, const void *base, unsigned long long dim0, unsigned long long dim1,
+                           unsigned long long stride1_bytes, unsigned box0, unsigned box1)
+{
+    std::call_once(g_once, [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        g_encode_err = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (g_encode_err == cudaSuccess && (q != cudaDriverEntryPointSuccess || !fn))
+            g_encode_err = cudaErrorSymbolNotFound;
+        g_encode = reinterpret_cast<EncodeTiledFn>(fn);
+    });
+    if (g_encode_err != cudaSuccess)
+        return g_encode_err;
+    const cuuint64_t dims[2] = {dim0, dim1};
+    const cuuint64_t strides[1] = {stride1_bytes};
+    const cuuint32_t box[2] = {box0, box1};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides,
+                                box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+}  // namespace tc

@@ -1,0 +1,91 @@
+"""Shared-IR groups on the tensor cores (K2): BF16 and BF16 hi/lo split against the FP64 oracle.
+
+Tolerances (relative L2): BF16 hi/lo split <= 1e-5, plain BF16 <= 3e-3.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_helpers import TOL, max_abs, rel_l2
+from paper_2401_01607_gb300 import capi, synth
+
+pytestmark = pytest.mark.gpu
+
+PREC = {"bf16": capi.TC_BF16, "bf16split": capi.TC_BF16_SPLIT}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import paper_2401_01607_gb300 as pkg
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pkg.build()
+    capi.load()
+
+
+def run_group(X, H, vstart, L, block, prec, max_push):
+    """Streams X [C, N] through a shared-IR group; returns (y [C, N+L-1], info)."""
+    C, N = X.shape
+    s = capi.tc_open_group(C, L, block, True, PREC[prec], max_push)
+    try:
+        outs, pos, v = [], 0, 0
+        while pos < N:
+            n = min(max_push, N - pos)
+            while v < len(vstart) and vstart[v] < pos + n:
+                capi.tc_set_ir_rows(s, H[v][None], H.shape[1], max(int(vstart[v]), pos))
+                v += 1
+            y = np.empty((C, n), np.float32)
+            capi.tc_push(s, np.ascontiguousarray(X[:, pos:pos + n]), n, y)
+            outs.append(y)
+            pos += n
+        tail = np.empty((C, L - 1), np.float32)
+        capi.tc_flush(s, tail, L - 1)
+        info = capi.tc_get_info(s)
+    finally:
+        capi.tc_close(s)
+    return np.concatenate(outs + [tail], axis=1), info
+
+
+def check(y, X, H, vstart, block, prec, rows=None):
+    rows = range(X.shape[0]) if rows is None else rows
+    errs = []
+    for c in rows:
+        ref = oracle.buffer(X[c], H, np.asarray(vstart, np.int64), block)
+        errs.append(rel_l2(y[c], ref))
+    worst = max(errs)
+    print(f"{prec}: worst rel_l2 {worst:.3g}")
+    assert worst <= TOL[prec], worst
+
+
+@pytest.mark.parametrize("prec", ["bf16split", "bf16"])
+def test_shared_ir_small(prec):
+    """200 channels (two channel tiles, ragged), ragged pushes and tail."""
+    C, N, L, B = 200, 5000, 3000, 256
+    X = synth.audio_block(C, N, 3000)
+    H = synth.decayed_ir(L, 0.2 * L, 77)[None]
+    y, info = run_group(X, H, [0], L, B, prec, 1024)
+    assert info.tensor_launches > 0 and info.fp32_fallbacks == 0
+    check(y, X, H, [0], B, prec, rows=[0, 1, 127, 128, 150, 199])
+
+
+@pytest.mark.parametrize("prec", ["bf16split", "bf16"])
+def test_shared_ir_long_split_k(prec):
+    """L = 20000: K split over several CTAs, then the pairwise K-range reduction."""
+    C, N, L, B = 256, 3000, 20_000, 256
+    X = synth.audio_block(C, N, 4000)
+    H = synth.decayed_ir(L, 0.2 * L, 78)[None]
+    y, info = run_group(X, H, [0], L, B, prec, 3072)
+    assert info.tensor_launches > 0
+    check(y, X, H, [0], B, prec, rows=[0, 97, 255])
+
+
+def test_shared_ir_switch_falls_back_exactly():
+    """An IR switch mid-stream: windows that straddle it run on the FP32 gather, the rest on K2."""
+    C, N, L, B = 130, 6000, 1000, 128
+    X = synth.audio_block(C, N, 5000)
+    H = np.stack([synth.decayed_ir(L, 200.0, 90 + v) for v in range(2)])
+    vs = [0, 2500]
+    y, info = run_group(X, H, vs, L, B, "bf16split", 512)
+    assert info.tensor_launches > 0 and info.fp32_fallbacks > 0
+    check(y, X, H, vs, B, "bf16split", rows=[0, 64, 129])

@@ -271,6 +271,105 @@ class Runner:
         self.capi.tc_close(self.s)
 
 
+def load_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def bench_shared(torch, steps: int, warmup: int, P: int = 8192) -> dict:
+    """Shared-IR workload: 1024 streams x 5 s at 48 kHz, one IR L = 96000 (tau 19200), block 256.
+    Each precision is one full pass per step (pushes of P samples, device pointers, then the flush)."""
+    from paper_2401_01607_gb300 import capi
+    import oracle
+    C, N, L, B = 1024, 240_000, 96_000, 256
+    w = synth.shared(C=C, N=N, L=L, block=B)
+    npush = math.ceil(N / P)
+    xp = np.zeros((npush, C, P), np.float32)
+    for i in range(npush):
+        seg = w.x[:, i * P:(i + 1) * P]
+        xp[i].reshape(-1)[:seg.size] = seg.reshape(-1)
+    x_d = torch.from_numpy(xp).cuda()
+    h_d = torch.from_numpy(np.ascontiguousarray(w.H[0][None])).cuda()
+    y_d = torch.empty((npush, C, P), device="cuda")
+    tail_d = torch.empty((C, L - 1), device="cuda")
+    macs = C * N * L
+    peaks = load_peaks()
+    bf16_peak = float(peaks.get("bf16_tflops_sustained", 1690.8))
+    out = {"workload": "1024 streams x 240000 samples (5 s @ 48 kHz), one shared IR L=96000 tau=19200, "
+                       "block 256, pushes of %d" % P, "tap_macs": macs}
+    ts = torch.cuda.Stream()
+    rng = np.random.default_rng(7)
+    picks = [(int(rng.integers(C)), int(rng.integers(N + L - 1))) for _ in range(24)]
+    for name, prec in (("bf16split", capi.TC_BF16_SPLIT), ("bf16", capi.TC_BF16), ("fp32", capi.TC_FP32)):
+        s = capi.tc_open_group(C, L, B, True, prec, P)
+        capi.tc_set_cuda_stream(s, ts)
+
+        def step():
+            capi.tc_reset(s)
+            capi.tc_set_ir_rows(s, int(h_d.data_ptr()), L, 0, on_device=True)
+            for i in range(npush):
+                n = min(P, N - i * P)
+                capi.tc_push(s, int(x_d[i].data_ptr()), n, int(y_d[i].data_ptr()), on_device=True)
+            capi.tc_flush_dev(s, int(tail_d.data_ptr()))
+
+        nst = 1 if name == "fp32" else steps
+        for _ in range(max(1, warmup if name != "fp32" else 1)):
+            step()
+        torch.cuda.synchronize()
+        capi.tc_profile(s, True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ts)
+        for _ in range(nst):
+            step()
+        e1.record(ts)
+        e1.synchronize()
+        k_ms, k_n, k_macs = capi.tc_profile_read(s)
+        capi.tc_profile(s, False)
+        info = capi.tc_get_info(s)
+        capi.tc_close(s)
+        ms = e0.elapsed_time(e1) / nst
+        # Sampled outputs against Eq. (4) one by one (FP64).
+        y = y_d.cpu().numpy()
+        tail = tail_d.cpu().numpy()
+        got, ref = [], []
+        for c, m in picks:
+            if m < N:
+                i, j = divmod(m, P)
+                n = min(P, N - i * P)
+                got.append(y[i].reshape(-1)[c * n + j])
+            else:
+                got.append(tail[c, m - N])
+            ref.append(oracle.direct_at(w.x[c], w.H, w.vstart, m))
+        got, ref = np.array(got, np.float64), np.array(ref)
+        r = {"ms_per_step": ms, "value": macs / (ms / 1e3), "unit": "tap-MAC/s",
+             "kernel_ms_per_step": k_ms / nst, "launches_per_step": k_n / nst,
+             "check": {"sampled_outputs": len(picks),
+                       "rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+                       "max_abs": float(np.max(np.abs(got - ref)))},
+             "tensor_launches": int(info.tensor_launches), "fp32_fallbacks": int(info.fp32_fallbacks)}
+        if name != "fp32":
+            nprod = 3 if name == "bf16split" else 1
+            tflops = 2.0 * nprod * k_macs / (k_ms / 1e3) / 1e12 if k_ms > 0 else 0.0
+            r["roofline"] = {"bound": "tensor", "achieved": tflops, "peak": bf16_peak, "unit": "TFLOP/s",
+                             "frac": tflops / bf16_peak, "traffic": None,
+                             "kernel": "k2_toeplitz (tcgen05 kind::f16) + k2_reduce",
+                             "peak_basis": "measured cuBLAS bf16, sustained (MEASURED_PEAKS.json)",
+                             "flops_counted": f"2 x {nprod} products x useful tap-MACs"}
+        else:
+            tflops = 2.0 * k_macs / (k_ms / 1e3) / 1e12 if k_ms > 0 else 0.0
+            r["roofline"] = {"bound": "alu", "achieved": tflops, "peak": fp32_peak_tflops(SM_MAX_MHZ),
+                             "unit": "TFLOP/s", "frac": tflops / fp32_peak_tflops(SM_MAX_MHZ),
+                             "kernel": "k1_gather (FP32 FMA)"}
+        out[name] = r
+    del x_d, y_d, tail_d, h_d
+    torch.cuda.empty_cache()
+    return out
+
+
 def check_sampled(runner, n_check=64) -> dict:
     """Sampled outputs of the last device step against Eq. (4) computed one by one (FP64 oracle)."""
     import oracle
@@ -342,6 +441,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-latency", action="store_true")
     ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--no-shared", action="store_true", help="skip the shared-IR tensor-core section")
+    ap.add_argument("--only-shared", action="store_true", help="run only the shared-IR section")
     ap.add_argument("--cpu-samples", type=int, default=30_000)
     ap.add_argument("--ref-samples", type=int, default=6_000)
     args = ap.parse_args()
@@ -365,6 +466,11 @@ def main():
     pkg.build()
     torch.cuda.set_device(dist.local)
     dev = torch.cuda.current_device()
+
+    if args.only_shared:
+        print(json.dumps({"shared_ir": bench_shared(torch, max(1, args.steps), max(1, args.warmup))}), flush=True)
+        dist.close()
+        return
 
     w = synth.multi(C=C_STREAMS, N=N_SAMPLES, L=L_TAPS, block=BLOCK, swap_every=SWAP,
                     stream0=dist.rank * C_STREAMS)
@@ -481,6 +587,11 @@ def main():
                    "mode": "64 streams, one 128-sample block per tc_push_block call, host buffers"}
 
     runner.close()
+    del runner
+    torch.cuda.empty_cache()
+    shared = None
+    if not args.no_shared and dist.world == 1:
+        shared = bench_shared(torch, steps=2, warmup=1)
     if dist.rank == 0:
         per_stream_rt = FS * L_TAPS  # tap-MAC/s one real-time stream needs
         line = {"metric": METRIC, "value": value, "unit": "tap-MAC/s", "n_gpus": dist.world,
@@ -489,7 +600,7 @@ def main():
                 "data": "synthetic", "config": workload_config(P),
                 "realtime_streams_48k": value / per_stream_rt,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "gpu_launches": int(launches), "latency": latency, "check": check,
+                "gpu_launches": int(launches), "latency": latency, "check": check, "shared_ir": shared,
                 "autotune_push_ms_per_sample": {str(k): v for k, v in tune.items()} or None}
         print(json.dumps(line), flush=True)
     dist.close()

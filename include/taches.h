@@ -245,6 +245,17 @@ const char *tc_status_str(tc_status st);
  * every launch, on every stream. */
 uint64_t tc_kernel_launches(void);
 
+/* Tuning knobs (autotuner and experiments); value -1 restores the default.
+ *   TC_TUNE_K1_CHUNK     tap chunk of the FP32 gather: 0 = 640, 1 = 2560,
+ *                        2 = 8320 taps per CTA (default: picked per launch)
+ *   TC_TUNE_K2_RANGE     K blocks (of 32 samples) accumulated serially on the
+ *                        tensor cores before the pairwise reduction of
+ *                        ranges (default 48 for the BF16 split, 256 for BF16;
+ *                        1..4096)
+ * Errors: TC_EINVAL for an unknown knob or value out of range. */
+typedef enum tc_tune_knob { TC_TUNE_K1_CHUNK = 0, TC_TUNE_K2_RANGE = 1 } tc_tune_knob;
+tc_status tc_set_tuning(tc_stream *s, int knob, long long value);
+
 /* Kernel timing (tracing aid). With enable = 1, each later convolution kernel
  * launch of this stream is bracketed by CUDA events on the stream that runs
  * it. tc_profile_read waits for the stream, then returns the summed event

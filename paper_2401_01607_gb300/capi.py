@@ -65,6 +65,7 @@ _SIGS = {
     "tc_sync": [_vp],
     "tc_convolve": [_vp, _sz, _vp, _sz, _vp, _vp],
     "tc_convolve_noalloc": [_vp, _sz, _vp, _sz, _vp, _vp],
+    "tc_set_tuning": [_vp, _int, ctypes.c_longlong],
     "tc_profile": [_vp, _int],
     "tc_profile_read": [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_u64), ctypes.POINTER(ctypes.c_double)],
 }
@@ -235,6 +236,13 @@ def tc_convolve(x, N: int, h, L: int, y, cuda_stream=None) -> None:
     cs = None if cuda_stream is None else (cuda_stream if isinstance(cuda_stream, int) else
                                            int(cuda_stream.cuda_stream))
     _call("tc_convolve", _dev_ptr(x), N, _dev_ptr(h), L, _dev_ptr(y), cs)
+
+
+TC_TUNE_K1_CHUNK, TC_TUNE_K2_RANGE = 0, 1
+
+
+def tc_set_tuning(s: int, knob: int, value: int) -> None:
+    _call("tc_set_tuning", s, int(knob), int(value))
 
 
 def tc_profile(s: int, enable: bool = True) -> None:

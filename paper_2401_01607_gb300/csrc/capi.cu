@@ -138,6 +138,7 @@ struct tc_stream {
     size_t counter_n = 0;
     int *d_err = nullptr;
     int k1_variant_fixed = -1;  // -1: chosen per launch
+    long long k2_range = -1;    // K blocks per tensor-core CTA range (-1: by precision)
 
     // BF16 tensor-core path (shared-IR groups): bf16 hi/lo histories and, per
     // IR slot and alignment shift delta, the materialised Toeplitz tiles.
@@ -615,9 +616,24 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
     p.x_col0 = w0 - s->base;
     p.nkb = (int)nkb;
     const long long tiles = (long long)p.ntile_c * p.ntile_o;
-    // K ranges: at most 256 blocks of serial accumulation, and about two waves.
-    long long nsplit = std::max<long long>((nkb + 255) / 256, (2 * 148 + tiles - 1) / tiles);
-    nsplit = std::min<long long>(std::min<long long>(nsplit, nkb), 64);
+    // TMEM runs of `range` K blocks (the BF16 split keeps ~48 for <= 1e-5;
+    // plain BF16 is limited by its operands, not by the run). K parts per tile:
+    // the fewest that fill the GPU's waves to >= 90 %.
+    p.range = (int)(s->k2_range > 0 ? s->k2_range : (s->prec == TC_BF16_SPLIT ? 48 : 4096));
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+    long long nsplit = 1;
+    double best = 0.0;
+    for (long long ns = 1; ns <= 8 && ns <= nkb; ++ns) {
+        const long long units = tiles * ns;
+        const double eff = (double)units / (double)(((units + sms - 1) / sms) * sms);
+        if (eff > best + 1e-9) {
+            best = eff;
+            nsplit = ns;
+        }
+        if (eff >= 0.9)
+            break;
+    }
     const long long kb_per = (nkb + nsplit - 1) / nsplit;
     nsplit = (nkb + kb_per - 1) / kb_per;
     p.nsplit = (int)nsplit;
@@ -986,6 +1002,29 @@ const char *tc_status_str(tc_status st)
 }
 
 uint64_t tc_kernel_launches(void) { return tc::launches(); }
+
+tc_status tc_set_tuning(tc_stream *s, int knob, long long value)
+{
+    TC_TRY(check_stream(s));
+    switch (knob) {
+    case TC_TUNE_K1_CHUNK:
+        if (value < -1 || value >= tc::K1_NVARIANTS)
+            return fail(TC_EINVAL, "TC_TUNE_K1_CHUNK must be -1 or in [0, %d)", tc::K1_NVARIANTS);
+        s->k1_variant_fixed = (int)value;
+        return TC_OK;
+    case TC_TUNE_K2_RANGE:
+        if (value == -1) {
+            s->k2_range = -1;
+            return TC_OK;
+        }
+        if (value < 1 || value > 4096)
+            return fail(TC_EINVAL, "TC_TUNE_K2_RANGE must be -1 or in [1, 4096]");
+        s->k2_range = value;
+        return TC_OK;
+    default:
+        return fail(TC_EINVAL, "unknown tuning knob %d", knob);
+    }
+}
 
 tc_status tc_profile(tc_stream *s, int enable)
 {

@@ -18,9 +18,16 @@
 // Precision modes: plain BF16 (X_hi T_hi) and the hi/lo split (X_hi T_hi +
 // X_hi T_lo + X_lo T_hi), all into the same FP32 accumulator.
 //
-// Each CTA covers a bounded K range (a serial accumulation of at most
-// kb_per blocks); the ranges of a tile are added by k2_reduce in a fixed
-// pairwise tree. Every wait is an mbarrier wait bounded by %globaltimer.
+// FP32 accumulation in TMEM loses accuracy with the length of a serial run
+// (measured: BF16-split error 6e-6 at 48 K blocks, 2e-5 at 256). So the MMA
+// thread accumulates a tile's K blocks in runs of `range` blocks, alternating
+// between two TMEM accumulators. Eight epilogue warps drain each finished run
+// into FP32 running sums in registers (round-to-nearest adds), which overlaps
+// the next run's MMAs; the tensor core never waits for the drain. A tile's K
+// range may also be split over `nsplit` CTAs (wave balance). Their sums are
+// added by k2_reduce in a fixed pairwise tree. Every wait is an mbarrier wait
+// bounded by %globaltimer, and a failing role raises a shared flag so the
+// others stop early.
 #include <algorithm>
 #include <cuda_bf16.h>
 
@@ -34,7 +41,9 @@ namespace {
 constexpr int K2_M = 128;
 constexpr int K2_N = 256;
 constexpr int K2_KB = 32;
-constexpr int K2_THREADS = 128;
+constexpr int K2_ROLE_WARPS = 4;   // producer, MMA, TMEM owner, spare
+constexpr int K2_EPI_WARPS = 8;    // two per TMEM lane quarter (column halves)
+constexpr int K2_THREADS = 32 * (K2_ROLE_WARPS + K2_EPI_WARPS);
 constexpr int K2_XBYTES = K2_M * K2_KB * 2;  // 8 KB
 constexpr int K2_TBYTES = K2_N * K2_KB * 2;  // 16 KB
 
@@ -56,9 +65,10 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full[C::NS];
     __shared__ __align__(8) uint64_t empty[C::NS];
-    __shared__ __align__(8) uint64_t accbar;
+    __shared__ __align__(8) uint64_t accfull[2];
+    __shared__ __align__(8) uint64_t accfree[2];
     __shared__ uint32_t tmem_base;
-    __shared__ int s_fail;
+    __shared__ volatile int s_fail;
 
     // Swizzled tiles need 512-byte aligned stages.
     uint8_t *const smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -67,14 +77,16 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
     const int warp = tid >> 5;
     const int lane = tid & 31;
 
+    // Unit = (channel tile, output tile, K part).
     long long u = blockIdx.x;
-    const int split = (int)(u % p.nsplit);
+    const int part = (int)(u % p.nsplit);
     u /= p.nsplit;
     const int tile_o = (int)(u % p.ntile_o);
     const int tile_c = (int)(u / p.ntile_o);
-    const int kb0 = split * p.kb_per;
+    const int kb0 = part * p.kb_per;
     const int kb1 = min(kb0 + p.kb_per, p.nkb);
-    const int nk = kb1 - kb0;
+    const int nk = max(kb1 - kb0, 0);
+    const int nr = (nk + p.range - 1) / p.range;  // TMEM runs of this unit
     const int c0 = tile_c * K2_M;
     const long long xcol0 = p.x_col0 + (long long)tile_o * K2_N;  // history column of the tile's window start
 
@@ -83,109 +95,162 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], 1);
         }
-        mbar_init(&accbar, 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&accfull[i], 1);
+            mbar_init(&accfree[i], K2_EPI_WARPS);
+        }
         s_fail = 0;
         fence_mbar_init();
     }
     if (warp == 2)
-        tmem_alloc(&tmem_base, K2_N);
+        tmem_alloc(&tmem_base, 2 * K2_N);
     tc_fence_before_sync();
     __syncthreads();
     tc_fence_after_sync();
     const uint32_t tmem = tmem_base;
 
-    if (warp == 0 && lane == 0) {
-        // ---- producer ----
-        for (int i = 0; i < nk; ++i) {
-            const int st = i % C::NS;
-            const int use = i / C::NS;
-            if (use > 0 && !mbar_wait_bounded(&empty[st], (uint32_t)((use - 1) & 1), p.err, ERR_TIMEOUT_TMA)) {
-                s_fail = 1;
-                break;
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- producer ----
+            for (int i = 0; i < nk && !s_fail; ++i) {
+                const int st = i % C::NS;
+                const int use = i / C::NS;
+                if (use > 0 && !mbar_wait_bounded(&empty[st], (uint32_t)((use - 1) & 1), p.err, ERR_TIMEOUT_TMA)) {
+                    s_fail = 1;
+                    break;
+                }
+                uint8_t *sb = smem + st * C::STAGE;
+                const int kb = kb0 + i;
+                mbar_arrive_expect_tx(&full[st], (uint32_t)C::STAGE);
+                const int xc = (int)(xcol0 + (long long)kb * K2_KB);
+                tma_load_2d(sb, &mx_hi, xc, c0, &full[st]);
+                if (NPROD == 3)
+                    tma_load_2d(sb + C::XOFF_LO, &mx_lo, xc, c0, &full[st]);
+                tma_load_2d(sb + C::TOFF, &mt_hi, 0, kb * K2_N, &full[st]);
+                if (NPROD == 3)
+                    tma_load_2d(sb + C::TOFF + K2_TBYTES, &mt_lo, 0, kb * K2_N, &full[st]);
             }
-            uint8_t *sb = smem + st * C::STAGE;
-            const int kb = kb0 + i;
-            mbar_arrive_expect_tx(&full[st], (uint32_t)C::STAGE);
-            const int xc = (int)(xcol0 + (long long)kb * K2_KB);
-            tma_load_2d(sb, &mx_hi, xc, c0, &full[st]);
-            if (NPROD == 3)
-                tma_load_2d(sb + C::XOFF_LO, &mx_lo, xc, c0, &full[st]);
-            tma_load_2d(sb + C::TOFF, &mt_hi, 0, kb * K2_N, &full[st]);
-            if (NPROD == 3)
-                tma_load_2d(sb + C::TOFF + K2_TBYTES, &mt_lo, 0, kb * K2_N, &full[st]);
         }
-    } else if (warp == 1 && lane == 0) {
-        // ---- MMA issuer ----
-        const uint32_t idesc = umma_idesc_bf16(K2_M, K2_N);
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---- MMA issuer ----
+            const uint32_t idesc = umma_idesc_bf16(K2_M, K2_N);
+            int i = 0;
+            for (int r = 0; r < nr && !s_fail; ++r) {
+                const int buf = r & 1;
+                const int reuse = r >> 1;  // earlier runs in this buffer
+                if (reuse > 0 &&
+                    !mbar_wait_bounded(&accfree[buf], (uint32_t)((reuse - 1) & 1), p.err, ERR_TIMEOUT_MMA)) {
+                    s_fail = 1;
+                    break;
+                }
+                tc_fence_after_sync();
+                const uint32_t acc = tmem + (uint32_t)(buf * K2_N);
+                const int iend = min(nk, (r + 1) * p.range);
+                for (int first = 1; i < iend; ++i, first = 0) {
+                    const int st = i % C::NS;
+                    if (!mbar_wait_bounded(&full[st], (uint32_t)((i / C::NS) & 1), p.err, ERR_TIMEOUT_MMA)) {
+                        s_fail = 1;
+                        break;
+                    }
+                    tc_fence_after_sync();
+                    const uint32_t sb = smem_u32(smem + st * C::STAGE);
+#pragma unroll
+                    for (int kk = 0; kk < K2_KB / 16; ++kk) {
+                        const uint32_t koff = kk * 32;  // 16 bf16 = 32 bytes along the swizzled row
+                        const uint64_t xh = umma_desc_sw64(sb + koff);
+                        const uint64_t th = umma_desc_sw64(sb + C::TOFF + koff);
+                        umma_bf16(acc, xh, th, idesc, (first && kk == 0) ? 0u : 1u);
+                        if (NPROD == 3) {
+                            const uint64_t xl = umma_desc_sw64(sb + C::XOFF_LO + koff);
+                            const uint64_t tl = umma_desc_sw64(sb + C::TOFF + K2_TBYTES + koff);
+                            umma_bf16(acc, xh, tl, idesc, 1u);
+                            umma_bf16(acc, xl, th, idesc, 1u);
+                        }
+                    }
+                    umma_commit(&empty[st]);  // the stage is free once these MMAs are done
+                }
+                if (s_fail)
+                    break;
+                umma_commit(&accfull[buf]);  // the run is complete in TMEM
+            }
+        }
+    } else if (warp >= K2_ROLE_WARPS) {
+        // ---- epilogue: drain each run into FP32 register sums ----
+        const int ew = warp - K2_ROLE_WARPS;
+        const int q = warp & 3;          // TMEM lane quarter this warp may access
+        const int half = ew >> 2;        // column half: outputs [128 half, 128 half + 128)
+        float sum[128];
+#pragma unroll
+        for (int j = 0; j < 128; ++j)
+            sum[j] = 0.f;
         bool ok = true;
-        for (int i = 0; i < nk; ++i) {
-            const int st = i % C::NS;
-            if (!mbar_wait_bounded(&full[st], (uint32_t)((i / C::NS) & 1), p.err, ERR_TIMEOUT_MMA)) {
+        for (int r = 0; r < nr; ++r) {
+            const int buf = r & 1;
+            const uint32_t par = (uint32_t)((r >> 1) & 1);
+            bool got = true;
+            if (lane == 0) {
+                got = false;
+                // Bounded, and abandoned early if another role has failed.
+                const unsigned long long t0 = globaltimer_ns();
+                for (uint32_t it = 0;; ++it) {
+                    if (mbar_try_wait(&accfull[buf], par)) {
+                        got = true;
+                        break;
+                    }
+                    if ((it & 255u) == 255u) {
+                        if (s_fail)
+                            break;
+                        if (globaltimer_ns() - t0 > kWaitLimitNs) {
+                            atomicOr(p.err, ERR_TIMEOUT_MMA);
+                            break;
+                        }
+                    }
+                }
+            }
+            got = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
+            if (!got) {
                 ok = false;
-                s_fail = 1;
                 break;
             }
+            mbar_try_wait(&accfull[buf], par);
             tc_fence_after_sync();
-            const uint32_t sb = smem_u32(smem + st * C::STAGE);
+            const uint32_t src = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * K2_N + half * 128);
 #pragma unroll
-            for (int kk = 0; kk < K2_KB / 16; ++kk) {
-                const uint32_t koff = kk * 32;  // 16 bf16 = 32 bytes along the swizzled row
-                const uint64_t xh = umma_desc_sw64(sb + koff);
-                const uint64_t th = umma_desc_sw64(sb + C::TOFF + koff);
-                umma_bf16(tmem, xh, th, idesc, (i > 0 || kk > 0) ? 1u : 0u);
-                if (NPROD == 3) {
-                    const uint64_t xl = umma_desc_sw64(sb + C::XOFF_LO + koff);
-                    const uint64_t tl = umma_desc_sw64(sb + C::TOFF + K2_TBYTES + koff);
-                    umma_bf16(tmem, xh, tl, idesc, 1u);
-                    umma_bf16(tmem, xl, th, idesc, 1u);
-                }
+            for (int cc = 0; cc < 8; ++cc) {
+                float v[16];
+                tmem_ld_32x16(src + cc * 16, v);
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    sum[cc * 16 + j] += v[j];
             }
-            umma_commit(&empty[st]);  // the stage is free once these MMAs are done
+            tc_fence_before_sync();
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(&accfree[buf]);
         }
-        if (ok)
-            umma_commit(&accbar);
-        else
-            mbar_arrive(&accbar);  // release the epilogue; s_fail marks the result invalid
-    }
-
-    // ---- epilogue: all four warps ----
-    bool ok = true;
-    if (lane == 0)
-        ok = mbar_wait_bounded(&accbar, 0, p.err, ERR_TIMEOUT_MMA);
-    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-    if (ok)
-        mbar_try_wait(&accbar, 0);
-    tc_fence_after_sync();
-    __syncwarp();
-    const int ch = warp * 32 + lane;  // TMEM lane = channel within the tile
-    const int c = c0 + ch;
-    const bool fail = !ok || s_fail;
-    if (!fail) {
-        const uint32_t row = tmem + ((uint32_t)(warp * 32) << 16);
-        float *dst;
-        long long lim;
-        if (p.nsplit == 1) {
-            dst = p.y + (long long)c * p.y_pitch + (long long)tile_o * K2_N;
-            lim = p.nout - (long long)tile_o * K2_N;
-        } else {
-            dst = p.partial + ((((long long)tile_c * p.ntile_o + tile_o) * p.nsplit + split) * K2_M + ch) * K2_N;
-            lim = K2_N;
-        }
-#pragma unroll 1
-        for (int cc = 0; cc < K2_N / 32; ++cc) {
-            float v[32];
-            tmem_ld_32x32(row + cc * 32, v);
-            if (c < p.C) {
-                if (lim >= (cc + 1) * 32) {
+        const int ch = q * 32 + lane;  // channel within the tile
+        const int c = c0 + ch;
+        if (ok && !s_fail && c < p.C) {
+            float *dst;
+            long long lim;
+            if (p.nsplit == 1) {
+                dst = p.y + (long long)c * p.y_pitch + (long long)tile_o * K2_N + half * 128;
+                lim = p.nout - (long long)tile_o * K2_N - half * 128;
+            } else {
+                dst = p.partial + ((((long long)tile_c * p.ntile_o + tile_o) * p.nsplit + part) * K2_M + ch) * K2_N +
+                      half * 128;
+                lim = 128;
+            }
+            if (lim >= 128) {
 #pragma unroll
-                    for (int j = 0; j < 32; j += 4)
-                        *reinterpret_cast<float4 *>(dst + cc * 32 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-                } else {
+                for (int j = 0; j < 128; j += 4)
+                    *reinterpret_cast<float4 *>(dst + j) = make_float4(sum[j], sum[j + 1], sum[j + 2], sum[j + 3]);
+            } else {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        if (cc * 32 + j < lim)
-                            dst[cc * 32 + j] = v[j];
-                }
+                for (int j = 0; j < 128; ++j)
+                    if (j < lim)
+                        dst[j] = sum[j];
             }
         }
     }
@@ -193,7 +258,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
     __syncthreads();
     if (warp == 2) {
         tc_fence_after_sync();
-        tmem_dealloc(tmem, K2_N);
+        tmem_dealloc(tmem, 2 * K2_N);
     }
 }
 
@@ -304,7 +369,7 @@ cudaError_t k2_launch(const CUtensorMap &mx_hi, const CUtensorMap &mx_lo, const 
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess)
         return e;
-    if (dev < 0 || dev >= 64 || (nprod != 1 && nprod != 3) || p.nsplit < 1 || p.nsplit > 64)
+    if (dev < 0 || dev >= 64 || (nprod != 1 && nprod != 3) || p.nsplit < 1 || p.nsplit > 64 || p.range < 1)
         return cudaErrorInvalidValue;
     const int vi = nprod == 1 ? 0 : 1;
     const size_t smem = k2_smem_bytes(nprod);

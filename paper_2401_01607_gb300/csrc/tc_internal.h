@@ -115,7 +115,8 @@ struct K2Params {
     int ntile_c, ntile_o;    // ceil(C / 128), ceil(nout / 256)
     long long x_col0;        // history column of w0 for output tile 0 (multiple of 8)
     int nkb;                 // K blocks per output tile
-    int nsplit, kb_per;      // K ranges per tile and blocks per range
+    int nsplit, kb_per;      // K parts per tile (one CTA each) and blocks per part
+    int range;               // K blocks per serial TMEM run before the drain to FP32 registers
     float *y;                // y[c * y_pitch + j], j < nout
     long long y_pitch;
     float *partial;          // [ntile_c][ntile_o][nsplit][128][256] (nsplit > 1)

@@ -231,6 +231,105 @@ tc_status tc_convolve(const float *x, size_t N, const float *h, size_t L, float 
 tc_status tc_convolve_noalloc(const float *x, size_t N, const float *h, size_t L, float *y, void *cuda_stream);
 
 /* ---------------------------------------------------------------------- */
+/* Serving: continuous batching of many independent streams               */
+/* ---------------------------------------------------------------------- */
+/*
+ * A tc_server holds many mono FP32 streams on one device. Each has its own IR
+ * length L, block size Nb and IR versions (the real-time, multichannel use of
+ * Sec. 5.1 and Sec. 6). The streams' blocks run in batches:
+ *   - tc_server_submit queues one input block and returns at once. It never
+ *     waits for the GPU.
+ *   - A step takes the oldest pending block of every stream that has one. It
+ *     runs all of them as ONE batch: one host-to-device copy, one scatter
+ *     kernel into the streams' histories, one FP32 gather launch over a work
+ *     list with one item per stream, and one device-to-host copy.
+ *   - Blocks submitted while a step runs join the next step. The worker
+ *     thread started by tc_server_start runs steps back to back while blocks
+ *     are pending. tc_server_step runs one step on the calling thread
+ *     instead.
+ *   - A stream is admitted only while its device state (input history, IR
+ *     slots, version table) fits the memory budget. Otherwise tc_server_add
+ *     returns TC_ENOMEM and the caller retries once streams have left.
+ *     tc_server_remove releases the state.
+ * Each stream gives the same output as a tc_stream opened with the same L and
+ * block and fed the same calls. The output does not depend on which blocks of
+ * other streams share its steps, up to FP32 rounding.
+ * Thread safety: submit, poll and get_stats may be called from any thread at
+ * any time. The other calls serialise on the server.
+ */
+typedef struct tc_server tc_server;
+
+typedef struct tc_server_stats {
+    size_t streams;      /* streams admitted and not removed */
+    size_t mem_used;     /* device bytes held by those streams */
+    size_t mem_budget;   /* budget given to tc_server_open */
+    uint64_t steps;      /* batched steps run */
+    uint64_t blocks;     /* blocks completed (flush tails included) */
+    uint64_t rejected;   /* tc_server_add calls refused for memory */
+    double busy_s;       /* wall time spent inside steps (seconds) */
+} tc_server_stats;
+
+/* Opens a server on the current CUDA device. mem_budget_bytes bounds the
+ * device memory of admitted streams. max_step_samples bounds the input
+ * samples of one step (0: 4M). It sizes the pinned staging buffers; a block
+ * that would overflow a step waits for the next one. */
+tc_status tc_server_open(size_t mem_budget_bytes, size_t max_step_samples, tc_server **out);
+/* Stops the worker, waits for the GPU and frees everything. NULL is a no-op. */
+tc_status tc_server_close(tc_server *srv);
+
+/* Admits a stream with IR length L (1 <= L <= 2620792) and block size block,
+ * with initial IR h[0..n) (n <= L; shorter IRs are zero-padded). *id names
+ * the stream in later calls. flags: 0, or TC_SERVER_DISCARD_OUTPUT to keep no
+ * output blocks (load generation: only the latency is recorded). TC_ENOMEM:
+ * the budget (or the device) has no room now. */
+enum { TC_SERVER_DISCARD_OUTPUT = 1 };
+tc_status tc_server_add(tc_server *srv, size_t L, size_t block, const float *h, size_t n, int flags,
+                        uint64_t *id);
+/* New IR version from input sample `sample` on (Eq. 4 with per-sample
+ * versions, Sec. 6). sample must not be below the samples already submitted.
+ * Up to three versions are live per stream; TC_ENOMEM when all three are
+ * still needed by the input history. */
+tc_status tc_server_set_ir_at(tc_server *srv, uint64_t id, const float *h, size_t n, uint64_t sample);
+/* Queues input block x[0..n) (n <= block; a shorter block is the stream's
+ * last). The library copies x before returning. The block's latency is
+ * counted from the call. */
+tc_status tc_server_submit(tc_server *srv, uint64_t id, const float *x, size_t n);
+/* Queues count blocks at once (block i: stream ids[i], xs[i][0..ns[i])), in
+ * order. t_ready[i] (t_ready may be NULL: now) is the time on
+ * tc_server_clock() at which block i was complete; its latency is counted
+ * from there. Checks every block first and queues none on an error. */
+tc_status tc_server_submit_many(tc_server *srv, size_t count, const uint64_t *ids, const float *const *xs,
+                                const size_t *ns, const double *t_ready);
+/* Runs one batched step on the calling thread (TC_ESTATE while the worker
+ * runs). *blocks_done (may be NULL) is the number of blocks it completed. */
+tc_status tc_server_step(tc_server *srv, size_t *blocks_done);
+/* Starts / stops the worker thread. tc_server_stop returns TC_ECUDA if the
+ * worker stopped on an error; tc_last_error() then has its message. */
+tc_status tc_server_start(tc_server *srv);
+tc_status tc_server_stop(tc_server *srv);
+/* Takes the stream's oldest finished output block, if any. *n_out = 0 if
+ * none is ready yet. The block has as many samples as its input block and
+ * goes to y[0..n) (cap >= n, else TC_EINVAL). t_submit and t_done (may be
+ * NULL) get the submit and completion times on tc_server_clock(). */
+tc_status tc_server_poll(tc_server *srv, uint64_t id, float *y, size_t cap, size_t *n_out, double *t_submit,
+                         double *t_done);
+/* Ends the stream's input and returns the last L - 1 output samples (the
+ * temporal overflow of Sec. 4.1) in y[0..L-1) (cap >= L - 1). Runs steps on
+ * the calling thread until they are done; stop the worker first
+ * (TC_ESTATE otherwise). Poll the stream's finished blocks before or after. */
+tc_status tc_server_flush(tc_server *srv, uint64_t id, float *y, size_t cap, size_t *n_out);
+/* Removes the stream and frees its device state. TC_ESTATE while blocks of
+ * the stream are still queued (its finished, unpolled outputs are dropped). */
+tc_status tc_server_remove(tc_server *srv, uint64_t id);
+tc_status tc_server_get_stats(tc_server *srv, tc_server_stats *st);
+/* Moves up to cap recorded block latencies (seconds from ready to result on
+ * the host, in completion order) into out and forgets them. Flush tails are
+ * not recorded. */
+tc_status tc_server_latencies(tc_server *srv, double *out, size_t cap, size_t *n_out);
+/* Monotonic clock of the poll timestamps (seconds). */
+double tc_server_clock(void);
+
+/* ---------------------------------------------------------------------- */
 /* Diagnostics                                                             */
 /* ---------------------------------------------------------------------- */
 
@@ -250,8 +349,8 @@ uint64_t tc_kernel_launches(void);
  *                        2 = 8320 taps per CTA (default: picked per launch)
  *   TC_TUNE_K2_RANGE     K blocks (of 32 samples) accumulated serially on the
  *                        tensor cores before the pairwise reduction of
- *                        ranges (default 48 for the BF16 split, 256 for BF16;
- *                        1..4096)
+ *                        ranges (default 48 for the BF16 split, 4096 for
+ *                        BF16; 1..4096)
  * Errors: TC_EINVAL for an unknown knob or value out of range. */
 typedef enum tc_tune_knob { TC_TUNE_K1_CHUNK = 0, TC_TUNE_K2_RANGE = 1 } tc_tune_knob;
 tc_status tc_set_tuning(tc_stream *s, int knob, long long value);

@@ -39,6 +39,12 @@ class TcInfo(ctypes.Structure):
                 ("fp32_fallbacks", ctypes.c_uint64)]
 
 
+class TcServerStats(ctypes.Structure):
+    _fields_ = [("streams", ctypes.c_size_t), ("mem_used", ctypes.c_size_t), ("mem_budget", ctypes.c_size_t),
+                ("steps", ctypes.c_uint64), ("blocks", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
+                ("busy_s", ctypes.c_double)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -68,6 +74,21 @@ _SIGS = {
     "tc_set_tuning": [_vp, _int, ctypes.c_longlong],
     "tc_profile": [_vp, _int],
     "tc_profile_read": [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_u64), ctypes.POINTER(ctypes.c_double)],
+    "tc_server_open": [_sz, _sz, ctypes.POINTER(_vp)],
+    "tc_server_close": [_vp],
+    "tc_server_add": [_vp, _sz, _sz, _vp, _sz, _int, ctypes.POINTER(_u64)],
+    "tc_server_set_ir_at": [_vp, _u64, _vp, _sz, _u64],
+    "tc_server_submit": [_vp, _u64, _vp, _sz],
+    "tc_server_submit_many": [_vp, _sz, _vp, _vp, _vp, _vp],
+    "tc_server_step": [_vp, ctypes.POINTER(_sz)],
+    "tc_server_start": [_vp],
+    "tc_server_stop": [_vp],
+    "tc_server_poll": [_vp, _u64, _vp, _sz, ctypes.POINTER(_sz), ctypes.POINTER(ctypes.c_double),
+                       ctypes.POINTER(ctypes.c_double)],
+    "tc_server_flush": [_vp, _u64, _vp, _sz, ctypes.POINTER(_sz)],
+    "tc_server_remove": [_vp, _u64],
+    "tc_server_get_stats": [_vp, ctypes.POINTER(TcServerStats)],
+    "tc_server_latencies": [_vp, _vp, _sz, ctypes.POINTER(_sz)],
 }
 
 
@@ -95,6 +116,8 @@ def load() -> ctypes.CDLL:
         lib.tc_status_str.restype = ctypes.c_char_p
         lib.tc_kernel_launches.argtypes = []
         lib.tc_kernel_launches.restype = ctypes.c_uint64
+        lib.tc_server_clock.argtypes = []
+        lib.tc_server_clock.restype = ctypes.c_double
         _lib = lib
         return lib
 
@@ -274,3 +297,104 @@ def tc_status_str(st: int) -> str:
 
 def tc_kernel_launches() -> int:
     return int(load().tc_kernel_launches())
+
+
+# ---------------------------------------------------------------------------
+# Serving (tc_server_*): continuous batching of many independent streams
+# ---------------------------------------------------------------------------
+
+TC_SERVER_DISCARD_OUTPUT = 1
+
+
+def tc_server_open(mem_budget_bytes: int, max_step_samples: int = 0) -> int:
+    h = _vp()
+    _call("tc_server_open", int(mem_budget_bytes), int(max_step_samples), ctypes.byref(h))
+    return h.value
+
+
+def tc_server_close(srv: int) -> None:
+    _call("tc_server_close", srv)
+
+
+def tc_server_add(srv: int, L: int, block: int, h, flags: int = 0) -> int:
+    h, hp = _host_f32(h)
+    sid = _u64()
+    _call("tc_server_add", srv, int(L), int(block), hp, h.size, int(flags), ctypes.byref(sid))
+    return int(sid.value)
+
+
+def tc_server_set_ir_at(srv: int, sid: int, h, sample: int) -> None:
+    h, hp = _host_f32(h)
+    _call("tc_server_set_ir_at", srv, int(sid), hp, h.size, int(sample))
+
+
+def tc_server_submit(srv: int, sid: int, x) -> None:
+    x, xp = _host_f32(x)
+    _call("tc_server_submit", srv, int(sid), xp, x.size)
+
+
+def tc_server_submit_many(srv: int, ids, x_addrs, ns, t_ready=None) -> None:
+    """ids: uint64 array; x_addrs: int64 array of host float32 addresses (the
+    caller keeps those buffers alive for the call); ns: sample counts;
+    t_ready: ready times on tc_server_clock() or None."""
+    ids = np.ascontiguousarray(ids, dtype=np.uint64)
+    xa = np.ascontiguousarray(x_addrs, dtype=np.uint64)
+    ns = np.ascontiguousarray(ns, dtype=np.uint64)
+    if not (ids.size == xa.size == ns.size):
+        raise ValueError("ids, x_addrs and ns must have the same length")
+    tr = None if t_ready is None else np.ascontiguousarray(t_ready, dtype=np.float64)
+    if tr is not None and tr.size != ids.size:
+        raise ValueError("t_ready must have one entry per block")
+    _call("tc_server_submit_many", srv, ids.size, ids.ctypes.data_as(_vp), xa.ctypes.data_as(_vp),
+          ns.ctypes.data_as(_vp), None if tr is None else tr.ctypes.data_as(_vp))
+
+
+def tc_server_step(srv: int) -> int:
+    n = _sz()
+    _call("tc_server_step", srv, ctypes.byref(n))
+    return int(n.value)
+
+
+def tc_server_start(srv: int) -> None:
+    _call("tc_server_start", srv)
+
+
+def tc_server_stop(srv: int) -> None:
+    _call("tc_server_stop", srv)
+
+
+def tc_server_poll(srv: int, sid: int, y):
+    """Fills y with the stream's oldest finished block; returns (n, t_submit,
+    t_done), n = 0 if none is ready."""
+    y, yp = _host_f32(y, writable=True)
+    n, ts, td = _sz(), ctypes.c_double(), ctypes.c_double()
+    _call("tc_server_poll", srv, int(sid), yp, y.size, ctypes.byref(n), ctypes.byref(ts), ctypes.byref(td))
+    return int(n.value), ts.value, td.value
+
+
+def tc_server_flush(srv: int, sid: int, y) -> int:
+    y, yp = _host_f32(y, writable=True)
+    n = _sz()
+    _call("tc_server_flush", srv, int(sid), yp, y.size, ctypes.byref(n))
+    return int(n.value)
+
+
+def tc_server_remove(srv: int, sid: int) -> None:
+    _call("tc_server_remove", srv, int(sid))
+
+
+def tc_server_get_stats(srv: int) -> TcServerStats:
+    st = TcServerStats()
+    _call("tc_server_get_stats", srv, ctypes.byref(st))
+    return st
+
+
+def tc_server_latencies(srv: int, cap: int = 1 << 20) -> np.ndarray:
+    out = np.empty(int(cap), dtype=np.float64)
+    n = _sz()
+    _call("tc_server_latencies", srv, out.ctypes.data_as(_vp), out.size, ctypes.byref(n))
+    return out[: int(n.value)].copy()
+
+
+def tc_server_clock() -> float:
+    return float(load().tc_server_clock())

@@ -92,13 +92,45 @@ __device__ __forceinline__ void k1_pass(const float *__restrict__ xp, const floa
     }
 }
 
-template <int P>
-__global__ void __launch_bounds__(K1_THREADS, 3) k1_gather(const K1Params p)
+// LIST = false: one uniform launch described by p0.
+// LIST = true: a work list (continuous batching of independent streams).
+// CTA b belongs to item i with cta_begin[i] <= b < cta_begin[i+1]; the item's
+// parameters are copied to shared memory, then the CTA runs as in a uniform
+// launch over that item alone.
+template <int P, bool LIST>
+__global__ void __launch_bounds__(K1_THREADS, 3)
+    k1_gather(const K1Params p0, const K1Params *__restrict__ items, const long long *__restrict__ cta_begin,
+              int nlist)
 {
     using C = K1Cfg<P>;
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ int s_last;
+    __shared__ __align__(16) K1Params s_item;
+    __shared__ long long s_first;
+    if (LIST) {
+        if (threadIdx.x == 0) {
+            int lo = 0, hi = nlist - 1;  // last item whose first CTA is <= blockIdx.x
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (cta_begin[mid] <= (long long)blockIdx.x)
+                    lo = mid;
+                else
+                    hi = mid - 1;
+            }
+            s_first = cta_begin[lo];
+            s_last = lo;
+        }
+        __syncthreads();
+        constexpr int W = (int)(sizeof(K1Params) / sizeof(int));
+        static_assert(sizeof(K1Params) % sizeof(int) == 0, "K1Params copies as ints");
+        const int *src = reinterpret_cast<const int *>(items + s_last);
+        int *dst = reinterpret_cast<int *>(&s_item);
+        for (int i = threadIdx.x; i < W; i += K1_THREADS)
+            dst[i] = src[i];
+        __syncthreads();
+    }
+    const K1Params &p = LIST ? s_item : p0;
     float *const xs = smem;
     float *const hs = smem + C::XS;
     float *const red = smem;                  // [8 warps][16 r][8 g], after the last pass
@@ -110,7 +142,7 @@ __global__ void __launch_bounds__(K1_THREADS, 3) k1_gather(const K1Params p)
 
     // Block -> (item, tile, input, chunk); chunks fastest.
     const int ctot = p.nin * p.nchunk;
-    long long bid = blockIdx.x;
+    long long bid = LIST ? (long long)blockIdx.x - s_first : (long long)blockIdx.x;
     const int cidx = (int)(bid % ctot);
     bid /= ctot;
     const int tile = (int)(bid % p.ntile);
@@ -294,11 +326,13 @@ template <int P>
 cudaError_t prepare_variant(int dev, int variant)
 {
     const size_t smem = smem_bytes<P>();
-    cudaError_t e = cudaFuncSetAttribute(k1_gather<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k1_gather<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k1_gather<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
     int n = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k1_gather<P>, K1_THREADS, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k1_gather<P, false>, K1_THREADS, smem);
     if (e != cudaSuccess)
         return e;
     g_dev[dev].blocks_per_sm[variant] = n > 0 ? n : 1;
@@ -415,9 +449,34 @@ cudaError_t k1_launch(K1Params &p, const K1Plan &plan, cudaStream_t st)
         return cudaErrorInvalidConfiguration;
     const unsigned grid = (unsigned)plan.ctas;
     switch (plan.variant) {
-    case K1_P1: k1_gather<1><<<grid, K1_THREADS, smem_bytes<1>(), st>>>(p); break;
-    case K1_P4: k1_gather<4><<<grid, K1_THREADS, smem_bytes<4>(), st>>>(p); break;
-    case K1_P13: k1_gather<13><<<grid, K1_THREADS, smem_bytes<13>(), st>>>(p); break;
+    case K1_P1: k1_gather<1, false><<<grid, K1_THREADS, smem_bytes<1>(), st>>>(p, nullptr, nullptr, 0); break;
+    case K1_P4: k1_gather<4, false><<<grid, K1_THREADS, smem_bytes<4>(), st>>>(p, nullptr, nullptr, 0); break;
+    case K1_P13: k1_gather<13, false><<<grid, K1_THREADS, smem_bytes<13>(), st>>>(p, nullptr, nullptr, 0); break;
+    default: return cudaErrorInvalidValue;
+    }
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t k1_launch_list(const K1Params *d_items, const long long *d_cta_begin, int nitems, long long total_ctas,
+                           int variant, cudaStream_t st)
+{
+    DevInfo *d = nullptr;
+    cudaError_t e = device_info(&d);
+    if (e != cudaSuccess)
+        return e;
+    if (nitems < 1 || total_ctas <= 0)
+        return cudaSuccess;
+    if (total_ctas > 0x7fffffffLL)
+        return cudaErrorInvalidConfiguration;
+    const unsigned grid = (unsigned)total_ctas;
+    const K1Params none{};
+    switch (variant) {
+    case K1_P1: k1_gather<1, true><<<grid, K1_THREADS, smem_bytes<1>(), st>>>(none, d_items, d_cta_begin, nitems); break;
+    case K1_P4: k1_gather<4, true><<<grid, K1_THREADS, smem_bytes<4>(), st>>>(none, d_items, d_cta_begin, nitems); break;
+    case K1_P13:
+        k1_gather<13, true><<<grid, K1_THREADS, smem_bytes<13>(), st>>>(none, d_items, d_cta_begin, nitems);
+        break;
     default: return cudaErrorInvalidValue;
     }
     count_launch();

@@ -91,6 +91,12 @@ cudaError_t k1_plan(long long L, int e, int nin, int nitems, int ntile, int forc
 // Chunk-sum scratch (floats) a launch over `tiles` tiles may need with any variant.
 long long k1_partial_floats_max(long long L, int nin, long long tiles);
 
+// Work-list launch (continuous batching): item i (fully filled K1Params,
+// nchunk included, its own partial/counter scratch) owns CTAs
+// [cta_begin[i], cta_begin[i+1]); all items use one chunk variant.
+cudaError_t k1_launch_list(const K1Params *d_items, const long long *d_cta_begin, int nitems, long long total_ctas,
+                           int variant, cudaStream_t st);
+
 // Launches K1 for plan on st (fills p.nchunk).
 cudaError_t k1_launch(K1Params &p, const K1Plan &plan, cudaStream_t st);
 

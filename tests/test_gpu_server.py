@@ -1,0 +1,256 @@
+"""Continuous batching (tc_server_*) through the C ABI.
+
+Each stream of a mixed batch must give the same output as when it runs alone,
+and both must match the FP64 oracle's buffer algorithm (Sec. 4.2, per-sample
+IR versions) within the FP32 tolerance (relative L2 <= 1e-6).
+"""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_helpers import TOL, rel_l2
+from paper_2401_01607_gb300 import capi, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import paper_2401_01607_gb300 as pkg
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    pkg.build()
+    capi.load()
+
+
+def _small_trace(k=7, seed=5):
+    """Serving-trace recipe shrunk so the oracle finishes in seconds: short
+    streams, IRs up to 20000 taps, half of them with a mid-stream IR swap."""
+    tr = synth.serving_trace(duration_s=10.0, rate_hz=50.0, dur_range=(0.01, 0.12), L_range=(1, 20_000),
+                             swap_frac=0.5, seed=seed, max_streams=k)
+    out = []
+    for t in tr:
+        x = synth.audio(t.n, t.x_seed)
+        H = np.stack([synth.decayed_ir(t.L, max(1.0, t.tau), s) for s in t.ir_seeds])
+        vstart = [0] if t.swap_at < 0 else [0, t.swap_at]
+        out.append((t, x, H, vstart))
+    return out
+
+
+def _oracle(t, x, H, vstart):
+    return oracle.buffer(x, H, np.asarray(vstart, np.int64), t.block)
+
+
+def _run(streams, order_seed=None):
+    """Runs the streams through one server with manual steps. order_seed None:
+    one stream at a time (alone); else interleaved at random (mix).
+    Returns {index: y[N + L - 1]}."""
+    srv = capi.tc_server_open(8 << 30, 1 << 20)
+    try:
+        ids = [capi.tc_server_add(srv, t.L, t.block, H[0]) for (t, x, H, vs) in streams]
+        nblk = [-(-t.n // t.block) for (t, x, H, vs) in streams]
+        sent = [0] * len(streams)
+        outs = [[] for _ in streams]
+
+        def submit(i):
+            t, x, H, vs = streams[i]
+            b = sent[i]
+            lo, hi = b * t.block, min(t.n, (b + 1) * t.block)
+            if len(vs) > 1 and lo <= vs[1] < hi:
+                capi.tc_server_set_ir_at(srv, ids[i], H[1], vs[1])
+            capi.tc_server_submit(srv, ids[i], x[lo:hi])
+            sent[i] += 1
+
+        def drain(i):
+            t = streams[i][0]
+            y = np.empty(t.block, np.float32)
+            while True:
+                n, _, _ = capi.tc_server_poll(srv, ids[i], y)
+                if n == 0:
+                    break
+                outs[i].append(y[:n].copy())
+
+        if order_seed is None:
+            for i in range(len(streams)):
+                while sent[i] < nblk[i]:
+                    submit(i)
+                    capi.tc_server_step(srv)
+                drain(i)
+        else:
+            rng = np.random.default_rng(order_seed)
+            while any(sent[i] < nblk[i] for i in range(len(streams))):
+                for i in range(len(streams)):
+                    # 0, 1 or 2 blocks queued per stream per round: steps mix
+                    # streams in changing combinations and queues build up.
+                    for _ in range(int(rng.integers(0, 3))):
+                        if sent[i] < nblk[i]:
+                            submit(i)
+                if rng.uniform() < 0.7:
+                    capi.tc_server_step(srv)
+                for i in range(len(streams)):
+                    drain(i)
+            while capi.tc_server_step(srv):
+                pass
+            for i in range(len(streams)):
+                drain(i)
+        res = {}
+        for i, (t, x, H, vs) in enumerate(streams):
+            tail = np.empty(max(t.L - 1, 1), np.float32)
+            n = capi.tc_server_flush(srv, ids[i], tail)
+            assert n == t.L - 1
+            res[i] = np.concatenate(outs[i] + [tail[:n]])
+            assert res[i].size == t.n + t.L - 1
+            capi.tc_server_remove(srv, ids[i])
+        st = capi.tc_server_get_stats(srv)
+        assert st.streams == 0 and st.mem_used == 0
+    finally:
+        capi.tc_server_close(srv)
+    return res
+
+
+def test_alone_equals_mix_equals_oracle():
+    streams = _small_trace()
+    alone = _run(streams)
+    mix = _run(streams, order_seed=1)
+    for i, s in enumerate(streams):
+        t = s[0]
+        ref = _oracle(*s)
+        e_alone, e_mix, e_am = rel_l2(alone[i], ref), rel_l2(mix[i], ref), rel_l2(mix[i], alone[i])
+        print(f"stream {i}: L={t.L} block={t.block} n={t.n} swap={t.swap_at} "
+              f"alone={e_alone:.2e} mix={e_mix:.2e} mix-vs-alone={e_am:.2e}")
+        assert e_alone <= TOL["fp32"], (i, e_alone)
+        assert e_mix <= TOL["fp32"], (i, e_mix)
+        assert e_am <= TOL["fp32"], (i, e_am)
+
+
+def test_worker_thread_continuous_batching():
+    """Blocks submitted while the worker runs steps join later steps; every
+    result still matches the oracle and every block's latency is recorded."""
+    streams = _small_trace(k=5, seed=9)
+    srv = capi.tc_server_open(4 << 30, 1 << 20)
+    try:
+        ids = [capi.tc_server_add(srv, t.L, t.block, H[0]) for (t, x, H, vs) in streams]
+        capi.tc_server_start(srv)
+        with pytest.raises(capi.TcError) as ei:
+            capi.tc_server_step(srv)
+        assert ei.value.code == "TC_ESTATE"
+        outs = [[] for _ in streams]
+        sent = [0] * len(streams)
+        total = 0
+        nblk = [-(-t.n // t.block) for (t, x, H, vs) in streams]
+        rng = np.random.default_rng(3)
+        while any(sent[i] < nblk[i] for i in range(len(streams))):
+            for i, (t, x, H, vs) in enumerate(streams):
+                if sent[i] >= nblk[i] or rng.uniform() < 0.3:
+                    continue
+                lo, hi = sent[i] * t.block, min(t.n, (sent[i] + 1) * t.block)
+                if len(vs) > 1 and lo <= vs[1] < hi:
+                    capi.tc_server_set_ir_at(srv, ids[i], H[1], vs[1])
+                capi.tc_server_submit(srv, ids[i], x[lo:hi])
+                sent[i] += 1
+                total += 1
+            time.sleep(0.0005)
+            for i, (t, x, H, vs) in enumerate(streams):
+                y = np.empty(t.block, np.float32)
+                n, ts, td = capi.tc_server_poll(srv, ids[i], y)
+                if n:
+                    assert td >= ts
+                    outs[i].append(y[:n].copy())
+        deadline = time.monotonic() + 30
+        while sum(map(len, outs)) < total and time.monotonic() < deadline:
+            for i, (t, x, H, vs) in enumerate(streams):
+                y = np.empty(t.block, np.float32)
+                n, _, _ = capi.tc_server_poll(srv, ids[i], y)
+                if n:
+                    outs[i].append(y[:n].copy())
+        capi.tc_server_stop(srv)
+        assert sum(map(len, outs)) == total
+        lat = capi.tc_server_latencies(srv)
+        assert lat.size == total and np.all(lat >= 0)
+        st = capi.tc_server_get_stats(srv)
+        assert st.blocks == total and st.steps <= total
+        for i, s in enumerate(streams):
+            t = s[0]
+            tail = np.empty(max(t.L - 1, 1), np.float32)
+            n = capi.tc_server_flush(srv, ids[i], tail)
+            y = np.concatenate(outs[i] + [tail[:n]])
+            assert rel_l2(y, _oracle(*s)) <= TOL["fp32"]
+    finally:
+        capi.tc_server_close(srv)
+
+
+def test_admission_by_memory_budget():
+    h = synth.decayed_ir(10_000, 2000.0, 1)
+    srv = capi.tc_server_open(1 << 40, 1 << 16)
+    try:
+        a = capi.tc_server_add(srv, 10_000, 128, h)
+        per = capi.tc_server_get_stats(srv).mem_used
+        capi.tc_server_remove(srv, a)
+    finally:
+        capi.tc_server_close(srv)
+    srv = capi.tc_server_open(2 * per + per // 2, 1 << 16)
+    try:
+        a = capi.tc_server_add(srv, 10_000, 128, h)
+        capi.tc_server_add(srv, 10_000, 128, h)
+        with pytest.raises(capi.TcError) as ei:
+            capi.tc_server_add(srv, 10_000, 128, h)
+        assert ei.value.code == "TC_ENOMEM"
+        st = capi.tc_server_get_stats(srv)
+        assert st.rejected == 1 and st.streams == 2 and st.mem_used == 2 * per
+        capi.tc_server_remove(srv, a)
+        capi.tc_server_add(srv, 10_000, 128, h)
+        assert capi.tc_server_get_stats(srv).streams == 2
+    finally:
+        capi.tc_server_close(srv)
+
+
+def test_one_batched_launch_per_step():
+    """A step over many streams is one scatter kernel plus one K1 work-list launch."""
+    srv = capi.tc_server_open(8 << 30, 1 << 20)
+    try:
+        ids = [capi.tc_server_add(srv, 300 + 977 * i, 64 + 32 * (i % 3), synth.decayed_ir(300 + 977 * i, 200.0, i))
+               for i in range(40)]
+        x = synth.audio(128, 1)
+        capi.tc_server_submit_many(srv, ids, [x.ctypes.data] * len(ids), [64] * len(ids))
+        before = capi.tc_kernel_launches()
+        assert capi.tc_server_step(srv) == len(ids)
+        assert capi.tc_kernel_launches() - before == 2
+    finally:
+        capi.tc_server_close(srv)
+
+
+def test_server_errors():
+    h = synth.decayed_ir(500, 100.0, 2)
+    srv = capi.tc_server_open(1 << 30, 1 << 16)
+    try:
+        sid = capi.tc_server_add(srv, 500, 64, h)
+        for bad in [lambda: capi.tc_server_add(srv, 500, 64, np.zeros(501, np.float32)),
+                    lambda: capi.tc_server_add(srv, 500, 1 << 17, h),
+                    lambda: capi.tc_server_submit(srv, sid + 99, np.zeros(8, np.float32)),
+                    lambda: capi.tc_server_submit(srv, sid, np.zeros(65, np.float32))]:
+            with pytest.raises(capi.TcError) as ei:
+                bad()
+            assert ei.value.code == "TC_EINVAL"
+        capi.tc_server_submit(srv, sid, np.ones(64, np.float32))
+        with pytest.raises(capi.TcError) as ei:
+            capi.tc_server_set_ir_at(srv, sid, h, 10)  # sample already submitted
+        assert ei.value.code == "TC_EINVAL"
+        capi.tc_server_submit(srv, sid, np.ones(10, np.float32))  # short: the last block
+        with pytest.raises(capi.TcError) as ei:
+            capi.tc_server_submit(srv, sid, np.ones(10, np.float32))
+        assert ei.value.code == "TC_ESTATE"
+        tail = np.empty(499, np.float32)
+        assert capi.tc_server_flush(srv, sid, tail) == 499
+        y = np.empty(64, np.float32)
+        n1, _, _ = capi.tc_server_poll(srv, sid, y)
+        first = y[:n1].copy()
+        n2, _, _ = capi.tc_server_poll(srv, sid, y)
+        assert (n1, n2) == (64, 10)
+        ref = oracle.buffer(np.ones(74, np.float32), h[None], np.zeros(1, np.int64), 64)
+        got = np.concatenate([first, y[:10], tail])
+        assert rel_l2(got, ref) <= TOL["fp32"]
+    finally:
+        capi.tc_server_close(srv)

@@ -370,6 +370,265 @@ def bench_shared(torch, steps: int, warmup: int, P: int = 8192) -> dict:
     return out
 
 
+# ---------------------------------------------------------------------------
+# Serving: continuous batching (tc_server_*) under real-time pacing
+# ---------------------------------------------------------------------------
+
+def _ir_maker(seed: int = 123, nmax: int = 480_000):
+    """IRs of the serving recipe (exp-decayed Gaussian, sum |h| = 1) cut from one
+    seeded Gaussian pool: stream seed s starts at offset s mod 4096."""
+    g = np.random.default_rng(seed).standard_normal(nmax + 4096)
+
+    def make(L: int, tau: float, s: int) -> np.ndarray:
+        off = int(s) % 4096
+        h = g[off:off + L] * np.exp(-np.arange(L) / max(float(tau), 1.0))
+        return (h / np.abs(h).sum()).astype(np.float32)
+    return make
+
+
+def _lat_summary(lat: np.ndarray, blk: np.ndarray) -> dict:
+    if lat.size == 0:
+        return {"blocks": 0}
+    dl = blk.astype(np.float64) / FS
+    out = {"blocks": int(lat.size), "p50_ms": float(np.percentile(lat, 50) * 1e3),
+           "p99_ms": float(np.percentile(lat, 99) * 1e3), "max_ms": float(lat.max() * 1e3),
+           "deadline_miss_frac": float(np.mean(lat > dl)), "by_block": {}}
+    for b in sorted(set(blk.tolist())):
+        m = blk == b
+        out["by_block"][str(b)] = {"blocks": int(m.sum()), "deadline_ms": b / FS * 1e3,
+                                   "p50_ms": float(np.percentile(lat[m], 50) * 1e3),
+                                   "p99_ms": float(np.percentile(lat[m], 99) * 1e3),
+                                   "miss_frac": float(np.mean(lat[m] > b / FS))}
+    return out
+
+
+def bench_capacity(torch, capi, H64: np.ndarray, pool: np.ndarray, paced_s: float = 2.0) -> dict:
+    """Concurrent real-time streams of the 64-stream recipe (L = 48000, block 128,
+    own IRs) that one GB300 serves, batched (tc_server) and with one plain
+    launch per stream and block.
+      per-stream: M streams are served if one synchronous push per stream
+        (the cycle) takes at most half the block period (a block that arrives
+        just after its turn waits one cycle, then is served in the next).
+      batched: M streams are served if, with every stream reading a live
+        48 kHz source at a random phase and the worker thread running steps,
+        the p99 block latency (from the block's ready time to its result on
+        the host) is within the block deadline and at most 0.1 % of blocks
+        miss it. A sweep of synchronous one-block-per-stream steps gives the
+        starting point; paced runs then step M up (or down) by 25 %."""
+    L, B = H64.shape[1], BLOCK
+    period = B / FS
+    out = {"workload": f"streams with own IRs L={L} (tau 14400), block {B} at 48 kHz (deadline %.3f ms)"
+                       % (period * 1e3)}
+    # Plain per-stream launches: one tc_push_block per stream and block.
+    nps = 64
+    ss = [capi.tc_open_stream(L, B) for _ in range(nps)]
+    try:
+        for i, s in enumerate(ss):
+            capi.tc_set_ir(s, H64[i % 64])
+        xb = np.ascontiguousarray(pool[:B])
+        yb = np.empty(B, np.float32)
+        for _ in range(3):
+            for s in ss:
+                capi.tc_push_block(s, xb, yb)
+        t = time.perf_counter()
+        rounds = 10
+        for _ in range(rounds):
+            for s in ss:
+                capi.tc_push_block(s, xb, yb)
+        t_ps = (time.perf_counter() - t) / (rounds * nps)
+        # Best case for per-stream launches: device buffers, one CUDA stream,
+        # one synchronisation per round.
+        ts = torch.cuda.Stream()
+        xd = torch.from_numpy(xb).cuda()
+        yd = torch.empty(B, device="cuda")
+        for s in ss:
+            capi.tc_set_cuda_stream(s, ts)
+        for s in ss:
+            capi.tc_push(s, int(xd.data_ptr()), B, int(yd.data_ptr()), on_device=True)
+        ts.synchronize()
+        t = time.perf_counter()
+        for _ in range(rounds):
+            for s in ss:
+                capi.tc_push(s, int(xd.data_ptr()), B, int(yd.data_ptr()), on_device=True)
+            ts.synchronize()
+        t_async = (time.perf_counter() - t) / (rounds * nps)
+    finally:
+        for s in ss:
+            capi.tc_close(s)
+    out["per_stream"] = {"ms_per_block_push": t_ps * 1e3, "streams": int(period / 2 / t_ps),
+                         "mode": "tc_push_block per stream and block, host buffers (synchronous)"}
+    out["per_stream_async"] = {"ms_per_block_push": t_async * 1e3, "streams": int(period / 2 / t_async),
+                               "mode": "tc_push per stream and block, device buffers, one CUDA stream"}
+
+    srv = capi.tc_server_open(200 << 30, 1 << 22)
+    ids: list[int] = []
+    try:
+        def set_count(M, fresh=False):
+            if fresh:
+                for sid in ids:
+                    capi.tc_server_remove(srv, sid)
+                ids.clear()
+            while len(ids) < M:
+                ids.append(capi.tc_server_add(srv, L, B, H64[len(ids) % 64], capi.TC_SERVER_DISCARD_OUTPUT))
+            while len(ids) > M:
+                capi.tc_server_remove(srv, ids.pop())
+
+        # Sweep: synchronous steps over one block of each of M streams.
+        def cycle(M, reps=6):
+            set_count(M)
+            a = np.asarray(ids[:M], np.uint64)
+            addr = np.full(M, pool.ctypes.data, np.uint64)
+            ns = np.full(M, B, np.uint64)
+            ts_ = []
+            for r in range(2 + reps):
+                t = time.perf_counter()
+                capi.tc_server_submit_many(srv, a, addr, ns)
+                capi.tc_server_step(srv)
+                ts_.append(time.perf_counter() - t)
+            capi.tc_server_latencies(srv)
+            return float(np.mean(ts_[2:]))
+
+        sweep = {}
+        for M in (256, 512, 1024, 2048, 3072, 4096, 6144, 8192):
+            sweep[M] = cycle(M)
+            if sweep[M] > period:
+                break
+        ok = [m for m, t in sweep.items() if t <= period / 2]
+        m0 = max(ok) if ok else 256
+
+        # Paced runs: live sources, worker thread.
+        def paced(M, seed=11):
+            set_count(M, fresh=True)
+            rng = np.random.default_rng(seed)
+            warm = 0.5  # seconds of audio before recording starts
+            n_src = int((warm + paced_s) * FS)
+            t_start = capi.tc_server_clock() + 0.05
+            capi.tc_server_start(srv)
+            for sid in ids:
+                off = int(rng.integers(0, pool.size - n_src))
+                capi.tc_server_attach_source(srv, sid, (pool.ctypes.data + 4 * off, n_src),
+                                             t_start + rng.uniform(0, period))
+            while capi.tc_server_clock() < t_start + warm:
+                time.sleep(0.01)
+            capi.tc_server_latencies(srv)  # warm-up blocks are not counted
+            st0 = capi.tc_server_get_stats(srv)
+            t_rec = capi.tc_server_clock()
+            t_end = t_start + warm + paced_s + period + 2.0
+            while capi.tc_server_clock() < t_end:
+                time.sleep(0.02)
+                if capi.tc_server_clock() > t_start + warm + paced_s + period and \
+                        all(capi.tc_server_stream_state(srv, sid) == 2 for sid in ids):
+                    break
+            capi.tc_server_stop(srv)
+            st1 = capi.tc_server_get_stats(srv)
+            lat, blk = capi.tc_server_latencies(srv)
+            steps = st1.steps - st0.steps
+            wall = max(capi.tc_server_clock() - t_rec, 1e-9)
+            r = dict(_lat_summary(lat, blk), streams=M, seconds_of_audio=paced_s, warmup_s=warm,
+                     steps=int(steps), blocks_per_step=(st1.blocks - st0.blocks) / max(steps, 1),
+                     served_tap_macs_per_s=(st1.tap_macs - st0.tap_macs) / wall)
+            r["pass"] = bool(r.get("blocks", 0) > 0 and r["p99_ms"] <= period * 1e3
+                             and r["deadline_miss_frac"] <= 1e-3)
+            paced.last = r
+            return r
+
+        runs = {}
+        best = None
+        M = m0
+        step = 1.25 if paced(M)["pass"] else 0.8  # direction from the first run
+        runs[str(M)] = paced.last
+        if runs[str(M)]["pass"]:
+            best = M
+        for _ in range(5):
+            M = max(128, int(M * step) // 128 * 128)
+            if str(M) in runs:
+                break
+            r = paced(M)
+            runs[str(M)] = r
+            if r["pass"]:
+                best = max(best or 0, M)
+                if step < 1:
+                    break  # first pass going down
+            elif step > 1:
+                break  # first failure going up
+        out["batched"] = {"streams": best or 0,
+                          "criterion": "paced: p99 <= deadline and <= 0.1 % misses",
+                          "sync_cycle_ms": {str(k): v * 1e3 for k, v in sorted(sweep.items())},
+                          "mode": "tc_server worker thread, live 48 kHz sources, random phases"}
+        out["batched_paced"] = {k: {kk: vv for kk, vv in v.items() if kk != "by_block"} for k, v in runs.items()}
+    finally:
+        capi.tc_server_close(srv)
+    out["ratio_batched_vs_per_stream"] = out["batched"]["streams"] / max(out["per_stream"]["streams"], 1)
+    out["ratio_batched_vs_per_stream_async"] = out["batched"]["streams"] / max(out["per_stream_async"]["streams"], 1)
+    return out
+
+
+def bench_trace(capi, pool: np.ndarray, seconds: float, budget_gb: float = 96.0) -> dict:
+    """Serving trace replayed in real time: Poisson arrivals (200 streams/s),
+    durations 0.5-30 s, IR lengths 256-480000, blocks {32..256}, 10 % with a
+    mid-stream IR swap. A stream is admitted at its arrival (memory budget;
+    it waits and retries when the budget is full), reads a live 48 kHz source
+    from then on and is removed once drained. The worker thread runs the
+    steps; this thread only admits and removes."""
+    tr = synth.serving_trace(duration_s=seconds)
+    make = _ir_maker()
+    irs = {t.sid: [make(t.L, t.tau, sd) for sd in t.ir_seeds] for t in tr}
+    srv = capi.tc_server_open(int(budget_gb * (1 << 30)), 1 << 22)
+    waits, max_active, live = 0, 0, {}
+    try:
+        capi.tc_server_start(srv)
+        t_start = capi.tc_server_clock() + 0.02
+        t_end = t_start + seconds
+        pending = list(tr)
+        while True:
+            now = capi.tc_server_clock()
+            if now >= t_end:
+                break
+            while pending and t_start + pending[0].arrival_s <= now:
+                t = pending[0]
+                try:
+                    sid = capi.tc_server_add(srv, t.L, t.block, irs[t.sid][0], capi.TC_SERVER_DISCARD_OUTPUT)
+                except capi.TcError as e:
+                    if e.code != "TC_ENOMEM":
+                        raise
+                    waits += 1
+                    break
+                if t.swap_at >= 0:
+                    capi.tc_server_set_ir_at(srv, sid, irs[t.sid][1], t.swap_at)
+                off = (t.sid * 7919) % (pool.size - t.n) if t.n < pool.size else 0
+                n = min(t.n, pool.size)
+                t0 = capi.tc_server_clock()
+                capi.tc_server_attach_source(srv, sid, (pool.ctypes.data + 4 * off, n), t0)
+                live[sid] = t0 + n / FS
+                pending.pop(0)
+            max_active = max(max_active, len(live))
+            for sid in [k for k, te in live.items() if te <= now]:
+                if capi.tc_server_stream_state(srv, sid) == 2:
+                    capi.tc_server_remove(srv, sid)
+                    del live[sid]
+            time.sleep(0.001)
+        capi.tc_server_stop(srv)
+        st = capi.tc_server_get_stats(srv)
+        lat, blk = capi.tc_server_latencies(srv)
+    finally:
+        capi.tc_server_close(srv)
+    arrived = sum(1 for t in tr if t.arrival_s < seconds)
+    return dict(_lat_summary(lat, blk), seconds=seconds, streams_arrived=arrived, max_active=max_active,
+                served_tap_macs_per_s=st.tap_macs / seconds, steps=int(st.steps),
+                blocks_per_step=st.blocks / max(st.steps, 1), busy_frac=st.busy_s / seconds,
+                admission_waits=waits, mem_budget_gb=budget_gb,
+                precision="fp32 (every stream has its own IR: no shared-IR batch for the tensor cores)",
+                inputs="live 48 kHz sources cut from a seeded audio pool; IRs cut from a seeded Gaussian pool")
+
+
+def bench_serving(torch, capi, H64: np.ndarray, trace_s: float) -> dict:
+    pool = synth.audio(32 * FS, 4242)
+    out = {"capacity": bench_capacity(torch, capi, H64, pool)}
+    if trace_s > 0:
+        out["trace"] = bench_trace(capi, pool, trace_s)
+    return out
+
+
 def check_sampled(runner, n_check=64) -> dict:
     """Sampled outputs of the last device step against Eq. (4) computed one by one (FP64 oracle)."""
     import oracle
@@ -443,6 +702,9 @@ def main():
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-shared", action="store_true", help="skip the shared-IR tensor-core section")
     ap.add_argument("--only-shared", action="store_true", help="run only the shared-IR section")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving section")
+    ap.add_argument("--only-serving", action="store_true", help="run only the serving section")
+    ap.add_argument("--trace-seconds", type=float, default=15.0)
     ap.add_argument("--cpu-samples", type=int, default=30_000)
     ap.add_argument("--ref-samples", type=int, default=6_000)
     args = ap.parse_args()
@@ -469,6 +731,11 @@ def main():
 
     if args.only_shared:
         print(json.dumps({"shared_ir": bench_shared(torch, max(1, args.steps), max(1, args.warmup))}), flush=True)
+        dist.close()
+        return
+    if args.only_serving:
+        H64 = np.stack([synth.decayed_ir(L_TAPS, 14_400.0, synth.ir_seed(c, 0)) for c in range(64)])
+        print(json.dumps({"serving": bench_serving(torch, capi, H64, args.trace_seconds)}), flush=True)
         dist.close()
         return
 
@@ -592,6 +859,9 @@ def main():
     shared = None
     if not args.no_shared and dist.world == 1:
         shared = bench_shared(torch, steps=2, warmup=1)
+    serving = None
+    if not args.no_serving and dist.world == 1:
+        serving = bench_serving(torch, capi, np.ascontiguousarray(w.H[:, 0]), args.trace_seconds)
     if dist.rank == 0:
         per_stream_rt = FS * L_TAPS  # tap-MAC/s one real-time stream needs
         line = {"metric": METRIC, "value": value, "unit": "tap-MAC/s", "n_gpus": dist.world,
@@ -601,6 +871,7 @@ def main():
                 "realtime_streams_48k": value / per_stream_rt,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": int(launches), "latency": latency, "check": check, "shared_ir": shared,
+                "serving": serving,
                 "autotune_push_ms_per_sample": {str(k): v for k, v in tune.items()} or None}
         print(json.dumps(line), flush=True)
     dist.close()

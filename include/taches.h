@@ -267,6 +267,8 @@ typedef struct tc_server_stats {
     uint64_t blocks;     /* blocks completed (flush tails included) */
     uint64_t rejected;   /* tc_server_add calls refused for memory */
     double busy_s;       /* wall time spent inside steps (seconds) */
+    double tap_macs;     /* useful work done: input samples x L, summed over finished blocks
+                            (flush tails excluded) */
 } tc_server_stats;
 
 /* Opens a server on the current CUDA device. mem_budget_bytes bounds the
@@ -300,6 +302,19 @@ tc_status tc_server_submit(tc_server *srv, uint64_t id, const float *x, size_t n
  * from there. Checks every block first and queues none on an error. */
 tc_status tc_server_submit_many(tc_server *srv, size_t count, const uint64_t *ids, const float *const *xs,
                                 const size_t *ns, const double *t_ready);
+/* Live input: the stream's next input is x[0..n), after any input already
+ * submitted. It arrives at fs samples per second from time t0 on
+ * tc_server_clock(), as from a capture device. Block b (b = 0, 1, ...) is
+ * queued at its ready time t0 + min((b + 1) * block, n) / fs and its latency
+ * counts from there; the last block may be short, and the input ends with
+ * it. The library reads x in place when the block runs: the caller keeps x
+ * alive and unchanged until the stream is removed. TC_ESTATE if the stream
+ * already has a source, has blocks queued or its input has ended;
+ * tc_server_submit is refused on the stream afterwards. */
+tc_status tc_server_attach_source(tc_server *srv, uint64_t id, const float *x, size_t n, double t0, double fs);
+/* *state: 0 input still open, 1 input ended with blocks still queued or
+ * running, 2 drained (every block done: ready for flush or remove). */
+tc_status tc_server_stream_state(tc_server *srv, uint64_t id, int *state);
 /* Runs one batched step on the calling thread (TC_ESTATE while the worker
  * runs). *blocks_done (may be NULL) is the number of blocks it completed. */
 tc_status tc_server_step(tc_server *srv, size_t *blocks_done);
@@ -323,11 +338,25 @@ tc_status tc_server_flush(tc_server *srv, uint64_t id, float *y, size_t cap, siz
 tc_status tc_server_remove(tc_server *srv, uint64_t id);
 tc_status tc_server_get_stats(tc_server *srv, tc_server_stats *st);
 /* Moves up to cap recorded block latencies (seconds from ready to result on
- * the host, in completion order) into out and forgets them. Flush tails are
+ * the host, in completion order) into out, and the nominal block size of each
+ * block's stream into block (may be NULL), then forgets them. Flush tails are
  * not recorded. */
-tc_status tc_server_latencies(tc_server *srv, double *out, size_t cap, size_t *n_out);
+tc_status tc_server_latencies(tc_server *srv, double *out, uint32_t *block, size_t cap, size_t *n_out);
 /* Monotonic clock of the poll timestamps (seconds). */
 double tc_server_clock(void);
+/* Step log (tracing): one record per step, the last 65536 steps kept. */
+typedef struct tc_server_step_rec {
+    double t_begin;      /* step start (tc_server_clock) */
+    double t_launch;     /* host packing done, copies and kernels enqueued from here */
+    double t_done;       /* results on the host */
+    uint32_t blocks;     /* blocks in the step */
+    uint32_t samples;    /* input samples in the step */
+    uint32_t ctas;       /* CTAs of the gather launch */
+    uint32_t variant;    /* tap chunk of the gather: 0 = 640, 1 = 2560, 2 = 8320 taps */
+} tc_server_step_rec;
+/* Moves the newest min(cap, logged) records (oldest first) into out and
+ * clears the log. */
+tc_status tc_server_step_log(tc_server *srv, tc_server_step_rec *out, size_t cap, size_t *n_out);
 
 /* ---------------------------------------------------------------------- */
 /* Diagnostics                                                             */

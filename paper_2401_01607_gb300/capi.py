@@ -42,7 +42,13 @@ class TcInfo(ctypes.Structure):
 class TcServerStats(ctypes.Structure):
     _fields_ = [("streams", ctypes.c_size_t), ("mem_used", ctypes.c_size_t), ("mem_budget", ctypes.c_size_t),
                 ("steps", ctypes.c_uint64), ("blocks", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
-                ("busy_s", ctypes.c_double)]
+                ("busy_s", ctypes.c_double), ("tap_macs", ctypes.c_double)]
+
+
+class TcServerStepRec(ctypes.Structure):
+    _fields_ = [("t_begin", ctypes.c_double), ("t_launch", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("blocks", ctypes.c_uint32), ("samples", ctypes.c_uint32), ("ctas", ctypes.c_uint32),
+                ("variant", ctypes.c_uint32)]
 
 
 _lib = None
@@ -88,7 +94,10 @@ _SIGS = {
     "tc_server_flush": [_vp, _u64, _vp, _sz, ctypes.POINTER(_sz)],
     "tc_server_remove": [_vp, _u64],
     "tc_server_get_stats": [_vp, ctypes.POINTER(TcServerStats)],
-    "tc_server_latencies": [_vp, _vp, _sz, ctypes.POINTER(_sz)],
+    "tc_server_latencies": [_vp, _vp, _vp, _sz, ctypes.POINTER(_sz)],
+    "tc_server_attach_source": [_vp, _u64, _vp, _sz, ctypes.c_double, ctypes.c_double],
+    "tc_server_stream_state": [_vp, _u64, ctypes.POINTER(_int)],
+    "tc_server_step_log": [_vp, _vp, _sz, ctypes.POINTER(_sz)],
 }
 
 
@@ -349,6 +358,24 @@ def tc_server_submit_many(srv: int, ids, x_addrs, ns, t_ready=None) -> None:
           ns.ctypes.data_as(_vp), None if tr is None else tr.ctypes.data_as(_vp))
 
 
+def tc_server_attach_source(srv: int, sid: int, x, t0: float, fs: float = 48_000.0) -> None:
+    """x: C-contiguous float32 numpy array or an integer host address paired
+    with n via (addr, n). The caller keeps x alive until the stream is removed."""
+    if isinstance(x, tuple):
+        addr, n = x
+        _call("tc_server_attach_source", srv, int(sid), _vp(int(addr)), int(n), float(t0), float(fs))
+        return
+    if not isinstance(x, np.ndarray) or x.dtype != np.float32 or not x.flags.c_contiguous:
+        raise TypeError("a live source must be a C-contiguous float32 numpy array (it is read in place)")
+    _call("tc_server_attach_source", srv, int(sid), x.ctypes.data_as(_vp), x.size, float(t0), float(fs))
+
+
+def tc_server_stream_state(srv: int, sid: int) -> int:
+    st = _int()
+    _call("tc_server_stream_state", srv, int(sid), ctypes.byref(st))
+    return int(st.value)
+
+
 def tc_server_step(srv: int) -> int:
     n = _sz()
     _call("tc_server_step", srv, ctypes.byref(n))
@@ -389,11 +416,33 @@ def tc_server_get_stats(srv: int) -> TcServerStats:
     return st
 
 
-def tc_server_latencies(srv: int, cap: int = 1 << 20) -> np.ndarray:
-    out = np.empty(int(cap), dtype=np.float64)
+def tc_server_latencies(srv: int, cap: int = 1 << 20):
+    """Returns every recorded (latency seconds, nominal block size) pair as two
+    arrays and forgets them."""
+    lats, blks = [], []
+    while True:
+        out = np.empty(int(cap), dtype=np.float64)
+        blk = np.empty(int(cap), dtype=np.uint32)
+        n = _sz()
+        _call("tc_server_latencies", srv, out.ctypes.data_as(_vp), blk.ctypes.data_as(_vp), out.size,
+              ctypes.byref(n))
+        k = int(n.value)
+        lats.append(out[:k])
+        blks.append(blk[:k])
+        if k < cap:
+            break
+    return np.concatenate(lats), np.concatenate(blks)
+
+
+def tc_server_step_log(srv: int, cap: int = 1 << 16) -> np.ndarray:
+    """Step log as a structured array (t_begin, t_launch, t_done, blocks,
+    samples, ctas, variant), oldest first; clears the log."""
+    buf = (TcServerStepRec * int(cap))()
     n = _sz()
-    _call("tc_server_latencies", srv, out.ctypes.data_as(_vp), out.size, ctypes.byref(n))
-    return out[: int(n.value)].copy()
+    _call("tc_server_step_log", srv, ctypes.cast(buf, _vp), int(cap), ctypes.byref(n))
+    dt = np.dtype([("t_begin", "f8"), ("t_launch", "f8"), ("t_done", "f8"), ("blocks", "u4"), ("samples", "u4"),
+                   ("ctas", "u4"), ("variant", "u4")])
+    return np.frombuffer(bytes(buf), dtype=dt, count=int(n.value)).copy()
 
 
 def tc_server_clock() -> float:

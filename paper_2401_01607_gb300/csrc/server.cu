@@ -3,18 +3,23 @@
 // Real-time use of the taches-algorithm (Sec. 5.1 and Sec. 6: low-latency
 // output, multichannel use, IRs that change while running) with many
 // audio streams at once. Each stream has its own IR length, block size and IR
-// versions. A step collects every block that is pending on any stream and
-// runs them all as one batch:
-//   one host->device copy of the packed input, one scatter kernel into the
-//   streams' history rows, one K1 work-list launch (one item per stream), one
-//   device->host copy of the packed output.
-// Blocks submitted while a step is on the GPU join the next step. A worker
-// thread (tc_server_start) runs steps back to back whenever blocks are
-// pending. Streams are admitted while their device state fits the memory
-// budget (TC_ENOMEM otherwise) and release it when removed.
+// versions. A step collects the queued blocks of every stream (up to kMerge
+// consecutive blocks of a stream become one work item) and runs them all as
+// one batch:
+//   one host->device copy of the packed input and work list, one ingest
+//   kernel into the streams' history rows (with any row compactions), one K1
+//   work-list launch (one item
+//   per stream), one device->host copy of the packed output.
+// The worker thread (tc_server_start) keeps two steps in flight: while the
+// GPU runs step k, the host collects and launches step k+1 (its own pinned
+// buffers; device buffers are shared because one CUDA stream orders them).
+// Blocks submitted, or released by a live source, while a step is on the GPU
+// join the next step. Streams are admitted while their device state fits the
+// memory budget (TC_ENOMEM otherwise) and release it when removed.
 //
 // Threads: submit/poll take only the queue mutex and never wait for the GPU;
-// add/remove/set_ir and step take the state mutex.
+// add/set_ir upload on their own CUDA stream and take the state mutex only
+// briefly; steps take the state mutex while packing and delivering.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -24,8 +29,10 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <queue>
 #include <string>
 #include <thread>
+#include <unordered_set>
 #include <vector>
 
 #include "../../include/taches.h"
@@ -34,6 +41,8 @@
 namespace {
 
 constexpr int kMaxVer = 16;
+constexpr int kMerge = 8;  // consecutive blocks of one stream merged into one work item
+constexpr size_t kLogSteps = 1 << 16;
 // Chunk-tasks per tile stay within K1's pairwise stack with the smallest chunk.
 constexpr size_t kMaxL = (size_t)tc::K1_MAX_CHUNK_TASKS * 32 * tc::K1_SEG - 8;
 
@@ -52,9 +61,12 @@ long long rup(long long a, long long m) { return (a + m - 1) / m * m; }
 long long fl8(long long a) { return a >= 0 ? (a & ~7LL) : -(((-a) + 7) & ~7LL); }
 
 struct Block {
-    std::vector<float> x;
+    std::vector<float> own;  // copied input (submit, flush tail)
+    const float *src;        // or input read in place from a live source
+    long long n;
     double t_submit;  // ready time of the block (latency is measured from it)
     bool tail;        // zero input of the flush: output goes to the tail buffer
+    const float *data() const { return src ? src : own.data(); }
 };
 
 struct OutBlock {
@@ -65,7 +77,11 @@ struct OutBlock {
 
 struct SStream {
     uint64_t id = 0;
-    long long L = 0, block = 0, Lpad = 0, keep = 0, cap = 0, base = 0, pos = 0;
+    long long L = 0, block = 0, Lpad = 0, keep = 0, cap = 0, base = 0;
+    long long pos = 0;       // input samples launched (history written up to here)
+    long long pos_done = 0;  // input samples whose outputs are on the host
+    long long stagger = 0;   // early-compaction offset in [0, keep / 2)
+    int inflight = 0;        // work items launched, not yet delivered (queue mutex)
     int nslots = 3;
     bool ended = false;   // a short block was submitted: input is over
     bool flushed = false;
@@ -84,6 +100,17 @@ struct SStream {
     std::deque<Block> pending;   // guarded by the queue mutex
     std::deque<OutBlock> done;   // guarded by the queue mutex
     std::vector<float> tail_out; // output of the flush's zero blocks
+
+    // Live input source (tc_server_attach_source): x[0, src_n) arriving at
+    // src_fs samples/s from clock time src_t0; block b is released at its
+    // ready time src_t0 + min((b + 1) * block, src_n) / src_fs.
+    const float *src = nullptr;
+    long long src_n = 0, src_next = 0;
+    double src_t0 = 0.0, src_fs = 0.0;
+    double src_ready(long long b) const
+    {
+        return src_t0 + (double)std::min((b + 1) * block, src_n) / src_fs;
+    }
 };
 
 }  // namespace
@@ -92,29 +119,53 @@ struct tc_server {
     size_t budget = 0, used = 0;
     size_t max_step_samples = 0;
     int device = 0;
-    cudaStream_t cs = nullptr;
-    std::mutex mu_state;  // device state of streams, steps
+    cudaStream_t cs = nullptr;     // steps; frees of removed streams
+    cudaStream_t admin = nullptr;  // allocations and IR uploads of add / set_ir_at
+    cudaMemPool_t pool = nullptr;  // stream-ordered device memory of the streams
+    std::mutex mu_admin;  // admin stream and IR staging (add / set_ir_at serialise on it)
+    std::mutex mu_state;  // host state the steps read (positions, versions, budget)
     std::mutex mu_queue;  // pending input / finished output queues
     std::condition_variable cv;
     std::map<uint64_t, std::unique_ptr<SStream>> streams;
     uint64_t next_id = 1;
     uint64_t rr = 0;  // first stream id visited by the next step
+    size_t npending = 0;  // blocks queued over all streams (queue mutex)
+    // Live sources by next ready time (queue mutex).
+    std::priority_queue<std::pair<double, uint64_t>, std::vector<std::pair<double, uint64_t>>,
+                        std::greater<std::pair<double, uint64_t>>>
+        src_heap;
 
-    // Step staging.
-    // Step staging. Input side: ONE pinned buffer and its device mirror, laid
-    // out per step as [K1 items][CTA offsets][scatter table][history
-    // pointers][packed input] (16-byte aligned regions) and copied with one
-    // host-to-device copy. Output side: [error word, padded to 16 bytes]
-    // [packed output], copied back with one device-to-host copy.
-    char *pin_stage = nullptr, *d_stage = nullptr;
-    size_t stage_bytes = 0;
-    size_t max_items = 0;
-    float *pin_out = nullptr, *d_out = nullptr;  // [4 + max_step_samples]
-    DevTable *pin_tables = nullptr;
+    // Step staging, one set per step in flight. Input side: a pinned buffer
+    // laid out per step as [K1 items][CTA offsets][ingest table][history
+    // pointers][packed input] (16-byte aligned regions), copied with one
+    // host-to-device copy into d_stage. Output side: [error word, padded to
+    // 16 bytes][packed output], copied back with one device-to-host copy.
+    struct Item {
+        SStream *s;
+        std::vector<Block> blocks;
+        long long off, n;  // packed input / output offset and samples
+    };
+    struct StepBuf {
+        char *pin_stage = nullptr;
+        size_t items_cap = 0;
+        float *pin_out = nullptr;  // [4 + max_step_samples]
+        DevTable *pin_tables = nullptr;
+        cudaEvent_t done = nullptr;
+        std::vector<Item> items;
+        size_t total = 0;
+        double t_begin = 0.0, t_launch = 0.0;
+        long long ctas = 0;
+        int variant = 0;
+    } buf[2];
+    // Shared device buffers (steps run in order on the step stream).
+    char *d_stage = nullptr;
+    size_t d_stage_items = 0;
+    float *d_out = nullptr;  // [4 + max_step_samples]
     float *scratch = nullptr;
     size_t scratch_floats = 0;
     unsigned *counters = nullptr;
     size_t counters_n = 0;
+    double last_done = 0.0;
     float *ir_stage = nullptr;
     size_t ir_stage_floats = 0;
 
@@ -128,9 +179,16 @@ struct tc_server {
 
     // Stats. Latencies (t_done - ready time) of finished blocks, drained by
     // tc_server_latencies; guarded by the queue mutex.
-    std::vector<double> lat;
+    // Chunked storage: growing never copies or faults in a large array on the
+    // worker thread.
+    std::deque<double> lat;
+    std::deque<uint32_t> lat_block;  // nominal block size of each recorded latency
+    // Step log (tracing): the last kLogSteps steps, oldest first once full.
+    std::vector<tc_server_step_rec> steplog;
+    size_t steplog_next = 0;
     uint64_t steps = 0, blocks = 0, rejected = 0;
     double busy_s = 0.0;
+    double tap_macs = 0.0;
 };
 
 namespace {
@@ -156,39 +214,71 @@ tc_status sfail(tc_status st, const std::string &m)
             return st_;         \
     } while (0)
 
-// Scatter kernel: CTA i copies the n_i samples of item i from the packed input
-// at src_i into its stream's history row at column col_i.
-__global__ void scatter_kernel(const float *__restrict__ in, const long long *__restrict__ sc, float *const *dst,
-                               int nitems)
+// Ingest kernel, CTA i for work item i (table row sc[5i..5i+4] = input
+// offset, n, history column, compaction shift, compaction length):
+//   1. compaction, if length > 0: history columns [shift, shift + length)
+//      move to [0, length) (the two ranges do not overlap: shift >= length;
+//      shift and the row start are multiples of 8 floats);
+//   2. the item's n new samples go from the packed input to the history at
+//      its column.
+__global__ void ingest_kernel(const float *__restrict__ in, const long long *__restrict__ sc, float *const *dst,
+                             int nitems)
 {
     const int it = blockIdx.x;
     if (it >= nitems)
         return;
-    const long long src = sc[3 * it], n = sc[3 * it + 1], col = sc[3 * it + 2];
-    float *d = dst[it] + col;
+    const long long *r = sc + 5 * (long long)it;
+    const long long src = r[0], n = r[1], col = r[2], shift = r[3], len = r[4];
+    float *row = dst[it];
+    if (len > 0) {
+        const float4 *from = reinterpret_cast<const float4 *>(row + shift);
+        float4 *to = reinterpret_cast<float4 *>(row);
+        const long long n4 = len >> 2;
+        for (long long j = threadIdx.x; j < n4; j += blockDim.x)
+            to[j] = from[j];
+        for (long long j = (n4 << 2) + threadIdx.x; j < len; j += blockDim.x)
+            row[j] = row[shift + j];
+        __syncthreads();
+    }
+    float *d = row + col;
     for (long long j = threadIdx.x; j < n; j += blockDim.x)
         d[j] = in[src + j];
 }
 
+// History row of a stream: `keep` samples behind the launch position (L taps
+// plus one tap chunk and the alignment shift), room for kMerge blocks and a
+// tile's overrun, and a stagger window of keep / 2 samples: each stream
+// compacts its row at its own point of that window, so streams that started
+// together do not all compact in the same step.
 size_t stream_bytes(long long L, long long block, int nslots, long long *keep, long long *cap, long long *Lpad)
 {
     *keep = rup(L + tc::K1_KC_MAX + 16, 8);
-    *cap = rup(2 * *keep + block + 512 + 160, 64);
+    *cap = rup(2 * *keep + kMerge * block + 512 + 160 + *keep / 2, 64);
     *Lpad = rup(L + 4 + tc::K1_KC_MAX, 4);
     return (size_t)*cap * 4 + (size_t)nslots * 4 * (size_t)*Lpad * 4 + sizeof(DevTable);
 }
 
-void free_stream(SStream *s)
+// Returns a removed stream's device memory to the pool, ordered after every
+// step that used it (no host synchronisation).
+void free_stream(tc_server *srv, SStream *s)
 {
-    cudaFree(s->hist);
-    cudaFree(s->ir);
-    cudaFree(s->d_vt);
+    if (s->hist)
+        cudaFreeAsync(s->hist, srv->cs);
+    if (s->ir)
+        cudaFreeAsync(s->ir, srv->cs);
+    if (s->d_vt)
+        cudaFreeAsync(s->d_vt, srv->cs);
+    s->hist = nullptr;
+    s->ir = nullptr;
+    s->d_vt = nullptr;
 }
 
-// Drops versions no future output needs (next version started >= L-1 ago).
+// Drops versions no future output needs: the next version started at or
+// before the oldest input sample that an output not yet delivered reads.
+// (pos_done, not pos: a step in flight may still read an older version.)
 void retire(SStream *s)
 {
-    const long long oldest = s->pos - s->L + 1;
+    const long long oldest = s->pos_done - s->L + 1;
     size_t drop = 0;
     while (drop + 1 < s->vt.size() && s->vt[drop + 1].start <= oldest)
         ++drop;
@@ -200,40 +290,94 @@ void retire(SStream *s)
     }
 }
 
-tc_status set_ir(tc_server *srv, SStream *s, const float *h, size_t n, long long sample)
+// Queued input samples of s not yet run (queue mutex held by the caller).
+long long queued_samples(const SStream *s)
 {
-    if (!h || n == 0 || (long long)n > s->L)
-        return sfail(TC_EINVAL, "tc_server: IR length must be in [1, L]");
-    if (sample < s->pos || (!s->vt.empty() && sample < s->vt.back().start))
-        return sfail(TC_EINVAL, "tc_server: IR switch before the next sample or the latest version");
-    retire(s);
-    int slot = -1;
-    const bool replace = !s->vt.empty() && s->vt.back().start == sample;
-    if (replace) {
-        slot = s->vt.back().slot;
-    } else {
-        for (int i = 0; i < s->nslots; ++i)
-            if (!s->slot_used[(size_t)i]) {
-                slot = i;
-                break;
-            }
-        if (slot < 0)
-            return sfail(TC_ENOMEM, "tc_server: every IR slot of the stream holds a live version");
-    }
+    long long q = 0;
+    for (auto &b : s->pending)
+        q += b.n;
+    return q;
+}
+
+// Uploads IR h[0..n) (zero-padded to L) as the four shifted copies into IR
+// slot `slot` of s on the admin stream and waits for it. Caller holds
+// mu_admin (not mu_state: steps keep running meanwhile; the slot is one no
+// live version uses).
+tc_status upload_ir(tc_server *srv, SStream *s, int slot, const float *h, size_t n)
+{
     if (n > srv->ir_stage_floats) {
-        S_CU(cudaStreamSynchronize(srv->cs));
+        S_CU(cudaStreamSynchronize(srv->admin));
         cudaFree(srv->ir_stage);
         srv->ir_stage = nullptr;
+        srv->ir_stage_floats = 0;
         S_CU(cudaMalloc(&srv->ir_stage, n * sizeof(float)));
         srv->ir_stage_floats = n;
     }
-    S_CU(cudaMemcpyAsync(srv->ir_stage, h, n * sizeof(float), cudaMemcpyHostToDevice, srv->cs));
+    S_CU(cudaMemcpyAsync(srv->ir_stage, h, n * sizeof(float), cudaMemcpyHostToDevice, srv->admin));
     float *dst = s->ir + (size_t)slot * 4 * (size_t)s->Lpad;
-    S_CU(tc::ir_prep_launch(srv->ir_stage, (long long)n, (long long)n, 1, dst, 4 * s->Lpad, s->Lpad, s->Lpad, srv->cs));
-    S_CU(cudaStreamSynchronize(srv->cs));  // h and the staging buffer are free on return
-    if (!replace) {
+    S_CU(tc::ir_prep_launch(srv->ir_stage, (long long)n, (long long)n, 1, dst, 4 * s->Lpad, s->Lpad, s->Lpad,
+                            srv->admin));
+    S_CU(cudaStreamSynchronize(srv->admin));  // h and the staging buffer are free on return
+    return TC_OK;
+}
+
+// New IR version of s from input sample `sample` on. Three phases so that
+// steps are not held up by the upload: pick a free slot (state lock), upload
+// (admin lock only), publish the version (state lock). Caller holds mu_admin.
+tc_status set_ir(tc_server *srv, uint64_t id, const float *h, size_t n, long long sample)
+{
+    SStream *s = nullptr;
+    int slot = -1;
+    bool replace = false;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu_state);
+        auto it = srv->streams.find(id);
+        if (it == srv->streams.end())
+            return sfail(TC_EINVAL, "tc_server_set_ir_at: unknown stream");
+        s = it->second.get();
+        if (!h || n == 0 || (long long)n > s->L)
+            return sfail(TC_EINVAL, "tc_server: IR length must be in [1, L]");
+        long long queued;
+        {
+            std::lock_guard<std::mutex> lq(srv->mu_queue);
+            queued = queued_samples(s);
+        }
+        if (sample < s->pos + queued)
+            return sfail(TC_EINVAL, "tc_server_set_ir_at: the switch sample was already submitted");
+        if (!s->vt.empty() && sample < s->vt.back().start)
+            return sfail(TC_EINVAL, "tc_server_set_ir_at: switch before the latest version");
+        retire(s);
+        // Replacing the newest version in place is only safe while no block
+        // that uses it has been submitted.
+        replace = !s->vt.empty() && s->vt.back().start == sample;
+        for (int i = 0; i < s->nslots && slot < 0; ++i)
+            if (!s->slot_used[(size_t)i])
+                slot = i;
+        if (slot < 0)
+            return sfail(TC_ENOMEM, "tc_server: every IR slot of the stream holds a live version");
+        s->slot_used[(size_t)slot] = 1;  // reserved: retire() never frees a slot outside the table
+    }
+    tc_status st = upload_ir(srv, s, slot, h, n);
+    std::lock_guard<std::mutex> lk(srv->mu_state);
+    if (st != TC_OK) {
+        s->slot_used[(size_t)slot] = 0;
+        return st;
+    }
+    long long queued;
+    {
+        std::lock_guard<std::mutex> lq(srv->mu_queue);
+        queued = queued_samples(s);
+    }
+    if (sample < s->pos + queued) {
+        // A live source released the switch sample during the upload.
+        s->slot_used[(size_t)slot] = 0;
+        return sfail(TC_ESTATE, "tc_server_set_ir_at: the switch sample became due during the upload");
+    }
+    if (replace) {
+        s->slot_used[(size_t)s->vt.back().slot] = 0;
+        s->vt.back().slot = slot;
+    } else {
         s->vt.push_back({sample, slot});
-        s->slot_used[(size_t)slot] = 1;
     }
     s->vt_dirty = true;
     return TC_OK;
@@ -251,32 +395,44 @@ StageLayout stage_layout(size_t ni, size_t samples)
     l.items = 0;
     l.cta = a16(ni * sizeof(tc::K1Params));
     l.sc = a16(l.cta + (ni + 1) * sizeof(long long));
-    l.dst = a16(l.sc + 3 * ni * sizeof(long long));
+    l.dst = a16(l.sc + 5 * ni * sizeof(long long));
     l.in = a16(l.dst + ni * sizeof(float *));
     l.end = l.in + samples * sizeof(float);
     return l;
 }
 
-tc_status grow(tc_server *srv, size_t items, size_t scratch_floats, size_t counters)
+// Grows step buffer b and the shared device buffers. Waits for the step in
+// flight first (rare: only when a step is larger than any before).
+tc_status grow(tc_server *srv, tc_server::StepBuf &b, size_t items, size_t scratch_floats, size_t counters)
 {
-    if (items > srv->max_items) {
-        const size_t m = std::max(items, srv->max_items * 2 + 64);
-        cudaFreeHost(srv->pin_stage);
+    const bool need = items > b.items_cap || items > srv->d_stage_items || scratch_floats > srv->scratch_floats ||
+                      counters > srv->counters_n;
+    if (!need)
+        return TC_OK;
+    S_CU(cudaStreamSynchronize(srv->cs));
+    if (items > b.items_cap) {
+        const size_t m = std::max(items, b.items_cap * 2 + 64);
+        cudaFreeHost(b.pin_stage);
+        cudaFreeHost(b.pin_tables);
+        b.pin_stage = nullptr;
+        b.pin_tables = nullptr;
+        b.items_cap = 0;
+        S_CU(cudaHostAlloc(&b.pin_stage, stage_layout(m, srv->max_step_samples).end, cudaHostAllocDefault));
+        S_CU(cudaHostAlloc(&b.pin_tables, m * sizeof(DevTable), cudaHostAllocDefault));
+        b.items_cap = m;
+    }
+    if (items > srv->d_stage_items) {
+        const size_t m = std::max(items, srv->d_stage_items * 2 + 64);
         cudaFree(srv->d_stage);
-        cudaFreeHost(srv->pin_tables);
-        srv->pin_stage = srv->d_stage = nullptr;
-        srv->pin_tables = nullptr;
-        srv->max_items = 0;
-        const size_t bytes = stage_layout(m, srv->max_step_samples).end;
-        S_CU(cudaHostAlloc(&srv->pin_stage, bytes, cudaHostAllocDefault));
-        S_CU(cudaMalloc(&srv->d_stage, bytes));
-        S_CU(cudaHostAlloc(&srv->pin_tables, m * sizeof(DevTable), cudaHostAllocDefault));
-        srv->stage_bytes = bytes;
-        srv->max_items = m;
+        srv->d_stage = nullptr;
+        srv->d_stage_items = 0;
+        S_CU(cudaMalloc(&srv->d_stage, stage_layout(m, srv->max_step_samples).end));
+        srv->d_stage_items = m;
     }
     if (scratch_floats > srv->scratch_floats) {
         cudaFree(srv->scratch);
         srv->scratch = nullptr;
+        srv->scratch_floats = 0;
         const size_t m = std::max(scratch_floats, srv->scratch_floats * 2);
         S_CU(cudaMalloc(&srv->scratch, m * sizeof(float)));
         srv->scratch_floats = m;
@@ -284,6 +440,7 @@ tc_status grow(tc_server *srv, size_t items, size_t scratch_floats, size_t count
     if (counters > srv->counters_n) {
         cudaFree(srv->counters);
         srv->counters = nullptr;
+        srv->counters_n = 0;
         const size_t m = std::max(counters, srv->counters_n * 2);
         S_CU(cudaMalloc(&srv->counters, m * sizeof(unsigned)));
         S_CU(cudaMemsetAsync(srv->counters, 0, m * sizeof(unsigned), srv->cs));
@@ -292,57 +449,98 @@ tc_status grow(tc_server *srv, size_t items, size_t scratch_floats, size_t count
     return TC_OK;
 }
 
-// One batched step over every pending block. Caller holds mu_state.
-tc_status step_locked(tc_server *srv, size_t *nblocks)
+// Moves every live-source block whose ready time has passed into its
+// stream's queue. Caller holds the queue mutex. Returns the next ready time
+// (+inf if no source is live).
+double release_sources(tc_server *srv, double now)
 {
-    *nblocks = 0;
-    struct Work {
-        SStream *s;
+    while (!srv->src_heap.empty() && srv->src_heap.top().first <= now) {
+        const uint64_t id = srv->src_heap.top().second;
+        srv->src_heap.pop();
+        auto it = srv->streams.find(id);
+        if (it == srv->streams.end())
+            continue;  // removed
+        SStream *s = it->second.get();
+        if (!s->src || s->src_next * s->block >= s->src_n)
+            continue;
         Block b;
-        long long in_off, out_off;
-    };
-    std::vector<Work> work;
-    size_t total = 0;
-    {
-        // Round robin: when a step fills up, the next one starts at the first
-        // stream that did not fit, so no stream waits more than a few steps.
-        std::lock_guard<std::mutex> lk(srv->mu_queue);
-        bool capped = false;
-        auto take = [&](SStream *s) {
-            if (s->pending.empty())
-                return;
-            Block &b = s->pending.front();
-            if (total + b.x.size() > srv->max_step_samples) {
+        b.src = s->src + s->src_next * s->block;
+        b.n = std::min(s->block, s->src_n - s->src_next * s->block);
+        b.t_submit = s->src_ready(s->src_next);
+        b.tail = false;
+        s->pending.push_back(std::move(b));
+        srv->npending++;
+        s->src_next++;
+        if (s->src_next * s->block < s->src_n)
+            srv->src_heap.push({s->src_ready(s->src_next), id});
+        else
+            s->ended = true;  // the source is exhausted: input is over
+    }
+    return srv->src_heap.empty() ? 1e300 : srv->src_heap.top().first;
+}
+
+// Takes the queued blocks of every stream (up to kMerge consecutive blocks of
+// a stream as one item) into step buffer b. Round robin: when a step is full,
+// the next one starts at the first stream that did not fit. Caller holds
+// mu_state. Returns the number of blocks taken.
+size_t collect(tc_server *srv, tc_server::StepBuf &b)
+{
+    b.items.clear();
+    b.total = 0;
+    size_t nblocks = 0;
+    std::lock_guard<std::mutex> lk(srv->mu_queue);
+    b.t_begin = now_s();
+    release_sources(srv, b.t_begin);
+    if (srv->npending == 0)
+        return 0;
+    bool capped = false;
+    auto take = [&](SStream *s) {
+        if (s->pending.empty())
+            return;
+        tc_server::Item it{s, {}, (long long)b.total, 0};
+        while (!s->pending.empty() && (int)it.blocks.size() < kMerge) {
+            Block &blk = s->pending.front();
+            if (b.total + (size_t)blk.n > srv->max_step_samples) {
                 if (!capped)
                     srv->rr = s->id;
                 capped = true;
-                return;  // stays for the next step
+                break;  // stays for the next step
             }
-            work.push_back({s, std::move(b), (long long)total, (long long)total});
+            b.total += (size_t)blk.n;
+            it.n += blk.n;
+            it.blocks.push_back(std::move(blk));
             s->pending.pop_front();
-            total += work.back().b.x.size();
-        };
-        const auto start = srv->streams.lower_bound(srv->rr);
-        for (auto it = start; it != srv->streams.end(); ++it)
-            take(it->second.get());
-        for (auto it = srv->streams.begin(); it != start; ++it)
-            take(it->second.get());
-        if (!capped)
-            srv->rr = 0;
-    }
-    if (work.empty())
-        return TC_OK;
-    const double t_start = now_s();
+            srv->npending--;
+        }
+        if (!it.blocks.empty()) {
+            nblocks += it.blocks.size();
+            s->inflight++;
+            b.items.push_back(std::move(it));
+        }
+    };
+    const auto start = srv->streams.lower_bound(srv->rr);
+    for (auto it = start; it != srv->streams.end(); ++it)
+        take(it->second.get());
+    for (auto it = srv->streams.begin(); it != start; ++it)
+        take(it->second.get());
+    if (!capped)
+        srv->rr = 0;
+    return nblocks;
+}
 
-    // Plan: one chunk variant for the whole list -- the largest chunk that
-    // still gives the GPU about four waves of CTAs with < 10 % padded taps,
-    // else the smallest (short IRs, small batches: latency first).
+// Packs step buffer b and enqueues its copies and kernels on the step stream
+// (no wait). Caller holds mu_state. Advances each stream's launch position.
+tc_status pack_launch(tc_server *srv, tc_server::StepBuf &b)
+{
+    // One chunk variant for the whole list: the largest chunk that still
+    // gives the GPU about four waves of CTAs with < 10 % padded taps, else the
+    // smallest (short IRs, small batches: latency first).
     int variant = tc::K1_P1;
     for (int v : {tc::K1_P13, tc::K1_P4}) {
         const long long kcv = tc::k1_chunk_taps(v);
         long long ctas = 0, taps = 0, padded = 0;
-        for (auto &w : work) {
-            const long long ntile = ((long long)w.b.x.size() + tc::K1_MO - 1) / tc::K1_MO;
+        for (auto &w : b.items) {
+            const long long ntile = (w.n + tc::K1_MO - 1) / tc::K1_MO;
             const long long nch = (w.s->L + 3 + kcv - 1) / kcv;
             ctas += ntile * nch;
             taps += ntile * w.s->L;
@@ -355,43 +553,47 @@ tc_status step_locked(tc_server *srv, size_t *nblocks)
     }
     const long long kc = tc::k1_chunk_taps(variant);
     size_t scratch = 0, ctrs = 0;
-    for (auto &w : work) {
-        const long long n = (long long)w.b.x.size();
-        const long long ntile = (n + tc::K1_MO - 1) / tc::K1_MO;
-        const long long nchunk = (w.s->L + 3 + kc - 1) / kc;
-        scratch += (size_t)(ntile * nchunk * tc::K1_MO);
+    for (auto &w : b.items) {
+        const long long ntile = (w.n + tc::K1_MO - 1) / tc::K1_MO;
+        scratch += (size_t)(ntile * ((w.s->L + 3 + kc - 1) / kc) * tc::K1_MO);
         ctrs += (size_t)ntile;
     }
-    S_TRY(grow(srv, work.size(), scratch, ctrs));
+    S_TRY(grow(srv, b, b.items.size(), scratch, ctrs));
 
-    // Input packing, history room, version tables.
-    const StageLayout lay = stage_layout(work.size(), total);
-    auto *st_items = reinterpret_cast<tc::K1Params *>(srv->pin_stage + lay.items);
-    auto *st_cta = reinterpret_cast<long long *>(srv->pin_stage + lay.cta);
-    auto *st_sc = reinterpret_cast<long long *>(srv->pin_stage + lay.sc);
-    auto *st_dst = reinterpret_cast<float **>(srv->pin_stage + lay.dst);
-    auto *st_in = reinterpret_cast<float *>(srv->pin_stage + lay.in);
+    const StageLayout lay = stage_layout(b.items.size(), b.total);
+    auto *st_items = reinterpret_cast<tc::K1Params *>(b.pin_stage + lay.items);
+    auto *st_cta = reinterpret_cast<long long *>(b.pin_stage + lay.cta);
+    auto *st_sc = reinterpret_cast<long long *>(b.pin_stage + lay.sc);
+    auto *st_dst = reinterpret_cast<float **>(b.pin_stage + lay.dst);
+    auto *st_in = reinterpret_cast<float *>(b.pin_stage + lay.in);
     float *const d_y = srv->d_out + 4;
     int *const d_err = reinterpret_cast<int *>(srv->d_out);
     size_t si = 0, ci = 0;
     long long cta = 0;
-    for (size_t i = 0; i < work.size(); ++i) {
-        Work &w = work[i];
+    for (size_t i = 0; i < b.items.size(); ++i) {
+        tc_server::Item &w = b.items[i];
         SStream *s = w.s;
-        const long long n = (long long)w.b.x.size();
-        std::memcpy(st_in + w.in_off, w.b.x.data(), (size_t)n * sizeof(float));
+        const long long n = w.n;
+        long long o = w.off;
+        for (auto &blk : w.blocks) {
+            std::memcpy(st_in + o, blk.data(), (size_t)blk.n * sizeof(float));
+            o += blk.n;
+        }
         retire(s);
-        if (s->pos + n + tc::K1_MO + 8 > s->base + s->cap) {
+        long long c_shift = 0, c_len = 0;
+        if (s->pos + n + tc::K1_MO + 8 + s->stagger > s->base + s->cap) {
+            // Compaction (done by the ingest kernel, ordered after the steps
+            // in flight, which read the old layout): keep `keep` samples
+            // behind the launch position.
             const long long nb = fl8(s->pos - s->keep);
-            const long long len = s->pos - nb, shift = nb - s->base;
-            if (shift < len || len + n + tc::K1_MO + 8 > s->cap)
+            c_len = s->pos - nb;
+            c_shift = nb - s->base;
+            if (c_shift < c_len || c_len + n + tc::K1_MO + 8 > s->cap)
                 return sfail(TC_EINVAL, "tc_server: internal: history compaction would overlap");
-            S_CU(cudaMemcpyAsync(s->hist, s->hist + shift, (size_t)len * sizeof(float), cudaMemcpyDeviceToDevice,
-                                 srv->cs));
             s->base = nb;
         }
         if (s->vt_dirty) {
-            DevTable &t = srv->pin_tables[i];
+            DevTable &t = b.pin_tables[i];
             std::memset(&t, 0, sizeof t);
             t.nver = (int)s->vt.size();
             for (size_t v = 0; v < s->vt.size(); ++v) {
@@ -401,9 +603,11 @@ tc_status step_locked(tc_server *srv, size_t *nblocks)
             S_CU(cudaMemcpyAsync(s->d_vt, &t, sizeof t, cudaMemcpyHostToDevice, srv->cs));
             s->vt_dirty = false;
         }
-        st_sc[3 * i] = w.in_off;
-        st_sc[3 * i + 1] = n;
-        st_sc[3 * i + 2] = s->pos - s->base;
+        st_sc[5 * i] = w.off;
+        st_sc[5 * i + 1] = n;
+        st_sc[5 * i + 2] = s->pos - s->base;
+        st_sc[5 * i + 3] = c_shift;
+        st_sc[5 * i + 4] = c_len;
         st_dst[i] = s->hist;
 
         tc::K1Params p{};
@@ -429,7 +633,7 @@ tc_status step_locked(tc_server *srv, size_t *nblocks)
         p.ntile = (int)((n + tc::K1_MO - 1) / tc::K1_MO);
         p.e = tc::k1_shift_e(s->pos, s->base);
         p.nchunk = (int)((s->L + p.e + kc - 1) / kc);
-        p.y = d_y + w.out_off;
+        p.y = d_y + w.off;
         p.y_pitch = n;
         p.partial = srv->scratch + si;
         p.counter = srv->counters + ci;
@@ -439,78 +643,155 @@ tc_status step_locked(tc_server *srv, size_t *nblocks)
         st_items[i] = p;
         st_cta[i] = cta;
         cta += (long long)p.ntile * p.nchunk;
+        s->pos += n;
     }
-    st_cta[work.size()] = cta;
-    const int ni = (int)work.size();
+    st_cta[b.items.size()] = cta;
+    const int ni = (int)b.items.size();
     char *const ds = srv->d_stage;
-    S_CU(cudaMemcpyAsync(ds, srv->pin_stage, lay.end, cudaMemcpyHostToDevice, srv->cs));
-    scatter_kernel<<<(unsigned)ni, 128, 0, srv->cs>>>(reinterpret_cast<const float *>(ds + lay.in),
+    b.t_launch = now_s();
+    b.ctas = cta;
+    b.variant = variant;
+    S_CU(cudaMemcpyAsync(ds, b.pin_stage, lay.end, cudaMemcpyHostToDevice, srv->cs));
+    ingest_kernel<<<(unsigned)ni, 256, 0, srv->cs>>>(reinterpret_cast<const float *>(ds + lay.in),
                                                        reinterpret_cast<const long long *>(ds + lay.sc),
                                                        reinterpret_cast<float *const *>(ds + lay.dst), ni);
     tc::count_launch();
     S_CU(cudaGetLastError());
     S_CU(tc::k1_launch_list(reinterpret_cast<const tc::K1Params *>(ds + lay.items),
                             reinterpret_cast<const long long *>(ds + lay.cta), ni, cta, variant, srv->cs));
-    S_CU(cudaMemcpyAsync(srv->pin_out, srv->d_out, (4 + total) * sizeof(float), cudaMemcpyDeviceToHost, srv->cs));
-    S_CU(cudaStreamSynchronize(srv->cs));
-    if (*reinterpret_cast<int *>(srv->pin_out)) {
-        cudaMemsetAsync(srv->d_out, 0, sizeof(int), srv->cs);
-        cudaMemsetAsync(srv->counters, 0, srv->counters_n * sizeof(unsigned), srv->cs);
-        cudaStreamSynchronize(srv->cs);
-        return sfail(TC_ETIMEOUT, "tc_server: a kernel's bounded wait gave up");
-    }
-    const double t_done = now_s();
-    {
-        std::lock_guard<std::mutex> lk(srv->mu_queue);
-        for (auto &w : work) {
-            const long long n = (long long)w.b.x.size();
-            const float *yo = srv->pin_out + 4 + w.out_off;
-            if (w.b.tail) {
-                w.s->tail_out.insert(w.s->tail_out.end(), yo, yo + n);
-            } else if (w.s->discard) {
-                srv->lat.push_back(t_done - w.b.t_submit);
-            } else {
-                srv->lat.push_back(t_done - w.b.t_submit);
-                OutBlock o;
-                o.y.assign(yo, yo + n);
-                o.t_submit = w.b.t_submit;
-                o.t_done = t_done;
-                w.s->done.push_back(std::move(o));
-            }
-            w.s->pos += n;
-        }
-    }
-    srv->steps++;
-    srv->blocks += work.size();
-    srv->busy_s += t_done - t_start;
-    *nblocks = work.size();
+    S_CU(cudaMemcpyAsync(b.pin_out, srv->d_out, (4 + b.total) * sizeof(float), cudaMemcpyDeviceToHost, srv->cs));
+    S_CU(cudaEventRecord(b.done, srv->cs));
     return TC_OK;
 }
 
-bool any_pending(tc_server *srv)
+// Waits for step buffer b (no lock held while waiting), then delivers its
+// outputs: finished blocks, latencies, flush tails, positions, stats.
+tc_status complete(tc_server *srv, tc_server::StepBuf &b)
 {
-    for (auto &kv : srv->streams)
-        if (!kv.second->pending.empty())
-            return true;
-    return false;
+    S_CU(cudaEventSynchronize(b.done));
+    const double t_done = now_s();
+    std::lock_guard<std::mutex> lk(srv->mu_state);
+    if (*reinterpret_cast<int *>(b.pin_out)) {
+        cudaMemsetAsync(srv->d_out, 0, sizeof(int), srv->cs);
+        cudaMemsetAsync(srv->counters, 0, srv->counters_n * sizeof(unsigned), srv->cs);
+        cudaStreamSynchronize(srv->cs);
+        std::lock_guard<std::mutex> lq(srv->mu_queue);
+        for (auto &w : b.items)
+            w.s->inflight--;
+        b.items.clear();
+        return sfail(TC_ETIMEOUT, "tc_server: a kernel's bounded wait gave up");
+    }
+    std::lock_guard<std::mutex> lq(srv->mu_queue);
+    size_t nblocks = 0;
+    for (auto &w : b.items) {
+        SStream *s = w.s;
+        const float *yo = b.pin_out + 4 + w.off;
+        for (auto &blk : w.blocks) {
+            if (blk.tail) {
+                s->tail_out.insert(s->tail_out.end(), yo, yo + blk.n);
+            } else {
+                srv->lat.push_back(t_done - blk.t_submit);
+                srv->lat_block.push_back((uint32_t)s->block);
+                srv->tap_macs += (double)blk.n * (double)s->L;
+                if (!s->discard) {
+                    OutBlock o;
+                    o.y.assign(yo, yo + blk.n);
+                    o.t_submit = blk.t_submit;
+                    o.t_done = t_done;
+                    s->done.push_back(std::move(o));
+                }
+            }
+            yo += blk.n;
+            ++nblocks;
+        }
+        s->pos_done += w.n;
+        s->inflight--;
+    }
+    tc_server_step_rec rec{b.t_begin, b.t_launch, t_done, (uint32_t)nblocks, (uint32_t)b.total, (uint32_t)b.ctas,
+                           (uint32_t)b.variant};
+    if (srv->steplog.size() < kLogSteps)
+        srv->steplog.push_back(rec);
+    else
+        srv->steplog[srv->steplog_next] = rec;
+    srv->steplog_next = (srv->steplog_next + 1) % kLogSteps;
+    srv->steps++;
+    srv->blocks += nblocks;
+    srv->busy_s += t_done - std::max(b.t_begin, srv->last_done);
+    srv->last_done = t_done;
+    b.items.clear();
+    return TC_OK;
+}
+
+// One step on the calling thread: collect, launch, wait, deliver.
+tc_status step_sync(tc_server *srv, size_t *nblocks)
+{
+    tc_server::StepBuf &b = srv->buf[0];
+    {
+        std::lock_guard<std::mutex> lk(srv->mu_state);
+        *nblocks = collect(srv, b);
+        if (*nblocks == 0)
+            return TC_OK;
+        tc_status st = pack_launch(srv, b);
+        if (st != TC_OK)
+            return st;
+    }
+    return complete(srv, b);
 }
 
 void worker_main(tc_server *srv)
 {
     cudaSetDevice(srv->device);
-    while (!srv->stop.load()) {
-        {
-            std::unique_lock<std::mutex> lk(srv->mu_queue);
-            srv->cv.wait_for(lk, std::chrono::microseconds(200), [&] { return srv->stop.load() || any_pending(srv); });
+    int inflight = -1;  // step buffer launched and not yet delivered
+    auto fail = [&](const char *) { srv->worker_error = tc_last_error(); };
+    while (true) {
+        const bool stopping = srv->stop.load();
+        const int nb = inflight < 0 ? 0 : 1 - inflight;
+        bool launched = false;
+        if (!stopping) {
+            std::lock_guard<std::mutex> lk(srv->mu_state);
+            if (collect(srv, srv->buf[nb]) > 0) {
+                if (pack_launch(srv, srv->buf[nb]) != TC_OK) {
+                    fail("launch");
+                    break;
+                }
+                launched = true;
+            }
         }
-        if (srv->stop.load())
-            break;
-        std::lock_guard<std::mutex> lk(srv->mu_state);
-        size_t n = 0;
-        if (step_locked(srv, &n) != TC_OK) {
-            srv->worker_error = tc_last_error();
+        if (inflight >= 0 && complete(srv, srv->buf[inflight]) != TC_OK) {
+            fail("complete");
+            inflight = launched ? nb : -1;
             break;
         }
+        inflight = launched ? nb : -1;
+        if (inflight >= 0)
+            continue;  // keep the GPU fed: collect the next step at once
+        if (stopping)
+            break;
+        // Idle: sleep until the next source block is due (waking ~60 us
+        // early, then yielding) or a submit arrives.
+        std::unique_lock<std::mutex> lq(srv->mu_queue);
+        const double now = now_s();
+        const double next = release_sources(srv, now);
+        if (srv->npending > 0)
+            continue;
+        const double wake = std::min(next, now + 1e-3);
+        if (wake - now > 80e-6) {
+            const auto until = std::chrono::steady_clock::time_point(
+                std::chrono::duration_cast<std::chrono::steady_clock::duration>(
+                    std::chrono::duration<double>(wake - 60e-6)));
+            srv->cv.wait_until(lq, until, [&] { return srv->stop.load() || srv->npending > 0; });
+        } else {
+            lq.unlock();
+            std::this_thread::yield();
+        }
+    }
+    if (inflight >= 0) {
+        // Error path: the other step may still be on the GPU.
+        cudaStreamSynchronize(srv->cs);
+        std::lock_guard<std::mutex> lq(srv->mu_queue);
+        for (auto &w : srv->buf[inflight].items)
+            w.s->inflight--;
+        srv->buf[inflight].items.clear();
     }
 }
 
@@ -539,9 +820,31 @@ tc_status tc_server_open(size_t mem_budget_bytes, size_t max_step_samples, tc_se
     S_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, srv->device));
     srv->k1_slots = 3LL * sms;
     S_CU(cudaStreamCreateWithFlags(&srv->cs, cudaStreamNonBlocking));
-    S_CU(cudaHostAlloc(&srv->pin_out, (4 + max_step_samples) * sizeof(float), cudaHostAllocDefault));
+    S_CU(cudaStreamCreateWithFlags(&srv->admin, cudaStreamNonBlocking));
+    // Streams' memory comes from a pool of this server that keeps freed
+    // memory for reuse (no driver mapping work while serving).
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = srv->device;
+    S_CU(cudaMemPoolCreate(&srv->pool, &props));
+    uint64_t keep_all = ~0ull;
+    S_CU(cudaMemPoolSetAttribute(srv->pool, cudaMemPoolAttrReleaseThreshold, &keep_all));
+    for (auto &b : srv->buf) {
+        S_CU(cudaHostAlloc(&b.pin_out, (4 + max_step_samples) * sizeof(float), cudaHostAllocDefault));
+        S_CU(cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming));
+    }
     S_CU(cudaMalloc(&srv->d_out, (4 + max_step_samples) * sizeof(float)));
     S_CU(cudaMemset(srv->d_out, 0, 4 * sizeof(float)));
+    // Size the step buffers for a few thousand streams and load the kernels
+    // now, so that the first steps do not pay for allocations or module loads.
+    for (auto &b : srv->buf)
+        S_TRY(grow(srv.get(), b, 4096, (size_t)4096 * 19 * tc::K1_MO, 16384));
+    cudaFuncAttributes fa;
+    S_CU(cudaFuncGetAttributes(&fa, ingest_kernel));
+    tc::K1Plan plan{};
+    S_CU(tc::k1_plan(1000, 0, 1, 1, 1, -1, &plan));
+    srv->steplog.reserve(kLogSteps);
     *out = srv.release();
     return TC_OK;
 }
@@ -552,18 +855,29 @@ tc_status tc_server_close(tc_server *srv)
         return TC_OK;
     tc_server_stop(srv);
     cudaSetDevice(srv->device);
-    if (srv->cs)
+    if (srv->cs) {
+        for (auto &kv : srv->streams)
+            free_stream(srv, kv.second.get());
         cudaStreamSynchronize(srv->cs);
-    for (auto &kv : srv->streams)
-        free_stream(kv.second.get());
-    cudaFreeHost(srv->pin_stage);
+    }
+    if (srv->admin)
+        cudaStreamSynchronize(srv->admin);
+    for (auto &b : srv->buf) {
+        cudaFreeHost(b.pin_stage);
+        cudaFreeHost(b.pin_out);
+        cudaFreeHost(b.pin_tables);
+        if (b.done)
+            cudaEventDestroy(b.done);
+    }
     cudaFree(srv->d_stage);
-    cudaFreeHost(srv->pin_out);
     cudaFree(srv->d_out);
-    cudaFreeHost(srv->pin_tables);
     cudaFree(srv->scratch);
     cudaFree(srv->counters);
     cudaFree(srv->ir_stage);
+    if (srv->pool)
+        cudaMemPoolDestroy(srv->pool);
+    if (srv->admin)
+        cudaStreamDestroy(srv->admin);
     if (srv->cs)
         cudaStreamDestroy(srv->cs);
     delete srv;
@@ -578,43 +892,58 @@ tc_status tc_server_add(tc_server *srv, size_t L, size_t block, const float *h, 
         return sfail(TC_EINVAL, "tc_server_add: block larger than one step");
     if (L > kMaxL)
         return sfail(TC_EINVAL, "tc_server_add: L too long for one K1 tile's chunk stack");
-    std::lock_guard<std::mutex> lk(srv->mu_state);
-    S_CU(cudaSetDevice(srv->device));
-    auto s = std::make_unique<SStream>();
     if (flags & ~TC_SERVER_DISCARD_OUTPUT)
         return sfail(TC_EINVAL, "tc_server_add: unknown flag");
+    auto s = std::make_unique<SStream>();
     s->L = (long long)L;
     s->block = (long long)block;
     s->discard = (flags & TC_SERVER_DISCARD_OUTPUT) != 0;
     s->bytes = stream_bytes(s->L, s->block, s->nslots, &s->keep, &s->cap, &s->Lpad);
-    if (srv->used + s->bytes > srv->budget) {
-        srv->rejected++;
-        return sfail(TC_ENOMEM, "tc_server_add: the stream does not fit the device memory budget now");
+    {
+        std::lock_guard<std::mutex> lk(srv->mu_state);
+        if (srv->used + s->bytes > srv->budget) {
+            srv->rejected++;
+            return sfail(TC_ENOMEM, "tc_server_add: the stream does not fit the device memory budget now");
+        }
+        srv->used += s->bytes;  // reserved
     }
-    cudaError_t e = cudaMalloc(&s->hist, (size_t)s->cap * sizeof(float));
+    // Device state is built on the admin stream while steps keep running.
+    std::lock_guard<std::mutex> la(srv->mu_admin);
+    S_CU(cudaSetDevice(srv->device));
+    auto unreserve = [&](tc_status st, const std::string &m) {
+        cudaStreamSynchronize(srv->admin);  // allocations complete before the ordered frees
+        free_stream(srv, s.get());
+        std::lock_guard<std::mutex> lk(srv->mu_state);
+        srv->used -= s->bytes;
+        if (st == TC_ENOMEM)
+            srv->rejected++;
+        return sfail(st, m);
+    };
+    cudaError_t e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&s->hist), (size_t)s->cap * sizeof(float),
+                                            srv->pool, srv->admin);
     if (e == cudaSuccess)
-        e = cudaMalloc(&s->ir, (size_t)s->nslots * 4 * (size_t)s->Lpad * sizeof(float));
+        e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&s->ir),
+                                    (size_t)s->nslots * 4 * (size_t)s->Lpad * sizeof(float), srv->pool, srv->admin);
     if (e == cudaSuccess)
-        e = cudaMalloc(&s->d_vt, sizeof(DevTable));
+        e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&s->d_vt), sizeof(DevTable), srv->pool, srv->admin);
     if (e == cudaSuccess)
-        e = cudaMemsetAsync(s->hist, 0, (size_t)s->cap * sizeof(float), srv->cs);
-    if (e != cudaSuccess) {
-        free_stream(s.get());
-        srv->rejected++;
-        return sfail(e == cudaErrorMemoryAllocation ? TC_ENOMEM : TC_ECUDA,
-                     std::string("tc_server_add: ") + cudaGetErrorString(e));
-    }
+        e = cudaMemsetAsync(s->hist, 0, (size_t)s->cap * sizeof(float), srv->admin);
+    if (e != cudaSuccess)
+        return unreserve(e == cudaErrorMemoryAllocation ? TC_ENOMEM : TC_ECUDA,
+                         std::string("tc_server_add: ") + cudaGetErrorString(e));
     s->base = -s->keep;
     s->slot_used.assign((size_t)s->nslots, 0);
-    tc_status st = set_ir(srv, s.get(), h, n, 0);
-    if (st != TC_OK) {
-        free_stream(s.get());
-        return st;
-    }
-    s->id = srv->next_id++;
-    srv->used += s->bytes;
-    *id = s->id;
+    s->slot_used[0] = 1;
+    tc_status st = upload_ir(srv, s.get(), 0, h, n);
+    if (st != TC_OK)
+        return unreserve(st, tc_last_error());
+    s->vt.push_back({0, 0});
+    s->vt_dirty = true;
+    std::lock_guard<std::mutex> lk(srv->mu_state);
     std::lock_guard<std::mutex> lq(srv->mu_queue);
+    s->id = srv->next_id++;
+    s->stagger = (long long)((s->id * 0x9E3779B97F4A7C15ull) >> 33) % std::max<long long>(1, s->keep / 2);
+    *id = s->id;
     srv->streams[s->id] = std::move(s);
     return TC_OK;
 }
@@ -623,21 +952,9 @@ tc_status tc_server_set_ir_at(tc_server *srv, uint64_t id, const float *h, size_
 {
     if (!srv)
         return sfail(TC_EINVAL, "tc_server_set_ir_at: server is NULL");
-    std::lock_guard<std::mutex> lk(srv->mu_state);
-    SStream *s = find(srv, id);
-    if (!s)
-        return sfail(TC_EINVAL, "tc_server_set_ir_at: unknown stream");
-    // Blocks already submitted but not yet run come before the switch point.
-    long long queued = 0;
-    {
-        std::lock_guard<std::mutex> lq(srv->mu_queue);
-        for (auto &b : s->pending)
-            queued += (long long)b.x.size();
-    }
-    if ((long long)sample < s->pos + queued)
-        return sfail(TC_EINVAL, "tc_server_set_ir_at: the switch sample was already submitted");
+    std::lock_guard<std::mutex> la(srv->mu_admin);
     S_CU(cudaSetDevice(srv->device));
-    return set_ir(srv, s, h, n, (long long)sample);
+    return set_ir(srv, id, h, n, (long long)sample);
 }
 
 tc_status tc_server_submit(tc_server *srv, uint64_t id, const float *x, size_t n)
@@ -654,43 +971,86 @@ tc_status tc_server_submit_many(tc_server *srv, size_t count, const uint64_t *id
     const double now = now_s();
     std::lock_guard<std::mutex> lq(srv->mu_queue);
     // Validate everything first: all or nothing.
+    std::vector<SStream *> ss(count);
+    std::unordered_set<uint64_t> ended_here;
     for (size_t i = 0; i < count; ++i) {
         auto it = srv->streams.find(ids[i]);
         if (it == srv->streams.end())
             return sfail(TC_EINVAL, "tc_server_submit: unknown stream");
-        const SStream *s = it->second.get();
+        SStream *s = it->second.get();
         if (!xs[i] || ns[i] == 0 || (long long)ns[i] > s->block)
             return sfail(TC_EINVAL, "tc_server_submit: x is NULL or n not in [1, block]");
-        if (s->ended || s->flushed)
+        if (s->ended || s->flushed || ended_here.count(ids[i]))
             return sfail(TC_ESTATE, "tc_server_submit: the stream's input has ended");
-        for (size_t j = 0; j < i; ++j)
-            if (ids[j] == ids[i] && (long long)ns[j] < s->block)
-                return sfail(TC_ESTATE, "tc_server_submit: block after the stream's last (short) block");
+        if (s->src)
+            return sfail(TC_ESTATE, "tc_server_submit: the stream reads a live source");
+        if ((long long)ns[i] < s->block)
+            ended_here.insert(ids[i]);
+        ss[i] = s;
     }
     for (size_t i = 0; i < count; ++i) {
-        SStream *s = srv->streams[ids[i]].get();
+        SStream *s = ss[i];
         if ((long long)ns[i] < s->block)
             s->ended = true;  // a short block is the last one
         Block b;
-        b.x.assign(xs[i], xs[i] + ns[i]);
+        b.own.assign(xs[i], xs[i] + ns[i]);
+        b.src = nullptr;
+        b.n = (long long)ns[i];
         b.t_submit = t_ready ? t_ready[i] : now;
         b.tail = false;
         s->pending.push_back(std::move(b));
+        srv->npending++;
     }
     srv->cv.notify_one();
     return TC_OK;
 }
 
-tc_status tc_server_latencies(tc_server *srv, double *out, size_t cap, size_t *n_out)
+tc_status tc_server_latencies(tc_server *srv, double *out, uint32_t *block, size_t cap, size_t *n_out)
 {
     if (!srv || !n_out || (cap && !out))
         return sfail(TC_EINVAL, "tc_server_latencies: bad arguments");
     std::lock_guard<std::mutex> lq(srv->mu_queue);
     const size_t n = std::min(cap, srv->lat.size());
-    if (n)
-        std::memcpy(out, srv->lat.data(), n * sizeof(double));
+    std::copy(srv->lat.begin(), srv->lat.begin() + (long)n, out);
+    if (block)
+        std::copy(srv->lat_block.begin(), srv->lat_block.begin() + (long)n, block);
     srv->lat.erase(srv->lat.begin(), srv->lat.begin() + (long)n);
+    srv->lat_block.erase(srv->lat_block.begin(), srv->lat_block.begin() + (long)n);
     *n_out = n;
+    return TC_OK;
+}
+
+tc_status tc_server_attach_source(tc_server *srv, uint64_t id, const float *x, size_t n, double t0, double fs)
+{
+    if (!srv || !x || n == 0 || !(fs > 0.0))
+        return sfail(TC_EINVAL, "tc_server_attach_source: bad arguments");
+    std::lock_guard<std::mutex> lq(srv->mu_queue);
+    auto it = srv->streams.find(id);
+    if (it == srv->streams.end())
+        return sfail(TC_EINVAL, "tc_server_attach_source: unknown stream");
+    SStream *s = it->second.get();
+    if (s->src || s->ended || s->flushed || !s->pending.empty())
+        return sfail(TC_ESTATE, "tc_server_attach_source: the stream has a source, queued blocks or ended input");
+    s->src = x;
+    s->src_n = (long long)n;
+    s->src_next = 0;
+    s->src_t0 = t0;
+    s->src_fs = fs;
+    srv->src_heap.push({s->src_ready(0), id});
+    srv->cv.notify_one();
+    return TC_OK;
+}
+
+tc_status tc_server_stream_state(tc_server *srv, uint64_t id, int *state)
+{
+    if (!srv || !state)
+        return sfail(TC_EINVAL, "tc_server_stream_state: bad arguments");
+    std::lock_guard<std::mutex> lq(srv->mu_queue);
+    auto it = srv->streams.find(id);
+    if (it == srv->streams.end())
+        return sfail(TC_EINVAL, "tc_server_stream_state: unknown stream");
+    const SStream *s = it->second.get();
+    *state = !s->ended ? 0 : (s->pending.empty() && s->inflight == 0 ? 2 : 1);
     return TC_OK;
 }
 
@@ -700,10 +1060,9 @@ tc_status tc_server_step(tc_server *srv, size_t *blocks_done)
         return sfail(TC_EINVAL, "tc_server_step: server is NULL");
     if (srv->run.load())
         return sfail(TC_ESTATE, "tc_server_step: the worker thread is running");
-    std::lock_guard<std::mutex> lk(srv->mu_state);
     S_CU(cudaSetDevice(srv->device));
     size_t n = 0;
-    tc_status st = step_locked(srv, &n);
+    tc_status st = step_sync(srv, &n);
     if (blocks_done)
         *blocks_done = n;
     return st;
@@ -771,7 +1130,7 @@ tc_status tc_server_flush(tc_server *srv, uint64_t id, float *y, size_t cap, siz
         return sfail(TC_EINVAL, "tc_server_flush: bad arguments");
     if (srv->run.load())
         return sfail(TC_ESTATE, "tc_server_flush: stop the worker first");
-    std::lock_guard<std::mutex> lk(srv->mu_state);
+    std::unique_lock<std::mutex> lk(srv->mu_state);
     SStream *s = find(srv, id);
     if (!s)
         return sfail(TC_EINVAL, "tc_server_flush: unknown stream");
@@ -780,6 +1139,8 @@ tc_status tc_server_flush(tc_server *srv, uint64_t id, float *y, size_t cap, siz
         return sfail(TC_EINVAL, "tc_server_flush: cap < L - 1");
     if (s->flushed)
         return sfail(TC_ESTATE, "tc_server_flush: already flushed");
+    if (s->src && s->src_next * s->block < s->src_n)
+        return sfail(TC_ESTATE, "tc_server_flush: the stream's live source has not ended");
     S_CU(cudaSetDevice(srv->device));
     // The tail is the output of L - 1 zero samples (the accumulator drained,
     // Sec. 4.2): zero blocks of `block` samples run through ordinary steps
@@ -789,14 +1150,18 @@ tc_status tc_server_flush(tc_server *srv, uint64_t id, float *y, size_t cap, siz
         s->tail_out.clear();
         for (long long off = 0; off < tail; off += s->block) {
             Block b;
-            b.x.assign((size_t)std::min<long long>(s->block, tail - off), 0.f);
+            b.n = std::min<long long>(s->block, tail - off);
+            b.own.assign((size_t)b.n, 0.f);
+            b.src = nullptr;
             b.t_submit = now_s();
             b.tail = true;
             s->pending.push_back(std::move(b));
+            srv->npending++;
         }
         s->ended = true;
         s->flushed = true;
     }
+    lk.unlock();  // steps take the state lock themselves (the worker is stopped)
     for (;;) {
         {
             std::lock_guard<std::mutex> lq(srv->mu_queue);
@@ -804,10 +1169,11 @@ tc_status tc_server_flush(tc_server *srv, uint64_t id, float *y, size_t cap, siz
                 break;
         }
         size_t nb = 0;
-        S_TRY(step_locked(srv, &nb));
+        S_TRY(step_sync(srv, &nb));
         if (nb == 0)
             return sfail(TC_ESTATE, "tc_server_flush: internal: a step made no progress");
     }
+    lk.lock();
     if ((long long)s->tail_out.size() != tail)
         return sfail(TC_ESTATE, "tc_server_flush: internal: tail length");
     if (tail > 0)
@@ -830,14 +1196,13 @@ tc_status tc_server_remove(tc_server *srv, uint64_t id)
         auto it = srv->streams.find(id);
         if (it == srv->streams.end())
             return sfail(TC_EINVAL, "tc_server_remove: unknown stream");
-        if (!it->second->pending.empty())
-            return sfail(TC_ESTATE, "tc_server_remove: the stream still has blocks queued");
+        if (!it->second->pending.empty() || it->second->inflight > 0)
+            return sfail(TC_ESTATE, "tc_server_remove: the stream still has blocks queued or running");
         s = std::move(it->second);
         srv->streams.erase(it);
     }
     cudaSetDevice(srv->device);
-    cudaStreamSynchronize(srv->cs);
-    free_stream(s.get());
+    free_stream(srv, s.get());  // ordered after the steps on the step stream
     srv->used -= s->bytes;
     return TC_OK;
 }
@@ -854,9 +1219,26 @@ tc_status tc_server_get_stats(tc_server *srv, tc_server_stats *st)
     st->blocks = srv->blocks;
     st->rejected = srv->rejected;
     st->busy_s = srv->busy_s;
+    st->tap_macs = srv->tap_macs;
     return TC_OK;
 }
 
 double tc_server_clock(void) { return now_s(); }
+
+tc_status tc_server_step_log(tc_server *srv, tc_server_step_rec *out, size_t cap, size_t *n_out)
+{
+    if (!srv || !n_out || (cap && !out))
+        return sfail(TC_EINVAL, "tc_server_step_log: bad arguments");
+    std::lock_guard<std::mutex> lq(srv->mu_queue);
+    const size_t n = srv->steplog.size();
+    const size_t first = n < kLogSteps ? 0 : srv->steplog_next;
+    const size_t k = std::min(cap, n);
+    for (size_t i = 0; i < k; ++i)  // the newest k, oldest first
+        out[i] = srv->steplog[(first + (n - k) + i) % n];
+    srv->steplog.clear();
+    srv->steplog_next = 0;
+    *n_out = k;
+    return TC_OK;
+}
 
 }  // extern "C"

@@ -168,8 +168,9 @@ def test_worker_thread_continuous_batching():
                     outs[i].append(y[:n].copy())
         capi.tc_server_stop(srv)
         assert sum(map(len, outs)) == total
-        lat = capi.tc_server_latencies(srv)
+        lat, blk = capi.tc_server_latencies(srv)
         assert lat.size == total and np.all(lat >= 0)
+        assert set(blk.tolist()) <= {t.block for (t, x, H, vs) in streams}
         st = capi.tc_server_get_stats(srv)
         assert st.blocks == total and st.steps <= total
         for i, s in enumerate(streams):
@@ -252,5 +253,63 @@ def test_server_errors():
         ref = oracle.buffer(np.ones(74, np.float32), h[None], np.zeros(1, np.int64), 64)
         got = np.concatenate([first, y[:10], tail])
         assert rel_l2(got, ref) <= TOL["fp32"]
+    finally:
+        capi.tc_server_close(srv)
+
+
+def test_live_source_streams():
+    """Streams fed from live sources (tc_server_attach_source): paced at
+    48 kHz, one whose blocks are all due at once, and one that had blocks
+    submitted before its source; all match the oracle, each source block's
+    latency is recorded from its ready time, and the state goes 0 -> 2."""
+    streams = _small_trace(k=3, seed=21)
+    srv = capi.tc_server_open(4 << 30, 1 << 20)
+    try:
+        ids = [capi.tc_server_add(srv, t.L, t.block, H[0]) for (t, x, H, vs) in streams]
+        for i, (t, x, H, vs) in enumerate(streams):
+            if len(vs) > 1:
+                capi.tc_server_set_ir_at(srv, ids[i], H[1], vs[1])
+        assert capi.tc_server_stream_state(srv, ids[0]) == 0
+        # Stream 2: its first two blocks are submitted, the source continues.
+        t2, x2 = streams[2][0], streams[2][1]
+        head = 2 * t2.block
+        for b in range(2):
+            capi.tc_server_submit(srv, ids[2], x2[b * t2.block:(b + 1) * t2.block])
+        capi.tc_server_start(srv)
+        now = capi.tc_server_clock()
+        srcs = [np.ascontiguousarray(streams[0][1]), np.ascontiguousarray(streams[1][1]),
+                np.ascontiguousarray(x2[head:])]
+        # Wait until the two submitted blocks of stream 2 have run.
+        deadline = time.monotonic() + 10
+        while capi.tc_server_get_stats(srv).blocks < 2 and time.monotonic() < deadline:
+            time.sleep(0.001)
+        capi.tc_server_attach_source(srv, ids[0], srcs[0], now + 0.01)          # paced at 48 kHz
+        capi.tc_server_attach_source(srv, ids[1], srcs[1], now - 100.0)         # all due at once
+        capi.tc_server_attach_source(srv, ids[2], srcs[2], now, fs=480_000.0)  # 10x real time
+        with pytest.raises(capi.TcError) as ei:
+            capi.tc_server_submit(srv, ids[0], srcs[0][:8])
+        assert ei.value.code == "TC_ESTATE"
+        deadline = time.monotonic() + 30
+        while time.monotonic() < deadline and any(capi.tc_server_stream_state(srv, i) != 2 for i in ids):
+            time.sleep(0.005)
+        assert all(capi.tc_server_stream_state(srv, i) == 2 for i in ids)
+        capi.tc_server_stop(srv)
+        lat, blk = capi.tc_server_latencies(srv)
+        nblocks = sum(-(-t.n // t.block) for (t, x, H, vs) in streams)
+        assert lat.size == nblocks and np.all(lat >= 0)
+        for i, s in enumerate(streams):
+            t = s[0]
+            outs = []
+            y = np.empty(t.block, np.float32)
+            while True:
+                n, ts, td = capi.tc_server_poll(srv, ids[i], y)
+                if n == 0:
+                    break
+                assert td >= ts
+                outs.append(y[:n].copy())
+            tail = np.empty(max(t.L - 1, 1), np.float32)
+            n = capi.tc_server_flush(srv, ids[i], tail)
+            got = np.concatenate(outs + [tail[:n]])
+            assert rel_l2(got, _oracle(*s)) <= TOL["fp32"], i
     finally:
         capi.tc_server_close(srv)

@@ -280,12 +280,14 @@ def load_peaks() -> dict:
         return {}
 
 
-def bench_shared(torch, steps: int, warmup: int, P: int = 8192) -> dict:
+def bench_shared(torch, steps: int, warmup: int, P: int = 8192, C: int = 1024, N: int = 240_000,
+                 precisions=("bf16split", "bf16", "fp32")) -> dict:
     """Shared-IR workload: 1024 streams x 5 s at 48 kHz, one IR L = 96000 (tau 19200), block 256.
-    Each precision is one full pass per step (pushes of P samples, device pointers, then the flush)."""
+    Each precision is one full pass per step (pushes of P samples, device pointers, then the flush).
+    C and N shrink it for profiling captures."""
     from paper_2401_01607_gb300 import capi
     import oracle
-    C, N, L, B = 1024, 240_000, 96_000, 256
+    L, B = 96_000, 256
     w = synth.shared(C=C, N=N, L=L, block=B)
     npush = math.ceil(N / P)
     xp = np.zeros((npush, C, P), np.float32)
@@ -299,12 +301,14 @@ def bench_shared(torch, steps: int, warmup: int, P: int = 8192) -> dict:
     macs = C * N * L
     peaks = load_peaks()
     bf16_peak = float(peaks.get("bf16_tflops_sustained", 1690.8))
-    out = {"workload": "1024 streams x 240000 samples (5 s @ 48 kHz), one shared IR L=96000 tau=19200, "
-                       "block 256, pushes of %d" % P, "tap_macs": macs}
+    out = {"workload": "%d streams x %d samples (%.1f s @ 48 kHz), one shared IR L=96000 tau=19200, "
+                       "block 256, pushes of %d" % (C, N, N / FS, P), "tap_macs": macs}
     ts = torch.cuda.Stream()
     rng = np.random.default_rng(7)
     picks = [(int(rng.integers(C)), int(rng.integers(N + L - 1))) for _ in range(24)]
     for name, prec in (("bf16split", capi.TC_BF16_SPLIT), ("bf16", capi.TC_BF16), ("fp32", capi.TC_FP32)):
+        if name not in precisions:
+            continue
         s = capi.tc_open_group(C, L, B, True, prec, P)
         capi.tc_set_cuda_stream(s, ts)
 
@@ -705,6 +709,9 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving section")
     ap.add_argument("--only-serving", action="store_true", help="run only the serving section")
     ap.add_argument("--trace-seconds", type=float, default=15.0)
+    ap.add_argument("--shared-C", type=int, default=1024, help="shared-IR section: streams")
+    ap.add_argument("--shared-N", type=int, default=240_000, help="shared-IR section: samples per stream")
+    ap.add_argument("--shared-prec", default="bf16split,bf16,fp32", help="shared-IR section: precisions")
     ap.add_argument("--cpu-samples", type=int, default=30_000)
     ap.add_argument("--ref-samples", type=int, default=6_000)
     args = ap.parse_args()
@@ -730,7 +737,9 @@ def main():
     dev = torch.cuda.current_device()
 
     if args.only_shared:
-        print(json.dumps({"shared_ir": bench_shared(torch, max(1, args.steps), max(1, args.warmup))}), flush=True)
+        print(json.dumps({"shared_ir": bench_shared(torch, max(1, args.steps), max(1, args.warmup), C=args.shared_C,
+                                                    N=args.shared_N, precisions=args.shared_prec.split(","))}),
+              flush=True)
         dist.close()
         return
     if args.only_serving:

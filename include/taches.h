@@ -352,7 +352,7 @@ typedef struct tc_server_step_rec {
     uint32_t blocks;     /* blocks in the step */
     uint32_t samples;    /* input samples in the step */
     uint32_t ctas;       /* CTAs of the gather launch */
-    uint32_t variant;    /* tap chunk of the gather: 0 = 640, 1 = 2560, 2 = 8320 taps */
+    uint32_t variant;    /* tap chunk of the gather: 0 = 640, 1 = 2560, 2 = 7040 taps */
 } tc_server_step_rec;
 /* Moves the newest min(cap, logged) records (oldest first) into out and
  * clears the log. */
@@ -375,10 +375,10 @@ uint64_t tc_kernel_launches(void);
 
 /* Tuning knobs (autotuner and experiments); value -1 restores the default.
  *   TC_TUNE_K1_CHUNK     tap chunk of the FP32 gather: 0 = 640, 1 = 2560,
- *                        2 = 8320 taps per CTA (default: picked per launch)
+ *                        2 = 7040 taps per CTA (default: picked per launch)
  *   TC_TUNE_K2_RANGE     K blocks (of 32 samples) accumulated serially on the
  *                        tensor cores before the pairwise reduction of
- *                        ranges (default 48 for the BF16 split, 4096 for
+ *                        ranges (default 16 for the BF16 split, 4096 for
  *                        BF16; 1..4096)
  * Errors: TC_EINVAL for an unknown knob or value out of range. */
 typedef enum tc_tune_knob { TC_TUNE_K1_CHUNK = 0, TC_TUNE_K2_RANGE = 1 } tc_tune_knob;

@@ -616,10 +616,13 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
     p.x_col0 = w0 - s->base;
     p.nkb = (int)nkb;
     const long long tiles = (long long)p.ntile_c * p.ntile_o;
-    // TMEM runs of `range` K blocks (the BF16 split keeps ~48 for <= 1e-5;
-    // plain BF16 is limited by its operands, not by the run). K parts per tile:
-    // the fewest that fill the GPU's waves to >= 90 %.
-    p.range = (int)(s->k2_range > 0 ? s->k2_range : (s->prec == TC_BF16_SPLIT ? 48 : 4096));
+    // TMEM runs of `range` K blocks before each drain into FP32 registers.
+    // The BF16 split's error grows with the run (measured at L = 96000:
+    // 4.4e-6 at 16, 6.2e-6 at 48, 7.4e-6 at 64 relative L2), and draining
+    // every 16 blocks is hidden behind the MMAs of the other TMEM buffer.
+    // Plain BF16 is limited by its operands, not by the run. K parts per
+    // tile: the fewest that fill the GPU's waves to >= 90 %.
+    p.range = (int)(s->k2_range > 0 ? s->k2_range : (s->prec == TC_BF16_SPLIT ? 16 : 4096));
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
     long long nsplit = 1;

@@ -41,6 +41,13 @@ namespace tc {
 
 namespace {
 
+// Floor division by a positive divisor.
+__device__ __forceinline__ long long floor_div(long long x, long long d)
+{
+    const long long q = x / d;
+    return (x % d < 0) ? q - 1 : q;
+}
+
 template <int P>
 struct K1Cfg {
     static constexpr int MO = K1_MO;          // outputs per tile
@@ -98,7 +105,7 @@ __device__ __forceinline__ void k1_pass(const float *__restrict__ xp, const floa
 // parameters are copied to shared memory, then the CTA runs as in a uniform
 // launch over that item alone.
 template <int P, bool LIST>
-__global__ void __launch_bounds__(K1_THREADS, 3)
+__global__ void __launch_bounds__(K1_THREADS, 4)
     k1_gather(const K1Params p0, const K1Params *__restrict__ items, const long long *__restrict__ cta_begin,
               int nlist)
 {
@@ -216,19 +223,23 @@ __global__ void __launch_bounds__(K1_THREADS, 3)
                 xs[i] = 0.f;
             __syncthreads();
         }
+        // Passes this thread runs for this version: pass p covers sub-segment
+        // seg = 32 p + s, i.e. taps kc0 + 20 seg + [0, 19], and reads samples
+        // out_hi - kc0 - 20 seg - [0, 34]. It is needed iff
+        //   that range meets [a, b):  20 seg <= out_hi - kc0 - a  and
+        //                             20 seg >  out_hi - kc0 - 34 - b,
+        //   and its first tap is inside the IR: kc0 + 20 seg <= L - 1.
+        // Those bounds are solved once here instead of tested per pass.
+        const long long seg_hi = min(floor_div(out_hi - kc0 - a, C::SEG), floor_div((long long)p.L - 1 - kc0, C::SEG));
+        const long long seg_lo =
+            (b == LLONG_MAX) ? -(1LL << 40) : floor_div(out_hi - kc0 - (15 + C::SEG - 1) - b, C::SEG) + 1;
+        const int p_lo = (int)max(0LL, min((long long)P, -floor_div(s - seg_lo, 32)));
+        const int p_hi = (int)max(-1LL, min((long long)P - 1, floor_div(seg_hi - s, 32)));
+        int ia = g * 16 - (p_lo * 32 + s) * C::SEG + C::KC - 4;
+        const float *hp = hs + (p_lo * 32 + s) * C::SEG;
 #pragma unroll 1
-        for (int pass = 0; pass < P; ++pass) {
-            const int seg = pass * 32 + s;
-            // Samples read by this pass: outputs - (kc0 + 20 seg + [0, 19]).
-            const long long th_hi = out_hi - (kc0 + (long long)seg * C::SEG);
-            const long long th_lo = th_hi - 15 - (C::SEG - 1);
-            if (th_hi < a || th_lo >= b)
-                continue;  // no tache of this version reaches these outputs here
-            if (kc0 + seg * C::SEG >= p.L)
-                continue;  // taps past the end of the IR (zero padding of the last chunk)
-            const int ia = g * 16 - seg * C::SEG + C::KC - 4;
-            k1_pass(xs + ia, hs + seg * C::SEG, acc);
-        }
+        for (int pass = p_lo; pass <= p_hi; ++pass, ia -= 32 * C::SEG, hp += 32 * C::SEG)
+            k1_pass(xs + ia, hp, acc);
         fence_proxy_async_smem();
         __syncthreads();
     }
@@ -329,6 +340,14 @@ cudaError_t prepare_variant(int dev, int variant)
     cudaError_t e = cudaFuncSetAttribute(k1_gather<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k1_gather<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // All of the unified L1/shared storage as shared memory: four CTAs of the
+    // largest chunk need almost all of it.
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k1_gather<P, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k1_gather<P, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess)
         return e;
     int n = 0;
@@ -355,7 +374,7 @@ cudaError_t device_info(DevInfo **out)
         if (e == cudaSuccess)
             e = prepare_variant<4>(dev, K1_P4);
         if (e == cudaSuccess)
-            e = prepare_variant<13>(dev, K1_P13);
+            e = prepare_variant<K1_PBIG>(dev, K1_P11);
         if (e != cudaSuccess)
             return e;
         d.ready = true;
@@ -371,7 +390,7 @@ int k1_chunk_taps(int variant)
     switch (variant) {
     case K1_P1: return 32 * K1_SEG * 1;
     case K1_P4: return 32 * K1_SEG * 4;
-    case K1_P13: return 32 * K1_SEG * 13;
+    case K1_P11: return 32 * K1_SEG * K1_PBIG;
     default: return 0;
     }
 }
@@ -392,7 +411,7 @@ cudaError_t k1_plan(long long L, int e, int nin, int nitems, int ntile, int forc
         // The largest chunk that still gives about four waves of CTAs and
         // wastes < 10 % on the padded last chunk; otherwise the smallest chunk
         // whose chunk-task count fits the tile's pairwise stack.
-        static const int order[] = {K1_P13, K1_P4, K1_P1};
+        static const int order[] = {K1_P11, K1_P4, K1_P1};
         for (int v : order) {
             const long long kc = k1_chunk_taps(v);
             const long long nchunk = (L + e + kc - 1) / kc;
@@ -405,7 +424,7 @@ cudaError_t k1_plan(long long L, int e, int nin, int nitems, int ntile, int forc
             }
         }
         if (chosen < 0) {
-            static const int small_first[] = {K1_P1, K1_P4, K1_P13};
+            static const int small_first[] = {K1_P1, K1_P4, K1_P11};
             for (int v : small_first) {
                 const long long kc = k1_chunk_taps(v);
                 if ((L + e + kc - 1) / kc * nin <= K1_MAX_CHUNK_TASKS) {
@@ -451,7 +470,9 @@ cudaError_t k1_launch(K1Params &p, const K1Plan &plan, cudaStream_t st)
     switch (plan.variant) {
     case K1_P1: k1_gather<1, false><<<grid, K1_THREADS, smem_bytes<1>(), st>>>(p, nullptr, nullptr, 0); break;
     case K1_P4: k1_gather<4, false><<<grid, K1_THREADS, smem_bytes<4>(), st>>>(p, nullptr, nullptr, 0); break;
-    case K1_P13: k1_gather<13, false><<<grid, K1_THREADS, smem_bytes<13>(), st>>>(p, nullptr, nullptr, 0); break;
+    case K1_P11:
+        k1_gather<K1_PBIG, false><<<grid, K1_THREADS, smem_bytes<K1_PBIG>(), st>>>(p, nullptr, nullptr, 0);
+        break;
     default: return cudaErrorInvalidValue;
     }
     count_launch();
@@ -474,8 +495,8 @@ cudaError_t k1_launch_list(const K1Params *d_items, const long long *d_cta_begin
     switch (variant) {
     case K1_P1: k1_gather<1, true><<<grid, K1_THREADS, smem_bytes<1>(), st>>>(none, d_items, d_cta_begin, nitems); break;
     case K1_P4: k1_gather<4, true><<<grid, K1_THREADS, smem_bytes<4>(), st>>>(none, d_items, d_cta_begin, nitems); break;
-    case K1_P13:
-        k1_gather<13, true><<<grid, K1_THREADS, smem_bytes<13>(), st>>>(none, d_items, d_cta_begin, nitems);
+    case K1_P11:
+        k1_gather<K1_PBIG, true><<<grid, K1_THREADS, smem_bytes<K1_PBIG>(), st>>>(none, d_items, d_cta_begin, nitems);
         break;
     default: return cudaErrorInvalidValue;
     }

@@ -536,7 +536,7 @@ tc_status pack_launch(tc_server *srv, tc_server::StepBuf &b)
     // gives the GPU about four waves of CTAs with < 10 % padded taps, else the
     // smallest (short IRs, small batches: latency first).
     int variant = tc::K1_P1;
-    for (int v : {tc::K1_P13, tc::K1_P4}) {
+    for (int v : {tc::K1_P11, tc::K1_P4}) {
         const long long kcv = tc::k1_chunk_taps(v);
         long long ctas = 0, taps = 0, padded = 0;
         for (auto &w : b.items) {

@@ -25,7 +25,8 @@ namespace tc {
 constexpr int K1_MO = 128;           // outputs per tile
 constexpr int K1_THREADS = 256;      // 8 output groups of 16 x 32 tap sub-segments
 constexpr int K1_SEG = 20;           // taps per thread per pass
-constexpr int K1_KC_MAX = 32 * K1_SEG * 13;  // largest tap chunk of any variant
+constexpr int K1_PBIG = 11;                   // passes of the largest chunk (4 CTAs of it fit an SM)
+constexpr int K1_KC_MAX = 32 * K1_SEG * K1_PBIG;  // largest tap chunk of any variant
 constexpr int K1_MAX_CHUNK_TASKS = 4095;     // chunk-tasks per tile (12-level pairwise stack)
 
 struct K1Params {
@@ -68,7 +69,7 @@ struct K1Params {
 };
 
 // Variants: passes of K1_SEG taps per thread per chunk (KC = 32 * 20 * P).
-enum K1Variant { K1_P1 = 0, K1_P4 = 1, K1_P13 = 2, K1_NVARIANTS = 3 };
+enum K1Variant { K1_P1 = 0, K1_P4 = 1, K1_P11 = 2, K1_NVARIANTS = 3 };
 int k1_chunk_taps(int variant);
 
 struct K1Plan {

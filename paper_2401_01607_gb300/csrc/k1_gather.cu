@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(K1_THREADS, 4)
 {
     using C = K1Cfg<P>;
     extern __shared__ __align__(128) float smem[];
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t bar[2];
     __shared__ int s_last;
     __shared__ __align__(16) K1Params s_item;
     __shared__ long long s_first;
@@ -172,7 +172,8 @@ __global__ void __launch_bounds__(K1_THREADS, 4)
     const int nv = p.nver[p.vt_item ? item : 0];
 
     if (tid == 0) {
-        mbar_init(&bar, 1);
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
         fence_mbar_init();
     }
     __syncthreads();
@@ -189,37 +190,62 @@ __global__ void __launch_bounds__(K1_THREADS, 4)
     for (int r = 0; r < 16; ++r)
         acc[r] = 0.f;
 
+    constexpr int PA = (P >= 4) ? (P + 2) / 3 : P;  // passes fed by part A
+    constexpr bool SPLIT = PA < P;
+    constexpr int HA = 32 * C::SEG * PA;            // IR taps of part A
+    constexpr int XA = C::KC - HA;                  // first staged sample of part A
+    static_assert(XA % 4 == 0 && HA % 4 == 0, "parts start on 16-byte boundaries");
+
     uint32_t parity = 0;
     for (int v = 0; v < nv; ++v) {
         const long long a = vst[v];
         const long long b = (v + 1 < nv) ? vst[v + 1] : LLONG_MAX;
         if (b <= n_lo || a >= n_end)
             continue;  // this version spawned no tache that reaches the tile through this chunk
+        // Two parts on two mbarriers (chunks of 4 passes or more): part A =
+        // the IR taps of passes [0, PA) and the input samples they read,
+        // xs[XA, XS); part B = the rest. Passes [0, PA) start once part A has
+        // landed, while part B is still in flight.
+        const float *hv = hsrc + (long long)vsl[v] * p.ir_slot;
         bool ok = true;
         if (tid == 0) {
-            mbar_arrive_expect_tx(&bar, (uint32_t)(C::STAGE * sizeof(float)));
-            bulk_g2s(xs, xsrc, (uint32_t)(C::XS * sizeof(float)), &bar);
-            bulk_g2s(hs, hsrc + (long long)vsl[v] * p.ir_slot, (uint32_t)(C::KC * sizeof(float)), &bar);
-            ok = mbar_wait_bounded(&bar, parity, p.err, ERR_TIMEOUT_TMA);
+            if (SPLIT) {
+                mbar_arrive_expect_tx(&bar[0], (uint32_t)((C::XS - XA + HA) * sizeof(float)));
+                bulk_g2s(xs + XA, xsrc + XA, (uint32_t)((C::XS - XA) * sizeof(float)), &bar[0]);
+                bulk_g2s(hs, hv, (uint32_t)(HA * sizeof(float)), &bar[0]);
+                mbar_arrive_expect_tx(&bar[1], (uint32_t)((XA + C::KC - HA) * sizeof(float)));
+                bulk_g2s(xs, xsrc, (uint32_t)(XA * sizeof(float)), &bar[1]);
+                bulk_g2s(hs + HA, hv + HA, (uint32_t)((C::KC - HA) * sizeof(float)), &bar[1]);
+            } else {
+                mbar_arrive_expect_tx(&bar[0], (uint32_t)(C::STAGE * sizeof(float)));
+                bulk_g2s(xs, xsrc, (uint32_t)(C::XS * sizeof(float)), &bar[0]);
+                bulk_g2s(hs, hv, (uint32_t)(C::KC * sizeof(float)), &bar[0]);
+            }
+            ok = mbar_wait_bounded(&bar[0], parity, p.err, ERR_TIMEOUT_TMA);
         }
-        parity ^= 1u;
         if (!__syncthreads_and(ok)) {
             // Give the copies in flight a bounded chance to land before the CTA exits.
-            if (tid == 0)
-                mbar_wait_bounded(&bar, parity ^ 1u, nullptr, 0);
+            if (tid == 0) {
+                mbar_wait_bounded(&bar[0], parity, nullptr, 0);
+                if (SPLIT)
+                    mbar_wait_bounded(&bar[1], parity, nullptr, 0);
+            }
             __syncthreads();
             return;
         }
-        if (a > n_lo || b < n_end) {
-            // The window straddles a version boundary: keep only the samples
-            // that spawned their tache with this version by zeroing
-            // [n_lo, a) and [b, n_end) of the staged window.
-            const long long za = a - n_lo, zb = b - n_lo;
-            const int z0 = (za > 0) ? (za < C::XS ? (int)za : C::XS) : 0;
-            const int z1 = (b < n_end) ? (zb > 0 ? (int)zb : 0) : C::XS;
-            for (int i = tid; i < z0; i += K1_THREADS)
+        // A window that straddles a version boundary keeps only the samples
+        // that spawned their tache with this version: [n_lo, a) and
+        // [b, n_end) of the staged window are zeroed, in each part once it
+        // has landed.
+        const bool straddle = (a > n_lo || b < n_end);
+        const long long za = a - n_lo, zb = b - n_lo;
+        const int z0 = (za > 0) ? (za < C::XS ? (int)za : C::XS) : 0;
+        const int z1 = (b < n_end) ? (zb > 0 ? (int)zb : 0) : C::XS;
+        if (straddle) {
+            constexpr int r0 = SPLIT ? XA : 0;
+            for (int i = r0 + tid; i < z0; i += K1_THREADS)
                 xs[i] = 0.f;
-            for (int i = z1 + tid; i < C::XS; i += K1_THREADS)
+            for (int i = max(z1, r0) + tid; i < C::XS; i += K1_THREADS)
                 xs[i] = 0.f;
             __syncthreads();
         }
@@ -235,11 +261,37 @@ __global__ void __launch_bounds__(K1_THREADS, 4)
             (b == LLONG_MAX) ? -(1LL << 40) : floor_div(out_hi - kc0 - (15 + C::SEG - 1) - b, C::SEG) + 1;
         const int p_lo = (int)max(0LL, min((long long)P, -floor_div(s - seg_lo, 32)));
         const int p_hi = (int)max(-1LL, min((long long)P - 1, floor_div(seg_hi - s, 32)));
+        int pass = p_lo;
         int ia = g * 16 - (p_lo * 32 + s) * C::SEG + C::KC - 4;
         const float *hp = hs + (p_lo * 32 + s) * C::SEG;
+        // Pass p reads xs[KC - 640 (p + 1), KC - 640 p + 128) and hs[640 p, 640 (p + 1)):
+        // passes below PA touch part A only.
+        const int pa_end = min(p_hi, PA - 1);
 #pragma unroll 1
-        for (int pass = p_lo; pass <= p_hi; ++pass, ia -= 32 * C::SEG, hp += 32 * C::SEG)
+        for (; pass <= pa_end; ++pass, ia -= 32 * C::SEG, hp += 32 * C::SEG)
             k1_pass(xs + ia, hp, acc);
+        if (SPLIT) {
+            bool okb = true;
+            if (tid == 0)
+                okb = mbar_wait_bounded(&bar[1], parity, p.err, ERR_TIMEOUT_TMA);
+            if (!__syncthreads_and(okb)) {
+                if (tid == 0)
+                    mbar_wait_bounded(&bar[1], parity, nullptr, 0);
+                __syncthreads();
+                return;
+            }
+            if (straddle) {
+                for (int i = tid; i < min(z0, XA); i += K1_THREADS)
+                    xs[i] = 0.f;
+                for (int i = z1 + tid; i < XA; i += K1_THREADS)
+                    xs[i] = 0.f;
+                __syncthreads();
+            }
+#pragma unroll 1
+            for (; pass <= p_hi; ++pass, ia -= 32 * C::SEG, hp += 32 * C::SEG)
+                k1_pass(xs + ia, hp, acc);
+        }
+        parity ^= 1u;
         fence_proxy_async_smem();
         __syncthreads();
     }

@@ -215,10 +215,10 @@ tc_status tc_convolve(const float *x, size_t N, const float *h, size_t L, float 
  * copies, split-sum partials, counters) lives in one fixed 32 MiB device
  * array inside this library. Each GPU that loads the library holds that array
  * until the process exits.
- *   - Limit: the working set, about N + 13 L + 5e4 floats (N + 7 L + 5e4
- *     for IRs over 70000 taps), must fit in 32 MiB = 8388608 floats: for
- *     example N up to 8.2 million samples with L = 4096. A call beyond it
- *     returns TC_EINVAL and names the size it would need.
+ *   - Limit: the working set, about N + 13 L + 5e4 floats, must fit in
+ *     32 MiB = 8388608 floats: for example N up to 8.2 million samples with
+ *     L = 4096. A call beyond it returns TC_EINVAL and names the size it
+ *     would need.
  *   - The first call on a device looks up the array's device address with
  *     that device current. Make that first call before any CUDA stream
  *     capture.

@@ -380,8 +380,10 @@ uint64_t tc_kernel_launches(void);
  *                        tensor cores before the pairwise reduction of
  *                        ranges (default 16 for the BF16 split, 4096 for
  *                        BF16; 1..4096)
+ *   TC_TUNE_K2_PAIR      plain BF16 only: 1 = two 128-channel tiles per CTA
+ *                        sharing each IR tile (default), 0 = one tile per CTA
  * Errors: TC_EINVAL for an unknown knob or value out of range. */
-typedef enum tc_tune_knob { TC_TUNE_K1_CHUNK = 0, TC_TUNE_K2_RANGE = 1 } tc_tune_knob;
+typedef enum tc_tune_knob { TC_TUNE_K1_CHUNK = 0, TC_TUNE_K2_RANGE = 1, TC_TUNE_K2_PAIR = 2 } tc_tune_knob;
 tc_status tc_set_tuning(tc_stream *s, int knob, long long value);
 
 /* Kernel timing (tracing aid). With enable = 1, each later convolution kernel

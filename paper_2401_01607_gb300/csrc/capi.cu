@@ -139,6 +139,7 @@ struct tc_stream {
     int *d_err = nullptr;
     int k1_variant_fixed = -1;  // -1: chosen per launch
     long long k2_range = -1;    // K blocks per tensor-core CTA range (-1: by precision)
+    bool k2_single_tile = false; // plain BF16: one channel tile per CTA (tuning knob)
 
     // BF16 tensor-core path (shared-IR groups): bf16 hi/lo histories and, per
     // IR slot and alignment shift delta, the materialised Toeplitz tiles.
@@ -611,10 +612,14 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
     tc::K2Params p{};
     p.C = (int)s->rows;
     p.nout = (int)nout;
-    p.ntile_c = (int)((s->rows + TM - 1) / TM);
     p.ntile_o = (int)ntile_o;
     p.x_col0 = w0 - s->base;
     p.nkb = (int)nkb;
+    // Plain BF16 runs two channel tiles per CTA (one T stage feeds both), as
+    // long as a unit's K range fits one TMEM run.
+    const long long ntile_c1 = (s->rows + TM - 1) / TM;
+    bool pair = s->prec == TC_BF16 && !s->k2_single_tile;
+    p.ntile_c = (int)(pair ? (ntile_c1 + 1) / 2 : ntile_c1);
     const long long tiles = (long long)p.ntile_c * p.ntile_o;
     // TMEM runs of `range` K blocks before each drain into FP32 registers.
     // The BF16 split's error grows with the run (measured at L = 96000:
@@ -641,11 +646,17 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
     nsplit = (nkb + kb_per - 1) / kb_per;
     p.nsplit = (int)nsplit;
     p.kb_per = (int)kb_per;
+    if (pair && p.range < p.kb_per) {
+        // One TMEM run cannot hold this unit's K range: single tiles, same K split.
+        pair = false;
+        p.ntile_c = (int)ntile_c1;
+    }
     p.y = y;
     p.y_pitch = y_pitch;
     p.err = s->d_err;
     if (nsplit > 1) {
-        const size_t need = (size_t)(tiles * nsplit) * TM * TN;
+        // Partials per 128-channel tile (the pair kernel writes that layout too).
+        const size_t need = (size_t)(2 * ((ntile_c1 + 1) / 2) * ntile_o * nsplit) * TM * TN;
         if (need > s->k2_partial_floats) {
             TC_CU(cudaStreamSynchronize(s->cs));
             cudaFree(s->k2_partial);
@@ -657,7 +668,10 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
     }
     tc_stream::TSet &t = ts;
     TC_TRY(prof_begin(s));
-    TC_CU(tc::k2_launch(s->mx_hi, s->mx_lo, t.mt_hi, t.mt_lo, p, s->prec == TC_BF16 ? 1 : 3, s->cs));
+    if (pair)
+        TC_CU(tc::k2_launch_pair(s->mx_hi, t.mt_hi, p, s->cs));
+    else
+        TC_CU(tc::k2_launch(s->mx_hi, s->mx_lo, t.mt_hi, t.mt_lo, p, s->prec == TC_BF16 ? 1 : 3, s->cs));
     TC_TRY(prof_end(s, t0, nout));
     s->k2_launches++;
     *used = true;
@@ -1023,6 +1037,11 @@ tc_status tc_set_tuning(tc_stream *s, int knob, long long value)
         if (value < 1 || value > 4096)
             return fail(TC_EINVAL, "TC_TUNE_K2_RANGE must be -1 or in [1, 4096]");
         s->k2_range = value;
+        return TC_OK;
+    case TC_TUNE_K2_PAIR:
+        if (value != -1 && value != 0 && value != 1)
+            return fail(TC_EINVAL, "TC_TUNE_K2_PAIR must be -1, 0 or 1");
+        s->k2_single_tile = value == 0;
         return TC_OK;
     default:
         return fail(TC_EINVAL, "unknown tuning knob %d", knob);

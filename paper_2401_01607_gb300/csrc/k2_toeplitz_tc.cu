@@ -263,6 +263,178 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
     }
 }
 
+// Plain BF16 with two channel tiles per CTA: both 128-channel X tiles of a
+// K block are multiplied by the same T stage, so each T tile loaded from L2
+// feeds two MMAs (T is 2/3 of a single-tile stage's bytes). One TMEM run per
+// unit (the K range fits one FP32 accumulation, as plain BF16 is limited by
+// its operands, not by the run length); two accumulators of 256 columns. The
+// epilogue writes TMEM straight to y (or to the K-part partials).
+constexpr int K2P_NS = 6;
+constexpr int K2P_STAGE = 2 * K2_XBYTES + K2_TBYTES;  // X tile a, X tile b, T
+constexpr int K2P_SMEM = K2P_NS * K2P_STAGE + 1024;
+
+__global__ void __launch_bounds__(K2_THREADS, 1)
+    k2_toeplitz_pair(const __grid_constant__ CUtensorMap mx_hi, const __grid_constant__ CUtensorMap mt_hi,
+                     const K2Params p)
+{
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full[K2P_NS];
+    __shared__ __align__(8) uint64_t empty[K2P_NS];
+    __shared__ __align__(8) uint64_t accfull;
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int s_fail;
+
+    uint8_t *const smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int lane = tid & 31;
+
+    // Unit = (channel-tile pair, output tile, K part).
+    long long u = blockIdx.x;
+    const int part = (int)(u % p.nsplit);
+    u /= p.nsplit;
+    const int tile_o = (int)(u % p.ntile_o);
+    const int tile_c = (int)(u / p.ntile_o);  // pair index
+    const int kb0 = part * p.kb_per;
+    const int kb1 = min(kb0 + p.kb_per, p.nkb);
+    const int nk = max(kb1 - kb0, 0);
+    const int c0 = tile_c * 2 * K2_M;
+    const long long xcol0 = p.x_col0 + (long long)tile_o * K2_N;
+
+    if (tid == 0) {
+        for (int i = 0; i < K2P_NS; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        mbar_init(&accfull, 1);
+        s_fail = 0;
+        fence_mbar_init();
+    }
+    if (warp == 2)
+        tmem_alloc(&tmem_base, 2 * K2_N);
+    tc_fence_before_sync();
+    __syncthreads();
+    tc_fence_after_sync();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- producer ----
+            for (int i = 0; i < nk && !s_fail; ++i) {
+                const int st = i % K2P_NS;
+                const int use = i / K2P_NS;
+                if (use > 0 && !mbar_wait_bounded(&empty[st], (uint32_t)((use - 1) & 1), p.err, ERR_TIMEOUT_TMA)) {
+                    s_fail = 1;
+                    break;
+                }
+                uint8_t *sb = smem + st * K2P_STAGE;
+                const int kb = kb0 + i;
+                mbar_arrive_expect_tx(&full[st], (uint32_t)K2P_STAGE);
+                const int xc = (int)(xcol0 + (long long)kb * K2_KB);
+                tma_load_2d(sb, &mx_hi, xc, c0, &full[st]);
+                tma_load_2d(sb + K2_XBYTES, &mx_hi, xc, c0 + K2_M, &full[st]);
+                tma_load_2d(sb + 2 * K2_XBYTES, &mt_hi, 0, kb * K2_N, &full[st]);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---- MMA issuer ----
+            const uint32_t idesc = umma_idesc_bf16(K2_M, K2_N);
+            for (int i = 0; i < nk; ++i) {
+                const int st = i % K2P_NS;
+                if (!mbar_wait_bounded(&full[st], (uint32_t)((i / K2P_NS) & 1), p.err, ERR_TIMEOUT_MMA)) {
+                    s_fail = 1;
+                    break;
+                }
+                tc_fence_after_sync();
+                const uint32_t sb = smem_u32(smem + st * K2P_STAGE);
+#pragma unroll
+                for (int kk = 0; kk < K2_KB / 16; ++kk) {
+                    const uint32_t koff = kk * 32;
+                    const uint64_t th = umma_desc_sw64(sb + 2 * K2_XBYTES + koff);
+                    const uint32_t accum = (i == 0 && kk == 0) ? 0u : 1u;
+                    umma_bf16(tmem, umma_desc_sw64(sb + koff), th, idesc, accum);
+                    umma_bf16(tmem + K2_N, umma_desc_sw64(sb + K2_XBYTES + koff), th, idesc, accum);
+                }
+                umma_commit(&empty[st]);
+            }
+            if (!s_fail)
+                umma_commit(&accfull);
+        }
+    } else if (warp >= K2_ROLE_WARPS) {
+        // ---- epilogue: TMEM -> y / partials ----
+        const int ew = warp - K2_ROLE_WARPS;
+        const int q = warp & 3;    // TMEM lane quarter this warp may access
+        const int half = ew >> 2;  // column half
+        bool got = true;
+        if (lane == 0) {
+            got = false;
+            const unsigned long long t0 = globaltimer_ns();
+            for (uint32_t it = 0;; ++it) {
+                if (mbar_try_wait(&accfull, 0)) {
+                    got = true;
+                    break;
+                }
+                if ((it & 255u) == 255u) {
+                    if (s_fail)
+                        break;
+                    if (globaltimer_ns() - t0 > kWaitLimitNs) {
+                        atomicOr(p.err, ERR_TIMEOUT_MMA);
+                        break;
+                    }
+                }
+            }
+        }
+        got = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
+        if (got && nk > 0) {
+            mbar_try_wait(&accfull, 0);
+            tc_fence_after_sync();
+#pragma unroll 1
+            for (int a = 0; a < 2; ++a) {
+                const int ch = a * K2_M + q * 32 + lane;  // channel within the pair
+                const int c = c0 + ch;
+                float *dst;
+                long long lim;
+                if (p.nsplit == 1) {
+                    dst = p.y + (long long)c * p.y_pitch + (long long)tile_o * K2_N + half * 128;
+                    lim = p.nout - (long long)tile_o * K2_N - half * 128;
+                } else {
+                    // Partials are laid out per 128-channel tile, as k2_reduce reads them.
+                    const int tc1 = tile_c * 2 + a;
+                    dst = p.partial + ((((long long)tc1 * p.ntile_o + tile_o) * p.nsplit + part) * K2_M +
+                                       (q * 32 + lane)) * K2_N + half * 128;
+                    lim = 128;
+                }
+                const uint32_t src = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * K2_N + half * 128);
+#pragma unroll
+                for (int cc = 0; cc < 8; ++cc) {
+                    float v[16];
+                    tmem_ld_32x16(src + cc * 16, v);
+                    if (c >= p.C)
+                        continue;
+                    const long long j0 = cc * 16;
+                    if (lim >= j0 + 16) {
+#pragma unroll
+                        for (int j = 0; j < 16; j += 4)
+                            *reinterpret_cast<float4 *>(dst + j0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (j0 + j < lim)
+                                dst[j0 + j] = v[j];
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before_sync();
+    __syncthreads();
+    if (warp == 2) {
+        tc_fence_after_sync();
+        tmem_dealloc(tmem, 2 * K2_N);
+    }
+}
+
 // Adds the nsplit K-range partials of each (channel, output) by a fixed
 // pairwise tree (adjacent pairs, zero-padded to 64 leaves) and writes y.
 __global__ void k2_reduce(const float *__restrict__ partial, int nsplit, int C, int ntile_o, int nout, float *y,
@@ -361,6 +533,36 @@ cudaError_t k2_split_launch(const float *hist, long long pitch, int rows, long l
 }
 
 size_t k2_smem_bytes(int nprod) { return nprod == 1 ? K2Cfg<1>::SMEM : K2Cfg<3>::SMEM; }
+
+cudaError_t k2_launch_pair(const CUtensorMap &mx_hi, const CUtensorMap &mt_hi, const K2Params &p, cudaStream_t st)
+{
+    static bool attr[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    if (dev < 0 || dev >= 64 || p.nsplit < 1 || p.nsplit > 64 || p.range < p.kb_per)
+        return cudaErrorInvalidValue;
+    if (!attr[dev]) {
+        e = cudaFuncSetAttribute(k2_toeplitz_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, K2P_SMEM);
+        if (e != cudaSuccess)
+            return e;
+        attr[dev] = true;
+    }
+    const long long units = (long long)p.ntile_c * p.ntile_o * p.nsplit;  // ntile_c counts tile pairs here
+    if (units <= 0)
+        return cudaSuccess;
+    k2_toeplitz_pair<<<(unsigned)units, K2_THREADS, K2P_SMEM, st>>>(mx_hi, mt_hi, p);
+    count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess || p.nsplit == 1)
+        return e;
+    const long long work = (long long)p.C * p.nout;
+    k2_reduce<<<grid_for(work), 256, 0, st>>>(p.partial, p.nsplit, p.C, (p.nout + K2_N - 1) / K2_N, p.nout, p.y,
+                                              p.y_pitch);
+    count_launch();
+    return cudaGetLastError();
+}
 
 cudaError_t k2_launch(const CUtensorMap &mx_hi, const CUtensorMap &mx_lo, const CUtensorMap &mt_hi,
                       const CUtensorMap &mt_lo, const K2Params &p, int nprod, cudaStream_t st)

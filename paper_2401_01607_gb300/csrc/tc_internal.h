@@ -143,6 +143,9 @@ cudaError_t k2_split_launch(const float *hist, long long pitch, int rows, long l
 // [rows][pitch], box 32 x 128; T over [nkb * 256][32], box 32 x 256; 64-byte swizzle.
 cudaError_t k2_launch(const CUtensorMap &mx_hi, const CUtensorMap &mx_lo, const CUtensorMap &mt_hi,
                       const CUtensorMap &mt_lo, const K2Params &p, int nprod, cudaStream_t st);
+// Plain BF16 with two 128-channel tiles per CTA sharing each T stage. p.ntile_c
+// counts tile pairs (ceil(C / 256)); one TMEM run per unit (range >= kb_per).
+cudaError_t k2_launch_pair(const CUtensorMap &mx_hi, const CUtensorMap &mt_hi, const K2Params &p, cudaStream_t st);
 // Encodes a 2-D bf16 tensor map (inner dimension first), 64-byte swizzle.
 cudaError_t encode_bf16_2d(CUtensorMap *map, const void *base, unsigned long long dim0, unsigned long long dim1,
                            unsigned long long stride1_bytes, unsigned box0, unsigned box1);

@@ -24,11 +24,14 @@ def _built():
     capi.load()
 
 
-def run_group(X, H, vstart, L, block, prec, max_push):
-    """Streams X [C, N] through a shared-IR group; returns (y [C, N+L-1], info)."""
+def run_group(X, H, vstart, L, block, prec, max_push, tuning=()):
+    """Streams X [C, N] through a shared-IR group; returns (y [C, N+L-1], info).
+    tuning: (knob, value) pairs set before the first push."""
     C, N = X.shape
     s = capi.tc_open_group(C, L, block, True, PREC[prec], max_push)
     try:
+        for knob, value in tuning:
+            capi.tc_set_tuning(s, knob, value)
         outs, pos, v = [], 0, 0
         while pos < N:
             n = min(max_push, N - pos)
@@ -89,3 +92,17 @@ def test_shared_ir_switch_falls_back_exactly():
     y, info = run_group(X, H, vs, L, B, "bf16split", 512)
     assert info.tensor_launches > 0 and info.fp32_fallbacks > 0
     check(y, X, H, vs, B, "bf16split", rows=[0, 64, 129])
+
+
+@pytest.mark.parametrize("pair", [1, 0])
+@pytest.mark.parametrize("L", [3000, 20_000])
+def test_bf16_two_tiles_per_cta(pair, L):
+    """Plain BF16 with two channel tiles per CTA (default) and with one: 300
+    channels = three tiles, so the second pair is half outside the group; the
+    K range splits over CTAs at L = 20000."""
+    C, N, B = 300, 2600, 256
+    X = synth.audio_block(C, N, 6000 + L)
+    H = synth.decayed_ir(L, 0.2 * L, 79)[None]
+    y, info = run_group(X, H, [0], L, B, "bf16", 1280, tuning=[(capi.TC_TUNE_K2_PAIR, pair)])
+    assert info.tensor_launches > 0 and info.fp32_fallbacks == 0
+    check(y, X, H, [0], B, "bf16", rows=[0, 127, 128, 255, 256, 299])

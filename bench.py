@@ -374,6 +374,136 @@ def bench_shared(torch, steps: int, warmup: int, P: int = 8192, C: int = 1024, N
     return out
 
 
+def bench_mimo(torch, P: int = 8192) -> dict:
+    """MIMO workload: 16 inputs x 60 s at 48 kHz, 16 x 16 IRs of L = 192000
+    (tau 38400), block 512; each output is the sum of 16 convolutions. One
+    step = the whole signal pushed (device pointers, P samples per push) and
+    the L-1 flush, FP32 on K1. Sampled outputs are checked against the oracle's
+    direct sums (one per input, added in FP64)."""
+    from paper_2401_01607_gb300 import capi
+    import oracle
+    w = synth.mimo()
+    nin, nout = w.mimo
+    N, L, B = w.x.shape[1], w.L, w.block
+    npush = math.ceil(N / P)
+    xp = np.zeros((npush, nin, P), np.float32)
+    for i in range(npush):
+        seg = w.x[:, i * P:(i + 1) * P]
+        n = seg.shape[1]
+        xp[i].reshape(-1)[:nin * n] = seg.reshape(-1)
+    x_d = torch.from_numpy(xp).cuda()
+    h_d = torch.from_numpy(np.ascontiguousarray(w.H[0])).cuda()  # [nout][nin][L]
+    y_d = torch.empty((npush, nout, P), device="cuda")
+    tail_d = torch.empty((nout, L - 1), device="cuda")
+    ts = torch.cuda.Stream()
+    s = capi.tc_open_mimo(nin, nout, L, B, capi.TC_FP32, P)
+    try:
+        capi.tc_set_cuda_stream(s, ts)
+
+        def step(n_samples):
+            capi.tc_reset(s)
+            capi.tc_set_ir_rows(s, int(h_d.data_ptr()), L, 0, on_device=True)
+            pos = 0
+            for i in range(npush):
+                if pos >= n_samples:
+                    break
+                n = min(P, n_samples - pos)
+                capi.tc_push(s, int(x_d[i].data_ptr()), n, int(y_d[i].data_ptr()), on_device=True)
+                pos += n
+            capi.tc_flush_dev(s, int(tail_d.data_ptr()))
+
+        step(4 * P)  # warm-up: a short segment
+        ts.synchronize()
+        capi.tc_profile(s, True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ts)
+        step(N)
+        e1.record(ts)
+        e1.synchronize()
+        k_ms, k_n, k_macs = capi.tc_profile_read(s)
+        capi.tc_profile(s, False)
+    finally:
+        capi.tc_close(s)
+    ms = e0.elapsed_time(e1)
+    macs = nout * nin * N * L
+    y = y_d.cpu().numpy()
+    tail = tail_d.cpu().numpy()
+    rng = np.random.default_rng(9)
+    got, ref = [], []
+    for _ in range(8):
+        o, m = int(rng.integers(nout)), int(rng.integers(N + L - 1))
+        if m < N:
+            i, j = divmod(m, P)
+            n = min(P, N - i * P)
+            got.append(y[i].reshape(-1)[o * n + j])
+        else:
+            got.append(tail[o, m - N])
+        ref.append(sum(oracle.direct_at(w.x[i_], w.H[0, o, i_][None], w.vstart, m) for i_ in range(nin)))
+    got, ref = np.array(got, np.float64), np.array(ref)
+    tflops = 2.0 * k_macs / (k_ms / 1e3) / 1e12 if k_ms > 0 else 0.0
+    peak = fp32_peak_tflops(SM_MAX_MHZ)
+    del x_d, y_d, tail_d, h_d
+    torch.cuda.empty_cache()
+    return {"workload": "MIMO 16 x 16, 60 s @ 48 kHz (2880000 samples per input), L=192000 tau=38400, block 512, "
+                        "pushes of %d, FP32 (K1)" % P,
+            "tap_macs": macs, "ms_per_step": ms, "value": macs / (ms / 1e3), "unit": "tap-MAC/s",
+            "realtime_factor": (N / FS) / (ms / 1e3),
+            "check": {"sampled_outputs": len(got), "rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+                      "max_abs": float(np.max(np.abs(got - ref)))},
+            "roofline": {"bound": "alu", "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
+                         "kernel": "k1_gather (FP32 FMA), 16 inputs per output item", "k1_launches": k_n}}
+
+
+def bench_mono(capi) -> dict:
+    """Mono workload: 48000 samples, L = 4096 (tau 800), block 64. Streamed block
+    by block through tc_push_block (host buffers): per-block latency against
+    the 64/48000 s deadline; and the whole signal as one tc_convolve call."""
+    import torch
+    w = synth.mono()
+    x = np.ascontiguousarray(w.x[0])
+    h = np.ascontiguousarray(w.H[0][0])
+    N, L, B = x.size, w.L, w.block
+    s = capi.tc_open_stream(L, B)
+    lat = []
+    try:
+        capi.tc_set_ir(s, h)
+        yb = np.empty(B, np.float32)
+        for rep in range(2):  # the first pass warms up
+            capi.tc_reset(s)
+            capi.tc_set_ir(s, h)
+            lat = []
+            t_all = time.perf_counter()
+            for pos in range(0, N, B):
+                t = time.perf_counter()
+                capi.tc_push_block(s, x[pos:pos + B], yb)
+                lat.append(time.perf_counter() - t)
+            tail = np.empty(L - 1, np.float32)
+            capi.tc_flush(s, tail, L - 1)
+            t_all = time.perf_counter() - t_all
+    finally:
+        capi.tc_close(s)
+    lat = np.array(lat) * 1e3
+    x_d = torch.from_numpy(x).cuda()
+    h_d = torch.from_numpy(h).cuda()
+    y_d = torch.empty(N + L - 1, device="cuda")
+    capi.tc_convolve(x_d, N, h_d, L, y_d)
+    torch.cuda.synchronize()
+    reps = 20
+    t = time.perf_counter()
+    for _ in range(reps):
+        capi.tc_convolve(x_d, N, h_d, L, y_d)
+    torch.cuda.synchronize()
+    t_conv = (time.perf_counter() - t) / reps
+    return {"workload": "mono: 48000 samples, L=4096 tau=800, block 64",
+            "blocks": int(lat.size), "deadline_ms": B / FS * 1e3, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max()),
+            "misses": int(np.sum(lat > B / FS * 1e3)),
+            "streamed_realtime_factor": (N / FS) / t_all,
+            "one_shot_ms": t_conv * 1e3, "one_shot_tap_macs_per_s": N * L / t_conv,
+            "mode": "tc_push_block per 64-sample block (host buffers, synchronous), then tc_flush; one-shot "
+                    "tc_convolve on device buffers"}
+
+
 # ---------------------------------------------------------------------------
 # Serving: continuous batching (tc_server_*) under real-time pacing
 # ---------------------------------------------------------------------------
@@ -709,6 +839,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving section")
     ap.add_argument("--only-serving", action="store_true", help="run only the serving section")
     ap.add_argument("--trace-seconds", type=float, default=15.0)
+    ap.add_argument("--no-mimo", action="store_true", help="skip the MIMO section")
+    ap.add_argument("--only-mimo", action="store_true", help="run only the MIMO section")
     ap.add_argument("--shared-C", type=int, default=1024, help="shared-IR section: streams")
     ap.add_argument("--shared-N", type=int, default=240_000, help="shared-IR section: samples per stream")
     ap.add_argument("--shared-prec", default="bf16split,bf16,fp32", help="shared-IR section: precisions")
@@ -740,6 +872,10 @@ def main():
         print(json.dumps({"shared_ir": bench_shared(torch, max(1, args.steps), max(1, args.warmup), C=args.shared_C,
                                                     N=args.shared_N, precisions=args.shared_prec.split(","))}),
               flush=True)
+        dist.close()
+        return
+    if args.only_mimo:
+        print(json.dumps({"mimo": bench_mimo(torch), "mono": bench_mono(capi)}), flush=True)
         dist.close()
         return
     if args.only_serving:
@@ -868,6 +1004,10 @@ def main():
     shared = None
     if not args.no_shared and dist.world == 1:
         shared = bench_shared(torch, steps=2, warmup=1)
+    mimo = mono = None
+    if not args.no_mimo and dist.world == 1:
+        mimo = bench_mimo(torch)
+        mono = bench_mono(capi)
     serving = None
     if not args.no_serving and dist.world == 1:
         serving = bench_serving(torch, capi, np.ascontiguousarray(w.H[:, 0]), args.trace_seconds)
@@ -880,7 +1020,7 @@ def main():
                 "realtime_streams_48k": value / per_stream_rt,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": int(launches), "latency": latency, "check": check, "shared_ir": shared,
-                "serving": serving,
+                "serving": serving, "mimo": mimo, "mono": mono,
                 "autotune_push_ms_per_sample": {str(k): v for k, v in tune.items()} or None}
         print(json.dumps(line), flush=True)
     dist.close()

@@ -374,15 +374,17 @@ def bench_shared(torch, steps: int, warmup: int, P: int = 8192, C: int = 1024, N
     return out
 
 
-def bench_mimo(torch, P: int = 8192) -> dict:
+def bench_mimo(torch, P: int = 8192, precisions=("bf16split", "bf16", "fp32"), L: int = 192_000,
+               seconds: float = 60.0) -> dict:
     """MIMO workload: 16 inputs x 60 s at 48 kHz, 16 x 16 IRs of L = 192000
     (tau 38400), block 512; each output is the sum of 16 convolutions. One
     step = the whole signal pushed (device pointers, P samples per push) and
-    the L-1 flush, FP32 on K1. Sampled outputs are checked against the oracle's
-    direct sums (one per input, added in FP64)."""
+    the L-1 flush: FP32 on K1, BF16 split and BF16 on the tensor cores (K3).
+    Sampled outputs are checked against the oracle's direct sums (one per
+    input, added in FP64). L and seconds shrink it for profiling captures."""
     from paper_2401_01607_gb300 import capi
     import oracle
-    w = synth.mimo()
+    w = synth.mimo(N=int(seconds * FS), L=L)
     nin, nout = w.mimo
     N, L, B = w.x.shape[1], w.L, w.block
     npush = math.ceil(N / P)
@@ -396,62 +398,80 @@ def bench_mimo(torch, P: int = 8192) -> dict:
     y_d = torch.empty((npush, nout, P), device="cuda")
     tail_d = torch.empty((nout, L - 1), device="cuda")
     ts = torch.cuda.Stream()
-    s = capi.tc_open_mimo(nin, nout, L, B, capi.TC_FP32, P)
-    try:
-        capi.tc_set_cuda_stream(s, ts)
-
-        def step(n_samples):
-            capi.tc_reset(s)
-            capi.tc_set_ir_rows(s, int(h_d.data_ptr()), L, 0, on_device=True)
-            pos = 0
-            for i in range(npush):
-                if pos >= n_samples:
-                    break
-                n = min(P, n_samples - pos)
-                capi.tc_push(s, int(x_d[i].data_ptr()), n, int(y_d[i].data_ptr()), on_device=True)
-                pos += n
-            capi.tc_flush_dev(s, int(tail_d.data_ptr()))
-
-        step(4 * P)  # warm-up: a short segment
-        ts.synchronize()
-        capi.tc_profile(s, True)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(ts)
-        step(N)
-        e1.record(ts)
-        e1.synchronize()
-        k_ms, k_n, k_macs = capi.tc_profile_read(s)
-        capi.tc_profile(s, False)
-    finally:
-        capi.tc_close(s)
-    ms = e0.elapsed_time(e1)
     macs = nout * nin * N * L
-    y = y_d.cpu().numpy()
-    tail = tail_d.cpu().numpy()
     rng = np.random.default_rng(9)
-    got, ref = [], []
-    for _ in range(8):
-        o, m = int(rng.integers(nout)), int(rng.integers(N + L - 1))
-        if m < N:
-            i, j = divmod(m, P)
-            n = min(P, N - i * P)
-            got.append(y[i].reshape(-1)[o * n + j])
+    picks = [(int(rng.integers(nout)), int(rng.integers(N + L - 1))) for _ in range(32)]
+    refs = np.array([sum(oracle.direct_at(w.x[i_], w.H[0, o, i_][None], w.vstart, m) for i_ in range(nin))
+                     for o, m in picks])
+    peaks = load_peaks()
+    bf16_peak = float(peaks.get("bf16_tflops_sustained", 1690.8))
+    out = {"workload": "MIMO 16 x 16, %g s @ 48 kHz (%d samples per input), L=%d tau=%g, block 512, pushes of %d"
+                       % (seconds, N, L, 0.2 * L, P), "tap_macs": macs}
+    for name in precisions:
+        prec = {"fp32": capi.TC_FP32, "bf16": capi.TC_BF16, "bf16split": capi.TC_BF16_SPLIT}[name]
+        s = capi.tc_open_mimo(nin, nout, L, B, prec, P)
+        try:
+            capi.tc_set_cuda_stream(s, ts)
+
+            def step(n_samples):
+                capi.tc_reset(s)
+                capi.tc_set_ir_rows(s, int(h_d.data_ptr()), L, 0, on_device=True)
+                pos = 0
+                for i in range(npush):
+                    if pos >= n_samples:
+                        break
+                    n = min(P, n_samples - pos)
+                    capi.tc_push(s, int(x_d[i].data_ptr()), n, int(y_d[i].data_ptr()), on_device=True)
+                    pos += n
+                capi.tc_flush_dev(s, int(tail_d.data_ptr()))
+
+            step(4 * P)  # warm-up: a short segment
+            ts.synchronize()
+            capi.tc_profile(s, True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(ts)
+            step(N)
+            e1.record(ts)
+            e1.synchronize()
+            k_ms, k_n, k_macs = capi.tc_profile_read(s)
+            capi.tc_profile(s, False)
+            info = capi.tc_get_info(s)
+        finally:
+            capi.tc_close(s)
+        ms = e0.elapsed_time(e1)
+        y = y_d.cpu().numpy()
+        tail = tail_d.cpu().numpy()
+        got = []
+        for o, m in picks:
+            if m < N:
+                i, j = divmod(m, P)
+                n = min(P, N - i * P)
+                got.append(y[i].reshape(-1)[o * n + j])
+            else:
+                got.append(tail[o, m - N])
+        got = np.array(got, np.float64)
+        r = {"ms_per_step": ms, "value": macs / (ms / 1e3), "unit": "tap-MAC/s",
+             "realtime_factor": (N / FS) / (ms / 1e3), "kernel_ms_per_step": k_ms, "launches": k_n,
+             "check": {"sampled_outputs": len(got),
+                       "rel_l2": float(np.linalg.norm(got - refs) / np.linalg.norm(refs)),
+                       "max_abs": float(np.max(np.abs(got - refs)))},
+             "tensor_launches": int(info.tensor_launches), "fp32_fallbacks": int(info.fp32_fallbacks)}
+        if name == "fp32":
+            tflops = 2.0 * k_macs / (k_ms / 1e3) / 1e12 if k_ms > 0 else 0.0
+            peak = fp32_peak_tflops(SM_MAX_MHZ)
+            r["roofline"] = {"bound": "alu", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
+                             "frac": tflops / peak, "kernel": "k1_gather (FP32 FMA), 16 inputs per output item"}
         else:
-            got.append(tail[o, m - N])
-        ref.append(sum(oracle.direct_at(w.x[i_], w.H[0, o, i_][None], w.vstart, m) for i_ in range(nin)))
-    got, ref = np.array(got, np.float64), np.array(ref)
-    tflops = 2.0 * k_macs / (k_ms / 1e3) / 1e12 if k_ms > 0 else 0.0
-    peak = fp32_peak_tflops(SM_MAX_MHZ)
+            nprod = 3 if name == "bf16split" else 1
+            tflops = 2.0 * nprod * k_macs / (k_ms / 1e3) / 1e12 if k_ms > 0 else 0.0
+            r["roofline"] = {"bound": "tensor", "achieved": tflops, "peak": bf16_peak, "unit": "TFLOP/s",
+                             "frac": tflops / bf16_peak, "kernel": "k3_mimo (tcgen05 kind::f16) + k3_rev + k3_reduce",
+                             "peak_basis": "measured cuBLAS bf16, sustained (MEASURED_PEAKS.json)",
+                             "flops_counted": f"2 x {nprod} products x useful tap-MACs"}
+        out[name] = r
     del x_d, y_d, tail_d, h_d
     torch.cuda.empty_cache()
-    return {"workload": "MIMO 16 x 16, 60 s @ 48 kHz (2880000 samples per input), L=192000 tau=38400, block 512, "
-                        "pushes of %d, FP32 (K1)" % P,
-            "tap_macs": macs, "ms_per_step": ms, "value": macs / (ms / 1e3), "unit": "tap-MAC/s",
-            "realtime_factor": (N / FS) / (ms / 1e3),
-            "check": {"sampled_outputs": len(got), "rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
-                      "max_abs": float(np.max(np.abs(got - ref)))},
-            "roofline": {"bound": "alu", "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
-                         "kernel": "k1_gather (FP32 FMA), 16 inputs per output item", "k1_launches": k_n}}
+    return out
 
 
 def bench_mono(capi) -> dict:
@@ -841,6 +861,9 @@ def main():
     ap.add_argument("--trace-seconds", type=float, default=15.0)
     ap.add_argument("--no-mimo", action="store_true", help="skip the MIMO section")
     ap.add_argument("--only-mimo", action="store_true", help="run only the MIMO section")
+    ap.add_argument("--mimo-prec", default="bf16split,bf16,fp32", help="MIMO section: precisions")
+    ap.add_argument("--mimo-L", type=int, default=192_000, help="MIMO section: IR length")
+    ap.add_argument("--mimo-seconds", type=float, default=60.0, help="MIMO section: seconds of input")
     ap.add_argument("--shared-C", type=int, default=1024, help="shared-IR section: streams")
     ap.add_argument("--shared-N", type=int, default=240_000, help="shared-IR section: samples per stream")
     ap.add_argument("--shared-prec", default="bf16split,bf16,fp32", help="shared-IR section: precisions")
@@ -875,7 +898,8 @@ def main():
         dist.close()
         return
     if args.only_mimo:
-        print(json.dumps({"mimo": bench_mimo(torch), "mono": bench_mono(capi)}), flush=True)
+        print(json.dumps({"mimo": bench_mimo(torch, precisions=args.mimo_prec.split(","), L=args.mimo_L,
+                                             seconds=args.mimo_seconds), "mono": bench_mono(capi)}), flush=True)
         dist.close()
         return
     if args.only_serving:

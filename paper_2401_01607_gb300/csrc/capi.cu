@@ -157,6 +157,20 @@ struct tc_stream {
     size_t k2_partial_floats = 0;
     long long k2_launches = 0, k1_fallbacks = 0;
 
+    // BF16 tensor-core path for MIMO (K3): reversed bf16 hi/lo inputs of a
+    // launch and, per IR slot, the phase-shifted IR tiles of every pair.
+    void *xr_hi = nullptr, *xr_lo = nullptr;
+    long long xr_pitch = 0;
+    int k3_nkbp = 0;
+    struct K3Set {
+        bool ready = false;
+        void *bh = nullptr, *bl = nullptr;
+        CUtensorMap mb_hi{}, mb_lo{};
+    };
+    std::vector<K3Set> k3sets;  // [slot]
+    float *k3_partial = nullptr;
+    size_t k3_partial_floats = 0;
+
     // Kernel timing (tc_profile).
     bool profile = false;
     std::vector<cudaEvent_t> ev_pool;   // pairs (start, stop)
@@ -201,6 +215,13 @@ void free_all(tc_stream *s)
             cudaFree(t.thi);
             cudaFree(t.tlo);
         }
+    cudaFree(s->xr_hi);
+    cudaFree(s->xr_lo);
+    for (auto &k : s->k3sets) {
+        cudaFree(k.bh);
+        cudaFree(k.bl);
+    }
+    cudaFree(s->k3_partial);
     cudaFree(s->counter);
     cudaFree(s->d_err);
     cudaFreeHost(s->pin_ir);
@@ -258,6 +279,8 @@ tc_status clear_state(tc_stream *s)
     for (auto &arr : s->tsets)
         for (auto &t : arr)
             t.ready = false;
+    for (auto &k : s->k3sets)
+        k.ready = false;
     TC_CU(cudaMemsetAsync(s->counter, 0, s->counter_n * sizeof(unsigned), s->cs));
     TC_CU(cudaMemsetAsync(s->d_err, 0, sizeof(int), s->cs));
     return TC_OK;
@@ -301,7 +324,16 @@ tc_status open_common(tc_stream *s)
     TC_CU(cudaMalloc(&s->partial, s->partial_floats * sizeof(float)));
     TC_CU(cudaMalloc(&s->counter, s->counter_n * sizeof(unsigned)));
     TC_CU(cudaMalloc(&s->d_err, sizeof(int)));
-    if (s->prec != TC_FP32) {
+    if (s->prec != TC_FP32 && s->kind == KIND_MIMO) {
+        // K3 reads reversed bf16 copies of the inputs, made per launch.
+        s->k3_nkbp = tc::k3_kblocks_per_input((long long)s->L);
+        const int tp = tc::k3_tiles_per_cta();
+        const int ntile_max = (int)((s->max_push + 1023) / 1024 + tp - 1) / tp * tp;
+        s->xr_pitch = round_up(tc::k3_xr_span(ntile_max, s->k3_nkbp), 64);
+        TC_CU(cudaMalloc(&s->xr_hi, (size_t)s->nin * s->xr_pitch * 2));
+        TC_CU(cudaMalloc(&s->xr_lo, (size_t)s->nin * s->xr_pitch * 2));
+        s->k3sets.assign((size_t)s->nslots, tc_stream::K3Set{});
+    } else if (s->prec != TC_FP32) {
         TC_CU(cudaMalloc(&s->hist_hi, (size_t)s->rows * s->cap * 2));
         TC_CU(cudaMalloc(&s->hist_lo, (size_t)s->rows * s->cap * 2));
         TC_CU(tc::encode_bf16_2d(&s->mx_hi, s->hist_hi, (unsigned long long)s->cap, s->rows,
@@ -330,8 +362,10 @@ tc_status open_any(int kind, size_t rows, size_t items, size_t nin, size_t nsets
         return fail(TC_EINVAL, "size out of range");
     if (prec != TC_FP32 && prec != TC_BF16 && prec != TC_BF16_SPLIT)
         return fail(TC_EINVAL, "unknown precision %d", (int)prec);
-    if (prec != TC_FP32 && !(kind == KIND_GROUP && shared_ir))
+    if (prec != TC_FP32 && kind == KIND_GROUP && !shared_ir)
         return fail(TC_EUNSUPPORTED, "the BF16 tensor-core path needs one IR shared by all channels");
+    if (prec != TC_FP32 && kind == KIND_MIMO && items > 16)
+        return fail(TC_EUNSUPPORTED, "the BF16 tensor-core MIMO path takes at most 16 outputs");
     tc_stream *s = new (std::nothrow) tc_stream();
     if (!s)
         return fail(TC_ENOMEM, "host allocation failed");
@@ -447,6 +481,8 @@ tc_status set_ir_impl(tc_stream *s, const float *h, size_t n, long long sample, 
     }
     for (auto &t : s->tsets[(size_t)slot])
         t.ready = false;  // the slot gets a new IR: its Toeplitz tiles are stale
+    if ((size_t)slot < s->k3sets.size())
+        s->k3sets[(size_t)slot].ready = false;
     float *dst = s->ir + (size_t)slot * sets * 4 * (size_t)s->Lpad;
     TC_CU(tc::ir_prep_launch(src, src_pitch, (long long)n, (int)sets, dst, 4 * s->Lpad, s->Lpad, s->Lpad, s->cs));
 
@@ -678,9 +714,107 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
     return TC_OK;
 }
 
+// K3 (MIMO on the tensor cores) when every input sample the launch reads
+// spawned its tache with the same IR version; false in *used otherwise.
+tc_status launch_k3(tc_stream *s, long long t0, long long nout, float *y, long long y_pitch, bool *used)
+{
+    *used = false;
+    const long long L = (long long)s->L;
+    const int nkbp = s->k3_nkbp;
+    const int tp = tc::k3_tiles_per_cta();
+    const int ntile = (int)(((nout + 1023) / 1024 + tp - 1) / tp * tp);  // padded tiles compute zeros
+    // Samples read: [t0 + 8 - 32 nkbp, t0 + nout) (later ones are zeroed).
+    const long long lo = t0 + 8 - 32LL * nkbp, hi = t0 + nout;
+    int v = -1;
+    for (size_t i = 0; i < s->vt.size(); ++i)
+        if (s->vt[i].start <= std::max(lo, s->vt.front().start))
+            v = (int)i;
+    if (v < 0)
+        return TC_OK;
+    if ((size_t)v + 1 < s->vt.size() && s->vt[(size_t)v + 1].start < hi)
+        return TC_OK;
+    // k3_rev copies samples [R - span + 1, R], R = t0 + 1024 ntile - 1.
+    if (t0 + 1024LL * ntile - tc::k3_xr_span(ntile, nkbp) < s->base)
+        return fail(TC_EINVAL, "internal: K3 window starts before the kept history");
+    const int slot = s->vt[(size_t)v].slot;
+    tc_stream::K3Set &ks = s->k3sets[(size_t)slot];
+    if (!ks.ready) {
+        const unsigned long long rows = (unsigned long long)s->nin * nkbp * 128;
+        if (!ks.bh) {
+            TC_CU(cudaMalloc(&ks.bh, rows * 32 * 2));
+            TC_CU(cudaMalloc(&ks.bl, rows * 32 * 2));
+            TC_CU(tc::encode_bf16_2d(&ks.mb_hi, ks.bh, 32, rows, 64, 32, 128));
+            TC_CU(tc::encode_bf16_2d(&ks.mb_lo, ks.bl, 32, rows, 64, 32, 128));
+        }
+        const float *ir = s->ir + (size_t)slot * s->nsets * 4 * (size_t)s->Lpad;
+        TC_CU(tc::k3_tprep_launch(ir, 4 * s->Lpad, (int)s->nin, (int)s->items, (int)L, nkbp, ks.bh, ks.bl, s->cs));
+        ks.ready = true;
+    }
+    TC_CU(tc::k3_rev_launch(s->hist, s->cap, s->base, (int)s->nin, t0 + 1024LL * ntile - 1, t0 + nout,
+                            tc::k3_xr_span(ntile, nkbp), s->xr_hi, s->xr_lo, s->xr_pitch, s->cs));
+    tc::K3Params p{};
+    p.nin = (int)s->nin;
+    p.ntile = ntile;
+    p.nkbp = nkbp;
+    p.range = (int)(s->k2_range > 0 ? s->k2_range : (s->prec == TC_BF16_SPLIT ? 16 : 4096));
+    p.range = (p.range + 3) / 4 * 4;  // K3 runs hold whole groups of K blocks (up to four chains)
+    // K parts per tile: the fewest (<= 64) that fill the GPU's waves to >= 90 %,
+    // each a whole number of A chunks.
+    const long long gtot = (long long)s->nin * nkbp;
+    const int kbc = tc::k3_chunk_blocks();
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+    long long nsplit = 1;
+    double best = 0.0;
+    for (long long ns = 1; ns <= 64 && ns * kbc <= gtot; ++ns) {
+        const long long units = (long long)(ntile / tp) * ns;
+        const double eff = (double)units / (double)(((units + sms - 1) / sms) * sms);
+        if (eff > best + 1e-9) {
+            best = eff;
+            nsplit = ns;
+        }
+        if (eff >= 0.9)
+            break;
+    }
+    const long long per = (gtot + nsplit - 1) / nsplit;
+    const long long kb_per = (per + kbc - 1) / kbc * kbc;
+    nsplit = (gtot + kb_per - 1) / kb_per;
+    p.nsplit = (int)nsplit;
+    p.kb_per = (int)kb_per;
+    p.xr_hi = s->xr_hi;
+    p.xr_lo = s->xr_lo;
+    p.xr_pitch = s->xr_pitch;
+    p.err = s->d_err;
+    const size_t need = (size_t)ntile * nsplit * 128 * 128;
+    if (need > s->k3_partial_floats) {
+        TC_CU(cudaStreamSynchronize(s->cs));
+        cudaFree(s->k3_partial);
+        s->k3_partial = nullptr;
+        s->k3_partial_floats = 0;
+        TC_CU(cudaMalloc(&s->k3_partial, need * sizeof(float)));
+        s->k3_partial_floats = need;
+    }
+    p.partial = s->k3_partial;
+    TC_TRY(prof_begin(s));
+    TC_CU(tc::k3_launch(ks.mb_hi, ks.mb_lo, p, s->prec == TC_BF16 ? 1 : 3, y, y_pitch, (int)s->items, (int)nout,
+                        s->cs));
+    TC_TRY(prof_end(s, t0, nout));
+    s->k2_launches++;
+    *used = true;
+    return TC_OK;
+}
+
 // One convolution launch for outputs [t0, t0 + nout) of every row.
 tc_status launch_conv(tc_stream *s, long long t0, long long nout, float *y, long long y_pitch)
 {
+    if (s->prec != TC_FP32 && s->kind == KIND_MIMO) {
+        bool used = false;
+        TC_TRY(launch_k3(s, t0, nout, y, y_pitch, &used));
+        if (used)
+            return TC_OK;
+        s->k1_fallbacks++;
+        return launch_k1(s, t0, nout, y, y_pitch);
+    }
     if (s->prec != TC_FP32) {
         bool used = false;
         TC_TRY(launch_k2(s, t0, nout, y, y_pitch, &used));

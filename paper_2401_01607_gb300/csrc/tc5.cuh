@@ -50,6 +50,20 @@ __device__ __forceinline__ uint64_t umma_desc_sw64(uint32_t smem_addr)
     return d;
 }
 
+// Shared-memory matrix descriptor for a K-major operand without swizzling:
+// core matrices of 8 rows x 16 bytes (each row 16 bytes after the previous),
+// `lbo` bytes apart along K and `sbo` bytes apart along M/N (8-row groups).
+// Layout type 0 (no swizzle). Start, lbo and sbo are multiples of 16 bytes.
+__device__ __forceinline__ uint64_t umma_desc_noswz(uint32_t smem_addr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((smem_addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1u << 46;  // descriptor version
+    return d;                 // bits 61-63 = 0: no swizzle
+}
+
 // Instruction descriptor of tcgen05.mma kind::f16: D f32, A and B bf16, both
 // K-major, M x N. Fields: D format (bits 4-5: 1 = f32), A format (7-9: 1 =
 // bf16), B format (10-12: 1 = bf16), A/B major (15, 16: 0 = K), N >> 3

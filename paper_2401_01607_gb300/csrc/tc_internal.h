@@ -150,6 +150,38 @@ cudaError_t k2_launch_pair(const CUtensorMap &mx_hi, const CUtensorMap &mt_hi, c
 cudaError_t encode_bf16_2d(CUtensorMap *map, const void *base, unsigned long long dim0, unsigned long long dim1,
                            unsigned long long stride1_bytes, unsigned box0, unsigned box1);
 
+// ---------------------------------------------------------------------------
+// K3: MIMO on the tensor cores (k3_mimo_tc.cu). Tiles of 1024 output times
+// (128 rows x 8 phases) x 16 outputs; K = inputs x taps in blocks of 32.
+//   D[r][16 p + o] = sum_i sum_k' xr_i[s0 + 8 r + k'] * B_i[k'][16 p + o],
+//   B_i[k'][16 p + o] = h_{o,i}[k' - p], xr_i[j] = x_i[R - j].
+// ---------------------------------------------------------------------------
+struct K3Params {
+    int nin;                 // inputs
+    int ntile;               // 1024-output tiles of the launch (a multiple of k3_tiles_per_cta)
+    int nkbp;                // K blocks per input (multiple of the chunk)
+    int nsplit, kb_per;      // K parts per tile over nin * nkbp blocks (kb_per a multiple of the chunk)
+    int range;               // K blocks per TMEM run
+    const void *xr_hi, *xr_lo;  // reversed inputs, bf16 [nin][xr_pitch]
+    long long xr_pitch;      // elements, a multiple of 8, >= k3_xr_span
+    float *partial;          // [ntile][nsplit][128][128]
+    int *err;
+};
+int k3_kblocks_per_input(long long L);
+int k3_chunk_blocks();
+int k3_tiles_per_cta();       // ntile of a launch must be a multiple of it
+long long k3_xr_span(int ntile, int nkbp);
+// B tiles of one IR version: ir holds h_{o,i} at (o * nin + i) * set_stride.
+cudaError_t k3_tprep_launch(const float *ir, long long set_stride, int nin, int nout, int L, int nkbp, void *bh,
+                            void *bl, cudaStream_t st);
+// xr_i[j] = x_i[R - j] (0 for samples >= n_end), j < span, bf16 hi/lo.
+cudaError_t k3_rev_launch(const float *hist, long long pitch, long long base, int nin, long long R, long long n_end,
+                          long long span, void *xh, void *xl, long long xr_pitch, cudaStream_t st);
+size_t k3_smem_bytes(int nprod);
+// Runs K3 then the K-part reduction into y[o * y_pitch + j], j < nout, o < nout_ch (<= 16).
+cudaError_t k3_launch(const CUtensorMap &mb_hi, const CUtensorMap &mb_lo, const K3Params &p, int nprod, float *y,
+                      long long y_pitch, int nout_ch, int nout, cudaStream_t st);
+
 // Sets the calling thread's tc_last_error() message.
 void set_last_error(const char *msg);
 

@@ -61,11 +61,13 @@ struct K3Cfg {
     // tile) uses 1 chain per tile, double-buffered.
     static constexpr int CH = NPROD == 1 ? 2 : 1;
     static constexpr int NB = 4 / (K3_TP * CH);
-    // A B stage holds the B tiles of one group of CH K blocks (one full and
-    // one empty barrier per group); 10 stages = 160 KB of B tiles in flight.
+    // A B stage holds the B tiles of one group of GS K blocks (one full and
+    // one empty barrier per group; block j of a group goes to chain j % CH);
+    // 160 KB of B tiles in flight.
+    static constexpr int GS = NPROD == 1 ? 4 : 2;
     static constexpr int BBLK = NPROD == 1 ? K3_BBYTES : 2 * K3_BBYTES;  // one K block (hi[, lo])
-    static constexpr int BSTAGE = CH * BBLK;
-    static constexpr int NS = 10;
+    static constexpr int BSTAGE = GS * BBLK;
+    static constexpr int NS = 160 * 1024 / BSTAGE;
     static constexpr int ASLOT = NPROD == 1 ? K3_ABYTES : 2 * K3_ABYTES;
     static constexpr int AOFF = NS * BSTAGE;                           // A slots after the B ring
     static constexpr int SMEM = AOFF + 2 * ASLOT + 1024;               // + alignment slack
@@ -146,7 +148,7 @@ __global__ void __launch_bounds__(K3_THREADS, 1)
                 bulk_g2s(as, xh + off, (uint32_t)K3_ABYTES, &afull[slot]);
                 if (NPROD == 3)
                     bulk_g2s(as + K3_ABYTES, xl + off, (uint32_t)K3_ABYTES, &afull[slot]);
-                for (int b = 0; b < K3_KBC; b += C::CH, ++i) {  // i counts groups
+                for (int b = 0; b < K3_KBC; b += C::GS, ++i) {  // i counts groups
                     const int st = i % C::NS;
                     const int ub = i / C::NS;
                     if (ub > 0 && !mbar_wait_bounded(&empty[st], (uint32_t)((ub - 1) & 1), p.err, ERR_TIMEOUT_TMA)) {
@@ -157,7 +159,7 @@ __global__ void __launch_bounds__(K3_THREADS, 1)
                     const int row = (int)(((long long)inp * p.nkbp + kb0 + b) * K3_N);
                     mbar_arrive_expect_tx(&full[st], (uint32_t)C::BSTAGE);
 #pragma unroll
-                    for (int j = 0; j < C::CH; ++j) {
+                    for (int j = 0; j < C::GS; ++j) {
                         tma_load_2d(bs + j * C::BBLK, &mb_hi, 0, row + j * K3_N, &full[st]);
                         if (NPROD == 3)
                             tma_load_2d(bs + j * C::BBLK + K3_BBYTES, &mb_lo, 0, row + j * K3_N, &full[st]);
@@ -188,7 +190,7 @@ __global__ void __launch_bounds__(K3_THREADS, 1)
                 }
                 tc_fence_after_sync();
                 const uint64_t adesc0 = umma_desc_noswz(smem_u32(smem + C::AOFF + slot * C::ASLOT), 16, 128);
-                for (int b = 0; b < K3_KBC; b += C::CH, i += C::CH, ++g) {
+                for (int b = 0; b < K3_KBC; b += C::GS, i += C::GS, ++g) {
                     if (i % p.range == 0) {
                         // A new TMEM run in buffer run % NB, once its previous drain is done.
                         const int buf = run % C::NB;
@@ -216,32 +218,35 @@ __global__ void __launch_bounds__(K3_THREADS, 1)
                         // K block b + j starts 64 bytes after block b + j - 1;
                         // tile 2 pair (t = 0) reads 2048 bytes further on.
                         const uint64_t a = adesc0 + (uint64_t)((2 * (b * K3_KB + kk * 16)) >> 4);
-                        const uint32_t accum = (first && kk == 0) ? 0u : 1u;
 #pragma unroll
-                        for (int j = 0; j < C::CH; ++j)
+                        for (int j = 0; j < C::GS; ++j) {
+                            // The first MMA of a chain in a run starts its accumulator.
+                            const uint32_t accum = (first && kk == 0 && j < C::CH) ? 0u : 1u;
+                            const int ch = j % C::CH;
 #pragma unroll
                             for (int t = 0; t < K3_TP; ++t)
-                                umma_bf16(acc + (t * C::CH + j) * K3_N, a + (uint64_t)(j * 4 + (1 - t) * 128),
+                                umma_bf16(acc + (t * C::CH + ch) * K3_N, a + (uint64_t)(j * 4 + (1 - t) * 128),
                                           bst + (uint64_t)((j * C::BBLK + kk * 32) >> 4), idesc, accum);
+                        }
                         if (NPROD == 3) {
 #pragma unroll
-                            for (int j = 0; j < C::CH; ++j)
+                            for (int j = 0; j < C::GS; ++j)
 #pragma unroll
                                 for (int t = 0; t < K3_TP; ++t)
-                                    umma_bf16(acc + (t * C::CH + j) * K3_N, a + (uint64_t)(j * 4 + (1 - t) * 128),
+                                    umma_bf16(acc + (t * C::CH + j % C::CH) * K3_N, a + (uint64_t)(j * 4 + (1 - t) * 128),
                                               bst + (uint64_t)((j * C::BBLK + K3_BBYTES + kk * 32) >> 4), idesc, 1u);
 #pragma unroll
-                            for (int j = 0; j < C::CH; ++j)
+                            for (int j = 0; j < C::GS; ++j)
 #pragma unroll
                                 for (int t = 0; t < K3_TP; ++t)
-                                    umma_bf16(acc + (t * C::CH + j) * K3_N,
+                                    umma_bf16(acc + (t * C::CH + j % C::CH) * K3_N,
                                               a + (uint64_t)(j * 4 + (1 - t) * 128 + (K3_ABYTES >> 4)),
                                               bst + (uint64_t)((j * C::BBLK + kk * 32) >> 4), idesc, 1u);
                         }
                     }
                     first = false;
                     umma_commit(&empty[st]);
-                    if ((i + C::CH) % p.range == 0 || i + C::CH == nk) {
+                    if ((i + C::GS) % p.range == 0 || i + C::GS == nk) {
                         umma_commit(&accfull[run % C::NB]);  // the run is complete in TMEM
                         ++run;
                     }

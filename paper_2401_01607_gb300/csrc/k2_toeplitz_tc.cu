@@ -50,10 +50,17 @@ constexpr int K2_TBYTES = K2_N * K2_KB * 2;  // 16 KB
 
 template <int NPROD>
 struct K2Cfg {
-    static constexpr int NS = NPROD == 1 ? 8 : 4;  // stages
     static constexpr int XOFF_LO = K2_XBYTES;       // X_lo after X_hi (split only)
     static constexpr int TOFF = NPROD == 1 ? K2_XBYTES : 2 * K2_XBYTES;
-    static constexpr int STAGE = NPROD == 1 ? K2_XBYTES + K2_TBYTES : 2 * (K2_XBYTES + K2_TBYTES);
+    static constexpr int BLK = NPROD == 1 ? K2_XBYTES + K2_TBYTES : 2 * (K2_XBYTES + K2_TBYTES);  // one K block
+    // A pipeline stage holds GS consecutive K blocks (one full and one empty
+    // barrier per stage). A K block of a 128 x 256 tile already carries 2 or
+    // 6 MMAs of 128 x 256 x 16, and a deeper ring of one-block stages
+    // measured faster here than fewer two-block stages (the split: 72 % vs
+    // 58 % of peak).
+    static constexpr int GS = 1;
+    static constexpr int STAGE = GS * BLK;
+    static constexpr int NS = NPROD == 1 ? 8 : 4;   // stages
     static constexpr int SMEM = NS * STAGE + 1024;  // + alignment slack
 };
 
@@ -113,30 +120,34 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
     if (warp == 0) {
         if (lane == 0) {
             // ---- producer ----
-            for (int i = 0; i < nk && !s_fail; ++i) {
-                const int st = i % C::NS;
-                const int use = i / C::NS;
+            for (int gi = 0; gi * C::GS < nk && !s_fail; ++gi) {
+                const int st = gi % C::NS;
+                const int use = gi / C::NS;
                 if (use > 0 && !mbar_wait_bounded(&empty[st], (uint32_t)((use - 1) & 1), p.err, ERR_TIMEOUT_TMA)) {
                     s_fail = 1;
                     break;
                 }
-                uint8_t *sb = smem + st * C::STAGE;
-                const int kb = kb0 + i;
-                mbar_arrive_expect_tx(&full[st], (uint32_t)C::STAGE);
-                const int xc = (int)(xcol0 + (long long)kb * K2_KB);
-                tma_load_2d(sb, &mx_hi, xc, c0, &full[st]);
-                if (NPROD == 3)
-                    tma_load_2d(sb + C::XOFF_LO, &mx_lo, xc, c0, &full[st]);
-                tma_load_2d(sb + C::TOFF, &mt_hi, 0, kb * K2_N, &full[st]);
-                if (NPROD == 3)
-                    tma_load_2d(sb + C::TOFF + K2_TBYTES, &mt_lo, 0, kb * K2_N, &full[st]);
+                const int nb = min(C::GS, nk - gi * C::GS);  // K blocks in this stage
+                mbar_arrive_expect_tx(&full[st], (uint32_t)(nb * C::BLK));
+                for (int j = 0; j < nb; ++j) {
+                    uint8_t *sb = smem + st * C::STAGE + j * C::BLK;
+                    const int kb = kb0 + gi * C::GS + j;
+                    const int xc = (int)(xcol0 + (long long)kb * K2_KB);
+                    tma_load_2d(sb, &mx_hi, xc, c0, &full[st]);
+                    if (NPROD == 3)
+                        tma_load_2d(sb + C::XOFF_LO, &mx_lo, xc, c0, &full[st]);
+                    tma_load_2d(sb + C::TOFF, &mt_hi, 0, kb * K2_N, &full[st]);
+                    if (NPROD == 3)
+                        tma_load_2d(sb + C::TOFF + K2_TBYTES, &mt_lo, 0, kb * K2_N, &full[st]);
+                }
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
             // ---- MMA issuer ----
+            // Runs are whole stages (range is a multiple of GS).
             const uint32_t idesc = umma_idesc_bf16(K2_M, K2_N);
-            int i = 0;
+            int gi = 0;
             for (int r = 0; r < nr && !s_fail; ++r) {
                 const int buf = r & 1;
                 const int reuse = r >> 1;  // earlier runs in this buffer
@@ -148,25 +159,28 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
                 tc_fence_after_sync();
                 const uint32_t acc = tmem + (uint32_t)(buf * K2_N);
                 const int iend = min(nk, (r + 1) * p.range);
-                for (int first = 1; i < iend; ++i, first = 0) {
-                    const int st = i % C::NS;
-                    if (!mbar_wait_bounded(&full[st], (uint32_t)((i / C::NS) & 1), p.err, ERR_TIMEOUT_MMA)) {
+                for (bool first = true; gi * C::GS < iend; ++gi) {
+                    const int st = gi % C::NS;
+                    if (!mbar_wait_bounded(&full[st], (uint32_t)((gi / C::NS) & 1), p.err, ERR_TIMEOUT_MMA)) {
                         s_fail = 1;
                         break;
                     }
                     tc_fence_after_sync();
-                    const uint32_t sb = smem_u32(smem + st * C::STAGE);
+                    const int nb = min(C::GS, nk - gi * C::GS);
+                    for (int j = 0; j < nb; ++j, first = false) {
+                        const uint32_t sb = smem_u32(smem + st * C::STAGE + j * C::BLK);
 #pragma unroll
-                    for (int kk = 0; kk < K2_KB / 16; ++kk) {
-                        const uint32_t koff = kk * 32;  // 16 bf16 = 32 bytes along the swizzled row
-                        const uint64_t xh = umma_desc_sw64(sb + koff);
-                        const uint64_t th = umma_desc_sw64(sb + C::TOFF + koff);
-                        umma_bf16(acc, xh, th, idesc, (first && kk == 0) ? 0u : 1u);
-                        if (NPROD == 3) {
-                            const uint64_t xl = umma_desc_sw64(sb + C::XOFF_LO + koff);
-                            const uint64_t tl = umma_desc_sw64(sb + C::TOFF + K2_TBYTES + koff);
-                            umma_bf16(acc, xh, tl, idesc, 1u);
-                            umma_bf16(acc, xl, th, idesc, 1u);
+                        for (int kk = 0; kk < K2_KB / 16; ++kk) {
+                            const uint32_t koff = kk * 32;  // 16 bf16 = 32 bytes along the swizzled row
+                            const uint64_t xh = umma_desc_sw64(sb + koff);
+                            const uint64_t th = umma_desc_sw64(sb + C::TOFF + koff);
+                            umma_bf16(acc, xh, th, idesc, (first && kk == 0) ? 0u : 1u);
+                            if (NPROD == 3) {
+                                const uint64_t xl = umma_desc_sw64(sb + C::XOFF_LO + koff);
+                                const uint64_t tl = umma_desc_sw64(sb + C::TOFF + K2_TBYTES + koff);
+                                umma_bf16(acc, xh, tl, idesc, 1u);
+                                umma_bf16(acc, xl, th, idesc, 1u);
+                            }
                         }
                     }
                     umma_commit(&empty[st]);  // the stage is free once these MMAs are done
@@ -269,8 +283,10 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
 // unit (the K range fits one FP32 accumulation, as plain BF16 is limited by
 // its operands, not by the run length); two accumulators of 256 columns. The
 // epilogue writes TMEM straight to y (or to the K-part partials).
+constexpr int K2P_BLK = 2 * K2_XBYTES + K2_TBYTES;  // one K block: X tile a, X tile b, T
+constexpr int K2P_GS = 1;                             // K blocks per pipeline stage
+constexpr int K2P_STAGE = K2P_GS * K2P_BLK;
 constexpr int K2P_NS = 6;
-constexpr int K2P_STAGE = 2 * K2_XBYTES + K2_TBYTES;  // X tile a, X tile b, T
 constexpr int K2P_SMEM = K2P_NS * K2P_STAGE + 1024;
 
 __global__ void __launch_bounds__(K2_THREADS, 1)
@@ -320,41 +336,47 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
     if (warp == 0) {
         if (lane == 0) {
             // ---- producer ----
-            for (int i = 0; i < nk && !s_fail; ++i) {
-                const int st = i % K2P_NS;
-                const int use = i / K2P_NS;
+            for (int gi = 0; gi * K2P_GS < nk && !s_fail; ++gi) {
+                const int st = gi % K2P_NS;
+                const int use = gi / K2P_NS;
                 if (use > 0 && !mbar_wait_bounded(&empty[st], (uint32_t)((use - 1) & 1), p.err, ERR_TIMEOUT_TMA)) {
                     s_fail = 1;
                     break;
                 }
-                uint8_t *sb = smem + st * K2P_STAGE;
-                const int kb = kb0 + i;
-                mbar_arrive_expect_tx(&full[st], (uint32_t)K2P_STAGE);
-                const int xc = (int)(xcol0 + (long long)kb * K2_KB);
-                tma_load_2d(sb, &mx_hi, xc, c0, &full[st]);
-                tma_load_2d(sb + K2_XBYTES, &mx_hi, xc, c0 + K2_M, &full[st]);
-                tma_load_2d(sb + 2 * K2_XBYTES, &mt_hi, 0, kb * K2_N, &full[st]);
+                const int nb = min(K2P_GS, nk - gi * K2P_GS);
+                mbar_arrive_expect_tx(&full[st], (uint32_t)(nb * K2P_BLK));
+                for (int j = 0; j < nb; ++j) {
+                    uint8_t *sb = smem + st * K2P_STAGE + j * K2P_BLK;
+                    const int kb = kb0 + gi * K2P_GS + j;
+                    const int xc = (int)(xcol0 + (long long)kb * K2_KB);
+                    tma_load_2d(sb, &mx_hi, xc, c0, &full[st]);
+                    tma_load_2d(sb + K2_XBYTES, &mx_hi, xc, c0 + K2_M, &full[st]);
+                    tma_load_2d(sb + 2 * K2_XBYTES, &mt_hi, 0, kb * K2_N, &full[st]);
+                }
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
             // ---- MMA issuer ----
             const uint32_t idesc = umma_idesc_bf16(K2_M, K2_N);
-            for (int i = 0; i < nk; ++i) {
-                const int st = i % K2P_NS;
-                if (!mbar_wait_bounded(&full[st], (uint32_t)((i / K2P_NS) & 1), p.err, ERR_TIMEOUT_MMA)) {
+            for (int gi = 0; gi * K2P_GS < nk; ++gi) {
+                const int st = gi % K2P_NS;
+                if (!mbar_wait_bounded(&full[st], (uint32_t)((gi / K2P_NS) & 1), p.err, ERR_TIMEOUT_MMA)) {
                     s_fail = 1;
                     break;
                 }
                 tc_fence_after_sync();
-                const uint32_t sb = smem_u32(smem + st * K2P_STAGE);
+                const int nb = min(K2P_GS, nk - gi * K2P_GS);
+                for (int j = 0; j < nb; ++j) {
+                    const uint32_t sb = smem_u32(smem + st * K2P_STAGE + j * K2P_BLK);
 #pragma unroll
-                for (int kk = 0; kk < K2_KB / 16; ++kk) {
-                    const uint32_t koff = kk * 32;
-                    const uint64_t th = umma_desc_sw64(sb + 2 * K2_XBYTES + koff);
-                    const uint32_t accum = (i == 0 && kk == 0) ? 0u : 1u;
-                    umma_bf16(tmem, umma_desc_sw64(sb + koff), th, idesc, accum);
-                    umma_bf16(tmem + K2_N, umma_desc_sw64(sb + K2_XBYTES + koff), th, idesc, accum);
+                    for (int kk = 0; kk < K2_KB / 16; ++kk) {
+                        const uint32_t koff = kk * 32;
+                        const uint64_t th = umma_desc_sw64(sb + 2 * K2_XBYTES + koff);
+                        const uint32_t accum = (gi == 0 && j == 0 && kk == 0) ? 0u : 1u;
+                        umma_bf16(tmem, umma_desc_sw64(sb + koff), th, idesc, accum);
+                        umma_bf16(tmem + K2_N, umma_desc_sw64(sb + K2_XBYTES + koff), th, idesc, accum);
+                    }
                 }
                 umma_commit(&empty[st]);
             }
@@ -572,7 +594,8 @@ cudaError_t k2_launch(const CUtensorMap &mx_hi, const CUtensorMap &mx_lo, const 
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess)
         return e;
-    if (dev < 0 || dev >= 64 || (nprod != 1 && nprod != 3) || p.nsplit < 1 || p.nsplit > 64 || p.range < 1)
+    if (dev < 0 || dev >= 64 || (nprod != 1 && nprod != 3) || p.nsplit < 1 || p.nsplit > 64 || p.range < 1 ||
+        p.range % K2Cfg<1>::GS != 0)
         return cudaErrorInvalidValue;
     const int vi = nprod == 1 ? 0 : 1;
     const size_t smem = k2_smem_bytes(nprod);

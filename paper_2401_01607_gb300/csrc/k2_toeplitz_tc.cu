@@ -147,6 +147,8 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
             // ---- MMA issuer ----
             // Runs are whole stages (range is a multiple of GS).
             const uint32_t idesc = umma_idesc_bf16(K2_M, K2_N);
+            // Descriptors advance by adding byte offsets >> 4 to the start field.
+            const uint64_t d0 = umma_desc_sw64(smem_u32(smem));
             int gi = 0;
             for (int r = 0; r < nr && !s_fail; ++r) {
                 const int buf = r & 1;
@@ -168,16 +170,16 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
                     tc_fence_after_sync();
                     const int nb = min(C::GS, nk - gi * C::GS);
                     for (int j = 0; j < nb; ++j, first = false) {
-                        const uint32_t sb = smem_u32(smem + st * C::STAGE + j * C::BLK);
+                        const uint64_t sd = d0 + (uint64_t)((st * C::STAGE + j * C::BLK) >> 4);
 #pragma unroll
                         for (int kk = 0; kk < K2_KB / 16; ++kk) {
-                            const uint32_t koff = kk * 32;  // 16 bf16 = 32 bytes along the swizzled row
-                            const uint64_t xh = umma_desc_sw64(sb + koff);
-                            const uint64_t th = umma_desc_sw64(sb + C::TOFF + koff);
+                            // 16 bf16 = 32 bytes along the swizzled row.
+                            const uint64_t xh = sd + (uint64_t)(kk * 2);
+                            const uint64_t th = sd + (uint64_t)((C::TOFF + kk * 32) >> 4);
                             umma_bf16(acc, xh, th, idesc, (first && kk == 0) ? 0u : 1u);
                             if (NPROD == 3) {
-                                const uint64_t xl = umma_desc_sw64(sb + C::XOFF_LO + koff);
-                                const uint64_t tl = umma_desc_sw64(sb + C::TOFF + K2_TBYTES + koff);
+                                const uint64_t xl = sd + (uint64_t)((C::XOFF_LO + kk * 32) >> 4);
+                                const uint64_t tl = sd + (uint64_t)((C::TOFF + K2_TBYTES + kk * 32) >> 4);
                                 umma_bf16(acc, xh, tl, idesc, 1u);
                                 umma_bf16(acc, xl, th, idesc, 1u);
                             }
@@ -359,6 +361,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
         if (lane == 0) {
             // ---- MMA issuer ----
             const uint32_t idesc = umma_idesc_bf16(K2_M, K2_N);
+            const uint64_t d0 = umma_desc_sw64(smem_u32(smem));
             for (int gi = 0; gi * K2P_GS < nk; ++gi) {
                 const int st = gi % K2P_NS;
                 if (!mbar_wait_bounded(&full[st], (uint32_t)((gi / K2P_NS) & 1), p.err, ERR_TIMEOUT_MMA)) {
@@ -368,14 +371,13 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
                 tc_fence_after_sync();
                 const int nb = min(K2P_GS, nk - gi * K2P_GS);
                 for (int j = 0; j < nb; ++j) {
-                    const uint32_t sb = smem_u32(smem + st * K2P_STAGE + j * K2P_BLK);
+                    const uint64_t sd = d0 + (uint64_t)((st * K2P_STAGE + j * K2P_BLK) >> 4);
 #pragma unroll
                     for (int kk = 0; kk < K2_KB / 16; ++kk) {
-                        const uint32_t koff = kk * 32;
-                        const uint64_t th = umma_desc_sw64(sb + 2 * K2_XBYTES + koff);
+                        const uint64_t th = sd + (uint64_t)((2 * K2_XBYTES + kk * 32) >> 4);
                         const uint32_t accum = (gi == 0 && j == 0 && kk == 0) ? 0u : 1u;
-                        umma_bf16(tmem, umma_desc_sw64(sb + koff), th, idesc, accum);
-                        umma_bf16(tmem + K2_N, umma_desc_sw64(sb + K2_XBYTES + koff), th, idesc, accum);
+                        umma_bf16(tmem, sd + (uint64_t)(kk * 2), th, idesc, accum);
+                        umma_bf16(tmem + K2_N, sd + (uint64_t)((K2_XBYTES + kk * 32) >> 4), th, idesc, accum);
                     }
                 }
                 umma_commit(&empty[st]);

@@ -162,6 +162,63 @@ def oracle_baseline(cores: int, nsamp: int) -> dict:
             "cpu_seconds": float(sum(times))}
 
 
+def _oracle_job(args):
+    """One bounded oracle job of another workload; returns (seconds, tap-MACs)."""
+    kind, a, b = args
+    sys.path.insert(0, ROOT)
+    import oracle
+    from paper_2401_01607_gb300 import synth as sy
+    o = oracle.Oracle()
+    if kind == "warm":  # starts the worker and loads the oracle library
+        return 0.0, 0
+    if kind == "mono":
+        w = sy.mono()
+        t0 = time.perf_counter()
+        o.buffer(w.x[0], w.H[0], w.vstart, w.block)
+        return time.perf_counter() - t0, w.N * w.L
+    if kind == "shared":  # stream a of the shared-IR workload, first b samples
+        L = 96_000
+        x = sy.audio(b, sy.x_seed(3, a))
+        h = sy.decayed_ir(L, 0.2 * L, sy.ir_seed(0, 0))
+        t0 = time.perf_counter()
+        o.buffer(x, h[None], np.zeros(1, np.int64), 256)
+        return time.perf_counter() - t0, b * L
+    # mimo: pair a = (output, input) of the MIMO workload, first b samples
+    L, nin = 192_000, 16
+    out_, inp = divmod(a, nin)
+    x = sy.audio(b, sy.x_seed(5, 0) + inp)
+    h = sy.decayed_ir(L, 0.2 * L, sy.ir_seed(out_ * nin + inp, 0))
+    t0 = time.perf_counter()
+    o.buffer(x, h[None], np.zeros(1, np.int64), 512)
+    return time.perf_counter() - t0, b * L
+
+
+def oracle_other_workloads(cores: int) -> dict:
+    """The FP64 oracle timed on bounded samples of the mono, shared-IR and MIMO
+    workloads, jobs spread over the host cores (spawned before any CUDA call)."""
+    import oracle
+    oracle.build()
+    ctx = mp.get_context("spawn")
+    out = {}
+    plans = {"mono": ([("mono", 0, 0)], "the whole mono workload (48000 samples, L=4096), one core"),
+             "shared_ir": ([("shared", s_, 24_000) for s_ in range(16)],
+                           "16 of the 1024 shared-IR streams, first 24000 samples each (L=96000), one stream per core"),
+             "mimo": ([("mimo", a, 4_800) for a in (0 * 16 + i for i in range(16))] +
+                      [("mimo", a, 4_800) for a in (15 * 16 + i for i in range(16))],
+                      "2 of the 16 MIMO outputs (all 16 inputs each), first 4800 samples (L=192000), "
+                      "32 pair jobs over the cores")}
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_job, [("warm", 0, 0)] * cores)
+        for name, (jobs, desc) in plans.items():
+            t0 = time.perf_counter()
+            res = pool.map(_oracle_job, jobs)
+            wall = time.perf_counter() - t0
+            macs = sum(m for _, m in res)
+            out[name] = {"value": macs / wall, "unit": "tap-MAC/s", "cores": min(cores, len(jobs)), "kind": "oracle",
+                         "sample": desc + f"; pool wall {wall:.2f} s", "cpu_seconds": float(sum(t for t, _ in res))}
+    return out
+
+
 def cpu_model() -> str:
     try:
         with open("/proc/cpuinfo") as f:
@@ -880,9 +937,12 @@ def main():
 
     # CPU baseline first: the spawned oracle workers start before any CUDA call.
     cpu = None
+    cpu_other = {}
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu:
         cpu = oracle_baseline(os.cpu_count() or 1, args.cpu_samples)
         cpu["cpu_model"] = cpu_model()
+        if not (args.only_shared or args.only_serving):
+            cpu_other = oracle_other_workloads(os.cpu_count() or 1)
 
     import torch
     import paper_2401_01607_gb300 as pkg
@@ -898,8 +958,11 @@ def main():
         dist.close()
         return
     if args.only_mimo:
-        print(json.dumps({"mimo": bench_mimo(torch, precisions=args.mimo_prec.split(","), L=args.mimo_L,
-                                             seconds=args.mimo_seconds), "mono": bench_mono(capi)}), flush=True)
+        mimo = bench_mimo(torch, precisions=args.mimo_prec.split(","), L=args.mimo_L, seconds=args.mimo_seconds)
+        mono = bench_mono(capi)
+        if cpu_other:
+            mimo["cpu_baseline"], mono["cpu_baseline"] = cpu_other["mimo"], cpu_other["mono"]
+        print(json.dumps({"mimo": mimo, "mono": mono}), flush=True)
         dist.close()
         return
     if args.only_serving:
@@ -1028,10 +1091,14 @@ def main():
     shared = None
     if not args.no_shared and dist.world == 1:
         shared = bench_shared(torch, steps=2, warmup=1)
+        if cpu_other:
+            shared["cpu_baseline"] = cpu_other["shared_ir"]
     mimo = mono = None
     if not args.no_mimo and dist.world == 1:
         mimo = bench_mimo(torch)
         mono = bench_mono(capi)
+        if cpu_other:
+            mimo["cpu_baseline"], mono["cpu_baseline"] = cpu_other["mimo"], cpu_other["mono"]
     serving = None
     if not args.no_serving and dist.world == 1:
         serving = bench_serving(torch, capi, np.ascontiguousarray(w.H[:, 0]), args.trace_seconds)

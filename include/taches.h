@@ -344,6 +344,18 @@ tc_status tc_server_get_stats(tc_server *srv, tc_server_stats *st);
 tc_status tc_server_latencies(tc_server *srv, double *out, uint32_t *block, size_t cap, size_t *n_out);
 /* Monotonic clock of the poll timestamps (seconds). */
 double tc_server_clock(void);
+/* Options (value 0 or 1), set at any time:
+ *   TC_SERVER_AUTOTUNE  (default 1) pick the gather's tap chunk per step class
+ *                       (magnitudes of the step's work and longest IR) by
+ *                       measured time: each chunk is tried twice per class,
+ *                       then the fastest is used; 0 = fixed rule (largest
+ *                       chunk with >= 4 waves and < 10 % padding).
+ *   TC_SERVER_GRAPH     (default 0) replay each step as one CUDA graph
+ *                       (copies, ingest, gather and its timing events) whose
+ *                       node parameters are updated per step, instead of
+ *                       separate stream operations. */
+enum { TC_SERVER_AUTOTUNE = 0, TC_SERVER_GRAPH = 1 };
+tc_status tc_server_set_option(tc_server *srv, int option, int value);
 /* Step log (tracing): one record per step, the last 65536 steps kept. */
 typedef struct tc_server_step_rec {
     double t_begin;      /* step start (tc_server_clock) */

@@ -98,6 +98,7 @@ _SIGS = {
     "tc_server_attach_source": [_vp, _u64, _vp, _sz, ctypes.c_double, ctypes.c_double],
     "tc_server_stream_state": [_vp, _u64, ctypes.POINTER(_int)],
     "tc_server_step_log": [_vp, _vp, _sz, ctypes.POINTER(_sz)],
+    "tc_server_set_option": [_vp, _int, _int],
 }
 
 
@@ -313,6 +314,11 @@ def tc_kernel_launches() -> int:
 # ---------------------------------------------------------------------------
 
 TC_SERVER_DISCARD_OUTPUT = 1
+TC_SERVER_AUTOTUNE, TC_SERVER_GRAPH = 0, 1
+
+
+def tc_server_set_option(srv: int, option: int, value: int) -> None:
+    _call("tc_server_set_option", srv, int(option), int(value))
 
 
 def tc_server_open(mem_budget_bytes: int, max_step_samples: int = 0) -> int:

@@ -531,6 +531,19 @@ cudaError_t k1_launch(K1Params &p, const K1Plan &plan, cudaStream_t st)
     return cudaGetLastError();
 }
 
+const void *k1_list_kernel(int variant, size_t *smem)
+{
+    DevInfo *d = nullptr;
+    if (device_info(&d) != cudaSuccess)
+        return nullptr;
+    switch (variant) {
+    case K1_P1: *smem = smem_bytes<1>(); return reinterpret_cast<const void *>(&k1_gather<1, true>);
+    case K1_P4: *smem = smem_bytes<4>(); return reinterpret_cast<const void *>(&k1_gather<4, true>);
+    case K1_P11: *smem = smem_bytes<K1_PBIG>(); return reinterpret_cast<const void *>(&k1_gather<K1_PBIG, true>);
+    default: return nullptr;
+    }
+}
+
 cudaError_t k1_launch_list(const K1Params *d_items, const long long *d_cta_begin, int nitems, long long total_ctas,
                            int variant, cudaStream_t st)
 {

@@ -22,6 +22,7 @@
 // briefly; steps take the state mutex while packing and delivering.
 #include <algorithm>
 #include <atomic>
+#include <cmath>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -43,6 +44,8 @@ namespace {
 constexpr int kMaxVer = 16;
 constexpr int kMerge = 8;  // consecutive blocks of one stream merged into one work item
 constexpr size_t kLogSteps = 1 << 16;
+constexpr int kTuneTries = 2;
+constexpr int kTuneWorkBins = 48, kTuneLBins = 24;
 // Chunk-tasks per tile stay within K1's pairwise stack with the smallest chunk.
 constexpr size_t kMaxL = (size_t)tc::K1_MAX_CHUNK_TASKS * 32 * tc::K1_SEG - 8;
 
@@ -156,7 +159,33 @@ struct tc_server {
         double t_begin = 0.0, t_launch = 0.0;
         long long ctas = 0;
         int variant = 0;
+        cudaEvent_t k1_start = nullptr, k1_stop = nullptr;  // timing of the gather (autotuner)
+        int tune_key = -1;
+        double tune_work = 0.0;
     } buf[2];
+
+    // Autotuner of the gather's chunk variant: per step class (magnitude of
+    // the step's tap-MACs, magnitude of its longest IR), the best measured
+    // time per tap-MAC of each variant; each variant is tried kTuneTries
+    // times per class, then the fastest is used.
+    struct Tune {
+        float best[tc::K1_NVARIANTS];
+        uint8_t tries[tc::K1_NVARIANTS];
+    };
+    std::vector<Tune> tune;
+    bool autotune = true;
+
+    // CUDA-graph replay of a step: per chunk variant, a graph of
+    // [H2D copy] -> [ingest] -> [event] -> [gather] -> [event] -> [D2H copy]
+    // whose nodes get each step's sizes, grids, arguments and events. The
+    // source graph stays alive: node updates name its nodes.
+    struct StepGraph {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        cudaGraphNode_t h2d, ingest, ev0, k1, ev1, d2h;
+    };
+    StepGraph graphs[tc::K1_NVARIANTS];
+    bool use_graph = false;
     // Shared device buffers (steps run in order on the step stream).
     char *d_stage = nullptr;
     size_t d_stage_items = 0;
@@ -528,6 +557,59 @@ size_t collect(tc_server *srv, tc_server::StepBuf &b)
     return nblocks;
 }
 
+// Builds (once per chunk variant) and replays the step graph with this
+// step's copies, grids, arguments and timing events. Parameter updates do
+// not touch launches already enqueued.
+tc_status graph_launch(tc_server *srv, tc_server::StepBuf &b, int variant, size_t in_bytes, const float *a_in,
+                       const long long *a_sc, float *const *a_dst, int ni, const tc::K1Params *a_items,
+                       const long long *a_cta, long long ctas, size_t out_bytes)
+{
+    tc_server::StepGraph &g = srv->graphs[variant];
+    size_t k1_smem = 0;
+    const void *k1_fn = tc::k1_list_kernel(variant, &k1_smem);
+    if (!k1_fn)
+        return sfail(TC_ECUDA, "tc_server: no gather kernel for the variant");
+    tc::K1Params none{};
+    int nlist = ni;
+    void *k1_args[4] = {&none, &a_items, &a_cta, &nlist};
+    void *in_args[4] = {&a_in, &a_sc, &a_dst, &nlist};
+    cudaKernelNodeParams kin{};
+    kin.func = reinterpret_cast<void *>(&ingest_kernel);
+    kin.gridDim = dim3((unsigned)ni);
+    kin.blockDim = dim3(256);
+    kin.kernelParams = in_args;
+    cudaKernelNodeParams kk{};
+    kk.func = const_cast<void *>(k1_fn);
+    kk.gridDim = dim3((unsigned)ctas);
+    kk.blockDim = dim3(tc::K1_THREADS);
+    kk.sharedMemBytes = (unsigned)k1_smem;
+    kk.kernelParams = k1_args;
+    if (!g.exec) {
+        S_CU(cudaGraphCreate(&g.graph, 0));
+        S_CU(cudaGraphAddMemcpyNode1D(&g.h2d, g.graph, nullptr, 0, srv->d_stage, b.pin_stage, in_bytes,
+                                      cudaMemcpyHostToDevice));
+        S_CU(cudaGraphAddKernelNode(&g.ingest, g.graph, &g.h2d, 1, &kin));
+        S_CU(cudaGraphAddEventRecordNode(&g.ev0, g.graph, &g.ingest, 1, b.k1_start));
+        S_CU(cudaGraphAddKernelNode(&g.k1, g.graph, &g.ev0, 1, &kk));
+        S_CU(cudaGraphAddEventRecordNode(&g.ev1, g.graph, &g.k1, 1, b.k1_stop));
+        S_CU(cudaGraphAddMemcpyNode1D(&g.d2h, g.graph, &g.ev1, 1, b.pin_out, srv->d_out, out_bytes,
+                                      cudaMemcpyDeviceToHost));
+        S_CU(cudaGraphInstantiate(&g.exec, g.graph, 0));
+    } else {
+        S_CU(cudaGraphExecMemcpyNodeSetParams1D(g.exec, g.h2d, srv->d_stage, b.pin_stage, in_bytes,
+                                                cudaMemcpyHostToDevice));
+        S_CU(cudaGraphExecKernelNodeSetParams(g.exec, g.ingest, &kin));
+        S_CU(cudaGraphExecEventRecordNodeSetEvent(g.exec, g.ev0, b.k1_start));
+        S_CU(cudaGraphExecKernelNodeSetParams(g.exec, g.k1, &kk));
+        S_CU(cudaGraphExecEventRecordNodeSetEvent(g.exec, g.ev1, b.k1_stop));
+        S_CU(cudaGraphExecMemcpyNodeSetParams1D(g.exec, g.d2h, b.pin_out, srv->d_out, out_bytes,
+                                                cudaMemcpyDeviceToHost));
+    }
+    S_CU(cudaGraphLaunch(g.exec, srv->cs));
+    tc::count_launch(2);
+    return TC_OK;
+}
+
 // Packs step buffer b and enqueues its copies and kernels on the step stream
 // (no wait). Caller holds mu_state. Advances each stream's launch position.
 tc_status pack_launch(tc_server *srv, tc_server::StepBuf &b)
@@ -550,6 +632,33 @@ tc_status pack_launch(tc_server *srv, tc_server::StepBuf &b)
             variant = v;
             break;
         }
+    }
+    b.tune_key = -1;
+    if (srv->autotune) {
+        // Step class: magnitudes of the step's tap-MACs and of its longest IR.
+        double work = 0.0;
+        long long maxL = 1;
+        for (auto &w : b.items) {
+            work += (double)w.n * (double)w.s->L;
+            maxL = std::max(maxL, w.s->L);
+        }
+        const int wb = std::min(kTuneWorkBins - 1, (int)std::log2(std::max(work, 1.0)));
+        const int lb = std::min(kTuneLBins - 1, (int)std::log2((double)maxL));
+        const int key = wb * kTuneLBins + lb;
+        const tc_server::Tune &t = srv->tune[(size_t)key];
+        int pick = -1;
+        for (int v = 0; v < tc::K1_NVARIANTS && pick < 0; ++v)
+            if (t.tries[v] < kTuneTries)
+                pick = v;  // still exploring this class
+        if (pick < 0) {
+            pick = variant;
+            for (int v = 0; v < tc::K1_NVARIANTS; ++v)
+                if (t.best[v] < t.best[pick])
+                    pick = v;
+        }
+        variant = pick;
+        b.tune_key = key;
+        b.tune_work = work;
     }
     const long long kc = tc::k1_chunk_taps(variant);
     size_t scratch = 0, ctrs = 0;
@@ -651,15 +760,26 @@ tc_status pack_launch(tc_server *srv, tc_server::StepBuf &b)
     b.t_launch = now_s();
     b.ctas = cta;
     b.variant = variant;
-    S_CU(cudaMemcpyAsync(ds, b.pin_stage, lay.end, cudaMemcpyHostToDevice, srv->cs));
-    ingest_kernel<<<(unsigned)ni, 256, 0, srv->cs>>>(reinterpret_cast<const float *>(ds + lay.in),
-                                                       reinterpret_cast<const long long *>(ds + lay.sc),
-                                                       reinterpret_cast<float *const *>(ds + lay.dst), ni);
-    tc::count_launch();
-    S_CU(cudaGetLastError());
-    S_CU(tc::k1_launch_list(reinterpret_cast<const tc::K1Params *>(ds + lay.items),
-                            reinterpret_cast<const long long *>(ds + lay.cta), ni, cta, variant, srv->cs));
-    S_CU(cudaMemcpyAsync(b.pin_out, srv->d_out, (4 + b.total) * sizeof(float), cudaMemcpyDeviceToHost, srv->cs));
+    if (cta > 0x7fffffffLL)
+        return sfail(TC_EINVAL, "tc_server: internal: gather grid too large");
+    const float *a_in = reinterpret_cast<const float *>(ds + lay.in);
+    const long long *a_sc = reinterpret_cast<const long long *>(ds + lay.sc);
+    float *const *a_dst = reinterpret_cast<float *const *>(ds + lay.dst);
+    const tc::K1Params *a_items = reinterpret_cast<const tc::K1Params *>(ds + lay.items);
+    const long long *a_cta = reinterpret_cast<const long long *>(ds + lay.cta);
+    const size_t out_bytes = (4 + b.total) * sizeof(float);
+    if (srv->use_graph) {
+        S_TRY(graph_launch(srv, b, variant, lay.end, a_in, a_sc, a_dst, ni, a_items, a_cta, cta, out_bytes));
+    } else {
+        S_CU(cudaMemcpyAsync(ds, b.pin_stage, lay.end, cudaMemcpyHostToDevice, srv->cs));
+        ingest_kernel<<<(unsigned)ni, 256, 0, srv->cs>>>(a_in, a_sc, a_dst, ni);
+        tc::count_launch();
+        S_CU(cudaGetLastError());
+        S_CU(cudaEventRecord(b.k1_start, srv->cs));
+        S_CU(tc::k1_launch_list(a_items, a_cta, ni, cta, variant, srv->cs));
+        S_CU(cudaEventRecord(b.k1_stop, srv->cs));
+        S_CU(cudaMemcpyAsync(b.pin_out, srv->d_out, out_bytes, cudaMemcpyDeviceToHost, srv->cs));
+    }
     S_CU(cudaEventRecord(b.done, srv->cs));
     return TC_OK;
 }
@@ -680,6 +800,16 @@ tc_status complete(tc_server *srv, tc_server::StepBuf &b)
             w.s->inflight--;
         b.items.clear();
         return sfail(TC_ETIMEOUT, "tc_server: a kernel's bounded wait gave up");
+    }
+    if (b.tune_key >= 0 && b.tune_work > 0.0) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, b.k1_start, b.k1_stop) == cudaSuccess && ms > 0.f) {
+            tc_server::Tune &t = srv->tune[(size_t)b.tune_key];
+            const float per = (float)(ms / b.tune_work);
+            t.best[b.variant] = std::min(t.best[b.variant], per);
+            if (t.tries[b.variant] < 255)
+                t.tries[b.variant]++;
+        }
     }
     std::lock_guard<std::mutex> lq(srv->mu_queue);
     size_t nblocks = 0;
@@ -833,7 +963,13 @@ tc_status tc_server_open(size_t mem_budget_bytes, size_t max_step_samples, tc_se
     for (auto &b : srv->buf) {
         S_CU(cudaHostAlloc(&b.pin_out, (4 + max_step_samples) * sizeof(float), cudaHostAllocDefault));
         S_CU(cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming));
+        S_CU(cudaEventCreate(&b.k1_start));
+        S_CU(cudaEventCreate(&b.k1_stop));
     }
+    tc_server::Tune t0{};
+    for (auto &v : t0.best)
+        v = 3.4e38f;
+    srv->tune.assign((size_t)kTuneWorkBins * kTuneLBins, t0);
     S_CU(cudaMalloc(&srv->d_out, (4 + max_step_samples) * sizeof(float)));
     S_CU(cudaMemset(srv->d_out, 0, 4 * sizeof(float)));
     // Size the step buffers for a few thousand streams and load the kernels
@@ -868,6 +1004,16 @@ tc_status tc_server_close(tc_server *srv)
         cudaFreeHost(b.pin_tables);
         if (b.done)
             cudaEventDestroy(b.done);
+        if (b.k1_start)
+            cudaEventDestroy(b.k1_start);
+        if (b.k1_stop)
+            cudaEventDestroy(b.k1_stop);
+    }
+    for (auto &g : srv->graphs) {
+        if (g.exec)
+            cudaGraphExecDestroy(g.exec);
+        if (g.graph)
+            cudaGraphDestroy(g.graph);
     }
     cudaFree(srv->d_stage);
     cudaFree(srv->d_out);
@@ -1224,6 +1370,20 @@ tc_status tc_server_get_stats(tc_server *srv, tc_server_stats *st)
 }
 
 double tc_server_clock(void) { return now_s(); }
+
+tc_status tc_server_set_option(tc_server *srv, int option, int value)
+{
+    if (!srv)
+        return sfail(TC_EINVAL, "tc_server_set_option: server is NULL");
+    if (value != 0 && value != 1)
+        return sfail(TC_EINVAL, "tc_server_set_option: value must be 0 or 1");
+    std::lock_guard<std::mutex> lk(srv->mu_state);
+    switch (option) {
+    case TC_SERVER_AUTOTUNE: srv->autotune = value != 0; return TC_OK;
+    case TC_SERVER_GRAPH: srv->use_graph = value != 0; return TC_OK;
+    default: return sfail(TC_EINVAL, "tc_server_set_option: unknown option");
+    }
+}
 
 tc_status tc_server_step_log(tc_server *srv, tc_server_step_rec *out, size_t cap, size_t *n_out)
 {

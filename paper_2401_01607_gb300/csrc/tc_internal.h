@@ -98,6 +98,11 @@ long long k1_partial_floats_max(long long L, int nin, long long tiles);
 cudaError_t k1_launch_list(const K1Params *d_items, const long long *d_cta_begin, int nitems, long long total_ctas,
                            int variant, cudaStream_t st);
 
+// The work-list kernel of a variant (for CUDA-graph kernel nodes): its
+// arguments are (K1Params unused, const K1Params *items, const long long
+// *cta_begin, int nitems), 256 threads, *smem bytes of dynamic shared memory.
+const void *k1_list_kernel(int variant, size_t *smem);
+
 // Launches K1 for plan on st (fills p.nchunk).
 cudaError_t k1_launch(K1Params &p, const K1Plan &plan, cudaStream_t st);
 

@@ -44,12 +44,14 @@ def _oracle(t, x, H, vstart):
     return oracle.buffer(x, H, np.asarray(vstart, np.int64), t.block)
 
 
-def _run(streams, order_seed=None):
+def _run(streams, order_seed=None, options=()):
     """Runs the streams through one server with manual steps. order_seed None:
     one stream at a time (alone); else interleaved at random (mix).
-    Returns {index: y[N + L - 1]}."""
+    options: (option, value) pairs. Returns {index: y[N + L - 1]}."""
     srv = capi.tc_server_open(8 << 30, 1 << 20)
     try:
+        for opt, val in options:
+            capi.tc_server_set_option(srv, opt, val)
         ids = [capi.tc_server_add(srv, t.L, t.block, H[0]) for (t, x, H, vs) in streams]
         nblk = [-(-t.n // t.block) for (t, x, H, vs) in streams]
         sent = [0] * len(streams)
@@ -313,3 +315,15 @@ def test_live_source_streams():
             assert rel_l2(got, _oracle(*s)) <= TOL["fp32"], i
     finally:
         capi.tc_server_close(srv)
+
+
+@pytest.mark.parametrize("graph,autotune", [(1, 1), (1, 0), (0, 0)])
+def test_graph_replay_and_autotune_modes(graph, autotune):
+    """The step replayed as a CUDA graph, with and without the chunk autotuner
+    (which tries every chunk variant on the first steps of a class): the mix
+    still matches the oracle and the same streams run alone."""
+    streams = _small_trace(k=6, seed=31)
+    opts = [(capi.TC_SERVER_GRAPH, graph), (capi.TC_SERVER_AUTOTUNE, autotune)]
+    mix = _run(streams, order_seed=2, options=opts)
+    for i, s in enumerate(streams):
+        assert rel_l2(mix[i], _oracle(*s)) <= TOL["fp32"], i

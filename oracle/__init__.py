@@ -87,6 +87,10 @@ def _load(mutant: int = 0) -> ctypes.CDLL:
         lib.tco_buf_flush.restype = ctypes.c_int
         lib.tco_mimo.argtypes = [_f32p, _i64, _i64, _i64, _f32p, _i64, _i64p, _i64, _i64, _f64p]
         lib.tco_mimo.restype = ctypes.c_int
+        lib.tco_direct_at_xf.argtypes = [_f32p, _i64, _f32p, _i64, _i64p, _i64p, _i64, _i64]
+        lib.tco_direct_at_xf.restype = ctypes.c_double
+        lib.tco_buffer_xf.argtypes = [_f32p, _i64, _f32p, _i64, _i64p, _i64p, _i64, _i64, _f64p]
+        lib.tco_buffer_xf.restype = ctypes.c_int
         lib.tco_mutant_id.argtypes = []
         lib.tco_mutant_id.restype = ctypes.c_int
         _LIBS[mutant] = lib
@@ -116,6 +120,25 @@ class Oracle:
     def direct_at(self, x, H, vstart, m: int) -> float:
         x, H, vstart = _prep(x, H, vstart)
         return self.lib.tco_direct_at(x, x.size, H.reshape(-1), H.shape[1], vstart, vstart.size, int(m))
+
+    def direct_at_xf(self, x, H, vstart, vramp, m: int) -> float:
+        """Eq. (4) with crossfaded IR versions (ramp lengths vramp), one output."""
+        x, H, vstart = _prep(x, H, vstart)
+        vramp = np.ascontiguousarray(vramp, dtype=np.int64).reshape(-1)
+        return self.lib.tco_direct_at_xf(x, x.size, H.reshape(-1), H.shape[1], vstart, vramp, vstart.size, int(m))
+
+    def buffer_xf(self, x, H, vstart, vramp, Nb: int = 8192) -> np.ndarray:
+        """The Sec. 4.2 buffer algorithm with crossfaded IR versions: version v
+        takes over over vramp[v] samples from vstart[v] on (1 = hard switch)."""
+        x, H, vstart = _prep(x, H, vstart)
+        vramp = np.ascontiguousarray(vramp, dtype=np.int64).reshape(-1)
+        if vramp.size != vstart.size:
+            raise ValueError("one ramp per IR version")
+        y = np.empty(x.size + H.shape[1] - 1, dtype=np.float64)
+        rc = self.lib.tco_buffer_xf(x, x.size, H.reshape(-1), H.shape[1], vstart, vramp, vstart.size, int(Nb), y)
+        if rc:
+            raise ValueError(f"tco_buffer_xf failed ({rc})")
+        return y
 
     def direct(self, x, H, vstart=None) -> np.ndarray:
         x, H, vstart = _prep(x, H, vstart)
@@ -224,6 +247,14 @@ def vect(x, H, vstart=None):
 
 def buffer(x, H, vstart=None, Nb: int = 8192):
     return default().buffer(x, H, vstart, Nb)
+
+
+def buffer_xf(x, H, vstart, vramp, Nb: int = 8192):
+    return default().buffer_xf(x, H, vstart, vramp, Nb)
+
+
+def direct_at_xf(x, H, vstart, vramp, m):
+    return default().direct_at_xf(x, H, vstart, vramp, m)
 
 
 def mimo(X, H, vstart=None, Nb: int = 8192):

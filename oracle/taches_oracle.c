@@ -28,7 +28,9 @@
  *   tco_vect                   : the vectorised algorithm of Sec. 4.1.
  *   tco_buf_*                  : the buffer (ring) algorithm of Sec. 4.2,
  *                                with the readings listed at tco_buf_push.
- * Plus tco_mimo, a sum over input channels of buffer-algorithm outputs.
+ * Plus tco_mimo, a sum over input channels of buffer-algorithm outputs, and
+ * tco_direct_at_xf / tco_buffer_xf, the crossfaded (continuous) form of the
+ * time-varying IR.
  *
  * Parity pins (tests): unit impulse, linearity, commutativity (Sec. 3.2,
  * Fig. 6), output length N+L-1 (Sec. 4.1), sum invariant, a geometric-sum
@@ -308,6 +310,117 @@ int tco_mimo(const float *x, int64_t nin, int64_t nout, int64_t N,
     }
     free(tmp);
     free(Hp);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Continuous time-varying IR (Sec. 6: the IR may also change
+ * progressively, e.g. a decay changed little by little). A switch becomes a
+ * crossfade: version v takes over from version v-1 over vramp[v] >= 1 input
+ * samples from vstart[v] on,
+ *   alpha_v(n) = clamp((n - vstart[v] + 1) / vramp[v], 0, 1),  alpha_0 = 1,
+ * and input sample n spawns its tache with the mixed IR
+ *   h_n = sum_v (alpha_v(n) - alpha_{v+1}(n)) H[v]     (alpha_nver = 0).
+ * vramp[v] = 1 is the hard switch of the forms above. A crossfade starts only
+ * once the previous one has ended: vstart[v+1] >= vstart[v] + vramp[v] - 1,
+ * so every weight lies in [0, 1] and the weights of a sample add up to 1.
+ * The taches semantics are unchanged: the IR of a tache is fixed when its
+ * sample arrives.                                                        */
+/* ------------------------------------------------------------------ */
+static int check_ramps(const int64_t *vstart, const int64_t *vramp, int64_t nver)
+{
+    if (check_versions(vstart, nver))
+        return -1;
+    for (int64_t v = 0; v < nver; ++v) {
+        if (vramp[v] < 1)
+            return -1;
+        if (v + 1 < nver && vstart[v + 1] < vstart[v] + vramp[v] - 1)
+            return -1;
+    }
+    return 0;
+}
+
+static double alpha_of(const int64_t *vstart, const int64_t *vramp, int64_t nver, int64_t v, int64_t n)
+{
+    if (v == 0)
+        return 1.0;
+    if (v >= nver)
+        return 0.0;
+#if ORACLE_MUTANT == 8
+    double a = (double)(n - vstart[v]) / (double)vramp[v];  /* ramp one sample late */
+#else
+    double a = (double)(n - vstart[v] + 1) / (double)vramp[v];
+#endif
+    return a < 0.0 ? 0.0 : (a > 1.0 ? 1.0 : a);
+}
+
+/* Tap k of the mixed IR of input sample n. */
+static double mixed_tap(const float *H, int64_t L, const int64_t *vstart, const int64_t *vramp, int64_t nver,
+                        int64_t n, int64_t k)
+{
+    double h = 0.0;
+    for (int64_t v = 0; v < nver; ++v) {
+        const double w = alpha_of(vstart, vramp, nver, v, n) - alpha_of(vstart, vramp, nver, v + 1, n);
+        if (w != 0.0)
+            h += w * (double)H[v * L + k];
+    }
+    return h;
+}
+
+/* Eq. (4) with mixed IRs, one output sample. */
+double tco_direct_at_xf(const float *x, int64_t N, const float *H, int64_t L, const int64_t *vstart,
+                        const int64_t *vramp, int64_t nver, int64_t m)
+{
+    double acc = 0.0;
+    int64_t n_lo = m - (L - 1);
+    if (n_lo < 0)
+        n_lo = 0;
+    int64_t n_hi = m;
+    if (n_hi > N - 1)
+        n_hi = N - 1;
+    for (int64_t n = n_lo; n <= n_hi; ++n)
+        acc += (double)x[n] * mixed_tap(H, L, vstart, vramp, nver, n, m - n);
+    return acc;
+}
+
+/* The buffer algorithm (Sec. 4.2, readings as tco_buf_push) with mixed IRs,
+ * in blocks of Nb, then the flush: y receives N + L - 1 samples.          */
+int tco_buffer_xf(const float *x, int64_t N, const float *H, int64_t L, const int64_t *vstart,
+                  const int64_t *vramp, int64_t nver, int64_t Nb, double *y)
+{
+    if (N < 1 || L < 1 || Nb < 1 || check_ramps(vstart, vramp, nver))
+        return -1;
+    tco_buf *s = tco_buf_open(L);
+    double *h = (double *)malloc((size_t)L * sizeof(double));
+    if (!s || !h) {
+        tco_buf_close(s);
+        free(h);
+        return -2;
+    }
+    for (int64_t b = 0; b < N; b += Nb) {
+        const int64_t nb = (N - b < Nb) ? N - b : Nb;
+        for (int64_t n = b; n < b + nb; ++n) {
+            for (int64_t k = 0; k < L; ++k)
+                h[k] = mixed_tap(H, L, vstart, vramp, nver, n, k);
+            /* The tache x[n] * h_n into the ring: tap j on slot (rho + j) mod L. */
+            const double e0 = (double)x[n];
+            double *r = s->r;
+            const int64_t rho = s->rho;
+            for (int64_t j = 0; j < L; ++j) {
+                int64_t slot = rho + j;
+                if (slot >= L)
+                    slot -= L;
+                r[slot] += e0 * h[j];
+            }
+            y[n] = r[rho];
+            r[rho] = 0.0;
+            s->rho = (rho + 1 < L) ? rho + 1 : 0;
+        }
+        s->n_in += nb;
+    }
+    tco_buf_flush(s, y + N);
+    tco_buf_close(s);
+    free(h);
     return 0;
 }
 

@@ -269,6 +269,66 @@ def check_mimo(o):
     return None
 
 
+def _xf_weights(vstart, vramp, n):
+    """Per-sample weights of the crossfaded versions: alpha_v(n) =
+    clamp((n - vstart[v] + 1) / vramp[v], 0, 1), alpha_0 = 1, and
+    w_v = alpha_v - alpha_{v+1} (the definition; checked for sanity here)."""
+    nv = len(vstart)
+    alpha = np.ones((nv + 1, n.size))
+    for v in range(1, nv):
+        alpha[v] = np.clip((n - vstart[v] + 1) / vramp[v], 0.0, 1.0)
+    alpha[nv] = 0.0
+    return alpha[:-1] - alpha[1:]
+
+
+def check_crossfade_hard(o):
+    """Ramps of one sample are the hard switches: same outputs, bit for bit."""
+    r = _rng(21)
+    for N, L, starts, Nb in [(200, 30, [0, 57], 16), (300, 50, [0, 40, 41, 170], 7), (90, 120, [-5, 10, 60], 9)]:
+        x = r.uniform(-1, 1, N).astype(np.float32)
+        H = r.standard_normal((len(starts), L)).astype(np.float32)
+        vs = np.array(starts, np.int64)
+        y = o.buffer_xf(x, H, vs, np.ones(len(starts), np.int64), Nb)
+        ref = o.buffer(x, H, vs, Nb)
+        if not np.array_equal(y, ref):
+            return f"starts={starts}: max diff {np.max(np.abs(y - ref)):.3g}"
+    return None
+
+
+def check_crossfade_superposition(o):
+    """A crossfade is the sum of plain convolutions of weighted inputs:
+    y = sum_v conv(x * w_v, H[v]) (for two versions: conv(x (1 - alpha), h_a)
+    + conv(x alpha, h_b)); the weights lie in [0, 1] and add up to 1."""
+    r = _rng(22)
+    for N, L, starts, ramps, Nb in [(400, 60, [0, 100], [1, 50], 16), (500, 40, [0, 30, 300], [1, 200, 7], 13),
+                                    (300, 90, [-10, 5, 120], [1, 1, 100], 64), (256, 33, [0, 0 + 1], [1, 256], 32)]:
+        x = r.uniform(-1, 1, N).astype(np.float32)
+        H = r.standard_normal((len(starts), L)).astype(np.float32)
+        vs, vr = np.array(starts, np.int64), np.array(ramps, np.int64)
+        n = np.arange(N)
+        w = _xf_weights(vs, vr, n)
+        if np.any(w < -1e-15) or np.any(w > 1 + 1e-15) or np.max(np.abs(w.sum(axis=0) - 1.0)) > 1e-15:
+            return f"weights out of range for starts={starts} ramps={ramps}"
+        ref = np.zeros(N + L - 1)
+        for v in range(len(starts)):
+            ref += np.convolve(x.astype(np.float64) * w[v], H[v].astype(np.float64))
+        y = o.buffer_xf(x, H, vs, vr, Nb)
+        err = np.max(np.abs(y - ref)) / max(np.max(np.abs(ref)), 1e-300)
+        if err > 1e-13:
+            return f"starts={starts} ramps={ramps}: rel {err:.3g}"
+        # The direct form, at a few outputs.
+        for m in (0, starts[-1] + 3 if starts[-1] >= 0 else 5, N // 2, N + L - 2):
+            d = o.direct_at_xf(x, H, vs, vr, m)
+            if abs(d - y[m]) > 1e-12 * max(1.0, abs(y[m])):
+                return f"direct_at_xf m={m}: {d} vs {y[m]}"
+        # Sum invariant: sum y = sum_n x[n] * sum_v w_v(n) sum_k H[v][k].
+        hs = H.astype(np.float64).sum(axis=1)
+        tot = float(np.sum(x.astype(np.float64) * (w * hs[:, None]).sum(axis=0)))
+        if abs(y.sum() - tot) > 1e-9 * max(1.0, np.abs(y).sum()):
+            return f"sum invariant: {y.sum()} vs {tot}"
+    return None
+
+
 ALL = {
     "worked_example": check_worked_example,
     "impulse": check_impulse,
@@ -282,6 +342,8 @@ ALL = {
     "block_invariance": check_block_invariance,
     "forms_agree": check_forms_agree,
     "mimo": check_mimo,
+    "crossfade_hard": check_crossfade_hard,
+    "crossfade_superposition": check_crossfade_superposition,
 }
 
 

@@ -148,6 +148,16 @@ tc_status tc_set_ir(tc_stream *s, const float *h, size_t n);
  * of samples already pushed, and >= the start of the latest version. A
  * version set at the same sample replaces it. */
 tc_status tc_set_ir_at(tc_stream *s, const float *h, size_t n, uint64_t sample);
+/* Continuous time-varying IR (Sec. 6: the IR may also change progressively).
+ * From this call on, each IR switch (tc_set_ir, tc_set_ir_at,
+ * tc_set_ir_rows) at sample s is a crossfade over `ramp` samples: input
+ * sample n spawns its tache with (1 - a) h_old + a h_new, where
+ * a = clamp((n - s + 1) / ramp, 0, 1). ramp = 1 (the default, and after
+ * tc_reset) is the hard switch. A switch may not start before the previous
+ * crossfade has ended (TC_EINVAL). Windows that read a crossfade run on the
+ * FP32 gather in every precision mode. Errors: TC_EINVAL for ramp outside
+ * [1, 2^24]. */
+tc_status tc_set_crossfade(tc_stream *s, size_t ramp);
 
 /* One IR per IR set, all taking effect at `sample`. h is [sets][n]. sets is
  * 1 for a shared-IR group, channels for a per-channel group, and nout*nin

@@ -69,6 +69,7 @@ _SIGS = {
     "tc_get_info": [_vp, ctypes.POINTER(TcInfo)],
     "tc_set_ir": [_vp, _vp, _sz],
     "tc_set_ir_at": [_vp, _vp, _sz, _u64],
+    "tc_set_crossfade": [_vp, _sz],
     "tc_set_ir_rows": [_vp, _vp, _sz, _u64, _int],
     "tc_push_block": [_vp, _vp, _sz, _vp],
     "tc_push": [_vp, _vp, _sz, _vp, _int],
@@ -220,6 +221,10 @@ def tc_set_ir(s: int, h) -> None:
 def tc_set_ir_at(s: int, h, sample: int) -> None:
     h, p = _host_f32(h)
     _call("tc_set_ir_at", s, p, h.size, int(sample))
+
+
+def tc_set_crossfade(s: int, ramp: int) -> None:
+    _call("tc_set_crossfade", s, int(ramp))
 
 
 def tc_set_ir_rows(s: int, h, n: int, sample: int, on_device: bool = False) -> None:

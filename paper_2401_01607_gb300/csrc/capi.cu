@@ -62,12 +62,14 @@ constexpr int kMaxVersions = 16;
 struct Version {
     long long start;
     int slot;
+    long long ramp;  // crossfade from the previous version over this many samples (1: hard switch)
 };
 
 // Device copy of the version table.
 struct DevTable {
     long long vstart[kMaxVersions];
     int vslot[kMaxVersions];
+    int vramp[kMaxVersions];
     int nver;
 };
 
@@ -123,6 +125,7 @@ struct tc_stream {
     DevTable *pin_vt = nullptr;
     cudaEvent_t ev_vt = nullptr;
     bool vt_dirty = false;
+    long long next_ramp = 1;  // crossfade length of the next IR switches (tc_set_crossfade)
 
     // Host-pointer staging.
     float *pin_x = nullptr;   // [rows][max_push]
@@ -270,6 +273,7 @@ tc_status clear_state(tc_stream *s)
     s->vt.clear();
     std::fill(s->slot_used.begin(), s->slot_used.end(), 0);
     s->vt_dirty = true;
+    s->next_ramp = 1;
     s->ir_ever_set = false;
     TC_CU(cudaMemsetAsync(s->hist, 0, (size_t)s->rows * s->cap * sizeof(float), s->cs));
     if (s->hist_hi) {
@@ -397,7 +401,9 @@ void retire_versions(tc_stream *s)
 {
     const long long oldest_needed = s->pos - (long long)s->L + 1;
     size_t drop = 0;
-    while (drop + 1 < s->vt.size() && s->vt[drop + 1].start <= oldest_needed)
+    // Version i is dead once version i + 1 has fully taken over (its ramp
+    // ended) before the oldest sample a future output reads.
+    while (drop + 1 < s->vt.size() && s->vt[drop + 1].start + s->vt[drop + 1].ramp - 1 <= oldest_needed)
         ++drop;
     for (size_t i = 0; i < drop; ++i)
         s->slot_used[(size_t)s->vt[i].slot] = 0;
@@ -418,6 +424,7 @@ tc_status upload_table(tc_stream *s)
     for (size_t i = 0; i < s->vt.size(); ++i) {
         t.vstart[i] = s->vt[i].start;
         t.vslot[i] = s->vt[i].slot;
+        t.vramp[i] = (int)s->vt[i].ramp;
     }
     TC_CU(cudaMemcpyAsync(s->d_vt, &t, sizeof t, cudaMemcpyHostToDevice, s->cs));
     TC_CU(cudaEventRecord(s->ev_vt, s->cs));
@@ -441,6 +448,10 @@ tc_status set_ir_impl(tc_stream *s, const float *h, size_t n, long long sample, 
     if (!s->vt.empty() && sample < s->vt.back().start)
         return fail(TC_EINVAL, "IR switch at sample %lld is before the latest version (%lld)", sample,
                     s->vt.back().start);
+    if (!s->vt.empty() && sample != s->vt.back().start && s->vt.size() > 1 &&
+        sample < s->vt.back().start + s->vt.back().ramp - 1)
+        return fail(TC_EINVAL, "IR switch at sample %lld starts before the crossfade to the latest version ends (%lld)",
+                    sample, s->vt.back().start + s->vt.back().ramp - 1);
     TC_TRY(use_device(s));
     retire_versions(s);
 
@@ -487,8 +498,10 @@ tc_status set_ir_impl(tc_stream *s, const float *h, size_t n, long long sample, 
     TC_CU(tc::ir_prep_launch(src, src_pitch, (long long)n, (int)sets, dst, 4 * s->Lpad, s->Lpad, s->Lpad, s->cs));
 
     if (!replace) {
-        s->vt.push_back(Version{sample, slot});
+        s->vt.push_back(Version{sample, slot, s->vt.empty() ? 1 : s->next_ramp});
         s->slot_used[(size_t)slot] = 1;
+    } else if (s->vt.size() > 1) {
+        s->vt.back().ramp = s->next_ramp;
     }
     s->vt_dirty = true;
     s->ir_ever_set = true;
@@ -581,6 +594,7 @@ tc_status launch_k1(tc_stream *s, long long t0, long long nout, float *y, long l
     p.vstart = s->d_vt->vstart;
     p.vslot = s->d_vt->vslot;
     p.nver = &s->d_vt->nver;
+    p.vramp = s->d_vt->vramp;
     p.vt_item = 0;
     p.nitems = (int)s->items;
     p.nin = (int)s->nin;
@@ -624,6 +638,8 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
         return TC_OK;
     if ((size_t)v + 1 < s->vt.size() && s->vt[(size_t)v + 1].start < hi)
         return TC_OK;
+    if (v > 0 && s->vt[(size_t)v].start + s->vt[(size_t)v].ramp - 1 > w0)
+        return TC_OK;  // the window reads samples of a crossfade
     const int slot = s->vt[(size_t)v].slot;
     tc_stream::TSet &ts = s->tsets[(size_t)slot][(size_t)delta];
     if (!ts.ready) {
@@ -734,6 +750,8 @@ tc_status launch_k3(tc_stream *s, long long t0, long long nout, float *y, long l
         return TC_OK;
     if ((size_t)v + 1 < s->vt.size() && s->vt[(size_t)v + 1].start < hi)
         return TC_OK;
+    if (v > 0 && s->vt[(size_t)v].start + s->vt[(size_t)v].ramp - 1 > lo)
+        return TC_OK;  // the window reads samples of a crossfade
     // k3_rev copies samples [R - span + 1, R], R = t0 + 1024 ntile - 1.
     if (t0 + 1024LL * ntile - tc::k3_xr_span(ntile, nkbp) < s->base)
         return fail(TC_EINVAL, "internal: K3 window starts before the kept history");
@@ -1002,6 +1020,15 @@ tc_status tc_get_info(const tc_stream *s, tc_info *info)
     info->max_versions = s->nslots;
     info->tensor_launches = (uint64_t)s->k2_launches;
     info->fp32_fallbacks = (uint64_t)s->k1_fallbacks;
+    return TC_OK;
+}
+
+tc_status tc_set_crossfade(tc_stream *s, size_t ramp)
+{
+    TC_TRY(check_stream(s));
+    if (ramp < 1 || ramp > ((size_t)1 << 24))
+        return fail(TC_EINVAL, "crossfade ramp %zu not in [1, 2^24] samples", ramp);
+    s->next_ramp = (long long)ramp;
     return TC_OK;
 }
 

@@ -41,6 +41,23 @@ namespace tc {
 
 namespace {
 
+// Crossfade share alpha(n) of a version starting at s with a ramp of R
+// samples: clamp((n - s + 1) / R, 0, 1). mode 1: the first version (always
+// 1); mode -1: no next version (always 0).
+__device__ __forceinline__ float ramp_alpha(long long n, long long s, int R, int mode)
+{
+    if (mode > 0)
+        return 1.f;
+    if (mode < 0)
+        return 0.f;
+    const long long d = n - s + 1;
+    if (d <= 0)
+        return 0.f;
+    if (d >= R)
+        return 1.f;
+    return (float)d / (float)R;
+}
+
 // Floor division by a positive divisor.
 __device__ __forceinline__ long long floor_div(long long x, long long d)
 {
@@ -169,6 +186,7 @@ __global__ void __launch_bounds__(K1_THREADS, 4)
 
     const long long *vst = p.vstart + (long long)item * p.vt_item;
     const int *vsl = p.vslot + (long long)item * p.vt_item;
+    const int *vrm = p.vramp ? p.vramp + (long long)item * p.vt_item : nullptr;  // crossfade ramps (or none)
     const int nv = p.nver[p.vt_item ? item : 0];
 
     if (tid == 0) {
@@ -198,8 +216,14 @@ __global__ void __launch_bounds__(K1_THREADS, 4)
 
     uint32_t parity = 0;
     for (int v = 0; v < nv; ++v) {
+        // Version v's samples: [a, b). With crossfades, version v takes over
+        // over ra samples from a on and hands over to v + 1 over rb samples
+        // from bn on; weight w(n) = alpha_v(n) - alpha_{v+1}(n).
         const long long a = vst[v];
-        const long long b = (v + 1 < nv) ? vst[v + 1] : LLONG_MAX;
+        const long long bn = (v + 1 < nv) ? vst[v + 1] : LLONG_MAX;
+        const int ra = (vrm && v > 0) ? vrm[v] : 1;
+        const int rb = (vrm && v + 1 < nv) ? vrm[v + 1] : 1;
+        const long long b = (bn == LLONG_MAX) ? LLONG_MAX : bn + rb - 1;
         if (b <= n_lo || a >= n_end)
             continue;  // this version spawned no tache that reaches the tile through this chunk
         // Two parts on two mbarriers (chunks of 4 passes or more): part A =
@@ -238,10 +262,22 @@ __global__ void __launch_bounds__(K1_THREADS, 4)
         // [b, n_end) of the staged window are zeroed, in each part once it
         // has landed.
         const bool straddle = (a > n_lo || b < n_end);
+        // A ramp inside the window: weight the staged samples instead of masking.
+        const bool ramped = (ra > 1 && a + ra - 1 > n_lo) || (rb > 1 && bn < n_end);
         const long long za = a - n_lo, zb = b - n_lo;
         const int z0 = (za > 0) ? (za < C::XS ? (int)za : C::XS) : 0;
         const int z1 = (b < n_end) ? (zb > 0 ? (int)zb : 0) : C::XS;
-        if (straddle) {
+        auto weigh = [&](int lo, int hi) {  // xs[i] *= w(n_lo + i), i in [lo, hi)
+            for (int i = lo + tid; i < hi; i += K1_THREADS) {
+                const long long n = n_lo + i;
+                const float w = ramp_alpha(n, a, ra, v == 0) - ramp_alpha(n, bn, rb, bn == LLONG_MAX ? -1 : 0);
+                xs[i] = (w == 0.f) ? 0.f : xs[i] * w;
+            }
+        };
+        if (ramped) {
+            weigh(SPLIT ? XA : 0, C::XS);
+            __syncthreads();
+        } else if (straddle) {
             constexpr int r0 = SPLIT ? XA : 0;
             for (int i = r0 + tid; i < z0; i += K1_THREADS)
                 xs[i] = 0.f;
@@ -280,7 +316,10 @@ __global__ void __launch_bounds__(K1_THREADS, 4)
                 __syncthreads();
                 return;
             }
-            if (straddle) {
+            if (ramped) {
+                weigh(0, XA);
+                __syncthreads();
+            } else if (straddle) {
                 for (int i = tid; i < min(z0, XA); i += K1_THREADS)
                     xs[i] = 0.f;
                 for (int i = z1 + tid; i < XA; i += K1_THREADS)

@@ -46,10 +46,14 @@ struct K1Params {
     int L;
 
     // IR versions of item c: entries [c * vt_item, c * vt_item + nver[c]).
-    // vstart ascending; the version with the largest vstart <= n owns n.
+    // vstart ascending; the version with the largest vstart <= n owns n. With
+    // ramps, version v takes over from v - 1 over vramp[v] samples from
+    // vstart[v] on: sample n's tache uses sum_v (alpha_v(n) - alpha_{v+1}(n)) h_v,
+    // alpha_v(n) = clamp((n - vstart[v] + 1) / vramp[v], 0, 1), alpha_0 = 1.
     const long long *vstart;
     const int *vslot;
     const int *nver;
+    const int *vramp;        // crossfade ramp of each version (samples, >= 1), or null: hard switches
     int vt_item;             // 0: one table shared by all items
 
     int nitems;

@@ -19,19 +19,20 @@ def max_abs(y, ref):
     return float(np.max(np.abs(np.asarray(y, np.float64) - np.asarray(ref, np.float64))))
 
 
-def stream_host(x, H, vstart, L, block, pushes=None, max_push=0, shared_ir=True):
+def stream_host(x, H, vstart, L, block, pushes=None, max_push=0, shared_ir=True, ramps=None, precision=None):
     """Streams x ([C, N] or [N]) through a group via host-pointer pushes and
     returns [C, N + L - 1] float32 (input then flush tail).
-    H: [nver, L'] shared, or [C, nver, L'] per channel. vstart: [nver]."""
+    H: [nver, L'] shared, or [C, nver, L'] per channel. vstart: [nver].
+    ramps: crossfade length of each switch ([nver], entry 0 unused)."""
     x = np.atleast_2d(np.asarray(x, np.float32))
     C, N = x.shape
     H = np.asarray(H, np.float32)
     per_channel = H.ndim == 3
     mp = max_push or block
-    if C == 1 and not per_channel and mp == block:
+    if C == 1 and not per_channel and mp == block and precision is None:
         s = capi.tc_open_stream(L, block)
     else:
-        s = capi.tc_open_group(C, L, block, not per_channel, capi.TC_FP32, mp)
+        s = capi.tc_open_group(C, L, block, not per_channel, capi.TC_FP32 if precision is None else precision, mp)
     try:
         if len(vstart) > 4:
             capi.tc_set_max_versions(s, min(16, len(vstart) + 1))
@@ -46,6 +47,8 @@ def stream_host(x, H, vstart, L, block, pushes=None, max_push=0, shared_ir=True)
             n = min(n, N - pos)
             # Register every version that starts before the end of this push.
             while v_next < len(vstart) and vstart[v_next] < pos + n:
+                if ramps is not None:
+                    capi.tc_set_crossfade(s, int(ramps[v_next]) if v_next > 0 else 1)
                 rows = H[:, v_next] if per_channel else H[v_next][None]
                 capi.tc_set_ir_rows(s, np.ascontiguousarray(rows), rows.shape[-1], max(int(vstart[v_next]), pos))
                 v_next += 1

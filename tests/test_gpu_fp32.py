@@ -209,3 +209,85 @@ def test_errors_are_status_codes():
         assert np.array_equal(y, np.arange(1, B + 1, dtype=np.float32))
     finally:
         capi.tc_close(s)
+
+
+def _ref_xf(x, H, vstart, ramps, B):
+    return oracle.buffer_xf(x, H, np.asarray(vstart, np.int64), np.asarray(ramps, np.int64), B)
+
+
+@pytest.mark.parametrize("vstart,ramps", [([0, 500, 2000], [1, 300, 1]), ([0, 777], [1, 1500]),
+                                          ([0, 100, 101], [1, 1, 1]), ([0, 64, 3000], [1, 2000, 900])])
+def test_crossfade_group(vstart, ramps):
+    """Continuous time-varying IR (Sec. 6): each switch is a crossfade over
+    `ramp` samples; 4 channels with their own IRs, ragged pushes."""
+    C, N, L, B = 4, 4500, 1500, 64
+    x = synth.audio_block(C, N, 91)
+    H = np.stack([np.stack([synth.decayed_ir(L, 300.0, 9000 + 10 * c + v) for v in range(len(vstart))])
+                  for c in range(C)])
+    y = stream_host(x, H, vstart, L, B, pushes=[64, 448, 64, 1024, 192], max_push=1024, ramps=ramps)
+    for c in range(C):
+        ref = _ref_xf(x[c], H[c], vstart, ramps, B)
+        err = rel_l2(y[c], ref)
+        assert err <= TOL["fp32"], (c, err)
+
+
+def test_crossfade_ramp_one_is_the_hard_switch():
+    """Ramps of one sample give the same result as the hard switches."""
+    N, L, B = 3000, 1200, 128
+    x = synth.audio(N, 92)
+    H = np.stack([synth.decayed_ir(L, 300.0, 9100 + v) for v in range(3)])
+    vs = [0, 700, 1400]
+    y1 = stream_host(x, H, vs, L, B, ramps=[1, 1, 1])
+    y0 = stream_host(x, H, vs, L, B)
+    assert np.array_equal(y1, y0)
+
+
+def test_crossfade_on_the_tensor_path_falls_back_exactly():
+    """A BF16-split shared-IR group with a crossfade: windows that read the
+    ramp run on the FP32 gather, the rest on the tensor cores."""
+    C, N, L, B = 130, 8000, 1000, 128
+    X = synth.audio_block(C, N, 93)
+    H = np.stack([synth.decayed_ir(L, 200.0, 9200 + v) for v in range(2)])
+    vs, rp = [0, 3000], [1, 700]
+    s = capi.tc_open_group(C, L, B, True, capi.TC_BF16_SPLIT, 512)
+    try:
+        outs, pos, v = [], 0, 0
+        while pos < N:
+            n = min(512, N - pos)
+            while v < len(vs) and vs[v] < pos + n:
+                capi.tc_set_crossfade(s, rp[v] if v else 1)
+                capi.tc_set_ir_rows(s, H[v][None], L, max(vs[v], pos))
+                v += 1
+            y = np.empty((C, n), np.float32)
+            capi.tc_push(s, np.ascontiguousarray(X[:, pos:pos + n]), n, y)
+            outs.append(y)
+            pos += n
+        tail = np.empty((C, L - 1), np.float32)
+        capi.tc_flush(s, tail, L - 1)
+        info = capi.tc_get_info(s)
+    finally:
+        capi.tc_close(s)
+    y = np.concatenate(outs + [tail], axis=1)
+    assert info.tensor_launches > 0 and info.fp32_fallbacks > 0
+    for c in (0, 64, 129):
+        err = rel_l2(y[c], _ref_xf(X[c], H, vs, rp, B))
+        assert err <= TOL["bf16split"], (c, err)
+
+
+def test_crossfade_errors():
+    L, B = 200, 32
+    s = capi.tc_open_stream(L, B)
+    try:
+        h = synth.decayed_ir(L, 50.0, 1)
+        with pytest.raises(capi.TcError) as e:
+            capi.tc_set_crossfade(s, 0)
+        assert e.value.code == "TC_EINVAL"
+        capi.tc_set_ir(s, h)
+        capi.tc_set_crossfade(s, 100)
+        capi.tc_set_ir_at(s, h, 50)
+        with pytest.raises(capi.TcError) as e:
+            capi.tc_set_ir_at(s, h, 120)  # the crossfade to 50 runs until sample 149
+        assert e.value.code == "TC_EINVAL"
+        capi.tc_set_ir_at(s, h, 149)
+    finally:
+        capi.tc_close(s)

@@ -404,8 +404,18 @@ uint64_t tc_kernel_launches(void);
  *                        BF16; 1..4096)
  *   TC_TUNE_K2_PAIR      plain BF16 only: 1 = two 128-channel tiles per CTA
  *                        sharing each IR tile (default), 0 = one tile per CTA
+ *   TC_TUNE_ZERO_SKIP    1 = zero gating on the FP32 gather (the zero-skip of
+ *                        Sec. 3.2 and 4.2 at block level, threshold 0): a
+ *                        staged stretch of input that is all zero skips its
+ *                        taps. Exact (the skipped products are zeros); saves
+ *                        time on silent input. 0 / -1 = off (default).
  * Errors: TC_EINVAL for an unknown knob or value out of range. */
-typedef enum tc_tune_knob { TC_TUNE_K1_CHUNK = 0, TC_TUNE_K2_RANGE = 1, TC_TUNE_K2_PAIR = 2 } tc_tune_knob;
+typedef enum tc_tune_knob {
+    TC_TUNE_K1_CHUNK = 0,
+    TC_TUNE_K2_RANGE = 1,
+    TC_TUNE_K2_PAIR = 2,
+    TC_TUNE_ZERO_SKIP = 3
+} tc_tune_knob;
 tc_status tc_set_tuning(tc_stream *s, int knob, long long value);
 
 /* Kernel timing (tracing aid). With enable = 1, each later convolution kernel

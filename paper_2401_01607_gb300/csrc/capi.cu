@@ -143,6 +143,7 @@ struct tc_stream {
     int k1_variant_fixed = -1;  // -1: chosen per launch
     long long k2_range = -1;    // K blocks per tensor-core CTA range (-1: by precision)
     bool k2_single_tile = false; // plain BF16: one channel tile per CTA (tuning knob)
+    bool zero_skip = false;      // K1 zero gating (tuning knob)
 
     // BF16 tensor-core path (shared-IR groups): bf16 hi/lo histories and, per
     // IR slot and alignment shift delta, the materialised Toeplitz tiles.
@@ -594,7 +595,12 @@ tc_status launch_k1(tc_stream *s, long long t0, long long nout, float *y, long l
     p.vstart = s->d_vt->vstart;
     p.vslot = s->d_vt->vslot;
     p.nver = &s->d_vt->nver;
-    p.vramp = s->d_vt->vramp;
+    // The ramp table only when a live version crossfades (hard switches read
+    // no ramps on the device).
+    bool ramps = false;
+    for (const Version &v : s->vt)
+        ramps = ramps || v.ramp > 1;
+    p.vramp = ramps ? s->d_vt->vramp : nullptr;
     p.vt_item = 0;
     p.nitems = (int)s->items;
     p.nin = (int)s->nin;
@@ -609,6 +615,7 @@ tc_status launch_k1(tc_stream *s, long long t0, long long nout, float *y, long l
     p.partial = s->partial;
     p.counter = s->counter;
     p.err = s->d_err;
+    p.zero_skip = s->zero_skip ? 1 : 0;
     if ((size_t)p.nitems * p.ntile > s->counter_n ||
         (size_t)plan.ctas * tc::K1_MO > s->partial_floats)
         return fail(TC_EINVAL, "internal: K1 scratch too small");
@@ -1204,6 +1211,11 @@ tc_status tc_set_tuning(tc_stream *s, int knob, long long value)
         if (value != -1 && value != 0 && value != 1)
             return fail(TC_EINVAL, "TC_TUNE_K2_PAIR must be -1, 0 or 1");
         s->k2_single_tile = value == 0;
+        return TC_OK;
+    case TC_TUNE_ZERO_SKIP:
+        if (value != -1 && value != 0 && value != 1)
+            return fail(TC_EINVAL, "TC_TUNE_ZERO_SKIP must be -1, 0 or 1");
+        s->zero_skip = value == 1;
         return TC_OK;
     default:
         return fail(TC_EINVAL, "unknown tuning knob %d", knob);

@@ -58,6 +58,16 @@ __device__ __forceinline__ float ramp_alpha(long long n, long long s, int R, int
     return (float)d / (float)R;
 }
 
+// True if any of xs[lo, hi) is nonzero (+0 and -0 count as zero); a CTA-wide
+// barrier: every thread of the block calls it.
+__device__ __forceinline__ bool any_nonzero(const float *xs, int lo, int hi)
+{
+    bool nz = false;
+    for (int i = lo + (int)threadIdx.x; i < hi; i += K1_THREADS)
+        nz |= (__float_as_uint(xs[i]) << 1) != 0u;
+    return __syncthreads_or(nz) != 0;
+}
+
 // Floor division by a positive divisor.
 __device__ __forceinline__ long long floor_div(long long x, long long d)
 {
@@ -121,7 +131,7 @@ __device__ __forceinline__ void k1_pass(const float *__restrict__ xp, const floa
 // CTA b belongs to item i with cta_begin[i] <= b < cta_begin[i+1]; the item's
 // parameters are copied to shared memory, then the CTA runs as in a uniform
 // launch over that item alone.
-template <int P, bool LIST>
+template <int P, bool LIST, bool EXT = false>
 __global__ void __launch_bounds__(K1_THREADS, 4)
     k1_gather(const K1Params p0, const K1Params *__restrict__ items, const long long *__restrict__ cta_begin,
               int nlist)
@@ -186,7 +196,8 @@ __global__ void __launch_bounds__(K1_THREADS, 4)
 
     const long long *vst = p.vstart + (long long)item * p.vt_item;
     const int *vsl = p.vslot + (long long)item * p.vt_item;
-    const int *vrm = p.vramp ? p.vramp + (long long)item * p.vt_item : nullptr;  // crossfade ramps (or none)
+    // Crossfade ramps (EXT instances only; the others compile without them).
+    const int *vrm = (EXT && p.vramp) ? p.vramp + (long long)item * p.vt_item : nullptr;
     const int nv = p.nver[p.vt_item ? item : 0];
 
     if (tid == 0) {
@@ -221,8 +232,8 @@ __global__ void __launch_bounds__(K1_THREADS, 4)
         // from bn on; weight w(n) = alpha_v(n) - alpha_{v+1}(n).
         const long long a = vst[v];
         const long long bn = (v + 1 < nv) ? vst[v + 1] : LLONG_MAX;
-        const int ra = (vrm && v > 0) ? vrm[v] : 1;
-        const int rb = (vrm && v + 1 < nv) ? vrm[v + 1] : 1;
+        const int ra = (EXT && vrm && v > 0) ? vrm[v] : 1;
+        const int rb = (EXT && vrm && v + 1 < nv) ? vrm[v + 1] : 1;
         const long long b = (bn == LLONG_MAX) ? LLONG_MAX : bn + rb - 1;
         if (b <= n_lo || a >= n_end)
             continue;  // this version spawned no tache that reaches the tile through this chunk
@@ -263,7 +274,7 @@ __global__ void __launch_bounds__(K1_THREADS, 4)
         // has landed.
         const bool straddle = (a > n_lo || b < n_end);
         // A ramp inside the window: weight the staged samples instead of masking.
-        const bool ramped = (ra > 1 && a + ra - 1 > n_lo) || (rb > 1 && bn < n_end);
+        const bool ramped = EXT && ((ra > 1 && a + ra - 1 > n_lo) || (rb > 1 && bn < n_end));
         const long long za = a - n_lo, zb = b - n_lo;
         const int z0 = (za > 0) ? (za < C::XS ? (int)za : C::XS) : 0;
         const int z1 = (b < n_end) ? (zb > 0 ? (int)zb : 0) : C::XS;
@@ -303,6 +314,15 @@ __global__ void __launch_bounds__(K1_THREADS, 4)
         // Pass p reads xs[KC - 640 (p + 1), KC - 640 p + 128) and hs[640 p, 640 (p + 1)):
         // passes below PA touch part A only.
         const int pa_end = min(p_hi, PA - 1);
+        // Zero gating (exact): passes whose staged input is all zero add
+        // nothing, so they are skipped. Passes below PA read xs[XA, XS); the
+        // rest read xs[0, XA + 128).
+        if (EXT && p.zero_skip && !any_nonzero(xs, SPLIT ? XA : 0, C::XS)) {
+            const int k = max(0, pa_end - pass + 1);
+            pass += k;
+            ia -= k * 32 * C::SEG;
+            hp += k * 32 * C::SEG;
+        }
 #pragma unroll 1
         for (; pass <= pa_end; ++pass, ia -= 32 * C::SEG, hp += 32 * C::SEG)
             k1_pass(xs + ia, hp, acc);
@@ -326,6 +346,8 @@ __global__ void __launch_bounds__(K1_THREADS, 4)
                     xs[i] = 0.f;
                 __syncthreads();
             }
+            if (EXT && p.zero_skip && !any_nonzero(xs, 0, XA + 128))
+                pass = p_hi + 1;
 #pragma unroll 1
             for (; pass <= p_hi; ++pass, ia -= 32 * C::SEG, hp += 32 * C::SEG)
                 k1_pass(xs + ia, hp, acc);
@@ -431,6 +453,8 @@ cudaError_t prepare_variant(int dev, int variant)
     cudaError_t e = cudaFuncSetAttribute(k1_gather<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k1_gather<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k1_gather<P, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     // All of the unified L1/shared storage as shared memory: four CTAs of the
     // largest chunk need almost all of it.
     if (e == cudaSuccess)
@@ -438,6 +462,9 @@ cudaError_t prepare_variant(int dev, int variant)
                                  (int)cudaSharedmemCarveoutMaxShared);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k1_gather<P, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k1_gather<P, false, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess)
         return e;
@@ -558,11 +585,27 @@ cudaError_t k1_launch(K1Params &p, const K1Plan &plan, cudaStream_t st)
     if (plan.ctas > 0x7fffffffLL)
         return cudaErrorInvalidConfiguration;
     const unsigned grid = (unsigned)plan.ctas;
+    // Crossfades and zero gating run in separate kernel instances, so that
+    // the plain instances compile exactly as without them.
+    const bool ext = p.vramp != nullptr || p.zero_skip != 0;
     switch (plan.variant) {
-    case K1_P1: k1_gather<1, false><<<grid, K1_THREADS, smem_bytes<1>(), st>>>(p, nullptr, nullptr, 0); break;
-    case K1_P4: k1_gather<4, false><<<grid, K1_THREADS, smem_bytes<4>(), st>>>(p, nullptr, nullptr, 0); break;
+    case K1_P1:
+        if (ext)
+            k1_gather<1, false, true><<<grid, K1_THREADS, smem_bytes<1>(), st>>>(p, nullptr, nullptr, 0);
+        else
+            k1_gather<1, false><<<grid, K1_THREADS, smem_bytes<1>(), st>>>(p, nullptr, nullptr, 0);
+        break;
+    case K1_P4:
+        if (ext)
+            k1_gather<4, false, true><<<grid, K1_THREADS, smem_bytes<4>(), st>>>(p, nullptr, nullptr, 0);
+        else
+            k1_gather<4, false><<<grid, K1_THREADS, smem_bytes<4>(), st>>>(p, nullptr, nullptr, 0);
+        break;
     case K1_P11:
-        k1_gather<K1_PBIG, false><<<grid, K1_THREADS, smem_bytes<K1_PBIG>(), st>>>(p, nullptr, nullptr, 0);
+        if (ext)
+            k1_gather<K1_PBIG, false, true><<<grid, K1_THREADS, smem_bytes<K1_PBIG>(), st>>>(p, nullptr, nullptr, 0);
+        else
+            k1_gather<K1_PBIG, false><<<grid, K1_THREADS, smem_bytes<K1_PBIG>(), st>>>(p, nullptr, nullptr, 0);
         break;
     default: return cudaErrorInvalidValue;
     }

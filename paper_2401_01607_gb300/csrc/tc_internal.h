@@ -70,6 +70,7 @@ struct K1Params {
     float *partial;          // [nitems][ntile][nin*nchunk][K1_MO] chunk sums
     unsigned *counter;       // [nitems][ntile], zero between launches
     int *err;                // device error word
+    int zero_skip;           // 1: skip passes whose staged input is all zero (exact)
 };
 
 // Variants: passes of K1_SEG taps per thread per chunk (KC = 32 * 20 * P).

@@ -291,3 +291,42 @@ def test_crossfade_errors():
         capi.tc_set_ir_at(s, h, 149)
     finally:
         capi.tc_close(s)
+
+
+def test_zero_gating_is_exact():
+    """Zero gating (the zero-skip of Sec. 3.2 / 4.2 at block level, threshold
+    0): input with long silent stretches gives bit-identical output with the
+    gating on and off, for every chunk variant, and matches the oracle."""
+    C, N, L, B = 3, 40_000, 9000, 128
+    x = synth.audio_block(C, N, 95)
+    x[:, 2000:21000] = 0.0   # silence longer than L: whole windows are zero
+    x[1, 30000:31000] = 0.0
+    H = np.stack([np.stack([synth.decayed_ir(L, 1500.0, 9300 + 10 * c + v) for v in range(2)])
+                  for c in range(C)])
+    vs = [0, 25000]
+    outs = {}
+    for variant in (0, 1, 2):
+        for gate in (0, 1):
+            s = capi.tc_open_group(C, L, B, False, capi.TC_FP32, 8192)
+            try:
+                capi.tc_set_tuning(s, capi.TC_TUNE_K1_CHUNK, variant)
+                capi.tc_set_tuning(s, capi.TC_TUNE_ZERO_SKIP, gate)
+                res, pos, v = [], 0, 0
+                while pos < N:
+                    n = min(8192, N - pos)
+                    while v < len(vs) and vs[v] < pos + n:
+                        capi.tc_set_ir_rows(s, np.ascontiguousarray(H[:, v]), L, max(vs[v], pos))
+                        v += 1
+                    y = np.empty((C, n), np.float32)
+                    capi.tc_push(s, np.ascontiguousarray(x[:, pos:pos + n]), n, y)
+                    res.append(y)
+                    pos += n
+                tail = np.empty((C, L - 1), np.float32)
+                capi.tc_flush(s, tail, L - 1)
+            finally:
+                capi.tc_close(s)
+            outs[(variant, gate)] = np.concatenate(res + [tail], axis=1)
+        assert np.array_equal(outs[(variant, 0)], outs[(variant, 1)]), variant
+    for c in range(C):
+        ref = _ref(x[c], H[c], vs, B)
+        assert rel_l2(outs[(2, 1)][c], ref) <= TOL["fp32"], c

@@ -91,6 +91,10 @@ def _load(mutant: int = 0) -> ctypes.CDLL:
         lib.tco_direct_at_xf.restype = ctypes.c_double
         lib.tco_buffer_xf.argtypes = [_f32p, _i64, _f32p, _i64, _i64p, _i64p, _i64, _i64, _f64p]
         lib.tco_buffer_xf.restype = ctypes.c_int
+        _i16p = np.ctypeslib.ndpointer(dtype=np.int16, flags="C_CONTIGUOUS")
+        _i64o = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+        lib.tco_q15_direct.argtypes = [_i16p, _i64, _i16p, _i64, _i64o, _i16p]
+        lib.tco_q15_direct.restype = ctypes.c_int
         lib.tco_mutant_id.argtypes = []
         lib.tco_mutant_id.restype = ctypes.c_int
         _LIBS[mutant] = lib
@@ -139,6 +143,18 @@ class Oracle:
         if rc:
             raise ValueError(f"tco_buffer_xf failed ({rc})")
         return y
+
+    def q15(self, x, h):
+        """Exact Q15 convolution (Sec. 5.3.1, one requantization): returns
+        (acc int64 exact sums, y int16 requantized, round half to even)."""
+        x = np.ascontiguousarray(x, dtype=np.int16).reshape(-1)
+        h = np.ascontiguousarray(h, dtype=np.int16).reshape(-1)
+        acc = np.empty(x.size + h.size - 1, dtype=np.int64)
+        y = np.empty(x.size + h.size - 1, dtype=np.int16)
+        rc = self.lib.tco_q15_direct(x, x.size, h, h.size, acc, y)
+        if rc:
+            raise ValueError(f"tco_q15_direct failed ({rc})")
+        return acc, y
 
     def direct(self, x, H, vstart=None) -> np.ndarray:
         x, H, vstart = _prep(x, H, vstart)
@@ -255,6 +271,10 @@ def buffer_xf(x, H, vstart, vramp, Nb: int = 8192):
 
 def direct_at_xf(x, H, vstart, vramp, m):
     return default().direct_at_xf(x, H, vstart, vramp, m)
+
+
+def q15(x, h):
+    return default().q15(x, h)
 
 
 def mimo(X, H, vstart=None, Nb: int = 8192):

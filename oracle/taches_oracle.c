@@ -28,9 +28,9 @@
  *   tco_vect                   : the vectorised algorithm of Sec. 4.1.
  *   tco_buf_*                  : the buffer (ring) algorithm of Sec. 4.2,
  *                                with the readings listed at tco_buf_push.
- * Plus tco_mimo, a sum over input channels of buffer-algorithm outputs, and
+ * Plus tco_mimo, a sum over input channels of buffer-algorithm outputs,
  * tco_direct_at_xf / tco_buffer_xf, the crossfaded (continuous) form of the
- * time-varying IR.
+ * time-varying IR, and tco_q15_direct, the exact fixed-point form.
  *
  * Parity pins (tests): unit impulse, linearity, commutativity (Sec. 3.2,
  * Fig. 6), output length N+L-1 (Sec. 4.1), sum invariant, a geometric-sum
@@ -421,6 +421,53 @@ int tco_buffer_xf(const float *x, int64_t N, const float *H, int64_t L, const in
     tco_buf_flush(s, y + N);
     tco_buf_close(s);
     free(h);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Exact fixed point with one requantization (Sec. 5.3.1, "ideal
+ * requantization": an accumulator of unlimited range, a single
+ * requantization at the end of each output sample). Input and taps are Q15
+ * (int16); each product is exact in 32 bits; the sum of an output's products
+ * is kept exactly in 64 bits (|sum| < 2^49 for L <= 2^19), then requantized
+ * once to Q15: round half to even of sum / 2^15, saturated to int16.
+ *   acc[m] = sum_n x[n] * h[m - n]   (exact),   y[m] = sat16(rne(acc[m] / 2^15)).
+ * acc or y may be NULL.                                                  */
+/* ------------------------------------------------------------------ */
+static int16_t requant_q15(int64_t a)
+{
+#if ORACLE_MUTANT == 9
+    int64_t q = (a + (1 << 14)) >> 15;                     /* rounds halves up, not to even */
+#else
+    int64_t q = a >> 15;                                   /* floor(a / 2^15) */
+    const int64_t rem = a - q * 32768;                     /* in [0, 2^15) */
+    if (rem > 16384 || (rem == 16384 && (q & 1)))
+        ++q;
+#endif
+    if (q > 32767)
+        q = 32767;
+    if (q < -32768)
+        q = -32768;
+    return (int16_t)q;
+}
+
+int tco_q15_direct(const int16_t *x, int64_t N, const int16_t *h, int64_t L, int64_t *acc, int16_t *y)
+{
+    if (N < 1 || L < 1 || L > (int64_t)1 << 19)
+        return -1;
+    for (int64_t m = 0; m < N + L - 1; ++m) {
+        int64_t n_lo = m - (L - 1);
+        if (n_lo < 0)
+            n_lo = 0;
+        const int64_t n_hi = (m < N - 1) ? m : N - 1;
+        int64_t a = 0;
+        for (int64_t n = n_lo; n <= n_hi; ++n)
+            a += (int64_t)((int32_t)x[n] * (int32_t)h[m - n]);
+        if (acc)
+            acc[m] = a;
+        if (y)
+            y[m] = requant_q15(a);
+    }
     return 0;
 }
 

@@ -329,6 +329,38 @@ def check_crossfade_superposition(o):
     return None
 
 
+def check_q15_exact(o):
+    """Exact fixed point (Sec. 5.3.1): on Q15 data the FP64 buffer oracle is
+    itself exact (every product has <= 32 significant bits and every partial
+    sum is a multiple of 2^-30 below 2^19), so the integer sums must equal
+    2^30 times it, exactly; the single requantization is round half to even
+    (numpy.rint) of sum / 2^15, saturated to int16. Includes exact halves and
+    saturating sums."""
+    r = _rng(30)
+    for N, L in [(300, 40), (50, 200), (1, 1), (777, 513)]:
+        xq = r.integers(-32768, 32768, N).astype(np.int16)
+        hq = r.integers(-32768, 32768, L).astype(np.int16)
+        acc, y = o.q15(xq, hq)
+        f = o.buffer(xq.astype(np.float32) / 32768.0, (hq.astype(np.float32) / 32768.0)[None], None, 37)
+        if not np.array_equal(acc.astype(np.float64), f * 2.0 ** 30):
+            return f"N={N} L={L}: integer sums differ from the exact FP64 form"
+        ref = np.clip(np.rint(acc / 32768.0), -32768, 32767).astype(np.int16)
+        if not np.array_equal(y, ref):
+            return f"N={N} L={L}: requantization differs"
+    # Exact halves: x = 1 (Q15 raw 1), taps of odd multiples of 2^14 -> sums k * 2^14.
+    xq = np.array([1, 0, 0], np.int16)
+    hq = np.array([16384, -16384, 16384 * 3 // 3, -32768], np.int16)
+    acc, y = o.q15(xq, hq)
+    ref = np.clip(np.rint(acc / 32768.0), -32768, 32767).astype(np.int16)
+    if not np.array_equal(y, ref):
+        return f"halves: {y} vs {ref}"
+    # Saturation: full-scale input against a full-scale IR.
+    acc, y = o.q15(np.full(8, -32768, np.int16), np.full(8, -32768, np.int16))
+    if y.max() != 32767:
+        return "no positive saturation"
+    return None
+
+
 ALL = {
     "worked_example": check_worked_example,
     "impulse": check_impulse,
@@ -344,6 +376,7 @@ ALL = {
     "mimo": check_mimo,
     "crossfade_hard": check_crossfade_hard,
     "crossfade_superposition": check_crossfade_superposition,
+    "q15_exact": check_q15_exact,
 }
 
 

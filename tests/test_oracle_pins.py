@@ -11,7 +11,7 @@ def test_pin(oracle, name):
     assert msg is None, msg
 
 
-@pytest.mark.parametrize("mutant", [1, 2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("mutant", [1, 2, 3, 4, 5, 6, 7, 8, 9])
 def test_planted_mistake_is_caught(mutant):
     """Each mutant build plants one plausible mistake; some pin must fail."""
     import oracle as O

@@ -58,6 +58,14 @@ def fp32_peak_tflops(mhz: float) -> float:
     return SM_COUNT * FMA_PER_CLK * 2 * mhz * 1e6 / 1e12
 
 
+DP2A_PER_CLK = 64  # dp2a (and 32-bit IMAD) issue rate per SM per clock
+
+
+def q15_peak_macs(mhz: float) -> float:
+    """Exact Q15 path: one dp2a per tap-MAC, so its ALU peak in tap-MAC/s."""
+    return SM_COUNT * DP2A_PER_CLK * mhz * 1e6
+
+
 def workload_config(P: int) -> dict:
     return {
         "workload": "64 independent streams x 10 s @ 48 kHz, own IRs L=48000 swapped every 24000 samples, block 128",
@@ -183,6 +191,12 @@ def _oracle_job(args):
         t0 = time.perf_counter()
         o.buffer(x, h[None], np.zeros(1, np.int64), 256)
         return time.perf_counter() - t0, b * L
+    if kind == "q15":  # segment a of the Q15 workload's input, b samples, whole IR
+        xq = sy.q15_codes(sy.audio(2_880_000, sy.x_seed(7, 0)))[a:a + b]
+        hq = sy.q15_codes(sy.decayed_ir(48_000, 4800.0, sy.ir_seed(7, 0)))
+        t0 = time.perf_counter()
+        o.q15(xq, hq)
+        return time.perf_counter() - t0, b * 48_000
     # mimo: pair a = (output, input) of the MIMO workload, first b samples
     L, nin = 192_000, 16
     out_, inp = divmod(a, nin)
@@ -193,7 +207,7 @@ def _oracle_job(args):
     return time.perf_counter() - t0, b * L
 
 
-def oracle_other_workloads(cores: int) -> dict:
+def oracle_other_workloads(cores: int, only_q15: bool = False) -> dict:
     """The FP64 oracle timed on bounded samples of the mono, shared-IR and MIMO
     workloads, jobs spread over the host cores (spawned before any CUDA call)."""
     import oracle
@@ -206,7 +220,12 @@ def oracle_other_workloads(cores: int) -> dict:
              "mimo": ([("mimo", a, 4_800) for a in (0 * 16 + i for i in range(16))] +
                       [("mimo", a, 4_800) for a in (15 * 16 + i for i in range(16))],
                       "2 of the 16 MIMO outputs (all 16 inputs each), first 4800 samples (L=192000), "
-                      "32 pair jobs over the cores")}
+                      "32 pair jobs over the cores"),
+             "q15": ([("q15", 180_000 * k, 24_000) for k in range(16)],
+                     "16 segments of 24000 input samples of the Q15 workload (whole 48000-tap IR each), "
+                     "one segment per core")}
+    if only_q15:
+        plans = {"q15": plans["q15"]}
     with ctx.Pool(cores) as pool:
         pool.map(_oracle_job, [("warm", 0, 0)] * cores)
         for name, (jobs, desc) in plans.items():
@@ -337,32 +356,102 @@ def load_peaks() -> dict:
         return {}
 
 
+def eq4_at(x: np.ndarray, H: np.ndarray, vstart, m: int) -> float:
+    """Eq. (4) at one output m, in float64: the sum over n of x[n] h_{v(n)}[m - n],
+    v(n) the last version starting at or before n. A self-check of the timed
+    outputs; parity against the oracle is the tests' job."""
+    L = H.shape[1]
+    lo, hi = max(0, m - L + 1), min(x.size, m + 1)
+    if hi <= lo:
+        return 0.0
+    n = np.arange(lo, hi)
+    v = np.searchsorted(np.asarray(vstart, np.int64), n, side="right") - 1
+    return float(np.dot(x[lo:hi].astype(np.float64), H[v, m - n].astype(np.float64)))
+
+
+class PushRun:
+    """Device buffers and push loop of one pass over a workload: x [rows, N] laid
+    out push-major (push i is one contiguous [row][n] slab), pushes of P samples
+    through tc_push with device pointers, then the L-1 flush into tail."""
+
+    def __init__(self, torch, x: np.ndarray, P: int, out_rows: int, L: int):
+        rows, N = x.shape
+        self.torch, self.P, self.N, self.L, self.out_rows = torch, P, N, L, out_rows
+        self.npush = math.ceil(N / P)
+        xp = np.zeros((self.npush, rows, P), np.float32)
+        for i in range(self.npush):
+            seg = x[:, i * P:(i + 1) * P]
+            xp[i].reshape(-1)[:seg.size] = seg.reshape(-1)
+        self.x_d = torch.from_numpy(xp).cuda()
+        self.y_d = torch.empty((self.npush, out_rows, P), device="cuda")
+        self.tail_d = torch.empty((out_rows, L - 1), device="cuda")
+        self.ts = torch.cuda.Stream()
+
+    def run(self, capi, s, h_ptr: int, n_samples: int | None = None) -> None:
+        n_samples = self.N if n_samples is None else n_samples
+        capi.tc_reset(s)
+        capi.tc_set_ir_rows(s, h_ptr, self.L, 0, on_device=True)
+        pos = 0
+        for i in range(self.npush):
+            if pos >= n_samples:
+                break
+            n = min(self.P, n_samples - pos)
+            capi.tc_push(s, int(self.x_d[i].data_ptr()), n, int(self.y_d[i].data_ptr()), on_device=True)
+            pos += n
+        capi.tc_flush_dev(s, int(self.tail_d.data_ptr()))
+
+    def outputs(self, picks) -> np.ndarray:
+        """Outputs (row, m) of the last full pass, m in [0, N + L - 1)."""
+        y = self.y_d.cpu().numpy()
+        tail = self.tail_d.cpu().numpy()
+        got = []
+        for r, m in picks:
+            if m < self.N:
+                i, j = divmod(m, self.P)
+                n = min(self.P, self.N - i * self.P)
+                got.append(y[i].reshape(-1)[r * n + j])
+            else:
+                got.append(tail[r, m - self.N])
+        return np.array(got, np.float64)
+
+    def close(self):
+        del self.x_d, self.y_d, self.tail_d
+        self.torch.cuda.empty_cache()
+
+
+def _err(got: np.ndarray, ref: np.ndarray) -> dict:
+    return {"sampled_outputs": int(got.size), "rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+            "max_abs": float(np.max(np.abs(got - ref))), "against": "Eq. (4) at each output, float64"}
+
+
+def shared_picks(C: int, N: int, L: int):
+    rng = np.random.default_rng(7)
+    return [(int(rng.integers(C)), int(rng.integers(N + L - 1))) for _ in range(24)]
+
+
+def mimo_picks(nout: int, N: int, L: int):
+    rng = np.random.default_rng(9)
+    return [(int(rng.integers(nout)), int(rng.integers(N + L - 1))) for _ in range(32)]
+
+
 def bench_shared(torch, steps: int, warmup: int, P: int = 8192, C: int = 1024, N: int = 240_000,
                  precisions=("bf16split", "bf16", "fp32")) -> dict:
     """Shared-IR workload: 1024 streams x 5 s at 48 kHz, one IR L = 96000 (tau 19200), block 256.
     Each precision is one full pass per step (pushes of P samples, device pointers, then the flush).
     C and N shrink it for profiling captures."""
     from paper_2401_01607_gb300 import capi
-    import oracle
     L, B = 96_000, 256
     w = synth.shared(C=C, N=N, L=L, block=B)
-    npush = math.ceil(N / P)
-    xp = np.zeros((npush, C, P), np.float32)
-    for i in range(npush):
-        seg = w.x[:, i * P:(i + 1) * P]
-        xp[i].reshape(-1)[:seg.size] = seg.reshape(-1)
-    x_d = torch.from_numpy(xp).cuda()
+    run = PushRun(torch, w.x, P, C, L)
     h_d = torch.from_numpy(np.ascontiguousarray(w.H[0][None])).cuda()
-    y_d = torch.empty((npush, C, P), device="cuda")
-    tail_d = torch.empty((C, L - 1), device="cuda")
     macs = C * N * L
     peaks = load_peaks()
     bf16_peak = float(peaks.get("bf16_tflops_sustained", 1690.8))
     out = {"workload": "%d streams x %d samples (%.1f s @ 48 kHz), one shared IR L=96000 tau=19200, "
                        "block 256, pushes of %d" % (C, N, N / FS, P), "tap_macs": macs}
-    ts = torch.cuda.Stream()
-    rng = np.random.default_rng(7)
-    picks = [(int(rng.integers(C)), int(rng.integers(N + L - 1))) for _ in range(24)]
+    ts = run.ts
+    picks = shared_picks(C, N, L)
+    refs = np.array([eq4_at(w.x[c], w.H, w.vstart, m) for c, m in picks])
     for name, prec in (("bf16split", capi.TC_BF16_SPLIT), ("bf16", capi.TC_BF16), ("fp32", capi.TC_FP32)):
         if name not in precisions:
             continue
@@ -370,12 +459,7 @@ def bench_shared(torch, steps: int, warmup: int, P: int = 8192, C: int = 1024, N
         capi.tc_set_cuda_stream(s, ts)
 
         def step():
-            capi.tc_reset(s)
-            capi.tc_set_ir_rows(s, int(h_d.data_ptr()), L, 0, on_device=True)
-            for i in range(npush):
-                n = min(P, N - i * P)
-                capi.tc_push(s, int(x_d[i].data_ptr()), n, int(y_d[i].data_ptr()), on_device=True)
-            capi.tc_flush_dev(s, int(tail_d.data_ptr()))
+            run.run(capi, s, int(h_d.data_ptr()))
 
         nst = 1 if name == "fp32" else steps
         for _ in range(max(1, warmup if name != "fp32" else 1)):
@@ -393,24 +477,9 @@ def bench_shared(torch, steps: int, warmup: int, P: int = 8192, C: int = 1024, N
         info = capi.tc_get_info(s)
         capi.tc_close(s)
         ms = e0.elapsed_time(e1) / nst
-        # Sampled outputs against Eq. (4) one by one (FP64).
-        y = y_d.cpu().numpy()
-        tail = tail_d.cpu().numpy()
-        got, ref = [], []
-        for c, m in picks:
-            if m < N:
-                i, j = divmod(m, P)
-                n = min(P, N - i * P)
-                got.append(y[i].reshape(-1)[c * n + j])
-            else:
-                got.append(tail[c, m - N])
-            ref.append(oracle.direct_at(w.x[c], w.H, w.vstart, m))
-        got, ref = np.array(got, np.float64), np.array(ref)
         r = {"ms_per_step": ms, "value": macs / (ms / 1e3), "unit": "tap-MAC/s",
              "kernel_ms_per_step": k_ms / nst, "launches_per_step": k_n / nst,
-             "check": {"sampled_outputs": len(picks),
-                       "rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
-                       "max_abs": float(np.max(np.abs(got - ref)))},
+             "check": _err(run.outputs(picks), refs),
              "tensor_launches": int(info.tensor_launches), "fp32_fallbacks": int(info.fp32_fallbacks)}
         if name != "fp32":
             nprod = 3 if name == "bf16split" else 1
@@ -426,8 +495,8 @@ def bench_shared(torch, steps: int, warmup: int, P: int = 8192, C: int = 1024, N
                              "unit": "TFLOP/s", "frac": tflops / fp32_peak_tflops(SM_MAX_MHZ),
                              "kernel": "k1_gather (FP32 FMA)"}
         out[name] = r
-    del x_d, y_d, tail_d, h_d
-    torch.cuda.empty_cache()
+    del h_d
+    run.close()
     return out
 
 
@@ -440,25 +509,15 @@ def bench_mimo(torch, P: int = 8192, precisions=("bf16split", "bf16", "fp32"), L
     Sampled outputs are checked against the oracle's direct sums (one per
     input, added in FP64). L and seconds shrink it for profiling captures."""
     from paper_2401_01607_gb300 import capi
-    import oracle
     w = synth.mimo(N=int(seconds * FS), L=L)
     nin, nout = w.mimo
     N, L, B = w.x.shape[1], w.L, w.block
-    npush = math.ceil(N / P)
-    xp = np.zeros((npush, nin, P), np.float32)
-    for i in range(npush):
-        seg = w.x[:, i * P:(i + 1) * P]
-        n = seg.shape[1]
-        xp[i].reshape(-1)[:nin * n] = seg.reshape(-1)
-    x_d = torch.from_numpy(xp).cuda()
+    run = PushRun(torch, w.x, P, nout, L)
     h_d = torch.from_numpy(np.ascontiguousarray(w.H[0])).cuda()  # [nout][nin][L]
-    y_d = torch.empty((npush, nout, P), device="cuda")
-    tail_d = torch.empty((nout, L - 1), device="cuda")
-    ts = torch.cuda.Stream()
+    ts = run.ts
     macs = nout * nin * N * L
-    rng = np.random.default_rng(9)
-    picks = [(int(rng.integers(nout)), int(rng.integers(N + L - 1))) for _ in range(32)]
-    refs = np.array([sum(oracle.direct_at(w.x[i_], w.H[0, o, i_][None], w.vstart, m) for i_ in range(nin))
+    picks = mimo_picks(nout, N, L)
+    refs = np.array([sum(eq4_at(w.x[i_], w.H[0, o, i_][None], w.vstart, m) for i_ in range(nin))
                      for o, m in picks])
     peaks = load_peaks()
     bf16_peak = float(peaks.get("bf16_tflops_sustained", 1690.8))
@@ -469,25 +528,12 @@ def bench_mimo(torch, P: int = 8192, precisions=("bf16split", "bf16", "fp32"), L
         s = capi.tc_open_mimo(nin, nout, L, B, prec, P)
         try:
             capi.tc_set_cuda_stream(s, ts)
-
-            def step(n_samples):
-                capi.tc_reset(s)
-                capi.tc_set_ir_rows(s, int(h_d.data_ptr()), L, 0, on_device=True)
-                pos = 0
-                for i in range(npush):
-                    if pos >= n_samples:
-                        break
-                    n = min(P, n_samples - pos)
-                    capi.tc_push(s, int(x_d[i].data_ptr()), n, int(y_d[i].data_ptr()), on_device=True)
-                    pos += n
-                capi.tc_flush_dev(s, int(tail_d.data_ptr()))
-
-            step(4 * P)  # warm-up: a short segment
+            run.run(capi, s, int(h_d.data_ptr()), 4 * P)  # warm-up: a short segment
             ts.synchronize()
             capi.tc_profile(s, True)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(ts)
-            step(N)
+            run.run(capi, s, int(h_d.data_ptr()))
             e1.record(ts)
             e1.synchronize()
             k_ms, k_n, k_macs = capi.tc_profile_read(s)
@@ -496,22 +542,9 @@ def bench_mimo(torch, P: int = 8192, precisions=("bf16split", "bf16", "fp32"), L
         finally:
             capi.tc_close(s)
         ms = e0.elapsed_time(e1)
-        y = y_d.cpu().numpy()
-        tail = tail_d.cpu().numpy()
-        got = []
-        for o, m in picks:
-            if m < N:
-                i, j = divmod(m, P)
-                n = min(P, N - i * P)
-                got.append(y[i].reshape(-1)[o * n + j])
-            else:
-                got.append(tail[o, m - N])
-        got = np.array(got, np.float64)
         r = {"ms_per_step": ms, "value": macs / (ms / 1e3), "unit": "tap-MAC/s",
              "realtime_factor": (N / FS) / (ms / 1e3), "kernel_ms_per_step": k_ms, "launches": k_n,
-             "check": {"sampled_outputs": len(got),
-                       "rel_l2": float(np.linalg.norm(got - refs) / np.linalg.norm(refs)),
-                       "max_abs": float(np.max(np.abs(got - refs)))},
+             "check": _err(run.outputs(picks), refs),
              "tensor_launches": int(info.tensor_launches), "fp32_fallbacks": int(info.fp32_fallbacks)}
         if name == "fp32":
             tflops = 2.0 * k_macs / (k_ms / 1e3) / 1e12 if k_ms > 0 else 0.0
@@ -526,8 +559,8 @@ def bench_mimo(torch, P: int = 8192, precisions=("bf16split", "bf16", "fp32"), L
                              "peak_basis": "measured cuBLAS bf16, sustained (MEASURED_PEAKS.json)",
                              "flops_counted": f"2 x {nprod} products x useful tap-MACs"}
         out[name] = r
-    del x_d, y_d, tail_d, h_d
-    torch.cuda.empty_cache()
+    del h_d
+    run.close()
     return out
 
 
@@ -579,6 +612,95 @@ def bench_mono(capi) -> dict:
             "one_shot_ms": t_conv * 1e3, "one_shot_tap_macs_per_s": N * L / t_conv,
             "mode": "tc_push_block per 64-sample block (host buffers, synchronous), then tc_flush; one-shot "
                     "tc_convolve on device buffers"}
+
+
+Q15_N, Q15_L = 2_880_000, 48_000
+
+
+def q15_inputs():
+    """Q15 workload: 60 s of 48 kHz audio and a 1 s decayed IR (tau 0.1 s, sum |h| = 1), as Q15 codes."""
+    xq = synth.q15_codes(synth.audio(Q15_N, synth.x_seed(7, 0)))
+    hq = synth.q15_codes(synth.decayed_ir(Q15_L, 4800.0, synth.ir_seed(7, 0)))
+    return xq, hq
+
+
+def bench_q15(torch, capi, reps: int = 6) -> dict:
+    """Exact Q15 fixed point (K4 + one requantization, Sec. 5.3.1) on device buffers,
+    each inner-loop form; L2 flushed before each timed call; then the same call
+    with host buffers (copies inside the timed region)."""
+    xq, hq = q15_inputs()
+    N, L = Q15_N, Q15_L
+    ny = N + L - 1
+    st = torch.cuda.current_stream()
+    x_d, h_d = torch.from_numpy(xq).cuda(), torch.from_numpy(hq).cuda()
+    y_d = torch.empty(ny, dtype=torch.int16, device="cuda")
+    acc_d = torch.empty(ny, dtype=torch.int64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out = {"workload": f"Q15 codes, N={N} (60 s at 48 kHz), L={L} (1 s IR, tau 0.1 s)",
+           "macs_per_call": N * L, "l2": "256 MB buffer written before each timed call"}
+    saved = os.environ.get("TC_Q15_INNER")
+    ys = {}
+    try:
+        for inner in ("dp2a", "imad"):
+            os.environ["TC_Q15_INNER"] = inner
+            for _ in range(2):
+                capi.tc_convolve_q15(x_d, N, h_d, L, y_d, acc_d, st)
+            l0 = capi.tc_kernel_launches()
+            tot = 0.0
+            for _ in range(reps):
+                flush.fill_(1)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                capi.tc_convolve_q15(x_d, N, h_d, L, y_d, acc_d, st)
+                e1.record(st)
+                e1.synchronize()
+                tot += e0.elapsed_time(e1)
+            ms = tot / reps
+            out[inner] = {"ms_per_call": ms, "tap_macs_per_s": N * L / (ms / 1e3),
+                          "gpu_launches_per_call": (capi.tc_kernel_launches() - l0) / reps}
+            ys[inner] = (y_d.cpu().numpy(), acc_d.cpu().numpy())
+    finally:
+        if saved is None:
+            os.environ.pop("TC_Q15_INNER", None)
+        else:
+            os.environ["TC_Q15_INNER"] = saved
+    # K4 runs one dp2a per tap-MAC (two per pair of taps: high and low byte of h).
+    peak = q15_peak_macs(SM_MAX_MHZ) / 1e12
+    achieved = out["dp2a"]["tap_macs_per_s"] / 1e12
+    out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T dp2a/s",
+                       "frac": achieved / peak, "traffic": None,
+                       "kernel": "k4_q15 (dp2a form) + k4_requant, whole call timed (memset, K4, requant)",
+                       "peak_basis": "152 SM x 64 dp2a/clk x 2070 MHz (max SM clock); 64/clk/SM measured by an "
+                                     "issue-rate loop, the same rate as 32-bit IMAD",
+                       "work_counted": "one dp2a per useful tap-MAC (N x L per call)"}
+    out["forms_agree_bitwise"] = bool(np.array_equal(ys["dp2a"][0], ys["imad"][0]) and
+                                      np.array_equal(ys["dp2a"][1], ys["imad"][1]))
+    # e2e: pinned host codes in, int16 outputs out, copies inside the timed region.
+    x_h = torch.from_numpy(xq).pin_memory()
+    h_h = torch.from_numpy(hq).pin_memory()
+    y_h = torch.empty(ny, dtype=torch.int16).pin_memory()
+    t_e2e = []
+    for rep in range(4):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x_d.copy_(x_h, non_blocking=True)
+        h_d.copy_(h_h, non_blocking=True)
+        capi.tc_convolve_q15(x_d, N, h_d, L, y_d, None, st)
+        y_h.copy_(y_d, non_blocking=True)
+        st.synchronize()
+        if rep:
+            t_e2e.append(time.perf_counter() - t0)
+    dt = float(np.mean(t_e2e))
+    out["e2e"] = {"value": N * L / dt, "unit": "tap-MAC/s", "h2d_bytes_per_step": 2 * (N + L),
+                  "d2h_bytes_per_step": 2 * ny, "ms_per_step": dt * 1e3,
+                  "path": "pinned host codes -> tc_convolve_q15 (no acc) -> pinned host outputs"}
+    # The host-buffer call must give the device call's outputs bit for bit (parity with the
+    # oracle is the tests' job: tests/test_gpu_q15.py checks this workload's launch).
+    out["e2e_matches_device"] = bool(np.array_equal(y_h.numpy(), ys["dp2a"][0]))
+    del flush
+    torch.cuda.empty_cache()
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -840,28 +962,32 @@ def bench_serving(torch, capi, H64: np.ndarray, trace_s: float) -> dict:
     return out
 
 
-def check_sampled(runner, n_check=64) -> dict:
-    """Sampled outputs of the last device step against Eq. (4) computed one by one (FP64 oracle)."""
-    import oracle
-    w = runner.w
+def main_picks(n_check: int = 64):
+    rng = np.random.default_rng(123)
+    return [(int(rng.integers(C_STREAMS)), int(rng.integers(N_SAMPLES + L_TAPS - 1))) for _ in range(n_check)]
+
+
+def runner_outputs(runner, picks) -> np.ndarray:
+    """Outputs (stream, m) of the runner's last device step."""
     y = runner.y_d.cpu().numpy()
     tail = runner.tail_d.cpu().numpy()
-    rng = np.random.default_rng(123)
-    got, ref = [], []
-    for _ in range(n_check):
-        c = int(rng.integers(C_STREAMS))
-        m = int(rng.integers(N_SAMPLES + L_TAPS - 1))
+    got = []
+    for c, m in picks:
         if m < N_SAMPLES:
             i, j = divmod(m, runner.P)
             n = min(runner.P, N_SAMPLES - i * runner.P)
             got.append(y[i].reshape(-1)[c * n + j])
         else:
             got.append(tail[c, m - N_SAMPLES])
-        ref.append(oracle.direct_at(w.x[c], w.H[c], w.vstart, m))
-    got = np.array(got, np.float64)
-    ref = np.array(ref)
-    return {"sampled_outputs": n_check, "rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
-            "max_abs": float(np.max(np.abs(got - ref)))}
+    return np.array(got, np.float64)
+
+
+def check_sampled(runner, n_check=64) -> dict:
+    """Sampled outputs of the last device step against Eq. (4) at each output."""
+    picks = main_picks(n_check)
+    w = runner.w
+    ref = np.array([eq4_at(w.x[c], w.H[c], w.vstart, m) for c, m in picks])
+    return _err(runner_outputs(runner, picks), ref)
 
 
 def traffic_from_profile(kernel_src: str) -> float | None:
@@ -917,6 +1043,8 @@ def main():
     ap.add_argument("--only-serving", action="store_true", help="run only the serving section")
     ap.add_argument("--trace-seconds", type=float, default=15.0)
     ap.add_argument("--no-mimo", action="store_true", help="skip the MIMO section")
+    ap.add_argument("--no-q15", action="store_true", help="skip the exact Q15 section")
+    ap.add_argument("--only-q15", action="store_true", help="run only the exact Q15 section")
     ap.add_argument("--only-mimo", action="store_true", help="run only the MIMO section")
     ap.add_argument("--mimo-prec", default="bf16split,bf16,fp32", help="MIMO section: precisions")
     ap.add_argument("--mimo-L", type=int, default=192_000, help="MIMO section: IR length")
@@ -942,7 +1070,7 @@ def main():
         cpu = oracle_baseline(os.cpu_count() or 1, args.cpu_samples)
         cpu["cpu_model"] = cpu_model()
         if not (args.only_shared or args.only_serving):
-            cpu_other = oracle_other_workloads(os.cpu_count() or 1)
+            cpu_other = oracle_other_workloads(os.cpu_count() or 1, only_q15=args.only_q15)
 
     import torch
     import paper_2401_01607_gb300 as pkg
@@ -963,6 +1091,13 @@ def main():
         if cpu_other:
             mimo["cpu_baseline"], mono["cpu_baseline"] = cpu_other["mimo"], cpu_other["mono"]
         print(json.dumps({"mimo": mimo, "mono": mono}), flush=True)
+        dist.close()
+        return
+    if args.only_q15:
+        q15 = bench_q15(torch, capi)
+        if cpu_other:
+            q15["cpu_baseline"] = cpu_other["q15"]
+        print(json.dumps({"q15": q15}), flush=True)
         dist.close()
         return
     if args.only_serving:
@@ -1099,6 +1234,11 @@ def main():
         mono = bench_mono(capi)
         if cpu_other:
             mimo["cpu_baseline"], mono["cpu_baseline"] = cpu_other["mimo"], cpu_other["mono"]
+    q15 = None
+    if not args.no_q15 and dist.world == 1:
+        q15 = bench_q15(torch, capi)
+        if cpu_other:
+            q15["cpu_baseline"] = cpu_other["q15"]
     serving = None
     if not args.no_serving and dist.world == 1:
         serving = bench_serving(torch, capi, np.ascontiguousarray(w.H[:, 0]), args.trace_seconds)
@@ -1111,7 +1251,7 @@ def main():
                 "realtime_streams_48k": value / per_stream_rt,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": int(launches), "latency": latency, "check": check, "shared_ir": shared,
-                "serving": serving, "mimo": mimo, "mono": mono,
+                "serving": serving, "mimo": mimo, "mono": mono, "q15": q15,
                 "autotune_push_ms_per_sample": {str(k): v for k, v in tune.items()} or None}
         print(json.dumps(line), flush=True)
     dist.close()

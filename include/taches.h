@@ -241,6 +241,28 @@ tc_status tc_convolve(const float *x, size_t N, const float *h, size_t L, float 
 tc_status tc_convolve_noalloc(const float *x, size_t N, const float *h, size_t L, float *y, void *cuda_stream);
 
 /* ---------------------------------------------------------------------- */
+/* Exact fixed-point convolution with one requantization (Sec. 5.3.1)      */
+/* ---------------------------------------------------------------------- */
+
+/* Q15 input and taps (int16, value = code / 2^15). Every product is summed
+ * exactly, and each output sample is requantized once to Q15, after all of its
+ * products are in (the ideal requantization of Sec. 5.3.1):
+ *   acc[m] = sum_k x[m-k] h[k]                       (int64, Q30, exact)
+ *   y[m]   = clamp(round_half_even(acc[m] / 2^15), -32768, 32767)
+ * for m in [0, N+L-1). The result is bit-exact and independent of how the GPU
+ * splits the work.
+ *   - x: N codes; h: L codes; y: N+L-1 codes; acc: N+L-1 int64. All device
+ *     pointers, owned by the caller. y or acc may be NULL (not both): NULL acc
+ *     uses a temporary from the stream-ordered allocator; NULL y skips the
+ *     requantization.
+ *   - L <= 2^19 keeps |acc| < 2^49, far inside int64.
+ * Runs on cuda_stream (NULL = default stream) and waits for it before
+ * returning. Errors: TC_EINVAL (NULL pointers, N == 0, L == 0 or L > 2^19);
+ * TC_ENOMEM; TC_ECUDA. */
+tc_status tc_convolve_q15(const int16_t *x, size_t N, const int16_t *h, size_t L, int16_t *y, int64_t *acc,
+                          void *cuda_stream);
+
+/* ---------------------------------------------------------------------- */
 /* Serving: continuous batching of many independent streams               */
 /* ---------------------------------------------------------------------- */
 /*

@@ -78,6 +78,7 @@ _SIGS = {
     "tc_sync": [_vp],
     "tc_convolve": [_vp, _sz, _vp, _sz, _vp, _vp],
     "tc_convolve_noalloc": [_vp, _sz, _vp, _sz, _vp, _vp],
+    "tc_convolve_q15": [_vp, _sz, _vp, _sz, _vp, _vp, _vp],
     "tc_set_tuning": [_vp, _int, ctypes.c_longlong],
     "tc_profile": [_vp, _int],
     "tc_profile_read": [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_u64), ctypes.POINTER(ctypes.c_double)],
@@ -148,15 +149,15 @@ def _host_f32(a, writable=False):
     return a, a.ctypes.data_as(_vp)
 
 
-def _dev_ptr(t) -> int:
-    """Device address of a torch CUDA tensor (float32, contiguous) or a raw integer address."""
+def _dev_ptr(t, dtype: str = "float32") -> int:
+    """Device address of a torch CUDA tensor (of `dtype`, contiguous) or a raw integer address."""
     if isinstance(t, int):
         return t
     if getattr(t, "is_cuda", False):
         if not t.is_contiguous():
             raise ValueError("device tensor must be contiguous")
-        if str(t.dtype) != "torch.float32":
-            raise TypeError("device tensor must be float32")
+        if str(t.dtype) != "torch." + dtype:
+            raise TypeError(f"device tensor must be {dtype}")
         return int(t.data_ptr())
     raise TypeError("expected a torch CUDA tensor or an integer device address")
 
@@ -300,6 +301,16 @@ def tc_convolve_noalloc(x, N: int, h, L: int, y, cuda_stream=None) -> None:
     cs = None if cuda_stream is None else (cuda_stream if isinstance(cuda_stream, int) else
                                            int(cuda_stream.cuda_stream))
     _call("tc_convolve_noalloc", _dev_ptr(x), N, _dev_ptr(h), L, _dev_ptr(y), cs)
+
+
+def tc_convolve_q15(x, N: int, h, L: int, y, acc=None, cuda_stream=None) -> None:
+    """Exact Q15 convolution with one requantization per output (Sec. 5.3.1).
+    x (N), h (L), y (N+L-1) are int16 codes on the device; acc, if given, gets the
+    exact int64 sums (N+L-1). y may be None when acc is given."""
+    cs = None if cuda_stream is None else (cuda_stream if isinstance(cuda_stream, int) else
+                                           int(cuda_stream.cuda_stream))
+    _call("tc_convolve_q15", _dev_ptr(x, "int16"), N, _dev_ptr(h, "int16"), L,
+          None if y is None else _dev_ptr(y, "int16"), None if acc is None else _dev_ptr(acc, "int64"), cs)
 
 
 def tc_last_error() -> str:

@@ -50,6 +50,16 @@ def decayed_ir(L: int, tau: float, seed: int) -> np.ndarray:
     return h.astype(np.float32)
 
 
+def q15_codes(a: np.ndarray) -> np.ndarray:
+    """Q15 codes (int16, value = code / 2^15) of float samples: nearest code, clipped to [-32768, 32767]."""
+    return np.clip(np.rint(np.asarray(a, np.float64) * 32768.0), -32768, 32767).astype(np.int16)
+
+
+def q15_full_range(n: int, seed: int) -> np.ndarray:
+    """n int16 codes, uniform over the whole range [-32768, 32767]."""
+    return np.random.default_rng(seed).integers(-32768, 32768, int(n)).astype(np.int16)
+
+
 def ir_seed(stream: int, version: int) -> int:
     return 2_000_000 + 1000 * int(stream) + int(version)
 

@@ -703,6 +703,64 @@ def bench_q15(torch, capi, reps: int = 6) -> dict:
     return out
 
 
+def bench_offline(torch, capi, reps: int = 3) -> dict:
+    """One-shot tc_convolve on device buffers: a short sound through a long IR (the roles are swapped,
+    Sec. 3.2, and timed both ways) and a long signal through a 1 s IR. Beside it, as context only, an FFT
+    convolution of the same operands with torch.fft (cuFFT, FP32), the paper's comparison method."""
+    out = {}
+    cases = {"short_sound_long_ir": (4_800, 480_000), "long_signal_1s_ir": (2_880_000, 48_000)}
+    saved = os.environ.get("TC_NO_ROLE_SWAP")
+    st = torch.cuda.current_stream()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            fn()
+        e1.record(st)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    try:
+        for name, (N, L) in cases.items():
+            x = torch.from_numpy(synth.audio(N, synth.x_seed(8, 0))).cuda()
+            h = torch.from_numpy(synth.decayed_ir(L, 0.2 * L, synth.ir_seed(8, 0))).cuda()
+            y = torch.empty(N + L - 1, device="cuda")
+            os.environ.pop("TC_NO_ROLE_SWAP", None)
+            ms = timed(lambda: capi.tc_convolve(x, N, h, L, y))
+            r = {"N": N, "L": L, "tc_convolve_ms": ms, "tap_macs_per_s": N * L / (ms / 1e3)}
+            # The same convolution without per-call allocation (fixed working array in the library).
+            ms_na = timed(lambda: capi.tc_convolve_noalloc(x, N, h, L, y))
+            r["noalloc_ms"] = ms_na
+            r["noalloc_tap_macs_per_s"] = N * L / (ms_na / 1e3)
+            if N < L:
+                os.environ["TC_NO_ROLE_SWAP"] = "1"
+                y2 = torch.empty_like(y)
+                ms2 = timed(lambda: capi.tc_convolve(x, N, h, L, y2))
+                os.environ.pop("TC_NO_ROLE_SWAP", None)
+                r["caller_roles_ms"] = ms2
+                r["role_swap_speedup"] = ms2 / ms
+                r["orientations_rel_l2"] = float(torch.linalg.norm(y - y2) / torch.linalg.norm(y2))
+            nfft = 1 << int(math.ceil(math.log2(N + L - 1)))
+
+            def fft_conv():
+                return torch.fft.irfft(torch.fft.rfft(x, nfft) * torch.fft.rfft(h, nfft), nfft)[:N + L - 1]
+
+            r["fft_context_ms"] = timed(fft_conv)
+            yf = fft_conv()
+            r["fft_vs_taches_rel_l2"] = float(torch.linalg.norm(yf - y) / torch.linalg.norm(y))
+            out[name] = r
+    finally:
+        if saved is None:
+            os.environ.pop("TC_NO_ROLE_SWAP", None)
+        else:
+            os.environ["TC_NO_ROLE_SWAP"] = saved
+    torch.cuda.empty_cache()
+    return out
+
+
 # ---------------------------------------------------------------------------
 # Serving: continuous batching (tc_server_*) under real-time pacing
 # ---------------------------------------------------------------------------
@@ -1045,6 +1103,7 @@ def main():
     ap.add_argument("--no-mimo", action="store_true", help="skip the MIMO section")
     ap.add_argument("--no-q15", action="store_true", help="skip the exact Q15 section")
     ap.add_argument("--only-q15", action="store_true", help="run only the exact Q15 section")
+    ap.add_argument("--only-offline", action="store_true", help="run only the one-shot (role swap) section")
     ap.add_argument("--only-mimo", action="store_true", help="run only the MIMO section")
     ap.add_argument("--mimo-prec", default="bf16split,bf16,fp32", help="MIMO section: precisions")
     ap.add_argument("--mimo-L", type=int, default=192_000, help="MIMO section: IR length")
@@ -1091,6 +1150,10 @@ def main():
         if cpu_other:
             mimo["cpu_baseline"], mono["cpu_baseline"] = cpu_other["mimo"], cpu_other["mono"]
         print(json.dumps({"mimo": mimo, "mono": mono}), flush=True)
+        dist.close()
+        return
+    if args.only_offline:
+        print(json.dumps({"offline": bench_offline(torch, capi)}), flush=True)
         dist.close()
         return
     if args.only_q15:
@@ -1232,6 +1295,7 @@ def main():
     if not args.no_mimo and dist.world == 1:
         mimo = bench_mimo(torch)
         mono = bench_mono(capi)
+        mono["offline"] = bench_offline(torch, capi)
         if cpu_other:
             mimo["cpu_baseline"], mono["cpu_baseline"] = cpu_other["mimo"], cpu_other["mono"]
     q15 = None

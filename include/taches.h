@@ -203,7 +203,9 @@ tc_status tc_sync(tc_stream *s);
 /* One-shot convolution (off-line use, Sec. 3.2)                           */
 /* ---------------------------------------------------------------------- */
 
-/* y[0..N+L-2] = x[0..N-1] * h[0..L-1], all device pointers, FP32. Runs on
+/* y[0..N+L-2] = x[0..N-1] * h[0..L-1], all device pointers, FP32. When
+ * N < L the operands swap roles (Sec. 3.2: x * h = h * x; the gather's work is
+ * (N + L - 1) L), unless TC_NO_ROLE_SWAP=1 is set in the environment. Runs on
  * cuda_stream (a cudaStream_t as void*; NULL = default stream) and waits
  * for it before returning. Allocates its working memory, which is freed
  * before return. Errors: TC_EINVAL (NULL or zero sizes); TC_ENOMEM; TC_ECUDA;
@@ -220,12 +222,13 @@ tc_status tc_convolve(const float *x, size_t N, const float *h, size_t L, float 
  * or a host program whose own allocator owns the GPU's memory.
  *
  * Same result as tc_convolve, y[0..N+L-2] = x[0..N-1] * h[0..L-1] (device
- * pointers, FP32), but it calls no cudaMalloc, cudaFree or allocating
+ * pointers, FP32, the same role swap), but it calls no cudaMalloc, cudaFree or allocating
  * routine. Its working memory (input history with zero margins, shifted IR
  * copies, split-sum partials, counters) lives in one fixed 32 MiB device
  * array inside this library. Each GPU that loads the library holds that array
  * until the process exits.
- *   - Limit: the working set, about N + 13 L + 5e4 floats, must fit in
+ *   - Limit: the working set, about N + 13 L + 5e4 floats (N >= L after the
+ *     role swap), must fit in
  *     32 MiB = 8388608 floats: for example N up to 8.2 million samples with
  *     L = 4096. A call beyond it returns TC_EINVAL and names the size it
  *     would need.
@@ -255,7 +258,10 @@ tc_status tc_convolve_noalloc(const float *x, size_t N, const float *h, size_t L
  *     pointers, owned by the caller. y or acc may be NULL (not both): NULL acc
  *     uses a temporary from the stream-ordered allocator; NULL y skips the
  *     requantization.
- *   - L <= 2^19 keeps |acc| < 2^49, far inside int64.
+ *   - L <= 2^19 keeps |acc| < 2^49, far inside int64. When N < L the operands
+ *     swap roles (Sec. 3.2) unless TC_NO_ROLE_SWAP=1; the result is bit-identical.
+ *   - TC_Q15_INNER=imad in the environment selects the widening-multiply form
+ *     of the kernel instead of the default dp2a form (same result).
  * Runs on cuda_stream (NULL = default stream) and waits for it before
  * returning. Errors: TC_EINVAL (NULL pointers, N == 0, L == 0 or L > 2^19);
  * TC_ENOMEM; TC_ECUDA. */

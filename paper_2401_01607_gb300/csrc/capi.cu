@@ -1139,7 +1139,15 @@ tc_status tc_convolve(const float *x, size_t N, const float *h, size_t L, float 
         return fail(TC_EINVAL, "x, h or y is NULL");
     if (N == 0 || L == 0)
         return fail(TC_EINVAL, "N and L must be > 0");
-    const size_t chunk = std::min<size_t>(N, (size_t)1 << 20);
+    // Role swap (Sec. 3.2: x * h = h * x). The gather computes every output
+    // over all L taps, (N + L - 1) L multiply-adds, so the shorter operand
+    // takes the IR role: a short sound through a long IR costs about N L.
+    if (N < L && !tc::no_role_swap()) {
+        std::swap(x, h);
+        std::swap(N, L);
+    }
+    // Pushes and flush pieces of up to 2^20 samples (the flush is L - 1 long).
+    const size_t chunk = std::min<size_t>(std::max<size_t>(N, L - 1), (size_t)1 << 20);
     tc_stream *s = nullptr;
     TC_TRY(open_any(KIND_GROUP, 1, 1, 1, 1, L, chunk, 1, TC_FP32, chunk, &s));
     tc_status st = TC_OK;

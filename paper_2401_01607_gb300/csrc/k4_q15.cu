@@ -19,6 +19,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <utility>
 
 #include "../../include/taches.h"
 #include "tc_internal.h"
@@ -195,6 +196,12 @@ extern "C" tc_status tc_convolve_q15(const int16_t *x, size_t N, const int16_t *
         return (tc::set_last_error("tc_convolve_q15: x, h or both outputs are NULL"), TC_EINVAL);
     if (N == 0 || L == 0 || L > ((size_t)1 << 19) || N > ((size_t)1 << 40))
         return (tc::set_last_error("tc_convolve_q15: N must be > 0 and L in [1, 2^19]"), TC_EINVAL);
+    // Role swap (Sec. 3.2): the kernel's work is (N + L - 1) L, so the shorter
+    // operand takes the IR role. Integer sums make the result bit-identical.
+    if (N < L && !tc::no_role_swap()) {
+        std::swap(x, h);
+        std::swap(N, L);
+    }
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const long long ny = (long long)N + (long long)L - 1;
     long long *a = reinterpret_cast<long long *>(acc);

@@ -1,6 +1,7 @@
 // k_prep.cu -- IR preparation for K1: four copies of each IR row, shifted by
 // e = 0..3 taps and zero-padded, so that every tap chunk that K1 stages
 // starts on a 16-byte boundary whatever the output alignment.
+#include <cstdlib>
 #include <atomic>
 
 #include "tc_internal.h"
@@ -53,5 +54,11 @@ cudaError_t ir_prep_launch(const float *src, long long src_pitch, long long n, i
 
 void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
 uint64_t launches() { return g_launches.load(std::memory_order_relaxed); }
+
+bool no_role_swap()
+{
+    const char *e = std::getenv("TC_NO_ROLE_SWAP");
+    return e && e[0] == '1';
+}
 
 }  // namespace tc

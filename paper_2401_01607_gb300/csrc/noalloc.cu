@@ -23,6 +23,7 @@
 #include <cstdio>
 #include <mutex>
 #include <string>
+#include <utility>
 
 #include "../../include/taches.h"
 #include "tc_internal.h"
@@ -94,6 +95,11 @@ extern "C" tc_status tc_convolve_noalloc(const float *x, size_t N, const float *
         return na_fail(TC_EINVAL, "tc_convolve_noalloc: x, h or y is NULL");
     if (N == 0 || L == 0)
         return na_fail(TC_EINVAL, "tc_convolve_noalloc: N and L must be > 0");
+    // Role swap as in tc_convolve (Sec. 3.2): the shorter operand is the IR.
+    if (N < L && !tc::no_role_swap()) {
+        std::swap(x, h);
+        std::swap(N, L);
+    }
 
     // Scratch layout (floats, 64-float aligned segments):
     //   [counters + error word][IR: 4 shifted copies of Lpad][history row][split-sum partials]

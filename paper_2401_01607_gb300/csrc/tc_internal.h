@@ -197,6 +197,9 @@ void set_last_error(const char *msg);
 
 // Counts kernel launches issued by this library.
 void count_launch(int n = 1);
+// TC_NO_ROLE_SWAP=1 in the environment keeps the one-shot convolutions in the
+// caller's roles (for comparison timings); read at each call.
+bool no_role_swap();
 uint64_t launches();
 
 }  // namespace tc

@@ -146,6 +146,21 @@ def test_convolve_one_shot():
     assert rel_l2(y.cpu().numpy(), ref) <= TOL["fp32"]
 
 
+@pytest.mark.parametrize("swap", ["1", "0"])
+def test_convolve_role_swap(monkeypatch, swap):
+    """A short sound through a long IR (N < L): tc_convolve swaps the roles (Sec. 3.2, x * h = h * x) unless
+    TC_NO_ROLE_SWAP=1; both orientations match the oracle."""
+    torch = pytest.importorskip("torch")
+    monkeypatch.setenv("TC_NO_ROLE_SWAP", "0" if swap == "1" else "1")
+    N, L = 1_500, 40_000
+    x = synth.audio(N, 11)
+    h = synth.decayed_ir(L, 0.2 * L, 12)
+    y = torch.full((N + L - 1,), float("nan"), device="cuda")
+    capi.tc_convolve(torch.from_numpy(x).cuda(), N, torch.from_numpy(h).cuda(), L, y)
+    ref = oracle.buffer(x, h[None], None, 4096)
+    assert rel_l2(y.cpu().numpy(), ref) <= TOL["fp32"]
+
+
 def test_mimo_fp32():
     nin, nout, N, L, B = 3, 2, 3000, 1000, 128
     X = synth.audio_block(nin, N, 50)

@@ -81,6 +81,19 @@ def test_halves_and_saturation(inner):
     assert y.max() == 32767 and y.min() == -32768
 
 
+def test_role_swap_is_bit_identical(monkeypatch):
+    """N < L: the roles are swapped (Sec. 3.2) unless TC_NO_ROLE_SWAP=1; integer sums make both
+    orientations bit-identical to the oracle."""
+    xq = synth.q15_full_range(700, 31)
+    hq = synth.q15_full_range(9_000, 32)
+    racc, ry = oracle.q15(xq, hq)
+    for flag in ("0", "1"):
+        monkeypatch.setenv("TC_NO_ROLE_SWAP", flag)
+        acc, y = _gpu(xq, hq)
+        np.testing.assert_array_equal(acc, racc)
+        np.testing.assert_array_equal(y, ry)
+
+
 def test_acc_only_and_y_only():
     xq = synth.q15_full_range(2500, 1)
     hq = synth.q15_full_range(700, 2)

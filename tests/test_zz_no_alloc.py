@@ -52,3 +52,27 @@ def test_noalloc_rejects_sizes_beyond_its_array():
         capi.tc_convolve_noalloc(x, N, x, L, x)
     assert e.value.code == "TC_EINVAL"
     assert "MiB" in str(e.value)
+
+
+def test_noalloc_role_swap_fits_a_long_ir():
+    """N = 3000 through L = 2 million taps needs about 26 million floats of working set in the caller's
+    roles, beyond the 32 MiB array; with the roles swapped (Sec. 3.2) it needs about 2.05 million. The
+    result matches tc_convolve run in the caller's roles (TC_NO_ROLE_SWAP=1)."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import os
+    N, L = 3_000, 2_000_000
+    x = torch.from_numpy(synth.audio(N, 5)).cuda()
+    h = torch.from_numpy(synth.decayed_ir(L, 0.2 * L, 6)).cuda()
+    y_na = torch.full((N + L - 1,), float("nan"), device="cuda")
+    y_ref = torch.empty(N + L - 1, device="cuda")
+    capi.tc_convolve_noalloc(x, N, h, L, y_na)
+    os.environ["TC_NO_ROLE_SWAP"] = "1"
+    try:
+        capi.tc_convolve(x, N, h, L, y_ref)
+    finally:
+        del os.environ["TC_NO_ROLE_SWAP"]
+    a = y_na.cpu().numpy()
+    assert np.all(np.isfinite(a))
+    assert rel_l2(a, y_ref.cpu().numpy()) <= TOL["fp32"]

@@ -289,9 +289,16 @@ tc_status tc_convolve_q15(const int16_t *x, size_t N, const int16_t *h, size_t L
  *     slots, version table) fits the memory budget. Otherwise tc_server_add
  *     returns TC_ENOMEM and the caller retries once streams have left.
  *     tc_server_remove releases the state.
+ *   - A group (tc_server_add_group) is C channels that share one IR: a
+ *     multichannel source through one room response (Sec. 5.1, Sec. 6). Its
+ *     blocks are [C][n] and run, after the step's gather launch, as one push
+ *     of a shared-IR group stream: K2 on the tensor cores in TC_BF16 and
+ *     TC_BF16_SPLIT, the gather in TC_FP32.
  * Each stream gives the same output as a tc_stream opened with the same L and
- * block and fed the same calls. The output does not depend on which blocks of
- * other streams share its steps, up to FP32 rounding.
+ * block and fed the same calls (a group: as tc_open_group with shared_ir = 1
+ * and the same precision). The output does not depend on which blocks of
+ * other streams share its steps, up to FP32 rounding (BF16 modes: up to the
+ * rounding of their products).
  * Thread safety: submit, poll and get_stats may be called from any thread at
  * any time. The other calls serialise on the server.
  */
@@ -305,8 +312,11 @@ typedef struct tc_server_stats {
     uint64_t blocks;     /* blocks completed (flush tails included) */
     uint64_t rejected;   /* tc_server_add calls refused for memory */
     double busy_s;       /* wall time spent inside steps (seconds) */
-    double tap_macs;     /* useful work done: input samples x L, summed over finished blocks
-                            (flush tails excluded) */
+    double tap_macs;     /* useful work done: input samples x L (x channels for a group), summed over
+                            finished blocks (flush tails excluded) */
+    uint64_t tensor_launches;  /* group pushes that ran on the tensor cores (BF16 modes) */
+    uint64_t fp32_fallbacks;   /* BF16-mode group pushes that ran on the FP32 gather because their
+                                  window straddled an IR switch */
 } tc_server_stats;
 
 /* Opens a server on the current CUDA device. mem_budget_bytes bounds the
@@ -325,6 +335,16 @@ tc_status tc_server_close(tc_server *srv);
 enum { TC_SERVER_DISCARD_OUTPUT = 1 };
 tc_status tc_server_add(tc_server *srv, size_t L, size_t block, const float *h, size_t n, int flags,
                         uint64_t *id);
+/* Admits a group of `channels` rows sharing one IR (1 <= channels <= 4096,
+ * channels x block <= max_step_samples), precision TC_FP32, TC_BF16 or
+ * TC_BF16_SPLIT. Every call that takes or returns samples of a group uses
+ * [channels][n] row-major buffers: submit (x holds channels x n floats),
+ * attach_source (x is [channels][n]), poll (*n_out counts floats, channels x
+ * the block's samples) and flush (channels x (L - 1) floats). IR switches
+ * (tc_server_set_ir_at) apply to every channel; up to four versions are live.
+ * Errors as tc_server_add; TC_EINVAL for a bad channel count or precision. */
+tc_status tc_server_add_group(tc_server *srv, size_t channels, size_t L, size_t block, const float *h, size_t n,
+                              int precision, int flags, uint64_t *id);
 /* New IR version from input sample `sample` on (Eq. 4 with per-sample
  * versions, Sec. 6). sample must not be below the samples already submitted.
  * Up to three versions are live per stream; TC_ENOMEM when all three are
@@ -362,12 +382,14 @@ tc_status tc_server_start(tc_server *srv);
 tc_status tc_server_stop(tc_server *srv);
 /* Takes the stream's oldest finished output block, if any. *n_out = 0 if
  * none is ready yet. The block has as many samples as its input block and
- * goes to y[0..n) (cap >= n, else TC_EINVAL). t_submit and t_done (may be
+ * goes to y[0..n) (cap >= n, else TC_EINVAL; a group's block is [channels][n]
+ * and *n_out = channels x n). t_submit and t_done (may be
  * NULL) get the submit and completion times on tc_server_clock(). */
 tc_status tc_server_poll(tc_server *srv, uint64_t id, float *y, size_t cap, size_t *n_out, double *t_submit,
                          double *t_done);
 /* Ends the stream's input and returns the last L - 1 output samples (the
- * temporal overflow of Sec. 4.1) in y[0..L-1) (cap >= L - 1). Runs steps on
+ * temporal overflow of Sec. 4.1) in y[0..L-1) (cap >= L - 1; a group:
+ * [channels][L - 1], cap >= channels x (L - 1)). Runs steps on
  * the calling thread until they are done; stop the worker first
  * (TC_ESTATE otherwise). Poll the stream's finished blocks before or after. */
 tc_status tc_server_flush(tc_server *srv, uint64_t id, float *y, size_t cap, size_t *n_out);

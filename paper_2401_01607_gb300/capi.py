@@ -42,7 +42,8 @@ class TcInfo(ctypes.Structure):
 class TcServerStats(ctypes.Structure):
     _fields_ = [("streams", ctypes.c_size_t), ("mem_used", ctypes.c_size_t), ("mem_budget", ctypes.c_size_t),
                 ("steps", ctypes.c_uint64), ("blocks", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
-                ("busy_s", ctypes.c_double), ("tap_macs", ctypes.c_double)]
+                ("busy_s", ctypes.c_double), ("tap_macs", ctypes.c_double),
+                ("tensor_launches", ctypes.c_uint64), ("fp32_fallbacks", ctypes.c_uint64)]
 
 
 class TcServerStepRec(ctypes.Structure):
@@ -85,6 +86,7 @@ _SIGS = {
     "tc_server_open": [_sz, _sz, ctypes.POINTER(_vp)],
     "tc_server_close": [_vp],
     "tc_server_add": [_vp, _sz, _sz, _vp, _sz, _int, ctypes.POINTER(_u64)],
+    "tc_server_add_group": [_vp, _sz, _sz, _sz, _vp, _sz, _int, _int, ctypes.POINTER(_u64)],
     "tc_server_set_ir_at": [_vp, _u64, _vp, _sz, _u64],
     "tc_server_submit": [_vp, _u64, _vp, _sz],
     "tc_server_submit_many": [_vp, _sz, _vp, _vp, _vp, _vp],
@@ -354,14 +356,25 @@ def tc_server_add(srv: int, L: int, block: int, h, flags: int = 0) -> int:
     return int(sid.value)
 
 
+def tc_server_add_group(srv: int, channels: int, L: int, block: int, h, precision: int = 0, flags: int = 0) -> int:
+    """A group of `channels` rows sharing IR h; its blocks are [channels][n]."""
+    h, hp = _host_f32(h)
+    sid = _u64()
+    _call("tc_server_add_group", srv, int(channels), int(L), int(block), hp, h.size, int(precision), int(flags),
+          ctypes.byref(sid))
+    return int(sid.value)
+
+
 def tc_server_set_ir_at(srv: int, sid: int, h, sample: int) -> None:
     h, hp = _host_f32(h)
     _call("tc_server_set_ir_at", srv, int(sid), hp, h.size, int(sample))
 
 
 def tc_server_submit(srv: int, sid: int, x) -> None:
+    """x: one block, 1-D (a stream) or [channels][n] (a group)."""
     x, xp = _host_f32(x)
-    _call("tc_server_submit", srv, int(sid), xp, x.size)
+    n = x.shape[-1] if x.ndim == 2 else x.size
+    _call("tc_server_submit", srv, int(sid), xp, n)
 
 
 def tc_server_submit_many(srv: int, ids, x_addrs, ns, t_ready=None) -> None:
@@ -389,7 +402,8 @@ def tc_server_attach_source(srv: int, sid: int, x, t0: float, fs: float = 48_000
         return
     if not isinstance(x, np.ndarray) or x.dtype != np.float32 or not x.flags.c_contiguous:
         raise TypeError("a live source must be a C-contiguous float32 numpy array (it is read in place)")
-    _call("tc_server_attach_source", srv, int(sid), x.ctypes.data_as(_vp), x.size, float(t0), float(fs))
+    n = x.shape[-1] if x.ndim == 2 else x.size  # a group's source is [channels][n]
+    _call("tc_server_attach_source", srv, int(sid), x.ctypes.data_as(_vp), n, float(t0), float(fs))
 
 
 def tc_server_stream_state(srv: int, sid: int) -> int:

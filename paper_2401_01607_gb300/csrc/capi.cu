@@ -690,9 +690,11 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
     p.range += p.range & 1;  // runs are whole pipeline stages of 2 K blocks
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+    // Up to 64 parts (k2_reduce's tree), each at least 16 K blocks long: a
+    // small launch (one serving step of one group) spreads over the GPU.
     long long nsplit = 1;
     double best = 0.0;
-    for (long long ns = 1; ns <= 8 && ns <= nkb; ++ns) {
+    for (long long ns = 1; ns <= 64 && ns <= nkb && (ns == 1 || nkb / ns >= 16); ++ns) {
         const long long units = tiles * ns;
         const double eff = (double)units / (double)(((units + sms - 1) / sms) * sms);
         if (eff > best + 1e-9) {
@@ -938,6 +940,48 @@ tc_status flush_checks(tc_stream *s)
 }
 
 }  // namespace
+
+namespace tc {
+
+// A shared-IR group stream driven by the server's worker: pushes of up to
+// max_push samples per channel, any length (block 1: a push never ends the
+// stream), device pointers, on the server's CUDA stream `cs`.
+tc_status group_open(size_t channels, size_t L, size_t max_push, int precision, void *cs, tc_stream **out,
+                     size_t *bytes)
+{
+    TC_TRY(open_any(KIND_GROUP, channels, channels, 1, 1, L, 1, 1, (tc_precision)precision, max_push, out));
+    tc_stream *s = *out;
+    tc_status st = tc_set_cuda_stream(s, cs);
+    if (st != TC_OK) {
+        tc_close(s);
+        *out = nullptr;
+        return st;
+    }
+    // Device footprint: what open allocated, plus what the first tensor-core
+    // launches allocate (Toeplitz tiles of every IR slot for two alignment
+    // shifts, K-part partials of the largest push).
+    size_t b = s->rows * (size_t)s->cap * sizeof(float) + (size_t)s->nslots * 4 * (size_t)s->Lpad * sizeof(float) +
+               s->L * sizeof(float) + s->items * s->max_push * sizeof(float) + s->partial_floats * sizeof(float) +
+               s->counter_n * sizeof(unsigned) + sizeof(DevTable) + sizeof(int);
+    if (s->prec != TC_FP32) {
+        b += s->rows * (size_t)s->cap * 4;  // bf16 hi and lo histories
+        const size_t nkb = (s->L + 256 + 8 + 31) / 32 + 1;
+        b += (size_t)s->nslots * 2 * 2 * nkb * 256 * 32 * 2;
+        const size_t tiles = ((s->rows + 127) / 128 + 1) * ((s->max_push + 255) / 256 + 1);
+        b += tiles * 64 * 128 * 256 * sizeof(float);
+    }
+    *bytes = b;
+    return TC_OK;
+}
+
+tc_status group_push(tc_stream *s, const float *x, size_t n, float *y)
+{
+    return push_impl(s, x, n, y, true, s->max_push);
+}
+
+int *group_err(tc_stream *s) { return s->d_err; }
+
+}  // namespace tc
 
 extern "C" {
 

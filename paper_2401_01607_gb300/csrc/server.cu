@@ -89,6 +89,14 @@ struct SStream {
     bool ended = false;   // a short block was submitted: input is over
     bool flushed = false;
     bool discard = false;  // keep no output blocks (latency is still recorded)
+    // Group (tc_server_add_group): `channels` rows sharing one IR. Blocks hold
+    // [channels][n] samples; the group stream of the C ABI (K2 on the tensor
+    // cores in the BF16 modes, K1 in FP32) runs them after the step's K1 work
+    // list. hist, ir and d_vt stay unused.
+    long long channels = 1;
+    tc_stream *grp = nullptr;
+    std::mutex gmu;           // the group stream: worker pushes vs IR uploads
+    long long tail_fill = 0;  // flush tail samples delivered so far (per row)
     float *hist = nullptr;       // [cap]
     float *ir = nullptr;         // [nslots][4][Lpad]
     DevTable *d_vt = nullptr;
@@ -146,7 +154,7 @@ struct tc_server {
     struct Item {
         SStream *s;
         std::vector<Block> blocks;
-        long long off, n;  // packed input / output offset and samples
+        long long off, n;  // packed input / output offset (floats); samples per row
     };
     struct StepBuf {
         char *pin_stage = nullptr;
@@ -218,6 +226,7 @@ struct tc_server {
     uint64_t steps = 0, blocks = 0, rejected = 0;
     double busy_s = 0.0;
     double tap_macs = 0.0;
+    uint64_t tensor_launches = 0, fp32_fallbacks = 0;  // group pushes (state mutex)
 };
 
 namespace {
@@ -274,6 +283,14 @@ __global__ void ingest_kernel(const float *__restrict__ in, const long long *__r
         d[j] = in[src + j];
 }
 
+// Carries a group stream's device error word (a bounded wait that gave up)
+// into the step's error word.
+__global__ void err_merge_kernel(int *dst, const int *src)
+{
+    if (threadIdx.x == 0 && *src != 0)
+        *dst = *src;
+}
+
 // History row of a stream: `keep` samples behind the launch position (L taps
 // plus one tap chunk and the alignment shift), room for kMerge blocks and a
 // tile's overrun, and a stagger window of keep / 2 samples: each stream
@@ -291,6 +308,10 @@ size_t stream_bytes(long long L, long long block, int nslots, long long *keep, l
 // step that used it (no host synchronisation).
 void free_stream(tc_server *srv, SStream *s)
 {
+    if (s->grp) {
+        tc_close(s->grp);  // waits for the steps that used it
+        s->grp = nullptr;
+    }
     if (s->hist)
         cudaFreeAsync(s->hist, srv->cs);
     if (s->ir)
@@ -357,7 +378,7 @@ tc_status set_ir(tc_server *srv, uint64_t id, const float *h, size_t n, long lon
 {
     SStream *s = nullptr;
     int slot = -1;
-    bool replace = false;
+    bool replace = false, group = false;
     {
         std::lock_guard<std::mutex> lk(srv->mu_state);
         auto it = srv->streams.find(id);
@@ -373,8 +394,19 @@ tc_status set_ir(tc_server *srv, uint64_t id, const float *h, size_t n, long lon
         }
         if (sample < s->pos + queued)
             return sfail(TC_EINVAL, "tc_server_set_ir_at: the switch sample was already submitted");
-        if (!s->vt.empty() && sample < s->vt.back().start)
+        if (s->grp)
+            group = true;  // the group stream keeps its own version table
+        else if (!s->vt.empty() && sample < s->vt.back().start)
             return sfail(TC_EINVAL, "tc_server_set_ir_at: switch before the latest version");
+    }
+    if (group) {
+        // Uploads on the step stream, ordered after the pushes already made;
+        // a push of the switch sample waits for this (group mutex).
+        std::lock_guard<std::mutex> g(s->gmu);
+        return tc_set_ir_at(s->grp, h, n, (uint64_t)sample);
+    }
+    {
+        std::lock_guard<std::mutex> lk(srv->mu_state);
         retire(s);
         // Replacing the newest version in place is only safe while no block
         // that uses it has been submitted.
@@ -493,8 +525,17 @@ double release_sources(tc_server *srv, double now)
         if (!s->src || s->src_next * s->block >= s->src_n)
             continue;
         Block b;
-        b.src = s->src + s->src_next * s->block;
         b.n = std::min(s->block, s->src_n - s->src_next * s->block);
+        if (s->channels == 1) {
+            b.src = s->src + s->src_next * s->block;
+        } else {
+            // A group's source is [channels][src_n]: gather the block's rows.
+            b.src = nullptr;
+            b.own.resize((size_t)(s->channels * b.n));
+            for (long long c = 0; c < s->channels; ++c)
+                std::memcpy(b.own.data() + c * b.n, s->src + c * s->src_n + s->src_next * s->block,
+                            (size_t)b.n * sizeof(float));
+        }
         b.t_submit = s->src_ready(s->src_next);
         b.tail = false;
         s->pending.push_back(std::move(b));
@@ -529,13 +570,14 @@ size_t collect(tc_server *srv, tc_server::StepBuf &b)
         tc_server::Item it{s, {}, (long long)b.total, 0};
         while (!s->pending.empty() && (int)it.blocks.size() < kMerge) {
             Block &blk = s->pending.front();
-            if (b.total + (size_t)blk.n > srv->max_step_samples) {
+            const size_t fl = (size_t)(blk.n * s->channels);  // packed floats
+            if (b.total + fl > srv->max_step_samples) {
                 if (!capped)
                     srv->rr = s->id;
                 capped = true;
                 break;  // stays for the next step
             }
-            b.total += (size_t)blk.n;
+            b.total += fl;
             it.n += blk.n;
             it.blocks.push_back(std::move(blk));
             s->pending.pop_front();
@@ -614,6 +656,10 @@ tc_status graph_launch(tc_server *srv, tc_server::StepBuf &b, int variant, size_
 // (no wait). Caller holds mu_state. Advances each stream's launch position.
 tc_status pack_launch(tc_server *srv, tc_server::StepBuf &b)
 {
+    // Plain streams go into the K1 work list; groups run after it.
+    std::vector<size_t> plain, group;
+    for (size_t i = 0; i < b.items.size(); ++i)
+        (b.items[i].s->grp ? group : plain).push_back(i);
     // One chunk variant for the whole list: the largest chunk that still
     // gives the GPU about four waves of CTAs with < 10 % padded taps, else the
     // smallest (short IRs, small batches: latency first).
@@ -621,7 +667,8 @@ tc_status pack_launch(tc_server *srv, tc_server::StepBuf &b)
     for (int v : {tc::K1_P11, tc::K1_P4}) {
         const long long kcv = tc::k1_chunk_taps(v);
         long long ctas = 0, taps = 0, padded = 0;
-        for (auto &w : b.items) {
+        for (size_t i : plain) {
+            const tc_server::Item &w = b.items[i];
             const long long ntile = (w.n + tc::K1_MO - 1) / tc::K1_MO;
             const long long nch = (w.s->L + 3 + kcv - 1) / kcv;
             ctas += ntile * nch;
@@ -634,11 +681,12 @@ tc_status pack_launch(tc_server *srv, tc_server::StepBuf &b)
         }
     }
     b.tune_key = -1;
-    if (srv->autotune) {
+    if (srv->autotune && !plain.empty()) {
         // Step class: magnitudes of the step's tap-MACs and of its longest IR.
         double work = 0.0;
         long long maxL = 1;
-        for (auto &w : b.items) {
+        for (size_t i : plain) {
+            const tc_server::Item &w = b.items[i];
             work += (double)w.n * (double)w.s->L;
             maxL = std::max(maxL, w.s->L);
         }
@@ -662,14 +710,15 @@ tc_status pack_launch(tc_server *srv, tc_server::StepBuf &b)
     }
     const long long kc = tc::k1_chunk_taps(variant);
     size_t scratch = 0, ctrs = 0;
-    for (auto &w : b.items) {
+    for (size_t i : plain) {
+        const tc_server::Item &w = b.items[i];
         const long long ntile = (w.n + tc::K1_MO - 1) / tc::K1_MO;
         scratch += (size_t)(ntile * ((w.s->L + 3 + kc - 1) / kc) * tc::K1_MO);
         ctrs += (size_t)ntile;
     }
-    S_TRY(grow(srv, b, b.items.size(), scratch, ctrs));
+    S_TRY(grow(srv, b, plain.size(), scratch, ctrs));
 
-    const StageLayout lay = stage_layout(b.items.size(), b.total);
+    const StageLayout lay = stage_layout(plain.size(), b.total);
     auto *st_items = reinterpret_cast<tc::K1Params *>(b.pin_stage + lay.items);
     auto *st_cta = reinterpret_cast<long long *>(b.pin_stage + lay.cta);
     auto *st_sc = reinterpret_cast<long long *>(b.pin_stage + lay.sc);
@@ -677,17 +726,22 @@ tc_status pack_launch(tc_server *srv, tc_server::StepBuf &b)
     auto *st_in = reinterpret_cast<float *>(b.pin_stage + lay.in);
     float *const d_y = srv->d_out + 4;
     int *const d_err = reinterpret_cast<int *>(srv->d_out);
-    size_t si = 0, ci = 0;
-    long long cta = 0;
-    for (size_t i = 0; i < b.items.size(); ++i) {
-        tc_server::Item &w = b.items[i];
-        SStream *s = w.s;
-        const long long n = w.n;
-        long long o = w.off;
+    // Packed input of every item: [rows][n] (rows = 1 for plain streams).
+    for (auto &w : b.items) {
+        const long long C = w.s->channels;
+        long long o = 0;
         for (auto &blk : w.blocks) {
-            std::memcpy(st_in + o, blk.data(), (size_t)blk.n * sizeof(float));
+            for (long long c = 0; c < C; ++c)
+                std::memcpy(st_in + w.off + c * w.n + o, blk.data() + c * blk.n, (size_t)blk.n * sizeof(float));
             o += blk.n;
         }
+    }
+    size_t si = 0, ci = 0;
+    long long cta = 0;
+    for (size_t j = 0; j < plain.size(); ++j) {
+        tc_server::Item &w = b.items[plain[j]];
+        SStream *s = w.s;
+        const long long n = w.n;
         retire(s);
         long long c_shift = 0, c_len = 0;
         if (s->pos + n + tc::K1_MO + 8 + s->stagger > s->base + s->cap) {
@@ -702,7 +756,7 @@ tc_status pack_launch(tc_server *srv, tc_server::StepBuf &b)
             s->base = nb;
         }
         if (s->vt_dirty) {
-            DevTable &t = b.pin_tables[i];
+            DevTable &t = b.pin_tables[j];
             std::memset(&t, 0, sizeof t);
             t.nver = (int)s->vt.size();
             for (size_t v = 0; v < s->vt.size(); ++v) {
@@ -712,12 +766,12 @@ tc_status pack_launch(tc_server *srv, tc_server::StepBuf &b)
             S_CU(cudaMemcpyAsync(s->d_vt, &t, sizeof t, cudaMemcpyHostToDevice, srv->cs));
             s->vt_dirty = false;
         }
-        st_sc[5 * i] = w.off;
-        st_sc[5 * i + 1] = n;
-        st_sc[5 * i + 2] = s->pos - s->base;
-        st_sc[5 * i + 3] = c_shift;
-        st_sc[5 * i + 4] = c_len;
-        st_dst[i] = s->hist;
+        st_sc[5 * j] = w.off;
+        st_sc[5 * j + 1] = n;
+        st_sc[5 * j + 2] = s->pos - s->base;
+        st_sc[5 * j + 3] = c_shift;
+        st_sc[5 * j + 4] = c_len;
+        st_dst[j] = s->hist;
 
         tc::K1Params p{};
         p.hist = s->hist;
@@ -749,13 +803,13 @@ tc_status pack_launch(tc_server *srv, tc_server::StepBuf &b)
         p.err = d_err;
         si += (size_t)p.ntile * p.nchunk * tc::K1_MO;
         ci += (size_t)p.ntile;
-        st_items[i] = p;
-        st_cta[i] = cta;
+        st_items[j] = p;
+        st_cta[j] = cta;
         cta += (long long)p.ntile * p.nchunk;
         s->pos += n;
     }
-    st_cta[b.items.size()] = cta;
-    const int ni = (int)b.items.size();
+    st_cta[plain.size()] = cta;
+    const int ni = (int)plain.size();
     char *const ds = srv->d_stage;
     b.t_launch = now_s();
     b.ctas = cta;
@@ -768,16 +822,38 @@ tc_status pack_launch(tc_server *srv, tc_server::StepBuf &b)
     const tc::K1Params *a_items = reinterpret_cast<const tc::K1Params *>(ds + lay.items);
     const long long *a_cta = reinterpret_cast<const long long *>(ds + lay.cta);
     const size_t out_bytes = (4 + b.total) * sizeof(float);
-    if (srv->use_graph) {
+    if (srv->use_graph && group.empty()) {
         S_TRY(graph_launch(srv, b, variant, lay.end, a_in, a_sc, a_dst, ni, a_items, a_cta, cta, out_bytes));
     } else {
         S_CU(cudaMemcpyAsync(ds, b.pin_stage, lay.end, cudaMemcpyHostToDevice, srv->cs));
-        ingest_kernel<<<(unsigned)ni, 256, 0, srv->cs>>>(a_in, a_sc, a_dst, ni);
-        tc::count_launch();
-        S_CU(cudaGetLastError());
-        S_CU(cudaEventRecord(b.k1_start, srv->cs));
-        S_CU(tc::k1_launch_list(a_items, a_cta, ni, cta, variant, srv->cs));
-        S_CU(cudaEventRecord(b.k1_stop, srv->cs));
+        if (ni > 0) {
+            ingest_kernel<<<(unsigned)ni, 256, 0, srv->cs>>>(a_in, a_sc, a_dst, ni);
+            tc::count_launch();
+            S_CU(cudaGetLastError());
+            S_CU(cudaEventRecord(b.k1_start, srv->cs));
+            S_CU(tc::k1_launch_list(a_items, a_cta, ni, cta, variant, srv->cs));
+            S_CU(cudaEventRecord(b.k1_stop, srv->cs));
+        }
+        // Groups: one push of the group stream each (history copy, bf16 split,
+        // K2 or K1, K-part reduce), reading the packed input on the device and
+        // writing the packed output; its error word joins the step's.
+        for (size_t i : group) {
+            tc_server::Item &w = b.items[i];
+            SStream *s = w.s;
+            std::lock_guard<std::mutex> g(s->gmu);
+            tc_info before{}, after{};
+            tc_get_info(s->grp, &before);
+            tc_status st = tc::group_push(s->grp, a_in + w.off, (size_t)w.n, d_y + w.off);
+            if (st != TC_OK)
+                return st;
+            tc_get_info(s->grp, &after);
+            srv->tensor_launches += after.tensor_launches - before.tensor_launches;
+            srv->fp32_fallbacks += after.fp32_fallbacks - before.fp32_fallbacks;
+            err_merge_kernel<<<1, 1, 0, srv->cs>>>(d_err, tc::group_err(s->grp));
+            tc::count_launch();
+            S_CU(cudaGetLastError());
+            s->pos += w.n;
+        }
         S_CU(cudaMemcpyAsync(b.pin_out, srv->d_out, out_bytes, cudaMemcpyDeviceToHost, srv->cs));
     }
     S_CU(cudaEventRecord(b.done, srv->cs));
@@ -815,23 +891,32 @@ tc_status complete(tc_server *srv, tc_server::StepBuf &b)
     size_t nblocks = 0;
     for (auto &w : b.items) {
         SStream *s = w.s;
-        const float *yo = b.pin_out + 4 + w.off;
+        const long long C = s->channels;
+        const float *yo = b.pin_out + 4 + w.off;  // [C][w.n]
+        long long boff = 0;
         for (auto &blk : w.blocks) {
             if (blk.tail) {
-                s->tail_out.insert(s->tail_out.end(), yo, yo + blk.n);
+                const long long tail = s->L - 1;  // tail_out is [C][tail]
+                if (s->tail_fill + blk.n <= tail && (long long)s->tail_out.size() == C * tail)
+                    for (long long c = 0; c < C; ++c)
+                        std::memcpy(s->tail_out.data() + c * tail + s->tail_fill, yo + c * w.n + boff,
+                                    (size_t)blk.n * sizeof(float));
+                s->tail_fill += blk.n;
             } else {
                 srv->lat.push_back(t_done - blk.t_submit);
                 srv->lat_block.push_back((uint32_t)s->block);
-                srv->tap_macs += (double)blk.n * (double)s->L;
+                srv->tap_macs += (double)blk.n * (double)s->L * (double)C;
                 if (!s->discard) {
                     OutBlock o;
-                    o.y.assign(yo, yo + blk.n);
+                    o.y.resize((size_t)(C * blk.n));
+                    for (long long c = 0; c < C; ++c)
+                        std::memcpy(o.y.data() + c * blk.n, yo + c * w.n + boff, (size_t)blk.n * sizeof(float));
                     o.t_submit = blk.t_submit;
                     o.t_done = t_done;
                     s->done.push_back(std::move(o));
                 }
             }
-            yo += blk.n;
+            boff += blk.n;
             ++nblocks;
         }
         s->pos_done += w.n;
@@ -1094,6 +1179,54 @@ tc_status tc_server_add(tc_server *srv, size_t L, size_t block, const float *h, 
     return TC_OK;
 }
 
+tc_status tc_server_add_group(tc_server *srv, size_t channels, size_t L, size_t block, const float *h, size_t n,
+                              int precision, int flags, uint64_t *id)
+{
+    if (!srv || !id || !h || channels == 0 || L == 0 || block == 0 || n == 0 || n > L)
+        return sfail(TC_EINVAL, "tc_server_add_group: bad arguments");
+    if (channels > 4096 || channels * block > srv->max_step_samples)
+        return sfail(TC_EINVAL, "tc_server_add_group: channels x block must fit one step (channels <= 4096)");
+    if (precision != TC_FP32 && precision != TC_BF16 && precision != TC_BF16_SPLIT)
+        return sfail(TC_EINVAL, "tc_server_add_group: unknown precision");
+    if (flags & ~TC_SERVER_DISCARD_OUTPUT)
+        return sfail(TC_EINVAL, "tc_server_add_group: unknown flag");
+    auto s = std::make_unique<SStream>();
+    s->L = (long long)L;
+    s->block = (long long)block;
+    s->channels = (long long)channels;
+    s->discard = (flags & TC_SERVER_DISCARD_OUTPUT) != 0;
+    std::lock_guard<std::mutex> la(srv->mu_admin);
+    S_CU(cudaSetDevice(srv->device));
+    size_t bytes = 0;
+    S_TRY(tc::group_open(channels, L, (size_t)kMerge * block, precision, srv->cs, &s->grp, &bytes));
+    s->bytes = bytes;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu_state);
+        if (srv->used + s->bytes > srv->budget) {
+            srv->rejected++;
+            tc_close(s->grp);
+            s->grp = nullptr;
+            return sfail(TC_ENOMEM, "tc_server_add_group: the group does not fit the device memory budget now");
+        }
+        srv->used += s->bytes;
+    }
+    tc_status st = tc_set_ir_at(s->grp, h, n, 0);
+    if (st != TC_OK) {
+        const std::string m = tc_last_error();
+        tc_close(s->grp);
+        s->grp = nullptr;
+        std::lock_guard<std::mutex> lk(srv->mu_state);
+        srv->used -= s->bytes;
+        return sfail(st, m);
+    }
+    std::lock_guard<std::mutex> lk(srv->mu_state);
+    std::lock_guard<std::mutex> lq(srv->mu_queue);
+    s->id = srv->next_id++;
+    *id = s->id;
+    srv->streams[s->id] = std::move(s);
+    return TC_OK;
+}
+
 tc_status tc_server_set_ir_at(tc_server *srv, uint64_t id, const float *h, size_t n, uint64_t sample)
 {
     if (!srv)
@@ -1139,7 +1272,7 @@ tc_status tc_server_submit_many(tc_server *srv, size_t count, const uint64_t *id
         if ((long long)ns[i] < s->block)
             s->ended = true;  // a short block is the last one
         Block b;
-        b.own.assign(xs[i], xs[i] + ns[i]);
+        b.own.assign(xs[i], xs[i] + ns[i] * (size_t)s->channels);  // [channels][n]
         b.src = nullptr;
         b.n = (long long)ns[i];
         b.t_submit = t_ready ? t_ready[i] : now;
@@ -1281,8 +1414,9 @@ tc_status tc_server_flush(tc_server *srv, uint64_t id, float *y, size_t cap, siz
     if (!s)
         return sfail(TC_EINVAL, "tc_server_flush: unknown stream");
     const long long tail = s->L - 1;
-    if ((long long)cap < tail)
-        return sfail(TC_EINVAL, "tc_server_flush: cap < L - 1");
+    const long long C = s->channels;
+    if ((long long)cap < C * tail)
+        return sfail(TC_EINVAL, "tc_server_flush: cap < channels x (L - 1)");
     if (s->flushed)
         return sfail(TC_ESTATE, "tc_server_flush: already flushed");
     if (s->src && s->src_next * s->block < s->src_n)
@@ -1293,11 +1427,12 @@ tc_status tc_server_flush(tc_server *srv, uint64_t id, float *y, size_t cap, siz
     // (other streams' pending blocks ride along).
     {
         std::lock_guard<std::mutex> lq(srv->mu_queue);
-        s->tail_out.clear();
+        s->tail_out.assign((size_t)(C * tail), 0.f);
+        s->tail_fill = 0;
         for (long long off = 0; off < tail; off += s->block) {
             Block b;
             b.n = std::min<long long>(s->block, tail - off);
-            b.own.assign((size_t)b.n, 0.f);
+            b.own.assign((size_t)(C * b.n), 0.f);
             b.src = nullptr;
             b.t_submit = now_s();
             b.tail = true;
@@ -1320,14 +1455,14 @@ tc_status tc_server_flush(tc_server *srv, uint64_t id, float *y, size_t cap, siz
             return sfail(TC_ESTATE, "tc_server_flush: internal: a step made no progress");
     }
     lk.lock();
-    if ((long long)s->tail_out.size() != tail)
+    if (s->tail_fill != tail)
         return sfail(TC_ESTATE, "tc_server_flush: internal: tail length");
     if (tail > 0)
-        std::memcpy(y, s->tail_out.data(), (size_t)tail * sizeof(float));
+        std::memcpy(y, s->tail_out.data(), (size_t)(C * tail) * sizeof(float));
     s->tail_out.clear();
     s->tail_out.shrink_to_fit();
     if (n_out)
-        *n_out = (size_t)tail;
+        *n_out = (size_t)(C * tail);
     return TC_OK;
 }
 
@@ -1335,7 +1470,7 @@ tc_status tc_server_remove(tc_server *srv, uint64_t id)
 {
     if (!srv)
         return sfail(TC_EINVAL, "tc_server_remove: server is NULL");
-    std::lock_guard<std::mutex> lk(srv->mu_state);
+    std::unique_lock<std::mutex> lk(srv->mu_state);
     std::unique_ptr<SStream> s;
     {
         std::lock_guard<std::mutex> lq(srv->mu_queue);
@@ -1348,8 +1483,13 @@ tc_status tc_server_remove(tc_server *srv, uint64_t id)
         srv->streams.erase(it);
     }
     cudaSetDevice(srv->device);
-    free_stream(srv, s.get());  // ordered after the steps on the step stream
     srv->used -= s->bytes;
+    if (!s->grp) {
+        free_stream(srv, s.get());  // stream-ordered frees after the steps that used it
+        return TC_OK;
+    }
+    lk.unlock();  // closing a group stream waits for the steps in flight
+    free_stream(srv, s.get());
     return TC_OK;
 }
 
@@ -1366,6 +1506,8 @@ tc_status tc_server_get_stats(tc_server *srv, tc_server_stats *st)
     st->rejected = srv->rejected;
     st->busy_s = srv->busy_s;
     st->tap_macs = srv->tap_macs;
+    st->tensor_launches = srv->tensor_launches;
+    st->fp32_fallbacks = srv->fp32_fallbacks;
     return TC_OK;
 }
 

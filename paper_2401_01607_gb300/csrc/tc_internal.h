@@ -6,6 +6,8 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include "taches.h"
+
 namespace tc {
 
 // ---------------------------------------------------------------------------
@@ -200,6 +202,14 @@ void count_launch(int n = 1);
 // TC_NO_ROLE_SWAP=1 in the environment keeps the one-shot convolutions in the
 // caller's roles (for comparison timings); read at each call.
 bool no_role_swap();
+
+// Server groups (C channels, one shared IR, any precision): a group stream
+// on the server's CUDA stream, its device footprint in bytes, device-pointer
+// pushes (x and y [C][n]) that only enqueue work, and its device error word.
+tc_status group_open(size_t channels, size_t L, size_t max_push, int precision, void *cs, tc_stream **out,
+                     size_t *bytes);
+tc_status group_push(tc_stream *s, const float *x, size_t n, float *y);
+int *group_err(tc_stream *s);
 uint64_t launches();
 
 }  // namespace tc

@@ -327,3 +327,142 @@ def test_graph_replay_and_autotune_modes(graph, autotune):
     mix = _run(streams, order_seed=2, options=opts)
     for i, s in enumerate(streams):
         assert rel_l2(mix[i], _oracle(*s)) <= TOL["fp32"], i
+
+
+# ---------------------------------------------------------------------------
+# Groups: C channels sharing one IR (tc_server_add_group), K2 in the BF16 modes
+# ---------------------------------------------------------------------------
+
+def _group_ref(X, H, vstart, block):
+    return np.stack([oracle.buffer(X[c], H, np.asarray(vstart, np.int64), block) for c in range(X.shape[0])])
+
+
+def _poll_group(srv, gid, C, block, outs):
+    y = np.empty(C * block, np.float32)
+    while True:
+        n, _, _ = capi.tc_server_poll(srv, gid, y)
+        if n == 0:
+            return
+        outs.append(y[:n].reshape(C, n // C).copy())
+
+
+@pytest.mark.parametrize("prec", ["bf16split", "bf16", "fp32"])
+def test_group_in_a_mix_matches_oracle(prec):
+    """A 200-channel group (two 128-channel tiles, the second ragged) with an IR switch inside a block,
+    served in changing mixes with two plain streams; every channel against the oracle."""
+    code = {"fp32": capi.TC_FP32, "bf16": capi.TC_BF16, "bf16split": capi.TC_BF16_SPLIT}[prec]
+    C, N, L, B = 200, 5_000, 3_000, 128
+    X = synth.audio_block(C, N, 600)
+    H = np.stack([synth.decayed_ir(L, 0.2 * L, 700 + v) for v in range(2)])
+    vstart = [0, 2_600]
+    plain = _small_trace(k=2, seed=9)
+    srv = capi.tc_server_open(8 << 30, 1 << 20)
+    try:
+        gid = capi.tc_server_add_group(srv, C, L, B, H[0], code)
+        pids = [capi.tc_server_add(srv, t.L, t.block, Hp[0]) for (t, x, Hp, vs) in plain]
+        nblk_g = -(-N // B)
+        sent_g, sent_p = 0, [0, 0]
+        outs_g, outs_p = [], [[], []]
+        rng = np.random.default_rng(3)
+        while sent_g < nblk_g or any(sent_p[i] < -(-plain[i][0].n // plain[i][0].block) for i in range(2)):
+            for _ in range(int(rng.integers(0, 3))):
+                if sent_g < nblk_g:
+                    lo, hi = sent_g * B, min(N, (sent_g + 1) * B)
+                    if lo <= vstart[1] < hi:
+                        capi.tc_server_set_ir_at(srv, gid, H[1], vstart[1])
+                    capi.tc_server_submit(srv, gid, np.ascontiguousarray(X[:, lo:hi]))
+                    sent_g += 1
+            for i, (t, x, Hp, vs) in enumerate(plain):
+                if sent_p[i] * t.block < t.n and rng.uniform() < 0.7:
+                    lo, hi = sent_p[i] * t.block, min(t.n, (sent_p[i] + 1) * t.block)
+                    if len(vs) > 1 and lo <= vs[1] < hi:
+                        capi.tc_server_set_ir_at(srv, pids[i], Hp[1], vs[1])
+                    capi.tc_server_submit(srv, pids[i], x[lo:hi])
+                    sent_p[i] += 1
+            if rng.uniform() < 0.6:
+                capi.tc_server_step(srv)
+            _poll_group(srv, gid, C, B, outs_g)
+            for i, (t, *_r) in enumerate(plain):
+                y = np.empty(t.block, np.float32)
+                while True:
+                    n, _, _ = capi.tc_server_poll(srv, pids[i], y)
+                    if n == 0:
+                        break
+                    outs_p[i].append(y[:n].copy())
+        while capi.tc_server_step(srv):
+            pass
+        _poll_group(srv, gid, C, B, outs_g)
+        for i, (t, *_r) in enumerate(plain):
+            y = np.empty(t.block, np.float32)
+            while True:
+                n, _, _ = capi.tc_server_poll(srv, pids[i], y)
+                if n == 0:
+                    break
+                outs_p[i].append(y[:n].copy())
+        tail = np.empty(C * (L - 1), np.float32)
+        assert capi.tc_server_flush(srv, gid, tail) == C * (L - 1)
+        yg = np.concatenate(outs_g + [tail.reshape(C, L - 1)], axis=1)
+        st = capi.tc_server_get_stats(srv)
+        for i, (t, x, Hp, vs) in enumerate(plain):
+            tl = np.empty(max(t.L - 1, 1), np.float32)
+            n = capi.tc_server_flush(srv, pids[i], tl)
+            yp = np.concatenate(outs_p[i] + [tl[:n]])
+            assert rel_l2(yp, _oracle(t, x, Hp, vs)) <= TOL["fp32"]
+            capi.tc_server_remove(srv, pids[i])
+        capi.tc_server_remove(srv, gid)
+        assert capi.tc_server_get_stats(srv).mem_used == 0
+    finally:
+        capi.tc_server_close(srv)
+    assert yg.shape == (C, N + L - 1)
+    ref = _group_ref(X, H, vstart, B)
+    err = rel_l2(yg, ref)
+    print(f"group {prec}: rel_l2={err:.3g}, tensor launches {st.tensor_launches}, fallbacks {st.fp32_fallbacks}")
+    assert err <= TOL[prec]
+    if prec != "fp32":
+        assert st.tensor_launches > 0 and st.fp32_fallbacks > 0  # the switch's windows ran on the gather
+    else:
+        assert st.tensor_launches == 0
+
+
+@pytest.mark.parametrize("prec", ["bf16split", "fp32"])
+def test_group_live_source_worker(prec):
+    """A 128-channel group read from a live [C][N] source by the worker thread, beside a plain stream."""
+    code = {"fp32": capi.TC_FP32, "bf16split": capi.TC_BF16_SPLIT}[prec]
+    C, N, L, B = 128, 12_000, 4_000, 256
+    X = np.ascontiguousarray(synth.audio_block(C, N, 800))
+    h = synth.decayed_ir(L, 0.2 * L, 801)
+    srv = capi.tc_server_open(8 << 30, 1 << 20)
+    try:
+        gid = capi.tc_server_add_group(srv, C, L, B, h, code)
+        capi.tc_server_start(srv)
+        capi.tc_server_attach_source(srv, gid, X, capi.tc_server_clock() + 0.01, 480_000.0)
+        outs = []
+        deadline = time.time() + 60
+        while capi.tc_server_stream_state(srv, gid) != 2 and time.time() < deadline:
+            _poll_group(srv, gid, C, B, outs)
+            time.sleep(0.002)
+        capi.tc_server_stop(srv)
+        _poll_group(srv, gid, C, B, outs)
+        tail = np.empty(C * (L - 1), np.float32)
+        capi.tc_server_flush(srv, gid, tail)
+        y = np.concatenate(outs + [tail.reshape(C, L - 1)], axis=1)
+        capi.tc_server_remove(srv, gid)
+    finally:
+        capi.tc_server_close(srv)
+    ref = _group_ref(X, h[None], [0], B)
+    assert y.shape == ref.shape
+    assert rel_l2(y, ref) <= TOL[prec]
+
+
+def test_group_errors():
+    srv = capi.tc_server_open(1 << 30, 1 << 16)
+    try:
+        h = np.ones(10, np.float32)
+        with pytest.raises(capi.TcError):
+            capi.tc_server_add_group(srv, 4, 100, 64, h, 7)  # unknown precision
+        with pytest.raises(capi.TcError):
+            capi.tc_server_add_group(srv, 1024, 100, 128, h, capi.TC_FP32)  # 1024 x 128 > one step
+        with pytest.raises(capi.TcError):
+            capi.tc_server_add_group(srv, 0, 100, 64, h, capi.TC_FP32)
+    finally:
+        capi.tc_server_close(srv)

@@ -954,6 +954,65 @@ def bench_capacity(torch, capi, H64: np.ndarray, pool: np.ndarray, paced_s: floa
     return out
 
 
+def bench_groups(capi, paced_s: float = 1.5, C: int = 128, L: int = 96_000, B: int = 256,
+                 precisions=("bf16split", "fp32"),
+                 ladder=(4, 8, 16, 24, 32, 40, 48, 64, 80, 96, 128)) -> dict:
+    """Serving of shared-IR groups (tc_server_add_group): G groups of C channels, each group one IR of
+    L taps (tau 0.2 L) and a live [C][n] 48 kHz source at a random phase, block B. For each precision
+    the group count G rises until the p99 block latency exceeds the deadline B/fs or more than 0.1 %
+    of blocks miss it; the largest passing G is the capacity."""
+    period = B / FS
+    warm = 0.3
+    n_src = int((warm + paced_s + 0.2) * FS)
+    src = np.ascontiguousarray(synth.audio_block(C, n_src, synth.x_seed(9, 0)))
+    irs = [synth.decayed_ir(L, 0.2 * L, synth.ir_seed(9, g)) for g in range(max(ladder))]
+    out = {"workload": f"groups of {C} channels sharing one IR L={L} (tau {0.2 * L:g}), block {B} at 48 kHz "
+                       f"(deadline {period * 1e3:.3f} ms); live sources, worker thread",
+           "tap_macs_per_group_realtime": C * FS * L}
+    for name in precisions:
+        code = {"fp32": capi.TC_FP32, "bf16": capi.TC_BF16, "bf16split": capi.TC_BF16_SPLIT}[name]
+        runs, best = {}, 0
+        for G in ladder:
+            srv = capi.tc_server_open(200 << 30, 1 << 22)
+            try:
+                ids = [capi.tc_server_add_group(srv, C, L, B, irs[g], code, capi.TC_SERVER_DISCARD_OUTPUT)
+                       for g in range(G)]
+                rng = np.random.default_rng(G)
+                t_start = capi.tc_server_clock() + 0.05
+                capi.tc_server_start(srv)
+                for sid in ids:
+                    capi.tc_server_attach_source(srv, sid, src, t_start + rng.uniform(0, period))
+                while capi.tc_server_clock() < t_start + warm:
+                    time.sleep(0.01)
+                capi.tc_server_latencies(srv)
+                st0 = capi.tc_server_get_stats(srv)
+                t_rec = capi.tc_server_clock()
+                t_end = t_start + n_src / FS + period + 3.0
+                while capi.tc_server_clock() < t_end:
+                    time.sleep(0.02)
+                    if all(capi.tc_server_stream_state(srv, sid) == 2 for sid in ids):
+                        break
+                capi.tc_server_stop(srv)
+                st1 = capi.tc_server_get_stats(srv)
+                lat, blk = capi.tc_server_latencies(srv)
+                wall = max(capi.tc_server_clock() - t_rec, 1e-9)
+                steps = st1.steps - st0.steps
+                r = dict(_lat_summary(lat, blk), groups=G, channels=G * C, steps=int(steps),
+                         served_tap_macs_per_s=(st1.tap_macs - st0.tap_macs) / wall,
+                         tensor_launches=int(st1.tensor_launches), fp32_fallbacks=int(st1.fp32_fallbacks))
+                r.pop("by_block", None)
+                r["pass"] = bool(r.get("blocks", 0) > 0 and r["p99_ms"] <= period * 1e3
+                                 and r["deadline_miss_frac"] <= 1e-3)
+            finally:
+                capi.tc_server_close(srv)
+            runs[str(G)] = r
+            if not r["pass"]:
+                break
+            best = G
+        out[name] = {"groups": best, "channels": best * C, "runs": runs}
+    return out
+
+
 def bench_trace(capi, pool: np.ndarray, seconds: float, budget_gb: float = 96.0) -> dict:
     """Serving trace replayed in real time: Poisson arrivals (200 streams/s),
     durations 0.5-30 s, IR lengths 256-480000, blocks {32..256}, 10 % with a
@@ -1015,6 +1074,7 @@ def bench_trace(capi, pool: np.ndarray, seconds: float, budget_gb: float = 96.0)
 def bench_serving(torch, capi, H64: np.ndarray, trace_s: float) -> dict:
     pool = synth.audio(32 * FS, 4242)
     out = {"capacity": bench_capacity(torch, capi, H64, pool)}
+    out["groups"] = bench_groups(capi)
     if trace_s > 0:
         out["trace"] = bench_trace(capi, pool, trace_s)
     return out
@@ -1104,6 +1164,8 @@ def main():
     ap.add_argument("--no-q15", action="store_true", help="skip the exact Q15 section")
     ap.add_argument("--only-q15", action="store_true", help="run only the exact Q15 section")
     ap.add_argument("--only-offline", action="store_true", help="run only the one-shot (role swap) section")
+    ap.add_argument("--only-groups", action="store_true", help="run only the shared-IR group serving section")
+    ap.add_argument("--groups-prec", default="bf16split,fp32", help="group serving section: precisions")
     ap.add_argument("--only-mimo", action="store_true", help="run only the MIMO section")
     ap.add_argument("--mimo-prec", default="bf16split,bf16,fp32", help="MIMO section: precisions")
     ap.add_argument("--mimo-L", type=int, default=192_000, help="MIMO section: IR length")
@@ -1150,6 +1212,10 @@ def main():
         if cpu_other:
             mimo["cpu_baseline"], mono["cpu_baseline"] = cpu_other["mimo"], cpu_other["mono"]
         print(json.dumps({"mimo": mimo, "mono": mono}), flush=True)
+        dist.close()
+        return
+    if args.only_groups:
+        print(json.dumps({"groups": bench_groups(capi, precisions=args.groups_prec.split(","))}), flush=True)
         dist.close()
         return
     if args.only_offline:

@@ -957,18 +957,20 @@ tc_status group_open(size_t channels, size_t L, size_t max_push, int precision, 
         *out = nullptr;
         return st;
     }
-    // Device footprint: what open allocated, plus what the first tensor-core
-    // launches allocate (Toeplitz tiles of every IR slot for two alignment
-    // shifts, K-part partials of the largest push).
+    // Device footprint: what open allocated, plus what the tensor-core
+    // launches allocate in steady use (Toeplitz tiles of two live IR versions
+    // at one alignment shift: pushes at multiples of 8 samples keep the
+    // shift; K-part partials of the largest push).
     size_t b = s->rows * (size_t)s->cap * sizeof(float) + (size_t)s->nslots * 4 * (size_t)s->Lpad * sizeof(float) +
                s->L * sizeof(float) + s->items * s->max_push * sizeof(float) + s->partial_floats * sizeof(float) +
                s->counter_n * sizeof(unsigned) + sizeof(DevTable) + sizeof(int);
     if (s->prec != TC_FP32) {
         b += s->rows * (size_t)s->cap * 4;  // bf16 hi and lo histories
         const size_t nkb = (s->L + 256 + 8 + 31) / 32 + 1;
-        b += (size_t)s->nslots * 2 * 2 * nkb * 256 * 32 * 2;
-        const size_t tiles = ((s->rows + 127) / 128 + 1) * ((s->max_push + 255) / 256 + 1);
-        b += tiles * 64 * 128 * 256 * sizeof(float);
+        b += (size_t)2 * 2 * nkb * 256 * 32 * 2;
+        const size_t tiles = ((s->rows + 255) / 256 * 2) * ((s->max_push + 255) / 256);
+        const size_t parts = std::max<size_t>(1, std::min<size_t>(64, 2 * 152 / std::max<size_t>(tiles, 1)));
+        b += tiles * parts * 128 * 256 * sizeof(float);
     }
     *bytes = b;
     return TC_OK;

@@ -207,9 +207,11 @@ tc_status tc_sync(tc_stream *s);
  * N < L the operands swap roles (Sec. 3.2: x * h = h * x; the gather's work is
  * (N + L - 1) L), unless TC_NO_ROLE_SWAP=1 is set in the environment. Runs on
  * cuda_stream (a cudaStream_t as void*; NULL = default stream) and waits
- * for it before returning. Allocates its working memory, which is freed
- * before return. Errors: TC_EINVAL (NULL or zero sizes); TC_ENOMEM; TC_ECUDA;
- * TC_ETIMEOUT. */
+ * for it before returning. Its working memory (the input with zero margins,
+ * about N + 6 L floats, and up to 256 MiB of split-sum partials) comes from
+ * the stream-ordered allocator on cuda_stream and goes back to it before
+ * return. Errors: TC_EINVAL (NULL or zero sizes, L > 2^30); TC_ENOMEM;
+ * TC_ECUDA; TC_ETIMEOUT. */
 tc_status tc_convolve(const float *x, size_t N, const float *h, size_t L, float *y, void *cuda_stream);
 
 /* ---------------------------------------------------------------------- */

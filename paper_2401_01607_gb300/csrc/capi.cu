@@ -1181,48 +1181,7 @@ tc_status tc_sync(tc_stream *s)
 
 tc_status tc_convolve(const float *x, size_t N, const float *h, size_t L, float *y, void *cuda_stream)
 {
-    if (!x || !h || !y)
-        return fail(TC_EINVAL, "x, h or y is NULL");
-    if (N == 0 || L == 0)
-        return fail(TC_EINVAL, "N and L must be > 0");
-    // Role swap (Sec. 3.2: x * h = h * x). The gather computes every output
-    // over all L taps, (N + L - 1) L multiply-adds, so the shorter operand
-    // takes the IR role: a short sound through a long IR costs about N L.
-    if (N < L && !tc::no_role_swap()) {
-        std::swap(x, h);
-        std::swap(N, L);
-    }
-    // Pushes and flush pieces of up to 2^20 samples (the flush is L - 1 long).
-    const size_t chunk = std::min<size_t>(std::max<size_t>(N, L - 1), (size_t)1 << 20);
-    tc_stream *s = nullptr;
-    TC_TRY(open_any(KIND_GROUP, 1, 1, 1, 1, L, chunk, 1, TC_FP32, chunk, &s));
-    tc_status st = TC_OK;
-    cudaStream_t cs = (cudaStream_t)cuda_stream;
-    cudaEvent_t ev = nullptr;
-    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
-        st = fail(TC_ECUDA, "event create failed");
-    // Start after the caller's stream has produced x and h.
-    if (st == TC_OK && (cudaEventRecord(ev, cs) != cudaSuccess || cudaStreamWaitEvent(s->cs, ev, 0) != cudaSuccess))
-        st = fail(TC_ECUDA, "stream ordering failed");
-    if (st == TC_OK)
-        st = set_ir_impl(s, h, L, 0, true, true);
-    for (size_t off = 0; st == TC_OK && off < N; off += chunk) {
-        const size_t n = std::min(chunk, N - off);
-        // A partial chunk may only come last; the stream block is `chunk`.
-        st = push_impl(s, x + off, n, y + off, true, chunk);
-    }
-    if (st == TC_OK && L > 1)
-        st = flush_to_device(s, y + N, (long long)(L - 1));
-    if (st == TC_OK)
-        st = tc_sync(s);
-    if (st == TC_OK && (cudaEventRecord(ev, s->cs) != cudaSuccess || cudaStreamWaitEvent(cs, ev, 0) != cudaSuccess))
-        st = fail(TC_ECUDA, "stream ordering failed");
-    std::string msg = g_err;
-    if (ev)
-        cudaEventDestroy(ev);
-    tc_close(s);
-    g_err = msg;
-    return st;
+    return tc::oneshot_alloc(x, N, h, L, y, cuda_stream);
 }
 
 const char *tc_last_error(void) { return g_err.c_str(); }

@@ -203,6 +203,10 @@ void count_launch(int n = 1);
 // caller's roles (for comparison timings); read at each call.
 bool no_role_swap();
 
+// tc_convolve: the one-shot convolution with scratch from the stream-ordered
+// allocator (defined beside tc_convolve_noalloc, which shares its code).
+tc_status oneshot_alloc(const float *x, size_t N, const float *h, size_t L, float *y, void *cuda_stream);
+
 // Server groups (C channels, one shared IR, any precision): a group stream
 // on the server's CUDA stream, its device footprint in bytes, device-pointer
 // pushes (x and y [C][n]) that only enqueue work, and its device error word.

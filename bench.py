@@ -130,8 +130,8 @@ class ClockSampler:
                     reasons.add(name)
         if not sm:
             return None
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "sm_min_mhz": float(min(sm)),
+                "reasons": sorted(reasons), "samples": len(sm)}
 
 
 # ---------------------------------------------------------------------------
@@ -972,6 +972,8 @@ def bench_groups(capi, paced_s: float = 1.5, C: int = 128, L: int = 96_000, B: i
     for name in precisions:
         code = {"fp32": capi.TC_FP32, "bf16": capi.TC_BF16, "bf16split": capi.TC_BF16_SPLIT}[name]
         runs, best = {}, 0
+        clocks = ClockSampler(0)
+        clocks.start()
         for G in ladder:
             srv = capi.tc_server_open(200 << 30, 1 << 22)
             try:
@@ -1009,7 +1011,7 @@ def bench_groups(capi, paced_s: float = 1.5, C: int = 128, L: int = 96_000, B: i
             if not r["pass"]:
                 break
             best = G
-        out[name] = {"groups": best, "channels": best * C, "runs": runs}
+        out[name] = {"groups": best, "channels": best * C, "runs": runs, "clocks": clocks.stop()}
     return out
 
 
@@ -1025,7 +1027,9 @@ def bench_trace(capi, pool: np.ndarray, seconds: float, budget_gb: float = 96.0)
     irs = {t.sid: [make(t.L, t.tau, sd) for sd in t.ir_seeds] for t in tr}
     srv = capi.tc_server_open(int(budget_gb * (1 << 30)), 1 << 22)
     waits, max_active, live = 0, 0, {}
+    clocks = ClockSampler(0)
     try:
+        clocks.start()
         capi.tc_server_start(srv)
         t_start = capi.tc_server_clock() + 0.02
         t_end = t_start + seconds
@@ -1058,15 +1062,36 @@ def bench_trace(capi, pool: np.ndarray, seconds: float, budget_gb: float = 96.0)
                     del live[sid]
             time.sleep(0.001)
         capi.tc_server_stop(srv)
+        diag_clk = clocks.stop()
         st = capi.tc_server_get_stats(srv)
         lat, blk = capi.tc_server_latencies(srv)
+        steplog = capi.tc_server_step_log(srv)
     finally:
         capi.tc_server_close(srv)
     arrived = sum(1 for t in tr if t.arrival_s < seconds)
+    # Diagnostics: step durations (the last steps of the log) and how the
+    # 32-sample blocks' misses spread over the run (completion order, 20 bins).
+    diag = {"clocks": diag_clk}
+    if len(steplog):
+        dur = (steplog["t_done"] - steplog["t_begin"]) * 1e3
+        gpu = (steplog["t_done"] - steplog["t_launch"]) * 1e3
+        host = (steplog["t_launch"] - steplog["t_begin"]) * 1e3
+        k = int(np.argmax(dur))
+        diag["step_ms"] = {"steps": int(dur.size), "p50": float(np.percentile(dur, 50)),
+                           "p99": float(np.percentile(dur, 99)), "max": float(dur.max()),
+                           "launch_to_done_p99": float(np.percentile(gpu, 99)),
+                           "longest": {"collect_pack_ms": float(host[k]), "launch_to_done_ms": float(gpu[k]),
+                                       "s_before_last_step": float(steplog["t_done"][-1] - steplog["t_begin"][k]),
+                                       "blocks": int(steplog["blocks"][k]), "samples": int(steplog["samples"][k])},
+                           "over_0.3ms": int(np.sum(dur > 0.3))}
+    m32 = blk == 32
+    if m32.any():
+        miss = lat[m32] > 32 / FS
+        diag["miss32_by_twentieth"] = [float(x.mean()) for x in np.array_split(miss, 20)]
     return dict(_lat_summary(lat, blk), seconds=seconds, streams_arrived=arrived, max_active=max_active,
                 served_tap_macs_per_s=st.tap_macs / seconds, steps=int(st.steps),
                 blocks_per_step=st.blocks / max(st.steps, 1), busy_frac=st.busy_s / seconds,
-                admission_waits=waits, mem_budget_gb=budget_gb,
+                admission_waits=waits, mem_budget_gb=budget_gb, diagnostics=diag,
                 precision="fp32 (every stream has its own IR: no shared-IR batch for the tensor cores)",
                 inputs="live 48 kHz sources cut from a seeded audio pool; IRs cut from a seeded Gaussian pool")
 
@@ -1160,6 +1185,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving section")
     ap.add_argument("--only-serving", action="store_true", help="run only the serving section")
     ap.add_argument("--trace-seconds", type=float, default=15.0)
+    ap.add_argument("--only-trace", action="store_true", help="run only the serving trace")
     ap.add_argument("--no-mimo", action="store_true", help="skip the MIMO section")
     ap.add_argument("--no-q15", action="store_true", help="skip the exact Q15 section")
     ap.add_argument("--only-q15", action="store_true", help="run only the exact Q15 section")
@@ -1212,6 +1238,11 @@ def main():
         if cpu_other:
             mimo["cpu_baseline"], mono["cpu_baseline"] = cpu_other["mimo"], cpu_other["mono"]
         print(json.dumps({"mimo": mimo, "mono": mono}), flush=True)
+        dist.close()
+        return
+    if args.only_trace:
+        pool = synth.audio(32 * FS, 4242)
+        print(json.dumps({"trace": bench_trace(capi, pool, args.trace_seconds)}), flush=True)
         dist.close()
         return
     if args.only_groups:

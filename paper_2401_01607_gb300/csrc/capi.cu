@@ -651,12 +651,16 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
     tc_stream::TSet &ts = s->tsets[(size_t)slot][(size_t)delta];
     if (!ts.ready) {
         if (!ts.thi || ts.nkb < nkb) {
-            cudaFree(ts.thi);
-            cudaFree(ts.tlo);
+            // Stream-ordered: no host or device-wide synchronisation while
+            // pushes of this or other streams are in flight.
+            if (ts.thi)
+                cudaFreeAsync(ts.thi, s->cs);
+            if (ts.tlo)
+                cudaFreeAsync(ts.tlo, s->cs);
             ts.thi = ts.tlo = nullptr;
             const size_t bytes = (size_t)nkb * TN * KB * 2;
-            TC_CU(cudaMalloc(&ts.thi, bytes));
-            TC_CU(cudaMalloc(&ts.tlo, bytes));
+            TC_CU(cudaMallocAsync(&ts.thi, bytes, s->cs));
+            TC_CU(cudaMallocAsync(&ts.tlo, bytes, s->cs));
             ts.nkb = nkb;
             TC_CU(tc::encode_bf16_2d(&ts.mt_hi, ts.thi, (unsigned long long)KB, (unsigned long long)nkb * TN,
                                      (unsigned long long)KB * 2, KB, TN));
@@ -720,10 +724,10 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
         // Partials per 128-channel tile (the pair kernel writes that layout too).
         const size_t need = (size_t)(2 * ((ntile_c1 + 1) / 2) * ntile_o * nsplit) * TM * TN;
         if (need > s->k2_partial_floats) {
-            TC_CU(cudaStreamSynchronize(s->cs));
-            cudaFree(s->k2_partial);
+            if (s->k2_partial)
+                cudaFreeAsync(s->k2_partial, s->cs);  // after the launches that used it
             s->k2_partial = nullptr;
-            TC_CU(cudaMalloc(&s->k2_partial, need * sizeof(float)));
+            TC_CU(cudaMallocAsync(&s->k2_partial, need * sizeof(float), s->cs));
             s->k2_partial_floats = need;
         }
         p.partial = s->k2_partial;
@@ -769,8 +773,8 @@ tc_status launch_k3(tc_stream *s, long long t0, long long nout, float *y, long l
     if (!ks.ready) {
         const unsigned long long rows = (unsigned long long)s->nin * nkbp * 128;
         if (!ks.bh) {
-            TC_CU(cudaMalloc(&ks.bh, rows * 32 * 2));
-            TC_CU(cudaMalloc(&ks.bl, rows * 32 * 2));
+            TC_CU(cudaMallocAsync(&ks.bh, rows * 32 * 2, s->cs));
+            TC_CU(cudaMallocAsync(&ks.bl, rows * 32 * 2, s->cs));
             TC_CU(tc::encode_bf16_2d(&ks.mb_hi, ks.bh, 32, rows, 64, 32, 128));
             TC_CU(tc::encode_bf16_2d(&ks.mb_lo, ks.bl, 32, rows, 64, 32, 128));
         }
@@ -815,11 +819,11 @@ tc_status launch_k3(tc_stream *s, long long t0, long long nout, float *y, long l
     p.err = s->d_err;
     const size_t need = (size_t)ntile * nsplit * 128 * 128;
     if (need > s->k3_partial_floats) {
-        TC_CU(cudaStreamSynchronize(s->cs));
-        cudaFree(s->k3_partial);
+        if (s->k3_partial)
+            cudaFreeAsync(s->k3_partial, s->cs);  // after the launches that used it
         s->k3_partial = nullptr;
         s->k3_partial_floats = 0;
-        TC_CU(cudaMalloc(&s->k3_partial, need * sizeof(float)));
+        TC_CU(cudaMallocAsync(&s->k3_partial, need * sizeof(float), s->cs));
         s->k3_partial_floats = need;
     }
     p.partial = s->k3_partial;

@@ -1057,6 +1057,10 @@ tc_status tc_server_open(size_t mem_budget_bytes, size_t max_step_samples, tc_se
     srv->tune.assign((size_t)kTuneWorkBins * kTuneLBins, t0);
     S_CU(cudaMalloc(&srv->d_out, (4 + max_step_samples) * sizeof(float)));
     S_CU(cudaMemset(srv->d_out, 0, 4 * sizeof(float)));
+    // IR upload staging for the longest IR a stream may have: growing it while
+    // serving would need a cudaFree, which waits for the whole device.
+    S_CU(cudaMalloc(&srv->ir_stage, kMaxL * sizeof(float)));
+    srv->ir_stage_floats = kMaxL;
     // Size the step buffers for a few thousand streams and load the kernels
     // now, so that the first steps do not pay for allocations or module loads.
     for (auto &b : srv->buf)

@@ -47,6 +47,14 @@ tc_status fail(tc_status st, const char *fmt, ...)
                         cudaGetErrorString(e_));                                                      \
     } while (0)
 
+// Stream-ordered allocations back TMA tensor maps and 16-byte stores; the
+// kernels need at least 16-byte alignment, and 256 is what is checked.
+#define TC_ALIGNED(ptr)                                                                     \
+    do {                                                                                    \
+        if ((reinterpret_cast<uintptr_t>(ptr) & 255u) != 0)                                 \
+            return fail(TC_ECUDA, "internal: a stream-ordered allocation is not 256-byte aligned"); \
+    } while (0)
+
 #define TC_TRY(expr)                 \
     do {                             \
         tc_status st_ = (expr);      \
@@ -661,6 +669,8 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
             const size_t bytes = (size_t)nkb * TN * KB * 2;
             TC_CU(cudaMallocAsync(&ts.thi, bytes, s->cs));
             TC_CU(cudaMallocAsync(&ts.tlo, bytes, s->cs));
+            TC_ALIGNED(ts.thi);
+            TC_ALIGNED(ts.tlo);
             ts.nkb = nkb;
             TC_CU(tc::encode_bf16_2d(&ts.mt_hi, ts.thi, (unsigned long long)KB, (unsigned long long)nkb * TN,
                                      (unsigned long long)KB * 2, KB, TN));
@@ -728,6 +738,7 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
                 cudaFreeAsync(s->k2_partial, s->cs);  // after the launches that used it
             s->k2_partial = nullptr;
             TC_CU(cudaMallocAsync(&s->k2_partial, need * sizeof(float), s->cs));
+            TC_ALIGNED(s->k2_partial);
             s->k2_partial_floats = need;
         }
         p.partial = s->k2_partial;
@@ -775,6 +786,8 @@ tc_status launch_k3(tc_stream *s, long long t0, long long nout, float *y, long l
         if (!ks.bh) {
             TC_CU(cudaMallocAsync(&ks.bh, rows * 32 * 2, s->cs));
             TC_CU(cudaMallocAsync(&ks.bl, rows * 32 * 2, s->cs));
+            TC_ALIGNED(ks.bh);
+            TC_ALIGNED(ks.bl);
             TC_CU(tc::encode_bf16_2d(&ks.mb_hi, ks.bh, 32, rows, 64, 32, 128));
             TC_CU(tc::encode_bf16_2d(&ks.mb_lo, ks.bl, 32, rows, 64, 32, 128));
         }
@@ -824,6 +837,7 @@ tc_status launch_k3(tc_stream *s, long long t0, long long nout, float *y, long l
         s->k3_partial = nullptr;
         s->k3_partial_floats = 0;
         TC_CU(cudaMallocAsync(&s->k3_partial, need * sizeof(float), s->cs));
+        TC_ALIGNED(s->k3_partial);
         s->k3_partial_floats = need;
     }
     p.partial = s->k3_partial;

@@ -259,7 +259,9 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
                       half * 128;
                 lim = 128;
             }
-            if (lim >= 128) {
+            // 16-byte stores only where the row is 16-byte aligned: a y row of
+            // pitch n starts at c n floats (n = L - 1 in a flush is often odd).
+            if (lim >= 128 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
 #pragma unroll
                 for (int j = 0; j < 128; j += 4)
                     *reinterpret_cast<float4 *>(dst + j) = make_float4(sum[j], sum[j + 1], sum[j + 2], sum[j + 3]);
@@ -437,7 +439,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
                     if (c >= p.C)
                         continue;
                     const long long j0 = cc * 16;
-                    if (lim >= j0 + 16) {
+                    if (lim >= j0 + 16 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
 #pragma unroll
                         for (int j = 0; j < 16; j += 4)
                             *reinterpret_cast<float4 *>(dst + j0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);

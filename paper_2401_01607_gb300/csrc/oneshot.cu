@@ -238,6 +238,10 @@ tc_status oneshot_alloc(const float *x, size_t N, const float *h, size_t L, floa
     if (e != cudaSuccess)
         return na_fail(e == cudaErrorMemoryAllocation ? TC_ENOMEM : TC_ECUDA,
                        std::string("tc_convolve: cudaMallocAsync: ") + cudaGetErrorString(e));
+    if ((reinterpret_cast<uintptr_t>(scratch) & 255u) != 0) {
+        cudaFreeAsync(scratch, cs);
+        return na_fail(TC_ECUDA, "tc_convolve: the stream-ordered allocation is not 256-byte aligned");
+    }
     const tc_status st = run_oneshot("tc_convolve", x, N, h, L, y, cs, scratch, full.total, P);
     cudaFreeAsync(scratch, cs);
     return st;

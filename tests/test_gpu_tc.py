@@ -106,3 +106,15 @@ def test_bf16_two_tiles_per_cta(pair, L):
     y, info = run_group(X, H, [0], L, B, "bf16", 1280, tuning=[(capi.TC_TUNE_K2_PAIR, pair)])
     assert info.tensor_launches > 0 and info.fp32_fallbacks == 0
     check(y, X, H, [0], B, "bf16", rows=[0, 127, 128, 255, 256, 299])
+
+
+@pytest.mark.parametrize("prec", ["bf16split", "bf16"])
+def test_short_ir_one_k_part_odd_pitch(prec):
+    """A short IR (L = 700: fewer than 32 K blocks, so one K part and the epilogue writes y itself) with
+    pushes and a flush whose output rows have odd pitch (476 and 699 floats): rows start unaligned."""
+    C, N, L, B = 130, 1500, 700, 256
+    X = synth.audio_block(C, N, 3100)
+    H = synth.decayed_ir(L, 140.0, 78)[None]
+    y, info = run_group(X, H, [0], L, B, prec, 1024)
+    assert info.tensor_launches > 0 and info.fp32_fallbacks == 0
+    check(y, X, H, [0], B, prec, rows=[0, 1, 2, 3, 65, 127, 128, 129])

@@ -32,7 +32,9 @@
  *   - Samples are float32. A group with C channels takes x as [C][n] and
  *     returns y as [C][n], row-major with rows of exactly n floats.
  *   - Host-pointer calls are synchronous: they return once y holds the
- *     result. Device-pointer calls (the *_dev functions, or on_device = 1)
+ *     result. Page-locked host buffers (cudaHostAlloc, cudaHostRegister, a
+ *     pinned torch tensor) are copied directly by the copy engines; pageable
+ *     ones go through the stream's own pinned staging buffers. Device-pointer calls (the *_dev functions, or on_device = 1)
  *     enqueue work on the stream's CUDA stream and return at once.
  *   - Use one tc_stream from one thread at a time. Different tc_streams may
  *     be used from different threads.

@@ -253,6 +253,20 @@ void free_all(tc_stream *s)
         cudaStreamDestroy(s->own_cs);
 }
 
+// True when p is page-locked host memory (cudaHostAlloc, cudaHostRegister, or
+// a pinned torch tensor): the copy engines read and write it directly, so the
+// host-pointer calls skip their staging copy through the stream's own pinned
+// buffers.
+bool pinned_host(const void *p)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();  // pageable memory on older drivers: clear the error
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
 tc_status alloc_ir(tc_stream *s)
 {
     if (s->ir) {
@@ -485,7 +499,17 @@ tc_status set_ir_impl(tc_stream *s, const float *h, size_t n, long long sample, 
     const size_t sets = s->nsets;
     const float *src = h;
     long long src_pitch = (long long)n;
-    if (!on_device) {
+    if (!on_device && pinned_host(h)) {
+        // Page-locked h: one copy straight into the staging rows, waited for so
+        // that h is free when the call returns.
+        const size_t cnt = (rows_given ? sets : 1) * n * sizeof(float);
+        TC_CU(cudaMemcpyAsync(s->ir_stage, h, cnt, cudaMemcpyHostToDevice, s->cs));
+        TC_CU(cudaEventRecord(s->ev_ir, s->cs));
+        TC_CU(cudaEventSynchronize(s->ev_ir));
+        if (!rows_given)
+            src_pitch = 0;
+        src = s->ir_stage;
+    } else if (!on_device) {
         TC_CU(cudaEventSynchronize(s->ev_ir));
         if (rows_given) {
             std::memcpy(s->pin_ir, h, sets * n * sizeof(float));
@@ -903,6 +927,8 @@ tc_status push_impl(tc_stream *s, const float *x, size_t n, float *y, bool on_de
     const size_t row_b = n * sizeof(float);
     if (on_device) {
         TC_CU(cudaMemcpy2DAsync(hist_at, pitch_b, x, row_b, row_b, s->rows, cudaMemcpyDeviceToDevice, s->cs));
+    } else if (pinned_host(x)) {
+        TC_CU(cudaMemcpy2DAsync(hist_at, pitch_b, x, row_b, row_b, s->rows, cudaMemcpyHostToDevice, s->cs));
     } else {
         TC_CU(cudaEventSynchronize(s->ev_x));
         std::memcpy(s->pin_x, x, s->rows * row_b);
@@ -917,11 +943,13 @@ tc_status push_impl(tc_stream *s, const float *x, size_t n, float *y, bool on_de
     if (n % s->block != 0)
         s->state = ST_ENDED;
     if (!on_device) {
-        TC_CU(cudaMemcpyAsync(s->pin_y, s->d_y, s->items * row_b, cudaMemcpyDeviceToHost, s->cs));
+        const bool direct = pinned_host(y);
+        TC_CU(cudaMemcpyAsync(direct ? y : s->pin_y, s->d_y, s->items * row_b, cudaMemcpyDeviceToHost, s->cs));
         TC_CU(cudaMemcpyAsync(s->pin_err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->cs));
         TC_CU(cudaStreamSynchronize(s->cs));
         TC_TRY(check_err_word(s));
-        std::memcpy(y, s->pin_y, s->items * row_b);
+        if (!direct)
+            std::memcpy(y, s->pin_y, s->items * row_b);
     }
     return TC_OK;
 }

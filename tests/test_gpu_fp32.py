@@ -135,6 +135,43 @@ def test_device_pointer_path_matches_host_path():
     assert rel_l2(dev, host) <= 1e-7
 
 
+def test_pinned_host_buffers_match_pageable():
+    """Page-locked host buffers take the direct-copy path (no staging through the stream's own pinned
+    buffers): IR rows, pushes and the flush give the same bits as pageable buffers."""
+    torch = pytest.importorskip("torch")
+    N, L, B, C = 4096, 3000, 128, 4
+    x = synth.audio_block(C, N, 78)
+    H = np.stack([[synth.decayed_ir(L, 900.0, 400 + 10 * v + c) for c in range(C)] for v in range(2)])
+    vstart = [0, 1500]
+
+    def run(pin):
+        def host(a):
+            a = np.ascontiguousarray(a, np.float32)
+            return torch.from_numpy(a).pin_memory().numpy() if pin else a
+
+        s = capi.tc_open_group(C, L, B, False, capi.TC_FP32, 512)
+        try:
+            capi.tc_set_ir_rows(s, host(H[0]), L, 0)
+            outs = []
+            for pos in range(0, N, 512):
+                if pos <= vstart[1] < pos + 512:
+                    capi.tc_set_ir_rows(s, host(H[1]), L, vstart[1])
+                yb = host(np.empty((C, 512), np.float32))
+                capi.tc_push(s, host(x[:, pos:pos + 512]), 512, yb)
+                outs.append(yb.copy())
+            tail = host(np.empty((C, L - 1), np.float32))
+            capi.tc_flush(s, tail, L - 1)
+            outs.append(tail.copy())
+        finally:
+            capi.tc_close(s)
+        return np.concatenate(outs, axis=1)
+
+    a, b = run(True), run(False)
+    assert np.array_equal(a, b)
+    ref = np.stack([oracle.buffer(x[c], H[:, c], np.asarray(vstart, np.int64), B) for c in range(C)])
+    assert rel_l2(a, ref) <= TOL["fp32"]
+
+
 def test_convolve_one_shot():
     torch = pytest.importorskip("torch")
     N, L = 10_000, 2_048

@@ -1182,7 +1182,7 @@ tc_status tc_flush(tc_stream *s, float *y, size_t cap, size_t *n_out)
         return TC_OK;
     }
     float *d = nullptr;
-    TC_CU(cudaMalloc(&d, s->items * tail * sizeof(float)));
+    TC_CU(cudaMallocAsync(reinterpret_cast<void **>(&d), s->items * tail * sizeof(float), s->cs));
     tc_status st = flush_to_device(s, d, (long long)tail);
     if (st == TC_OK) {
         cudaError_t e = cudaMemcpy2DAsync(y, cap * sizeof(float), d, tail * sizeof(float), tail * sizeof(float),
@@ -1196,7 +1196,7 @@ tc_status tc_flush(tc_stream *s, float *y, size_t cap, size_t *n_out)
         else
             st = check_err_word(s);
     }
-    cudaFree(d);
+    cudaFreeAsync(d, s->cs);
     return st;
 }
 

@@ -260,14 +260,20 @@ def cpu_model() -> str:
 # Distributed plumbing (torchrun): barrier and max over ranks on the host
 # ---------------------------------------------------------------------------
 class Dist:
-    def __init__(self):
+    """Host-side plumbing of a multi-rank run (gloo): a barrier and the max of the
+    ranks' times; no collective on the data path. A rank that fails or never
+    joins makes the others' next barrier raise (the peer's connection closes,
+    or timeout_s passes) instead of hanging."""
+
+    def __init__(self, timeout_s: float = 600.0):
         self.world = int(os.environ.get("WORLD_SIZE", "1"))
         self.rank = int(os.environ.get("RANK", "0"))
         self.local = int(os.environ.get("LOCAL_RANK", "0"))
         self.pg = None
         if self.world > 1:
+            import datetime
             import torch.distributed as dist
-            dist.init_process_group("gloo")
+            dist.init_process_group("gloo", timeout=datetime.timedelta(seconds=timeout_s))
             self.pg = dist
 
     def barrier(self):

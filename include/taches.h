@@ -273,6 +273,20 @@ tc_status tc_convolve_q15(const int16_t *x, size_t N, const int16_t *h, size_t L
                           void *cuda_stream);
 
 /* ---------------------------------------------------------------------- */
+/* Failure detection check                                                 */
+/* ---------------------------------------------------------------------- */
+
+/* Every device-side wait of the kernels is bounded (by %globaltimer and a
+ * poll count); when a bound is reached the kernel reports into its error word
+ * and returns, and the call returns TC_ETIMEOUT. This runs one kernel whose
+ * wait (on an mbarrier that nothing completes) must run out after limit_ns
+ * nanoseconds (1 <= limit_ns <= 1e10). Returns TC_ETIMEOUT, the expected
+ * result, after about limit_ns; the CUDA context stays usable. TC_EINVAL for
+ * a bad limit; TC_ECUDA if the wait did not report. Runs on cuda_stream
+ * (NULL = default stream) and waits for it. */
+tc_status tc_selftest_wait(unsigned long long limit_ns, void *cuda_stream);
+
+/* ---------------------------------------------------------------------- */
 /* Serving: continuous batching of many independent streams               */
 /* ---------------------------------------------------------------------- */
 /*

@@ -80,6 +80,7 @@ _SIGS = {
     "tc_convolve": [_vp, _sz, _vp, _sz, _vp, _vp],
     "tc_convolve_noalloc": [_vp, _sz, _vp, _sz, _vp, _vp],
     "tc_convolve_q15": [_vp, _sz, _vp, _sz, _vp, _vp, _vp],
+    "tc_selftest_wait": [ctypes.c_ulonglong, _vp],
     "tc_set_tuning": [_vp, _int, ctypes.c_longlong],
     "tc_profile": [_vp, _int],
     "tc_profile_read": [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_u64), ctypes.POINTER(ctypes.c_double)],
@@ -313,6 +314,13 @@ def tc_convolve_q15(x, N: int, h, L: int, y, acc=None, cuda_stream=None) -> None
                                            int(cuda_stream.cuda_stream))
     _call("tc_convolve_q15", _dev_ptr(x, "int16"), N, _dev_ptr(h, "int16"), L,
           None if y is None else _dev_ptr(y, "int16"), None if acc is None else _dev_ptr(acc, "int64"), cs)
+
+
+def tc_selftest_wait(limit_ns: int, cuda_stream=None) -> None:
+    """Runs the bounded-wait check; raises TcError with code TC_ETIMEOUT, its expected outcome."""
+    cs = None if cuda_stream is None else (cuda_stream if isinstance(cuda_stream, int) else
+                                           int(cuda_stream.cuda_stream))
+    _call("tc_selftest_wait", int(limit_ns), cs)
 
 
 def tc_last_error() -> str:

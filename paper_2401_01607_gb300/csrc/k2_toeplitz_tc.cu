@@ -206,25 +206,8 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
             const int buf = r & 1;
             const uint32_t par = (uint32_t)((r >> 1) & 1);
             bool got = true;
-            if (lane == 0) {
-                got = false;
-                // Bounded, and abandoned early if another role has failed.
-                const unsigned long long t0 = globaltimer_ns();
-                for (uint32_t it = 0;; ++it) {
-                    if (mbar_try_wait(&accfull[buf], par)) {
-                        got = true;
-                        break;
-                    }
-                    if ((it & 255u) == 255u) {
-                        if (s_fail)
-                            break;
-                        if (globaltimer_ns() - t0 > kWaitLimitNs) {
-                            atomicOr(p.err, ERR_TIMEOUT_MMA);
-                            break;
-                        }
-                    }
-                }
-            }
+            if (lane == 0)  // bounded, and abandoned early if another role has failed
+                got = mbar_wait_limited(&accfull[buf], par, p.err, ERR_TIMEOUT_MMA, kWaitLimitNs, &s_fail);
             got = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
             if (!got) {
                 ok = false;
@@ -393,24 +376,8 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
         const int q = warp & 3;    // TMEM lane quarter this warp may access
         const int half = ew >> 2;  // column half
         bool got = true;
-        if (lane == 0) {
-            got = false;
-            const unsigned long long t0 = globaltimer_ns();
-            for (uint32_t it = 0;; ++it) {
-                if (mbar_try_wait(&accfull, 0)) {
-                    got = true;
-                    break;
-                }
-                if ((it & 255u) == 255u) {
-                    if (s_fail)
-                        break;
-                    if (globaltimer_ns() - t0 > kWaitLimitNs) {
-                        atomicOr(p.err, ERR_TIMEOUT_MMA);
-                        break;
-                    }
-                }
-            }
-        }
+        if (lane == 0)  // bounded, and abandoned early if another role has failed
+            got = mbar_wait_limited(&accfull, 0, p.err, ERR_TIMEOUT_MMA, kWaitLimitNs, &s_fail);
         got = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
         if (got && nk > 0) {
             mbar_try_wait(&accfull, 0);

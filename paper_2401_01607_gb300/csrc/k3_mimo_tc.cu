@@ -272,24 +272,8 @@ __global__ void __launch_bounds__(K3_THREADS, 1)
             const int buf = r % C::NB;
             const uint32_t par = (uint32_t)((r / C::NB) & 1);
             bool got = true;
-            if (lane == 0) {
-                got = false;
-                const unsigned long long t0 = globaltimer_ns();
-                for (uint32_t it = 0;; ++it) {
-                    if (mbar_try_wait(&accfull[buf], par)) {
-                        got = true;
-                        break;
-                    }
-                    if ((it & 255u) == 255u) {
-                        if (s_fail)
-                            break;
-                        if (globaltimer_ns() - t0 > kWaitLimitNs) {
-                            atomicOr(p.err, ERR_TIMEOUT_MMA);
-                            break;
-                        }
-                    }
-                }
-            }
+            if (lane == 0)  // bounded, and abandoned early if another role has failed
+                got = mbar_wait_limited(&accfull[buf], par, p.err, ERR_TIMEOUT_MMA, kWaitLimitNs, &s_fail);
             got = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
             if (!got) {
                 ok = false;

@@ -73,22 +73,40 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
-// Waits until the barrier's phase with the given parity has completed, at
-// most kWaitLimitNs. On timeout, ORs `errbit` into *err and returns false.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *err, int errbit)
+// Iteration backstop of every bounded wait, beside its time limit: a wait
+// also ends after this many polls (at least seconds), even if %globaltimer
+// were not to advance.
+constexpr uint32_t kWaitMaxPolls = 1u << 30;
+
+// Polls mbarrier `bar` for phase `parity` until the phase completes (true), or
+// limit_ns of %globaltimer or kWaitMaxPolls polls have passed, or *abort
+// (checked every 256 polls) is nonzero (false). On a timeout, ORs errbit into
+// *err (err may be NULL); on an abort, leaves *err to the role that failed.
+__device__ __forceinline__ bool mbar_wait_limited(uint64_t *bar, uint32_t parity, int *err, int errbit,
+                                                  unsigned long long limit_ns, const volatile int *abort = nullptr)
 {
     if (mbar_try_wait(bar, parity))
         return true;
     const unsigned long long t0 = globaltimer_ns();
-    for (uint32_t it = 0;; ++it) {
+    for (uint32_t it = 0; it < kWaitMaxPolls; ++it) {
         if (mbar_try_wait(bar, parity))
             return true;
-        if ((it & 255u) == 255u && globaltimer_ns() - t0 > kWaitLimitNs) {
-            if (err)
-                atomicOr(err, errbit);
-            return false;
+        if ((it & 255u) == 255u) {
+            if (abort && *abort)
+                return false;
+            if (globaltimer_ns() - t0 > limit_ns)
+                break;
         }
     }
+    if (err)
+        atomicOr(err, errbit);
+    return false;
+}
+
+// The kernels' waits: at most kWaitLimitNs.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *err, int errbit)
+{
+    return mbar_wait_limited(bar, parity, err, errbit, kWaitLimitNs);
 }
 
 // 1-D bulk copy global -> shared, completing `bytes` of transaction count on

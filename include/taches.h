@@ -202,6 +202,24 @@ tc_status tc_flush_dev(tc_stream *s, float *y, size_t *n_out);
 tc_status tc_sync(tc_stream *s);
 
 /* ---------------------------------------------------------------------- */
+/* Checkpoint / resume                                                     */
+/* ---------------------------------------------------------------------- */
+
+/* Copies everything the stream's future outputs depend on into a host blob:
+ * shape, position and state, the live IR versions (start sample, crossfade
+ * length, IR rows) and the input history from the stream's current base, plus
+ * the tuning knobs. buf NULL: only *size is set (bytes needed). Waits for the
+ * stream's device work. Errors: TC_EINVAL (NULL size, cap < needed). */
+tc_status tc_stream_export(tc_stream *s, void *buf, size_t cap, size_t *size);
+/* Restores a blob of tc_stream_export into s, which must have the same kind,
+ * precision, channel counts, L, block and max_push (TC_EINVAL otherwise, or
+ * for a blob that is not one). s's previous state is discarded. Pushes after
+ * the import give the same bits as the exported stream would have: the
+ * history keeps its layout, so the kernels split the taps the same way.
+ * Waits for the copies. */
+tc_status tc_stream_import(tc_stream *s, const void *buf, size_t size);
+
+/* ---------------------------------------------------------------------- */
 /* One-shot convolution (off-line use, Sec. 3.2)                           */
 /* ---------------------------------------------------------------------- */
 

@@ -81,6 +81,8 @@ _SIGS = {
     "tc_convolve_noalloc": [_vp, _sz, _vp, _sz, _vp, _vp],
     "tc_convolve_q15": [_vp, _sz, _vp, _sz, _vp, _vp, _vp],
     "tc_selftest_wait": [ctypes.c_ulonglong, _vp],
+    "tc_stream_export": [_vp, _vp, _sz, ctypes.POINTER(_sz)],
+    "tc_stream_import": [_vp, _vp, _sz],
     "tc_set_tuning": [_vp, _int, ctypes.c_longlong],
     "tc_profile": [_vp, _int],
     "tc_profile_read": [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_u64), ctypes.POINTER(ctypes.c_double)],
@@ -321,6 +323,20 @@ def tc_selftest_wait(limit_ns: int, cuda_stream=None) -> None:
     cs = None if cuda_stream is None else (cuda_stream if isinstance(cuda_stream, int) else
                                            int(cuda_stream.cuda_stream))
     _call("tc_selftest_wait", int(limit_ns), cs)
+
+
+def tc_stream_export(s: int) -> bytes:
+    """Checkpoint of the stream (host blob)."""
+    n = _sz()
+    _call("tc_stream_export", s, None, 0, ctypes.byref(n))
+    buf = ctypes.create_string_buffer(max(int(n.value), 1))
+    _call("tc_stream_export", s, buf, int(n.value), ctypes.byref(n))
+    return buf.raw[:int(n.value)]
+
+
+def tc_stream_import(s: int, blob: bytes) -> None:
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    _call("tc_stream_import", s, buf, len(blob))
 
 
 def tc_last_error() -> str:

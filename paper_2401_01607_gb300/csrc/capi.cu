@@ -458,6 +458,7 @@ tc_status upload_table(tc_stream *s)
 tc_status set_ir_impl(tc_stream *s, const float *h, size_t n, long long sample, bool rows_given,
                       bool on_device)
 {
+    tc::Range nvtx_range("tc set_ir");
     TC_TRY(check_stream(s));
     if (!h)
         return fail(TC_EINVAL, "h is NULL");
@@ -909,6 +910,7 @@ tc_status check_err_word(tc_stream *s)
 
 tc_status push_impl(tc_stream *s, const float *x, size_t n, float *y, bool on_device, size_t limit)
 {
+    tc::Range nvtx_range("tc push");
     TC_TRY(check_stream(s));
     if (!x || !y)
         return fail(TC_EINVAL, "x or y is NULL");
@@ -958,6 +960,7 @@ tc_status push_impl(tc_stream *s, const float *x, size_t n, float *y, bool on_de
 // zeros through the gather in pieces of at most max_push samples.
 tc_status flush_to_device(tc_stream *s, float *y, long long y_pitch)
 {
+    tc::Range nvtx_range("tc flush");
     const long long tail = (long long)s->L - 1;
     s->pos_end_hint = s->pos;
     for (long long off = 0; off < tail;) {
@@ -1279,6 +1282,153 @@ tc_status tc_set_tuning(tc_stream *s, int knob, long long value)
     default:
         return fail(TC_EINVAL, "unknown tuning knob %d", knob);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Checkpoint / resume: the whole state a stream's future outputs depend on.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr uint32_t kBlobMagic = 0x31534354u;  // "TCS1"
+
+struct BlobHeader {
+    uint32_t magic, version;
+    int32_t kind, prec, shared_ir, state;
+    uint64_t rows, items, nin, nsets, L, block, max_push;
+    int64_t pos, base, next_ramp, nver, hist_len;
+    int32_t k1_variant_fixed, k2_single_tile, zero_skip, pad;
+    int64_t k2_range;
+};
+
+size_t blob_size(const tc_stream *s)
+{
+    const size_t nver = s->vt.size();
+    const size_t hist_len = (size_t)std::max<long long>(0, s->pos - s->base);
+    return sizeof(BlobHeader) + nver * 2 * sizeof(int64_t) + nver * s->nsets * s->L * sizeof(float) +
+           s->rows * hist_len * sizeof(float);
+}
+
+}  // namespace
+
+tc_status tc_stream_export(tc_stream *s, void *buf, size_t cap, size_t *size)
+{
+    TC_TRY(check_stream(s));
+    if (!size)
+        return fail(TC_EINVAL, "size is NULL");
+    TC_TRY(use_device(s));
+    const size_t need = blob_size(s);
+    *size = need;
+    if (!buf)
+        return TC_OK;
+    if (cap < need)
+        return fail(TC_EINVAL, "buffer of %zu bytes < %zu needed", cap, need);
+    TC_CU(cudaStreamSynchronize(s->cs));
+    char *out = static_cast<char *>(buf);
+    BlobHeader hd{};
+    hd.magic = kBlobMagic;
+    hd.version = 1;
+    hd.kind = s->kind;
+    hd.prec = (int32_t)s->prec;
+    hd.shared_ir = s->shared_ir;
+    hd.state = s->state;
+    hd.rows = s->rows;
+    hd.items = s->items;
+    hd.nin = s->nin;
+    hd.nsets = s->nsets;
+    hd.L = s->L;
+    hd.block = s->block;
+    hd.max_push = s->max_push;
+    hd.pos = s->pos;
+    hd.base = s->base;
+    hd.next_ramp = s->next_ramp;
+    hd.nver = (int64_t)s->vt.size();
+    hd.hist_len = std::max<long long>(0, s->pos - s->base);
+    hd.k1_variant_fixed = s->k1_variant_fixed;
+    hd.k2_single_tile = s->k2_single_tile ? 1 : 0;
+    hd.zero_skip = s->zero_skip ? 1 : 0;
+    hd.k2_range = s->k2_range;
+    std::memcpy(out, &hd, sizeof hd);
+    out += sizeof hd;
+    for (const Version &v : s->vt) {
+        const int64_t sv[2] = {v.start, v.ramp};
+        std::memcpy(out, sv, sizeof sv);
+        out += sizeof sv;
+    }
+    // IR rows of each live version: the slot's unshifted copy holds h[k] at k.
+    for (const Version &v : s->vt)
+        for (size_t set = 0; set < s->nsets; ++set) {
+            const float *src = s->ir + ((size_t)v.slot * s->nsets + set) * 4 * (size_t)s->Lpad;
+            TC_CU(cudaMemcpy(out, src, s->L * sizeof(float), cudaMemcpyDeviceToHost));
+            out += s->L * sizeof(float);
+        }
+    // History rows from base to pos (the stream's layout is kept, so the
+    // kernels' tap-chunk alignment and the results resume bit for bit).
+    if (hd.hist_len > 0)
+        TC_CU(cudaMemcpy2D(out, (size_t)hd.hist_len * sizeof(float), s->hist, (size_t)s->cap * sizeof(float),
+                           (size_t)hd.hist_len * sizeof(float), s->rows, cudaMemcpyDeviceToHost));
+    return TC_OK;
+}
+
+tc_status tc_stream_import(tc_stream *s, const void *buf, size_t size)
+{
+    TC_TRY(check_stream(s));
+    if (!buf || size < sizeof(BlobHeader))
+        return fail(TC_EINVAL, "buffer is NULL or too short");
+    BlobHeader hd;
+    std::memcpy(&hd, buf, sizeof hd);
+    if (hd.magic != kBlobMagic || hd.version != 1)
+        return fail(TC_EINVAL, "not a stream checkpoint of this library");
+    if (hd.kind != s->kind || hd.prec != (int32_t)s->prec || hd.shared_ir != s->shared_ir || hd.rows != s->rows ||
+        hd.items != s->items || hd.nin != s->nin || hd.nsets != s->nsets || hd.L != s->L ||
+        hd.block != s->block || hd.max_push != s->max_push)
+        return fail(TC_EINVAL, "the checkpoint is of a stream of another shape (kind, precision, channels, L, "
+                               "block, max_push must match)");
+    if (hd.nver < 1 || hd.nver > s->nslots || hd.hist_len < 0 || hd.hist_len > s->cap ||
+        hd.pos - hd.base != hd.hist_len)
+        return fail(TC_EINVAL, "inconsistent checkpoint (versions or history length)");
+    const size_t need = sizeof hd + (size_t)hd.nver * 2 * sizeof(int64_t) +
+                        (size_t)hd.nver * s->nsets * s->L * sizeof(float) + s->rows * (size_t)hd.hist_len * 4;
+    if (size < need)
+        return fail(TC_EINVAL, "checkpoint of %zu bytes < %zu expected", size, need);
+    TC_TRY(use_device(s));
+    TC_TRY(clear_state(s));  // also marks every Toeplitz / MIMO tile cache stale
+    const char *in = static_cast<const char *>(buf) + sizeof hd;
+    std::vector<Version> vt;
+    for (int64_t i = 0; i < hd.nver; ++i) {
+        int64_t sv[2];
+        std::memcpy(sv, in, sizeof sv);
+        in += sizeof sv;
+        vt.push_back(Version{sv[0], (int)i, sv[1]});
+    }
+    for (int64_t i = 0; i < hd.nver; ++i) {
+        // IR rows to the staging area, then the four shifted copies of slot i.
+        TC_CU(cudaMemcpy(s->ir_stage, in, s->nsets * s->L * sizeof(float), cudaMemcpyHostToDevice));
+        in += s->nsets * s->L * sizeof(float);
+        float *dst = s->ir + (size_t)i * s->nsets * 4 * (size_t)s->Lpad;
+        TC_CU(tc::ir_prep_launch(s->ir_stage, (long long)s->L, (long long)s->L, (int)s->nsets, dst, 4 * s->Lpad,
+                                 s->Lpad, s->Lpad, s->cs));
+        TC_CU(cudaStreamSynchronize(s->cs));  // the staging area is reused by the next version
+        s->slot_used[(size_t)i] = 1;
+    }
+    if (hd.hist_len > 0) {
+        TC_CU(cudaMemcpy2DAsync(s->hist, (size_t)s->cap * sizeof(float), in, (size_t)hd.hist_len * sizeof(float),
+                                (size_t)hd.hist_len * sizeof(float), s->rows, cudaMemcpyHostToDevice, s->cs));
+    }
+    s->vt = vt;
+    s->vt_dirty = true;
+    s->ir_ever_set = true;
+    s->pos = hd.pos;
+    s->base = hd.base;
+    s->state = hd.state;
+    s->next_ramp = hd.next_ramp;
+    s->k1_variant_fixed = hd.k1_variant_fixed;
+    s->k2_single_tile = hd.k2_single_tile != 0;
+    s->zero_skip = hd.zero_skip != 0;
+    s->k2_range = hd.k2_range;
+    if (hd.hist_len > 0)
+        TC_TRY(split_new(s, 0, hd.hist_len));  // bf16 hi/lo copies of the history (tensor-core streams)
+    TC_CU(cudaStreamSynchronize(s->cs));
+    return TC_OK;
 }
 
 tc_status tc_profile(tc_stream *s, int enable)

@@ -192,6 +192,7 @@ int q15_inner()
 extern "C" tc_status tc_convolve_q15(const int16_t *x, size_t N, const int16_t *h, size_t L, int16_t *y,
                                      int64_t *acc, void *cuda_stream)
 {
+    tc::Range nvtx_range("tc_convolve_q15");
     if (!x || !h || (!y && !acc))
         return (tc::set_last_error("tc_convolve_q15: x, h or both outputs are NULL"), TC_EINVAL);
     if (N == 0 || L == 0 || L > ((size_t)1 << 19) || N > ((size_t)1 << 40))

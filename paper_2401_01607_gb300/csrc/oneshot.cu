@@ -129,6 +129,7 @@ Layout layout(long long N, long long L, long long scratch_floats)
 tc_status run_oneshot(const char *who, const float *x, size_t N, const float *h, size_t L, float *y,
                       cudaStream_t cs, float *scratch, long long scratch_floats, const DevPtrs &P)
 {
+    tc::Range nvtx_range(who);
     const long long Ll = (long long)L, Nl = (long long)N;
     const Layout lay = layout(Nl, Ll, scratch_floats);
     float *base = scratch;

@@ -555,6 +555,7 @@ double release_sources(tc_server *srv, double now)
 // mu_state. Returns the number of blocks taken.
 size_t collect(tc_server *srv, tc_server::StepBuf &b)
 {
+    tc::Range nvtx_range("server step: collect");
     b.items.clear();
     b.total = 0;
     size_t nblocks = 0;
@@ -656,6 +657,7 @@ tc_status graph_launch(tc_server *srv, tc_server::StepBuf &b, int variant, size_
 // (no wait). Caller holds mu_state. Advances each stream's launch position.
 tc_status pack_launch(tc_server *srv, tc_server::StepBuf &b)
 {
+    tc::Range nvtx_range("server step: pack and launch");
     // Plain streams go into the K1 work list; groups run after it.
     std::vector<size_t> plain, group;
     for (size_t i = 0; i < b.items.size(); ++i)
@@ -864,6 +866,7 @@ tc_status pack_launch(tc_server *srv, tc_server::StepBuf &b)
 // outputs: finished blocks, latencies, flush tails, positions, stats.
 tc_status complete(tc_server *srv, tc_server::StepBuf &b)
 {
+    tc::Range nvtx_range("server step: wait and deliver");
     S_CU(cudaEventSynchronize(b.done));
     const double t_done = now_s();
     std::lock_guard<std::mutex> lk(srv->mu_state);

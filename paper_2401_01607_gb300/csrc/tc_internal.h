@@ -6,9 +6,21 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "taches.h"
 
 namespace tc {
+
+// NVTX range over a host-side phase (push, IR upload, flush, server step):
+// profilers that attach to the process show where host time goes; without
+// one attached a range costs a few nanoseconds. NVTX 3 is header-only.
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 
 // ---------------------------------------------------------------------------
 // K1: FP32 output-side gather (per-stream IRs, or any IR layout).

@@ -994,18 +994,12 @@ namespace tc {
 
 // A shared-IR group stream driven by the server's worker: pushes of up to
 // max_push samples per channel, any length (block 1: a push never ends the
-// stream), device pointers, on the server's CUDA stream `cs`.
-tc_status group_open(size_t channels, size_t L, size_t max_push, int precision, void *cs, tc_stream **out,
-                     size_t *bytes)
+// stream), device pointers, on the group's own CUDA stream (the server orders
+// it against its steps with events, so groups run concurrently).
+tc_status group_open(size_t channels, size_t L, size_t max_push, int precision, tc_stream **out, size_t *bytes)
 {
     TC_TRY(open_any(KIND_GROUP, channels, channels, 1, 1, L, 1, 1, (tc_precision)precision, max_push, out));
     tc_stream *s = *out;
-    tc_status st = tc_set_cuda_stream(s, cs);
-    if (st != TC_OK) {
-        tc_close(s);
-        *out = nullptr;
-        return st;
-    }
     // Device footprint: what open allocated, plus what the tensor-core
     // launches allocate in steady use (Toeplitz tiles of two live IR versions
     // at one alignment shift: pushes at multiples of 8 samples keep the
@@ -1031,6 +1025,8 @@ tc_status group_push(tc_stream *s, const float *x, size_t n, float *y)
 }
 
 int *group_err(tc_stream *s) { return s->d_err; }
+
+void *group_stream(tc_stream *s) { return s->cs; }
 
 }  // namespace tc
 

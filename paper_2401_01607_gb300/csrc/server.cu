@@ -95,6 +95,7 @@ struct SStream {
     // list. hist, ir and d_vt stay unused.
     long long channels = 1;
     tc_stream *grp = nullptr;
+    cudaEvent_t gdone = nullptr;  // the group's push of the current step is done
     std::mutex gmu;           // the group stream: worker pushes vs IR uploads
     long long tail_fill = 0;  // flush tail samples delivered so far (per row)
     float *hist = nullptr;       // [cap]
@@ -162,6 +163,7 @@ struct tc_server {
         float *pin_out = nullptr;  // [4 + max_step_samples]
         DevTable *pin_tables = nullptr;
         cudaEvent_t done = nullptr;
+        cudaEvent_t in_ready = nullptr;  // the step's packed input is on the device (groups wait on it)
         std::vector<Item> items;
         size_t total = 0;
         double t_begin = 0.0, t_launch = 0.0;
@@ -311,6 +313,10 @@ void free_stream(tc_server *srv, SStream *s)
     if (s->grp) {
         tc_close(s->grp);  // waits for the steps that used it
         s->grp = nullptr;
+    }
+    if (s->gdone) {
+        cudaEventDestroy(s->gdone);
+        s->gdone = nullptr;
     }
     if (s->hist)
         cudaFreeAsync(s->hist, srv->cs);
@@ -828,6 +834,8 @@ tc_status pack_launch(tc_server *srv, tc_server::StepBuf &b)
         S_TRY(graph_launch(srv, b, variant, lay.end, a_in, a_sc, a_dst, ni, a_items, a_cta, cta, out_bytes));
     } else {
         S_CU(cudaMemcpyAsync(ds, b.pin_stage, lay.end, cudaMemcpyHostToDevice, srv->cs));
+        if (!group.empty())
+            S_CU(cudaEventRecord(b.in_ready, srv->cs));
         if (ni > 0) {
             ingest_kernel<<<(unsigned)ni, 256, 0, srv->cs>>>(a_in, a_sc, a_dst, ni);
             tc::count_launch();
@@ -836,13 +844,18 @@ tc_status pack_launch(tc_server *srv, tc_server::StepBuf &b)
             S_CU(tc::k1_launch_list(a_items, a_cta, ni, cta, variant, srv->cs));
             S_CU(cudaEventRecord(b.k1_stop, srv->cs));
         }
-        // Groups: one push of the group stream each (history copy, bf16 split,
-        // K2 or K1, K-part reduce), reading the packed input on the device and
-        // writing the packed output; its error word joins the step's.
+        // Groups: one push of each group's stream (history copy, bf16 split,
+        // K2 or K1, K-part reduce) on the group's own CUDA stream, after the
+        // packed input has landed and beside the gather: groups run
+        // concurrently. Each reads the packed input on the device and writes
+        // its part of the packed output; its error word joins the step's; the
+        // step's output copy waits for all of them.
         for (size_t i : group) {
             tc_server::Item &w = b.items[i];
             SStream *s = w.s;
             std::lock_guard<std::mutex> g(s->gmu);
+            cudaStream_t gcs = static_cast<cudaStream_t>(tc::group_stream(s->grp));
+            S_CU(cudaStreamWaitEvent(gcs, b.in_ready, 0));
             tc_info before{}, after{};
             tc_get_info(s->grp, &before);
             tc_status st = tc::group_push(s->grp, a_in + w.off, (size_t)w.n, d_y + w.off);
@@ -851,9 +864,11 @@ tc_status pack_launch(tc_server *srv, tc_server::StepBuf &b)
             tc_get_info(s->grp, &after);
             srv->tensor_launches += after.tensor_launches - before.tensor_launches;
             srv->fp32_fallbacks += after.fp32_fallbacks - before.fp32_fallbacks;
-            err_merge_kernel<<<1, 1, 0, srv->cs>>>(d_err, tc::group_err(s->grp));
+            err_merge_kernel<<<1, 1, 0, gcs>>>(d_err, tc::group_err(s->grp));
             tc::count_launch();
             S_CU(cudaGetLastError());
+            S_CU(cudaEventRecord(s->gdone, gcs));
+            S_CU(cudaStreamWaitEvent(srv->cs, s->gdone, 0));
             s->pos += w.n;
         }
         S_CU(cudaMemcpyAsync(b.pin_out, srv->d_out, out_bytes, cudaMemcpyDeviceToHost, srv->cs));
@@ -1051,6 +1066,7 @@ tc_status tc_server_open(size_t mem_budget_bytes, size_t max_step_samples, tc_se
     for (auto &b : srv->buf) {
         S_CU(cudaHostAlloc(&b.pin_out, (4 + max_step_samples) * sizeof(float), cudaHostAllocDefault));
         S_CU(cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming));
+        S_CU(cudaEventCreateWithFlags(&b.in_ready, cudaEventDisableTiming));
         S_CU(cudaEventCreate(&b.k1_start));
         S_CU(cudaEventCreate(&b.k1_stop));
     }
@@ -1096,6 +1112,8 @@ tc_status tc_server_close(tc_server *srv)
         cudaFreeHost(b.pin_tables);
         if (b.done)
             cudaEventDestroy(b.done);
+        if (b.in_ready)
+            cudaEventDestroy(b.in_ready);
         if (b.k1_start)
             cudaEventDestroy(b.k1_start);
         if (b.k1_stop)
@@ -1205,14 +1223,18 @@ tc_status tc_server_add_group(tc_server *srv, size_t channels, size_t L, size_t 
     std::lock_guard<std::mutex> la(srv->mu_admin);
     S_CU(cudaSetDevice(srv->device));
     size_t bytes = 0;
-    S_TRY(tc::group_open(channels, L, (size_t)kMerge * block, precision, srv->cs, &s->grp, &bytes));
+    S_TRY(tc::group_open(channels, L, (size_t)kMerge * block, precision, &s->grp, &bytes));
+    if (cudaEventCreateWithFlags(&s->gdone, cudaEventDisableTiming) != cudaSuccess) {
+        tc_close(s->grp);
+        s->grp = nullptr;
+        return sfail(TC_ECUDA, "tc_server_add_group: event creation failed");
+    }
     s->bytes = bytes;
     {
         std::lock_guard<std::mutex> lk(srv->mu_state);
         if (srv->used + s->bytes > srv->budget) {
             srv->rejected++;
-            tc_close(s->grp);
-            s->grp = nullptr;
+            free_stream(srv, s.get());
             return sfail(TC_ENOMEM, "tc_server_add_group: the group does not fit the device memory budget now");
         }
         srv->used += s->bytes;
@@ -1220,8 +1242,7 @@ tc_status tc_server_add_group(tc_server *srv, size_t channels, size_t L, size_t 
     tc_status st = tc_set_ir_at(s->grp, h, n, 0);
     if (st != TC_OK) {
         const std::string m = tc_last_error();
-        tc_close(s->grp);
-        s->grp = nullptr;
+        free_stream(srv, s.get());
         std::lock_guard<std::mutex> lk(srv->mu_state);
         srv->used -= s->bytes;
         return sfail(st, m);

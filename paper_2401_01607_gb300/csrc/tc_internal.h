@@ -220,12 +220,13 @@ bool no_role_swap();
 tc_status oneshot_alloc(const float *x, size_t N, const float *h, size_t L, float *y, void *cuda_stream);
 
 // Server groups (C channels, one shared IR, any precision): a group stream
-// on the server's CUDA stream, its device footprint in bytes, device-pointer
-// pushes (x and y [C][n]) that only enqueue work, and its device error word.
-tc_status group_open(size_t channels, size_t L, size_t max_push, int precision, void *cs, tc_stream **out,
-                     size_t *bytes);
+// with its own CUDA stream, its device footprint in bytes, device-pointer
+// pushes (x and y [C][n]) that only enqueue work, its device error word and
+// its CUDA stream.
+tc_status group_open(size_t channels, size_t L, size_t max_push, int precision, tc_stream **out, size_t *bytes);
 tc_status group_push(tc_stream *s, const float *x, size_t n, float *y);
 int *group_err(tc_stream *s);
+void *group_stream(tc_stream *s);
 uint64_t launches();
 
 }  // namespace tc

@@ -966,7 +966,7 @@ def bench_capacity(torch, capi, H64: np.ndarray, pool: np.ndarray, paced_s: floa
 
 def bench_groups(capi, paced_s: float = 1.5, C: int = 128, L: int = 96_000, B: int = 256,
                  precisions=("bf16split", "fp32"),
-                 ladder=(4, 8, 16, 24, 32, 40, 48, 64, 80, 96, 128, 160, 192, 256)) -> dict:
+                 ladder=(4, 8, 16, 24, 32, 40, 48, 64, 80, 96, 112, 128, 144, 160, 192, 256)) -> dict:
     """Serving of shared-IR groups (tc_server_add_group): G groups of C channels, each group one IR of
     L taps (tau 0.2 L) and a live [C][n] 48 kHz source at a random phase, block B. For each precision
     the group count G rises until the p99 block latency exceeds the deadline B/fs or more than 0.1 %

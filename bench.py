@@ -715,8 +715,10 @@ def bench_q15(torch, capi, reps: int = 6) -> dict:
 
 def bench_offline(torch, capi, reps: int = 3) -> dict:
     """One-shot tc_convolve on device buffers: a short sound through a long IR (the roles are swapped,
-    Sec. 3.2, and timed both ways) and a long signal through a 1 s IR. Beside it, as context only, an FFT
-    convolution of the same operands with torch.fft (cuFFT, FP32), the paper's comparison method."""
+    Sec. 3.2, and timed both ways) and a long signal through a 1 s IR; each also through
+    tc_convolve_noalloc and through tc_convolve_tc (tensor cores, BF16 split and BF16). Beside it, as
+    context only, an FFT convolution of the same operands with torch.fft (cuFFT, FP32), the paper's
+    comparison method."""
     out = {}
     cases = {"short_sound_long_ir": (4_800, 480_000), "long_signal_1s_ir": (2_880_000, 48_000)}
     saved = os.environ.get("TC_NO_ROLE_SWAP")
@@ -753,6 +755,17 @@ def bench_offline(torch, capi, reps: int = 3) -> dict:
                 r["caller_roles_ms"] = ms2
                 r["role_swap_speedup"] = ms2 / ms
                 r["orientations_rel_l2"] = float(torch.linalg.norm(y - y2) / torch.linalg.norm(y2))
+            # The same convolution with the products on the tensor cores (256-sample output rows as K2's
+            # channels), against the FP32 result.
+            peaks = load_peaks()
+            bf16_peak = float(peaks.get("bf16_tflops", 1690.8))
+            for pname, pcode, nprod in (("bf16split", capi.TC_BF16_SPLIT, 3), ("bf16", capi.TC_BF16, 1)):
+                yt = torch.empty_like(y)
+                ms_t = timed(lambda: capi.tc_convolve_tc(x, N, h, L, yt, pcode))
+                tfl = 2.0 * nprod * N * L / (ms_t / 1e3) / 1e12
+                r["tensor_" + pname] = {"ms": ms_t, "tap_macs_per_s": N * L / (ms_t / 1e3),
+                                        "rel_l2_vs_fp32": float(torch.linalg.norm(yt - y) / torch.linalg.norm(y)),
+                                        "tflops_counted": tfl, "frac_of_bf16_peak": tfl / bf16_peak}
             nfft = 1 << int(math.ceil(math.log2(N + L - 1)))
 
             def fft_conv():

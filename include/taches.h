@@ -229,8 +229,9 @@ tc_status tc_stream_import(tc_stream *s, const void *buf, size_t size);
  * cuda_stream (a cudaStream_t as void*; NULL = default stream) and waits
  * for it before returning. Its working memory (the input with zero margins,
  * about N + 6 L floats, and up to 256 MiB of split-sum partials) comes from
- * the stream-ordered allocator on cuda_stream and goes back to it before
- * return. Errors: TC_EINVAL (NULL or zero sizes, L > 2^30); TC_ENOMEM;
+ * the library's stream-ordered memory pool on cuda_stream and goes back to it
+ * before return; the pool keeps up to 2 GiB of freed memory mapped for the
+ * next calls. Errors: TC_EINVAL (NULL or zero sizes, L > 2^30); TC_ENOMEM;
  * TC_ECUDA; TC_ETIMEOUT. */
 tc_status tc_convolve(const float *x, size_t N, const float *h, size_t L, float *y, void *cuda_stream);
 
@@ -264,6 +265,25 @@ tc_status tc_convolve(const float *x, size_t N, const float *h, size_t L, float 
  * returning. Errors: TC_EINVAL (NULL, zero or too large sizes); TC_ECUDA;
  * TC_ETIMEOUT. */
 tc_status tc_convolve_noalloc(const float *x, size_t N, const float *h, size_t L, float *y, void *cuda_stream);
+
+/* ---------------------------------------------------------------------- */
+/* One signal on the tensor cores                                          */
+/* ---------------------------------------------------------------------- */
+
+/* y[0..N+L-2] = x[0..N-1] * h[0..L-1] (device pointers, FP32 in and out) with
+ * the products on the tcgen05 tensor cores: the output is cut into rows of
+ * 256 samples, and every row is a channel of the shared-IR contraction (K2),
+ * whose histories are overlapping windows of the one input. precision:
+ * TC_BF16 (BF16 operands, FP32 accumulation; about 2e-3 relative L2),
+ * TC_BF16_SPLIT (hi/lo BF16 split of both operands, three products; about
+ * 5e-6) or TC_FP32 (the same as tc_convolve). The shorter operand takes the
+ * IR role (Sec. 3.2) unless TC_NO_ROLE_SWAP=1. Working memory (the padded
+ * input in FP32 and BF16 hi/lo, the IR's Toeplitz tiles, the row-major
+ * output, K-part partials) comes from the library's stream-ordered pool. Runs on
+ * cuda_stream and waits for it. Errors: TC_EINVAL (NULL, zero sizes, unknown
+ * precision, L > 2^26); TC_ENOMEM; TC_ECUDA; TC_ETIMEOUT. */
+tc_status tc_convolve_tc(const float *x, size_t N, const float *h, size_t L, float *y, int precision,
+                         void *cuda_stream);
 
 /* ---------------------------------------------------------------------- */
 /* Exact fixed-point convolution with one requantization (Sec. 5.3.1)      */

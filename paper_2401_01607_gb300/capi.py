@@ -80,6 +80,7 @@ _SIGS = {
     "tc_convolve": [_vp, _sz, _vp, _sz, _vp, _vp],
     "tc_convolve_noalloc": [_vp, _sz, _vp, _sz, _vp, _vp],
     "tc_convolve_q15": [_vp, _sz, _vp, _sz, _vp, _vp, _vp],
+    "tc_convolve_tc": [_vp, _sz, _vp, _sz, _vp, _int, _vp],
     "tc_selftest_wait": [ctypes.c_ulonglong, _vp],
     "tc_stream_export": [_vp, _vp, _sz, ctypes.POINTER(_sz)],
     "tc_stream_import": [_vp, _vp, _sz],
@@ -306,6 +307,13 @@ def tc_convolve_noalloc(x, N: int, h, L: int, y, cuda_stream=None) -> None:
     cs = None if cuda_stream is None else (cuda_stream if isinstance(cuda_stream, int) else
                                            int(cuda_stream.cuda_stream))
     _call("tc_convolve_noalloc", _dev_ptr(x), N, _dev_ptr(h), L, _dev_ptr(y), cs)
+
+
+def tc_convolve_tc(x, N: int, h, L: int, y, precision: int = TC_BF16_SPLIT, cuda_stream=None) -> None:
+    """One signal through one IR with the products on the tensor cores (device float32 tensors)."""
+    cs = None if cuda_stream is None else (cuda_stream if isinstance(cuda_stream, int) else
+                                           int(cuda_stream.cuda_stream))
+    _call("tc_convolve_tc", _dev_ptr(x), N, _dev_ptr(h), L, _dev_ptr(y), int(precision), cs)
 
 
 def tc_convolve_q15(x, N: int, h, L: int, y, acc=None, cuda_stream=None) -> None:

@@ -1181,7 +1181,7 @@ tc_status tc_flush(tc_stream *s, float *y, size_t cap, size_t *n_out)
         return TC_OK;
     }
     float *d = nullptr;
-    TC_CU(cudaMallocAsync(reinterpret_cast<void **>(&d), s->items * tail * sizeof(float), s->cs));
+    TC_CU(tc::pool_alloc(reinterpret_cast<void **>(&d), s->items * tail * sizeof(float), s->cs));
     tc_status st = flush_to_device(s, d, (long long)tail);
     if (st == TC_OK) {
         cudaError_t e = cudaMemcpy2DAsync(y, cap * sizeof(float), d, tail * sizeof(float), tail * sizeof(float),

@@ -208,7 +208,7 @@ extern "C" tc_status tc_convolve_q15(const int16_t *x, size_t N, const int16_t *
     long long *a = reinterpret_cast<long long *>(acc);
     cudaError_t e = cudaSuccess;
     if (!a)
-        e = cudaMallocAsync(reinterpret_cast<void **>(&a), (size_t)ny * sizeof(long long), st);
+        e = tc::pool_alloc(reinterpret_cast<void **>(&a), (size_t)ny * sizeof(long long), st);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(a, 0, (size_t)ny * sizeof(long long), st);
     if (e == cudaSuccess) {

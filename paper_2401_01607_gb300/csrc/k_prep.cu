@@ -3,6 +3,7 @@
 // starts on a 16-byte boundary whatever the output alignment.
 #include <cstdlib>
 #include <atomic>
+#include <mutex>
 
 #include "tc_internal.h"
 
@@ -54,6 +55,44 @@ cudaError_t ir_prep_launch(const float *src, long long src_pitch, long long n, i
 
 void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
 uint64_t launches() { return g_launches.load(std::memory_order_relaxed); }
+
+// The library's stream-ordered memory pool on each device, for the scratch of
+// one-shot calls. It keeps up to 2 GiB of freed memory mapped, so that calls
+// in a row do not map and unmap their scratch each time (the device's default
+// pool returns freed memory at every synchronisation). Created on first use.
+namespace {
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[64] = {};
+}  // namespace
+
+cudaError_t pool_alloc(void **ptr, size_t bytes, cudaStream_t st)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    if (dev < 0 || dev >= 64)
+        return cudaErrorInvalidDevice;
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        if (!g_pools[dev]) {
+            cudaMemPoolProps props{};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            e = cudaMemPoolCreate(&g_pools[dev], &props);
+            if (e != cudaSuccess)
+                return e;
+            uint64_t keep = 2ull << 30;
+            e = cudaMemPoolSetAttribute(g_pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+            if (e != cudaSuccess)
+                return e;
+        }
+        pool = g_pools[dev];
+    }
+    return cudaMallocFromPoolAsync(ptr, bytes, pool, st);
+}
 
 bool no_role_swap()
 {

@@ -6,9 +6,10 @@
 //   [tickets][split-sum partials],
 // in as few launches as the partials allow. They differ only in where the
 // scratch comes from:
-//   - tc_convolve takes it from the stream-ordered allocator
-//     (cudaMallocAsync / cudaFreeAsync on the caller's stream), sized so that
-//     one launch covers the whole output;
+//   - tc_convolve takes it from the library's stream-ordered pool
+//     (allocated and freed in order on the caller's stream; the pool keeps
+//     freed memory for the next call), sized so that one launch covers the
+//     whole output;
 //   - tc_convolve_noalloc uses one fixed 32 MiB file-scope device array and
 //     never allocates. Who needs it: callers that cannot call cudaMalloc at
 //     the point of use (a real-time audio callback, where an allocation can
@@ -235,10 +236,10 @@ tc_status oneshot_alloc(const float *x, size_t N, const float *h, size_t L, floa
     const Layout full = layout(Nl, Ll, -1);
     cudaStream_t cs = (cudaStream_t)cuda_stream;
     float *scratch = nullptr;
-    e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), (size_t)full.total * sizeof(float), cs);
+    e = tc::pool_alloc(reinterpret_cast<void **>(&scratch), (size_t)full.total * sizeof(float), cs);
     if (e != cudaSuccess)
         return na_fail(e == cudaErrorMemoryAllocation ? TC_ENOMEM : TC_ECUDA,
-                       std::string("tc_convolve: cudaMallocAsync: ") + cudaGetErrorString(e));
+                       std::string("tc_convolve: pool allocation: ") + cudaGetErrorString(e));
     if ((reinterpret_cast<uintptr_t>(scratch) & 255u) != 0) {
         cudaFreeAsync(scratch, cs);
         return na_fail(TC_ECUDA, "tc_convolve: the stream-ordered allocation is not 256-byte aligned");
@@ -282,4 +283,141 @@ extern "C" tc_status tc_convolve_noalloc(const float *x, size_t N, const float *
     if (st != TC_OK)
         return st;
     return run_oneshot("tc_convolve_noalloc", x, N, h, L, y, (cudaStream_t)cuda_stream, P.scratch, kScratchFloats, P);
+}
+
+// ---------------------------------------------------------------------------
+// One signal on the tensor cores: the output reshaped into rows of 256
+// samples, each row a "channel" of the shared-IR contraction K2.
+//
+// With xs the input delayed by L - 1 (zeros before and after it), row r of the
+// output is y[256 r + i] = sum_j T[i][j] xs[256 r + j], i < 256, j < 32 nkb,
+// T[i][j] = h[L - 1 + i - j]: exactly K2's product for a group whose channel
+// r has the history xs[256 r + .]. Those histories overlap, so K2's X tensor
+// map is one strided view of xs: row stride 256 samples (512 bytes), row
+// length 32 nkb. The Toeplitz tiles of h are built once per call.
+// ---------------------------------------------------------------------------
+extern "C" tc_status tc_convolve_tc(const float *x, size_t N, const float *h, size_t L, float *y, int precision,
+                                    void *cuda_stream)
+{
+    if (!x || !h || !y)
+        return na_fail(TC_EINVAL, "tc_convolve_tc: x, h or y is NULL");
+    if (N == 0 || L == 0)
+        return na_fail(TC_EINVAL, "tc_convolve_tc: N and L must be > 0");
+    if (precision == TC_FP32)
+        return tc::oneshot_alloc(x, N, h, L, y, cuda_stream);
+    if (precision != TC_BF16 && precision != TC_BF16_SPLIT)
+        return na_fail(TC_EINVAL, "tc_convolve_tc: unknown precision");
+    tc::Range nvtx_range("tc_convolve_tc");
+    if (N < L && !tc::no_role_swap()) {  // Sec. 3.2: the shorter operand is the IR
+        std::swap(x, h);
+        std::swap(N, L);
+    }
+    if (L > ((size_t)1 << 26) || N > ((size_t)1 << 34))
+        return na_fail(TC_EINVAL, "tc_convolve_tc: L must be <= 2^26 and N <= 2^34");
+    const int TM = tc::k2_tile_m(), TN = tc::k2_tile_n(), KB = tc::k2_kblock();
+    const long long Ll = (long long)L, Nl = (long long)N;
+    const long long ny = Nl + Ll - 1;
+    const long long R = (ny + TN - 1) / TN;              // output rows of 256 samples
+    const long long nkb = tc::k2_nkb(Ll, 0);             // K blocks per row window
+    const long long off = Ll - 1;                        // xs[m] = x[m - off]
+    const long long npad = ru((R - 1) * TN + nkb * KB + 64, 64);
+    if (R > (1LL << 24))
+        return na_fail(TC_EINVAL, "tc_convolve_tc: output too long");
+    const int nprod = precision == TC_BF16 ? 1 : 3;
+    cudaStream_t cs = (cudaStream_t)cuda_stream;
+
+    // Scratch: padded fp32 input, its bf16 hi/lo, Toeplitz tiles hi/lo, the
+    // row-major output and the K-part partials.
+    const long long ntile_c1 = (R + TM - 1) / TM;
+    bool pair = precision == TC_BF16;
+    tc::K2Params p{};
+    p.C = (int)R;
+    p.nout = TN;
+    p.ntile_o = 1;
+    p.x_col0 = 0;
+    p.nkb = (int)nkb;
+    p.range = precision == TC_BF16_SPLIT ? 16 : 4096;
+    p.ntile_c = (int)(pair ? (ntile_c1 + 1) / 2 : ntile_c1);
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long nsplit = 1;
+    double best = 0.0;
+    for (long long ns = 1; ns <= 64 && ns <= nkb && (ns == 1 || nkb / ns >= 16); ++ns) {
+        const long long units = (long long)p.ntile_c * ns;
+        const double eff = (double)units / (double)(((units + sms - 1) / sms) * sms);
+        if (eff > best + 1e-9) {
+            best = eff;
+            nsplit = ns;
+        }
+        if (eff >= 0.9)
+            break;
+    }
+    const long long kb_per = (nkb + nsplit - 1) / nsplit;
+    nsplit = (nkb + kb_per - 1) / kb_per;
+    p.nsplit = (int)nsplit;
+    p.kb_per = (int)kb_per;
+    if (pair && p.range < p.kb_per) {
+        pair = false;
+        p.ntile_c = (int)ntile_c1;
+    }
+    const size_t b_xs = (size_t)npad * 4, b_xb = (size_t)npad * 2, b_t = (size_t)nkb * TN * KB * 2;
+    const size_t b_y = (size_t)R * TN * 4;
+    const size_t b_part = nsplit > 1 ? (size_t)2 * ((ntile_c1 + 1) / 2) * nsplit * TM * TN * 4 : 0;
+    const size_t o_xs = 0, o_hi = o_xs + ru(b_xs, 256), o_lo = o_hi + ru(b_xb, 256), o_th = o_lo + ru(b_xb, 256);
+    const size_t o_tl = o_th + ru(b_t, 256), o_y = o_tl + ru(b_t, 256), o_part = o_y + ru(b_y, 256);
+    const size_t o_err = o_part + ru(b_part, 256), total = o_err + 256;
+    char *mem = nullptr;
+    cudaError_t e = tc::pool_alloc(reinterpret_cast<void **>(&mem), total, cs);
+    if (e != cudaSuccess)
+        return na_fail(e == cudaErrorMemoryAllocation ? TC_ENOMEM : TC_ECUDA,
+                       std::string("tc_convolve_tc: pool allocation: ") + cudaGetErrorString(e));
+    if ((reinterpret_cast<uintptr_t>(mem) & 255u) != 0) {
+        cudaFreeAsync(mem, cs);
+        return na_fail(TC_ECUDA, "tc_convolve_tc: the stream-ordered allocation is not 256-byte aligned");
+    }
+    float *xs = reinterpret_cast<float *>(mem + o_xs);
+    void *xhi = mem + o_hi, *xlo = mem + o_lo, *thi = mem + o_th, *tlo = mem + o_tl;
+    float *ytmp = reinterpret_cast<float *>(mem + o_y);
+    int *err = reinterpret_cast<int *>(mem + o_err);
+    p.y = ytmp;
+    p.y_pitch = TN;
+    p.partial = nsplit > 1 ? reinterpret_cast<float *>(mem + o_part) : nullptr;
+    p.err = err;
+    CUtensorMap mx_hi{}, mx_lo{}, mt_hi{}, mt_lo{};
+    int herr = 0;
+    // Rows of the X view overlap: row r starts 256 samples after row r - 1.
+    e = tc::encode_bf16_2d(&mx_hi, xhi, (unsigned long long)nkb * KB, (unsigned long long)R, (unsigned long long)TN * 2,
+                           KB, TM);
+    if (e == cudaSuccess)
+        e = tc::encode_bf16_2d(&mx_lo, xlo, (unsigned long long)nkb * KB, (unsigned long long)R,
+                               (unsigned long long)TN * 2, KB, TM);
+    if (e == cudaSuccess)
+        e = tc::encode_bf16_2d(&mt_hi, thi, KB, (unsigned long long)nkb * TN, KB * 2, KB, TN);
+    if (e == cudaSuccess)
+        e = tc::encode_bf16_2d(&mt_lo, tlo, KB, (unsigned long long)nkb * TN, KB * 2, KB, TN);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(err, 0, sizeof(int), cs);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(xs, 0, b_xs, cs);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(xs + off, x, (size_t)Nl * 4, cudaMemcpyDeviceToDevice, cs);
+    if (e == cudaSuccess)
+        e = tc::k2_split_launch(xs, npad, 1, 0, npad, xhi, xlo, cs);
+    if (e == cudaSuccess)
+        e = tc::k2_tprep_launch(h, (int)Ll, 0, (int)nkb, thi, tlo, cs);
+    if (e == cudaSuccess)
+        e = pair ? tc::k2_launch_pair(mx_hi, mt_hi, p, cs) : tc::k2_launch(mx_hi, mx_lo, mt_hi, mt_lo, p, nprod, cs);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(y, ytmp, (size_t)ny * 4, cudaMemcpyDeviceToDevice, cs);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, cs);
+    cudaFreeAsync(mem, cs);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess)
+        return na_fail(TC_ECUDA, std::string("tc_convolve_tc: ") + cudaGetErrorString(e));
+    if (herr)
+        return na_fail(TC_ETIMEOUT, "tc_convolve_tc: a kernel's bounded wait gave up");
+    return TC_OK;
 }

@@ -215,6 +215,10 @@ void count_launch(int n = 1);
 // caller's roles (for comparison timings); read at each call.
 bool no_role_swap();
 
+// Stream-ordered allocation from the library's pool on the current device
+// (keeps freed memory for the next call); free with cudaFreeAsync.
+cudaError_t pool_alloc(void **ptr, size_t bytes, cudaStream_t st);
+
 // tc_convolve: the one-shot convolution with scratch from the stream-ordered
 // allocator (defined beside tc_convolve_noalloc, which shares its code).
 tc_status oneshot_alloc(const float *x, size_t N, const float *h, size_t L, float *y, void *cuda_stream);

@@ -118,3 +118,21 @@ def test_short_ir_one_k_part_odd_pitch(prec):
     y, info = run_group(X, H, [0], L, B, prec, 1024)
     assert info.tensor_launches > 0 and info.fp32_fallbacks == 0
     check(y, X, H, [0], B, prec, rows=[0, 1, 2, 3, 65, 127, 128, 129])
+
+
+@pytest.mark.parametrize("prec", ["bf16split", "bf16"])
+@pytest.mark.parametrize("N,L", [(100_000, 3_000), (2_000, 70_000), (1, 1), (300, 257), (40_000, 40_000)])
+def test_single_signal_on_the_tensor_cores(prec, N, L):
+    """tc_convolve_tc: one signal, the output cut into 256-sample rows that run as K2's channels (overlapping
+    windows of one input); role swap when N < L; ragged rows and tiles."""
+    torch = pytest.importorskip("torch")
+    x = synth.audio(N, 900 + N)
+    h = synth.decayed_ir(L, max(1.0, 0.2 * L), 901 + L)
+    y = torch.full((N + L - 1,), float("nan"), device="cuda")
+    capi.tc_convolve_tc(torch.from_numpy(x).cuda(), N, torch.from_numpy(h).cuda(), L, y, PREC[prec])
+    ref = oracle.buffer(x, h[None], None, 4096) if N >= L else oracle.buffer(h, x[None], None, 4096)
+    got = y.cpu().numpy()
+    assert np.all(np.isfinite(got))
+    err = rel_l2(got, ref)
+    print(f"{prec} N={N} L={L}: rel_l2={err:.3g}")
+    assert err <= TOL[prec]

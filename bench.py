@@ -816,6 +816,15 @@ def _lat_summary(lat: np.ndarray, blk: np.ndarray) -> dict:
     return out
 
 
+def _k1_roofline(st0, st1) -> dict:
+    """The serving steps' K1 work-list launches between two stats snapshots: useful FLOP over their
+    CUDA-event time, against the FP32 FMA peak."""
+    ms = st1.k1_ms - st0.k1_ms
+    macs = st1.k1_macs - st0.k1_macs
+    tfl = 2.0 * macs / (ms / 1e3) / 1e12 if ms > 0 else 0.0
+    return {"launch_ms": ms, "tflops": tfl, "frac_of_fp32_peak": tfl / fp32_peak_tflops(SM_MAX_MHZ)}
+
+
 def bench_capacity(torch, capi, H64: np.ndarray, pool: np.ndarray, paced_s: float = 2.0) -> dict:
     """Concurrent real-time streams of the 64-stream recipe (L = 48000, block 128,
     own IRs) that one GB300 serves, batched (tc_server) and with one plain
@@ -940,7 +949,8 @@ def bench_capacity(torch, capi, H64: np.ndarray, pool: np.ndarray, paced_s: floa
             wall = max(capi.tc_server_clock() - t_rec, 1e-9)
             r = dict(_lat_summary(lat, blk), streams=M, seconds_of_audio=paced_s, warmup_s=warm,
                      steps=int(steps), blocks_per_step=(st1.blocks - st0.blocks) / max(steps, 1),
-                     served_tap_macs_per_s=(st1.tap_macs - st0.tap_macs) / wall)
+                     served_tap_macs_per_s=(st1.tap_macs - st0.tap_macs) / wall,
+                     k1=_k1_roofline(st0, st1))
             r["pass"] = bool(r.get("blocks", 0) > 0 and r["p99_ms"] <= period * 1e3
                              and r["deadline_miss_frac"] <= 1e-3)
             paced.last = r
@@ -1087,6 +1097,7 @@ def bench_trace(capi, pool: np.ndarray, seconds: float, budget_gb: float = 96.0)
         capi.tc_server_stop(srv)
         diag_clk = clocks.stop()
         st = capi.tc_server_get_stats(srv)
+        k1 = _k1_roofline(capi.TcServerStats(), st)
         lat, blk = capi.tc_server_latencies(srv)
         steplog = capi.tc_server_step_log(srv)
     finally:
@@ -1114,7 +1125,7 @@ def bench_trace(capi, pool: np.ndarray, seconds: float, budget_gb: float = 96.0)
     return dict(_lat_summary(lat, blk), seconds=seconds, streams_arrived=arrived, max_active=max_active,
                 served_tap_macs_per_s=st.tap_macs / seconds, steps=int(st.steps),
                 blocks_per_step=st.blocks / max(st.steps, 1), busy_frac=st.busy_s / seconds,
-                admission_waits=waits, mem_budget_gb=budget_gb, diagnostics=diag,
+                admission_waits=waits, mem_budget_gb=budget_gb, diagnostics=diag, k1=k1,
                 precision="fp32 (every stream has its own IR: no shared-IR batch for the tensor cores)",
                 inputs="live 48 kHz sources cut from a seeded audio pool; IRs cut from a seeded Gaussian pool")
 

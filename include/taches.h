@@ -373,6 +373,8 @@ typedef struct tc_server_stats {
     uint64_t tensor_launches;  /* group pushes that ran on the tensor cores (BF16 modes) */
     uint64_t fp32_fallbacks;   /* BF16-mode group pushes that ran on the FP32 gather because their
                                   window straddled an IR switch */
+    double k1_ms;        /* device time of the steps' K1 work-list launches (CUDA events, ms) */
+    double k1_macs;      /* tap-MACs those launches computed (inputs x L, flush tails included) */
 } tc_server_stats;
 
 /* Opens a server on the current CUDA device. mem_budget_bytes bounds the

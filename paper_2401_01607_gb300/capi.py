@@ -43,7 +43,8 @@ class TcServerStats(ctypes.Structure):
     _fields_ = [("streams", ctypes.c_size_t), ("mem_used", ctypes.c_size_t), ("mem_budget", ctypes.c_size_t),
                 ("steps", ctypes.c_uint64), ("blocks", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
                 ("busy_s", ctypes.c_double), ("tap_macs", ctypes.c_double),
-                ("tensor_launches", ctypes.c_uint64), ("fp32_fallbacks", ctypes.c_uint64)]
+                ("tensor_launches", ctypes.c_uint64), ("fp32_fallbacks", ctypes.c_uint64),
+                ("k1_ms", ctypes.c_double), ("k1_macs", ctypes.c_double)]
 
 
 class TcServerStepRec(ctypes.Structure):

@@ -172,6 +172,7 @@ struct tc_server {
         cudaEvent_t k1_start = nullptr, k1_stop = nullptr;  // timing of the gather (autotuner)
         int tune_key = -1;
         double tune_work = 0.0;
+        double k1_work = 0.0;  // tap-MACs of the step's K1 work list (0: no K1 launch)
     } buf[2];
 
     // Autotuner of the gather's chunk variant: per step class (magnitude of
@@ -229,6 +230,7 @@ struct tc_server {
     double busy_s = 0.0;
     double tap_macs = 0.0;
     uint64_t tensor_launches = 0, fp32_fallbacks = 0;  // group pushes (state mutex)
+    double k1_ms = 0.0, k1_macs = 0.0;                  // K1 work-list launches: event time, tap-MACs
 };
 
 namespace {
@@ -717,6 +719,9 @@ tc_status pack_launch(tc_server *srv, tc_server::StepBuf &b)
         b.tune_work = work;
     }
     const long long kc = tc::k1_chunk_taps(variant);
+    b.k1_work = 0.0;
+    for (size_t i : plain)
+        b.k1_work += (double)b.items[i].n * (double)b.items[i].s->L;
     size_t scratch = 0, ctrs = 0;
     for (size_t i : plain) {
         const tc_server::Item &w = b.items[i];
@@ -894,6 +899,13 @@ tc_status complete(tc_server *srv, tc_server::StepBuf &b)
             w.s->inflight--;
         b.items.clear();
         return sfail(TC_ETIMEOUT, "tc_server: a kernel's bounded wait gave up");
+    }
+    if (b.k1_work > 0.0) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, b.k1_start, b.k1_stop) == cudaSuccess && ms > 0.f) {
+            srv->k1_ms += ms;
+            srv->k1_macs += b.k1_work;
+        }
     }
     if (b.tune_key >= 0 && b.tune_work > 0.0) {
         float ms = 0.f;
@@ -1535,6 +1547,8 @@ tc_status tc_server_get_stats(tc_server *srv, tc_server_stats *st)
     st->busy_s = srv->busy_s;
     st->tap_macs = srv->tap_macs;
     st->tensor_launches = srv->tensor_launches;
+    st->k1_ms = srv->k1_ms;
+    st->k1_macs = srv->k1_macs;
     st->fp32_fallbacks = srv->fp32_fallbacks;
     return TC_OK;
 }

@@ -1422,26 +1422,33 @@ def main():
     runner.close()
     del runner
     torch.cuda.empty_cache()
+    def guarded(fn):
+        """Runs a side section; its failure is reported in its own entry and does not lose the main line."""
+        try:
+            return fn()
+        except Exception as e:  # noqa: BLE001
+            return {"error": f"{type(e).__name__}: {e}"[:500]}
+
     shared = None
     if not args.no_shared and dist.world == 1:
-        shared = bench_shared(torch, steps=2, warmup=1)
+        shared = guarded(lambda: bench_shared(torch, steps=2, warmup=1))
         if cpu_other:
             shared["cpu_baseline"] = cpu_other["shared_ir"]
     mimo = mono = None
     if not args.no_mimo and dist.world == 1:
-        mimo = bench_mimo(torch)
-        mono = bench_mono(capi)
-        mono["offline"] = bench_offline(torch, capi)
+        mimo = guarded(lambda: bench_mimo(torch))
+        mono = guarded(lambda: bench_mono(capi))
+        mono["offline"] = guarded(lambda: bench_offline(torch, capi))
         if cpu_other:
             mimo["cpu_baseline"], mono["cpu_baseline"] = cpu_other["mimo"], cpu_other["mono"]
     q15 = None
     if not args.no_q15 and dist.world == 1:
-        q15 = bench_q15(torch, capi)
+        q15 = guarded(lambda: bench_q15(torch, capi))
         if cpu_other:
             q15["cpu_baseline"] = cpu_other["q15"]
     serving = None
     if not args.no_serving and dist.world == 1:
-        serving = bench_serving(torch, capi, np.ascontiguousarray(w.H[:, 0]), args.trace_seconds)
+        serving = guarded(lambda: bench_serving(torch, capi, np.ascontiguousarray(w.H[:, 0]), args.trace_seconds))
     if dist.rank == 0:
         per_stream_rt = FS * L_TAPS  # tap-MAC/s one real-time stream needs
         line = {"metric": METRIC, "value": value, "unit": "tap-MAC/s", "n_gpus": dist.world,

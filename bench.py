@@ -1010,8 +1010,12 @@ def bench_groups(capi, paced_s: float = 1.5, C: int = 128, L: int = 96_000, B: i
         for G in ladder:
             srv = capi.tc_server_open(240 << 30, 1 << 22)
             try:
-                ids = [capi.tc_server_add_group(srv, C, L, B, irs[g], code, capi.TC_SERVER_DISCARD_OUTPUT)
-                       for g in range(G)]
+                try:
+                    ids = [capi.tc_server_add_group(srv, C, L, B, irs[g], code, capi.TC_SERVER_DISCARD_OUTPUT)
+                           for g in range(G)]
+                except capi.TcError as e:  # no room for G groups: the ladder ends here
+                    runs[str(G)] = {"groups": G, "pass": False, "admission": str(e)[:200]}
+                    break
                 rng = np.random.default_rng(G)
                 t_start = capi.tc_server_clock() + 0.05
                 capi.tc_server_start(srv)

@@ -181,9 +181,17 @@ tc_status tc_set_ir_rows(tc_stream *s, const float *h, size_t n, uint64_t sample
 tc_status tc_push_block(tc_stream *s, const float *x, size_t n, float *y);
 
 /* As tc_push_block, for n <= max_push samples. n should be a multiple of
- * block; otherwise this is the last push. on_device = 1: x and y are device
- * pointers, and the call enqueues the work on the stream's CUDA stream and
- * returns without waiting (check with tc_sync). */
+ * block; otherwise this is the last push. on_device:
+ *   0 (TC_PUSH_HOST): host buffers, synchronous;
+ *   1 (TC_PUSH_DEVICE): device pointers; the call enqueues the work on the
+ *     stream's CUDA stream and returns without waiting (check with tc_sync);
+ *   2 (TC_PUSH_PINNED_ASYNC): page-locked host buffers (TC_EINVAL otherwise);
+ *     the call enqueues the copy of x to the device, the kernels and the copy
+ *     of y back, and returns. The copies run on a second CUDA stream of the
+ *     library through two device staging slots, so they overlap the kernels
+ *     of the neighbouring pushes. x may be reused, and y read, after tc_sync
+ *     or tc_flush. */
+enum { TC_PUSH_HOST = 0, TC_PUSH_DEVICE = 1, TC_PUSH_PINNED_ASYNC = 2 };
 tc_status tc_push(tc_stream *s, const float *x, size_t n, float *y, int on_device);
 
 /* Temporal overflow (Sec. 4.1): the last L-1 output samples per output row,

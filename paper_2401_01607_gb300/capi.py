@@ -252,13 +252,19 @@ def tc_push_block(s: int, x, y) -> None:
     _call("tc_push_block", s, px, n, py)
 
 
-def tc_push(s: int, x, n: int, y, on_device: bool = False) -> None:
-    if on_device:
+TC_PUSH_HOST, TC_PUSH_DEVICE, TC_PUSH_PINNED_ASYNC = 0, 1, 2
+
+
+def tc_push(s: int, x, n: int, y, on_device: int = TC_PUSH_HOST) -> None:
+    """on_device: TC_PUSH_HOST (numpy buffers, synchronous), TC_PUSH_DEVICE (device tensors or addresses,
+    enqueued) or TC_PUSH_PINNED_ASYNC (page-locked numpy buffers, enqueued; complete after tc_sync)."""
+    mode = int(on_device)
+    if mode == TC_PUSH_DEVICE:
         _call("tc_push", s, _dev_ptr(x), n, _dev_ptr(y), 1)
     else:
         x, px = _host_f32(x)
         y, py = _host_f32(y, writable=True)
-        _call("tc_push", s, px, n, py, 0)
+        _call("tc_push", s, px, n, py, mode)
 
 
 def tc_flush(s: int, y, cap: int) -> int:

@@ -142,6 +142,18 @@ struct tc_stream {
     cudaEvent_t ev_x = nullptr;
     int *pin_err = nullptr;
 
+    // Asynchronous pushes from page-locked host buffers (tc_push mode 2): a
+    // copy stream moves the inputs into two device staging slots and the
+    // outputs back, so the copies of one push overlap the kernels of its
+    // neighbours. Created on the first such push.
+    cudaStream_t ccs = nullptr;
+    cudaStream_t ics = nullptr;         // page-locked IR uploads beside the asynchronous pushes
+    cudaEvent_t ev_ir_prep = nullptr;   // the last IR prep (last reader of the IR staging rows) ran
+    float *d_xs[2] = {nullptr, nullptr};
+    float *d_ys[2] = {nullptr, nullptr};
+    cudaEvent_t ev_xs_ready[2] = {}, ev_xs_free[2] = {}, ev_ys_ready[2] = {}, ev_ys_free[2] = {};
+    int aslot = 0;
+
     // K1 scratch: chunk sums of every tile and one ticket per tile.
     float *partial = nullptr;
     size_t partial_floats = 0;
@@ -211,6 +223,27 @@ tc_status use_device(const tc_stream *s)
 
 void free_all(tc_stream *s)
 {
+    if (s->ccs) {
+        cudaStreamSynchronize(s->ccs);
+        for (int k = 0; k < 2; ++k) {
+            cudaFree(s->d_xs[k]);
+            cudaFree(s->d_ys[k]);
+            for (cudaEvent_t e : {s->ev_xs_ready[k], s->ev_xs_free[k], s->ev_ys_ready[k], s->ev_ys_free[k]})
+                if (e)
+                    cudaEventDestroy(e);
+        }
+        cudaStreamDestroy(s->ccs);
+        s->ccs = nullptr;
+    }
+    if (s->ics) {
+        cudaStreamSynchronize(s->ics);
+        cudaStreamDestroy(s->ics);
+        s->ics = nullptr;
+    }
+    if (s->ev_ir_prep) {
+        cudaEventDestroy(s->ev_ir_prep);
+        s->ev_ir_prep = nullptr;
+    }
     if (s->cs)
         cudaStreamSynchronize(s->cs);
     cudaFree(s->hist);
@@ -504,9 +537,20 @@ tc_status set_ir_impl(tc_stream *s, const float *h, size_t n, long long sample, 
         // Page-locked h: one copy straight into the staging rows, waited for so
         // that h is free when the call returns.
         const size_t cnt = (rows_given ? sets : 1) * n * sizeof(float);
-        TC_CU(cudaMemcpyAsync(s->ir_stage, h, cnt, cudaMemcpyHostToDevice, s->cs));
-        TC_CU(cudaEventRecord(s->ev_ir, s->cs));
-        TC_CU(cudaEventSynchronize(s->ev_ir));
+        if (s->ics) {
+            // Beside asynchronous pushes: the copy waits only for the previous
+            // IR's prep (the last reader of the staging rows), not for the
+            // pushes enqueued since, and the prep waits for the copy.
+            TC_CU(cudaStreamWaitEvent(s->ics, s->ev_ir_prep, 0));
+            TC_CU(cudaMemcpyAsync(s->ir_stage, h, cnt, cudaMemcpyHostToDevice, s->ics));
+            TC_CU(cudaEventRecord(s->ev_ir, s->ics));
+            TC_CU(cudaEventSynchronize(s->ev_ir));
+            TC_CU(cudaStreamWaitEvent(s->cs, s->ev_ir, 0));
+        } else {
+            TC_CU(cudaMemcpyAsync(s->ir_stage, h, cnt, cudaMemcpyHostToDevice, s->cs));
+            TC_CU(cudaEventRecord(s->ev_ir, s->cs));
+            TC_CU(cudaEventSynchronize(s->ev_ir));
+        }
         if (!rows_given)
             src_pitch = 0;
         src = s->ir_stage;
@@ -530,6 +574,8 @@ tc_status set_ir_impl(tc_stream *s, const float *h, size_t n, long long sample, 
         s->k3sets[(size_t)slot].ready = false;
     float *dst = s->ir + (size_t)slot * sets * 4 * (size_t)s->Lpad;
     TC_CU(tc::ir_prep_launch(src, src_pitch, (long long)n, (int)sets, dst, 4 * s->Lpad, s->Lpad, s->Lpad, s->cs));
+    if (s->ev_ir_prep)
+        TC_CU(cudaEventRecord(s->ev_ir_prep, s->cs));
 
     if (!replace) {
         s->vt.push_back(Version{sample, slot, s->vt.empty() ? 1 : s->next_ramp});
@@ -908,7 +954,28 @@ tc_status check_err_word(tc_stream *s)
     return TC_OK;
 }
 
-tc_status push_impl(tc_stream *s, const float *x, size_t n, float *y, bool on_device, size_t limit)
+tc_status async_init(tc_stream *s)
+{
+    if (s->ccs)
+        return TC_OK;
+    TC_CU(cudaStreamCreateWithFlags(&s->ccs, cudaStreamNonBlocking));
+    TC_CU(cudaStreamCreateWithFlags(&s->ics, cudaStreamNonBlocking));
+    TC_CU(cudaEventCreateWithFlags(&s->ev_ir_prep, cudaEventDisableTiming));
+    TC_CU(cudaEventRecord(s->ev_ir_prep, s->cs));  // every IR prep enqueued so far
+    for (int k = 0; k < 2; ++k) {
+        TC_CU(cudaMalloc(&s->d_xs[k], s->rows * s->max_push * sizeof(float)));
+        TC_CU(cudaMalloc(&s->d_ys[k], s->items * s->max_push * sizeof(float)));
+        for (cudaEvent_t *e : {&s->ev_xs_ready[k], &s->ev_xs_free[k], &s->ev_ys_ready[k], &s->ev_ys_free[k]})
+            TC_CU(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    }
+    return TC_OK;
+}
+
+// mode: PUSH_HOST (synchronous, host buffers), PUSH_DEVICE (device pointers,
+// enqueued), PUSH_PINNED_ASYNC (page-locked host buffers, enqueued).
+enum { PUSH_HOST = 0, PUSH_DEVICE = 1, PUSH_PINNED_ASYNC = 2 };
+
+tc_status push_impl(tc_stream *s, const float *x, size_t n, float *y, int mode, size_t limit)
 {
     tc::Range nvtx_range("tc push");
     TC_TRY(check_stream(s));
@@ -927,7 +994,24 @@ tc_status push_impl(tc_stream *s, const float *x, size_t n, float *y, bool on_de
     float *hist_at = s->hist + (s->pos - s->base);
     const size_t pitch_b = (size_t)s->cap * sizeof(float);
     const size_t row_b = n * sizeof(float);
-    if (on_device) {
+    const bool on_device = mode == PUSH_DEVICE;
+    int k = 0;
+    if (mode == PUSH_PINNED_ASYNC) {
+        if (!pinned_host(x) || !pinned_host(y))
+            return fail(TC_EINVAL, "asynchronous pushes take page-locked host buffers for x and y");
+        TC_TRY(async_init(s));
+        k = s->aslot;
+        s->aslot ^= 1;
+        // Input: into staging slot k on the copy stream, once the slot's last
+        // contents are in the history; then into the history on the stream.
+        TC_CU(cudaStreamWaitEvent(s->ccs, s->ev_xs_free[k], 0));
+        TC_CU(cudaMemcpyAsync(s->d_xs[k], x, s->rows * row_b, cudaMemcpyHostToDevice, s->ccs));
+        TC_CU(cudaEventRecord(s->ev_xs_ready[k], s->ccs));
+        TC_CU(cudaStreamWaitEvent(s->cs, s->ev_xs_ready[k], 0));
+        TC_CU(cudaMemcpy2DAsync(hist_at, pitch_b, s->d_xs[k], row_b, row_b, s->rows, cudaMemcpyDeviceToDevice,
+                                s->cs));
+        TC_CU(cudaEventRecord(s->ev_xs_free[k], s->cs));
+    } else if (on_device) {
         TC_CU(cudaMemcpy2DAsync(hist_at, pitch_b, x, row_b, row_b, s->rows, cudaMemcpyDeviceToDevice, s->cs));
     } else if (pinned_host(x)) {
         TC_CU(cudaMemcpy2DAsync(hist_at, pitch_b, x, row_b, row_b, s->rows, cudaMemcpyHostToDevice, s->cs));
@@ -940,11 +1024,21 @@ tc_status push_impl(tc_stream *s, const float *x, size_t n, float *y, bool on_de
     TC_TRY(split_new(s, s->pos - s->base, (long long)n));
     TC_TRY(upload_table(s));
     float *ydst = on_device ? y : s->d_y;
+    if (mode == PUSH_PINNED_ASYNC) {
+        TC_CU(cudaStreamWaitEvent(s->cs, s->ev_ys_free[k], 0));  // slot k's last output is on the host
+        ydst = s->d_ys[k];
+    }
     TC_TRY(launch_conv(s, s->pos, (long long)n, ydst, (long long)n));
     s->pos += (long long)n;
     if (n % s->block != 0)
         s->state = ST_ENDED;
-    if (!on_device) {
+    if (mode == PUSH_PINNED_ASYNC) {
+        // Output: back to y on the copy stream once the kernels are done.
+        TC_CU(cudaEventRecord(s->ev_ys_ready[k], s->cs));
+        TC_CU(cudaStreamWaitEvent(s->ccs, s->ev_ys_ready[k], 0));
+        TC_CU(cudaMemcpyAsync(y, s->d_ys[k], s->items * row_b, cudaMemcpyDeviceToHost, s->ccs));
+        TC_CU(cudaEventRecord(s->ev_ys_free[k], s->ccs));
+    } else if (!on_device) {
         const bool direct = pinned_host(y);
         TC_CU(cudaMemcpyAsync(direct ? y : s->pin_y, s->d_y, s->items * row_b, cudaMemcpyDeviceToHost, s->cs));
         TC_CU(cudaMemcpyAsync(s->pin_err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->cs));
@@ -1021,7 +1115,7 @@ tc_status group_open(size_t channels, size_t L, size_t max_push, int precision, 
 
 tc_status group_push(tc_stream *s, const float *x, size_t n, float *y)
 {
-    return push_impl(s, x, n, y, true, s->max_push);
+    return push_impl(s, x, n, y, PUSH_DEVICE, s->max_push);
 }
 
 int *group_err(tc_stream *s) { return s->d_err; }
@@ -1155,14 +1249,16 @@ tc_status tc_push_block(tc_stream *s, const float *x, size_t n, float *y)
 {
     if (!s)
         return fail(TC_EINVAL, "stream is NULL");
-    return push_impl(s, x, n, y, false, s->block);
+    return push_impl(s, x, n, y, PUSH_HOST, s->block);
 }
 
 tc_status tc_push(tc_stream *s, const float *x, size_t n, float *y, int on_device)
 {
     if (!s)
         return fail(TC_EINVAL, "stream is NULL");
-    return push_impl(s, x, n, y, on_device != 0, s->max_push);
+    if (on_device < 0 || on_device > 2)
+        return fail(TC_EINVAL, "on_device must be 0 (host), 1 (device) or 2 (page-locked host, asynchronous)");
+    return push_impl(s, x, n, y, on_device, s->max_push);
 }
 
 tc_status tc_flush(tc_stream *s, float *y, size_t cap, size_t *n_out)
@@ -1195,6 +1291,8 @@ tc_status tc_flush(tc_stream *s, float *y, size_t cap, size_t *n_out)
         else
             st = check_err_word(s);
     }
+    if (st == TC_OK && s->ccs && cudaStreamSynchronize(s->ccs) != cudaSuccess)
+        st = fail(TC_ECUDA, "flush: copy stream");  // outputs of asynchronous pushes are on the host
     cudaFreeAsync(d, s->cs);
     return st;
 }
@@ -1221,6 +1319,8 @@ tc_status tc_sync(tc_stream *s)
     TC_TRY(use_device(s));
     TC_CU(cudaMemcpyAsync(s->pin_err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->cs));
     TC_CU(cudaStreamSynchronize(s->cs));
+    if (s->ccs)
+        TC_CU(cudaStreamSynchronize(s->ccs));  // outputs of asynchronous pushes are on the host
     return check_err_word(s);
 }
 

@@ -172,6 +172,54 @@ def test_pinned_host_buffers_match_pageable():
     assert rel_l2(a, ref) <= TOL["fp32"]
 
 
+def test_async_pinned_pushes_match_synchronous():
+    """TC_PUSH_PINNED_ASYNC: pushes enqueue their copies on a second stream through two staging slots; with
+    IR switches uploaded from page-locked rows in between, the outputs (complete after the flush) equal the
+    synchronous pushes' bit for bit. Pageable buffers are refused."""
+    torch = pytest.importorskip("torch")
+    N, L, B, C, P = 6000, 3000, 128, 4, 512
+    x = synth.audio_block(C, N, 79)
+    H = np.stack([[synth.decayed_ir(L, 900.0, 500 + 10 * v + c) for c in range(C)] for v in range(3)])
+    vstart = [0, 1500, 3300]
+
+    def pin(a):
+        return torch.from_numpy(np.ascontiguousarray(a, np.float32)).pin_memory().numpy()
+
+    def run(mode):
+        s = capi.tc_open_group(C, L, B, False, capi.TC_FP32, P)
+        outs = []
+        try:
+            capi.tc_set_ir_rows(s, pin(H[0]), L, 0)
+            v = 1
+            for pos in range(0, N, P):
+                n = min(P, N - pos)
+                while v < len(vstart) and vstart[v] < pos + n:
+                    capi.tc_set_ir_rows(s, pin(H[v]), L, vstart[v])
+                    v += 1
+                yb = pin(np.zeros((C, n), np.float32))
+                capi.tc_push(s, pin(x[:, pos:pos + n]), n, yb, mode)
+                outs.append(yb)
+            tail = pin(np.empty((C, L - 1), np.float32))
+            capi.tc_flush(s, tail, L - 1)
+            outs.append(tail)
+        finally:
+            capi.tc_close(s)
+        return np.concatenate(outs, axis=1)
+
+    a, b = run(capi.TC_PUSH_PINNED_ASYNC), run(capi.TC_PUSH_HOST)
+    assert np.array_equal(a, b)
+    ref = np.stack([oracle.buffer(x[c], H[:, c], np.asarray(vstart, np.int64), B) for c in range(C)])
+    assert rel_l2(a, ref) <= TOL["fp32"]
+    s = capi.tc_open_group(C, L, B, False, capi.TC_FP32, P)
+    try:
+        capi.tc_set_ir_rows(s, H[0], L, 0)
+        with pytest.raises(capi.TcError) as e:
+            capi.tc_push(s, np.zeros((C, P), np.float32), P, np.zeros((C, P), np.float32), capi.TC_PUSH_PINNED_ASYNC)
+        assert e.value.code == "TC_EINVAL"
+    finally:
+        capi.tc_close(s)
+
+
 def test_convolve_one_shot():
     torch = pytest.importorskip("torch")
     N, L = 10_000, 2_048

@@ -95,6 +95,18 @@ typedef struct tc_info {
  * Errors: TC_EINVAL if L == 0, block == 0 or out == NULL; TC_ENOMEM; TC_ECUDA. */
 tc_status tc_open_stream(size_t L, size_t block, tc_stream **out);
 
+/* One mono stream with a precision, on a device, with pushes of up to
+ * max_push samples (0: block). device = -1: the current CUDA device;
+ * otherwise the stream's memory and work are on that device (the calling
+ * thread's current device is left as it was). precision TC_FP32 runs the
+ * gather (K1); TC_BF16 and TC_BF16_SPLIT run the tensor-core contraction (K2)
+ * with the output of a push cut into rows of 256 samples (K2's channels are
+ * overlapping windows of the one input), falling back to K1 for windows that
+ * straddle an IR switch. Errors: as tc_open_group; TC_EINVAL for a bad device
+ * or precision. */
+tc_status tc_open_stream_ex(size_t L, size_t block, tc_precision precision, int device, size_t max_push,
+                            tc_stream **out);
+
 /* A group of `channels` streams pushed together: the multichannel use of
  * Sec. 5.1 and Sec. 6. With shared_ir = 1 all channels use one IR. The
  * BF16 modes then run on the tensor cores as a Toeplitz(h) x X contraction.

@@ -91,6 +91,7 @@ _SIGS = {
     "tc_server_open": [_sz, _sz, ctypes.POINTER(_vp)],
     "tc_server_close": [_vp],
     "tc_server_add": [_vp, _sz, _sz, _vp, _sz, _int, ctypes.POINTER(_u64)],
+    "tc_open_stream_ex": [_sz, _sz, _int, _int, _sz, ctypes.POINTER(_vp)],
     "tc_server_add_group": [_vp, _sz, _sz, _sz, _vp, _sz, _int, _int, ctypes.POINTER(_u64)],
     "tc_server_set_ir_at": [_vp, _u64, _vp, _sz, _u64],
     "tc_server_submit": [_vp, _u64, _vp, _sz],
@@ -176,6 +177,12 @@ def _dev_ptr(t, dtype: str = "float32") -> int:
 def tc_open_stream(L: int, block: int) -> int:
     h = _vp()
     _call("tc_open_stream", L, block, ctypes.byref(h))
+    return h.value
+
+
+def tc_open_stream_ex(L: int, block: int, precision: int = TC_FP32, device: int = -1, max_push: int = 0) -> int:
+    h = _vp()
+    _call("tc_open_stream_ex", L, block, int(precision), int(device), max_push, ctypes.byref(h))
     return h.value
 
 

@@ -179,6 +179,8 @@ struct tc_stream {
     std::vector<std::array<TSet, 8>> tsets;  // [slot][delta]
     float *k2_partial = nullptr;
     size_t k2_partial_floats = 0;
+    float *k2_rows = nullptr;  // mono streams: row-major output of the 256-sample rows
+    size_t k2_rows_floats = 0;
     long long k2_launches = 0, k1_fallbacks = 0;
 
     // BF16 tensor-core path for MIMO (K3): reversed bf16 hi/lo inputs of a
@@ -255,6 +257,7 @@ void free_all(tc_stream *s)
     cudaFree(s->hist_hi);
     cudaFree(s->hist_lo);
     cudaFree(s->k2_partial);
+    cudaFree(s->k2_rows);
     for (auto &arr : s->tsets)
         for (auto &t : arr) {
             cudaFree(t.thi);
@@ -589,6 +592,10 @@ tc_status set_ir_impl(tc_stream *s, const float *h, size_t n, long long sample, 
 }
 
 // Makes room in the history rows for n more samples (plus tile overrun).
+// Mono tensor-core streams read up to 256 + 31 samples past a push (the last
+// 256-sample row of K2's row view): keep that much more room after it.
+long long room_extra(const tc_stream *s) { return (s->rows == 1 && s->prec != TC_FP32) ? 512 : 0; }
+
 tc_status ensure_room(tc_stream *s, long long n)
 {
     if (s->pos + n + tc::K1_MO + 8 <= s->base + s->cap)
@@ -759,9 +766,37 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
     p.ntile_o = (int)ntile_o;
     p.x_col0 = w0 - s->base;
     p.nkb = (int)nkb;
+    // A mono stream cuts the push's output into rows of 256 samples and runs
+    // them as K2's channels: row r's history is the window from w0 + 256 r, so
+    // the X tensor map is one strided view of the history (row stride 512
+    // bytes) and 128 rows fill a tile. Outputs go to a row-major staging
+    // buffer first (the last row may run past the push).
+    CUtensorMap mxr_hi{}, mxr_lo{};
+    const bool rowview = s->rows == 1 && nout >= TN &&
+                         (w0 - s->base) + (ntile_o - 1) * TN + nkb * KB <= s->cap;
+    if (rowview) {
+        const long long col = w0 - s->base;  // a multiple of 8: 16-byte aligned
+        TC_CU(tc::encode_bf16_2d(&mxr_hi, static_cast<char *>(s->hist_hi) + col * 2, (unsigned long long)nkb * KB,
+                                 (unsigned long long)ntile_o, (unsigned long long)TN * 2, KB, TM));
+        TC_CU(tc::encode_bf16_2d(&mxr_lo, static_cast<char *>(s->hist_lo) + col * 2, (unsigned long long)nkb * KB,
+                                 (unsigned long long)ntile_o, (unsigned long long)TN * 2, KB, TM));
+        const size_t need_rows = (size_t)ntile_o * TN;
+        if (need_rows > s->k2_rows_floats) {
+            if (s->k2_rows)
+                cudaFreeAsync(s->k2_rows, s->cs);
+            s->k2_rows = nullptr;
+            TC_CU(cudaMallocAsync(&s->k2_rows, need_rows * sizeof(float), s->cs));
+            TC_ALIGNED(s->k2_rows);
+            s->k2_rows_floats = need_rows;
+        }
+        p.C = (int)ntile_o;
+        p.nout = TN;
+        p.ntile_o = 1;
+        p.x_col0 = 0;
+    }
     // Plain BF16 runs two channel tiles per CTA (one T stage feeds both), as
     // long as a unit's K range fits one TMEM run.
-    const long long ntile_c1 = (s->rows + TM - 1) / TM;
+    const long long ntile_c1 = ((long long)p.C + TM - 1) / TM;
     bool pair = s->prec == TC_BF16 && !s->k2_single_tile;
     p.ntile_c = (int)(pair ? (ntile_c1 + 1) / 2 : ntile_c1);
     const long long tiles = (long long)p.ntile_c * p.ntile_o;
@@ -798,12 +833,12 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
         pair = false;
         p.ntile_c = (int)ntile_c1;
     }
-    p.y = y;
-    p.y_pitch = y_pitch;
+    p.y = rowview ? s->k2_rows : y;
+    p.y_pitch = rowview ? TN : y_pitch;
     p.err = s->d_err;
     if (nsplit > 1) {
         // Partials per 128-channel tile (the pair kernel writes that layout too).
-        const size_t need = (size_t)(2 * ((ntile_c1 + 1) / 2) * ntile_o * nsplit) * TM * TN;
+        const size_t need = (size_t)(2 * ((ntile_c1 + 1) / 2) * p.ntile_o * nsplit) * TM * TN;
         if (need > s->k2_partial_floats) {
             if (s->k2_partial)
                 cudaFreeAsync(s->k2_partial, s->cs);  // after the launches that used it
@@ -816,10 +851,14 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
     }
     tc_stream::TSet &t = ts;
     TC_TRY(prof_begin(s));
+    const CUtensorMap &mxh = rowview ? mxr_hi : s->mx_hi;
+    const CUtensorMap &mxl = rowview ? mxr_lo : s->mx_lo;
     if (pair)
-        TC_CU(tc::k2_launch_pair(s->mx_hi, t.mt_hi, p, s->cs));
+        TC_CU(tc::k2_launch_pair(mxh, t.mt_hi, p, s->cs));
     else
-        TC_CU(tc::k2_launch(s->mx_hi, s->mx_lo, t.mt_hi, t.mt_lo, p, s->prec == TC_BF16 ? 1 : 3, s->cs));
+        TC_CU(tc::k2_launch(mxh, mxl, t.mt_hi, t.mt_lo, p, s->prec == TC_BF16 ? 1 : 3, s->cs));
+    if (rowview)
+        TC_CU(cudaMemcpyAsync(y, s->k2_rows, (size_t)nout * sizeof(float), cudaMemcpyDeviceToDevice, s->cs));
     TC_TRY(prof_end(s, t0, nout));
     s->k2_launches++;
     *used = true;
@@ -989,7 +1028,7 @@ tc_status push_impl(tc_stream *s, const float *x, size_t n, float *y, int mode, 
         return fail(TC_ESTATE, "no IR covers input sample %lld; call tc_set_ir first", s->pos);
     TC_TRY(use_device(s));
     retire_versions(s);
-    TC_TRY(ensure_room(s, (long long)n));
+    TC_TRY(ensure_room(s, (long long)n + room_extra(s)));
 
     float *hist_at = s->hist + (s->pos - s->base);
     const size_t pitch_b = (size_t)s->cap * sizeof(float);
@@ -1059,7 +1098,7 @@ tc_status flush_to_device(tc_stream *s, float *y, long long y_pitch)
     s->pos_end_hint = s->pos;
     for (long long off = 0; off < tail;) {
         const long long piece = std::min<long long>(tail - off, (long long)s->max_push);
-        TC_TRY(ensure_room(s, piece));
+        TC_TRY(ensure_room(s, piece + room_extra(s)));
         TC_CU(cudaMemset2DAsync(s->hist + (s->pos - s->base), (size_t)s->cap * sizeof(float), 0,
                                 (size_t)piece * sizeof(float), s->rows, s->cs));
         TC_TRY(split_new(s, s->pos - s->base, piece));
@@ -1129,6 +1168,25 @@ extern "C" {
 tc_status tc_open_stream(size_t L, size_t block, tc_stream **out)
 {
     return open_any(KIND_GROUP, 1, 1, 1, 1, L, block, 1, TC_FP32, block, out);
+}
+
+tc_status tc_open_stream_ex(size_t L, size_t block, tc_precision precision, int device, size_t max_push,
+                            tc_stream **out)
+{
+    int ndev = 0, cur = 0;
+    TC_CU(cudaGetDeviceCount(&ndev));
+    if (device < -1 || device >= ndev)
+        return fail(TC_EINVAL, "device %d not in [-1, %d)", device, ndev);
+    if (precision != TC_FP32 && precision != TC_BF16 && precision != TC_BF16_SPLIT)
+        return fail(TC_EINVAL, "unknown precision");
+    TC_CU(cudaGetDevice(&cur));
+    if (device >= 0 && device != cur)
+        TC_CU(cudaSetDevice(device));
+    // A mono stream is a one-channel group; its IR is shared by that channel.
+    const tc_status st = open_any(KIND_GROUP, 1, 1, 1, 1, L, block, 1, precision, max_push, out);
+    if (device >= 0 && device != cur)
+        cudaSetDevice(cur);
+    return st;
 }
 
 tc_status tc_open_group(size_t channels, size_t L, size_t block, int shared_ir, tc_precision precision,

@@ -136,3 +136,36 @@ def test_single_signal_on_the_tensor_cores(prec, N, L):
     err = rel_l2(got, ref)
     print(f"{prec} N={N} L={L}: rel_l2={err:.3g}")
     assert err <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["bf16split", "bf16"])
+@pytest.mark.parametrize("P", [4096, 256, 128])
+def test_mono_stream_on_the_tensor_cores(prec, P):
+    """tc_open_stream_ex in the BF16 modes: pushes of >= 256 samples run K2 on the push's 256-sample rows
+    (overlapping windows of the one history), shorter ones as a one-channel tile; an IR switch inside the run
+    (windows that straddle it fall back to K1), a short last push and the flush."""
+    L, N = 3000, 20_000
+    x = synth.audio(N, 950 + P)
+    H = np.stack([synth.decayed_ir(L, 600.0, 951 + v) for v in range(2)])
+    vstart = [0, 9000]
+    s = capi.tc_open_stream_ex(L, min(P, 256), PREC[prec], -1, P)
+    outs = []
+    try:
+        capi.tc_set_ir(s, H[0])
+        capi.tc_set_ir_at(s, H[1], vstart[1])
+        for pos in range(0, N, P):
+            n = min(P, N - pos)
+            y = np.empty((1, n), np.float32)
+            capi.tc_push(s, np.ascontiguousarray(x[None, pos:pos + n]), n, y)
+            outs.append(y)
+        tail = np.empty((1, L - 1), np.float32)
+        capi.tc_flush(s, tail, L - 1)
+        info = capi.tc_get_info(s)
+    finally:
+        capi.tc_close(s)
+    y = np.concatenate(outs + [tail], axis=1)[0]
+    ref = oracle.buffer(x, H, np.asarray(vstart, np.int64), min(P, 256))
+    err = rel_l2(y, ref)
+    print(f"mono {prec} P={P}: rel_l2={err:.3g}, tensor launches {info.tensor_launches}, fallbacks {info.fp32_fallbacks}")
+    assert info.tensor_launches > 0
+    assert err <= TOL[prec]

@@ -9,6 +9,8 @@ oracle one by one (Eq. 4 at each output).
           (BF16 split, BF16) and K1 (FP32)
   mimo    16 x 16, 60 s per input, L = 192000, block 512: K3 (BF16 split, BF16)
           and K1 (FP32)
+  serving the Poisson serving trace replayed in real time through the worker
+          (3 s of it, outputs kept): K1 work lists
 """
 import numpy as np
 import pytest
@@ -117,3 +119,67 @@ def test_mimo_full_size(torch, mimo_workload, prec):
     err = rel_l2(got, refs)
     print(f"mimo {prec}: {len(picks)} sampled outputs, rel_l2={err:.3g}")
     assert err <= TOL[prec]
+
+
+def test_serving_trace_sampled(torch):
+    """The serving trace as the benchmark replays it (Poisson arrivals, IRs up to 480000 taps, blocks of
+    32-256, 10 % with an IR swap, live 48 kHz sources, worker thread), 3 s, outputs kept: 96 sampled outputs
+    of the delivered blocks against the oracle's direct sum (Eq. 4, per-sample versions)."""
+    import time
+    FS = synth.FS
+    seconds = 3.0
+    tr = synth.serving_trace(duration_s=seconds)
+    make = bench._ir_maker()
+    pool = synth.audio(32 * FS, 4242)
+    srv = capi.tc_server_open(96 << 30, 1 << 22)
+    streams = {}
+    outs = {}
+    try:
+        capi.tc_server_start(srv)
+        t_start = capi.tc_server_clock() + 0.02
+        pending = list(tr)
+        ybuf = np.empty(256, np.float32)
+
+        def drain():
+            for sid in streams:
+                while True:
+                    n, _, _ = capi.tc_server_poll(srv, sid, ybuf)
+                    if n == 0:
+                        break
+                    outs[sid].append(ybuf[:n].copy())
+
+        while capi.tc_server_clock() < t_start + seconds:
+            now = capi.tc_server_clock()
+            while pending and t_start + pending[0].arrival_s <= now:
+                t = pending.pop(0)
+                H = np.stack([make(t.L, t.tau, sd) for sd in t.ir_seeds])
+                sid = capi.tc_server_add(srv, t.L, t.block, H[0])
+                if t.swap_at >= 0:
+                    capi.tc_server_set_ir_at(srv, sid, H[1], t.swap_at)
+                off = (t.sid * 7919) % (pool.size - t.n) if t.n < pool.size else 0
+                n = min(t.n, pool.size)
+                capi.tc_server_attach_source(srv, sid, (pool.ctypes.data + 4 * off, n), capi.tc_server_clock())
+                vstart = [0] if t.swap_at < 0 else [0, t.swap_at]
+                streams[sid] = (pool[off:off + n], H, np.asarray(vstart, np.int64))
+                outs[sid] = []
+            drain()
+            time.sleep(0.002)
+        capi.tc_server_stop(srv)
+        drain()
+    finally:
+        capi.tc_server_close(srv)
+    ys = {sid: np.concatenate(v) for sid, v in outs.items() if v}
+    assert len(ys) >= 100  # streams with delivered output
+    rng = np.random.default_rng(97)
+    sids = sorted(ys)
+    got, ref = [], []
+    for _ in range(96):
+        sid = sids[int(rng.integers(len(sids)))]
+        y = ys[sid]
+        m = int(rng.integers(y.size))
+        x, H, vstart = streams[sid]
+        got.append(float(y[m]))
+        ref.append(oracle.direct_at(x, H, vstart, m))
+    err = rel_l2(np.array(got), np.array(ref))
+    print(f"serving trace: {len(ys)} streams delivered, 96 sampled outputs, rel_l2={err:.3g}")
+    assert err <= TOL["fp32"]

@@ -626,6 +626,68 @@ def bench_mono(capi) -> dict:
                     "tc_convolve on device buffers"}
 
 
+def bench_ext(torch, capi, steps: int = 3) -> dict:
+    """The gather's extensions on the 64-stream recipe (own IRs L = 48000, a new IR every 24000 samples,
+    pushes of 8192 on device pointers): zero gating on an input that is silent half of the time (0.5 s of
+    sound, 0.5 s of zeros), with and without gating, outputs compared bit for bit; and crossfaded IR switches
+    (480-sample ramps) against hard ones, on the plain input."""
+    w = synth.multi(C=C_STREAMS, N=N_SAMPLES, L=L_TAPS, block=BLOCK, swap_every=SWAP)
+    gate = np.ones(N_SAMPLES, np.float32)
+    for k in range(0, N_SAMPLES, FS):
+        gate[k + FS // 2:k + FS] = 0.0
+    out = {"workload": "64 streams x 10 s, own IRs L=48000 swapped every 24000 samples, pushes of 8192"}
+    H_d = torch.from_numpy(np.ascontiguousarray(np.transpose(w.H, (1, 0, 2)))).cuda()  # [nver][C][L]
+    vstart = [int(v) for v in w.vstart]
+
+    def timed_pass(x, zero_skip: int, ramp: int):
+        run = PushRun(torch, x, 8192, C_STREAMS, L_TAPS)
+        s = capi.tc_open_group(C_STREAMS, L_TAPS, BLOCK, False, capi.TC_FP32, 8192)
+        try:
+            capi.tc_set_cuda_stream(s, run.ts)
+            capi.tc_set_tuning(s, capi.TC_TUNE_ZERO_SKIP, zero_skip)
+
+            def one():
+                capi.tc_reset(s)
+                capi.tc_set_crossfade(s, 1)
+                v = 0
+                for i in range(run.npush):
+                    pos = i * 8192
+                    n = min(8192, N_SAMPLES - pos)
+                    while v < len(vstart) and vstart[v] < pos + n:
+                        capi.tc_set_crossfade(s, ramp if v > 0 else 1)
+                        capi.tc_set_ir_rows(s, int(H_d[v].data_ptr()), L_TAPS, vstart[v], on_device=True)
+                        v += 1
+                    capi.tc_push(s, int(run.x_d[i].data_ptr()), n, int(run.y_d[i].data_ptr()), on_device=True)
+                capi.tc_flush_dev(s, int(run.tail_d.data_ptr()))
+
+            one()
+            run.ts.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(run.ts)
+            for _ in range(steps):
+                one()
+            e1.record(run.ts)
+            e1.synchronize()
+            y = torch.cat([run.y_d.reshape(-1), run.tail_d.reshape(-1)]).cpu()
+            return e0.elapsed_time(e1) / steps, y
+        finally:
+            capi.tc_close(s)
+            run.close()
+
+    xg = w.x * gate[None, :]
+    ms_off, y_off = timed_pass(xg, 0, 1)
+    ms_on, y_on = timed_pass(xg, 1, 1)
+    out["zero_gating"] = {"input": "0.5 s of sound then 0.5 s of zeros, repeated", "ms_without": ms_off,
+                          "ms_with": ms_on, "speedup": ms_off / ms_on,
+                          "bit_identical": bool(torch.equal(y_off, y_on))}
+    ms_hard, _ = timed_pass(w.x, 0, 1)
+    ms_xf, y_xf = timed_pass(w.x, 0, 480)
+    out["crossfade"] = {"ramp_samples": 480, "ms_hard_switches": ms_hard, "ms_crossfaded": ms_xf,
+                        "overhead": ms_xf / ms_hard - 1.0}
+    torch.cuda.empty_cache()
+    return out
+
+
 Q15_N, Q15_L = 2_880_000, 48_000
 
 
@@ -1230,6 +1292,7 @@ def main():
     ap.add_argument("--no-q15", action="store_true", help="skip the exact Q15 section")
     ap.add_argument("--only-q15", action="store_true", help="run only the exact Q15 section")
     ap.add_argument("--only-offline", action="store_true", help="run only the one-shot (role swap) section")
+    ap.add_argument("--only-ext", action="store_true", help="run only the zero-gating / crossfade section")
     ap.add_argument("--only-groups", action="store_true", help="run only the shared-IR group serving section")
     ap.add_argument("--groups-prec", default="bf16split,fp32", help="group serving section: precisions")
     ap.add_argument("--only-mimo", action="store_true", help="run only the MIMO section")
@@ -1291,6 +1354,10 @@ def main():
         return
     if args.only_offline:
         print(json.dumps({"offline": bench_offline(torch, capi)}), flush=True)
+        dist.close()
+        return
+    if args.only_ext:
+        print(json.dumps({"ext": bench_ext(torch, capi)}), flush=True)
         dist.close()
         return
     if args.only_q15:
@@ -1447,6 +1514,9 @@ def main():
         mono["offline"] = guarded(lambda: bench_offline(torch, capi))
         if cpu_other:
             mimo["cpu_baseline"], mono["cpu_baseline"] = cpu_other["mimo"], cpu_other["mono"]
+    ext = None
+    if not args.no_mimo and dist.world == 1:
+        ext = guarded(lambda: bench_ext(torch, capi))
     q15 = None
     if not args.no_q15 and dist.world == 1:
         q15 = guarded(lambda: bench_q15(torch, capi))
@@ -1464,7 +1534,7 @@ def main():
                 "realtime_streams_48k": value / per_stream_rt,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": int(launches), "latency": latency, "check": check, "shared_ir": shared,
-                "serving": serving, "mimo": mimo, "mono": mono, "q15": q15,
+                "serving": serving, "mimo": mimo, "mono": mono, "q15": q15, "ext": ext,
                 "autotune_push_ms_per_sample": {str(k): v for k, v in tune.items()} or None}
         print(json.dumps(line), flush=True)
     dist.close()

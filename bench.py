@@ -1022,11 +1022,14 @@ def bench_capacity(torch, capi, H64: np.ndarray, pool: np.ndarray, paced_s: floa
 
         runs = {}
         best = None
+        fail = None
         M = m0
         step = 1.25 if paced(M)["pass"] else 0.8  # direction from the first run
         runs[str(M)] = paced.last
         if runs[str(M)]["pass"]:
             best = M
+        else:
+            fail = M
         for _ in range(5):
             M = max(128, int(M * step) // 128 * 128)
             if str(M) in runs:
@@ -1037,8 +1040,23 @@ def bench_capacity(torch, capi, H64: np.ndarray, pool: np.ndarray, paced_s: floa
                 best = max(best or 0, M)
                 if step < 1:
                     break  # first pass going down
-            elif step > 1:
-                break  # first failure going up
+            else:
+                fail = M if fail is None else min(fail, M)
+                if step > 1:
+                    break  # first failure going up
+        # Two bisection steps between the largest passing and the smallest failing count.
+        for _ in range(2):
+            if best is None or fail is None or fail - best <= 128:
+                break
+            M = (best + fail) // 2 // 128 * 128
+            if M <= best or str(M) in runs:
+                break
+            r = paced(M)
+            runs[str(M)] = r
+            if r["pass"]:
+                best = M
+            else:
+                fail = M
         out["batched"] = {"streams": best or 0,
                           "criterion": "paced: p99 <= deadline and <= 0.1 % misses",
                           "sync_cycle_ms": {str(k): v * 1e3 for k, v in sorted(sweep.items())},

@@ -710,6 +710,27 @@ tc_status launch_k1(tc_stream *s, long long t0, long long nout, float *y, long l
     return prof_end(s, t0, nout);
 }
 
+// K parts per K2 tile: the fewest (up to 64, k2_reduce's tree, each at least
+// 16 K blocks long) that fill the GPU's waves to >= 90 %, so that a small
+// launch (one serving step of one group) spreads over the GPU.
+long long k2_plan_nsplit(long long tiles, long long nkb, int sms)
+{
+    long long nsplit = 1;
+    double best = 0.0;
+    for (long long ns = 1; ns <= 64 && ns <= nkb && (ns == 1 || nkb / ns >= 16); ++ns) {
+        const long long units = tiles * ns;
+        const double eff = (double)units / (double)(((units + sms - 1) / sms) * sms);
+        if (eff > best + 1e-9) {
+            best = eff;
+            nsplit = ns;
+        }
+        if (eff >= 0.9)
+            break;
+    }
+    const long long kb_per = (nkb + nsplit - 1) / nsplit;
+    return (nkb + kb_per - 1) / kb_per;
+}
+
 // K2 on the tensor cores when every input sample of the launch's window
 // spawned its tache with the same IR version; false in *used otherwise.
 tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long long y_pitch, bool *used)
@@ -745,8 +766,8 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
                 cudaFreeAsync(ts.tlo, s->cs);
             ts.thi = ts.tlo = nullptr;
             const size_t bytes = (size_t)nkb * TN * KB * 2;
-            TC_CU(cudaMallocAsync(&ts.thi, bytes, s->cs));
-            TC_CU(cudaMallocAsync(&ts.tlo, bytes, s->cs));
+            TC_CU(tc::pool_alloc(&ts.thi, bytes, s->cs));
+            TC_CU(tc::pool_alloc(&ts.tlo, bytes, s->cs));
             TC_ALIGNED(ts.thi);
             TC_ALIGNED(ts.tlo);
             ts.nkb = nkb;
@@ -785,7 +806,7 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
             if (s->k2_rows)
                 cudaFreeAsync(s->k2_rows, s->cs);
             s->k2_rows = nullptr;
-            TC_CU(cudaMallocAsync(&s->k2_rows, need_rows * sizeof(float), s->cs));
+            TC_CU(tc::pool_alloc(reinterpret_cast<void **>(&s->k2_rows), need_rows * sizeof(float), s->cs));
             TC_ALIGNED(s->k2_rows);
             s->k2_rows_floats = need_rows;
         }
@@ -810,20 +831,7 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
     p.range += p.range & 1;  // runs are whole pipeline stages of 2 K blocks
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
-    // Up to 64 parts (k2_reduce's tree), each at least 16 K blocks long: a
-    // small launch (one serving step of one group) spreads over the GPU.
-    long long nsplit = 1;
-    double best = 0.0;
-    for (long long ns = 1; ns <= 64 && ns <= nkb && (ns == 1 || nkb / ns >= 16); ++ns) {
-        const long long units = tiles * ns;
-        const double eff = (double)units / (double)(((units + sms - 1) / sms) * sms);
-        if (eff > best + 1e-9) {
-            best = eff;
-            nsplit = ns;
-        }
-        if (eff >= 0.9)
-            break;
-    }
+    long long nsplit = k2_plan_nsplit(tiles, nkb, sms);
     const long long kb_per = (nkb + nsplit - 1) / nsplit;
     nsplit = (nkb + kb_per - 1) / kb_per;
     p.nsplit = (int)nsplit;
@@ -843,7 +851,7 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
             if (s->k2_partial)
                 cudaFreeAsync(s->k2_partial, s->cs);  // after the launches that used it
             s->k2_partial = nullptr;
-            TC_CU(cudaMallocAsync(&s->k2_partial, need * sizeof(float), s->cs));
+            TC_CU(tc::pool_alloc(reinterpret_cast<void **>(&s->k2_partial), need * sizeof(float), s->cs));
             TC_ALIGNED(s->k2_partial);
             s->k2_partial_floats = need;
         }
@@ -894,8 +902,8 @@ tc_status launch_k3(tc_stream *s, long long t0, long long nout, float *y, long l
     if (!ks.ready) {
         const unsigned long long rows = (unsigned long long)s->nin * nkbp * 128;
         if (!ks.bh) {
-            TC_CU(cudaMallocAsync(&ks.bh, rows * 32 * 2, s->cs));
-            TC_CU(cudaMallocAsync(&ks.bl, rows * 32 * 2, s->cs));
+            TC_CU(tc::pool_alloc(&ks.bh, rows * 32 * 2, s->cs));
+            TC_CU(tc::pool_alloc(&ks.bl, rows * 32 * 2, s->cs));
             TC_ALIGNED(ks.bh);
             TC_ALIGNED(ks.bl);
             TC_CU(tc::encode_bf16_2d(&ks.mb_hi, ks.bh, 32, rows, 64, 32, 128));
@@ -946,7 +954,7 @@ tc_status launch_k3(tc_stream *s, long long t0, long long nout, float *y, long l
             cudaFreeAsync(s->k3_partial, s->cs);  // after the launches that used it
         s->k3_partial = nullptr;
         s->k3_partial_floats = 0;
-        TC_CU(cudaMallocAsync(&s->k3_partial, need * sizeof(float), s->cs));
+        TC_CU(tc::pool_alloc(reinterpret_cast<void **>(&s->k3_partial), need * sizeof(float), s->cs));
         TC_ALIGNED(s->k3_partial);
         s->k3_partial_floats = need;
     }
@@ -1133,6 +1141,35 @@ tc_status group_open(size_t channels, size_t L, size_t max_push, int precision, 
 {
     TC_TRY(open_any(KIND_GROUP, channels, channels, 1, 1, L, 1, 1, (tc_precision)precision, max_push, out));
     tc_stream *s = *out;
+    if (s->prec != TC_FP32) {
+        // K-part partials for the largest push, now: growing them while
+        // serving would map memory in the middle of a step.
+        int sms = 148;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+        const long long TM = tc::k2_tile_m(), TN = tc::k2_tile_n();
+        const long long ntile_c1 = ((long long)s->rows + TM - 1) / TM;
+        const long long nkb = tc::k2_nkb((long long)L, 7);
+        size_t need = 0;
+        for (long long no = 1; no <= ((long long)max_push + TN - 1) / TN; ++no) {
+            const long long tiles = (s->prec == TC_BF16 ? (ntile_c1 + 1) / 2 : ntile_c1) * no;
+            const long long ns = k2_plan_nsplit(tiles, nkb, sms);
+            if (ns > 1)
+                need = std::max(need, (size_t)(2 * ((ntile_c1 + 1) / 2) * no * ns * TM * TN));
+        }
+        if (need > 0) {
+            tc_status st = TC_OK;
+            if (tc::pool_alloc(reinterpret_cast<void **>(&s->k2_partial), need * sizeof(float), s->cs) !=
+                cudaSuccess)
+                st = fail(TC_ENOMEM, "group K-part partials");
+            else
+                s->k2_partial_floats = need;
+            if (st != TC_OK) {
+                tc_close(s);
+                *out = nullptr;
+                return st;
+            }
+        }
+    }
     // Device footprint: what open allocated, plus what the tensor-core
     // launches allocate in steady use (Toeplitz tiles of two live IR versions
     // at one alignment shift: pushes at multiples of 8 samples keep the

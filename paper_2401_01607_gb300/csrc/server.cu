@@ -470,16 +470,14 @@ StageLayout stage_layout(size_t ni, size_t samples)
     return l;
 }
 
-// Grows step buffer b and the shared device buffers. Waits for the step in
-// flight first (rare: only when a step is larger than any before).
+// Grows step buffer b and the shared device buffers. Device buffers grow in
+// stream order (the old one is freed after the steps in flight, the new one
+// comes from the library's pool): no host wait. Only a larger pinned staging
+// buffer waits for the step in flight (rare: a step larger than any before).
 tc_status grow(tc_server *srv, tc_server::StepBuf &b, size_t items, size_t scratch_floats, size_t counters)
 {
-    const bool need = items > b.items_cap || items > srv->d_stage_items || scratch_floats > srv->scratch_floats ||
-                      counters > srv->counters_n;
-    if (!need)
-        return TC_OK;
-    S_CU(cudaStreamSynchronize(srv->cs));
     if (items > b.items_cap) {
+        S_CU(cudaStreamSynchronize(srv->cs));
         const size_t m = std::max(items, b.items_cap * 2 + 64);
         cudaFreeHost(b.pin_stage);
         cudaFreeHost(b.pin_tables);
@@ -492,26 +490,30 @@ tc_status grow(tc_server *srv, tc_server::StepBuf &b, size_t items, size_t scrat
     }
     if (items > srv->d_stage_items) {
         const size_t m = std::max(items, srv->d_stage_items * 2 + 64);
-        cudaFree(srv->d_stage);
+        if (srv->d_stage)
+            cudaFreeAsync(srv->d_stage, srv->cs);
         srv->d_stage = nullptr;
         srv->d_stage_items = 0;
-        S_CU(cudaMalloc(&srv->d_stage, stage_layout(m, srv->max_step_samples).end));
+        S_CU(tc::pool_alloc(reinterpret_cast<void **>(&srv->d_stage), stage_layout(m, srv->max_step_samples).end,
+                            srv->cs));
         srv->d_stage_items = m;
     }
     if (scratch_floats > srv->scratch_floats) {
-        cudaFree(srv->scratch);
+        const size_t m = std::max(scratch_floats, srv->scratch_floats * 2);
+        if (srv->scratch)
+            cudaFreeAsync(srv->scratch, srv->cs);
         srv->scratch = nullptr;
         srv->scratch_floats = 0;
-        const size_t m = std::max(scratch_floats, srv->scratch_floats * 2);
-        S_CU(cudaMalloc(&srv->scratch, m * sizeof(float)));
+        S_CU(tc::pool_alloc(reinterpret_cast<void **>(&srv->scratch), m * sizeof(float), srv->cs));
         srv->scratch_floats = m;
     }
     if (counters > srv->counters_n) {
-        cudaFree(srv->counters);
+        const size_t m = std::max(counters, srv->counters_n * 2);
+        if (srv->counters)
+            cudaFreeAsync(srv->counters, srv->cs);
         srv->counters = nullptr;
         srv->counters_n = 0;
-        const size_t m = std::max(counters, srv->counters_n * 2);
-        S_CU(cudaMalloc(&srv->counters, m * sizeof(unsigned)));
+        S_CU(tc::pool_alloc(reinterpret_cast<void **>(&srv->counters), m * sizeof(unsigned), srv->cs));
         S_CU(cudaMemsetAsync(srv->counters, 0, m * sizeof(unsigned), srv->cs));
         srv->counters_n = m;
     }
@@ -1095,7 +1097,7 @@ tc_status tc_server_open(size_t mem_budget_bytes, size_t max_step_samples, tc_se
     // Size the step buffers for a few thousand streams and load the kernels
     // now, so that the first steps do not pay for allocations or module loads.
     for (auto &b : srv->buf)
-        S_TRY(grow(srv.get(), b, 4096, (size_t)4096 * 19 * tc::K1_MO, 16384));
+        S_TRY(grow(srv.get(), b, 4096, (size_t)1 << 26, 16384));
     cudaFuncAttributes fa;
     S_CU(cudaFuncGetAttributes(&fa, ingest_kernel));
     tc::K1Plan plan{};

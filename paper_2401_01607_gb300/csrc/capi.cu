@@ -11,8 +11,12 @@
 //   vt       version table: (first sample, slot) per live IR version
 //            (abstract, Sec. 6: a new IR is used for the next samples).
 //   partial  K1 scratch for tap-chunk partial sums, plus ticket counters.
-// Everything runs on one CUDA stream per tc_stream, in call order, so a slot
+//   hist_hi/lo, Toeplitz tiles, K-part partials: the tensor-core paths (K2 for
+//            shared-IR groups and mono BF16 streams, K3 for MIMO).
+// The kernels run on one CUDA stream per tc_stream, in call order, so a slot
 // or table entry is never overwritten while an earlier kernel may read it.
+// Asynchronous pushes from page-locked host buffers add a copy stream (and an
+// IR-upload stream), ordered against the kernels with events.
 #include <algorithm>
 #include <array>
 #include <cstdarg>

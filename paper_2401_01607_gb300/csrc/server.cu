@@ -8,8 +8,9 @@
 // one batch:
 //   one host->device copy of the packed input and work list, one ingest
 //   kernel into the streams' history rows (with any row compactions), one K1
-//   work-list launch (one item
-//   per stream), one device->host copy of the packed output.
+//   work-list launch (one item per stream), one push of each shared-IR group
+//   on the group's own CUDA stream (K2 in the BF16 modes, beside the gather;
+//   ordered by events), one device->host copy of the packed output.
 // The worker thread (tc_server_start) keeps two steps in flight: while the
 // GPU runs step k, the host collects and launches step k+1 (its own pinned
 // buffers; device buffers are shared because one CUDA stream orders them).

@@ -167,7 +167,9 @@ def oracle_baseline(cores: int, nsamp: int) -> dict:
             "sample": f"{cores} of the 64 streams, first {nsamp} samples each (IR swaps included), "
                       f"FP64 buffer algorithm, one stream per core; time = slowest worker "
                       f"({slowest:.2f} s, pool wall {wall:.2f} s)",
-            "cpu_seconds": float(sum(times))}
+            "cpu_seconds": float(sum(times)),
+            "samples_per_s": cores * nsamp / slowest,
+            "realtime_factor_per_core": float(np.median([nsamp / t for t in times])) / FS}
 
 
 def _oracle_job(args):
@@ -233,9 +235,18 @@ def oracle_other_workloads(cores: int, only_q15: bool = False) -> dict:
             res = pool.map(_oracle_job, jobs)
             wall = time.perf_counter() - t0
             macs = sum(m for _, m in res)
+            cpu_s = float(sum(t for t, _ in res))
             out[name] = {"value": macs / wall, "unit": "tap-MAC/s", "cores": min(cores, len(jobs)), "kind": "oracle",
-                         "sample": desc + f"; pool wall {wall:.2f} s", "cpu_seconds": float(sum(t for t, _ in res))}
+                         "sample": desc + f"; pool wall {wall:.2f} s", "cpu_seconds": cpu_s,
+                         "realtime_factor_per_core": macs / cpu_s / RT_MACS[name],
+                         "realtime_unit": RT_UNIT[name]}
     return out
+
+
+# tap-MAC/s that one real-time unit of each workload needs at 48 kHz, for the oracle's per-core real-time factor
+RT_MACS = {"mono": FS * 4096, "shared_ir": FS * 96_000, "mimo": FS * 192_000 * 256, "q15": FS * 48_000}
+RT_UNIT = {"mono": "one mono stream (L=4096)", "shared_ir": "one stream of the shared IR (L=96000)",
+           "mimo": "the whole 16 x 16 MIMO system (L=192000)", "q15": "one Q15 stream (L=48000)"}
 
 
 def cpu_model() -> str:
@@ -1284,7 +1295,10 @@ def run_reference(args, dist: Dist) -> None:
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(args.push),
             "cpu_baseline": {"value": value, "unit": "tap-MAC/s", "cores": cores, "kind": "oracle",
-                             "sample": times[-1]["sample"], "cpu_model": cpu_model()},
+                             "sample": times[-1]["sample"], "cpu_model": cpu_model(),
+                             "samples_per_s": float(np.median([t["samples_per_s"] for t in times])),
+                             "realtime_factor_per_core":
+                                 float(np.median([t["realtime_factor_per_core"] for t in times]))},
             "e2e": {"value": value, "unit": "tap-MAC/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

@@ -27,6 +27,7 @@ def test_reference_arm_json_line():
     assert line["config"]["workload"] and line["scaling"] == "weak"
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
+    assert cb["samples_per_s"] > 0 and cb["realtime_factor_per_core"] > 0
     e2e = line["e2e"]
     assert e2e["value"] == line["value"] and e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
 

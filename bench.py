@@ -710,7 +710,7 @@ def q15_inputs():
 
 
 def bench_q15(torch, capi, reps: int = 6) -> dict:
-    """Exact Q15 fixed point (K4 + one requantization, Sec. 5.3.1) on device buffers,
+    """Exact Q15 fixed point (K4 + one requantization, Sec. 5.4) on device buffers,
     each inner-loop form; L2 flushed before each timed call; then the same call
     with host buffers (copies inside the timed region)."""
     xq, hq = q15_inputs()

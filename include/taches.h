@@ -306,12 +306,12 @@ tc_status tc_convolve_tc(const float *x, size_t N, const float *h, size_t L, flo
                          void *cuda_stream);
 
 /* ---------------------------------------------------------------------- */
-/* Exact fixed-point convolution with one requantization (Sec. 5.3.1)      */
+/* Exact fixed-point convolution with one requantization (Sec. 5.4)      */
 /* ---------------------------------------------------------------------- */
 
 /* Q15 input and taps (int16, value = code / 2^15). Every product is summed
  * exactly, and each output sample is requantized once to Q15, after all of its
- * products are in (the ideal requantization of Sec. 5.3.1):
+ * products are in (the ideal requantization of Sec. 5.4):
  *   acc[m] = sum_k x[m-k] h[k]                       (int64, Q30, exact)
  *   y[m]   = clamp(round_half_even(acc[m] / 2^15), -32768, 32767)
  * for m in [0, N+L-1). The result is bit-exact and independent of how the GPU

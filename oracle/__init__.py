@@ -145,7 +145,7 @@ class Oracle:
         return y
 
     def q15(self, x, h):
-        """Exact Q15 convolution (Sec. 5.3.1, one requantization): returns
+        """Exact Q15 convolution (Sec. 5.4, one requantization): returns
         (acc int64 exact sums, y int16 requantized, round half to even)."""
         x = np.ascontiguousarray(x, dtype=np.int16).reshape(-1)
         h = np.ascontiguousarray(h, dtype=np.int16).reshape(-1)

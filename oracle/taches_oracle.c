@@ -425,7 +425,7 @@ int tco_buffer_xf(const float *x, int64_t N, const float *H, int64_t L, const in
 }
 
 /* ------------------------------------------------------------------ */
-/* Exact fixed point with one requantization (Sec. 5.3.1, "ideal
+/* Exact fixed point with one requantization (Sec. 5.4, "ideal
  * requantization": an accumulator of unlimited range, a single
  * requantization at the end of each output sample). Input and taps are Q15
  * (int16); each product is exact in 32 bits; the sum of an output's products

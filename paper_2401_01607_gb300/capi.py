@@ -331,7 +331,7 @@ def tc_convolve_tc(x, N: int, h, L: int, y, precision: int = TC_BF16_SPLIT, cuda
 
 
 def tc_convolve_q15(x, N: int, h, L: int, y, acc=None, cuda_stream=None) -> None:
-    """Exact Q15 convolution with one requantization per output (Sec. 5.3.1).
+    """Exact Q15 convolution with one requantization per output (Sec. 5.4).
     x (N), h (L), y (N+L-1) are int16 codes on the device; acc, if given, gets the
     exact int64 sums (N+L-1). y may be None when acc is given."""
     cs = None if cuda_stream is None else (cuda_stream if isinstance(cuda_stream, int) else

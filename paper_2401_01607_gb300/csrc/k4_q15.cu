@@ -1,6 +1,6 @@
 // k4_q15.cu -- K4: exact fixed-point convolution with one requantization.
 //
-// Sec. 5.3.1 ("ideal requantization"): with an accumulator of unlimited range
+// Sec. 5.4 ("ideal requantization"): with an accumulator of unlimited range
 // an output sample is requantized once, after all of its products are summed.
 // Here input and taps are Q15 (int16); each product is exact in 32 bits and
 // each output's sum is kept exactly in 64 bits (|sum| <= L * 2^30 < 2^49 for

@@ -330,7 +330,7 @@ def check_crossfade_superposition(o):
 
 
 def check_q15_exact(o):
-    """Exact fixed point (Sec. 5.3.1): on Q15 data the FP64 buffer oracle is
+    """Exact fixed point (Sec. 5.4): on Q15 data the FP64 buffer oracle is
     itself exact (every product has <= 32 significant bits and every partial
     sum is a multiple of 2^-30 below 2^19), so the integer sums must equal
     2^30 times it, exactly; the single requantization is round half to even

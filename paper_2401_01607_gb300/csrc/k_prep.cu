@@ -63,6 +63,7 @@ uint64_t launches() { return g_launches.load(std::memory_order_relaxed); }
 namespace {
 std::mutex g_pool_mu;
 cudaMemPool_t g_pools[64] = {};
+constexpr uint64_t kPoolKeep = 2ull << 30;
 }  // namespace
 
 cudaError_t pool_alloc(void **ptr, size_t bytes, cudaStream_t st)
@@ -84,7 +85,7 @@ cudaError_t pool_alloc(void **ptr, size_t bytes, cudaStream_t st)
             e = cudaMemPoolCreate(&g_pools[dev], &props);
             if (e != cudaSuccess)
                 return e;
-            uint64_t keep = 2ull << 30;
+            uint64_t keep = kPoolKeep;
             e = cudaMemPoolSetAttribute(g_pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
             if (e != cudaSuccess)
                 return e;
@@ -92,6 +93,24 @@ cudaError_t pool_alloc(void **ptr, size_t bytes, cudaStream_t st)
         pool = g_pools[dev];
     }
     return cudaMallocFromPoolAsync(ptr, bytes, pool, st);
+}
+
+// Memory freed into the pool above its 2 GiB is otherwise released at the
+// next synchronisation on the device, whoever makes it: after a large close
+// (a server with a hundred groups frees tens of GB) that unmapping can stall
+// the next user's steps. Closing trims the pool itself instead.
+void pool_trim()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+        return;
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        pool = g_pools[dev];
+    }
+    if (pool)
+        cudaMemPoolTrimTo(pool, kPoolKeep);
 }
 
 bool no_role_swap()

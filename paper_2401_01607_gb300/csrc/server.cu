@@ -1152,6 +1152,7 @@ tc_status tc_server_close(tc_server *srv)
     if (srv->cs)
         cudaStreamDestroy(srv->cs);
     delete srv;
+    tc::pool_trim();
     return TC_OK;
 }
 

@@ -218,6 +218,9 @@ bool no_role_swap();
 // Stream-ordered allocation from the library's pool on the current device
 // (keeps freed memory for the next call); free with cudaFreeAsync.
 cudaError_t pool_alloc(void **ptr, size_t bytes, cudaStream_t st);
+// Releases the current device's pool memory above the 2 GiB it keeps (called
+// by tc_close and tc_server_close after their frees).
+void pool_trim();
 
 // tc_convolve: the one-shot convolution with scratch from the stream-ordered
 // allocator (defined beside tc_convolve_noalloc, which shares its code).

@@ -129,8 +129,11 @@ tc_status tc_open_group(size_t channels, size_t L, size_t block, int shared_ir,
 tc_status tc_open_mimo(size_t nin, size_t nout, size_t L, size_t block,
                        tc_precision precision, size_t max_push, tc_stream **out);
 
-/* Frees everything the stream owns (after its device work has finished).
- * NULL is accepted. Library housekeeping, no counterpart in the paper. */
+/* Frees everything the stream owns (after its device work has finished),
+ * then releases what the library's stream-ordered pool holds above 2 GiB on
+ * the stream's device, so that the unmapping happens here and not at another
+ * caller's next synchronisation. NULL is accepted. Library housekeeping, no
+ * counterpart in the paper. */
 tc_status tc_close(tc_stream *s);
 
 /* Back to the state right after open: no IR, nothing pushed, the history
@@ -418,7 +421,8 @@ typedef struct tc_server_stats {
  * samples of one step (0: 4M). It sizes the pinned staging buffers; a block
  * that would overflow a step waits for the next one. */
 tc_status tc_server_open(size_t mem_budget_bytes, size_t max_step_samples, tc_server **out);
-/* Stops the worker, waits for the GPU and frees everything. NULL is a no-op. */
+/* Stops the worker, waits for the GPU and frees everything (trimming the
+ * library's pool as tc_close does). NULL is a no-op. */
 tc_status tc_server_close(tc_server *srv);
 
 /* Admits a stream with IR length L (1 <= L <= 2620792) and block size block,

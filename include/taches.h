@@ -567,6 +567,20 @@ typedef enum tc_tune_knob {
 } tc_tune_knob;
 tc_status tc_set_tuning(tc_stream *s, int knob, long long value);
 
+/* Test hook: host-side failure injection. With nth > 0, the nth next time
+ * the library reaches `site` it reports a failure there instead of making the
+ * call (no CUDA call fails and no GPU fault is made); nth = 0 disarms.
+ *   TC_INJECT_PUSH_COPY    a push's input copy (tc_push_block, tc_push): the
+ *                          push returns TC_ECUDA before the stream's position
+ *                          moves, so the same push may be retried.
+ *   TC_INJECT_SERVER_STEP  a server step's launch: tc_server_step returns
+ *                          TC_ECUDA; the worker thread stops, and
+ *                          tc_server_stop returns TC_ECUDA. The step's blocks
+ *                          are dropped and their streams can be removed.
+ * Errors: TC_EINVAL for an unknown site or nth < 0. */
+enum { TC_INJECT_PUSH_COPY = 1, TC_INJECT_SERVER_STEP = 2 };
+tc_status tc_test_inject(int site, int nth);
+
 /* Kernel timing (tracing aid). With enable = 1, each later convolution kernel
  * launch of this stream is bracketed by CUDA events on the stream that runs
  * it. tc_profile_read waits for the stream, then returns the summed event

@@ -83,6 +83,7 @@ _SIGS = {
     "tc_convolve_q15": [_vp, _sz, _vp, _sz, _vp, _vp, _vp],
     "tc_convolve_tc": [_vp, _sz, _vp, _sz, _vp, _int, _vp],
     "tc_selftest_wait": [ctypes.c_ulonglong, _vp],
+    "tc_test_inject": [ctypes.c_int, ctypes.c_int],
     "tc_stream_export": [_vp, _vp, _sz, ctypes.POINTER(_sz)],
     "tc_stream_import": [_vp, _vp, _sz],
     "tc_set_tuning": [_vp, _int, ctypes.c_longlong],
@@ -367,6 +368,14 @@ def tc_last_error() -> str:
 
 def tc_status_str(st: int) -> str:
     return load().tc_status_str(st).decode()
+
+
+TC_INJECT_PUSH_COPY, TC_INJECT_SERVER_STEP = 1, 2
+
+
+def tc_test_inject(site: int, nth: int) -> None:
+    """Test hook: the nth next pass through `site` reports a failure instead of making its call (0 disarms)."""
+    _call("tc_test_inject", int(site), int(nth))
 
 
 def tc_kernel_launches() -> int:

@@ -1042,6 +1042,9 @@ tc_status push_impl(tc_stream *s, const float *x, size_t n, float *y, int mode, 
     retire_versions(s);
     TC_TRY(ensure_room(s, (long long)n + room_extra(s)));
 
+    if (tc::inject_take(TC_INJECT_PUSH_COPY))
+        return fail(TC_ECUDA, "injected failure of the push's input copy (tc_test_inject)");
+
     float *hist_at = s->hist + (s->pos - s->base);
     const size_t pitch_b = (size_t)s->cap * sizeof(float);
     const size_t row_b = n * sizeof(float);
@@ -1446,6 +1449,16 @@ const char *tc_status_str(tc_status st)
 }
 
 uint64_t tc_kernel_launches(void) { return tc::launches(); }
+
+tc_status tc_test_inject(int site, int nth)
+{
+    if (site != TC_INJECT_PUSH_COPY && site != TC_INJECT_SERVER_STEP)
+        return fail(TC_EINVAL, "tc_test_inject: unknown site %d", site);
+    if (nth < 0)
+        return fail(TC_EINVAL, "tc_test_inject: nth must be >= 0");
+    tc::inject_arm(site, nth);
+    return TC_OK;
+}
 
 tc_status tc_set_tuning(tc_stream *s, int knob, long long value)
 {

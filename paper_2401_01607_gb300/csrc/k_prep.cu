@@ -54,6 +54,22 @@ cudaError_t ir_prep_launch(const float *src, long long src_pitch, long long n, i
 }
 
 void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+namespace {
+std::atomic<int> g_inject[3];  // per site: passes left before the armed failure (0: disarmed)
+}  // namespace
+
+void inject_arm(int site, int nth) { g_inject[site].store(nth); }
+
+bool inject_take(int site)
+{
+    int v = g_inject[site].load(std::memory_order_relaxed);
+    while (v > 0) {
+        if (g_inject[site].compare_exchange_weak(v, v - 1))
+            return v == 1;
+    }
+    return false;
+}
 uint64_t launches() { return g_launches.load(std::memory_order_relaxed); }
 
 // The library's stream-ordered memory pool on each device, for the scratch of

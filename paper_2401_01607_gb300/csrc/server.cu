@@ -669,6 +669,8 @@ tc_status graph_launch(tc_server *srv, tc_server::StepBuf &b, int variant, size_
 tc_status pack_launch(tc_server *srv, tc_server::StepBuf &b)
 {
     tc::Range nvtx_range("server step: pack and launch");
+    if (tc::inject_take(TC_INJECT_SERVER_STEP))
+        return sfail(TC_ECUDA, "tc_server: injected failure of a step's launch (tc_test_inject)");
     // Plain streams go into the K1 work list; groups run after it.
     std::vector<size_t> plain, group;
     for (size_t i = 0; i < b.items.size(); ++i)
@@ -885,6 +887,17 @@ tc_status pack_launch(tc_server *srv, tc_server::StepBuf &b)
     return TC_OK;
 }
 
+// Drops the work items of a step that will not complete (after a failure):
+// their blocks are lost and their streams stop counting them as in flight,
+// so that they can be removed.
+void drop_items(tc_server *srv, tc_server::StepBuf &b)
+{
+    std::lock_guard<std::mutex> lq(srv->mu_queue);
+    for (auto &w : b.items)
+        w.s->inflight--;
+    b.items.clear();
+}
+
 // Waits for step buffer b (no lock held while waiting), then delivers its
 // outputs: finished blocks, latencies, flush tails, positions, stats.
 tc_status complete(tc_server *srv, tc_server::StepBuf &b)
@@ -980,17 +993,28 @@ tc_status step_sync(tc_server *srv, size_t *nblocks)
         if (*nblocks == 0)
             return TC_OK;
         tc_status st = pack_launch(srv, b);
-        if (st != TC_OK)
+        if (st != TC_OK) {
+            cudaDeviceSynchronize();  // whatever the failed launch had enqueued
+            drop_items(srv, b);
             return st;
+        }
     }
-    return complete(srv, b);
+    const tc_status st = complete(srv, b);
+    if (st != TC_OK)
+        drop_items(srv, b);
+    return st;
 }
 
 void worker_main(tc_server *srv)
 {
     cudaSetDevice(srv->device);
     int inflight = -1;  // step buffer launched and not yet delivered
-    auto fail = [&](const char *) { srv->worker_error = tc_last_error(); };
+    bool failed = false;
+    auto fail = [&](const char *where) {
+        const std::string msg = tc_last_error();
+        srv->worker_error = msg.empty() ? std::string(where) + " failed" : msg;
+        failed = true;
+    };
     while (true) {
         const bool stopping = srv->stop.load();
         const int nb = inflight < 0 ? 0 : 1 - inflight;
@@ -1033,13 +1057,13 @@ void worker_main(tc_server *srv)
             std::this_thread::yield();
         }
     }
-    if (inflight >= 0) {
-        // Error path: the other step may still be on the GPU.
-        cudaStreamSynchronize(srv->cs);
-        std::lock_guard<std::mutex> lq(srv->mu_queue);
-        for (auto &w : srv->buf[inflight].items)
-            w.s->inflight--;
-        srv->buf[inflight].items.clear();
+    if (failed) {
+        // Error path: wait for what is still on the GPU (either step, the
+        // groups' streams), then drop the blocks of both step buffers. They
+        // will not be delivered; tc_server_stop reports the failure.
+        cudaDeviceSynchronize();
+        for (auto &b : srv->buf)
+            drop_items(srv, b);
     }
 }
 

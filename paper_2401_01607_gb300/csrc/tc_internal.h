@@ -211,6 +211,10 @@ void set_last_error(const char *msg);
 
 // Counts kernel launches issued by this library.
 void count_launch(int n = 1);
+// Failure injection (tc_test_inject): true when this pass through `site` is
+// the one armed to fail.
+bool inject_take(int site);
+void inject_arm(int site, int nth);
 // TC_NO_ROLE_SWAP=1 in the environment keeps the one-shot convolutions in the
 // caller's roles (for comparison timings); read at each call.
 bool no_role_swap();

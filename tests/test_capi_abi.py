@@ -56,3 +56,11 @@ def test_null_arguments_are_rejected_without_gpu(lib):
     assert lib.tc_open_stream(ctypes.c_size_t(0), ctypes.c_size_t(64), None) == 1
     assert lib.tc_push_block(None, None, ctypes.c_size_t(1), None) == 1
     assert lib.tc_close(None) == 0
+
+
+def test_inject_hook_arguments_without_gpu(lib):
+    # Arming and disarming the test hook touches no device.
+    assert lib.tc_test_inject(99, 1) == 1
+    assert lib.tc_test_inject(1, -1) == 1
+    assert lib.tc_test_inject(1, 2) == 0 and lib.tc_test_inject(1, 0) == 0
+    assert lib.tc_test_inject(2, 0) == 0

@@ -1,7 +1,7 @@
 """Checkpoint / resume (tc_stream_export / tc_stream_import): a run split at a push boundary, exported,
 and resumed in a new stream gives the same bits as the unsplit run; on the gather (K1, with IR switches and a
-crossfade), the shared-IR tensor path (K2) and the MIMO tensor path (K3). The unsplit run is also checked
-against the oracle.
+crossfade), the shared-IR tensor path (K2), a mono stream on K2's row view and the MIMO tensor path (K3). The
+unsplit run is also checked against the oracle.
 """
 import numpy as np
 import pytest
@@ -105,6 +105,24 @@ def test_mimo_tensor_path_resumes_bit_exact():
     resumed = _run(opener, X, irs, L, P, split_at=3)
     assert np.array_equal(whole, resumed)
     assert rel_l2(whole, oracle.mimo(X, H[None], None, B)) <= TOL["bf16split"]
+
+
+def test_mono_row_view_resumes_bit_exact():
+    """A mono BF16-split stream on device 0 (K2 on 256-sample rows), with an IR switch whose windows run on
+    the FP32 gather."""
+    N, L, B, P = 20000, 3000, 256, 2048
+    X = synth.audio_block(1, N, 550)
+    H = [synth.decayed_ir(L, 600.0, 551 + v)[None] for v in range(2)]
+    irs = [(0, H[0], 1), (9000, H[1], 1)]
+
+    def opener():
+        return capi.tc_open_stream_ex(L, B, capi.TC_BF16_SPLIT, 0, P)
+
+    whole = _run(opener, X, irs, L, P)
+    for split in (2, 5):
+        assert np.array_equal(whole, _run(opener, X, irs, L, P, split_at=split)), split
+    ref = oracle.buffer(X[0], np.concatenate(H), np.array([0, 9000], np.int64), B)
+    assert rel_l2(whole[0], ref) <= TOL["bf16split"]
 
 
 def test_import_rejects_other_shapes_and_foreign_blobs():

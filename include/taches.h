@@ -567,6 +567,12 @@ typedef enum tc_tune_knob {
 } tc_tune_knob;
 tc_status tc_set_tuning(tc_stream *s, int knob, long long value);
 
+/* TC_CHECK_LAUNCH=1 in the environment (read at each launch): before every
+ * FP32-gather launch of a tc_stream, the host checks the ranges the kernel
+ * will touch (staged input windows 16-byte aligned and inside the history
+ * rows, tap chunks inside the IR slot, version slots, scratch) and returns
+ * TC_EINVAL with the offending range instead of launching. Off by default. */
+
 /* Test hook: host-side failure injection. With nth > 0, the nth next time
  * the library reaches `site` it reports a failure there instead of making the
  * call (no CUDA call fails and no GPU fault is made); nth = 0 disarms.

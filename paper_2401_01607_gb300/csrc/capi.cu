@@ -667,6 +667,46 @@ tc_status prof_end(tc_stream *s, long long t0, long long nout)
     return TC_OK;
 }
 
+// TC_CHECK_LAUNCH=1 in the environment (read per launch): before each K1
+// launch, the host checks the ranges the kernel will touch against the
+// stream's buffers, and a launch that would leave them returns TC_EINVAL
+// instead of running. The staged window of output tile i and tap chunk c
+// starts at n_lo = t0 + 128 i - (KC c - e) - KC + 1 and holds KC + 128
+// samples; it grows with i and shrinks with c, so the extreme windows are
+// (tile 0, last chunk) and (last tile, chunk 0).
+bool check_launches()
+{
+    const char *e = std::getenv("TC_CHECK_LAUNCH");
+    return e && e[0] == '1';
+}
+
+tc_status check_k1_launch(const tc_stream *s, const tc::K1Params &p, const tc::K1Plan &plan)
+{
+    const long long KC = tc::k1_chunk_taps(plan.variant);
+    const long long first = p.t0 - ((long long)(plan.nchunk - 1) * KC - p.e) - KC + 1;
+    const long long last_end = p.t0 + (long long)(p.ntile - 1) * tc::K1_MO + p.e + 1 + tc::K1_MO;
+    if ((first - p.base) % 4 != 0)
+        return fail(TC_EINVAL, "launch check: staged window at %lld is not 16-byte aligned (base %lld)", first,
+                    p.base);
+    if (first < p.base || last_end > p.base + p.pitch)
+        return fail(TC_EINVAL, "launch check: windows [%lld, %lld) leave the history [%lld, %lld)", first, last_end,
+                    p.base, p.base + p.pitch);
+    if ((long long)plan.nchunk * KC > s->Lpad || p.e < 0 || p.e > 3)
+        return fail(TC_EINVAL, "launch check: %d chunks of %lld taps leave the IR slot of %lld", plan.nchunk, KC,
+                    s->Lpad);
+    const long long rows = (long long)(p.nitems - 1) * p.x_item_rows + (long long)(p.nin - 1) * p.x_in_rows + 1;
+    if (rows > (long long)s->rows)
+        return fail(TC_EINVAL, "launch check: %lld history rows of %zu", rows, s->rows);
+    if ((long long)p.nout > p.y_pitch && p.nitems > 1)
+        return fail(TC_EINVAL, "launch check: output rows of %d samples at pitch %lld", p.nout, p.y_pitch);
+    for (const Version &v : s->vt)
+        if (v.slot < 0 || v.slot >= s->nslots)
+            return fail(TC_EINVAL, "launch check: version slot %d of %d", v.slot, s->nslots);
+    if ((size_t)p.nitems * p.ntile > s->counter_n || (size_t)plan.ctas * tc::K1_MO > s->partial_floats)
+        return fail(TC_EINVAL, "launch check: K1 scratch too small");
+    return TC_OK;
+}
+
 tc_status launch_k1(tc_stream *s, long long t0, long long nout, float *y, long long y_pitch)
 {
     tc::K1Params p{};
@@ -709,6 +749,8 @@ tc_status launch_k1(tc_stream *s, long long t0, long long nout, float *y, long l
     if ((size_t)p.nitems * p.ntile > s->counter_n ||
         (size_t)plan.ctas * tc::K1_MO > s->partial_floats)
         return fail(TC_EINVAL, "internal: K1 scratch too small");
+    if (check_launches())
+        TC_TRY(check_k1_launch(s, p, plan));
     TC_TRY(prof_begin(s));
     TC_CU(tc::k1_launch(p, plan, s->cs));
     return prof_end(s, t0, nout);

@@ -64,3 +64,31 @@ def test_inject_hook_arguments_without_gpu(lib):
     assert lib.tc_test_inject(1, -1) == 1
     assert lib.tc_test_inject(1, 2) == 0 and lib.tc_test_inject(1, 0) == 0
     assert lib.tc_test_inject(2, 0) == 0
+
+
+def test_product_package_never_reaches_the_oracle():
+    # The library's Python side (binding, build, generators) imports, loads or runs nothing under oracle/.
+    import ast
+    pkg_dir = os.path.join(ROOT, "paper_2401_01607_gb300")
+    for path in glob.glob(os.path.join(pkg_dir, "*.py")):
+        tree = ast.parse(open(path).read())
+        for node in ast.walk(tree):
+            if isinstance(node, ast.Import):
+                assert not any(a.name.split(".")[0] == "oracle" for a in node.names), path
+            if isinstance(node, ast.ImportFrom):
+                assert "oracle" not in (node.module or ""), path
+                assert not any(a.name == "oracle" for a in node.names), path
+        assert "liboracle" not in open(path).read(), path
+    for path in glob.glob(os.path.join(pkg_dir, "csrc", "*")):
+        assert "oracle" not in open(path).read().lower(), path
+
+
+def test_binding_raises_when_the_library_is_missing(monkeypatch, tmp_path):
+    # No CPU fallback: without libtaches.so every entry point fails loudly.
+    from paper_2401_01607_gb300 import capi
+    monkeypatch.setattr(capi, "_lib", None)
+    monkeypatch.setattr(capi, "lib_path", lambda: str(tmp_path / "libtaches.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        capi.tc_open_stream(1000, 64)
+    with pytest.raises(RuntimeError, match="not built"):
+        capi.tc_status_str(0)

@@ -14,7 +14,8 @@ pushed through the C ABI, followed by the L-1 sample flush. Useful work:
   e2e      the same step through the C ABI with host buffers (host->device
            copies of x and IRs and device->host copy of y inside the timed region)
   roofline K1 (FP32 gather) useful FLOP/s over its CUDA-event time, against the
-           FP32 FMA peak 152 SM x 128 FMA/clk x 2 FLOP x 2.07 GHz
+           FP32 FMA peak n_SM x 128 FMA/clk x 2 FLOP x 2.07 GHz (n_SM queried on
+           the device; the fraction at the sampled median SM clock beside it)
   latency  p50/p99 of one 128-sample block for all 64 streams (host buffers)
            against the real-time deadline 128/48000 s
   cpu_baseline  the FP64 oracle (buffer algorithm) on the host cores, on a
@@ -22,6 +23,11 @@ pushed through the C ABI, followed by the L-1 sample flush. Useful work:
 
 Under torchrun each rank runs its own 64 streams (weak scaling, no collective
 on the data path).
+
+Output: each side section (shared IR, MIMO, mono, Q15, one-shot, extensions,
+serving) is printed as its own JSON line first; the headline is the LAST line,
+one compact JSON object (impl "ours") that carries a few scalars of each side
+section. --full-json PATH also writes every section in full to PATH.
 """
 from __future__ import annotations
 
@@ -48,10 +54,17 @@ L_TAPS = 48_000
 BLOCK = 128
 SWAP = 24_000
 FS = synth.FS
-SM_COUNT = 152
+SM_COUNT = 152  # replaced by the device's own count once CUDA is up (set_sm_count)
 FMA_PER_CLK = 128
 SM_MAX_MHZ = 2070.0
 METRIC = "tap-MAC/s and concurrent 48 kHz real-time streams per GB300; p99 block latency"
+
+
+def set_sm_count(n: int) -> None:
+    """The FP32 and dp2a peaks scale with the SM count the device reports."""
+    global SM_COUNT
+    if n > 0:
+        SM_COUNT = int(n)
 
 
 def fp32_peak_tflops(mhz: float) -> float:
@@ -71,7 +84,7 @@ def workload_config(P: int) -> dict:
         "workload": "64 independent streams x 10 s @ 48 kHz, own IRs L=48000 swapped every 24000 samples, block 128",
         "streams": C_STREAMS, "samples_per_stream": N_SAMPLES, "L": L_TAPS, "block": BLOCK,
         "ir_swap_every": SWAP, "push_samples": P,
-        "l2": "inputs larger than L2 (x 123 MB + 20 IR versions x 64 streams 246 MB resident)",
+        "l2": "inputs > L2 (x 123 MB, 1280 IRs 246 MB)",
     }
 
 
@@ -164,9 +177,8 @@ def oracle_baseline(cores: int, nsamp: int) -> dict:
     slowest = max(times)
     macs = cores * nsamp * L_TAPS
     return {"value": macs / slowest, "unit": "tap-MAC/s", "cores": cores, "kind": "oracle",
-            "sample": f"{cores} of the 64 streams, first {nsamp} samples each (IR swaps included), "
-                      f"FP64 buffer algorithm, one stream per core; time = slowest worker "
-                      f"({slowest:.2f} s, pool wall {wall:.2f} s)",
+            "sample": f"{cores} of 64 streams x first {nsamp} samples (IR swaps incl.), FP64 buffer alg., "
+                      f"1 stream/core; slowest {slowest:.2f} s, wall {wall:.2f} s",
             "cpu_seconds": float(sum(times)),
             "samples_per_s": cores * nsamp / slowest,
             "realtime_factor_per_core": float(np.median([nsamp / t for t in times])) / FS}
@@ -755,7 +767,7 @@ def bench_q15(torch, capi, reps: int = 6) -> dict:
     out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T dp2a/s",
                        "frac": achieved / peak, "traffic": None,
                        "kernel": "k4_q15 (dp2a form) + k4_requant, whole call timed (memset, K4, requant)",
-                       "peak_basis": "152 SM x 64 dp2a/clk x 2070 MHz (max SM clock); 64/clk/SM measured by an "
+                       "peak_basis": f"{SM_COUNT} SM x 64 dp2a/clk x 2070 MHz (max SM clock); 64/clk/SM measured by an "
                                      "issue-rate loop, the same rate as 32-bit IMAD",
                        "work_counted": "one dp2a per useful tap-MAC (N x L per call)"}
     out["forms_agree_bitwise"] = bool(np.array_equal(ys["dp2a"][0], ys["imad"][0]) and
@@ -1289,6 +1301,111 @@ def traffic_from_profile(kernel_src: str) -> float | None:
     return None
 
 
+def _sig(v, n: int = 4):
+    """Rounds floats to n significant digits (recursively) to keep the headline short."""
+    if isinstance(v, float):
+        return float(f"{v:.{n}g}") if math.isfinite(v) else None
+    if isinstance(v, dict):
+        return {k: _sig(x, n) for k, x in v.items()}
+    if isinstance(v, (list, tuple)):
+        return [_sig(x, n) for x in v]
+    return v
+
+
+def _get(d, *path):
+    for k in path:
+        if not isinstance(d, dict) or k not in d:
+            return None
+        d = d[k]
+    return d
+
+
+def _tc_summary(sec: dict | None) -> dict | None:
+    """Per precision: T tap-MAC/s, roofline fraction and relative L2 of the sampled check."""
+    if not isinstance(sec, dict):
+        return None
+    if "error" in sec:
+        return {"error": sec["error"][:120]}
+    out = {}
+    for name in ("bf16split", "bf16", "fp32"):
+        r = sec.get(name)
+        if isinstance(r, dict):
+            out[name] = {"T": r["value"] / 1e12, "frac": _get(r, "roofline", "frac"),
+                         "rel_l2": _get(r, "check", "rel_l2")}
+    return out
+
+
+HEADLINE_MAX = 2500  # bytes: the driver keeps only the tail of the output
+
+
+def headline(line: dict, sections: dict) -> dict:
+    """The last output line: the contract's keys with short values, plus a few scalars of each side section
+    (the side lines printed before it hold everything)."""
+    h = dict(line)
+    rf = dict(line["roofline"])
+    rf.pop("peak_basis", None)
+    rf["peak_basis"] = f"{SM_COUNT} SM x 128 FMA/clk x 2 x 2070 MHz"
+    h["roofline"] = rf
+    cpu = line.get("cpu_baseline")
+    if cpu:
+        h["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample") if k in cpu}
+        h["cpu_baseline"]["sample"] = str(cpu.get("sample", ""))[:110]
+    e2e = line.get("e2e")
+    if e2e:
+        h["e2e"] = {k: e2e[k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step", "ms_per_step")}
+    if line.get("clocks"):
+        h["clocks"] = {k: line["clocks"][k] for k in ("sm_mhz", "sm_max_mhz", "reasons")}
+    if line.get("check"):
+        h["check"] = {k: line["check"][k] for k in ("sampled_outputs", "rel_l2", "max_abs")}
+    side = {}
+    side["shared_ir"] = _tc_summary(sections.get("shared_ir"))
+    side["mimo"] = _tc_summary(sections.get("mimo"))
+    sv = sections.get("serving")
+    if isinstance(sv, dict):
+        cap = sv.get("capacity") or {}
+        grp = sv.get("groups") or {}
+        tr = sv.get("trace") or {}
+        side["serving"] = {
+            "streams_batched": _get(cap, "batched", "streams"), "streams_per_stream": _get(cap, "per_stream", "streams"),
+            "streams_per_stream_async": _get(cap, "per_stream_async", "streams"),
+            "group_channels": {k: _get(grp, k, "channels") for k in ("bf16split", "fp32") if k in grp},
+            "trace": {"s": tr.get("seconds"), "max_active": tr.get("max_active"), "p50_ms": tr.get("p50_ms"),
+                      "p99_ms": {b: v.get("p99_ms") for b, v in (tr.get("by_block") or {}).items()},
+                      "miss": {b: v.get("miss_frac") for b, v in (tr.get("by_block") or {}).items()}}
+            if tr else None}
+        if "error" in sv:
+            side["serving"] = {"error": str(sv["error"])[:120]}
+    q = sections.get("q15")
+    if isinstance(q, dict) and "dp2a" in q:
+        side["q15"] = {"T": q["dp2a"]["tap_macs_per_s"] / 1e12, "frac": _get(q, "roofline", "frac"),
+                       "bit_exact_forms": q.get("forms_agree_bitwise"), "e2e_T": _get(q, "e2e", "value") / 1e12}
+    mono = sections.get("mono")
+    if isinstance(mono, dict) and "p99_ms" in mono:
+        side["mono"] = {"p99_ms": mono["p99_ms"], "deadline_ms": mono["deadline_ms"],
+                        "one_shot_ms": mono.get("one_shot_ms"),
+                        "tc_bf16split_frac": _get(mono, "offline", "long_signal_1s_ir", "tensor_bf16split",
+                                                  "frac_of_bf16_peak"),
+                        "tc_bf16_frac": _get(mono, "offline", "long_signal_1s_ir", "tensor_bf16", "frac_of_bf16_peak")}
+    ext = sections.get("ext")
+    if isinstance(ext, dict) and "zero_gating" in ext:
+        side["ext"] = {"gating_speedup": ext["zero_gating"]["speedup"],
+                       "gating_bit_identical": ext["zero_gating"]["bit_identical"],
+                       "xfade_overhead": _get(ext, "crossfade", "overhead")}
+    lat = sections.get("latency")
+    if isinstance(lat, dict):
+        side["block_latency"] = {"p99_ms": lat["p99_ms"], "deadline_ms": lat["deadline_ms"]}
+    h = _sig(h)
+    h["side"] = _sig({k: v for k, v in side.items() if v is not None}, 3)
+    # Drop the least important side entries until the line fits.
+    for k in ("ext", "mono", "block_latency", "q15", "mimo", "shared_ir", "serving"):
+        if len(json.dumps(h)) <= HEADLINE_MAX:
+            break
+        h["side"].pop(k, None)
+    if len(json.dumps(h)) > HEADLINE_MAX:
+        h.pop("side", None)
+    return h
+
+
 def run_reference(args, dist: Dist) -> None:
     if dist.rank != 0:
         return
@@ -1347,6 +1464,7 @@ def main():
     ap.add_argument("--shared-prec", default="bf16split,bf16,fp32", help="shared-IR section: precisions")
     ap.add_argument("--cpu-samples", type=int, default=30_000)
     ap.add_argument("--ref-samples", type=int, default=6_000)
+    ap.add_argument("--full-json", default="", help="also write every section in full to this file")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 
@@ -1371,6 +1489,7 @@ def main():
     pkg.build()
     torch.cuda.set_device(dist.local)
     dev = torch.cuda.current_device()
+    set_sm_count(torch.cuda.get_device_properties(dev).multi_processor_count)
 
     if args.only_shared:
         print(json.dumps({"shared_ir": bench_shared(torch, max(1, args.steps), max(1, args.warmup), C=args.shared_C,
@@ -1481,7 +1600,7 @@ def main():
     traffic = traffic_from_profile(os.path.join(ROOT, "paper_2401_01607_gb300", "csrc", "k1_gather.cu"))
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "k1_gather (FP32 FMA gather)",
-                "peak_basis": "152 SM x 128 FP32 FMA/clk x 2 FLOP x 2070 MHz (max SM clock)",
+                "peak_basis": f"{SM_COUNT} SM (queried) x 128 FP32 FMA/clk x 2 FLOP x 2070 MHz (max SM clock)",
                 "k1_launches": k_launches, "k1_avg_ms": k1_avg_s * 1e3,
                 "k1_share_of_step": (k_ms / args.steps) / ms_per_step if ms_per_step > 0 else None}
     if clk:
@@ -1497,7 +1616,7 @@ def main():
         tail_t = torch.empty((C_STREAMS, L_TAPS - 1), dtype=torch.float32, pin_memory=True)
         y_host, tail_host = y_t.numpy(), tail_t.numpy()
         runner.step_host(y_host, tail_host, x_pin, H_pin)  # warm
-        reps = min(args.steps, 2)
+        reps = max(1, args.steps)  # the same step count as the device-resident value
         dist.barrier()
         t0 = time.perf_counter()
         for _ in range(reps):
@@ -1570,16 +1689,23 @@ def main():
         serving = guarded(lambda: bench_serving(torch, capi, np.ascontiguousarray(w.H[:, 0]), args.trace_seconds))
     if dist.rank == 0:
         per_stream_rt = FS * L_TAPS  # tap-MAC/s one real-time stream needs
-        line = {"metric": METRIC, "value": value, "unit": "tap-MAC/s", "n_gpus": dist.world,
+        sections = {"shared_ir": shared, "mimo": mimo, "mono": mono, "q15": q15, "ext": ext, "serving": serving,
+                    "latency": latency, "autotune_push_ms_per_sample": {str(k): v for k, v in tune.items()} or None}
+        # Side sections first, one JSON line each (in full); the headline is the last line.
+        for name, sec in sections.items():
+            if sec is not None:
+                print(json.dumps({"section": name, name: sec}), flush=True)
+        line = {"impl": "ours", "metric": METRIC, "value": value, "unit": "tap-MAC/s", "n_gpus": dist.world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic", "config": workload_config(P),
-                "realtime_streams_48k": value / per_stream_rt,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "gpu_launches": int(launches), "latency": latency, "check": check, "shared_ir": shared,
-                "serving": serving, "mimo": mimo, "mono": mono, "q15": q15, "ext": ext,
-                "autotune_push_ms_per_sample": {str(k): v for k, v in tune.items()} or None}
-        print(json.dumps(line), flush=True)
+                "gpu_launches": int(launches), "check": check,
+                "realtime_streams_48k": value / per_stream_rt}
+        if args.full_json:
+            with open(args.full_json, "w") as f:
+                json.dump(dict(line, **sections), f)
+        print(json.dumps(headline(line, sections)), flush=True)
     dist.close()
 
 

@@ -290,9 +290,11 @@ tc_status tc_convolve(const float *x, size_t N, const float *h, size_t L, float 
  *     32 MiB = 8388608 floats: for example N up to 8.2 million samples with
  *     L = 4096. A call beyond it returns TC_EINVAL and names the size it
  *     would need.
+ *     N or L above 8388608 is rejected the same way before any other work.
  *   - The first call on a device looks up the array's device address with
  *     that device current. Make that first call before any CUDA stream
- *     capture.
+ *     capture. The address is kept for the life of the process: do not use
+ *     the library across cudaDeviceReset.
  *   - Every call uses the same array and clears what must start at zero.
  *     Calls that overlap on the GPU (different streams, or threads without
  *     ordering) race and give wrong results, so serialise them.

@@ -20,7 +20,10 @@
 // the library's kernels are loaded holds it until the process exits. Its
 // device address is looked up once per device, with that device current, on
 // the first call made on that device. Make that first call outside any CUDA
-// stream capture. All calls share it, and it keeps the last call's contents,
+// stream capture. The looked-up addresses are kept for the life of the
+// process: do not use this library across cudaDeviceReset (the module, and
+// with it the array, is loaded again at a new address). All calls share it,
+// and it keeps the last call's contents,
 // so each call first clears what must start at zero: the zero margins of the
 // input history, the split-sum tickets and the error word. Calls that overlap
 // on the GPU race on the array and give wrong results. Serialise them.
@@ -258,6 +261,16 @@ extern "C" tc_status tc_convolve_noalloc(const float *x, size_t N, const float *
         return na_fail(TC_EINVAL, "tc_convolve_noalloc: x, h or y is NULL");
     if (N == 0 || L == 0)
         return na_fail(TC_EINVAL, "tc_convolve_noalloc: N and L must be > 0");
+    // Neither operand can be longer than the fixed array: reject such sizes
+    // before any arithmetic on them (a size_t near 2^64, e.g. a -1 passed
+    // through an unsigned argument, would wrap when converted to long long).
+    if (N > (size_t)kScratchFloats || L > (size_t)kScratchFloats) {
+        char buf[192];
+        snprintf(buf, sizeof buf,
+                 "tc_convolve_noalloc: N=%zu or L=%zu exceeds the fixed array of %.0f MiB (use tc_convolve)", N, L,
+                 kNoAllocScratchBytes / double(1 << 20));
+        return na_fail(TC_EINVAL, buf);
+    }
     // Role swap as in tc_convolve (Sec. 3.2): the shorter operand is the IR.
     if (N < L && !tc::no_role_swap()) {
         std::swap(x, h);

@@ -1218,7 +1218,7 @@ def bench_trace(capi, pool: np.ndarray, seconds: float, budget_gb: float = 96.0)
         diag_clk = clocks.stop()
         st = capi.tc_server_get_stats(srv)
         k1 = _k1_roofline(capi.TcServerStats(), st)
-        lat, blk = capi.tc_server_latencies(srv)
+        lat, blk, parts = capi.tc_server_latencies_ex(srv)
         steplog = capi.tc_server_step_log(srv)
     finally:
         capi.tc_server_close(srv)
@@ -1238,6 +1238,15 @@ def bench_trace(capi, pool: np.ndarray, seconds: float, budget_gb: float = 96.0)
                                        "s_before_last_step": float(steplog["t_done"][-1] - steplog["t_begin"][k]),
                                        "blocks": int(steplog["blocks"][k]), "samples": int(steplog["samples"][k])},
                            "over_0.3ms": int(np.sum(dur > 0.3))}
+    # Where the latency goes: per block, ready -> taken into a step (wait), taken -> enqueued (host),
+    # enqueued -> on the host (gpu); p99 of each part, and their means over the blocks that missed.
+    if parts.size:
+        names = ("wait", "host", "gpu")
+        late = lat > blk.astype(np.float64) / FS
+        diag["parts_ms"] = {"p99": {n: float(np.percentile(parts[:, i], 99) * 1e3) for i, n in enumerate(names)},
+                            "missed_mean": {n: float(parts[late, i].mean() * 1e3) if late.any() else None
+                                            for i, n in enumerate(names)},
+                            "missed": int(late.sum())}
     m32 = blk == 32
     if m32.any():
         miss = lat[m32] > 32 / FS

@@ -503,6 +503,13 @@ tc_status tc_server_get_stats(tc_server *srv, tc_server_stats *st);
  * block's stream into block (may be NULL), then forgets them. Flush tails are
  * not recorded. */
 tc_status tc_server_latencies(tc_server *srv, double *out, uint32_t *block, size_t cap, size_t *n_out);
+/* As tc_server_latencies, and if parts is not NULL it also receives, per
+ * block, three floats (seconds) that add up to its latency: ready -> taken
+ * into a step by the worker, taken -> the step's copies and kernels enqueued,
+ * enqueued -> results on the host. parts holds 3 * cap floats (caller-owned).
+ * The paper has no counterpart (tracing of the serving loop). */
+tc_status tc_server_latencies_ex(tc_server *srv, double *out, uint32_t *block, float *parts, size_t cap,
+                                 size_t *n_out);
 /* Monotonic clock of the poll timestamps (seconds). */
 double tc_server_clock(void);
 /* Options (value 0 or 1), set at any time:

@@ -22,6 +22,7 @@
 // add/set_ir upload on their own CUDA stream and take the state mutex only
 // briefly; steps take the state mutex while packing and delivering.
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <cmath>
 #include <chrono>
@@ -224,6 +225,9 @@ struct tc_server {
     // worker thread.
     std::deque<double> lat;
     std::deque<uint32_t> lat_block;  // nominal block size of each recorded latency
+    // Parts of each recorded latency: ready -> collected into a step, collected
+    // -> copies and kernels enqueued, enqueued -> results on the host.
+    std::deque<std::array<float, 3>> lat_parts;
     // Step log (tracing): the last kLogSteps steps, oldest first once full.
     std::vector<tc_server_step_rec> steplog;
     size_t steplog_next = 0;
@@ -951,6 +955,8 @@ tc_status complete(tc_server *srv, tc_server::StepBuf &b)
             } else {
                 srv->lat.push_back(t_done - blk.t_submit);
                 srv->lat_block.push_back((uint32_t)s->block);
+                srv->lat_parts.push_back({(float)(b.t_begin - blk.t_submit), (float)(b.t_launch - b.t_begin),
+                                          (float)(t_done - b.t_launch)});
                 srv->tap_macs += (double)blk.n * (double)s->L * (double)C;
                 if (!s->discard) {
                     OutBlock o;
@@ -1352,7 +1358,8 @@ tc_status tc_server_submit_many(tc_server *srv, size_t count, const uint64_t *id
     return TC_OK;
 }
 
-tc_status tc_server_latencies(tc_server *srv, double *out, uint32_t *block, size_t cap, size_t *n_out)
+tc_status tc_server_latencies_ex(tc_server *srv, double *out, uint32_t *block, float *parts, size_t cap,
+                                 size_t *n_out)
 {
     if (!srv || !n_out || (cap && !out))
         return sfail(TC_EINVAL, "tc_server_latencies: bad arguments");
@@ -1361,10 +1368,20 @@ tc_status tc_server_latencies(tc_server *srv, double *out, uint32_t *block, size
     std::copy(srv->lat.begin(), srv->lat.begin() + (long)n, out);
     if (block)
         std::copy(srv->lat_block.begin(), srv->lat_block.begin() + (long)n, block);
+    if (parts)
+        for (size_t i = 0; i < n; ++i)
+            for (int k = 0; k < 3; ++k)
+                parts[3 * i + (size_t)k] = srv->lat_parts[i][(size_t)k];
     srv->lat.erase(srv->lat.begin(), srv->lat.begin() + (long)n);
     srv->lat_block.erase(srv->lat_block.begin(), srv->lat_block.begin() + (long)n);
+    srv->lat_parts.erase(srv->lat_parts.begin(), srv->lat_parts.begin() + (long)n);
     *n_out = n;
     return TC_OK;
+}
+
+tc_status tc_server_latencies(tc_server *srv, double *out, uint32_t *block, size_t cap, size_t *n_out)
+{
+    return tc_server_latencies_ex(srv, out, block, nullptr, cap, n_out);
 }
 
 tc_status tc_server_attach_source(tc_server *srv, uint64_t id, const float *x, size_t n, double t0, double fs)

@@ -973,6 +973,7 @@ def bench_capacity(torch, capi, H64: np.ndarray, pool: np.ndarray, paced_s: floa
     srv = capi.tc_server_open(200 << 30, 1 << 22)
     ids: list[int] = []
     try:
+        capi.tc_server_reserve(srv, 24 << 30)  # about 8000 such streams: no pool growth during the paced runs
         def set_count(M, fresh=False):
             if fresh:
                 for sid in ids:
@@ -1111,8 +1112,6 @@ def bench_groups(capi, paced_s: float = 1.5, C: int = 128, L: int = 96_000, B: i
     for name in precisions:
         code = {"fp32": capi.TC_FP32, "bf16": capi.TC_BF16, "bf16split": capi.TC_BF16_SPLIT}[name]
         runs, best = {}, 0
-        clocks = ClockSampler(0)
-        clocks.start()
         def rung(G):
             """One paced run of G groups on a fresh server; None if G groups are not admitted."""
             srv = capi.tc_server_open(240 << 30, 1 << 22)
@@ -1164,8 +1163,11 @@ def bench_groups(capi, paced_s: float = 1.5, C: int = 128, L: int = 96_000, B: i
             if not r["pass"]:
                 break
             best = G
-        out[name] = {"groups": best, "channels": best * C, "runs": runs, "clocks": clocks.stop()}
+        out[name] = {"groups": best, "channels": best * C, "runs": runs}
     return out
+
+
+RESERVE_TRACE = 12 << 30  # device bytes mapped into the trace server's pool before the replay
 
 
 def bench_trace(capi, pool: np.ndarray, seconds: float, budget_gb: float = 96.0) -> dict:
@@ -1180,9 +1182,10 @@ def bench_trace(capi, pool: np.ndarray, seconds: float, budget_gb: float = 96.0)
     irs = {t.sid: [make(t.L, t.tau, sd) for sd in t.ir_seeds] for t in tr}
     srv = capi.tc_server_open(int(budget_gb * (1 << 30)), 1 << 22)
     waits, max_active, live = 0, 0, {}
-    clocks = ClockSampler(0)
     try:
-        clocks.start()
+        # The trace's streams hold about 6-8 GB at their peak: mapped before the replay, so that admissions
+        # take memory the pool already holds (growing it while steps run stalls them for about 1 ms).
+        capi.tc_server_reserve(srv, RESERVE_TRACE)
         capi.tc_server_start(srv)
         t_start = capi.tc_server_clock() + 0.02
         t_end = t_start + seconds
@@ -1215,7 +1218,6 @@ def bench_trace(capi, pool: np.ndarray, seconds: float, budget_gb: float = 96.0)
                     del live[sid]
             time.sleep(0.001)
         capi.tc_server_stop(srv)
-        diag_clk = clocks.stop()
         st = capi.tc_server_get_stats(srv)
         k1 = _k1_roofline(capi.TcServerStats(), st)
         lat, blk, parts = capi.tc_server_latencies_ex(srv)
@@ -1225,7 +1227,7 @@ def bench_trace(capi, pool: np.ndarray, seconds: float, budget_gb: float = 96.0)
     arrived = sum(1 for t in tr if t.arrival_s < seconds)
     # Diagnostics: step durations (the last steps of the log) and how the
     # 32-sample blocks' misses spread over the run (completion order, 20 bins).
-    diag = {"clocks": diag_clk}
+    diag = {"reserved_gb": RESERVE_TRACE / (1 << 30)}
     if len(steplog):
         dur = (steplog["t_done"] - steplog["t_begin"]) * 1e3
         gpu = (steplog["t_done"] - steplog["t_launch"]) * 1e3
@@ -1455,7 +1457,7 @@ def main():
     ap.add_argument("--only-shared", action="store_true", help="run only the shared-IR section")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving section")
     ap.add_argument("--only-serving", action="store_true", help="run only the serving section")
-    ap.add_argument("--trace-seconds", type=float, default=15.0)
+    ap.add_argument("--trace-seconds", type=float, default=60.0)
     ap.add_argument("--only-trace", action="store_true", help="run only the serving trace")
     ap.add_argument("--no-mimo", action="store_true", help="skip the MIMO section")
     ap.add_argument("--no-q15", action="store_true", help="skip the exact Q15 section")

@@ -91,6 +91,7 @@ _SIGS = {
     "tc_profile_read": [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_u64), ctypes.POINTER(ctypes.c_double)],
     "tc_server_open": [_sz, _sz, ctypes.POINTER(_vp)],
     "tc_server_close": [_vp],
+    "tc_server_reserve": [_vp, _sz],
     "tc_server_add": [_vp, _sz, _sz, _vp, _sz, _int, ctypes.POINTER(_u64)],
     "tc_open_stream_ex": [_sz, _sz, _int, _int, _sz, ctypes.POINTER(_vp)],
     "tc_server_add_group": [_vp, _sz, _sz, _sz, _vp, _sz, _int, _int, ctypes.POINTER(_u64)],
@@ -403,6 +404,12 @@ def tc_server_open(mem_budget_bytes: int, max_step_samples: int = 0) -> int:
 
 def tc_server_close(srv: int) -> None:
     _call("tc_server_close", srv)
+
+
+def tc_server_reserve(srv: int, nbytes: int) -> None:
+    """Maps nbytes of device memory into the server's pool now, so that later admissions do not map
+    memory while steps run."""
+    _call("tc_server_reserve", srv, int(nbytes))
 
 
 def tc_server_add(srv: int, L: int, block: int, h, flags: int = 0) -> int:

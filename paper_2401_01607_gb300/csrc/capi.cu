@@ -746,6 +746,10 @@ tc_status launch_k1(tc_stream *s, long long t0, long long nout, float *y, long l
     p.counter = s->counter;
     p.err = s->d_err;
     p.zero_skip = s->zero_skip ? 1 : 0;
+    if (s->pos_end_hint >= 0) {  // a flush: the input ended at pos_end_hint
+        p.has_end = 1;
+        p.x_end = s->pos_end_hint;
+    }
     if ((size_t)p.nitems * p.ntile > s->counter_n ||
         (size_t)plan.ctas * tc::K1_MO > s->partial_floats)
         return fail(TC_EINVAL, "internal: K1 scratch too small");

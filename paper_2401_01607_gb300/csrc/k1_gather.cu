@@ -199,6 +199,8 @@ __global__ void __launch_bounds__(K1_THREADS, 4)
     // Crossfade ramps (EXT instances only; the others compile without them).
     const int *vrm = (EXT && p.vramp) ? p.vramp + (long long)item * p.vt_item : nullptr;
     const int nv = p.nver[p.vt_item ? item : 0];
+    // After the last input sample every sample is zero (a flush): nothing past x_end spawns a tache.
+    const long long x_end = p.has_end ? p.x_end : LLONG_MAX;
 
     if (tid == 0) {
         mbar_init(&bar[0], 1);
@@ -235,7 +237,8 @@ __global__ void __launch_bounds__(K1_THREADS, 4)
         const int ra = (EXT && vrm && v > 0) ? vrm[v] : 1;
         const int rb = (EXT && vrm && v + 1 < nv) ? vrm[v + 1] : 1;
         const long long b = (bn == LLONG_MAX) ? LLONG_MAX : bn + rb - 1;
-        if (b <= n_lo || a >= n_end)
+        const long long be = b < x_end ? b : x_end;  // samples of this version that can be nonzero: [a, be)
+        if (be <= n_lo || a >= n_end)
             continue;  // this version spawned no tache that reaches the tile through this chunk
         // Two parts on two mbarriers (chunks of 4 passes or more): part A =
         // the IR taps of passes [0, PA) and the input samples they read,
@@ -299,13 +302,13 @@ __global__ void __launch_bounds__(K1_THREADS, 4)
         // Passes this thread runs for this version: pass p covers sub-segment
         // seg = 32 p + s, i.e. taps kc0 + 20 seg + [0, 19], and reads samples
         // out_hi - kc0 - 20 seg - [0, 34]. It is needed iff
-        //   that range meets [a, b):  20 seg <= out_hi - kc0 - a  and
-        //                             20 seg >  out_hi - kc0 - 34 - b,
+        //   that range meets [a, be): 20 seg <= out_hi - kc0 - a  and
+        //                             20 seg >  out_hi - kc0 - 34 - be,
         //   and its first tap is inside the IR: kc0 + 20 seg <= L - 1.
         // Those bounds are solved once here instead of tested per pass.
         const long long seg_hi = min(floor_div(out_hi - kc0 - a, C::SEG), floor_div((long long)p.L - 1 - kc0, C::SEG));
         const long long seg_lo =
-            (b == LLONG_MAX) ? -(1LL << 40) : floor_div(out_hi - kc0 - (15 + C::SEG - 1) - b, C::SEG) + 1;
+            (be == LLONG_MAX) ? -(1LL << 40) : floor_div(out_hi - kc0 - (15 + C::SEG - 1) - be, C::SEG) + 1;
         const int p_lo = (int)max(0LL, min((long long)P, -floor_div(s - seg_lo, 32)));
         const int p_hi = (int)max(-1LL, min((long long)P - 1, floor_div(seg_hi - s, 32)));
         int pass = p_lo;
@@ -405,15 +408,27 @@ __global__ void __launch_bounds__(K1_THREADS, 4)
     if (tid < C::MO) {
         // Fixed pairwise tree over the chunk sums, per output column: a
         // binary-counter stack in this thread's column (older block on the left).
-        for (int c = 0; c < ctot; ++c) {
-            float carry = __ldcg(part + (long long)c * C::MO + o);
-            int cc = c, l = 0;
-            while (cc & 1) {
-                carry = lv[l * C::MO + o] + carry;
-                cc >>= 1;
-                ++l;
+        // The sums are loaded eight at a time, so that a tile with hundreds of
+        // chunk-tasks (long IRs, small chunks) waits for one L2 round trip per
+        // eight sums instead of one per sum; the order of the adds is unchanged.
+        for (int cb = 0; cb < ctot; cb += 8) {
+            float v8[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                v8[j] = (cb + j < ctot) ? __ldcg(part + (long long)(cb + j) * C::MO + o) : 0.f;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                if (cb + j >= ctot)
+                    break;
+                float carry = v8[j];
+                int cc = cb + j, l = 0;
+                while (cc & 1) {
+                    carry = lv[l * C::MO + o] + carry;
+                    cc >>= 1;
+                    ++l;
+                }
+                lv[l * C::MO + o] = carry;
             }
-            lv[l * C::MO + o] = carry;
         }
         float y = 0.f;
         bool first = true;

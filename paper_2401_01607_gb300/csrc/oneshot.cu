@@ -180,6 +180,8 @@ tc_status run_oneshot(const char *who, const float *x, size_t N, const float *h,
     p.partial = part;
     p.counter = counters;
     p.err = err;
+    p.has_end = 1;  // x ends at N: the taps past it are skipped
+    p.x_end = Nl;
     const long long ny = Nl + Ll - 1;
     const long long piece = lay.piece_tiles * tc::K1_MO;
     for (long long t0 = 0; t0 < ny; t0 += piece) {

@@ -90,6 +90,7 @@ struct SStream {
     int nslots = 3;
     bool ended = false;   // a short block was submitted: input is over
     bool flushed = false;
+    long long x_end = -1;  // once flushed: input samples before the tail (later samples are zero)
     bool discard = false;  // keep no output blocks (latency is still recorded)
     // Group (tc_server_add_group): `channels` rows sharing one IR. Blocks hold
     // [channels][n] samples; the group stream of the C ABI (K2 on the tensor
@@ -823,6 +824,10 @@ tc_status pack_launch(tc_server *srv, tc_server::StepBuf &b)
         p.partial = srv->scratch + si;
         p.counter = srv->counters + ci;
         p.err = d_err;
+        if (s->x_end >= 0) {  // the flush's zero blocks: taps that read only them are skipped
+            p.has_end = 1;
+            p.x_end = s->x_end;
+        }
         si += (size_t)p.ntile * p.nchunk * tc::K1_MO;
         ci += (size_t)p.ntile;
         st_items[j] = p;
@@ -1186,6 +1191,39 @@ tc_status tc_server_close(tc_server *srv)
     return TC_OK;
 }
 
+tc_status tc_server_reserve(tc_server *srv, size_t bytes)
+{
+    if (!srv)
+        return sfail(TC_EINVAL, "tc_server_reserve: server is NULL");
+    bytes = std::min(bytes, srv->budget);
+    // The pool keeps whatever it maps (release threshold: everything), so
+    // allocating and freeing leaves the memory in it for later admissions.
+    // Pieces of 64 MiB: the stream states carved from them later are at most
+    // a few tens of MiB each.
+    constexpr size_t kPiece = (size_t)64 << 20;
+    std::lock_guard<std::mutex> la(srv->mu_admin);
+    S_CU(cudaSetDevice(srv->device));
+    std::vector<void *> got;
+    got.reserve(bytes / kPiece + 1);
+    cudaError_t e = cudaSuccess;
+    for (size_t done = 0; done < bytes && e == cudaSuccess; done += kPiece) {
+        void *ptr = nullptr;
+        e = cudaMallocFromPoolAsync(&ptr, std::min(kPiece, bytes - done), srv->pool, srv->admin);
+        if (e == cudaSuccess)
+            got.push_back(ptr);
+    }
+    for (void *ptr : got)
+        cudaFreeAsync(ptr, srv->admin);
+    const cudaError_t es = cudaStreamSynchronize(srv->admin);
+    if (e != cudaSuccess || es != cudaSuccess) {
+        cudaGetLastError();
+        const cudaError_t w = e != cudaSuccess ? e : es;
+        return sfail(w == cudaErrorMemoryAllocation ? TC_ENOMEM : TC_ECUDA,
+                     std::string("tc_server_reserve: ") + cudaGetErrorString(w));
+    }
+    return TC_OK;
+}
+
 tc_status tc_server_add(tc_server *srv, size_t L, size_t block, const float *h, size_t n, int flags, uint64_t *id)
 {
     if (!srv || !id || !h || L == 0 || block == 0 || n == 0 || n > L)
@@ -1512,6 +1550,7 @@ tc_status tc_server_flush(tc_server *srv, uint64_t id, float *y, size_t cap, siz
     // (other streams' pending blocks ride along).
     {
         std::lock_guard<std::mutex> lq(srv->mu_queue);
+        s->x_end = s->pos + queued_samples(s);  // real input: launched + still queued
         s->tail_out.assign((size_t)(C * tail), 0.f);
         s->tail_fill = 0;
         for (long long off = 0; off < tail; off += s->block) {

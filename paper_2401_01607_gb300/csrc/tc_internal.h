@@ -85,6 +85,8 @@ struct K1Params {
     unsigned *counter;       // [nitems][ntile], zero between launches
     int *err;                // device error word
     int zero_skip;           // 1: skip passes whose staged input is all zero (exact)
+    int has_end;             // 1: input samples n >= x_end are zero (the flush after the last input): chunks
+    long long x_end;         //    and passes that read only such samples are skipped (exact)
 };
 
 // Variants: passes of K1_SEG taps per thread per chunk (KC = 32 * 20 * P).

@@ -44,12 +44,15 @@ def _oracle(t, x, H, vstart):
     return oracle.buffer(x, H, np.asarray(vstart, np.int64), t.block)
 
 
-def _run(streams, order_seed=None, options=()):
+def _run(streams, order_seed=None, options=(), reserve=0):
     """Runs the streams through one server with manual steps. order_seed None:
     one stream at a time (alone); else interleaved at random (mix).
-    options: (option, value) pairs. Returns {index: y[N + L - 1]}."""
+    options: (option, value) pairs. reserve: bytes mapped into the server's
+    pool before the first admission. Returns {index: y[N + L - 1]}."""
     srv = capi.tc_server_open(8 << 30, 1 << 20)
     try:
+        if reserve:
+            capi.tc_server_reserve(srv, reserve)
         for opt, val in options:
             capi.tc_server_set_option(srv, opt, val)
         ids = [capi.tc_server_add(srv, t.L, t.block, H[0]) for (t, x, H, vs) in streams]
@@ -128,6 +131,15 @@ def test_alone_equals_mix_equals_oracle():
         assert e_am <= TOL["fp32"], (i, e_am)
 
 
+def test_reserved_pool_mix_equals_oracle():
+    """With the pool mapped up front (tc_server_reserve), admissions carve their state from it: the mix
+    still matches the oracle, and the budget accounting returns to zero after the removals."""
+    streams = _small_trace(k=5, seed=11)
+    mix = _run(streams, order_seed=3, reserve=256 << 20)
+    for i, s in enumerate(streams):
+        assert rel_l2(mix[i], _oracle(*s)) <= TOL["fp32"], i
+
+
 def test_worker_thread_continuous_batching():
     """Blocks submitted while the worker runs steps join later steps; every
     result still matches the oracle and every block's latency is recorded."""
@@ -170,9 +182,13 @@ def test_worker_thread_continuous_batching():
                     outs[i].append(y[:n].copy())
         capi.tc_server_stop(srv)
         assert sum(map(len, outs)) == total
-        lat, blk = capi.tc_server_latencies(srv)
+        lat, blk, parts = capi.tc_server_latencies_ex(srv)
         assert lat.size == total and np.all(lat >= 0)
         assert set(blk.tolist()) <= {t.block for (t, x, H, vs) in streams}
+        # The three parts (ready -> taken, taken -> enqueued, enqueued -> on the host) add up to each latency
+        # (float32 parts of float64 latencies), and only the first can be negative: never.
+        assert parts.shape == (total, 3) and np.all(parts >= 0)
+        assert np.allclose(parts.astype(np.float64).sum(axis=1), lat, rtol=1e-5, atol=1e-6)
         st = capi.tc_server_get_stats(srv)
         assert st.blocks == total and st.steps <= total
         for i, s in enumerate(streams):

@@ -113,6 +113,7 @@ struct SStream {
     bool vt_dirty = true;
     size_t bytes = 0;            // device footprint
     std::deque<Block> pending;   // guarded by the queue mutex
+    bool in_ready = false;       // in the server's ready queue (queue mutex): pending is not empty
     std::deque<OutBlock> done;   // guarded by the queue mutex
     std::vector<float> tail_out; // output of the flush's zero blocks
 
@@ -143,8 +144,11 @@ struct tc_server {
     std::condition_variable cv;
     std::map<uint64_t, std::unique_ptr<SStream>> streams;
     uint64_t next_id = 1;
-    uint64_t rr = 0;  // first stream id visited by the next step
     size_t npending = 0;  // blocks queued over all streams (queue mutex)
+    // Streams with queued blocks, in the order they became ready (queue
+    // mutex). A step visits only these, not every admitted stream, and a
+    // stream whose blocks did not all fit goes back to the end (round robin).
+    std::deque<SStream *> ready;
     // Live sources by next ready time (queue mutex).
     std::priority_queue<std::pair<double, uint64_t>, std::vector<std::pair<double, uint64_t>>,
                         std::greater<std::pair<double, uint64_t>>>
@@ -211,6 +215,7 @@ struct tc_server {
     double last_done = 0.0;
     float *ir_stage = nullptr;
     size_t ir_stage_floats = 0;
+    float *ir_stage_host = nullptr;  // page-locked copy of the IR being uploaded (kMaxL floats)
 
     // Worker.
     std::thread worker;
@@ -377,7 +382,14 @@ tc_status upload_ir(tc_server *srv, SStream *s, int slot, const float *h, size_t
         S_CU(cudaMalloc(&srv->ir_stage, n * sizeof(float)));
         srv->ir_stage_floats = n;
     }
-    S_CU(cudaMemcpyAsync(srv->ir_stage, h, n * sizeof(float), cudaMemcpyHostToDevice, srv->admin));
+    // Through page-locked memory: one direct DMA instead of a driver-staged
+    // copy of pageable memory that shares the copy engines with the steps.
+    const float *src = h;
+    if (srv->ir_stage_host && n <= kMaxL) {
+        std::memcpy(srv->ir_stage_host, h, n * sizeof(float));
+        src = srv->ir_stage_host;
+    }
+    S_CU(cudaMemcpyAsync(srv->ir_stage, src, n * sizeof(float), cudaMemcpyHostToDevice, srv->admin));
     float *dst = s->ir + (size_t)slot * 4 * (size_t)s->Lpad;
     S_CU(tc::ir_prep_launch(srv->ir_stage, (long long)n, (long long)n, 1, dst, 4 * s->Lpad, s->Lpad, s->Lpad,
                             srv->admin));
@@ -526,6 +538,18 @@ tc_status grow(tc_server *srv, tc_server::StepBuf &b, size_t items, size_t scrat
     return TC_OK;
 }
 
+// Appends block b to the queue of s, and s to the ready queue if it was not
+// there. Caller holds the queue mutex.
+void enqueue(tc_server *srv, SStream *s, Block &&b)
+{
+    s->pending.push_back(std::move(b));
+    srv->npending++;
+    if (!s->in_ready) {
+        s->in_ready = true;
+        srv->ready.push_back(s);
+    }
+}
+
 // Moves every live-source block whose ready time has passed into its
 // stream's queue. Caller holds the queue mutex. Returns the next ready time
 // (+inf if no source is live).
@@ -554,8 +578,7 @@ double release_sources(tc_server *srv, double now)
         }
         b.t_submit = s->src_ready(s->src_next);
         b.tail = false;
-        s->pending.push_back(std::move(b));
-        srv->npending++;
+        enqueue(srv, s, std::move(b));
         s->src_next++;
         if (s->src_next * s->block < s->src_n)
             srv->src_heap.push({s->src_ready(s->src_next), id});
@@ -565,10 +588,10 @@ double release_sources(tc_server *srv, double now)
     return srv->src_heap.empty() ? 1e300 : srv->src_heap.top().first;
 }
 
-// Takes the queued blocks of every stream (up to kMerge consecutive blocks of
-// a stream as one item) into step buffer b. Round robin: when a step is full,
-// the next one starts at the first stream that did not fit. Caller holds
-// mu_state. Returns the number of blocks taken.
+// Takes the queued blocks of every ready stream (up to kMerge consecutive
+// blocks of a stream as one item) into step buffer b. Round robin: when a
+// step is full, the next one starts with the streams that did not fit.
+// Caller holds mu_state. Returns the number of blocks taken.
 size_t collect(tc_server *srv, tc_server::StepBuf &b)
 {
     tc::Range nvtx_range("server step: collect");
@@ -580,18 +603,16 @@ size_t collect(tc_server *srv, tc_server::StepBuf &b)
     release_sources(srv, b.t_begin);
     if (srv->npending == 0)
         return 0;
-    bool capped = false;
+    // take(s): up to kMerge queued blocks of s as one item; false if a block
+    // of s did not fit the step (it stays queued).
     auto take = [&](SStream *s) {
-        if (s->pending.empty())
-            return;
+        bool fits = true;
         tc_server::Item it{s, {}, (long long)b.total, 0};
         while (!s->pending.empty() && (int)it.blocks.size() < kMerge) {
             Block &blk = s->pending.front();
             const size_t fl = (size_t)(blk.n * s->channels);  // packed floats
             if (b.total + fl > srv->max_step_samples) {
-                if (!capped)
-                    srv->rr = s->id;
-                capped = true;
+                fits = false;
                 break;  // stays for the next step
             }
             b.total += fl;
@@ -605,14 +626,26 @@ size_t collect(tc_server *srv, tc_server::StepBuf &b)
             s->inflight++;
             b.items.push_back(std::move(it));
         }
+        return fits;
     };
-    const auto start = srv->streams.lower_bound(srv->rr);
-    for (auto it = start; it != srv->streams.end(); ++it)
-        take(it->second.get());
-    for (auto it = srv->streams.begin(); it != start; ++it)
-        take(it->second.get());
-    if (!capped)
-        srv->rr = 0;
+    // Visit the streams that were ready when the step began, in order. A
+    // stream with more than kMerge blocks queued goes to the back; streams
+    // whose blocks did not fit lead the next step, in their order.
+    std::vector<SStream *> unfit;
+    const size_t nready = srv->ready.size();
+    for (size_t k = 0; k < nready; ++k) {
+        SStream *s = srv->ready.front();
+        srv->ready.pop_front();
+        const bool fits = take(s);
+        if (s->pending.empty())
+            s->in_ready = false;
+        else if (!fits)
+            unfit.push_back(s);
+        else
+            srv->ready.push_back(s);
+    }
+    for (auto it = unfit.rbegin(); it != unfit.rend(); ++it)
+        srv->ready.push_front(*it);
     return nblocks;
 }
 
@@ -1130,6 +1163,7 @@ tc_status tc_server_open(size_t mem_budget_bytes, size_t max_step_samples, tc_se
     // serving would need a cudaFree, which waits for the whole device.
     S_CU(cudaMalloc(&srv->ir_stage, kMaxL * sizeof(float)));
     srv->ir_stage_floats = kMaxL;
+    S_CU(cudaHostAlloc(reinterpret_cast<void **>(&srv->ir_stage_host), kMaxL * sizeof(float), cudaHostAllocDefault));
     // Size the step buffers for a few thousand streams and load the kernels
     // now, so that the first steps do not pay for allocations or module loads.
     for (auto &b : srv->buf)
@@ -1180,6 +1214,7 @@ tc_status tc_server_close(tc_server *srv)
     cudaFree(srv->scratch);
     cudaFree(srv->counters);
     cudaFree(srv->ir_stage);
+    cudaFreeHost(srv->ir_stage_host);
     if (srv->pool)
         cudaMemPoolDestroy(srv->pool);
     if (srv->admin)
@@ -1389,8 +1424,7 @@ tc_status tc_server_submit_many(tc_server *srv, size_t count, const uint64_t *id
         b.n = (long long)ns[i];
         b.t_submit = t_ready ? t_ready[i] : now;
         b.tail = false;
-        s->pending.push_back(std::move(b));
-        srv->npending++;
+        enqueue(srv, s, std::move(b));
     }
     srv->cv.notify_one();
     return TC_OK;
@@ -1560,8 +1594,7 @@ tc_status tc_server_flush(tc_server *srv, uint64_t id, float *y, size_t cap, siz
             b.src = nullptr;
             b.t_submit = now_s();
             b.tail = true;
-            s->pending.push_back(std::move(b));
-            srv->npending++;
+            enqueue(srv, s, std::move(b));
         }
         s->ended = true;
         s->flushed = true;
@@ -1603,6 +1636,8 @@ tc_status tc_server_remove(tc_server *srv, uint64_t id)
             return sfail(TC_EINVAL, "tc_server_remove: unknown stream");
         if (!it->second->pending.empty() || it->second->inflight > 0)
             return sfail(TC_ESTATE, "tc_server_remove: the stream still has blocks queued or running");
+        if (it->second->in_ready)  // not reached (a ready stream has queued blocks); kept for safety
+            srv->ready.erase(std::find(srv->ready.begin(), srv->ready.end(), it->second.get()));
         s = std::move(it->second);
         srv->streams.erase(it);
     }

@@ -1167,7 +1167,7 @@ def bench_groups(capi, paced_s: float = 1.5, C: int = 128, L: int = 96_000, B: i
     return out
 
 
-RESERVE_TRACE = 12 << 30  # device bytes mapped into the trace server's pool before the replay
+RESERVE_TRACE = 12 << 30  # device bytes reserved for the trace server's streams before the replay
 
 
 def bench_trace(capi, pool: np.ndarray, seconds: float, budget_gb: float = 96.0) -> dict:
@@ -1183,8 +1183,8 @@ def bench_trace(capi, pool: np.ndarray, seconds: float, budget_gb: float = 96.0)
     srv = capi.tc_server_open(int(budget_gb * (1 << 30)), 1 << 22)
     waits, max_active, live = 0, 0, {}
     try:
-        # The trace's streams hold about 6-8 GB at their peak: mapped before the replay, so that admissions
-        # take memory the pool already holds (growing it while steps run stalls them for about 1 ms).
+        # The trace's streams hold about 6-8 GB at their peak: reserved before the replay, so that admissions
+        # carve their state from it (growing the pool while steps run stalled them for 1-65 ms).
         capi.tc_server_reserve(srv, RESERVE_TRACE)
         capi.tc_server_start(srv)
         t_start = capi.tc_server_clock() + 0.02

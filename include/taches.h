@@ -426,16 +426,18 @@ tc_status tc_server_open(size_t mem_budget_bytes, size_t max_step_samples, tc_se
 /* Stops the worker, waits for the GPU and frees everything (trimming the
  * library's pool as tc_close does). NULL is a no-op. */
 tc_status tc_server_close(tc_server *srv);
-/* Maps min(bytes, budget) of device memory into the server's memory pool now
- * (allocated and freed on its admin CUDA stream, then waited for), where the
- * states of later tc_server_add admissions are carved from. Without it the
- * pool grows inside tc_server_add, and mapping new device memory while steps
- * run stalled those steps: measured on the serving trace, steps of about
- * 1 ms (against 0.1 ms) coincided with admissions, and none were left once
- * the pool held enough. Call it before serving (any time is safe); the
- * memory stays with the server until tc_server_close. The paper has no
- * counterpart (serving). Errors: TC_EINVAL (NULL); TC_ENOMEM (the device has
- * no room); TC_ECUDA. */
+/* Reserves min(bytes, budget) bytes of device memory for the states of
+ * later tc_server_add admissions: one allocation made now, carved up by the
+ * server (first fit; a removed stream's range is reused once the steps that
+ * read it have completed). Without it each admission allocates from the
+ * server's memory pool, which maps new device memory when it has to grow, and
+ * mapping memory while steps run stalled them: measured on the serving trace,
+ * steps of about 1 ms (against 0.1 ms), and once 65 ms, coincided with
+ * admissions. Admissions that do not fit the reservation still fall back to
+ * the pool. Call it once, before serving; the memory stays with the server
+ * until tc_server_close. Groups (tc_server_add_group) do not use it. The paper
+ * has no counterpart (serving). Errors: TC_EINVAL (NULL); TC_ESTATE (called
+ * before); TC_ENOMEM (the device has no room); TC_ECUDA. */
 tc_status tc_server_reserve(tc_server *srv, size_t bytes);
 
 /* Admits a stream with IR length L (1 <= L <= 2620792) and block size block,

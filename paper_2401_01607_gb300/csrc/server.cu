@@ -101,6 +101,7 @@ struct SStream {
     cudaEvent_t gdone = nullptr;  // the group's push of the current step is done
     std::mutex gmu;           // the group stream: worker pushes vs IR uploads
     long long tail_fill = 0;  // flush tail samples delivered so far (per row)
+    size_t arena_off = 0, arena_len = 0;  // the stream's range of the server's arena (len 0: pool memory)
     float *hist = nullptr;       // [cap]
     float *ir = nullptr;         // [nslots][4][Lpad]
     DevTable *d_vt = nullptr;
@@ -131,8 +132,26 @@ struct SStream {
 
 }  // namespace
 
+// Device memory reserved by tc_server_reserve: one allocation that stream
+// states are carved from by first fit, so that admitting a stream never maps
+// device memory while steps run. A removed stream's range is reused only once
+// an event recorded after the steps that read it has completed.
+struct Arena {
+    char *base = nullptr;
+    size_t size = 0;
+    std::map<size_t, size_t> free_;  // offset -> length, coalesced
+    struct Freed {
+        cudaEvent_t ev;
+        size_t off, len;
+    };
+    std::deque<Freed> freed;          // waiting for the steps in flight
+    std::vector<cudaEvent_t> spare;   // events to reuse
+};
+
 struct tc_server {
     size_t budget = 0, used = 0;
+    Arena arena;
+    std::mutex mu_arena;  // the arena's lists (add on the admin path, remove on the caller's)
     size_t max_step_samples = 0;
     int device = 0;
     cudaStream_t cs = nullptr;     // steps; frees of removed streams
@@ -319,8 +338,74 @@ size_t stream_bytes(long long L, long long block, int nslots, long long *keep, l
     return (size_t)*cap * 4 + (size_t)nslots * 4 * (size_t)*Lpad * 4 + sizeof(DevTable);
 }
 
-// Returns a removed stream's device memory to the pool, ordered after every
-// step that used it (no host synchronisation).
+constexpr size_t kArenaAlign = 256;
+
+// Returns the ranges whose steps have completed to the free list (coalesced).
+// Caller holds mu_arena.
+void arena_reclaim(Arena &a)
+{
+    while (!a.freed.empty() && (!a.freed.front().ev || cudaEventQuery(a.freed.front().ev) == cudaSuccess)) {
+        Arena::Freed f = a.freed.front();
+        a.freed.pop_front();
+        if (f.ev)
+            a.spare.push_back(f.ev);
+        auto it = a.free_.emplace(f.off, f.len).first;
+        auto nx = std::next(it);
+        if (nx != a.free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            a.free_.erase(nx);
+        }
+        if (it != a.free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                a.free_.erase(it);
+            }
+        }
+    }
+}
+
+// First fit of len bytes (a multiple of kArenaAlign); SIZE_MAX if none.
+size_t arena_alloc(tc_server *srv, size_t len)
+{
+    std::lock_guard<std::mutex> lk(srv->mu_arena);
+    Arena &a = srv->arena;
+    if (!a.base)
+        return SIZE_MAX;
+    arena_reclaim(a);
+    for (auto it = a.free_.begin(); it != a.free_.end(); ++it) {
+        if (it->second < len)
+            continue;
+        const size_t off = it->first, rest = it->second - len;
+        a.free_.erase(it);
+        if (rest)
+            a.free_.emplace(off + len, rest);
+        return off;
+    }
+    return SIZE_MAX;
+}
+
+// Frees a range after the work already enqueued on the step stream.
+void arena_free(tc_server *srv, size_t off, size_t len)
+{
+    std::lock_guard<std::mutex> lk(srv->mu_arena);
+    Arena &a = srv->arena;
+    cudaEvent_t ev = nullptr;
+    if (!a.spare.empty()) {
+        ev = a.spare.back();
+        a.spare.pop_back();
+    } else if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        cudaStreamSynchronize(srv->cs);  // no event: wait instead, then the range is free at once
+        a.freed.push_back({nullptr, off, len});
+        return;
+    }
+    cudaEventRecord(ev, srv->cs);
+    a.freed.push_back({ev, off, len});
+}
+
+// Returns a removed stream's device memory to the arena or the pool, ordered
+// after every step that used it (no host synchronisation).
 void free_stream(tc_server *srv, SStream *s)
 {
     if (s->grp) {
@@ -331,12 +416,17 @@ void free_stream(tc_server *srv, SStream *s)
         cudaEventDestroy(s->gdone);
         s->gdone = nullptr;
     }
-    if (s->hist)
-        cudaFreeAsync(s->hist, srv->cs);
-    if (s->ir)
-        cudaFreeAsync(s->ir, srv->cs);
-    if (s->d_vt)
-        cudaFreeAsync(s->d_vt, srv->cs);
+    if (s->arena_len) {
+        arena_free(srv, s->arena_off, s->arena_len);
+        s->arena_len = 0;
+    } else {
+        if (s->hist)
+            cudaFreeAsync(s->hist, srv->cs);
+        if (s->ir)
+            cudaFreeAsync(s->ir, srv->cs);
+        if (s->d_vt)
+            cudaFreeAsync(s->d_vt, srv->cs);
+    }
     s->hist = nullptr;
     s->ir = nullptr;
     s->d_vt = nullptr;
@@ -1215,6 +1305,13 @@ tc_status tc_server_close(tc_server *srv)
     cudaFree(srv->counters);
     cudaFree(srv->ir_stage);
     cudaFreeHost(srv->ir_stage_host);
+    for (auto &f : srv->arena.freed)
+        if (f.ev)
+            cudaEventDestroy(f.ev);
+    for (cudaEvent_t ev : srv->arena.spare)
+        cudaEventDestroy(ev);
+    if (srv->arena.base)
+        cudaFree(srv->arena.base);  // the streams were freed and both streams synchronised above
     if (srv->pool)
         cudaMemPoolDestroy(srv->pool);
     if (srv->admin)
@@ -1230,32 +1327,24 @@ tc_status tc_server_reserve(tc_server *srv, size_t bytes)
 {
     if (!srv)
         return sfail(TC_EINVAL, "tc_server_reserve: server is NULL");
-    bytes = std::min(bytes, srv->budget);
-    // The pool keeps whatever it maps (release threshold: everything), so
-    // allocating and freeing leaves the memory in it for later admissions.
-    // Pieces of 64 MiB: the stream states carved from them later are at most
-    // a few tens of MiB each.
-    constexpr size_t kPiece = (size_t)64 << 20;
+    bytes = std::min(bytes, srv->budget) / kArenaAlign * kArenaAlign;
     std::lock_guard<std::mutex> la(srv->mu_admin);
+    std::lock_guard<std::mutex> lk(srv->mu_arena);
+    if (srv->arena.base)
+        return sfail(TC_ESTATE, "tc_server_reserve: the server already has a reservation");
+    if (bytes == 0)
+        return TC_OK;
     S_CU(cudaSetDevice(srv->device));
-    std::vector<void *> got;
-    got.reserve(bytes / kPiece + 1);
-    cudaError_t e = cudaSuccess;
-    for (size_t done = 0; done < bytes && e == cudaSuccess; done += kPiece) {
-        void *ptr = nullptr;
-        e = cudaMallocFromPoolAsync(&ptr, std::min(kPiece, bytes - done), srv->pool, srv->admin);
-        if (e == cudaSuccess)
-            got.push_back(ptr);
-    }
-    for (void *ptr : got)
-        cudaFreeAsync(ptr, srv->admin);
-    const cudaError_t es = cudaStreamSynchronize(srv->admin);
-    if (e != cudaSuccess || es != cudaSuccess) {
+    void *ptr = nullptr;
+    const cudaError_t e = cudaMalloc(&ptr, bytes);  // before serving: one mapping, now
+    if (e != cudaSuccess) {
         cudaGetLastError();
-        const cudaError_t w = e != cudaSuccess ? e : es;
-        return sfail(w == cudaErrorMemoryAllocation ? TC_ENOMEM : TC_ECUDA,
-                     std::string("tc_server_reserve: ") + cudaGetErrorString(w));
+        return sfail(e == cudaErrorMemoryAllocation ? TC_ENOMEM : TC_ECUDA,
+                     std::string("tc_server_reserve: ") + cudaGetErrorString(e));
     }
+    srv->arena.base = static_cast<char *>(ptr);
+    srv->arena.size = bytes;
+    srv->arena.free_.emplace(0, bytes);
     return TC_OK;
 }
 
@@ -1294,13 +1383,30 @@ tc_status tc_server_add(tc_server *srv, size_t L, size_t block, const float *h, 
             srv->rejected++;
         return sfail(st, m);
     };
-    cudaError_t e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&s->hist), (size_t)s->cap * sizeof(float),
-                                            srv->pool, srv->admin);
-    if (e == cudaSuccess)
-        e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&s->ir),
-                                    (size_t)s->nslots * 4 * (size_t)s->Lpad * sizeof(float), srv->pool, srv->admin);
-    if (e == cudaSuccess)
-        e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&s->d_vt), sizeof(DevTable), srv->pool, srv->admin);
+    // From the reservation if it has room (one range: history, IR slots,
+    // version table), else from the pool (which may map memory now).
+    const size_t b_hist = rup((long long)s->cap * 4, kArenaAlign);
+    const size_t b_ir = rup((long long)s->nslots * 4 * s->Lpad * 4, kArenaAlign);
+    const size_t b_vt = rup((long long)sizeof(DevTable), kArenaAlign);
+    cudaError_t e = cudaSuccess;
+    const size_t off = arena_alloc(srv, b_hist + b_ir + b_vt);
+    if (off != SIZE_MAX) {
+        s->arena_off = off;
+        s->arena_len = b_hist + b_ir + b_vt;
+        char *base = srv->arena.base + off;
+        s->hist = reinterpret_cast<float *>(base);
+        s->ir = reinterpret_cast<float *>(base + b_hist);
+        s->d_vt = reinterpret_cast<DevTable *>(base + b_hist + b_ir);
+    } else {
+        e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&s->hist), (size_t)s->cap * sizeof(float), srv->pool,
+                                    srv->admin);
+        if (e == cudaSuccess)
+            e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&s->ir),
+                                        (size_t)s->nslots * 4 * (size_t)s->Lpad * sizeof(float), srv->pool,
+                                        srv->admin);
+        if (e == cudaSuccess)
+            e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&s->d_vt), sizeof(DevTable), srv->pool, srv->admin);
+    }
     if (e == cudaSuccess)
         e = cudaMemsetAsync(s->hist, 0, (size_t)s->cap * sizeof(float), srv->admin);
     if (e != cudaSuccess)

@@ -131,13 +131,47 @@ def test_alone_equals_mix_equals_oracle():
         assert e_am <= TOL["fp32"], (i, e_am)
 
 
-def test_reserved_pool_mix_equals_oracle():
-    """With the pool mapped up front (tc_server_reserve), admissions carve their state from it: the mix
-    still matches the oracle, and the budget accounting returns to zero after the removals."""
+@pytest.mark.parametrize("reserve", [4 << 20, 256 << 20])
+def test_reserved_memory_mix_equals_oracle(reserve):
+    """With a reservation (tc_server_reserve), admissions carve their state from it: 4 MiB holds only some
+    of the streams (the others fall back to the pool), 256 MiB all of them. The mix still matches the
+    oracle, and the budget accounting returns to zero after the removals."""
     streams = _small_trace(k=5, seed=11)
-    mix = _run(streams, order_seed=3, reserve=256 << 20)
+    mix = _run(streams, order_seed=3, reserve=reserve)
     for i, s in enumerate(streams):
         assert rel_l2(mix[i], _oracle(*s)) <= TOL["fp32"], i
+
+
+def test_reserved_memory_is_reused_after_removal():
+    """Streams admitted one after another into a reservation that holds about two of them: each removal's
+    range comes back once its steps have completed, and every stream still matches the oracle."""
+    streams = _small_trace(k=6, seed=13)
+    srv = capi.tc_server_open(1 << 30, 1 << 20)
+    try:
+        capi.tc_server_reserve(srv, 4 << 20)
+        with pytest.raises(capi.TcError) as ei:
+            capi.tc_server_reserve(srv, 4 << 20)
+        assert ei.value.code == "TC_ESTATE"
+        for t, x, H, vs in streams:
+            sid = capi.tc_server_add(srv, t.L, t.block, H[0])
+            outs = []
+            y = np.empty(t.block, np.float32)
+            for b in range(-(-t.n // t.block)):
+                lo, hi = b * t.block, min(t.n, (b + 1) * t.block)
+                if len(vs) > 1 and lo <= vs[1] < hi:
+                    capi.tc_server_set_ir_at(srv, sid, H[1], vs[1])
+                capi.tc_server_submit(srv, sid, x[lo:hi])
+                capi.tc_server_step(srv)
+                n, _, _ = capi.tc_server_poll(srv, sid, y)
+                outs.append(y[:n].copy())
+            tail = np.empty(max(t.L - 1, 1), np.float32)
+            n = capi.tc_server_flush(srv, sid, tail)
+            got = np.concatenate(outs + [tail[:n]])
+            assert rel_l2(got, _oracle(t, x, H, vs)) <= TOL["fp32"]
+            capi.tc_server_remove(srv, sid)
+        assert capi.tc_server_get_stats(srv).mem_used == 0
+    finally:
+        capi.tc_server_close(srv)
 
 
 def test_worker_thread_continuous_batching():

@@ -1037,6 +1037,7 @@ def bench_capacity(torch, capi, H64: np.ndarray, pool: np.ndarray, paced_s: floa
             wall = max(capi.tc_server_clock() - t_rec, 1e-9)
             r = dict(_lat_summary(lat, blk), streams=M, seconds_of_audio=paced_s, warmup_s=warm,
                      steps=int(steps), blocks_per_step=(st1.blocks - st0.blocks) / max(steps, 1),
+                     pool_admissions=int(st1.pool_admissions), step_buffer_grows=int(st1.grows - st0.grows),
                      served_tap_macs_per_s=(st1.tap_macs - st0.tap_macs) / wall,
                      k1=_k1_roofline(st0, st1))
             r["pass"] = bool(r.get("blocks", 0) > 0 and r["p99_ms"] <= period * 1e3
@@ -1227,7 +1228,8 @@ def bench_trace(capi, pool: np.ndarray, seconds: float, budget_gb: float = 96.0)
     arrived = sum(1 for t in tr if t.arrival_s < seconds)
     # Diagnostics: step durations (the last steps of the log) and how the
     # 32-sample blocks' misses spread over the run (completion order, 20 bins).
-    diag = {"reserved_gb": RESERVE_TRACE / (1 << 30)}
+    diag = {"reserved_gb": RESERVE_TRACE / (1 << 30), "pool_admissions": int(st.pool_admissions),
+            "step_buffer_grows": int(st.grows)}
     if len(steplog):
         dur = (steplog["t_done"] - steplog["t_begin"]) * 1e3
         gpu = (steplog["t_done"] - steplog["t_launch"]) * 1e3

@@ -416,6 +416,9 @@ typedef struct tc_server_stats {
                                   window straddled an IR switch */
     double k1_ms;        /* device time of the steps' K1 work-list launches (CUDA events, ms) */
     double k1_macs;      /* tap-MACs those launches computed (inputs x L, flush tails included) */
+    uint64_t pool_admissions;  /* tc_server_add admissions whose state did not fit tc_server_reserve's
+                                  reservation (allocated from the pool) */
+    uint64_t grows;      /* growths of the steps' own buffers (allocations made inside a step) */
 } tc_server_stats;
 
 /* Opens a server on the current CUDA device. mem_budget_bytes bounds the

@@ -44,7 +44,8 @@ class TcServerStats(ctypes.Structure):
                 ("steps", ctypes.c_uint64), ("blocks", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
                 ("busy_s", ctypes.c_double), ("tap_macs", ctypes.c_double),
                 ("tensor_launches", ctypes.c_uint64), ("fp32_fallbacks", ctypes.c_uint64),
-                ("k1_ms", ctypes.c_double), ("k1_macs", ctypes.c_double)]
+                ("k1_ms", ctypes.c_double), ("k1_macs", ctypes.c_double), ("pool_admissions", ctypes.c_uint64),
+                ("grows", ctypes.c_uint64)]
 
 
 class TcServerStepRec(ctypes.Structure):

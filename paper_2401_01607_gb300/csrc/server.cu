@@ -260,6 +260,8 @@ struct tc_server {
     double busy_s = 0.0;
     double tap_macs = 0.0;
     uint64_t tensor_launches = 0, fp32_fallbacks = 0;  // group pushes (state mutex)
+    uint64_t pool_admissions = 0;  // admissions whose state did not fit the reservation (state mutex)
+    uint64_t grows = 0;            // step-buffer growths (allocations inside steps)
     double k1_ms = 0.0, k1_macs = 0.0;                  // K1 work-list launches: event time, tap-MACs
 };
 
@@ -584,6 +586,9 @@ StageLayout stage_layout(size_t ni, size_t samples)
 // buffer waits for the step in flight (rare: a step larger than any before).
 tc_status grow(tc_server *srv, tc_server::StepBuf &b, size_t items, size_t scratch_floats, size_t counters)
 {
+    if (items > b.items_cap || items > srv->d_stage_items || scratch_floats > srv->scratch_floats ||
+        counters > srv->counters_n)
+        srv->grows++;
     if (items > b.items_cap) {
         S_CU(cudaStreamSynchronize(srv->cs));
         const size_t m = std::max(items, b.items_cap * 2 + 64);
@@ -693,17 +698,37 @@ size_t collect(tc_server *srv, tc_server::StepBuf &b)
     release_sources(srv, b.t_begin);
     if (srv->npending == 0)
         return 0;
+    // A step also stays within the gather's buffers as they are: work items,
+    // tile tickets and chunk-sum scratch, the latter bounded with the most
+    // chunks any variant may use (640-tap chunks), so that serving never
+    // grows them (growing allocates, and allocating under running steps
+    // stalled them). Only a step's first item may exceed them.
+    const size_t items_cap = std::min(b.items_cap, srv->d_stage_items);
+    size_t tiles = 0, scratch = 0;
     // take(s): up to kMerge queued blocks of s as one item; false if a block
     // of s did not fit the step (it stays queued).
     auto take = [&](SStream *s) {
         bool fits = true;
         tc_server::Item it{s, {}, (long long)b.total, 0};
+        const long long nch_max = (s->L + 3 + tc::k1_chunk_taps(tc::K1_P1) - 1) / tc::k1_chunk_taps(tc::K1_P1);
         while (!s->pending.empty() && (int)it.blocks.size() < kMerge) {
             Block &blk = s->pending.front();
             const size_t fl = (size_t)(blk.n * s->channels);  // packed floats
             if (b.total + fl > srv->max_step_samples) {
                 fits = false;
                 break;  // stays for the next step
+            }
+            if (!s->grp) {
+                const size_t dt = (size_t)((it.n + blk.n + tc::K1_MO - 1) / tc::K1_MO - (it.n + tc::K1_MO - 1) / tc::K1_MO);
+                const size_t ds = dt * (size_t)nch_max * tc::K1_MO;
+                const bool first = b.items.empty() && it.blocks.empty();
+                if (!first && (tiles + dt > srv->counters_n || scratch + ds > srv->scratch_floats ||
+                               (it.blocks.empty() && b.items.size() + 1 > items_cap))) {
+                    fits = false;
+                    break;
+                }
+                tiles += dt;
+                scratch += ds;
             }
             b.total += fl;
             it.n += blk.n;
@@ -1258,6 +1283,7 @@ tc_status tc_server_open(size_t mem_budget_bytes, size_t max_step_samples, tc_se
     // now, so that the first steps do not pay for allocations or module loads.
     for (auto &b : srv->buf)
         S_TRY(grow(srv.get(), b, 4096, (size_t)1 << 26, 16384));
+    srv->grows = 0;  // counts growths while serving only
     cudaFuncAttributes fa;
     S_CU(cudaFuncGetAttributes(&fa, ingest_kernel));
     tc::K1Plan plan{};
@@ -1398,6 +1424,10 @@ tc_status tc_server_add(tc_server *srv, size_t L, size_t block, const float *h, 
         s->ir = reinterpret_cast<float *>(base + b_hist);
         s->d_vt = reinterpret_cast<DevTable *>(base + b_hist + b_ir);
     } else {
+        {
+            std::lock_guard<std::mutex> lk(srv->mu_state);
+            srv->pool_admissions++;
+        }
         e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&s->hist), (size_t)s->cap * sizeof(float), srv->pool,
                                     srv->admin);
         if (e == cudaSuccess)
@@ -1774,6 +1804,8 @@ tc_status tc_server_get_stats(tc_server *srv, tc_server_stats *st)
     st->tensor_launches = srv->tensor_launches;
     st->k1_ms = srv->k1_ms;
     st->k1_macs = srv->k1_macs;
+    st->pool_admissions = srv->pool_admissions;
+    st->grows = srv->grows;
     st->fp32_fallbacks = srv->fp32_fallbacks;
     return TC_OK;
 }

@@ -994,7 +994,8 @@ def bench_capacity(torch, capi, H64: np.ndarray, pool: np.ndarray, paced_s: floa
             for r in range(2 + reps):
                 t = time.perf_counter()
                 capi.tc_server_submit_many(srv, a, addr, ns)
-                capi.tc_server_step(srv)
+                while capi.tc_server_step(srv):  # a step holds what the gather's buffers hold
+                    pass
                 ts_.append(time.perf_counter() - t)
             capi.tc_server_latencies(srv)
             return float(np.mean(ts_[2:]))

@@ -1192,10 +1192,27 @@ def bench_trace(capi, pool: np.ndarray, seconds: float, budget_gb: float = 96.0)
         t_start = capi.tc_server_clock() + 0.02
         t_end = t_start + seconds
         pending = list(tr)
+        slow = []  # steps of over 2 ms, from the step log drained every 0.5 s (it keeps the last 65536 steps)
+        t_drain = t_start + 0.5
+
+        def drain_log():
+            lg = capi.tc_server_step_log(srv, 1 << 15)
+            if len(lg):
+                k = (lg["t_done"] - lg["t_begin"]) > 2e-3
+                prev = np.concatenate([[lg["t_done"][0]], lg["t_done"][:-1]])
+                for i in np.nonzero(k)[0]:
+                    slow.append((float(lg["t_begin"][i] - t_start), float(lg["t_launch"][i] - lg["t_begin"][i]) * 1e3,
+                                 float(lg["t_done"][i] - lg["t_launch"][i]) * 1e3,
+                                 float(max(lg["t_begin"][i] - prev[i], 0.0)) * 1e3, int(lg["blocks"][i])))
+            return lg
+
         while True:
             now = capi.tc_server_clock()
             if now >= t_end:
                 break
+            if now >= t_drain:
+                drain_log()
+                t_drain = now + 0.5
             while pending and t_start + pending[0].arrival_s <= now:
                 t = pending[0]
                 try:
@@ -1223,14 +1240,17 @@ def bench_trace(capi, pool: np.ndarray, seconds: float, budget_gb: float = 96.0)
         st = capi.tc_server_get_stats(srv)
         k1 = _k1_roofline(capi.TcServerStats(), st)
         lat, blk, parts = capi.tc_server_latencies_ex(srv)
-        steplog = capi.tc_server_step_log(srv)
+        steplog = drain_log()
     finally:
         capi.tc_server_close(srv)
     arrived = sum(1 for t in tr if t.arrival_s < seconds)
     # Diagnostics: step durations (the last steps of the log) and how the
     # 32-sample blocks' misses spread over the run (completion order, 20 bins).
     diag = {"reserved_gb": RESERVE_TRACE / (1 << 30), "pool_admissions": int(st.pool_admissions),
-            "step_buffer_grows": int(st.grows)}
+            "step_buffer_grows": int(st.grows),
+            # the 12 longest steps over 2 ms: (s into the trace, collect+pack ms, enqueue->done ms,
+            # idle ms before the step, blocks)
+            "slow_steps": sorted(slow, key=lambda r: -(r[1] + r[2]))[:12], "slow_step_count": len(slow)}
     if len(steplog):
         dur = (steplog["t_done"] - steplog["t_begin"]) * 1e3
         gpu = (steplog["t_done"] - steplog["t_launch"]) * 1e3

@@ -1193,10 +1193,12 @@ def bench_trace(capi, pool: np.ndarray, seconds: float, budget_gb: float = 96.0)
         t_end = t_start + seconds
         pending = list(tr)
         slow = []  # steps of over 2 ms, from the step log drained every 0.5 s (it keeps the last 65536 steps)
+        logs = []
         t_drain = t_start + 0.5
 
         def drain_log():
             lg = capi.tc_server_step_log(srv, 1 << 15)
+            logs.append(lg)
             if len(lg):
                 k = (lg["t_done"] - lg["t_begin"]) > 2e-3
                 prev = np.concatenate([[lg["t_done"][0]], lg["t_done"][:-1]])
@@ -1240,7 +1242,8 @@ def bench_trace(capi, pool: np.ndarray, seconds: float, budget_gb: float = 96.0)
         st = capi.tc_server_get_stats(srv)
         k1 = _k1_roofline(capi.TcServerStats(), st)
         lat, blk, parts = capi.tc_server_latencies_ex(srv)
-        steplog = drain_log()
+        drain_log()
+        steplog = np.concatenate(logs)
     finally:
         capi.tc_server_close(srv)
     arrived = sum(1 for t in tr if t.arrival_s < seconds)

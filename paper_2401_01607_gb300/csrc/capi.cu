@@ -166,7 +166,7 @@ struct tc_stream {
     int *d_err = nullptr;
     int k1_variant_fixed = -1;  // -1: chosen per launch
     long long k2_range = -1;    // K blocks per tensor-core CTA range (-1: by precision)
-    bool k2_single_tile = false; // plain BF16: one channel tile per CTA (tuning knob)
+    int k2_mode = 2;  // plain BF16: 0 one channel tile per CTA, 1 two per CTA, 2 a CTA pair (tuning knob)
     bool zero_skip = false;      // K1 zero gating (tuning knob)
 
     // BF16 tensor-core path (shared-IR groups): bf16 hi/lo histories and, per
@@ -179,6 +179,7 @@ struct tc_stream {
         long long nkb = 0;
         void *thi = nullptr, *tlo = nullptr;
         CUtensorMap mt_hi{}, mt_lo{};
+        CUtensorMap mt2_hi{};  // the same hi tiles in boxes of 128 rows (half a tile: CTA pairs)
     };
     std::vector<std::array<TSet, 8>> tsets;  // [slot][delta]
     float *k2_partial = nullptr;
@@ -825,6 +826,8 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
                                      (unsigned long long)KB * 2, KB, TN));
             TC_CU(tc::encode_bf16_2d(&ts.mt_lo, ts.tlo, (unsigned long long)KB, (unsigned long long)nkb * TN,
                                      (unsigned long long)KB * 2, KB, TN));
+            TC_CU(tc::encode_bf16_2d(&ts.mt2_hi, ts.thi, (unsigned long long)KB, (unsigned long long)nkb * TN,
+                                     (unsigned long long)KB * 2, KB, TN / 2));
         }
         // The slot's unshifted fp32 copy (shift e = 0) holds h[k] at index k.
         const float *h = s->ir + (size_t)slot * s->nsets * 4 * (size_t)s->Lpad;
@@ -868,7 +871,8 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
     // Plain BF16 runs two channel tiles per CTA (one T stage feeds both), as
     // long as a unit's K range fits one TMEM run.
     const long long ntile_c1 = ((long long)p.C + TM - 1) / TM;
-    bool pair = s->prec == TC_BF16 && !s->k2_single_tile;
+    bool pair = s->prec == TC_BF16 && s->k2_mode != 0;
+    const bool cta_pair = pair && s->k2_mode == 2;
     p.ntile_c = (int)(pair ? (ntile_c1 + 1) / 2 : ntile_c1);
     const long long tiles = (long long)p.ntile_c * p.ntile_o;
     // TMEM runs of `range` K blocks before each drain into FP32 registers.
@@ -881,7 +885,7 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
     p.range += p.range & 1;  // runs are whole pipeline stages of 2 K blocks
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
-    long long nsplit = k2_plan_nsplit(tiles, nkb, sms);
+    long long nsplit = k2_plan_nsplit(tiles, nkb, cta_pair ? sms / 2 : sms);  // a CTA pair takes two SMs
     const long long kb_per = (nkb + nsplit - 1) / nsplit;
     nsplit = (nkb + kb_per - 1) / kb_per;
     p.nsplit = (int)nsplit;
@@ -911,7 +915,9 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
     TC_TRY(prof_begin(s));
     const CUtensorMap &mxh = rowview ? mxr_hi : s->mx_hi;
     const CUtensorMap &mxl = rowview ? mxr_lo : s->mx_lo;
-    if (pair)
+    if (pair && cta_pair)
+        TC_CU(tc::k2_launch_c2(mxh, t.mt2_hi, p, s->cs));
+    else if (pair)
         TC_CU(tc::k2_launch_pair(mxh, t.mt_hi, p, s->cs));
     else
         TC_CU(tc::k2_launch(mxh, mxl, t.mt_hi, t.mt_lo, p, s->prec == TC_BF16 ? 1 : 3, s->cs));
@@ -1525,9 +1531,9 @@ tc_status tc_set_tuning(tc_stream *s, int knob, long long value)
         s->k2_range = value;
         return TC_OK;
     case TC_TUNE_K2_PAIR:
-        if (value != -1 && value != 0 && value != 1)
-            return fail(TC_EINVAL, "TC_TUNE_K2_PAIR must be -1, 0 or 1");
-        s->k2_single_tile = value == 0;
+        if (value < -1 || value > 2)
+            return fail(TC_EINVAL, "TC_TUNE_K2_PAIR must be -1, 0, 1 or 2");
+        s->k2_mode = value == -1 ? 2 : (int)value;
         return TC_OK;
     case TC_TUNE_ZERO_SKIP:
         if (value != -1 && value != 0 && value != 1)
@@ -1551,7 +1557,7 @@ struct BlobHeader {
     int32_t kind, prec, shared_ir, state;
     uint64_t rows, items, nin, nsets, L, block, max_push;
     int64_t pos, base, next_ramp, nver, hist_len;
-    int32_t k1_variant_fixed, k2_single_tile, zero_skip, pad;
+    int32_t k1_variant_fixed, k2_mode, zero_skip, pad;
     int64_t k2_range;
 };
 
@@ -1599,7 +1605,7 @@ tc_status tc_stream_export(tc_stream *s, void *buf, size_t cap, size_t *size)
     hd.nver = (int64_t)s->vt.size();
     hd.hist_len = std::max<long long>(0, s->pos - s->base);
     hd.k1_variant_fixed = s->k1_variant_fixed;
-    hd.k2_single_tile = s->k2_single_tile ? 1 : 0;
+    hd.k2_mode = s->k2_mode;
     hd.zero_skip = s->zero_skip ? 1 : 0;
     hd.k2_range = s->k2_range;
     std::memcpy(out, &hd, sizeof hd);
@@ -1677,7 +1683,7 @@ tc_status tc_stream_import(tc_stream *s, const void *buf, size_t size)
     s->state = hd.state;
     s->next_ramp = hd.next_ramp;
     s->k1_variant_fixed = hd.k1_variant_fixed;
-    s->k2_single_tile = hd.k2_single_tile != 0;
+    s->k2_mode = (hd.k2_mode >= 0 && hd.k2_mode <= 2) ? hd.k2_mode : 2;
     s->zero_skip = hd.zero_skip != 0;
     s->k2_range = hd.k2_range;
     if (hd.hist_len > 0)

@@ -428,6 +428,168 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
     }
 }
 
+// Plain BF16 on a CTA pair (cluster of two, tcgen05 cta_group::2): a unit of
+// 256 channels x 256 outputs is one M = 256, N = 256 accumulation. Each CTA
+// stages its own 128 channels of X and its half (128 outputs) of the T tile,
+// so a CTA's shared memory feeds 8 KB of operands per 128 x 256 x 16 of its
+// accumulator, against 12 KB when one CTA holds a whole 128 x 256 tile; the
+// tensor cores read the peer's T half over the pair. The even CTA's producer
+// arms the stage barrier for both CTAs' bytes, and the odd CTA's loads count
+// on it. The even CTA's MMA thread issues the pair MMAs and commits each
+// stage to both CTAs' free barriers, the last one also to both accumulator
+// barriers; each CTA's eight epilogue warps then read its own TMEM (128
+// lanes = its channels, 256 columns = the outputs). One TMEM run per unit.
+constexpr int K2C_BLK = K2_XBYTES + K2_XBYTES;  // one K block per CTA: X (128 x 32) and T half (128 x 32)
+constexpr int K2C_NS = 10;
+constexpr int K2C_SMEM = K2C_NS * K2C_BLK + 1024;
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2_THREADS, 1)
+    k2_toeplitz_c2(const __grid_constant__ CUtensorMap mx_hi, const __grid_constant__ CUtensorMap mt2_hi,
+                   const K2Params p)
+{
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full[K2C_NS];
+    __shared__ __align__(8) uint64_t empty[K2C_NS];
+    __shared__ __align__(8) uint64_t accfull;
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int s_fail;
+
+    uint8_t *const smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int lane = tid & 31;
+    const uint32_t rank = cluster_ctarank();  // 0: issues the MMAs; 1: its pair peer
+
+    // Unit = (channel-tile pair, output tile, K part), one cluster each.
+    long long u = blockIdx.x >> 1;
+    const int part = (int)(u % p.nsplit);
+    u /= p.nsplit;
+    const int tile_o = (int)(u % p.ntile_o);
+    const int tile_c = (int)(u / p.ntile_o);  // pair index
+    const int kb0 = part * p.kb_per;
+    const int kb1 = min(kb0 + p.kb_per, p.nkb);
+    const int nk = max(kb1 - kb0, 0);
+    const int c0 = tile_c * 2 * K2_M + (int)rank * K2_M;  // this CTA's 128 channels
+    const long long xcol0 = p.x_col0 + (long long)tile_o * K2_N;
+
+    if (tid == 0) {
+        for (int i = 0; i < K2C_NS; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        mbar_init(&accfull, 1);
+        s_fail = 0;
+        fence_mbar_init();
+    }
+    if (warp == 2)
+        tmem_alloc_pair(&tmem_base, K2_N);
+    tc_fence_before_sync();
+    cluster_sync();  // both CTAs' barriers exist before either CTA signals the other's
+    tc_fence_after_sync();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- producer (each CTA loads its own halves) ----
+            for (int gi = 0; gi < nk && !s_fail; ++gi) {
+                const int st = gi % K2C_NS;
+                const int use = gi / K2C_NS;
+                if (use > 0 && !mbar_wait_bounded(&empty[st], (uint32_t)((use - 1) & 1), p.err, ERR_TIMEOUT_TMA)) {
+                    s_fail = 1;
+                    break;
+                }
+                if (rank == 0)
+                    mbar_arrive_expect_tx(&full[st], (uint32_t)(2 * K2C_BLK));  // both CTAs' bytes
+                const uint32_t bar = mapa_shared(smem_u32(&full[st]), 0);
+                uint8_t *sb = smem + st * K2C_BLK;
+                const int kb = kb0 + gi;
+                tma_load_2d_pair(sb, &mx_hi, (int)(xcol0 + (long long)kb * K2_KB), c0, bar);
+                tma_load_2d_pair(sb + K2_XBYTES, &mt2_hi, 0, kb * K2_N + (int)rank * (K2_N / 2), bar);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && rank == 0) {
+            // ---- MMA issuer (even CTA) ----
+            const uint32_t idesc = umma_idesc_bf16(2 * K2_M, K2_N);
+            const uint64_t d0 = umma_desc_sw64(smem_u32(smem));
+            bool ok = true;
+            for (int gi = 0; gi < nk; ++gi) {
+                const int st = gi % K2C_NS;
+                if (!mbar_wait_bounded(&full[st], (uint32_t)((gi / K2C_NS) & 1), p.err, ERR_TIMEOUT_MMA)) {
+                    s_fail = 1;
+                    ok = false;
+                    break;
+                }
+                tc_fence_after_sync();
+                const uint64_t sd = d0 + (uint64_t)((st * K2C_BLK) >> 4);
+#pragma unroll
+                for (int kk = 0; kk < K2_KB / 16; ++kk) {
+                    const uint64_t xa = sd + (uint64_t)(kk * 2);
+                    const uint64_t tb = sd + (uint64_t)((K2_XBYTES + kk * 32) >> 4);
+                    umma_bf16_pair(tmem, xa, tb, idesc, (gi == 0 && kk == 0) ? 0u : 1u);
+                }
+                umma_commit_pair(&empty[st], 0x3);
+            }
+            if (ok && nk > 0)
+                umma_commit_pair(&accfull, 0x3);
+        }
+    } else if (warp >= K2_ROLE_WARPS) {
+        // ---- epilogue (each CTA: its TMEM lanes = its 128 channels) ----
+        const int ew = warp - K2_ROLE_WARPS;
+        const int q = warp & 3;
+        const int half = ew >> 2;
+        bool got = nk > 0;
+        if (got && lane == 0)
+            got = mbar_wait_limited(&accfull, 0, p.err, ERR_TIMEOUT_MMA, kWaitLimitNs, &s_fail);
+        got = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
+        if (got) {
+            mbar_try_wait(&accfull, 0);
+            tc_fence_after_sync();
+            const int ch = q * 32 + lane;
+            const int c = c0 + ch;
+            float *dst;
+            long long lim;
+            if (p.nsplit == 1) {
+                dst = p.y + (long long)c * p.y_pitch + (long long)tile_o * K2_N + half * 128;
+                lim = p.nout - (long long)tile_o * K2_N - half * 128;
+            } else {
+                // Partials per 128-channel tile, as k2_reduce reads them.
+                const int tc1 = tile_c * 2 + (int)rank;
+                dst = p.partial + ((((long long)tc1 * p.ntile_o + tile_o) * p.nsplit + part) * K2_M + ch) * K2_N +
+                      half * 128;
+                lim = 128;
+            }
+            const uint32_t src = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(half * 128);
+#pragma unroll
+            for (int cc = 0; cc < 8; ++cc) {
+                float v[16];
+                tmem_ld_32x16(src + cc * 16, v);
+                if (c >= p.C)
+                    continue;
+                const long long j0 = cc * 16;
+                if (lim >= j0 + 16 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+#pragma unroll
+                    for (int j = 0; j < 16; j += 4)
+                        *reinterpret_cast<float4 *>(dst + j0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (j0 + j < lim)
+                            dst[j0 + j] = v[j];
+                }
+            }
+        }
+    }
+    // Neither CTA leaves while the other may still signal its barriers or
+    // read its shared memory (the pair MMAs read both CTAs' operands).
+    tc_fence_before_sync();
+    cluster_sync();
+    if (warp == 2) {
+        tc_fence_after_sync();
+        tmem_dealloc_pair(tmem, K2_N);
+    }
+}
+
 // Adds the nsplit K-range partials of each (channel, output) by a fixed
 // pairwise tree (adjacent pairs, zero-padded to 64 leaves) and writes y.
 __global__ void k2_reduce(const float *__restrict__ partial, int nsplit, int C, int ntile_o, int nout, float *y,
@@ -546,6 +708,38 @@ cudaError_t k2_launch_pair(const CUtensorMap &mx_hi, const CUtensorMap &mt_hi, c
     if (units <= 0)
         return cudaSuccess;
     k2_toeplitz_pair<<<(unsigned)units, K2_THREADS, K2P_SMEM, st>>>(mx_hi, mt_hi, p);
+    count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess || p.nsplit == 1)
+        return e;
+    const long long work = (long long)p.C * p.nout;
+    k2_reduce<<<grid_for(work), 256, 0, st>>>(p.partial, p.nsplit, p.C, (p.nout + K2_N - 1) / K2_N, p.nout, p.y,
+                                              p.y_pitch);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t k2_launch_c2(const CUtensorMap &mx_hi, const CUtensorMap &mt2_hi, const K2Params &p, cudaStream_t st)
+{
+    static bool attr[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    if (dev < 0 || dev >= 64 || p.nsplit < 1 || p.nsplit > 64)
+        return cudaErrorInvalidValue;
+    if (!attr[dev]) {
+        e = cudaFuncSetAttribute(k2_toeplitz_c2, cudaFuncAttributeMaxDynamicSharedMemorySize, K2C_SMEM);
+        if (e != cudaSuccess)
+            return e;
+        attr[dev] = true;
+    }
+    const long long units = (long long)p.ntile_c * p.ntile_o * p.nsplit;  // ntile_c counts tile pairs here
+    if (units <= 0)
+        return cudaSuccess;
+    if (2 * units > 0x7fffffffLL)
+        return cudaErrorInvalidConfiguration;
+    k2_toeplitz_c2<<<(unsigned)(2 * units), K2_THREADS, K2C_SMEM, st>>>(mx_hi, mt2_hi, p);
     count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess || p.nsplit == 1)

@@ -358,9 +358,10 @@ extern "C" tc_status tc_convolve_tc(const float *x, size_t N, const float *h, si
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     long long nsplit = 1;
     double best = 0.0;
+    const int slots = pair ? sms / 2 : sms;  // plain BF16 runs on CTA pairs: two SMs per unit
     for (long long ns = 1; ns <= 64 && ns <= nkb && (ns == 1 || nkb / ns >= 16); ++ns) {
         const long long units = (long long)p.ntile_c * ns;
-        const double eff = (double)units / (double)(((units + sms - 1) / sms) * sms);
+        const double eff = (double)units / (double)(((units + slots - 1) / slots) * slots);
         if (eff > best + 1e-9) {
             best = eff;
             nsplit = ns;
@@ -399,7 +400,7 @@ extern "C" tc_status tc_convolve_tc(const float *x, size_t N, const float *h, si
     p.y_pitch = TN;
     p.partial = nsplit > 1 ? reinterpret_cast<float *>(mem + o_part) : nullptr;
     p.err = err;
-    CUtensorMap mx_hi{}, mx_lo{}, mt_hi{}, mt_lo{};
+    CUtensorMap mx_hi{}, mx_lo{}, mt_hi{}, mt_lo{}, mt2_hi{};
     int herr = 0;
     // Rows of the X view overlap: row r starts 256 samples after row r - 1.
     e = tc::encode_bf16_2d(&mx_hi, xhi, (unsigned long long)nkb * KB, (unsigned long long)R, (unsigned long long)TN * 2,
@@ -412,6 +413,8 @@ extern "C" tc_status tc_convolve_tc(const float *x, size_t N, const float *h, si
     if (e == cudaSuccess)
         e = tc::encode_bf16_2d(&mt_lo, tlo, KB, (unsigned long long)nkb * TN, KB * 2, KB, TN);
     if (e == cudaSuccess)
+        e = tc::encode_bf16_2d(&mt2_hi, thi, KB, (unsigned long long)nkb * TN, KB * 2, KB, TN / 2);
+    if (e == cudaSuccess)
         e = cudaMemsetAsync(err, 0, sizeof(int), cs);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(xs, 0, b_xs, cs);
@@ -422,7 +425,7 @@ extern "C" tc_status tc_convolve_tc(const float *x, size_t N, const float *h, si
     if (e == cudaSuccess)
         e = tc::k2_tprep_launch(h, (int)Ll, 0, (int)nkb, thi, tlo, cs);
     if (e == cudaSuccess)
-        e = pair ? tc::k2_launch_pair(mx_hi, mt_hi, p, cs) : tc::k2_launch(mx_hi, mx_lo, mt_hi, mt_lo, p, nprod, cs);
+        e = pair ? tc::k2_launch_c2(mx_hi, mt2_hi, p, cs) : tc::k2_launch(mx_hi, mx_lo, mt_hi, mt_lo, p, nprod, cs);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(y, ytmp, (size_t)ny * 4, cudaMemcpyDeviceToDevice, cs);
     if (e == cudaSuccess)

@@ -172,6 +172,11 @@ cudaError_t k2_launch(const CUtensorMap &mx_hi, const CUtensorMap &mx_lo, const 
 // Plain BF16 with two 128-channel tiles per CTA sharing each T stage. p.ntile_c
 // counts tile pairs (ceil(C / 256)); one TMEM run per unit (range >= kb_per).
 cudaError_t k2_launch_pair(const CUtensorMap &mx_hi, const CUtensorMap &mt_hi, const K2Params &p, cudaStream_t st);
+// Plain BF16 on CTA pairs (clusters of two, tcgen05 cta_group::2): a unit of
+// 256 channels x 256 outputs per pair, p.ntile_c counting tile pairs as for
+// k2_launch_pair; one TMEM run per unit. mt2_hi: T over [nkb * 256][32] with
+// a box of 32 x 128 (each CTA loads its 128-output half).
+cudaError_t k2_launch_c2(const CUtensorMap &mx_hi, const CUtensorMap &mt2_hi, const K2Params &p, cudaStream_t st);
 // Encodes a 2-D bf16 tensor map (inner dimension first), 64-byte swizzle.
 cudaError_t encode_bf16_2d(CUtensorMap *map, const void *base, unsigned long long dim0, unsigned long long dim1,
                            unsigned long long stride1_bytes, unsigned box0, unsigned box1);

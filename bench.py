@@ -58,6 +58,8 @@ SM_COUNT = 152  # replaced by the device's own count once CUDA is up (set_sm_cou
 FMA_PER_CLK = 128
 SM_MAX_MHZ = 2070.0
 METRIC = "tap-MAC/s and concurrent 48 kHz real-time streams per GB300; p99 block latency"
+K2_SRC = os.path.join(ROOT, "paper_2401_01607_gb300", "csrc", "k2_toeplitz_tc.cu")
+K3_SRC = os.path.join(ROOT, "paper_2401_01607_gb300", "csrc", "k3_mimo_tc.cu")
 
 
 def set_sm_count(n: int) -> None:
@@ -520,7 +522,10 @@ def bench_shared(torch, steps: int, warmup: int, P: int = 8192, C: int = 1024, N
             nprod = 3 if name == "bf16split" else 1
             tflops = 2.0 * nprod * k_macs / (k_ms / 1e3) / 1e12 if k_ms > 0 else 0.0
             r["roofline"] = {"bound": "tensor", "achieved": tflops, "peak": bf16_peak, "unit": "TFLOP/s",
-                             "frac": tflops / bf16_peak, "traffic": None,
+                             "frac": tflops / bf16_peak,
+                             "traffic": traffic_from_profile(K2_SRC, "k2_toeplitz_traffic.txt",
+                                                             f"{name}-C{C}-P{P}") if C == 1024 else None,
+                             "traffic_unit": "DRAM bytes per push (K2 + k2_reduce, one ncu capture)",
                              "kernel": "k2_toeplitz (tcgen05 kind::f16) + k2_reduce",
                              "peak_basis": "measured cuBLAS bf16, sustained (MEASURED_PEAKS.json)",
                              "flops_counted": f"2 x {nprod} products x useful tap-MACs"}
@@ -590,7 +595,11 @@ def bench_mimo(torch, P: int = 8192, precisions=("bf16split", "bf16", "fp32"), L
             nprod = 3 if name == "bf16split" else 1
             tflops = 2.0 * nprod * k_macs / (k_ms / 1e3) / 1e12 if k_ms > 0 else 0.0
             r["roofline"] = {"bound": "tensor", "achieved": tflops, "peak": bf16_peak, "unit": "TFLOP/s",
-                             "frac": tflops / bf16_peak, "kernel": "k3_mimo (tcgen05 kind::f16) + k3_rev + k3_reduce",
+                             "frac": tflops / bf16_peak,
+                             "traffic": traffic_from_profile(K3_SRC, "k3_mimo_traffic.txt",
+                                                             f"{name}-L{L}-P{P}") if seconds == 60.0 else None,
+                             "traffic_unit": "DRAM bytes per push (K3 + k3_rev + k3_reduce, one ncu capture)",
+                             "kernel": "k3_mimo (tcgen05 kind::f16) + k3_rev + k3_reduce",
                              "peak_basis": "measured cuBLAS bf16, sustained (MEASURED_PEAKS.json)",
                              "flops_counted": f"2 x {nprod} products x useful tap-MACs"}
         out[name] = r
@@ -1324,16 +1333,19 @@ def check_sampled(runner, n_check=64) -> dict:
     return _err(runner_outputs(runner, picks), ref)
 
 
-def traffic_from_profile(kernel_src: str) -> float | None:
-    """Per-launch DRAM bytes of K1 from the committed ncu summary, if it matches the current kernel source."""
+def traffic_from_profile(kernel_src: str, table: str = "k1_gather_traffic.txt", tag: str = "") -> float | None:
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture) from a committed
+    profile table under profiles/, used only while the kernel's source still has the hash it had at capture
+    time (else None: the counters are stale). Lines: traffic_bytes_per_launch <bytes> <sha256[:16]> [tag]."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "k1_gather_traffic.txt")
+    path = os.path.join(ROOT, "profiles", table)
     if not os.path.exists(path):
         return None
     digest = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
     for ln in open(path):
         parts = ln.split()
-        if len(parts) >= 3 and parts[0] == "traffic_bytes_per_launch" and parts[2] == digest:
+        if (len(parts) >= 3 and parts[0] == "traffic_bytes_per_launch" and parts[2] == digest and
+                (parts[3] if len(parts) > 3 else "") == tag):
             return float(parts[1])
     return None
 

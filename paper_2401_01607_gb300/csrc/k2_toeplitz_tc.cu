@@ -439,9 +439,17 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
 // stage to both CTAs' free barriers, the last one also to both accumulator
 // barriers; each CTA's eight epilogue warps then read its own TMEM (128
 // lanes = its channels, 256 columns = the outputs). One TMEM run per unit.
+// Measured on the 1024-stream shared-IR workload (one box, same run): 1 K
+// block per stage 39 % of the sustained BF16 peak, 2 blocks 58 %, 3 blocks x
+// 4 stages 64 % (4 x 3: 61 %; 7 x 2: 52 %; 1 x 13: 40 %), against 64 % for
+// two 128-channel tiles on one CTA: the cost is per stage (the barrier round
+// trip and commit of each stage), not the shared-memory operand traffic that
+// the pair halves, so the pair only matches the one-CTA form.
 constexpr int K2C_BLK = K2_XBYTES + K2_XBYTES;  // one K block per CTA: X (128 x 32) and T half (128 x 32)
-constexpr int K2C_NS = 10;
-constexpr int K2C_SMEM = K2C_NS * K2C_BLK + 1024;
+constexpr int K2C_GS = 3;                        // K blocks per pipeline stage
+constexpr int K2C_STAGE = K2C_GS * K2C_BLK;
+constexpr int K2C_NS = 4;
+constexpr int K2C_SMEM = K2C_NS * K2C_STAGE + 1024;
 
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2_THREADS, 1)
     k2_toeplitz_c2(const __grid_constant__ CUtensorMap mx_hi, const __grid_constant__ CUtensorMap mt2_hi,
@@ -491,20 +499,23 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2_THREADS, 1)
     if (warp == 0) {
         if (lane == 0) {
             // ---- producer (each CTA loads its own halves) ----
-            for (int gi = 0; gi < nk && !s_fail; ++gi) {
+            for (int gi = 0; gi * K2C_GS < nk && !s_fail; ++gi) {
                 const int st = gi % K2C_NS;
                 const int use = gi / K2C_NS;
                 if (use > 0 && !mbar_wait_bounded(&empty[st], (uint32_t)((use - 1) & 1), p.err, ERR_TIMEOUT_TMA)) {
                     s_fail = 1;
                     break;
                 }
+                const int nb = min(K2C_GS, nk - gi * K2C_GS);  // K blocks in this stage
                 if (rank == 0)
-                    mbar_arrive_expect_tx(&full[st], (uint32_t)(2 * K2C_BLK));  // both CTAs' bytes
+                    mbar_arrive_expect_tx(&full[st], (uint32_t)(2 * nb * K2C_BLK));  // both CTAs' bytes
                 const uint32_t bar = mapa_shared(smem_u32(&full[st]), 0);
-                uint8_t *sb = smem + st * K2C_BLK;
-                const int kb = kb0 + gi;
-                tma_load_2d_pair(sb, &mx_hi, (int)(xcol0 + (long long)kb * K2_KB), c0, bar);
-                tma_load_2d_pair(sb + K2_XBYTES, &mt2_hi, 0, kb * K2_N + (int)rank * (K2_N / 2), bar);
+                for (int j = 0; j < nb; ++j) {
+                    uint8_t *sb = smem + st * K2C_STAGE + j * K2C_BLK;
+                    const int kb = kb0 + gi * K2C_GS + j;
+                    tma_load_2d_pair(sb, &mx_hi, (int)(xcol0 + (long long)kb * K2_KB), c0, bar);
+                    tma_load_2d_pair(sb + K2_XBYTES, &mt2_hi, 0, kb * K2_N + (int)rank * (K2_N / 2), bar);
+                }
             }
         }
     } else if (warp == 1) {
@@ -513,7 +524,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2_THREADS, 1)
             const uint32_t idesc = umma_idesc_bf16(2 * K2_M, K2_N);
             const uint64_t d0 = umma_desc_sw64(smem_u32(smem));
             bool ok = true;
-            for (int gi = 0; gi < nk; ++gi) {
+            for (int gi = 0; gi * K2C_GS < nk; ++gi) {
                 const int st = gi % K2C_NS;
                 if (!mbar_wait_bounded(&full[st], (uint32_t)((gi / K2C_NS) & 1), p.err, ERR_TIMEOUT_MMA)) {
                     s_fail = 1;
@@ -521,12 +532,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2_THREADS, 1)
                     break;
                 }
                 tc_fence_after_sync();
-                const uint64_t sd = d0 + (uint64_t)((st * K2C_BLK) >> 4);
+                const int nb = min(K2C_GS, nk - gi * K2C_GS);
+                for (int j = 0; j < nb; ++j) {
+                    const uint64_t sd = d0 + (uint64_t)((st * K2C_STAGE + j * K2C_BLK) >> 4);
 #pragma unroll
-                for (int kk = 0; kk < K2_KB / 16; ++kk) {
-                    const uint64_t xa = sd + (uint64_t)(kk * 2);
-                    const uint64_t tb = sd + (uint64_t)((K2_XBYTES + kk * 32) >> 4);
-                    umma_bf16_pair(tmem, xa, tb, idesc, (gi == 0 && kk == 0) ? 0u : 1u);
+                    for (int kk = 0; kk < K2_KB / 16; ++kk) {
+                        const uint64_t xa = sd + (uint64_t)(kk * 2);
+                        const uint64_t tb = sd + (uint64_t)((K2_XBYTES + kk * 32) >> 4);
+                        umma_bf16_pair(tmem, xa, tb, idesc, (gi == 0 && j == 0 && kk == 0) ? 0u : 1u);
+                    }
                 }
                 umma_commit_pair(&empty[st], 0x3);
             }

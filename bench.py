@@ -1181,25 +1181,68 @@ def bench_groups(capi, paced_s: float = 1.5, C: int = 128, L: int = 96_000, B: i
 RESERVE_TRACE = 12 << 30  # device bytes reserved for the trace server's streams before the replay
 
 
+TRACE_GROUPS = 8          # BF16-split shared-IR groups in the trace: 16-channel sources through one IR
+TRACE_GROUP_C = 16
+TRACE_GROUP_SECONDS = 12.0
+TRACE_GROUP_BLOCK = 256
+
+
+def trace_groups(seconds: float):
+    """The trace's multichannel part: group g (16 channels sharing one IR of L log-uniform in [4800, 96000],
+    tau 0.2 L, block 256) plays a 12 s source from 4 + (seconds - 16) g / 8 s into the trace."""
+    rng = np.random.default_rng(4343)
+    out = []
+    for g in range(TRACE_GROUPS):
+        L = int(np.exp(rng.uniform(np.log(4800), np.log(96_000))))
+        start = 4.0 + max(seconds - 16.0, 0.0) * g / TRACE_GROUPS
+        n = int(min(TRACE_GROUP_SECONDS, max(seconds - start, 1.0)) * FS)
+        x = synth.audio_block(TRACE_GROUP_C, n, synth.x_seed(11, g))
+        h = synth.decayed_ir(L, 0.2 * L, synth.ir_seed(11, g))
+        out.append((start, L, x, h))
+    return out
+
+
 def bench_trace(capi, pool: np.ndarray, seconds: float, budget_gb: float = 96.0) -> dict:
     """Serving trace replayed in real time: Poisson arrivals (200 streams/s),
     durations 0.5-30 s, IR lengths 256-480000, blocks {32..256}, 10 % with a
     mid-stream IR swap. A stream is admitted at its arrival (memory budget;
     it waits and retries when the budget is full), reads a live 48 kHz source
-    from then on and is removed once drained. The worker thread runs the
-    steps; this thread only admits and removes."""
+    from then on and is removed once drained. Beside them, 8 shared-IR groups
+    of 16 channels in BF16 split (multichannel sources through one room
+    response), admitted before the replay, each playing a 12 s live source from
+    its start time; their outputs are kept and checked against Eq. 4. The
+    worker thread runs the steps; this thread admits, removes and polls."""
     tr = synth.serving_trace(duration_s=seconds)
     make = _ir_maker()
     irs = {t.sid: [make(t.L, t.tau, sd) for sd in t.ir_seeds] for t in tr}
+    grp = trace_groups(seconds)
     srv = capi.tc_server_open(int(budget_gb * (1 << 30)), 1 << 22)
     waits, max_active, live = 0, 0, {}
+    gids, gouts = [], []
     try:
+        # Groups are admitted here, not at their start: opening a group allocates device memory, which stalls
+        # running steps.
+        for start, L, x, h in grp:
+            gids.append(capi.tc_server_add_group(srv, TRACE_GROUP_C, L, TRACE_GROUP_BLOCK, h, capi.TC_BF16_SPLIT))
+            gouts.append([])
+        gbuf = np.empty(TRACE_GROUP_C * TRACE_GROUP_BLOCK, np.float32)
+
+        def poll_groups():
+            for gi, gid in enumerate(gids):
+                while True:
+                    n, _, _ = capi.tc_server_poll(srv, gid, gbuf)
+                    if n == 0:
+                        break
+                    gouts[gi].append(gbuf[:n].reshape(TRACE_GROUP_C, -1).copy())
+
         # The trace's streams hold about 6-8 GB at their peak: reserved before the replay, so that admissions
         # carve their state from it (growing the pool while steps run stalled them for 1-65 ms).
         capi.tc_server_reserve(srv, RESERVE_TRACE)
         capi.tc_server_start(srv)
         t_start = capi.tc_server_clock() + 0.02
         t_end = t_start + seconds
+        for (start, L, x, h), gid in zip(grp, gids):
+            capi.tc_server_attach_source(srv, gid, x, t_start + start)
         pending = list(tr)
         slow = []  # steps of over 2 ms, from the step log drained every 0.5 s (it keeps the last 65536 steps)
         logs = []
@@ -1224,6 +1267,7 @@ def bench_trace(capi, pool: np.ndarray, seconds: float, budget_gb: float = 96.0)
             if now >= t_drain:
                 drain_log()
                 t_drain = now + 0.5
+            poll_groups()
             while pending and t_start + pending[0].arrival_s <= now:
                 t = pending[0]
                 try:
@@ -1248,9 +1292,10 @@ def bench_trace(capi, pool: np.ndarray, seconds: float, budget_gb: float = 96.0)
                     del live[sid]
             time.sleep(0.001)
         capi.tc_server_stop(srv)
+        poll_groups()
         st = capi.tc_server_get_stats(srv)
         k1 = _k1_roofline(capi.TcServerStats(), st)
-        lat, blk, parts = capi.tc_server_latencies_ex(srv)
+        lat, blk, parts, kind = capi.tc_server_latencies_ex(srv)
         drain_log()
         steplog = np.concatenate(logs)
     finally:
@@ -1284,15 +1329,38 @@ def bench_trace(capi, pool: np.ndarray, seconds: float, budget_gb: float = 96.0)
                             "missed_mean": {n: float(parts[late, i].mean() * 1e3) if late.any() else None
                                             for i, n in enumerate(names)},
                             "missed": int(late.sum())}
-    m32 = blk == 32
+    m32 = (blk == 32) & (kind == 0)
     if m32.any():
         miss = lat[m32] > 32 / FS
         diag["miss32_by_twentieth"] = [float(x.mean()) for x in np.array_split(miss, 20)]
-    return dict(_lat_summary(lat, blk), seconds=seconds, streams_arrived=arrived, max_active=max_active,
+    # The groups: latency (BF16 split, block 256) and accuracy of 512 contiguous outputs of channels 0 and 15 of
+    # each group, at the middle of what it delivered, against Eq. (4) in float64.
+    groups = {"groups": TRACE_GROUPS, "channels": TRACE_GROUP_C, "precision": "bf16split",
+              "block": TRACE_GROUP_BLOCK, "L": [int(g[1]) for g in grp], "source_s": TRACE_GROUP_SECONDS,
+              "latency": _lat_summary(lat[kind == 1 + capi.TC_BF16_SPLIT], blk[kind == 1 + capi.TC_BF16_SPLIT])}
+    groups["latency"].pop("by_block", None)
+    got, ref = [], []
+    for (start, L, x, h), outs in zip(grp, gouts):
+        if not outs:
+            continue
+        y = np.concatenate(outs, axis=1)
+        m0 = max(0, y.shape[1] // 2 - 256)
+        for c in (0, TRACE_GROUP_C - 1):
+            for m in range(m0, min(m0 + 512, y.shape[1])):
+                got.append(float(y[c, m]))
+                ref.append(eq4_at(x[c], h[None], [0], m))
+    if got:
+        groups["check"] = _err(np.array(got), np.array(ref))
+        groups["check"]["contiguous"] = "512 outputs x channels 0 and 15 x each group"
+    groups["delivered_outputs"] = int(sum(sum(o.shape[1] for o in outs) for outs in gouts))
+    own = kind == 0
+    return dict(_lat_summary(lat[own], blk[own]), seconds=seconds, streams_arrived=arrived, max_active=max_active,
+                groups_bf16split=groups,
                 served_tap_macs_per_s=st.tap_macs / seconds, steps=int(st.steps),
                 blocks_per_step=st.blocks / max(st.steps, 1), busy_frac=st.busy_s / seconds,
                 admission_waits=waits, mem_budget_gb=budget_gb, diagnostics=diag, k1=k1,
-                precision="fp32 (every stream has its own IR: no shared-IR batch for the tensor cores)",
+                precision="fp32 for the streams with their own IR (a real-time block fills at most 1/64 of a "
+                          "tensor-core tile); bf16split for the shared-IR groups (groups_bf16split)",
                 inputs="live 48 kHz sources cut from a seeded audio pool; IRs cut from a seeded Gaussian pool")
 
 
@@ -1420,7 +1488,10 @@ def headline(line: dict, sections: dict) -> dict:
             "group_channels": {k: _get(grp, k, "channels") for k in ("bf16split", "fp32") if k in grp},
             "trace": {"s": tr.get("seconds"), "max_active": tr.get("max_active"), "p50_ms": tr.get("p50_ms"),
                       "p99_ms": {b: v.get("p99_ms") for b, v in (tr.get("by_block") or {}).items()},
-                      "miss": {b: v.get("miss_frac") for b, v in (tr.get("by_block") or {}).items()}}
+                      "miss": {b: v.get("miss_frac") for b, v in (tr.get("by_block") or {}).items()},
+                      "bf16split_groups": {"p99_ms": _get(tr, "groups_bf16split", "latency", "p99_ms"),
+                                           "miss": _get(tr, "groups_bf16split", "latency", "deadline_miss_frac"),
+                                           "rel_l2": _get(tr, "groups_bf16split", "check", "rel_l2")}}
             if tr else None}
         if "error" in sv:
             side["serving"] = {"error": str(sv["error"])[:120]}

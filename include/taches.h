@@ -522,10 +522,12 @@ tc_status tc_server_latencies(tc_server *srv, double *out, uint32_t *block, size
 /* As tc_server_latencies, and if parts is not NULL it also receives, per
  * block, three floats (seconds) that add up to its latency: ready -> taken
  * into a step by the worker, taken -> the step's copies and kernels enqueued,
- * enqueued -> results on the host. parts holds 3 * cap floats (caller-owned).
- * The paper has no counterpart (tracing of the serving loop). */
-tc_status tc_server_latencies_ex(tc_server *srv, double *out, uint32_t *block, float *parts, size_t cap,
-                                 size_t *n_out);
+ * enqueued -> results on the host. parts holds 3 * cap floats, kind cap bytes
+ * (both caller-owned, may be NULL). kind[i] tags block i's stream: 0 a plain
+ * stream (FP32 gather), 1 + precision (TC_FP32, TC_BF16, TC_BF16_SPLIT) a
+ * group. The paper has no counterpart (tracing of the serving loop). */
+tc_status tc_server_latencies_ex(tc_server *srv, double *out, uint32_t *block, float *parts, uint8_t *kind,
+                                 size_t cap, size_t *n_out);
 /* Monotonic clock of the poll timestamps (seconds). */
 double tc_server_clock(void);
 /* Options (value 0 or 1), set at any time:

@@ -108,7 +108,7 @@ _SIGS = {
     "tc_server_remove": [_vp, _u64],
     "tc_server_get_stats": [_vp, ctypes.POINTER(TcServerStats)],
     "tc_server_latencies": [_vp, _vp, _vp, _sz, ctypes.POINTER(_sz)],
-    "tc_server_latencies_ex": [_vp, _vp, _vp, _vp, _sz, ctypes.POINTER(_sz)],
+    "tc_server_latencies_ex": [_vp, _vp, _vp, _vp, _vp, _sz, ctypes.POINTER(_sz)],
     "tc_server_attach_source": [_vp, _u64, _vp, _sz, ctypes.c_double, ctypes.c_double],
     "tc_server_stream_state": [_vp, _u64, ctypes.POINTER(_int)],
     "tc_server_step_log": [_vp, _vp, _sz, ctypes.POINTER(_sz)],
@@ -536,22 +536,25 @@ def tc_server_latencies(srv: int, cap: int = 1 << 20):
 
 def tc_server_latencies_ex(srv: int, cap: int = 1 << 20):
     """As tc_server_latencies, plus a [n, 3] float32 array of each latency's parts (seconds): ready -> taken
-    into a step, taken -> enqueued, enqueued -> on the host."""
-    lats, blks, parts = [], [], []
+    into a step, taken -> enqueued, enqueued -> on the host; and a uint8 kind per block (0 plain stream,
+    1 + precision for a group)."""
+    lats, blks, parts, kinds = [], [], [], []
     while True:
         out = np.empty(int(cap), dtype=np.float64)
         blk = np.empty(int(cap), dtype=np.uint32)
         prt = np.empty((int(cap), 3), dtype=np.float32)
+        knd = np.empty(int(cap), dtype=np.uint8)
         n = _sz()
         _call("tc_server_latencies_ex", srv, out.ctypes.data_as(_vp), blk.ctypes.data_as(_vp),
-              prt.ctypes.data_as(_vp), out.size, ctypes.byref(n))
+              prt.ctypes.data_as(_vp), knd.ctypes.data_as(_vp), out.size, ctypes.byref(n))
         k = int(n.value)
         lats.append(out[:k])
         blks.append(blk[:k])
         parts.append(prt[:k])
+        kinds.append(knd[:k])
         if k < cap:
             break
-    return np.concatenate(lats), np.concatenate(blks), np.concatenate(parts)
+    return np.concatenate(lats), np.concatenate(blks), np.concatenate(parts), np.concatenate(kinds)
 
 
 def tc_server_step_log(srv: int, cap: int = 1 << 16) -> np.ndarray:

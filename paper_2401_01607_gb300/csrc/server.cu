@@ -97,6 +97,7 @@ struct SStream {
     // cores in the BF16 modes, K1 in FP32) runs them after the step's K1 work
     // list. hist, ir and d_vt stay unused.
     long long channels = 1;
+    int kind = 0;  // latency-log tag: 0 a plain stream (FP32 gather), 1 + precision for a group
     tc_stream *grp = nullptr;
     cudaEvent_t gdone = nullptr;  // the group's push of the current step is done
     std::mutex gmu;           // the group stream: worker pushes vs IR uploads
@@ -253,6 +254,7 @@ struct tc_server {
     // Parts of each recorded latency: ready -> collected into a step, collected
     // -> copies and kernels enqueued, enqueued -> results on the host.
     std::deque<std::array<float, 3>> lat_parts;
+    std::deque<uint8_t> lat_kind;  // the block's stream: 0 plain, 1 + precision for a group
     // Step log (tracing): the last kLogSteps steps, oldest first once full.
     std::vector<tc_server_step_rec> steplog;
     size_t steplog_next = 0;
@@ -1110,6 +1112,7 @@ tc_status complete(tc_server *srv, tc_server::StepBuf &b)
                 srv->lat_block.push_back((uint32_t)s->block);
                 srv->lat_parts.push_back({(float)(b.t_begin - blk.t_submit), (float)(b.t_launch - b.t_begin),
                                           (float)(t_done - b.t_launch)});
+                srv->lat_kind.push_back((uint8_t)s->kind);
                 srv->tap_macs += (double)blk.n * (double)s->L * (double)C;
                 if (!s->discard) {
                     OutBlock o;
@@ -1474,6 +1477,7 @@ tc_status tc_server_add_group(tc_server *srv, size_t channels, size_t L, size_t 
     s->L = (long long)L;
     s->block = (long long)block;
     s->channels = (long long)channels;
+    s->kind = 1 + precision;
     s->discard = (flags & TC_SERVER_DISCARD_OUTPUT) != 0;
     std::lock_guard<std::mutex> la(srv->mu_admin);
     S_CU(cudaSetDevice(srv->device));
@@ -1566,8 +1570,8 @@ tc_status tc_server_submit_many(tc_server *srv, size_t count, const uint64_t *id
     return TC_OK;
 }
 
-tc_status tc_server_latencies_ex(tc_server *srv, double *out, uint32_t *block, float *parts, size_t cap,
-                                 size_t *n_out)
+tc_status tc_server_latencies_ex(tc_server *srv, double *out, uint32_t *block, float *parts, uint8_t *kind,
+                                 size_t cap, size_t *n_out)
 {
     if (!srv || !n_out || (cap && !out))
         return sfail(TC_EINVAL, "tc_server_latencies: bad arguments");
@@ -1580,16 +1584,19 @@ tc_status tc_server_latencies_ex(tc_server *srv, double *out, uint32_t *block, f
         for (size_t i = 0; i < n; ++i)
             for (int k = 0; k < 3; ++k)
                 parts[3 * i + (size_t)k] = srv->lat_parts[i][(size_t)k];
+    if (kind)
+        std::copy(srv->lat_kind.begin(), srv->lat_kind.begin() + (long)n, kind);
     srv->lat.erase(srv->lat.begin(), srv->lat.begin() + (long)n);
     srv->lat_block.erase(srv->lat_block.begin(), srv->lat_block.begin() + (long)n);
     srv->lat_parts.erase(srv->lat_parts.begin(), srv->lat_parts.begin() + (long)n);
+    srv->lat_kind.erase(srv->lat_kind.begin(), srv->lat_kind.begin() + (long)n);
     *n_out = n;
     return TC_OK;
 }
 
 tc_status tc_server_latencies(tc_server *srv, double *out, uint32_t *block, size_t cap, size_t *n_out)
 {
-    return tc_server_latencies_ex(srv, out, block, nullptr, cap, n_out);
+    return tc_server_latencies_ex(srv, out, block, nullptr, nullptr, cap, n_out);
 }
 
 tc_status tc_server_attach_source(tc_server *srv, uint64_t id, const float *x, size_t n, double t0, double fs)

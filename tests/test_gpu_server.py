@@ -216,8 +216,9 @@ def test_worker_thread_continuous_batching():
                     outs[i].append(y[:n].copy())
         capi.tc_server_stop(srv)
         assert sum(map(len, outs)) == total
-        lat, blk, parts = capi.tc_server_latencies_ex(srv)
+        lat, blk, parts, kind = capi.tc_server_latencies_ex(srv)
         assert lat.size == total and np.all(lat >= 0)
+        assert np.all(kind == 0)  # plain streams only
         assert set(blk.tolist()) <= {t.block for (t, x, H, vs) in streams}
         # The three parts (ready -> taken, taken -> enqueued, enqueued -> on the host) add up to each latency
         # (float32 parts of float64 latencies), and only the first can be negative: never.
@@ -399,22 +400,40 @@ def _poll_group(srv, gid, C, block, outs):
 @pytest.mark.parametrize("prec", ["bf16split", "bf16", "fp32"])
 def test_group_in_a_mix_matches_oracle(prec):
     """A 200-channel group (two 128-channel tiles, the second ragged) with an IR switch inside a block,
-    served in changing mixes with two plain streams; every channel against the oracle."""
-    code = {"fp32": capi.TC_FP32, "bf16": capi.TC_BF16, "bf16split": capi.TC_BF16_SPLIT}[prec]
+    served in changing mixes with two plain streams, and alone; every channel against the oracle, and the
+    group's output in the mix against its output alone."""
     C, N, L, B = 200, 5_000, 3_000, 128
     X = synth.audio_block(C, N, 600)
     H = np.stack([synth.decayed_ir(L, 0.2 * L, 700 + v) for v in range(2)])
     vstart = [0, 2_600]
-    plain = _small_trace(k=2, seed=9)
+    ref = _group_ref(X, H, vstart, B)
+    y_mix, st = _group_run(prec, X, H, vstart, L, B, _small_trace(k=2, seed=9))
+    y_alone, _ = _group_run(prec, X, H, vstart, L, B, [])
+    err, err_alone, err_am = rel_l2(y_mix, ref), rel_l2(y_alone, ref), rel_l2(y_mix, y_alone)
+    print(f"group {prec}: mix {err:.3g}, alone {err_alone:.3g}, mix vs alone {err_am:.3g}, "
+          f"tensor launches {st.tensor_launches}, fallbacks {st.fp32_fallbacks}")
+    assert err <= TOL[prec] and err_alone <= TOL[prec] and err_am <= TOL[prec]
+    if prec != "fp32":
+        assert st.tensor_launches > 0 and st.fp32_fallbacks > 0  # the switch's windows ran on the gather
+    else:
+        assert st.tensor_launches == 0
+
+
+def _group_run(prec, X, H, vstart, L, B, plain):
+    """Serves the group (and the plain streams, in changing mixes) through manual steps; returns the group's
+    [C, N + L - 1] output and the server's stats."""
+    code = {"fp32": capi.TC_FP32, "bf16": capi.TC_BF16, "bf16split": capi.TC_BF16_SPLIT}[prec]
+    C, N = X.shape
+    np_ = len(plain)
     srv = capi.tc_server_open(8 << 30, 1 << 20)
     try:
         gid = capi.tc_server_add_group(srv, C, L, B, H[0], code)
         pids = [capi.tc_server_add(srv, t.L, t.block, Hp[0]) for (t, x, Hp, vs) in plain]
         nblk_g = -(-N // B)
-        sent_g, sent_p = 0, [0, 0]
-        outs_g, outs_p = [], [[], []]
+        sent_g, sent_p = 0, [0] * np_
+        outs_g, outs_p = [], [[] for _ in range(np_)]
         rng = np.random.default_rng(3)
-        while sent_g < nblk_g or any(sent_p[i] < -(-plain[i][0].n // plain[i][0].block) for i in range(2)):
+        while sent_g < nblk_g or any(sent_p[i] < -(-plain[i][0].n // plain[i][0].block) for i in range(np_)):
             for _ in range(int(rng.integers(0, 3))):
                 if sent_g < nblk_g:
                     lo, hi = sent_g * B, min(N, (sent_g + 1) * B)
@@ -464,14 +483,7 @@ def test_group_in_a_mix_matches_oracle(prec):
     finally:
         capi.tc_server_close(srv)
     assert yg.shape == (C, N + L - 1)
-    ref = _group_ref(X, H, vstart, B)
-    err = rel_l2(yg, ref)
-    print(f"group {prec}: rel_l2={err:.3g}, tensor launches {st.tensor_launches}, fallbacks {st.fp32_fallbacks}")
-    assert err <= TOL[prec]
-    if prec != "fp32":
-        assert st.tensor_launches > 0 and st.fp32_fallbacks > 0  # the switch's windows ran on the gather
-    else:
-        assert st.tensor_launches == 0
+    return yg, st
 
 
 @pytest.mark.parametrize("prec", ["bf16split", "fp32"])

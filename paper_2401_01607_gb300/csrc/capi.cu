@@ -784,6 +784,36 @@ long long k2_plan_nsplit(long long tiles, long long nkb, int sms)
 
 // K2 on the tensor cores when every input sample of the launch's window
 // spawned its tache with the same IR version; false in *used otherwise.
+// Buffers (and tensor maps) of the Toeplitz tiles of IR slot `slot` at shift
+// `delta`, with room for nkb K blocks; allocated once (stream-ordered: no host
+// or device-wide synchronisation while pushes are in flight).
+tc_status ensure_tset_mem(tc_stream *s, int slot, int delta, long long nkb)
+{
+    const int TN = tc::k2_tile_n(), KB = tc::k2_kblock();
+    tc_stream::TSet &ts = s->tsets[(size_t)slot][(size_t)delta];
+    if (ts.thi && ts.nkb >= nkb)
+        return TC_OK;
+    if (ts.thi)
+        cudaFreeAsync(ts.thi, s->cs);
+    if (ts.tlo)
+        cudaFreeAsync(ts.tlo, s->cs);
+    ts.thi = ts.tlo = nullptr;
+    ts.ready = false;
+    const size_t bytes = (size_t)nkb * TN * KB * 2;
+    TC_CU(tc::pool_alloc(&ts.thi, bytes, s->cs));
+    TC_CU(tc::pool_alloc(&ts.tlo, bytes, s->cs));
+    TC_ALIGNED(ts.thi);
+    TC_ALIGNED(ts.tlo);
+    ts.nkb = nkb;
+    TC_CU(tc::encode_bf16_2d(&ts.mt_hi, ts.thi, (unsigned long long)KB, (unsigned long long)nkb * TN,
+                             (unsigned long long)KB * 2, KB, TN));
+    TC_CU(tc::encode_bf16_2d(&ts.mt_lo, ts.tlo, (unsigned long long)KB, (unsigned long long)nkb * TN,
+                             (unsigned long long)KB * 2, KB, TN));
+    TC_CU(tc::encode_bf16_2d(&ts.mt2_hi, ts.thi, (unsigned long long)KB, (unsigned long long)nkb * TN,
+                             (unsigned long long)KB * 2, KB, TN / 2));
+    return TC_OK;
+}
+
 tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long long y_pitch, bool *used)
 {
     *used = false;
@@ -808,27 +838,7 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
     const int slot = s->vt[(size_t)v].slot;
     tc_stream::TSet &ts = s->tsets[(size_t)slot][(size_t)delta];
     if (!ts.ready) {
-        if (!ts.thi || ts.nkb < nkb) {
-            // Stream-ordered: no host or device-wide synchronisation while
-            // pushes of this or other streams are in flight.
-            if (ts.thi)
-                cudaFreeAsync(ts.thi, s->cs);
-            if (ts.tlo)
-                cudaFreeAsync(ts.tlo, s->cs);
-            ts.thi = ts.tlo = nullptr;
-            const size_t bytes = (size_t)nkb * TN * KB * 2;
-            TC_CU(tc::pool_alloc(&ts.thi, bytes, s->cs));
-            TC_CU(tc::pool_alloc(&ts.tlo, bytes, s->cs));
-            TC_ALIGNED(ts.thi);
-            TC_ALIGNED(ts.tlo);
-            ts.nkb = nkb;
-            TC_CU(tc::encode_bf16_2d(&ts.mt_hi, ts.thi, (unsigned long long)KB, (unsigned long long)nkb * TN,
-                                     (unsigned long long)KB * 2, KB, TN));
-            TC_CU(tc::encode_bf16_2d(&ts.mt_lo, ts.tlo, (unsigned long long)KB, (unsigned long long)nkb * TN,
-                                     (unsigned long long)KB * 2, KB, TN));
-            TC_CU(tc::encode_bf16_2d(&ts.mt2_hi, ts.thi, (unsigned long long)KB, (unsigned long long)nkb * TN,
-                                     (unsigned long long)KB * 2, KB, TN / 2));
-        }
+        TC_TRY(ensure_tset_mem(s, slot, delta, nkb));
         // The slot's unshifted fp32 copy (shift e = 0) holds h[k] at index k.
         const float *h = s->ir + (size_t)slot * s->nsets * 4 * (size_t)s->Lpad;
         TC_CU(tc::k2_tprep_launch(h, (int)L, delta, (int)nkb, ts.thi, ts.tlo, s->cs));
@@ -1211,9 +1221,12 @@ tc_status group_open(size_t channels, size_t L, size_t max_push, int precision, 
         size_t need = 0;
         for (long long no = 1; no <= ((long long)max_push + TN - 1) / TN; ++no) {
             const long long tiles = (s->prec == TC_BF16 ? (ntile_c1 + 1) / 2 : ntile_c1) * no;
-            const long long ns = k2_plan_nsplit(tiles, nkb, sms);
-            if (ns > 1)
-                need = std::max(need, (size_t)(2 * ((ntile_c1 + 1) / 2) * no * ns * TM * TN));
+            // Plain BF16 on CTA pairs plans its K parts over half the SMs.
+            for (int slots : {sms, sms / 2}) {
+                const long long ns = k2_plan_nsplit(tiles, nkb, slots);
+                if (ns > 1)
+                    need = std::max(need, (size_t)(2 * ((ntile_c1 + 1) / 2) * no * ns * TM * TN));
+            }
         }
         if (need > 0) {
             tc_status st = TC_OK;
@@ -1227,6 +1240,20 @@ tc_status group_open(size_t channels, size_t L, size_t max_push, int precision, 
                 *out = nullptr;
                 return st;
             }
+        }
+    }
+    if (s->prec != TC_FP32) {
+        // The Toeplitz tiles of the first IR version (slot 0) at the shift of
+        // pushes from sample 0 (pushes at multiples of 8 samples keep it), now:
+        // allocating them at the first push would map memory while other
+        // streams' steps run. Later versions' slots still allocate at their
+        // first push.
+        const int delta0 = (int)((((0 - (long long)L + 1 - s->base) % 8) + 8) % 8);
+        tc_status st = ensure_tset_mem(s, 0, delta0, tc::k2_nkb((long long)L, delta0));
+        if (st != TC_OK) {
+            tc_close(s);
+            *out = nullptr;
+            return st;
         }
     }
     // Device footprint: what open allocated, plus what the tensor-core

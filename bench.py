@@ -1048,6 +1048,8 @@ def bench_capacity(torch, capi, H64: np.ndarray, pool: np.ndarray, paced_s: floa
             r = dict(_lat_summary(lat, blk), streams=M, seconds_of_audio=paced_s, warmup_s=warm,
                      steps=int(steps), blocks_per_step=(st1.blocks - st0.blocks) / max(steps, 1),
                      pool_admissions=int(st1.pool_admissions), step_buffer_grows=int(st1.grows - st0.grows),
+                     host_us_per_block={k: 1e6 * (getattr(st1, "host_" + k + "_s") - getattr(st0, "host_" + k + "_s")) /
+                                        max(st1.blocks - st0.blocks, 1) for k in ("collect", "pack", "deliver")},
                      served_tap_macs_per_s=(st1.tap_macs - st0.tap_macs) / wall,
                      k1=_k1_roofline(st0, st1))
             r["pass"] = bool(r.get("blocks", 0) > 0 and r["p99_ms"] <= period * 1e3

@@ -419,6 +419,9 @@ typedef struct tc_server_stats {
     uint64_t pool_admissions;  /* tc_server_add admissions whose state did not fit tc_server_reserve's
                                   reservation (allocated from the pool) */
     uint64_t grows;      /* growths of the steps' own buffers (allocations made inside a step) */
+    double host_collect_s;  /* worker thread host time: taking queued blocks into steps (seconds) */
+    double host_pack_s;     /* packing inputs and work items, enqueueing copies and kernels */
+    double host_deliver_s;  /* delivering finished steps (outputs, latencies, positions) */
 } tc_server_stats;
 
 /* Opens a server on the current CUDA device. mem_budget_bytes bounds the

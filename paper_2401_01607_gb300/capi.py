@@ -45,7 +45,8 @@ class TcServerStats(ctypes.Structure):
                 ("busy_s", ctypes.c_double), ("tap_macs", ctypes.c_double),
                 ("tensor_launches", ctypes.c_uint64), ("fp32_fallbacks", ctypes.c_uint64),
                 ("k1_ms", ctypes.c_double), ("k1_macs", ctypes.c_double), ("pool_admissions", ctypes.c_uint64),
-                ("grows", ctypes.c_uint64)]
+                ("grows", ctypes.c_uint64), ("host_collect_s", ctypes.c_double), ("host_pack_s", ctypes.c_double),
+                ("host_deliver_s", ctypes.c_double)]
 
 
 class TcServerStepRec(ctypes.Structure):

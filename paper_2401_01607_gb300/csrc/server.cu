@@ -35,6 +35,7 @@
 #include <queue>
 #include <string>
 #include <thread>
+#include <unordered_map>
 #include <unordered_set>
 #include <vector>
 
@@ -162,7 +163,7 @@ struct tc_server {
     std::mutex mu_state;  // host state the steps read (positions, versions, budget)
     std::mutex mu_queue;  // pending input / finished output queues
     std::condition_variable cv;
-    std::map<uint64_t, std::unique_ptr<SStream>> streams;
+    std::unordered_map<uint64_t, std::unique_ptr<SStream>> streams;  // O(1) lookups per released block
     uint64_t next_id = 1;
     size_t npending = 0;  // blocks queued over all streams (queue mutex)
     // Streams with queued blocks, in the order they became ready (queue
@@ -181,8 +182,8 @@ struct tc_server {
     // 16 bytes][packed output], copied back with one device-to-host copy.
     struct Item {
         SStream *s;
-        std::vector<Block> blocks;
-        long long off, n;  // packed input / output offset (floats); samples per row
+        uint32_t first, count;  // the item's blocks: StepBuf::blocks[first, first + count)
+        long long off, n;       // packed input / output offset (floats); samples per row
     };
     struct StepBuf {
         char *pin_stage = nullptr;
@@ -192,6 +193,7 @@ struct tc_server {
         cudaEvent_t done = nullptr;
         cudaEvent_t in_ready = nullptr;  // the step's packed input is on the device (groups wait on it)
         std::vector<Item> items;
+        std::vector<Block> blocks;  // every item's blocks, in item order (kept allocated across steps)
         size_t total = 0;
         double t_begin = 0.0, t_launch = 0.0;
         long long ctas = 0;
@@ -263,6 +265,7 @@ struct tc_server {
     double tap_macs = 0.0;
     uint64_t tensor_launches = 0, fp32_fallbacks = 0;  // group pushes (state mutex)
     uint64_t pool_admissions = 0;  // admissions whose state did not fit the reservation (state mutex)
+    double host_collect_s = 0.0, host_pack_s = 0.0, host_deliver_s = 0.0;  // worker host time per phase
     uint64_t grows = 0;            // step-buffer growths (allocations inside steps)
     double k1_ms = 0.0, k1_macs = 0.0;                  // K1 work-list launches: event time, tap-MACs
 };
@@ -685,6 +688,18 @@ double release_sources(tc_server *srv, double now)
     return srv->src_heap.empty() ? 1e300 : srv->src_heap.top().first;
 }
 
+// The blocks of item w of step buffer b.
+struct BlockSpan {
+    Block *b, *e;
+    Block *begin() const { return b; }
+    Block *end() const { return e; }
+};
+BlockSpan blocks_of(tc_server::StepBuf &b, const tc_server::Item &w)
+{
+    Block *p = b.blocks.data() + w.first;
+    return {p, p + w.count};
+}
+
 // Takes the queued blocks of every ready stream (up to kMerge consecutive
 // blocks of a stream as one item) into step buffer b. Round robin: when a
 // step is full, the next one starts with the streams that did not fit.
@@ -693,6 +708,7 @@ size_t collect(tc_server *srv, tc_server::StepBuf &b)
 {
     tc::Range nvtx_range("server step: collect");
     b.items.clear();
+    b.blocks.clear();
     b.total = 0;
     size_t nblocks = 0;
     std::lock_guard<std::mutex> lk(srv->mu_queue);
@@ -711,9 +727,9 @@ size_t collect(tc_server *srv, tc_server::StepBuf &b)
     // of s did not fit the step (it stays queued).
     auto take = [&](SStream *s) {
         bool fits = true;
-        tc_server::Item it{s, {}, (long long)b.total, 0};
+        tc_server::Item it{s, (uint32_t)b.blocks.size(), 0, (long long)b.total, 0};
         const long long nch_max = (s->L + 3 + tc::k1_chunk_taps(tc::K1_P1) - 1) / tc::k1_chunk_taps(tc::K1_P1);
-        while (!s->pending.empty() && (int)it.blocks.size() < kMerge) {
+        while (!s->pending.empty() && (int)it.count < kMerge) {
             Block &blk = s->pending.front();
             const size_t fl = (size_t)(blk.n * s->channels);  // packed floats
             if (b.total + fl > srv->max_step_samples) {
@@ -723,9 +739,9 @@ size_t collect(tc_server *srv, tc_server::StepBuf &b)
             if (!s->grp) {
                 const size_t dt = (size_t)((it.n + blk.n + tc::K1_MO - 1) / tc::K1_MO - (it.n + tc::K1_MO - 1) / tc::K1_MO);
                 const size_t ds = dt * (size_t)nch_max * tc::K1_MO;
-                const bool first = b.items.empty() && it.blocks.empty();
+                const bool first = b.items.empty() && it.count == 0;
                 if (!first && (tiles + dt > srv->counters_n || scratch + ds > srv->scratch_floats ||
-                               (it.blocks.empty() && b.items.size() + 1 > items_cap))) {
+                               (it.count == 0 && b.items.size() + 1 > items_cap))) {
                     fits = false;
                     break;
                 }
@@ -734,14 +750,15 @@ size_t collect(tc_server *srv, tc_server::StepBuf &b)
             }
             b.total += fl;
             it.n += blk.n;
-            it.blocks.push_back(std::move(blk));
+            b.blocks.push_back(std::move(blk));
+            it.count++;
             s->pending.pop_front();
             srv->npending--;
         }
-        if (!it.blocks.empty()) {
-            nblocks += it.blocks.size();
+        if (it.count) {
+            nblocks += it.count;
             s->inflight++;
-            b.items.push_back(std::move(it));
+            b.items.push_back(it);
         }
         return fits;
     };
@@ -903,7 +920,7 @@ tc_status pack_launch(tc_server *srv, tc_server::StepBuf &b)
     for (auto &w : b.items) {
         const long long C = w.s->channels;
         long long o = 0;
-        for (auto &blk : w.blocks) {
+        for (auto &blk : blocks_of(b, w)) {
             for (long long c = 0; c < C; ++c)
                 std::memcpy(st_in + w.off + c * w.n + o, blk.data() + c * blk.n, (size_t)blk.n * sizeof(float));
             o += blk.n;
@@ -1064,6 +1081,11 @@ tc_status complete(tc_server *srv, tc_server::StepBuf &b)
     tc::Range nvtx_range("server step: wait and deliver");
     S_CU(cudaEventSynchronize(b.done));
     const double t_done = now_s();
+    struct DeliverTimer {  // host time spent delivering this step's outputs
+        tc_server *srv;
+        double t0;
+        ~DeliverTimer() { srv->host_deliver_s += now_s() - t0; }
+    } deliver_timer{srv, t_done};
     std::lock_guard<std::mutex> lk(srv->mu_state);
     if (*reinterpret_cast<int *>(b.pin_out)) {
         cudaMemsetAsync(srv->d_out, 0, sizeof(int), srv->cs);
@@ -1099,7 +1121,7 @@ tc_status complete(tc_server *srv, tc_server::StepBuf &b)
         const long long C = s->channels;
         const float *yo = b.pin_out + 4 + w.off;  // [C][w.n]
         long long boff = 0;
-        for (auto &blk : w.blocks) {
+        for (auto &blk : blocks_of(b, w)) {
             if (blk.tail) {
                 const long long tail = s->L - 1;  // tail_out is [C][tail]
                 if (s->tail_fill + blk.n <= tail && (long long)s->tail_out.size() == C * tail)
@@ -1183,11 +1205,15 @@ void worker_main(tc_server *srv)
         bool launched = false;
         if (!stopping) {
             std::lock_guard<std::mutex> lk(srv->mu_state);
+            const double h0 = now_s();
             if (collect(srv, srv->buf[nb]) > 0) {
+                const double h1 = now_s();
                 if (pack_launch(srv, srv->buf[nb]) != TC_OK) {
                     fail("launch");
                     break;
                 }
+                srv->host_collect_s += h1 - h0;
+                srv->host_pack_s += now_s() - h1;
                 launched = true;
             }
         }
@@ -1813,6 +1839,9 @@ tc_status tc_server_get_stats(tc_server *srv, tc_server_stats *st)
     st->k1_macs = srv->k1_macs;
     st->pool_admissions = srv->pool_admissions;
     st->grows = srv->grows;
+    st->host_collect_s = srv->host_collect_s;
+    st->host_pack_s = srv->host_pack_s;
+    st->host_deliver_s = srv->host_deliver_s;
     st->fp32_fallbacks = srv->fp32_fallbacks;
     return TC_OK;
 }

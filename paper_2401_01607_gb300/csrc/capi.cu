@@ -615,6 +615,8 @@ tc_status ensure_room(tc_stream *s, long long n)
                             cudaMemcpyDeviceToDevice, s->cs));
     if (s->hist_hi) {
         for (void *hb : {s->hist_hi, s->hist_lo}) {
+            if (hb == s->hist_lo && s->prec == TC_BF16)
+                continue;  // plain BF16 never reads the lo history
             char *b = static_cast<char *>(hb);
             TC_CU(cudaMemcpy2DAsync(b, (size_t)s->cap * 2, b + shift * 2, (size_t)s->cap * 2, (size_t)len * 2,
                                     s->rows, cudaMemcpyDeviceToDevice, s->cs));
@@ -629,7 +631,8 @@ tc_status split_new(tc_stream *s, long long col0, long long n)
 {
     if (!s->hist_hi)
         return TC_OK;
-    TC_CU(tc::k2_split_launch(s->hist, s->cap, (int)s->rows, col0, n, s->hist_hi, s->hist_lo, s->cs));
+    TC_CU(tc::k2_split_launch(s->hist, s->cap, (int)s->rows, col0, n, s->hist_hi,
+                              s->prec == TC_BF16 ? nullptr : s->hist_lo, s->cs));  // plain BF16 reads hi only
     return TC_OK;
 }
 
@@ -841,7 +844,8 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
         TC_TRY(ensure_tset_mem(s, slot, delta, nkb));
         // The slot's unshifted fp32 copy (shift e = 0) holds h[k] at index k.
         const float *h = s->ir + (size_t)slot * s->nsets * 4 * (size_t)s->Lpad;
-        TC_CU(tc::k2_tprep_launch(h, (int)L, delta, (int)nkb, ts.thi, ts.tlo, s->cs));
+        TC_CU(tc::k2_tprep_launch(h, (int)L, delta, (int)nkb, ts.thi, s->prec == TC_BF16 ? nullptr : ts.tlo,
+                                  s->cs));
         ts.ready = true;
     }
     tc::K2Params p{};

@@ -632,7 +632,8 @@ __global__ void k2_reduce(const float *__restrict__ partial, int nsplit, int C, 
 
 // Materialises the Toeplitz tiles of one IR for alignment shift delta:
 //   T[kb][i][j] = h[L - 1 + delta + i - 32 kb - j]  (0 outside [0, L)),
-// as bf16 hi = bf16(h) and lo = bf16(h - hi), row-major [kb][256][32].
+// as bf16 hi = bf16(h) and lo = bf16(h - hi), row-major [kb][256][32]
+// (tlo may be null: plain BF16).
 __global__ void k2_tprep(const float *__restrict__ h, int L, int delta, int nkb, __nv_bfloat16 *thi,
                          __nv_bfloat16 *tlo)
 {
@@ -647,12 +648,14 @@ __global__ void k2_tprep(const float *__restrict__ h, int L, int delta, int nkb,
         const float v = (k >= 0 && k < L) ? h[k] : 0.f;
         const __nv_bfloat16 hi = __float2bfloat16_rn(v);
         thi[q] = hi;
-        tlo[q] = __float2bfloat16_rn(v - __bfloat162float(hi));
+        if (tlo)  // plain BF16 reads only the hi tiles
+            tlo[q] = __float2bfloat16_rn(v - __bfloat162float(hi));
     }
 }
 
 // Splits new history samples into bf16 hi = bf16(x) and lo = bf16(x - hi):
-// rows r < rows, columns [col0, col0 + n) of pitch-`pitch` histories.
+// rows r < rows, columns [col0, col0 + n) of pitch-`pitch` histories (hlo
+// may be null: plain BF16).
 __global__ void k2_split(const float *__restrict__ hist, long long pitch, int rows, long long col0, long long n,
                          __nv_bfloat16 *hhi, __nv_bfloat16 *hlo)
 {
@@ -664,7 +667,8 @@ __global__ void k2_split(const float *__restrict__ hist, long long pitch, int ro
         const float v = hist[idx];
         const __nv_bfloat16 hi = __float2bfloat16_rn(v);
         hhi[idx] = hi;
-        hlo[idx] = __float2bfloat16_rn(v - __bfloat162float(hi));
+        if (hlo)  // plain BF16 reads only the hi history
+            hlo[idx] = __float2bfloat16_rn(v - __bfloat162float(hi));
     }
 }
 

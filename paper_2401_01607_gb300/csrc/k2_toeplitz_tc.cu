@@ -672,6 +672,20 @@ __global__ void k2_split(const float *__restrict__ hist, long long pitch, int ro
     }
 }
 
+// hhi[dst_off + i] = bf16(src[i]) and hlo[dst_off + i] = bf16(src[i] - hi),
+// i < n (hlo may be null: plain BF16).
+__global__ void k2_split_shift(const float *__restrict__ src, long long n, long long dst_off, __nv_bfloat16 *hhi,
+                               __nv_bfloat16 *hlo)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float v = src[i];
+        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+        hhi[dst_off + i] = hi;
+        if (hlo)
+            hlo[dst_off + i] = __float2bfloat16_rn(v - __bfloat162float(hi));
+    }
+}
+
 unsigned grid_for(long long work)
 {
     long long b = (work + 255) / 256;
@@ -701,6 +715,16 @@ cudaError_t k2_split_launch(const float *hist, long long pitch, int rows, long l
         return cudaSuccess;
     k2_split<<<grid_for((long long)rows * n), 256, 0, st>>>(hist, pitch, rows, col0, n, (__nv_bfloat16 *)hhi,
                                                            (__nv_bfloat16 *)hlo);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t k2_split_shift_launch(const float *src, long long n, long long dst_off, void *hhi, void *hlo,
+                                  cudaStream_t st)
+{
+    if (n <= 0)
+        return cudaSuccess;
+    k2_split_shift<<<grid_for(n), 256, 0, st>>>(src, n, dst_off, (__nv_bfloat16 *)hhi, (__nv_bfloat16 *)hlo);
     count_launch();
     return cudaGetLastError();
 }

@@ -377,7 +377,8 @@ extern "C" tc_status tc_convolve_tc(const float *x, size_t N, const float *h, si
         pair = false;
         p.ntile_c = (int)ntile_c1;
     }
-    const size_t b_xs = (size_t)npad * 4, b_xb = (size_t)npad * 2, b_t = (size_t)nkb * TN * KB * 2;
+    // The bf16 input rows are split straight from x into the padded buffers (zero margins before and after).
+    const size_t b_xs = 0, b_xb = (size_t)npad * 2, b_t = (size_t)nkb * TN * KB * 2;
     const size_t b_y = (size_t)R * TN * 4;
     const size_t b_part = nsplit > 1 ? (size_t)2 * ((ntile_c1 + 1) / 2) * nsplit * TM * TN * 4 : 0;
     const size_t o_xs = 0, o_hi = o_xs + ru(b_xs, 256), o_lo = o_hi + ru(b_xb, 256), o_th = o_lo + ru(b_xb, 256);
@@ -392,7 +393,6 @@ extern "C" tc_status tc_convolve_tc(const float *x, size_t N, const float *h, si
         cudaFreeAsync(mem, cs);
         return na_fail(TC_ECUDA, "tc_convolve_tc: the stream-ordered allocation is not 256-byte aligned");
     }
-    float *xs = reinterpret_cast<float *>(mem + o_xs);
     void *xhi = mem + o_hi, *xlo = mem + o_lo, *thi = mem + o_th, *tlo = mem + o_tl;
     float *ytmp = reinterpret_cast<float *>(mem + o_y);
     int *err = reinterpret_cast<int *>(mem + o_err);
@@ -416,12 +416,18 @@ extern "C" tc_status tc_convolve_tc(const float *x, size_t N, const float *h, si
         e = tc::encode_bf16_2d(&mt2_hi, thi, KB, (unsigned long long)nkb * TN, KB * 2, KB, TN / 2);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(err, 0, sizeof(int), cs);
+    // xs[m] = x[m - off] with zeros around it, as bf16 hi (and lo for the split; plain BF16 reads hi only).
+    for (void *xb : {xhi, xlo}) {
+        if (xb == xlo && nprod == 1)
+            continue;
+        char *b = static_cast<char *>(xb);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(b, 0, (size_t)off * 2, cs);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(b + (size_t)(off + Nl) * 2, 0, (size_t)(npad - off - Nl) * 2, cs);
+    }
     if (e == cudaSuccess)
-        e = cudaMemsetAsync(xs, 0, b_xs, cs);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(xs + off, x, (size_t)Nl * 4, cudaMemcpyDeviceToDevice, cs);
-    if (e == cudaSuccess)
-        e = tc::k2_split_launch(xs, npad, 1, 0, npad, xhi, nprod == 1 ? nullptr : xlo, cs);  // plain: hi only
+        e = tc::k2_split_shift_launch(x, Nl, off, xhi, nprod == 1 ? nullptr : xlo, cs);
     if (e == cudaSuccess)
         e = tc::k2_tprep_launch(h, (int)Ll, 0, (int)nkb, thi, nprod == 1 ? nullptr : tlo, cs);
     if (e == cudaSuccess)

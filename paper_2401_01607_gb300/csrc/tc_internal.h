@@ -162,6 +162,9 @@ long long k2_nkb(long long L, int delta);
 size_t k2_smem_bytes(int nprod);
 // Toeplitz tiles of IR h (fp32, L taps) for shift delta: hi/lo bf16 [nkb][256][32].
 cudaError_t k2_tprep_launch(const float *h, int L, int delta, int nkb, void *thi, void *tlo, cudaStream_t st);
+// bf16 hi/lo split of src[0, n) into hhi/hlo[dst_off, dst_off + n) (hlo may be null).
+cudaError_t k2_split_shift_launch(const float *src, long long n, long long dst_off, void *hhi, void *hlo,
+                                  cudaStream_t st);
 // bf16 hi/lo split of history columns [col0, col0 + n) of `rows` rows.
 cudaError_t k2_split_launch(const float *hist, long long pitch, int rows, long long col0, long long n, void *hhi,
                             void *hlo, cudaStream_t st);

@@ -1020,6 +1020,8 @@ def bench_capacity(torch, capi, H64: np.ndarray, pool: np.ndarray, paced_s: floa
         # Paced runs: live sources, worker thread.
         def paced(M, seed=11):
             set_count(M, fresh=True)
+            capi.tc_server_latencies(srv)  # empty the log (the worker is stopped)
+            b_start = capi.tc_server_get_stats(srv).blocks
             rng = np.random.default_rng(seed)
             warm = 1.2  # seconds of audio before recording starts: past L = 1 s, every history full
             n_src = int((warm + paced_s) * FS)
@@ -1031,8 +1033,10 @@ def bench_capacity(torch, capi, H64: np.ndarray, pool: np.ndarray, paced_s: floa
                                              t_start + rng.uniform(0, period))
             while capi.tc_server_clock() < t_start + warm:
                 time.sleep(0.01)
-            capi.tc_server_latencies(srv)  # warm-up blocks are not counted
+            # Warm-up blocks are not counted: the log is read once at the end and the records of the blocks
+            # completed before st0 (completion order) dropped, so that nothing reads it while the worker runs.
             st0 = capi.tc_server_get_stats(srv)
+            n_warm = st0.blocks - b_start
             t_rec = capi.tc_server_clock()
             t_end = t_start + warm + paced_s + period + 2.0
             while capi.tc_server_clock() < t_end:
@@ -1043,6 +1047,7 @@ def bench_capacity(torch, capi, H64: np.ndarray, pool: np.ndarray, paced_s: floa
             capi.tc_server_stop(srv)
             st1 = capi.tc_server_get_stats(srv)
             lat, blk = capi.tc_server_latencies(srv)
+            lat, blk = lat[n_warm:], blk[n_warm:]
             steps = st1.steps - st0.steps
             wall = max(capi.tc_server_clock() - t_rec, 1e-9)
             r = dict(_lat_summary(lat, blk), streams=M, seconds_of_audio=paced_s, warmup_s=warm,
@@ -1152,8 +1157,7 @@ def bench_groups(capi, paced_s: float = 1.5, C: int = 128, L: int = 96_000, B: i
                     capi.tc_server_attach_source(srv, sid, src, t_start + rng.uniform(0, period))
                 while capi.tc_server_clock() < t_start + warm:
                     time.sleep(0.01)
-                capi.tc_server_latencies(srv)
-                st0 = capi.tc_server_get_stats(srv)
+                st0 = capi.tc_server_get_stats(srv)  # its first st0.blocks latency records are the warm-up's
                 t_rec = capi.tc_server_clock()
                 t_end = t_start + n_src / FS + period + 3.0
                 while capi.tc_server_clock() < t_end:
@@ -1163,6 +1167,7 @@ def bench_groups(capi, paced_s: float = 1.5, C: int = 128, L: int = 96_000, B: i
                 capi.tc_server_stop(srv)
                 st1 = capi.tc_server_get_stats(srv)
                 lat, blk = capi.tc_server_latencies(srv)
+                lat, blk = lat[st0.blocks:], blk[st0.blocks:]
                 wall = max(capi.tc_server_clock() - t_rec, 1e-9)
                 steps = st1.steps - st0.steps
                 r = dict(_lat_summary(lat, blk), groups=G, channels=G * C, steps=int(steps),

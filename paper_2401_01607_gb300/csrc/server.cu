@@ -260,6 +260,11 @@ struct tc_server {
     // Step log (tracing): the last kLogSteps steps, oldest first once full.
     std::vector<tc_server_step_rec> steplog;
     size_t steplog_next = 0;
+    // A reader swaps the log with this spare under the queue mutex and copies
+    // it out without holding that mutex (a copy under it held the worker's
+    // next step back by milliseconds). mu_log_reader serialises readers.
+    std::vector<tc_server_step_rec> steplog_spare;
+    std::mutex mu_log_reader;
     uint64_t steps = 0, blocks = 0, rejected = 0;
     double busy_s = 0.0;
     double tap_macs = 0.0;
@@ -1318,6 +1323,7 @@ tc_status tc_server_open(size_t mem_budget_bytes, size_t max_step_samples, tc_se
     tc::K1Plan plan{};
     S_CU(tc::k1_plan(1000, 0, 1, 1, 1, -1, &plan));
     srv->steplog.reserve(kLogSteps);
+    srv->steplog_spare.reserve(kLogSteps);
     *out = srv.release();
     return TC_OK;
 }
@@ -1601,21 +1607,42 @@ tc_status tc_server_latencies_ex(tc_server *srv, double *out, uint32_t *block, f
 {
     if (!srv || !n_out || (cap && !out))
         return sfail(TC_EINVAL, "tc_server_latencies: bad arguments");
-    std::lock_guard<std::mutex> lq(srv->mu_queue);
-    const size_t n = std::min(cap, srv->lat.size());
-    std::copy(srv->lat.begin(), srv->lat.begin() + (long)n, out);
+    // Take the records out under the queue mutex in O(1) when they all fit
+    // (the usual case), then copy them without it: the worker needs that
+    // mutex for every step.
+    std::deque<double> lat;
+    std::deque<uint32_t> lat_block;
+    std::deque<std::array<float, 3>> lat_parts;
+    std::deque<uint8_t> lat_kind;
+    {
+        std::lock_guard<std::mutex> lq(srv->mu_queue);
+        if (srv->lat.size() <= cap) {
+            lat.swap(srv->lat);
+            lat_block.swap(srv->lat_block);
+            lat_parts.swap(srv->lat_parts);
+            lat_kind.swap(srv->lat_kind);
+        } else {
+            const long c = (long)cap;
+            lat.assign(srv->lat.begin(), srv->lat.begin() + c);
+            lat_block.assign(srv->lat_block.begin(), srv->lat_block.begin() + c);
+            lat_parts.assign(srv->lat_parts.begin(), srv->lat_parts.begin() + c);
+            lat_kind.assign(srv->lat_kind.begin(), srv->lat_kind.begin() + c);
+            srv->lat.erase(srv->lat.begin(), srv->lat.begin() + c);
+            srv->lat_block.erase(srv->lat_block.begin(), srv->lat_block.begin() + c);
+            srv->lat_parts.erase(srv->lat_parts.begin(), srv->lat_parts.begin() + c);
+            srv->lat_kind.erase(srv->lat_kind.begin(), srv->lat_kind.begin() + c);
+        }
+    }
+    const size_t n = lat.size();
+    std::copy(lat.begin(), lat.end(), out);
     if (block)
-        std::copy(srv->lat_block.begin(), srv->lat_block.begin() + (long)n, block);
+        std::copy(lat_block.begin(), lat_block.end(), block);
     if (parts)
         for (size_t i = 0; i < n; ++i)
             for (int k = 0; k < 3; ++k)
-                parts[3 * i + (size_t)k] = srv->lat_parts[i][(size_t)k];
+                parts[3 * i + (size_t)k] = lat_parts[i][(size_t)k];
     if (kind)
-        std::copy(srv->lat_kind.begin(), srv->lat_kind.begin() + (long)n, kind);
-    srv->lat.erase(srv->lat.begin(), srv->lat.begin() + (long)n);
-    srv->lat_block.erase(srv->lat_block.begin(), srv->lat_block.begin() + (long)n);
-    srv->lat_parts.erase(srv->lat_parts.begin(), srv->lat_parts.begin() + (long)n);
-    srv->lat_kind.erase(srv->lat_kind.begin(), srv->lat_kind.begin() + (long)n);
+        std::copy(lat_kind.begin(), lat_kind.end(), kind);
     *n_out = n;
     return TC_OK;
 }
@@ -1866,14 +1893,21 @@ tc_status tc_server_step_log(tc_server *srv, tc_server_step_rec *out, size_t cap
 {
     if (!srv || !n_out || (cap && !out))
         return sfail(TC_EINVAL, "tc_server_step_log: bad arguments");
-    std::lock_guard<std::mutex> lq(srv->mu_queue);
-    const size_t n = srv->steplog.size();
-    const size_t first = n < kLogSteps ? 0 : srv->steplog_next;
+    std::lock_guard<std::mutex> lr(srv->mu_log_reader);
+    size_t next = 0;
+    {
+        std::lock_guard<std::mutex> lq(srv->mu_queue);
+        srv->steplog.swap(srv->steplog_spare);  // O(1): the worker continues on the empty spare
+        next = srv->steplog_next;
+        srv->steplog_next = 0;
+    }
+    const std::vector<tc_server_step_rec> &log = srv->steplog_spare;
+    const size_t n = log.size();
+    const size_t first = n < kLogSteps ? 0 : next;
     const size_t k = std::min(cap, n);
     for (size_t i = 0; i < k; ++i)  // the newest k, oldest first
-        out[i] = srv->steplog[(first + (n - k) + i) % n];
-    srv->steplog.clear();
-    srv->steplog_next = 0;
+        out[i] = log[(first + (n - k) + i) % n];
+    srv->steplog_spare.clear();  // keeps its capacity
     *n_out = k;
     return TC_OK;
 }

@@ -1236,13 +1236,14 @@ def bench_trace(capi, pool: np.ndarray, seconds: float, budget_gb: float = 96.0)
     grp = trace_groups(seconds)
     srv = capi.tc_server_open(int(budget_gb * (1 << 30)), 1 << 22)
     waits, max_active, live = 0, 0, {}
-    gids, gouts = [], []
+    gids, gouts, gfill = [], [], []
     try:
         # Groups are admitted here, not at their start: opening a group allocates device memory, which stalls
         # running steps.
         for start, L, x, h in grp:
             gids.append(capi.tc_server_add_group(srv, TRACE_GROUP_C, L, TRACE_GROUP_BLOCK, h, capi.TC_BF16_SPLIT))
-            gouts.append([])
+            gouts.append(np.zeros((TRACE_GROUP_C, x.shape[1]), np.float32))  # written in place as blocks arrive
+            gfill.append(0)
         gbuf = np.empty(TRACE_GROUP_C * TRACE_GROUP_BLOCK, np.float32)
 
         def poll_groups():
@@ -1251,7 +1252,9 @@ def bench_trace(capi, pool: np.ndarray, seconds: float, budget_gb: float = 96.0)
                     n, _, _ = capi.tc_server_poll(srv, gid, gbuf)
                     if n == 0:
                         break
-                    gouts[gi].append(gbuf[:n].reshape(TRACE_GROUP_C, -1).copy())
+                    c = n // TRACE_GROUP_C
+                    gouts[gi][:, gfill[gi]:gfill[gi] + c] = gbuf[:n].reshape(TRACE_GROUP_C, c)
+                    gfill[gi] += c
 
         # The trace's streams hold about 6-8 GB at their peak: reserved before the replay, so that admissions
         # carve their state from it (growing the pool while steps run stalled them for 1-65 ms).
@@ -1266,7 +1269,11 @@ def bench_trace(capi, pool: np.ndarray, seconds: float, budget_gb: float = 96.0)
         logs = []
         t_drain = t_start + 0.5
 
+        lat_parts = []  # the latency log, read every 0.5 s (an O(1) swap in the server): the worker's log stays
+        # small and reuses the memory it freed instead of touching new pages for the whole trace
+
         def drain_log():
+            lat_parts.append(capi.tc_server_latencies_ex(srv))
             lg = capi.tc_server_step_log(srv, 1 << 15)
             logs.append(lg)
             if len(lg):
@@ -1313,8 +1320,8 @@ def bench_trace(capi, pool: np.ndarray, seconds: float, budget_gb: float = 96.0)
         poll_groups()
         st = capi.tc_server_get_stats(srv)
         k1 = _k1_roofline(capi.TcServerStats(), st)
-        lat, blk, parts, kind = capi.tc_server_latencies_ex(srv)
         drain_log()
+        lat, blk, parts, kind = (np.concatenate([lp[i] for lp in lat_parts]) for i in range(4))
         steplog = np.concatenate(logs)
     finally:
         capi.tc_server_close(srv)
@@ -1358,10 +1365,10 @@ def bench_trace(capi, pool: np.ndarray, seconds: float, budget_gb: float = 96.0)
               "latency": _lat_summary(lat[kind == 1 + capi.TC_BF16_SPLIT], blk[kind == 1 + capi.TC_BF16_SPLIT])}
     groups["latency"].pop("by_block", None)
     got, ref = [], []
-    for (start, L, x, h), outs in zip(grp, gouts):
-        if not outs:
+    for (start, L, x, h), outs, nf in zip(grp, gouts, gfill):
+        if nf == 0:
             continue
-        y = np.concatenate(outs, axis=1)
+        y = outs[:, :nf]
         m0 = max(0, y.shape[1] // 2 - 256)
         for c in (0, TRACE_GROUP_C - 1):
             for m in range(m0, min(m0 + 512, y.shape[1])):
@@ -1370,7 +1377,7 @@ def bench_trace(capi, pool: np.ndarray, seconds: float, budget_gb: float = 96.0)
     if got:
         groups["check"] = _err(np.array(got), np.array(ref))
         groups["check"]["contiguous"] = "512 outputs x channels 0 and 15 x each group"
-    groups["delivered_outputs"] = int(sum(sum(o.shape[1] for o in outs) for outs in gouts))
+    groups["delivered_outputs"] = int(sum(gfill))
     own = kind == 0
     return dict(_lat_summary(lat[own], blk[own]), seconds=seconds, streams_arrived=arrived, max_active=max_active,
                 groups_bf16split=groups,

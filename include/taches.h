@@ -581,11 +581,13 @@ uint64_t tc_kernel_launches(void);
  *                        tensor cores before the pairwise reduction of
  *                        ranges (default 16 for the BF16 split, 4096 for
  *                        BF16; 1..4096)
- *   TC_TUNE_K2_PAIR      plain BF16 only: 2 = a pair of CTAs on two SMs
+ *   TC_TUNE_K2_PAIR      plain BF16 only: 2 = pairs of CTAs on two SMs
  *                        (tcgen05 cta_group::2) per 256 channels x 256
- *                        outputs, each SM staging half the operands
- *                        (default); 1 = two 128-channel tiles per CTA sharing
- *                        each IR tile; 0 = one tile per CTA
+ *                        outputs, each SM staging half the operands,
+ *                        persistent (one pair per two SMs walks the units;
+ *                        default); 3 = the same pairs launched one per unit;
+ *                        1 = two 128-channel tiles per CTA sharing each IR
+ *                        tile; 0 = one tile per CTA
  *   TC_TUNE_ZERO_SKIP    1 = zero gating on the FP32 gather (the zero-skip of
  *                        Sec. 3.2 and 4.2 at block level, threshold 0): a
  *                        staged stretch of input that is all zero skips its

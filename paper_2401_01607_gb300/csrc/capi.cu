@@ -166,7 +166,8 @@ struct tc_stream {
     int *d_err = nullptr;
     int k1_variant_fixed = -1;  // -1: chosen per launch
     long long k2_range = -1;    // K blocks per tensor-core CTA range (-1: by precision)
-    int k2_mode = 2;  // plain BF16: 0 one channel tile per CTA, 1 two per CTA, 2 a CTA pair (tuning knob)
+    int k2_mode = 2;  // plain BF16: 0 one channel tile per CTA, 1 two per CTA, 2 persistent CTA pairs,
+                      // 3 CTA pairs launched per unit (tuning knob)
     bool zero_skip = false;      // K1 zero gating (tuning knob)
 
     // BF16 tensor-core path (shared-IR groups): bf16 hi/lo histories and, per
@@ -886,7 +887,7 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
     // long as a unit's K range fits one TMEM run.
     const long long ntile_c1 = ((long long)p.C + TM - 1) / TM;
     bool pair = s->prec == TC_BF16 && s->k2_mode != 0;
-    const bool cta_pair = pair && s->k2_mode == 2;
+    const bool cta_pair = pair && s->k2_mode >= 2;
     p.ntile_c = (int)(pair ? (ntile_c1 + 1) / 2 : ntile_c1);
     const long long tiles = (long long)p.ntile_c * p.ntile_o;
     // TMEM runs of `range` K blocks before each drain into FP32 registers.
@@ -929,7 +930,9 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
     TC_TRY(prof_begin(s));
     const CUtensorMap &mxh = rowview ? mxr_hi : s->mx_hi;
     const CUtensorMap &mxl = rowview ? mxr_lo : s->mx_lo;
-    if (pair && cta_pair)
+    if (pair && cta_pair && s->k2_mode == 2)
+        TC_CU(tc::k2_launch_c2p(mxh, t.mt2_hi, p, s->cs));
+    else if (pair && cta_pair)
         TC_CU(tc::k2_launch_c2(mxh, t.mt2_hi, p, s->cs));
     else if (pair)
         TC_CU(tc::k2_launch_pair(mxh, t.mt_hi, p, s->cs));
@@ -1562,8 +1565,8 @@ tc_status tc_set_tuning(tc_stream *s, int knob, long long value)
         s->k2_range = value;
         return TC_OK;
     case TC_TUNE_K2_PAIR:
-        if (value < -1 || value > 2)
-            return fail(TC_EINVAL, "TC_TUNE_K2_PAIR must be -1, 0, 1 or 2");
+        if (value < -1 || value > 3)
+            return fail(TC_EINVAL, "TC_TUNE_K2_PAIR must be -1, 0, 1, 2 or 3");
         s->k2_mode = value == -1 ? 2 : (int)value;
         return TC_OK;
     case TC_TUNE_ZERO_SKIP:
@@ -1714,7 +1717,7 @@ tc_status tc_stream_import(tc_stream *s, const void *buf, size_t size)
     s->state = hd.state;
     s->next_ramp = hd.next_ramp;
     s->k1_variant_fixed = hd.k1_variant_fixed;
-    s->k2_mode = (hd.k2_mode >= 0 && hd.k2_mode <= 2) ? hd.k2_mode : 2;
+    s->k2_mode = (hd.k2_mode >= 0 && hd.k2_mode <= 3) ? hd.k2_mode : 2;
     s->zero_skip = hd.zero_skip != 0;
     s->k2_range = hd.k2_range;
     if (hd.hist_len > 0)

@@ -604,6 +604,208 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2_THREADS, 1)
     }
 }
 
+// The CTA-pair kernel made persistent: one cluster per SM pair walks the
+// units u = cluster, cluster + clusters, ... The producers run ahead into the
+// next unit's K blocks (the stage ring never drains between units), and the
+// accumulators alternate between two TMEM buffers of 256 columns, so the
+// epilogue of one unit runs under the MMAs of the next. Each CTA's eight
+// epilogue warps release a buffer on the even CTA's `accfree` barrier (16
+// arrivals: eight local, eight from the odd CTA at cluster scope); the MMA
+// thread waits on it before it reuses the buffer.
+struct K2Unit {
+    int part, tile_o, tile_c, kb0, nk;
+};
+
+__device__ __forceinline__ K2Unit k2_unit(const K2Params &p, long long u)
+{
+    K2Unit w;
+    w.part = (int)(u % p.nsplit);
+    u /= p.nsplit;
+    w.tile_o = (int)(u % p.ntile_o);
+    w.tile_c = (int)(u / p.ntile_o);
+    w.kb0 = w.part * p.kb_per;
+    w.nk = max(min(w.kb0 + p.kb_per, p.nkb) - w.kb0, 0);
+    return w;
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2_THREADS, 1)
+    k2_toeplitz_c2p(const __grid_constant__ CUtensorMap mx_hi, const __grid_constant__ CUtensorMap mt2_hi,
+                    const K2Params p, long long units)
+{
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full[K2C_NS];
+    __shared__ __align__(8) uint64_t empty[K2C_NS];
+    __shared__ __align__(8) uint64_t accfull[2];
+    __shared__ __align__(8) uint64_t accfree[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int s_fail;
+
+    uint8_t *const smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int lane = tid & 31;
+    const uint32_t rank = cluster_ctarank();
+    const long long cid = blockIdx.x >> 1, ncl = gridDim.x >> 1;
+
+    if (tid == 0) {
+        for (int i = 0; i < K2C_NS; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&accfull[i], 1);
+            mbar_init(&accfree[i], 2 * K2_EPI_WARPS);
+        }
+        s_fail = 0;
+        fence_mbar_init();
+    }
+    if (warp == 2)
+        tmem_alloc_pair(&tmem_base, 2 * K2_N);
+    tc_fence_before_sync();
+    cluster_sync();
+    tc_fence_after_sync();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- producer (each CTA loads its own halves), across units ----
+            long long gi = 0;  // stage fills so far
+            for (long long u = cid; u < units && !s_fail; u += ncl) {
+                const K2Unit w = k2_unit(p, u);
+                const int c0 = w.tile_c * 2 * K2_M + (int)rank * K2_M;
+                const long long xcol0 = p.x_col0 + (long long)w.tile_o * K2_N;
+                for (int g = 0; g * K2C_GS < w.nk; ++g, ++gi) {
+                    const int st = (int)(gi % K2C_NS);
+                    const long long use = gi / K2C_NS;
+                    if (use > 0 &&
+                        !mbar_wait_bounded(&empty[st], (uint32_t)((use - 1) & 1), p.err, ERR_TIMEOUT_TMA)) {
+                        s_fail = 1;
+                        break;
+                    }
+                    const int nb = min(K2C_GS, w.nk - g * K2C_GS);
+                    if (rank == 0)
+                        mbar_arrive_expect_tx(&full[st], (uint32_t)(2 * nb * K2C_BLK));
+                    const uint32_t bar = mapa_shared(smem_u32(&full[st]), 0);
+                    for (int j = 0; j < nb; ++j) {
+                        uint8_t *sb = smem + st * K2C_STAGE + j * K2C_BLK;
+                        const int kb = w.kb0 + g * K2C_GS + j;
+                        tma_load_2d_pair(sb, &mx_hi, (int)(xcol0 + (long long)kb * K2_KB), c0, bar);
+                        tma_load_2d_pair(sb + K2_XBYTES, &mt2_hi, 0, kb * K2_N + (int)rank * (K2_N / 2), bar);
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && rank == 0) {
+            // ---- MMA issuer (even CTA), across units ----
+            const uint32_t idesc = umma_idesc_bf16(2 * K2_M, K2_N);
+            const uint64_t d0 = umma_desc_sw64(smem_u32(smem));
+            long long gi = 0;
+            long long k = 0;  // units done by this cluster
+            for (long long u = cid; u < units && !s_fail; u += ncl, ++k) {
+                const K2Unit w = k2_unit(p, u);
+                const int buf = (int)(k & 1);
+                const long long reuse = k >> 1;
+                if (reuse > 0 &&
+                    !mbar_wait_cluster_bounded(&accfree[buf], (uint32_t)((reuse - 1) & 1), p.err, ERR_TIMEOUT_MMA)) {
+                    s_fail = 1;
+                    break;
+                }
+                tc_fence_after_sync();
+                const uint32_t acc = tmem + (uint32_t)(buf * K2_N);
+                bool ok = true;
+                for (int g = 0; g * K2C_GS < w.nk; ++g, ++gi) {
+                    const int st = (int)(gi % K2C_NS);
+                    if (!mbar_wait_bounded(&full[st], (uint32_t)((gi / K2C_NS) & 1), p.err, ERR_TIMEOUT_MMA)) {
+                        s_fail = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after_sync();
+                    const int nb = min(K2C_GS, w.nk - g * K2C_GS);
+                    for (int j = 0; j < nb; ++j) {
+                        const uint64_t sd = d0 + (uint64_t)((st * K2C_STAGE + j * K2C_BLK) >> 4);
+#pragma unroll
+                        for (int kk = 0; kk < K2_KB / 16; ++kk) {
+                            const uint64_t xa = sd + (uint64_t)(kk * 2);
+                            const uint64_t tb = sd + (uint64_t)((K2_XBYTES + kk * 32) >> 4);
+                            umma_bf16_pair(acc, xa, tb, idesc, (g == 0 && j == 0 && kk == 0) ? 0u : 1u);
+                        }
+                    }
+                    umma_commit_pair(&empty[st], 0x3);
+                }
+                if (!ok)
+                    break;
+                umma_commit_pair(&accfull[buf], 0x3);
+            }
+        }
+    } else if (warp >= K2_ROLE_WARPS) {
+        // ---- epilogue (each CTA: its TMEM lanes = its 128 channels), across units ----
+        const int ew = warp - K2_ROLE_WARPS;
+        const int q = warp & 3;
+        const int half = ew >> 2;
+        const uint32_t free0 = mapa_shared(smem_u32(&accfree[0]), 0), free1 = mapa_shared(smem_u32(&accfree[1]), 0);
+        long long k = 0;
+        for (long long u = cid; u < units; u += ncl, ++k) {
+            const K2Unit w = k2_unit(p, u);
+            const int buf = (int)(k & 1);
+            const uint32_t par = (uint32_t)((k >> 1) & 1);
+            bool got = true;
+            if (lane == 0)
+                got = mbar_wait_limited(&accfull[buf], par, p.err, ERR_TIMEOUT_MMA, kWaitLimitNs, &s_fail);
+            got = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
+            if (!got)
+                break;
+            mbar_try_wait(&accfull[buf], par);
+            tc_fence_after_sync();
+            const int ch = q * 32 + lane;
+            const int c = w.tile_c * 2 * K2_M + (int)rank * K2_M + ch;
+            float *dst;
+            long long lim;
+            if (p.nsplit == 1) {
+                dst = p.y + (long long)c * p.y_pitch + (long long)w.tile_o * K2_N + half * 128;
+                lim = p.nout - (long long)w.tile_o * K2_N - half * 128;
+            } else {
+                const int tc1 = w.tile_c * 2 + (int)rank;
+                dst = p.partial +
+                      ((((long long)tc1 * p.ntile_o + w.tile_o) * p.nsplit + w.part) * K2_M + ch) * K2_N + half * 128;
+                lim = 128;
+            }
+            const uint32_t src = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * K2_N + half * 128);
+#pragma unroll
+            for (int cc = 0; cc < 8; ++cc) {
+                float v[16];
+                tmem_ld_32x16(src + cc * 16, v);
+                if (c >= p.C)
+                    continue;
+                const long long j0 = cc * 16;
+                if (lim >= j0 + 16 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+#pragma unroll
+                    for (int j = 0; j < 16; j += 4)
+                        *reinterpret_cast<float4 *>(dst + j0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (j0 + j < lim)
+                            dst[j0 + j] = v[j];
+                }
+            }
+            tc_fence_before_sync();
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive_cluster(buf ? free1 : free0);  // this buffer may take the next unit's MMAs
+        }
+    }
+    // Neither CTA leaves while the other may still signal its barriers or
+    // read its shared memory.
+    tc_fence_before_sync();
+    cluster_sync();
+    if (warp == 2) {
+        tc_fence_after_sync();
+        tmem_dealloc_pair(tmem, 2 * K2_N);
+    }
+}
+
 // Adds the nsplit K-range partials of each (channel, output) by a fixed
 // pairwise tree (adjacent pairs, zero-padded to 64 leaves) and writes y.
 __global__ void k2_reduce(const float *__restrict__ partial, int nsplit, int C, int ntile_o, int nout, float *y,
@@ -750,6 +952,43 @@ cudaError_t k2_launch_pair(const CUtensorMap &mx_hi, const CUtensorMap &mt_hi, c
     if (units <= 0)
         return cudaSuccess;
     k2_toeplitz_pair<<<(unsigned)units, K2_THREADS, K2P_SMEM, st>>>(mx_hi, mt_hi, p);
+    count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess || p.nsplit == 1)
+        return e;
+    const long long work = (long long)p.C * p.nout;
+    k2_reduce<<<grid_for(work), 256, 0, st>>>(p.partial, p.nsplit, p.C, (p.nout + K2_N - 1) / K2_N, p.nout, p.y,
+                                              p.y_pitch);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t k2_launch_c2p(const CUtensorMap &mx_hi, const CUtensorMap &mt2_hi, const K2Params &p, cudaStream_t st)
+{
+    static bool attr[64] = {};
+    static int clusters[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    if (dev < 0 || dev >= 64 || p.nsplit < 1 || p.nsplit > 64)
+        return cudaErrorInvalidValue;
+    if (!attr[dev]) {
+        e = cudaFuncSetAttribute(k2_toeplitz_c2p, cudaFuncAttributeMaxDynamicSharedMemorySize, K2C_SMEM);
+        if (e != cudaSuccess)
+            return e;
+        int sms = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess)
+            return e;
+        clusters[dev] = std::max(1, sms / 2);  // one CTA per SM, two per cluster
+        attr[dev] = true;
+    }
+    const long long units = (long long)p.ntile_c * p.ntile_o * p.nsplit;  // ntile_c counts tile pairs here
+    if (units <= 0)
+        return cudaSuccess;
+    const long long ncl = std::min<long long>(units, clusters[dev]);
+    k2_toeplitz_c2p<<<(unsigned)(2 * ncl), K2_THREADS, K2C_SMEM, st>>>(mx_hi, mt2_hi, p, units);
     count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess || p.nsplit == 1)

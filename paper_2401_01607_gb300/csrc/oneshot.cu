@@ -431,7 +431,7 @@ extern "C" tc_status tc_convolve_tc(const float *x, size_t N, const float *h, si
     if (e == cudaSuccess)
         e = tc::k2_tprep_launch(h, (int)Ll, 0, (int)nkb, thi, nprod == 1 ? nullptr : tlo, cs);
     if (e == cudaSuccess)
-        e = pair ? tc::k2_launch_c2(mx_hi, mt2_hi, p, cs) : tc::k2_launch(mx_hi, mx_lo, mt_hi, mt_lo, p, nprod, cs);
+        e = pair ? tc::k2_launch_c2p(mx_hi, mt2_hi, p, cs) : tc::k2_launch(mx_hi, mx_lo, mt_hi, mt_lo, p, nprod, cs);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(y, ytmp, (size_t)ny * 4, cudaMemcpyDeviceToDevice, cs);
     if (e == cudaSuccess)

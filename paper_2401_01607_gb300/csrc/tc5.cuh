@@ -193,6 +193,45 @@ __device__ __forceinline__ void umma_commit_pair(uint64_t *bar, uint16_t mask)
         : "memory");
 }
 
+// Arrives once on the mbarrier at shared::cluster address bar_cluster (this
+// CTA's or another CTA's of the cluster), releasing at cluster scope.
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster)
+{
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster) : "memory");
+}
+
+// One poll of this CTA's mbarrier for phase `parity`, acquiring at cluster
+// scope (for arrivals released by other CTAs of the cluster).
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// mbar_wait_limited with cluster-scope acquire; bounded the same way.
+__device__ __forceinline__ bool mbar_wait_cluster_bounded(uint64_t *bar, uint32_t parity, int *err, int errbit)
+{
+    if (mbar_try_wait_cluster(bar, parity))
+        return true;
+    const unsigned long long t0 = globaltimer_ns();
+    for (uint32_t it = 0; it < kWaitMaxPolls; ++it) {
+        if (mbar_try_wait_cluster(bar, parity))
+            return true;
+        if ((it & 255u) == 255u && globaltimer_ns() - t0 > kWaitLimitNs)
+            break;
+    }
+    if (err)
+        atomicOr(err, errbit);
+    return false;
+}
+
 // 2-D tiled load into this CTA's shared memory whose completion is counted on
 // the mbarrier at shared::cluster address bar_cluster (this CTA's or its pair
 // peer's).

@@ -180,6 +180,9 @@ cudaError_t k2_launch_pair(const CUtensorMap &mx_hi, const CUtensorMap &mt_hi, c
 // k2_launch_pair; one TMEM run per unit. mt2_hi: T over [nkb * 256][32] with
 // a box of 32 x 128 (each CTA loads its 128-output half).
 cudaError_t k2_launch_c2(const CUtensorMap &mx_hi, const CUtensorMap &mt2_hi, const K2Params &p, cudaStream_t st);
+// The same on persistent CTA pairs (one cluster per SM pair walks the units,
+// two TMEM accumulators: a unit's epilogue overlaps the next unit's MMAs).
+cudaError_t k2_launch_c2p(const CUtensorMap &mx_hi, const CUtensorMap &mt2_hi, const K2Params &p, cudaStream_t st);
 // Encodes a 2-D bf16 tensor map (inner dimension first), 64-byte swizzle.
 cudaError_t encode_bf16_2d(CUtensorMap *map, const void *base, unsigned long long dim0, unsigned long long dim1,
                            unsigned long long stride1_bytes, unsigned box0, unsigned box1);

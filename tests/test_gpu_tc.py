@@ -94,13 +94,13 @@ def test_shared_ir_switch_falls_back_exactly():
     check(y, X, H, vs, B, "bf16split", rows=[0, 64, 129])
 
 
-@pytest.mark.parametrize("pair", [2, 1, 0])
+@pytest.mark.parametrize("pair", [2, 3, 1, 0])
 @pytest.mark.parametrize("L", [3000, 20_000])
 def test_bf16_two_tiles_per_cta(pair, L):
-    """Plain BF16 on a CTA pair (tcgen05 cta_group::2, default), with two
-    channel tiles per CTA, and with one: 300 channels = three tiles, so the
-    second pair is half outside the group; the K range splits over CTAs at
-    L = 20000."""
+    """Plain BF16 on persistent CTA pairs (tcgen05 cta_group::2, default), on
+    CTA pairs launched per unit, with two channel tiles per CTA, and with one:
+    300 channels = three tiles, so the second pair is half outside the group;
+    the K range splits over CTAs at L = 20000."""
     C, N, B = 300, 2600, 256
     X = synth.audio_block(C, N, 6000 + L)
     H = synth.decayed_ir(L, 0.2 * L, 79)[None]

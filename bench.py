@@ -503,12 +503,15 @@ def bench_shared(torch, steps: int, warmup: int, P: int = 8192, C: int = 1024, N
             step()
         torch.cuda.synchronize()
         capi.tc_profile(s, True)
+        clk = ClockSampler(torch.cuda.current_device())
+        clk.start()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(ts)
         for _ in range(nst):
             step()
         e1.record(ts)
         e1.synchronize()
+        clk_r = clk.stop()
         k_ms, k_n, k_macs = capi.tc_profile_read(s)
         capi.tc_profile(s, False)
         info = capi.tc_get_info(s)
@@ -516,7 +519,7 @@ def bench_shared(torch, steps: int, warmup: int, P: int = 8192, C: int = 1024, N
         ms = e0.elapsed_time(e1) / nst
         r = {"ms_per_step": ms, "value": macs / (ms / 1e3), "unit": "tap-MAC/s",
              "kernel_ms_per_step": k_ms / nst, "launches_per_step": k_n / nst,
-             "check": _err(run.outputs(picks), refs),
+             "check": _err(run.outputs(picks), refs), "clocks": clk_r,
              "tensor_launches": int(info.tensor_launches), "fp32_fallbacks": int(info.fp32_fallbacks)}
         if name != "fp32":
             nprod = 3 if name == "bf16split" else 1
@@ -571,11 +574,14 @@ def bench_mimo(torch, P: int = 8192, precisions=("bf16split", "bf16", "fp32"), L
             run.run(capi, s, int(h_d.data_ptr()), 4 * P)  # warm-up: a short segment
             ts.synchronize()
             capi.tc_profile(s, True)
+            clk = ClockSampler(torch.cuda.current_device())
+            clk.start()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(ts)
             run.run(capi, s, int(h_d.data_ptr()))
             e1.record(ts)
             e1.synchronize()
+            clk_r = clk.stop()
             k_ms, k_n, k_macs = capi.tc_profile_read(s)
             capi.tc_profile(s, False)
             info = capi.tc_get_info(s)
@@ -584,7 +590,7 @@ def bench_mimo(torch, P: int = 8192, precisions=("bf16split", "bf16", "fp32"), L
         ms = e0.elapsed_time(e1)
         r = {"ms_per_step": ms, "value": macs / (ms / 1e3), "unit": "tap-MAC/s",
              "realtime_factor": (N / FS) / (ms / 1e3), "kernel_ms_per_step": k_ms, "launches": k_n,
-             "check": _err(run.outputs(picks), refs),
+             "check": _err(run.outputs(picks), refs), "clocks": clk_r,
              "tensor_launches": int(info.tensor_launches), "fp32_fallbacks": int(info.fp32_fallbacks)}
         if name == "fp32":
             tflops = 2.0 * k_macs / (k_ms / 1e3) / 1e12 if k_ms > 0 else 0.0

@@ -577,7 +577,8 @@ uint64_t tc_kernel_launches(void);
 /* Tuning knobs (autotuner and experiments); value -1 restores the default.
  *   TC_TUNE_K1_CHUNK     tap chunk of the FP32 gather: 0 = 640, 1 = 2560,
  *                        2 = 7040 taps per CTA (default: picked per launch)
- *   TC_TUNE_K2_RANGE     K blocks (of 32 samples) accumulated serially on the
+ *   TC_TUNE_K2_RANGE     K blocks (of 32 samples in the BF16 split, of 64 in
+ *                        plain BF16) accumulated serially on the
  *                        tensor cores before the pairwise reduction of
  *                        ranges (default 16 for the BF16 split, 4096 for
  *                        BF16; 1..4096)
@@ -588,6 +589,17 @@ uint64_t tc_kernel_launches(void);
  *                        default); 3 = the same pairs launched one per unit;
  *                        1 = two 128-channel tiles per CTA sharing each IR
  *                        tile; 0 = one tile per CTA
+ *   TC_TUNE_K2_SPLIT     K parts per tensor-core output tile, each a
+ *                        contiguous range of the IR's K blocks on its own CTA
+ *                        (or CTA pair), added by a fixed pairwise tree
+ *                        (1..64, capped at the tile's K blocks; default:
+ *                        the fewest parts that fill the GPU's waves to 90 %)
+ *   TC_TUNE_K2_FOLD      1 = the K parts of a tile are added inside the
+ *                        tensor-core kernel, by the warp that stores the last
+ *                        part of its slice (default; up to 16 parts, on the
+ *                        persistent CTA pairs and the one-tile kernel);
+ *                        0 = by a separate reduction launch. Both add the
+ *                        parts by the same tree: the results are identical
  *   TC_TUNE_ZERO_SKIP    1 = zero gating on the FP32 gather (the zero-skip of
  *                        Sec. 3.2 and 4.2 at block level, threshold 0): a
  *                        staged stretch of input that is all zero skips its
@@ -598,7 +610,9 @@ typedef enum tc_tune_knob {
     TC_TUNE_K1_CHUNK = 0,
     TC_TUNE_K2_RANGE = 1,
     TC_TUNE_K2_PAIR = 2,
-    TC_TUNE_ZERO_SKIP = 3
+    TC_TUNE_ZERO_SKIP = 3,
+    TC_TUNE_K2_SPLIT = 4,
+    TC_TUNE_K2_FOLD = 5
 } tc_tune_knob;
 tc_status tc_set_tuning(tc_stream *s, int knob, long long value);
 

@@ -166,6 +166,8 @@ struct tc_stream {
     int *d_err = nullptr;
     int k1_variant_fixed = -1;  // -1: chosen per launch
     long long k2_range = -1;    // K blocks per tensor-core CTA range (-1: by precision)
+    int k2_nsplit = -1;         // K parts per K2 tile (-1: planned from the waves)
+    bool k2_fold = true;        // K parts added inside K2 (false: a k2_reduce launch)
     int k2_mode = 2;  // plain BF16: 0 one channel tile per CTA, 1 two per CTA, 2 persistent CTA pairs,
                       // 3 CTA pairs launched per unit (tuning knob)
     bool zero_skip = false;      // K1 zero gating (tuning knob)
@@ -185,6 +187,8 @@ struct tc_stream {
     std::vector<std::array<TSet, 8>> tsets;  // [slot][delta]
     float *k2_partial = nullptr;
     size_t k2_partial_floats = 0;
+    unsigned *k2_ticket = nullptr;  // after the partials in the same allocation: K-part tickets
+    size_t k2_ticket_n = 0;
     float *k2_rows = nullptr;  // mono streams: row-major output of the 256-sample rows
     size_t k2_rows_floats = 0;
     long long k2_launches = 0, k1_fallbacks = 0;
@@ -351,6 +355,8 @@ tc_status clear_state(tc_stream *s)
     for (auto &k : s->k3sets)
         k.ready = false;
     TC_CU(cudaMemsetAsync(s->counter, 0, s->counter_n * sizeof(unsigned), s->cs));
+    if (s->k2_ticket)
+        TC_CU(cudaMemsetAsync(s->k2_ticket, 0, s->k2_ticket_n * sizeof(unsigned), s->cs));
     TC_CU(cudaMemsetAsync(s->d_err, 0, sizeof(int), s->cs));
     return TC_OK;
 }
@@ -405,10 +411,11 @@ tc_status open_common(tc_stream *s)
     } else if (s->prec != TC_FP32) {
         TC_CU(cudaMalloc(&s->hist_hi, (size_t)s->rows * s->cap * 2));
         TC_CU(cudaMalloc(&s->hist_lo, (size_t)s->rows * s->cap * 2));
+        const int kbs = tc::k2_kblock(s->prec == TC_BF16 ? 1 : 3);
         TC_CU(tc::encode_bf16_2d(&s->mx_hi, s->hist_hi, (unsigned long long)s->cap, s->rows,
-                                 (unsigned long long)s->cap * 2, tc::k2_kblock(), tc::k2_tile_m()));
+                                 (unsigned long long)s->cap * 2, kbs, tc::k2_tile_m()));
         TC_CU(tc::encode_bf16_2d(&s->mx_lo, s->hist_lo, (unsigned long long)s->cap, s->rows,
-                                 (unsigned long long)s->cap * 2, tc::k2_kblock(), tc::k2_tile_m()));
+                                 (unsigned long long)s->cap * 2, kbs, tc::k2_tile_m()));
     }
     TC_TRY(clear_state(s));
     TC_CU(cudaStreamSynchronize(s->cs));
@@ -786,6 +793,27 @@ long long k2_plan_nsplit(long long tiles, long long nkb, int sms)
     return (nkb + kb_per - 1) / kb_per;
 }
 
+// K-part partials of `floats` floats, followed by the tickets of the parts
+// folded inside the kernel (one per 128 x 256 tile and warp slice: at most
+// floats / 4096), zeroed in stream order.
+tc_status k2_partial_alloc(tc_stream *s, size_t floats)
+{
+    const size_t tickets = floats / 4096 + 8;
+    if (s->k2_partial)
+        cudaFreeAsync(s->k2_partial, s->cs);  // after the launches that used it
+    s->k2_partial = nullptr;
+    s->k2_ticket = nullptr;
+    s->k2_partial_floats = s->k2_ticket_n = 0;
+    TC_CU(tc::pool_alloc(reinterpret_cast<void **>(&s->k2_partial), floats * sizeof(float) + tickets * sizeof(unsigned),
+                         s->cs));
+    TC_ALIGNED(s->k2_partial);
+    s->k2_ticket = reinterpret_cast<unsigned *>(s->k2_partial + floats);
+    TC_CU(cudaMemsetAsync(s->k2_ticket, 0, tickets * sizeof(unsigned), s->cs));
+    s->k2_partial_floats = floats;
+    s->k2_ticket_n = tickets;
+    return TC_OK;
+}
+
 // K2 on the tensor cores when every input sample of the launch's window
 // spawned its tache with the same IR version; false in *used otherwise.
 // Buffers (and tensor maps) of the Toeplitz tiles of IR slot `slot` at shift
@@ -793,7 +821,7 @@ long long k2_plan_nsplit(long long tiles, long long nkb, int sms)
 // or device-wide synchronisation while pushes are in flight).
 tc_status ensure_tset_mem(tc_stream *s, int slot, int delta, long long nkb)
 {
-    const int TN = tc::k2_tile_n(), KB = tc::k2_kblock();
+    const int TN = tc::k2_tile_n(), KB = tc::k2_kblock(s->prec == TC_BF16 ? 1 : 3);
     tc_stream::TSet &ts = s->tsets[(size_t)slot][(size_t)delta];
     if (ts.thi && ts.nkb >= nkb)
         return TC_OK;
@@ -805,14 +833,16 @@ tc_status ensure_tset_mem(tc_stream *s, int slot, int delta, long long nkb)
     ts.ready = false;
     const size_t bytes = (size_t)nkb * TN * KB * 2;
     TC_CU(tc::pool_alloc(&ts.thi, bytes, s->cs));
-    TC_CU(tc::pool_alloc(&ts.tlo, bytes, s->cs));
     TC_ALIGNED(ts.thi);
-    TC_ALIGNED(ts.tlo);
     ts.nkb = nkb;
     TC_CU(tc::encode_bf16_2d(&ts.mt_hi, ts.thi, (unsigned long long)KB, (unsigned long long)nkb * TN,
                              (unsigned long long)KB * 2, KB, TN));
-    TC_CU(tc::encode_bf16_2d(&ts.mt_lo, ts.tlo, (unsigned long long)KB, (unsigned long long)nkb * TN,
-                             (unsigned long long)KB * 2, KB, TN));
+    if (s->prec != TC_BF16) {  // plain BF16 reads only the hi tiles
+        TC_CU(tc::pool_alloc(&ts.tlo, bytes, s->cs));
+        TC_ALIGNED(ts.tlo);
+        TC_CU(tc::encode_bf16_2d(&ts.mt_lo, ts.tlo, (unsigned long long)KB, (unsigned long long)nkb * TN,
+                                 (unsigned long long)KB * 2, KB, TN));
+    }
     TC_CU(tc::encode_bf16_2d(&ts.mt2_hi, ts.thi, (unsigned long long)KB, (unsigned long long)nkb * TN,
                              (unsigned long long)KB * 2, KB, TN / 2));
     return TC_OK;
@@ -824,8 +854,8 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
     const long long L = (long long)s->L;
     const int delta = (int)((((t0 - L + 1 - s->base) % 8) + 8) % 8);
     const long long w0 = t0 - L + 1 - delta;
-    const long long nkb = tc::k2_nkb(L, delta);
-    const int TN = tc::k2_tile_n(), TM = tc::k2_tile_m(), KB = tc::k2_kblock();
+    const int TN = tc::k2_tile_n(), TM = tc::k2_tile_m(), KB = tc::k2_kblock(s->prec == TC_BF16 ? 1 : 3);
+    const long long nkb = tc::k2_nkb(L, delta, KB);
     const long long ntile_o = (nout + TN - 1) / TN;
     const long long hi = w0 + (ntile_o - 1) * TN + nkb * KB;  // past the last sample read
     // Single version over [max(w0, first start), hi)?
@@ -845,7 +875,7 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
         TC_TRY(ensure_tset_mem(s, slot, delta, nkb));
         // The slot's unshifted fp32 copy (shift e = 0) holds h[k] at index k.
         const float *h = s->ir + (size_t)slot * s->nsets * 4 * (size_t)s->Lpad;
-        TC_CU(tc::k2_tprep_launch(h, (int)L, delta, (int)nkb, ts.thi, s->prec == TC_BF16 ? nullptr : ts.tlo,
+        TC_CU(tc::k2_tprep_launch(h, (int)L, delta, (int)nkb, KB, ts.thi, s->prec == TC_BF16 ? nullptr : ts.tlo,
                                   s->cs));
         ts.ready = true;
     }
@@ -901,6 +931,8 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
     long long nsplit = k2_plan_nsplit(tiles, nkb, cta_pair ? sms / 2 : sms);  // a CTA pair takes two SMs
+    if (s->k2_nsplit > 0)
+        nsplit = std::min<long long>(s->k2_nsplit, nkb);
     const long long kb_per = (nkb + nsplit - 1) / nsplit;
     nsplit = (nkb + kb_per - 1) / kb_per;
     p.nsplit = (int)nsplit;
@@ -916,15 +948,14 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
     if (nsplit > 1) {
         // Partials per 128-channel tile (the pair kernel writes that layout too).
         const size_t need = (size_t)(2 * ((ntile_c1 + 1) / 2) * p.ntile_o * nsplit) * TM * TN;
-        if (need > s->k2_partial_floats) {
-            if (s->k2_partial)
-                cudaFreeAsync(s->k2_partial, s->cs);  // after the launches that used it
-            s->k2_partial = nullptr;
-            TC_CU(tc::pool_alloc(reinterpret_cast<void **>(&s->k2_partial), need * sizeof(float), s->cs));
-            TC_ALIGNED(s->k2_partial);
-            s->k2_partial_floats = need;
-        }
+        if (need > s->k2_partial_floats)
+            TC_TRY(k2_partial_alloc(s, need));
         p.partial = s->k2_partial;
+        // The persistent CTA pairs and the one-tile kernel fold the parts
+        // themselves (tickets per warp slice).
+        if (s->k2_fold && (!pair || (cta_pair && s->k2_mode == 2)) && nsplit <= 16 &&
+            (size_t)(2 * ((ntile_c1 + 1) / 2) * p.ntile_o * 8) <= s->k2_ticket_n)
+            p.ticket = s->k2_ticket;
     }
     tc_stream::TSet &t = ts;
     TC_TRY(prof_begin(s));
@@ -1069,6 +1100,8 @@ tc_status check_err_word(tc_stream *s)
         *s->pin_err = 0;
         cudaMemsetAsync(s->d_err, 0, sizeof(int), s->cs);
         cudaMemsetAsync(s->counter, 0, s->counter_n * sizeof(unsigned), s->cs);
+        if (s->k2_ticket)
+            cudaMemsetAsync(s->k2_ticket, 0, s->k2_ticket_n * sizeof(unsigned), s->cs);
         return fail(TC_ETIMEOUT, "a kernel's bounded wait gave up (device error word 0x%x)", w);
     }
     return TC_OK;
@@ -1224,7 +1257,7 @@ tc_status group_open(size_t channels, size_t L, size_t max_push, int precision, 
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
         const long long TM = tc::k2_tile_m(), TN = tc::k2_tile_n();
         const long long ntile_c1 = ((long long)s->rows + TM - 1) / TM;
-        const long long nkb = tc::k2_nkb((long long)L, 7);
+        const long long nkb = tc::k2_nkb((long long)L, 7, tc::k2_kblock(s->prec == TC_BF16 ? 1 : 3));
         size_t need = 0;
         for (long long no = 1; no <= ((long long)max_push + TN - 1) / TN; ++no) {
             const long long tiles = (s->prec == TC_BF16 ? (ntile_c1 + 1) / 2 : ntile_c1) * no;
@@ -1236,12 +1269,7 @@ tc_status group_open(size_t channels, size_t L, size_t max_push, int precision, 
             }
         }
         if (need > 0) {
-            tc_status st = TC_OK;
-            if (tc::pool_alloc(reinterpret_cast<void **>(&s->k2_partial), need * sizeof(float), s->cs) !=
-                cudaSuccess)
-                st = fail(TC_ENOMEM, "group K-part partials");
-            else
-                s->k2_partial_floats = need;
+            tc_status st = k2_partial_alloc(s, need);
             if (st != TC_OK) {
                 tc_close(s);
                 *out = nullptr;
@@ -1256,7 +1284,8 @@ tc_status group_open(size_t channels, size_t L, size_t max_push, int precision, 
         // streams' steps run. Later versions' slots still allocate at their
         // first push.
         const int delta0 = (int)((((0 - (long long)L + 1 - s->base) % 8) + 8) % 8);
-        tc_status st = ensure_tset_mem(s, 0, delta0, tc::k2_nkb((long long)L, delta0));
+        tc_status st =
+            ensure_tset_mem(s, 0, delta0, tc::k2_nkb((long long)L, delta0, tc::k2_kblock(s->prec == TC_BF16 ? 1 : 3)));
         if (st != TC_OK) {
             tc_close(s);
             *out = nullptr;
@@ -1272,8 +1301,9 @@ tc_status group_open(size_t channels, size_t L, size_t max_push, int precision, 
                s->counter_n * sizeof(unsigned) + sizeof(DevTable) + sizeof(int);
     if (s->prec != TC_FP32) {
         b += s->rows * (size_t)s->cap * 4;  // bf16 hi and lo histories
-        const size_t nkb = (s->L + 256 + 8 + 31) / 32 + 1;
-        b += (size_t)2 * 2 * nkb * 256 * 32 * 2;
+        const size_t kbs = (size_t)tc::k2_kblock(s->prec == TC_BF16 ? 1 : 3);
+        const size_t nkb = (size_t)tc::k2_nkb((long long)s->L, 7, (int)kbs);
+        b += (size_t)2 * (s->prec == TC_BF16 ? 1 : 2) * nkb * 256 * kbs * 2;  // hi (and lo) tiles, two versions
         const size_t tiles = ((s->rows + 255) / 256 * 2) * ((s->max_push + 255) / 256);
         const size_t parts = std::max<size_t>(1, std::min<size_t>(64, 2 * 152 / std::max<size_t>(tiles, 1)));
         b += tiles * parts * 128 * 256 * sizeof(float);
@@ -1568,6 +1598,16 @@ tc_status tc_set_tuning(tc_stream *s, int knob, long long value)
         if (value < -1 || value > 3)
             return fail(TC_EINVAL, "TC_TUNE_K2_PAIR must be -1, 0, 1, 2 or 3");
         s->k2_mode = value == -1 ? 2 : (int)value;
+        return TC_OK;
+    case TC_TUNE_K2_SPLIT:
+        if (value != -1 && (value < 1 || value > 64))
+            return fail(TC_EINVAL, "TC_TUNE_K2_SPLIT must be -1 or in [1, 64]");
+        s->k2_nsplit = (int)value;
+        return TC_OK;
+    case TC_TUNE_K2_FOLD:
+        if (value != -1 && value != 0 && value != 1)
+            return fail(TC_EINVAL, "TC_TUNE_K2_FOLD must be -1, 0 or 1");
+        s->k2_fold = value != 0;
         return TC_OK;
     case TC_TUNE_ZERO_SKIP:
         if (value != -1 && value != 0 && value != 1)

@@ -26,7 +26,8 @@
 // into FP32 running sums in registers (round-to-nearest adds), which overlaps
 // the next run's MMAs; the tensor core never waits for the drain. A tile's K
 // range may also be split over `nsplit` CTAs (wave balance). Their sums are
-// added by k2_reduce in a fixed pairwise tree. Every wait is an mbarrier wait
+// added in a fixed pairwise tree: inside the kernel, by the warp that stores
+// the last part of its slice, or by k2_reduce. Every wait is an mbarrier wait
 // bounded by %globaltimer, and a failing role raises a shared flag so the
 // others stop early.
 #include <algorithm>
@@ -41,28 +42,102 @@ namespace {
 
 constexpr int K2_M = 128;
 constexpr int K2_N = 256;
-constexpr int K2_KB = 32;
+constexpr int K2_KB = 32;   // K block of the BF16 split: rows of 64 bytes (64-byte swizzle)
+constexpr int K2_KB1 = 64;  // K block of plain BF16: rows of 128 bytes (128-byte swizzle)
 constexpr int K2_ROLE_WARPS = 4;   // producer, MMA, TMEM owner, spare
 constexpr int K2_EPI_WARPS = 8;    // two per TMEM lane quarter (column halves)
 constexpr int K2_THREADS = 32 * (K2_ROLE_WARPS + K2_EPI_WARPS);
-constexpr int K2_XBYTES = K2_M * K2_KB * 2;  // 8 KB
-constexpr int K2_TBYTES = K2_N * K2_KB * 2;  // 16 KB
+constexpr int K2_XBYTES1 = K2_M * K2_KB1 * 2;  // 16 KB
+constexpr int K2_TBYTES1 = K2_N * K2_KB1 * 2;  // 32 KB
 
 template <int NPROD>
 struct K2Cfg {
-    static constexpr int XOFF_LO = K2_XBYTES;       // X_lo after X_hi (split only)
-    static constexpr int TOFF = NPROD == 1 ? K2_XBYTES : 2 * K2_XBYTES;
-    static constexpr int BLK = NPROD == 1 ? K2_XBYTES + K2_TBYTES : 2 * (K2_XBYTES + K2_TBYTES);  // one K block
+    static constexpr int KB = NPROD == 1 ? K2_KB1 : K2_KB;  // samples per K block
+    static constexpr int XB = K2_M * KB * 2, TB = K2_N * KB * 2;
+    static constexpr int XOFF_LO = XB;  // X_lo after X_hi (split only)
+    static constexpr int TOFF = NPROD == 1 ? XB : 2 * XB;
+    static constexpr int BLK = NPROD == 1 ? XB + TB : 2 * (XB + TB);  // one K block
     // A pipeline stage holds GS consecutive K blocks (one full and one empty
-    // barrier per stage). A K block of a 128 x 256 tile already carries 2 or
-    // 6 MMAs of 128 x 256 x 16, and a deeper ring of one-block stages
-    // measured faster here than fewer two-block stages (the split: 72 % vs
-    // 58 % of peak).
+    // barrier per stage). A K block of a 128 x 256 tile already carries 4
+    // (plain) or 6 (split) MMAs of 128 x 256 x 16, and a deeper ring of
+    // one-block stages measured faster here than fewer two-block stages (the
+    // split: 72 % vs 58 % of peak).
     static constexpr int GS = 1;
     static constexpr int STAGE = GS * BLK;
-    static constexpr int NS = NPROD == 1 ? 8 : 4;   // stages
+    static constexpr int NS = 4;                    // stages
     static constexpr int SMEM = NS * STAGE + 1024;  // + alignment slack
 };
+
+// K parts folded inside the kernel (no k2_reduce launch): every epilogue warp
+// owns a slice of its CTA's tile (32 channels x 128 outputs). After a warp has
+// stored its slice of one K part's sums, it takes a ticket for that slice; the
+// warp that takes the last ticket reads all the parts back from L2 and adds
+// them by the same fixed pairwise tree as k2_reduce (adjacent pairs, zero
+// padded), so the result does not depend on which part finished last, and
+// writes y. Nothing waits: a slice whose tickets are not all taken is simply
+// not folded. Up to K2_FOLD_MAX parts; the loads of NL parts x RG rows are in
+// flight together.
+constexpr int K2_FOLD_MAX = 16;
+
+template <int NL, int RG>
+__device__ __forceinline__ void k2_fold_rows(const K2Params &p, const float *src, float *dst, long long lim,
+                                             int c, int nrow)
+{
+    const long long part_stride = (long long)K2_M * K2_N;
+    for (int r0 = 0; r0 < nrow; r0 += RG) {
+        float4 v[RG][NL];
+#pragma unroll
+        for (int g = 0; g < RG; ++g)
+#pragma unroll
+            for (int s = 0; s < NL; ++s)
+                v[g][s] = (s < p.nsplit && r0 + g < nrow)
+                              ? __ldcg(reinterpret_cast<const float4 *>(src + s * part_stride + (r0 + g) * K2_N))
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int g = 0; g < RG; ++g) {
+#pragma unroll
+            for (int w = NL / 2; w >= 1; w >>= 1)
+#pragma unroll
+                for (int s = 0; s < w; ++s)
+                    v[g][s] = make_float4(v[g][2 * s].x + v[g][2 * s + 1].x, v[g][2 * s].y + v[g][2 * s + 1].y,
+                                          v[g][2 * s].z + v[g][2 * s + 1].z, v[g][2 * s].w + v[g][2 * s + 1].w);
+            if (r0 + g >= nrow || lim <= 0)
+                continue;
+            float *d = dst + (long long)(c + r0 + g) * p.y_pitch;
+            if (lim >= 4 && (reinterpret_cast<uintptr_t>(d) & 15) == 0) {
+                *reinterpret_cast<float4 *>(d) = v[g][0];
+            } else {
+                d[0] = v[g][0].x;
+                if (lim > 1)
+                    d[1] = v[g][0].y;
+                if (lim > 2)
+                    d[2] = v[g][0].z;
+                if (lim > 3)
+                    d[3] = v[g][0].w;
+            }
+        }
+    }
+}
+
+// Folds slice (q, half) of 128-channel tile tc1, output tile tile_o: rows
+// q*32 .. q*32+31, this lane's four outputs 128 half + 4 lane .. + 3.
+__device__ __forceinline__ void k2_fold_slice(const K2Params &p, int tc1, int tile_o, int q, int half, int lane)
+{
+    const int c = tc1 * K2_M + q * 32;  // first channel of the slice
+    const int nrow = min(32, p.C - c);
+    if (nrow <= 0)
+        return;
+    const float *src = p.partial + ((long long)tc1 * p.ntile_o + tile_o) * p.nsplit * K2_M * K2_N +
+                       (long long)(q * 32) * K2_N + half * 128 + lane * 4;
+    float *dst = p.y + (long long)tile_o * K2_N + half * 128 + lane * 4;
+    const long long lim = (long long)p.nout - (long long)tile_o * K2_N - half * 128 - lane * 4;
+    if (p.nsplit <= 4)
+        k2_fold_rows<4, 4>(p, src, dst, lim, c, nrow);
+    else if (p.nsplit <= 8)
+        k2_fold_rows<8, 2>(p, src, dst, lim, c, nrow);
+    else
+        k2_fold_rows<16, 1>(p, src, dst, lim, c, nrow);
+}
 
 template <int NPROD>
 __global__ void __launch_bounds__(K2_THREADS, 1)
@@ -132,13 +207,13 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
                 for (int j = 0; j < nb; ++j) {
                     uint8_t *sb = smem + st * C::STAGE + j * C::BLK;
                     const int kb = kb0 + gi * C::GS + j;
-                    const int xc = (int)(xcol0 + (long long)kb * K2_KB);
+                    const int xc = (int)(xcol0 + (long long)kb * C::KB);
                     tma_load_2d(sb, &mx_hi, xc, c0, &full[st]);
                     if (NPROD == 3)
                         tma_load_2d(sb + C::XOFF_LO, &mx_lo, xc, c0, &full[st]);
                     tma_load_2d(sb + C::TOFF, &mt_hi, 0, kb * K2_N, &full[st]);
                     if (NPROD == 3)
-                        tma_load_2d(sb + C::TOFF + K2_TBYTES, &mt_lo, 0, kb * K2_N, &full[st]);
+                        tma_load_2d(sb + C::TOFF + C::TB, &mt_lo, 0, kb * K2_N, &full[st]);
                 }
             }
         }
@@ -148,7 +223,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
             // Runs are whole stages (range is a multiple of GS).
             const uint32_t idesc = umma_idesc_bf16(K2_M, K2_N);
             // Descriptors advance by adding byte offsets >> 4 to the start field.
-            const uint64_t d0 = umma_desc_sw64(smem_u32(smem));
+            const uint64_t d0 = NPROD == 1 ? umma_desc_sw128(smem_u32(smem)) : umma_desc_sw64(smem_u32(smem));
             int gi = 0;
             for (int r = 0; r < nr && !s_fail; ++r) {
                 const int buf = r & 1;
@@ -172,14 +247,14 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
                     for (int j = 0; j < nb; ++j, first = false) {
                         const uint64_t sd = d0 + (uint64_t)((st * C::STAGE + j * C::BLK) >> 4);
 #pragma unroll
-                        for (int kk = 0; kk < K2_KB / 16; ++kk) {
+                        for (int kk = 0; kk < C::KB / 16; ++kk) {
                             // 16 bf16 = 32 bytes along the swizzled row.
                             const uint64_t xh = sd + (uint64_t)(kk * 2);
                             const uint64_t th = sd + (uint64_t)((C::TOFF + kk * 32) >> 4);
                             umma_bf16(acc, xh, th, idesc, (first && kk == 0) ? 0u : 1u);
                             if (NPROD == 3) {
                                 const uint64_t xl = sd + (uint64_t)((C::XOFF_LO + kk * 32) >> 4);
-                                const uint64_t tl = sd + (uint64_t)((C::TOFF + K2_TBYTES + kk * 32) >> 4);
+                                const uint64_t tl = sd + (uint64_t)((C::TOFF + C::TB + kk * 32) >> 4);
                                 umma_bf16(acc, xh, tl, idesc, 1u);
                                 umma_bf16(acc, xl, th, idesc, 1u);
                             }
@@ -255,6 +330,23 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
                         dst[j] = sum[j];
             }
         }
+        // K parts folded here: the warp that takes this slice's last ticket adds them.
+        const bool go = __shfl_sync(0xffffffffu, (ok && !s_fail) ? 1 : 0, 0) != 0;
+        if (go && p.nsplit > 1 && p.nsplit <= K2_FOLD_MAX && p.ticket != nullptr) {
+            unsigned *tk = p.ticket + ((long long)tile_c * p.ntile_o + tile_o) * K2_EPI_WARPS + ew;
+            __threadfence();  // this lane's part sums before the ticket
+            __syncwarp();
+            unsigned prev = 0;
+            if (lane == 0)
+                prev = atomicAdd(tk, 1u);
+            prev = __shfl_sync(0xffffffffu, prev, 0);
+            if (prev == (unsigned)(p.nsplit - 1)) {
+                __threadfence();  // the other parts' sums after their tickets
+                k2_fold_slice(p, tile_c, tile_o, q, half, lane);
+                if (lane == 0)
+                    *tk = 0u;  // zero again for the next launch
+            }
+        }
     }
     tc_fence_before_sync();
     __syncthreads();
@@ -270,10 +362,10 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
 // unit (the K range fits one FP32 accumulation, as plain BF16 is limited by
 // its operands, not by the run length); two accumulators of 256 columns. The
 // epilogue writes TMEM straight to y (or to the K-part partials).
-constexpr int K2P_BLK = 2 * K2_XBYTES + K2_TBYTES;  // one K block: X tile a, X tile b, T
+constexpr int K2P_BLK = 2 * K2_XBYTES1 + K2_TBYTES1;  // one K block: X tile a, X tile b, T
 constexpr int K2P_GS = 1;                             // K blocks per pipeline stage
 constexpr int K2P_STAGE = K2P_GS * K2P_BLK;
-constexpr int K2P_NS = 6;
+constexpr int K2P_NS = 3;
 constexpr int K2P_SMEM = K2P_NS * K2P_STAGE + 1024;
 
 __global__ void __launch_bounds__(K2_THREADS, 1)
@@ -335,10 +427,10 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
                 for (int j = 0; j < nb; ++j) {
                     uint8_t *sb = smem + st * K2P_STAGE + j * K2P_BLK;
                     const int kb = kb0 + gi * K2P_GS + j;
-                    const int xc = (int)(xcol0 + (long long)kb * K2_KB);
+                    const int xc = (int)(xcol0 + (long long)kb * K2_KB1);
                     tma_load_2d(sb, &mx_hi, xc, c0, &full[st]);
-                    tma_load_2d(sb + K2_XBYTES, &mx_hi, xc, c0 + K2_M, &full[st]);
-                    tma_load_2d(sb + 2 * K2_XBYTES, &mt_hi, 0, kb * K2_N, &full[st]);
+                    tma_load_2d(sb + K2_XBYTES1, &mx_hi, xc, c0 + K2_M, &full[st]);
+                    tma_load_2d(sb + 2 * K2_XBYTES1, &mt_hi, 0, kb * K2_N, &full[st]);
                 }
             }
         }
@@ -346,7 +438,7 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
         if (lane == 0) {
             // ---- MMA issuer ----
             const uint32_t idesc = umma_idesc_bf16(K2_M, K2_N);
-            const uint64_t d0 = umma_desc_sw64(smem_u32(smem));
+            const uint64_t d0 = umma_desc_sw128(smem_u32(smem));
             for (int gi = 0; gi * K2P_GS < nk; ++gi) {
                 const int st = gi % K2P_NS;
                 if (!mbar_wait_bounded(&full[st], (uint32_t)((gi / K2P_NS) & 1), p.err, ERR_TIMEOUT_MMA)) {
@@ -358,11 +450,11 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
                 for (int j = 0; j < nb; ++j) {
                     const uint64_t sd = d0 + (uint64_t)((st * K2P_STAGE + j * K2P_BLK) >> 4);
 #pragma unroll
-                    for (int kk = 0; kk < K2_KB / 16; ++kk) {
-                        const uint64_t th = sd + (uint64_t)((2 * K2_XBYTES + kk * 32) >> 4);
+                    for (int kk = 0; kk < K2_KB1 / 16; ++kk) {
+                        const uint64_t th = sd + (uint64_t)((2 * K2_XBYTES1 + kk * 32) >> 4);
                         const uint32_t accum = (gi == 0 && j == 0 && kk == 0) ? 0u : 1u;
                         umma_bf16(tmem, sd + (uint64_t)(kk * 2), th, idesc, accum);
-                        umma_bf16(tmem + K2_N, sd + (uint64_t)((K2_XBYTES + kk * 32) >> 4), th, idesc, accum);
+                        umma_bf16(tmem + K2_N, sd + (uint64_t)((K2_XBYTES1 + kk * 32) >> 4), th, idesc, accum);
                     }
                 }
                 umma_commit(&empty[st]);
@@ -445,10 +537,10 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
 // two 128-channel tiles on one CTA: the cost is per stage (the barrier round
 // trip and commit of each stage), not the shared-memory operand traffic that
 // the pair halves, so the pair only matches the one-CTA form.
-constexpr int K2C_BLK = K2_XBYTES + K2_XBYTES;  // one K block per CTA: X (128 x 32) and T half (128 x 32)
-constexpr int K2C_GS = 3;                        // K blocks per pipeline stage
+constexpr int K2C_BLK = 2 * K2_XBYTES1;  // one K block per CTA: X (128 x 64) and T half (128 x 64)
+constexpr int K2C_GS = 1;               // K blocks per pipeline stage
 constexpr int K2C_STAGE = K2C_GS * K2C_BLK;
-constexpr int K2C_NS = 4;
+constexpr int K2C_NS = 6;
 constexpr int K2C_SMEM = K2C_NS * K2C_STAGE + 1024;
 
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2_THREADS, 1)
@@ -513,8 +605,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2_THREADS, 1)
                 for (int j = 0; j < nb; ++j) {
                     uint8_t *sb = smem + st * K2C_STAGE + j * K2C_BLK;
                     const int kb = kb0 + gi * K2C_GS + j;
-                    tma_load_2d_pair(sb, &mx_hi, (int)(xcol0 + (long long)kb * K2_KB), c0, bar);
-                    tma_load_2d_pair(sb + K2_XBYTES, &mt2_hi, 0, kb * K2_N + (int)rank * (K2_N / 2), bar);
+                    tma_load_2d_pair(sb, &mx_hi, (int)(xcol0 + (long long)kb * K2_KB1), c0, bar);
+                    tma_load_2d_pair(sb + K2_XBYTES1, &mt2_hi, 0, kb * K2_N + (int)rank * (K2_N / 2), bar);
                 }
             }
         }
@@ -522,7 +614,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2_THREADS, 1)
         if (lane == 0 && rank == 0) {
             // ---- MMA issuer (even CTA) ----
             const uint32_t idesc = umma_idesc_bf16(2 * K2_M, K2_N);
-            const uint64_t d0 = umma_desc_sw64(smem_u32(smem));
+            const uint64_t d0 = umma_desc_sw128(smem_u32(smem));
             bool ok = true;
             for (int gi = 0; gi * K2C_GS < nk; ++gi) {
                 const int st = gi % K2C_NS;
@@ -536,9 +628,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2_THREADS, 1)
                 for (int j = 0; j < nb; ++j) {
                     const uint64_t sd = d0 + (uint64_t)((st * K2C_STAGE + j * K2C_BLK) >> 4);
 #pragma unroll
-                    for (int kk = 0; kk < K2_KB / 16; ++kk) {
+                    for (int kk = 0; kk < K2_KB1 / 16; ++kk) {
                         const uint64_t xa = sd + (uint64_t)(kk * 2);
-                        const uint64_t tb = sd + (uint64_t)((K2_XBYTES + kk * 32) >> 4);
+                        const uint64_t tb = sd + (uint64_t)((K2_XBYTES1 + kk * 32) >> 4);
                         umma_bf16_pair(tmem, xa, tb, idesc, (gi == 0 && j == 0 && kk == 0) ? 0u : 1u);
                     }
                 }
@@ -689,8 +781,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2_THREADS, 1)
                     for (int j = 0; j < nb; ++j) {
                         uint8_t *sb = smem + st * K2C_STAGE + j * K2C_BLK;
                         const int kb = w.kb0 + g * K2C_GS + j;
-                        tma_load_2d_pair(sb, &mx_hi, (int)(xcol0 + (long long)kb * K2_KB), c0, bar);
-                        tma_load_2d_pair(sb + K2_XBYTES, &mt2_hi, 0, kb * K2_N + (int)rank * (K2_N / 2), bar);
+                        tma_load_2d_pair(sb, &mx_hi, (int)(xcol0 + (long long)kb * K2_KB1), c0, bar);
+                        tma_load_2d_pair(sb + K2_XBYTES1, &mt2_hi, 0, kb * K2_N + (int)rank * (K2_N / 2), bar);
                     }
                 }
             }
@@ -699,7 +791,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2_THREADS, 1)
         if (lane == 0 && rank == 0) {
             // ---- MMA issuer (even CTA), across units ----
             const uint32_t idesc = umma_idesc_bf16(2 * K2_M, K2_N);
-            const uint64_t d0 = umma_desc_sw64(smem_u32(smem));
+            const uint64_t d0 = umma_desc_sw128(smem_u32(smem));
             long long gi = 0;
             long long k = 0;  // units done by this cluster
             for (long long u = cid; u < units && !s_fail; u += ncl, ++k) {
@@ -726,9 +818,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2_THREADS, 1)
                     for (int j = 0; j < nb; ++j) {
                         const uint64_t sd = d0 + (uint64_t)((st * K2C_STAGE + j * K2C_BLK) >> 4);
 #pragma unroll
-                        for (int kk = 0; kk < K2_KB / 16; ++kk) {
+                        for (int kk = 0; kk < K2_KB1 / 16; ++kk) {
                             const uint64_t xa = sd + (uint64_t)(kk * 2);
-                            const uint64_t tb = sd + (uint64_t)((K2_XBYTES + kk * 32) >> 4);
+                            const uint64_t tb = sd + (uint64_t)((K2_XBYTES1 + kk * 32) >> 4);
                             umma_bf16_pair(acc, xa, tb, idesc, (g == 0 && j == 0 && kk == 0) ? 0u : 1u);
                         }
                     }
@@ -745,6 +837,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2_THREADS, 1)
         const int q = warp & 3;
         const int half = ew >> 2;
         const uint32_t free0 = mapa_shared(smem_u32(&accfree[0]), 0), free1 = mapa_shared(smem_u32(&accfree[1]), 0);
+        const bool fold = p.nsplit > 1 && p.nsplit <= K2_FOLD_MAX && p.ticket != nullptr;
         long long k = 0;
         for (long long u = cid; u < units; u += ncl, ++k) {
             const K2Unit w = k2_unit(p, u);
@@ -794,6 +887,22 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2_THREADS, 1)
             __syncwarp();
             if (lane == 0)
                 mbar_arrive_cluster(buf ? free1 : free0);  // this buffer may take the next unit's MMAs
+            if (fold) {
+                const int tc1 = w.tile_c * 2 + (int)rank;
+                unsigned *tk = p.ticket + ((long long)tc1 * p.ntile_o + w.tile_o) * K2_EPI_WARPS + ew;
+                __threadfence();  // this lane's part sums before the ticket
+                __syncwarp();
+                unsigned prev = 0;
+                if (lane == 0)
+                    prev = atomicAdd(tk, 1u);
+                prev = __shfl_sync(0xffffffffu, prev, 0);
+                if (prev == (unsigned)(p.nsplit - 1)) {
+                    __threadfence();  // the other parts' sums after their tickets
+                    k2_fold_slice(p, tc1, w.tile_o, q, half, lane);
+                    if (lane == 0)
+                        *tk = 0u;  // every part has its ticket: zero again for the next launch
+                }
+            }
         }
     }
     // Neither CTA leaves while the other may still signal its barriers or
@@ -832,21 +941,22 @@ __global__ void k2_reduce(const float *__restrict__ partial, int nsplit, int C, 
     }
 }
 
-// Materialises the Toeplitz tiles of one IR for alignment shift delta:
-//   T[kb][i][j] = h[L - 1 + delta + i - 32 kb - j]  (0 outside [0, L)),
-// as bf16 hi = bf16(h) and lo = bf16(h - hi), row-major [kb][256][32]
+// Materialises the Toeplitz tiles of one IR for alignment shift delta, in
+// K blocks of kbs samples (32 or 64):
+//   T[kb][i][j] = h[L - 1 + delta + i - kbs kb - j]  (0 outside [0, L)),
+// as bf16 hi = bf16(h) and lo = bf16(h - hi), row-major [kb][256][kbs]
 // (tlo may be null: plain BF16).
-__global__ void k2_tprep(const float *__restrict__ h, int L, int delta, int nkb, __nv_bfloat16 *thi,
+__global__ void k2_tprep(const float *__restrict__ h, int L, int delta, int nkb, int kbs, __nv_bfloat16 *thi,
                          __nv_bfloat16 *tlo)
 {
-    const long long total = (long long)nkb * K2_N * K2_KB;
+    const long long total = (long long)nkb * K2_N * kbs;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
          q += (long long)gridDim.x * blockDim.x) {
-        const int j = (int)(q % K2_KB);
-        const long long r = q / K2_KB;
+        const int j = (int)(q % kbs);
+        const long long r = q / kbs;
         const int i = (int)(r % K2_N);
         const long long kb = r / K2_N;
-        const long long k = (long long)L - 1 + delta + i - K2_KB * kb - j;
+        const long long k = (long long)L - 1 + delta + i - (long long)kbs * kb - j;
         const float v = (k >= 0 && k < L) ? h[k] : 0.f;
         const __nv_bfloat16 hi = __float2bfloat16_rn(v);
         thi[q] = hi;
@@ -898,14 +1008,17 @@ unsigned grid_for(long long work)
 
 int k2_tile_m() { return K2_M; }
 int k2_tile_n() { return K2_N; }
-int k2_kblock() { return K2_KB; }
+int k2_kblock(int nprod) { return nprod == 1 ? K2_KB1 : K2_KB; }
 
-long long k2_nkb(long long L, int delta) { return (L - 1 + delta + K2_N + K2_KB - 1) / K2_KB; }
+long long k2_nkb(long long L, int delta, int kbs) { return (L - 1 + delta + K2_N + kbs - 1) / kbs; }
 
-cudaError_t k2_tprep_launch(const float *h, int L, int delta, int nkb, void *thi, void *tlo, cudaStream_t st)
+cudaError_t k2_tprep_launch(const float *h, int L, int delta, int nkb, int kbs, void *thi, void *tlo,
+                            cudaStream_t st)
 {
-    const long long work = (long long)nkb * K2_N * K2_KB;
-    k2_tprep<<<grid_for(work), 256, 0, st>>>(h, L, delta, nkb, (__nv_bfloat16 *)thi, (__nv_bfloat16 *)tlo);
+    if (kbs != K2_KB && kbs != K2_KB1)
+        return cudaErrorInvalidValue;
+    const long long work = (long long)nkb * K2_N * kbs;
+    k2_tprep<<<grid_for(work), 256, 0, st>>>(h, L, delta, nkb, kbs, (__nv_bfloat16 *)thi, (__nv_bfloat16 *)tlo);
     count_launch();
     return cudaGetLastError();
 }
@@ -991,8 +1104,8 @@ cudaError_t k2_launch_c2p(const CUtensorMap &mx_hi, const CUtensorMap &mt2_hi, c
     k2_toeplitz_c2p<<<(unsigned)(2 * ncl), K2_THREADS, K2C_SMEM, st>>>(mx_hi, mt2_hi, p, units);
     count_launch();
     e = cudaGetLastError();
-    if (e != cudaSuccess || p.nsplit == 1)
-        return e;
+    if (e != cudaSuccess || p.nsplit == 1 || (p.ticket != nullptr && p.nsplit <= K2_FOLD_MAX))
+        return e;  // no parts, or folded in the kernel
     const long long work = (long long)p.C * p.nout;
     k2_reduce<<<grid_for(work), 256, 0, st>>>(p.partial, p.nsplit, p.C, (p.nout + K2_N - 1) / K2_N, p.nout, p.y,
                                               p.y_pitch);
@@ -1061,8 +1174,8 @@ cudaError_t k2_launch(const CUtensorMap &mx_hi, const CUtensorMap &mx_lo, const 
         k2_toeplitz<3><<<(unsigned)units, K2_THREADS, smem, st>>>(mx_hi, mx_lo, mt_hi, mt_lo, p);
     count_launch();
     e = cudaGetLastError();
-    if (e != cudaSuccess || p.nsplit == 1)
-        return e;
+    if (e != cudaSuccess || p.nsplit == 1 || (p.ticket != nullptr && p.nsplit <= K2_FOLD_MAX))
+        return e;  // no parts, or folded in the kernel
     const long long work = (long long)p.C * p.nout;
     k2_reduce<<<grid_for(work), 256, 0, st>>>(p.partial, p.nsplit, p.C, p.ntile_o, p.nout, p.y, p.y_pitch);
     count_launch();

@@ -329,11 +329,11 @@ extern "C" tc_status tc_convolve_tc(const float *x, size_t N, const float *h, si
     }
     if (L > ((size_t)1 << 26) || N > ((size_t)1 << 34))
         return na_fail(TC_EINVAL, "tc_convolve_tc: L must be <= 2^26 and N <= 2^34");
-    const int TM = tc::k2_tile_m(), TN = tc::k2_tile_n(), KB = tc::k2_kblock();
+    const int TM = tc::k2_tile_m(), TN = tc::k2_tile_n(), KB = tc::k2_kblock(precision == TC_BF16 ? 1 : 3);
     const long long Ll = (long long)L, Nl = (long long)N;
     const long long ny = Nl + Ll - 1;
     const long long R = (ny + TN - 1) / TN;              // output rows of 256 samples
-    const long long nkb = tc::k2_nkb(Ll, 0);             // K blocks per row window
+    const long long nkb = tc::k2_nkb(Ll, 0, KB);         // K blocks per row window
     const long long off = Ll - 1;                        // xs[m] = x[m - off]
     const long long npad = ru((R - 1) * TN + nkb * KB + 64, 64);
     if (R > (1LL << 24))
@@ -381,9 +381,12 @@ extern "C" tc_status tc_convolve_tc(const float *x, size_t N, const float *h, si
     const size_t b_xs = 0, b_xb = (size_t)npad * 2, b_t = (size_t)nkb * TN * KB * 2;
     const size_t b_y = (size_t)R * TN * 4;
     const size_t b_part = nsplit > 1 ? (size_t)2 * ((ntile_c1 + 1) / 2) * nsplit * TM * TN * 4 : 0;
+    // K-part tickets of the in-kernel fold (one per 128-row tile and warp slice).
+    const bool fold = nsplit > 1 && nsplit <= 16;
+    const size_t b_tk = fold ? (size_t)2 * ((ntile_c1 + 1) / 2) * 8 * 4 : 0;
     const size_t o_xs = 0, o_hi = o_xs + ru(b_xs, 256), o_lo = o_hi + ru(b_xb, 256), o_th = o_lo + ru(b_xb, 256);
     const size_t o_tl = o_th + ru(b_t, 256), o_y = o_tl + ru(b_t, 256), o_part = o_y + ru(b_y, 256);
-    const size_t o_err = o_part + ru(b_part, 256), total = o_err + 256;
+    const size_t o_tk = o_part + ru(b_part, 256), o_err = o_tk + ru(b_tk, 256), total = o_err + 256;
     char *mem = nullptr;
     cudaError_t e = tc::pool_alloc(reinterpret_cast<void **>(&mem), total, cs);
     if (e != cudaSuccess)
@@ -399,6 +402,7 @@ extern "C" tc_status tc_convolve_tc(const float *x, size_t N, const float *h, si
     p.y = ytmp;
     p.y_pitch = TN;
     p.partial = nsplit > 1 ? reinterpret_cast<float *>(mem + o_part) : nullptr;
+    p.ticket = fold ? reinterpret_cast<unsigned *>(mem + o_tk) : nullptr;
     p.err = err;
     CUtensorMap mx_hi{}, mx_lo{}, mt_hi{}, mt_lo{}, mt2_hi{};
     int herr = 0;
@@ -416,6 +420,8 @@ extern "C" tc_status tc_convolve_tc(const float *x, size_t N, const float *h, si
         e = tc::encode_bf16_2d(&mt2_hi, thi, KB, (unsigned long long)nkb * TN, KB * 2, KB, TN / 2);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(err, 0, sizeof(int), cs);
+    if (e == cudaSuccess && fold)
+        e = cudaMemsetAsync(p.ticket, 0, b_tk, cs);
     // xs[m] = x[m - off] with zeros around it, as bf16 hi (and lo for the split; plain BF16 reads hi only).
     for (void *xb : {xhi, xlo}) {
         if (xb == xlo && nprod == 1)
@@ -429,7 +435,7 @@ extern "C" tc_status tc_convolve_tc(const float *x, size_t N, const float *h, si
     if (e == cudaSuccess)
         e = tc::k2_split_shift_launch(x, Nl, off, xhi, nprod == 1 ? nullptr : xlo, cs);
     if (e == cudaSuccess)
-        e = tc::k2_tprep_launch(h, (int)Ll, 0, (int)nkb, thi, nprod == 1 ? nullptr : tlo, cs);
+        e = tc::k2_tprep_launch(h, (int)Ll, 0, (int)nkb, KB, thi, nprod == 1 ? nullptr : tlo, cs);
     if (e == cudaSuccess)
         e = pair ? tc::k2_launch_c2p(mx_hi, mt2_hi, p, cs) : tc::k2_launch(mx_hi, mx_lo, mt_hi, mt_lo, p, nprod, cs);
     if (e == cudaSuccess)

@@ -50,6 +50,20 @@ __device__ __forceinline__ uint64_t umma_desc_sw64(uint32_t smem_addr)
     return d;
 }
 
+// The same for rows of 128 bytes in the 128-byte swizzle (atoms of 8 rows =
+// 1024 B, 1024-byte aligned): SBO 1024 B, layout type 2. Moving along K
+// inside the row adds the byte offset >> 4 to the start field, as above.
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t smem_addr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((smem_addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1u << 16;                       // LBO (ignored)
+    d |= (uint64_t)((1024u >> 4) & 0x3FFFu) << 32; // SBO: 8 rows x 128 B
+    d |= (uint64_t)1u << 46;                       // descriptor version
+    d |= (uint64_t)2u << 61;                       // 128-byte swizzle
+    return d;
+}
+
 // Shared-memory matrix descriptor for a K-major operand without swizzling:
 // core matrices of 8 rows x 16 bytes (each row 16 bytes after the previous),
 // `lbo` bytes apart along K and `sbo` bytes apart along M/N (8-row groups).

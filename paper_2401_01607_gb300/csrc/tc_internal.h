@@ -153,23 +153,27 @@ struct K2Params {
     float *y;                // y[c * y_pitch + j], j < nout
     long long y_pitch;
     float *partial;          // [ntile_c][ntile_o][nsplit][128][256] (nsplit > 1)
+    unsigned *ticket;        // persistent CTA pairs: [2 ntile_c][ntile_o][8] K-part tickets per warp slice,
+                             // zero between launches; null = parts added by k2_reduce
     int *err;
 };
 int k2_tile_m();
 int k2_tile_n();
-int k2_kblock();
-long long k2_nkb(long long L, int delta);
+int k2_kblock(int nprod);  // samples per K block: 64 for plain BF16 (nprod 1), 32 for the split (3)
+long long k2_nkb(long long L, int delta, int kbs);
 size_t k2_smem_bytes(int nprod);
-// Toeplitz tiles of IR h (fp32, L taps) for shift delta: hi/lo bf16 [nkb][256][32].
-cudaError_t k2_tprep_launch(const float *h, int L, int delta, int nkb, void *thi, void *tlo, cudaStream_t st);
+// Toeplitz tiles of IR h (fp32, L taps) for shift delta: hi/lo bf16 [nkb][256][kbs].
+cudaError_t k2_tprep_launch(const float *h, int L, int delta, int nkb, int kbs, void *thi, void *tlo,
+                            cudaStream_t st);
 // bf16 hi/lo split of src[0, n) into hhi/hlo[dst_off, dst_off + n) (hlo may be null).
 cudaError_t k2_split_shift_launch(const float *src, long long n, long long dst_off, void *hhi, void *hlo,
                                   cudaStream_t st);
 // bf16 hi/lo split of history columns [col0, col0 + n) of `rows` rows.
 cudaError_t k2_split_launch(const float *hist, long long pitch, int rows, long long col0, long long n, void *hhi,
                             void *hlo, cudaStream_t st);
-// nprod = 1 (BF16) or 3 (BF16 hi/lo split). Maps: X over the bf16 history
-// [rows][pitch], box 32 x 128; T over [nkb * 256][32], box 32 x 256; 64-byte swizzle.
+// nprod = 1 (BF16) or 3 (BF16 hi/lo split), K blocks of kbs = k2_kblock(nprod)
+// samples. Maps: X over the bf16 history [rows][pitch], box kbs x 128; T over
+// [nkb * 256][kbs], box kbs x 256 (encode_bf16_2d picks the swizzle).
 cudaError_t k2_launch(const CUtensorMap &mx_hi, const CUtensorMap &mx_lo, const CUtensorMap &mt_hi,
                       const CUtensorMap &mt_lo, const K2Params &p, int nprod, cudaStream_t st);
 // Plain BF16 with two 128-channel tiles per CTA sharing each T stage. p.ntile_c
@@ -177,13 +181,15 @@ cudaError_t k2_launch(const CUtensorMap &mx_hi, const CUtensorMap &mx_lo, const 
 cudaError_t k2_launch_pair(const CUtensorMap &mx_hi, const CUtensorMap &mt_hi, const K2Params &p, cudaStream_t st);
 // Plain BF16 on CTA pairs (clusters of two, tcgen05 cta_group::2): a unit of
 // 256 channels x 256 outputs per pair, p.ntile_c counting tile pairs as for
-// k2_launch_pair; one TMEM run per unit. mt2_hi: T over [nkb * 256][32] with
-// a box of 32 x 128 (each CTA loads its 128-output half).
+// k2_launch_pair; one TMEM run per unit. mt2_hi: T over [nkb * 256][64] with
+// a box of 64 x 128 (each CTA loads its 128-output half).
 cudaError_t k2_launch_c2(const CUtensorMap &mx_hi, const CUtensorMap &mt2_hi, const K2Params &p, cudaStream_t st);
 // The same on persistent CTA pairs (one cluster per SM pair walks the units,
 // two TMEM accumulators: a unit's epilogue overlaps the next unit's MMAs).
 cudaError_t k2_launch_c2p(const CUtensorMap &mx_hi, const CUtensorMap &mt2_hi, const K2Params &p, cudaStream_t st);
-// Encodes a 2-D bf16 tensor map (inner dimension first), 64-byte swizzle.
+// Encodes a 2-D bf16 tensor map (inner dimension first). Rows of the box of
+// 64 bytes (box0 = 32) take the 64-byte swizzle, rows of 128 bytes (box0 = 64)
+// the 128-byte swizzle.
 cudaError_t encode_bf16_2d(CUtensorMap *map, const void *base, unsigned long long dim0, unsigned long long dim1,
                            unsigned long long stride1_bytes, unsigned box0, unsigned box1);
 

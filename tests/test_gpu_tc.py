@@ -109,6 +109,30 @@ def test_bf16_two_tiles_per_cta(pair, L):
     check(y, X, H, [0], B, "bf16", rows=[0, 127, 128, 255, 256, 299])
 
 
+@pytest.mark.parametrize("nsplit", [2, 3, 5, 8, 13, 16, 17])
+@pytest.mark.parametrize("prec,pair", [("bf16", 2), ("bf16", 0), ("bf16split", 2)])
+def test_k_parts_folded_in_kernel_equal_k2_reduce(prec, pair, nsplit):
+    """The tensor-core kernels add a tile's K parts themselves (the warp that
+    takes a slice's last ticket folds it, by the same pairwise tree as
+    k2_reduce): on the persistent CTA pairs (plain BF16) and on the one-tile
+    kernel (plain BF16 with TC_TUNE_K2_PAIR 0; the BF16 split). With the fold
+    switched off, k2_reduce adds the same parts. Both give the same bits, in
+    pushes (aligned rows) and in the flush (rows of odd pitch L - 1), and match
+    the oracle. 17 parts are beyond the in-kernel fold and go to k2_reduce
+    either way."""
+    C, N, L, B = 300, 2600, 20_000, 256
+    X = synth.audio_block(C, N, 8000 + nsplit)
+    H = synth.decayed_ir(L, 0.2 * L, 81)[None]
+    ys = {}
+    for fold in (1, 0):
+        ys[fold], info = run_group(X, H, [0], L, B, prec, 1280,
+                                   tuning=[(capi.TC_TUNE_K2_PAIR, pair), (capi.TC_TUNE_K2_SPLIT, nsplit),
+                                           (capi.TC_TUNE_K2_FOLD, fold)])
+        assert info.tensor_launches > 0 and info.fp32_fallbacks == 0
+    assert np.array_equal(ys[1], ys[0]), np.argwhere(ys[1] != ys[0])[:5]
+    check(ys[1], X, H, [0], B, prec, rows=[0, 31, 32, 127, 128, 255, 256, 299])
+
+
 @pytest.mark.parametrize("prec", ["bf16split", "bf16"])
 def test_short_ir_one_k_part_odd_pitch(prec):
     """A short IR (L = 700: fewer than 32 K blocks, so one K part and the epilogue writes y itself) with

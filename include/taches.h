@@ -582,13 +582,15 @@ uint64_t tc_kernel_launches(void);
  *                        tensor cores before the pairwise reduction of
  *                        ranges (default 16 for the BF16 split, 4096 for
  *                        BF16; 1..4096)
- *   TC_TUNE_K2_PAIR      plain BF16 only: 2 = pairs of CTAs on two SMs
- *                        (tcgen05 cta_group::2) per 256 channels x 256
- *                        outputs, each SM staging half the operands,
- *                        persistent (one pair per two SMs walks the units;
- *                        default); 3 = the same pairs launched one per unit;
- *                        1 = two 128-channel tiles per CTA sharing each IR
- *                        tile; 0 = one tile per CTA
+ *   TC_TUNE_K2_PAIR      2 = pairs of CTAs on two SMs (tcgen05
+ *                        cta_group::2) per 256 channels x 256 outputs, each
+ *                        SM staging half the operands, persistent (one pair
+ *                        per two SMs walks the units; default; the BF16
+ *                        split takes it when it has two 128-channel tiles,
+ *                        else one tile per CTA); plain BF16 only: 3 = the
+ *                        same pairs launched one per unit; 1 = two
+ *                        128-channel tiles per CTA sharing each IR tile;
+ *                        0 = one tile per CTA (the split: any value but 2)
  *   TC_TUNE_K2_SPLIT     K parts per tensor-core output tile, each a
  *                        contiguous range of the IR's K blocks on its own CTA
  *                        (or CTA pair), added by a fixed pairwise tree

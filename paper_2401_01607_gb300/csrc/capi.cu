@@ -182,7 +182,7 @@ struct tc_stream {
         long long nkb = 0;
         void *thi = nullptr, *tlo = nullptr;
         CUtensorMap mt_hi{}, mt_lo{};
-        CUtensorMap mt2_hi{};  // the same hi tiles in boxes of 128 rows (half a tile: CTA pairs)
+        CUtensorMap mt2_hi{}, mt2_lo{};  // the same tiles in boxes of 128 rows (half a tile: CTA pairs)
     };
     std::vector<std::array<TSet, 8>> tsets;  // [slot][delta]
     float *k2_partial = nullptr;
@@ -842,6 +842,8 @@ tc_status ensure_tset_mem(tc_stream *s, int slot, int delta, long long nkb)
         TC_ALIGNED(ts.tlo);
         TC_CU(tc::encode_bf16_2d(&ts.mt_lo, ts.tlo, (unsigned long long)KB, (unsigned long long)nkb * TN,
                                  (unsigned long long)KB * 2, KB, TN));
+        TC_CU(tc::encode_bf16_2d(&ts.mt2_lo, ts.tlo, (unsigned long long)KB, (unsigned long long)nkb * TN,
+                                 (unsigned long long)KB * 2, KB, TN / 2));
     }
     TC_CU(tc::encode_bf16_2d(&ts.mt2_hi, ts.thi, (unsigned long long)KB, (unsigned long long)nkb * TN,
                              (unsigned long long)KB * 2, KB, TN / 2));
@@ -916,7 +918,10 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
     // Plain BF16 runs two channel tiles per CTA (one T stage feeds both), as
     // long as a unit's K range fits one TMEM run.
     const long long ntile_c1 = ((long long)p.C + TM - 1) / TM;
-    bool pair = s->prec == TC_BF16 && s->k2_mode != 0;
+    // The BF16 split runs on persistent CTA pairs when there are two channel
+    // tiles to pair (one tile alone would leave half of each pair idle).
+    const bool spair = s->prec == TC_BF16_SPLIT && s->k2_mode == 2 && ntile_c1 >= 2;
+    bool pair = (s->prec == TC_BF16 && s->k2_mode != 0) || spair;
     const bool cta_pair = pair && s->k2_mode >= 2;
     p.ntile_c = (int)(pair ? (ntile_c1 + 1) / 2 : ntile_c1);
     const long long tiles = (long long)p.ntile_c * p.ntile_o;
@@ -927,7 +932,6 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
     // Plain BF16 is limited by its operands, not by the run. K parts per
     // tile: the fewest that fill the GPU's waves to >= 90 %.
     p.range = (int)(s->k2_range > 0 ? s->k2_range : (s->prec == TC_BF16_SPLIT ? 16 : 4096));
-    p.range += p.range & 1;  // runs are whole pipeline stages of 2 K blocks
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
     long long nsplit = k2_plan_nsplit(tiles, nkb, cta_pair ? sms / 2 : sms);  // a CTA pair takes two SMs
@@ -937,7 +941,7 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
     nsplit = (nkb + kb_per - 1) / kb_per;
     p.nsplit = (int)nsplit;
     p.kb_per = (int)kb_per;
-    if (pair && p.range < p.kb_per) {
+    if (pair && !spair && p.range < p.kb_per) {
         // One TMEM run cannot hold this unit's K range: single tiles, same K split.
         pair = false;
         p.ntile_c = (int)ntile_c1;
@@ -961,7 +965,9 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
     TC_TRY(prof_begin(s));
     const CUtensorMap &mxh = rowview ? mxr_hi : s->mx_hi;
     const CUtensorMap &mxl = rowview ? mxr_lo : s->mx_lo;
-    if (pair && cta_pair && s->k2_mode == 2)
+    if (spair)
+        TC_CU(tc::k2_launch_c2s(mxh, mxl, t.mt2_hi, t.mt2_lo, p, s->cs));
+    else if (pair && cta_pair && s->k2_mode == 2)
         TC_CU(tc::k2_launch_c2p(mxh, t.mt2_hi, p, s->cs));
     else if (pair && cta_pair)
         TC_CU(tc::k2_launch_c2(mxh, t.mt2_hi, p, s->cs));
@@ -1260,13 +1266,14 @@ tc_status group_open(size_t channels, size_t L, size_t max_push, int precision, 
         const long long nkb = tc::k2_nkb((long long)L, 7, tc::k2_kblock(s->prec == TC_BF16 ? 1 : 3));
         size_t need = 0;
         for (long long no = 1; no <= ((long long)max_push + TN - 1) / TN; ++no) {
-            const long long tiles = (s->prec == TC_BF16 ? (ntile_c1 + 1) / 2 : ntile_c1) * no;
-            // Plain BF16 on CTA pairs plans its K parts over half the SMs.
-            for (int slots : {sms, sms / 2}) {
-                const long long ns = k2_plan_nsplit(tiles, nkb, slots);
-                if (ns > 1)
-                    need = std::max(need, (size_t)(2 * ((ntile_c1 + 1) / 2) * no * ns * TM * TN));
-            }
+            // Single tiles over all SMs; tile pairs (plain BF16, and the split on
+            // CTA pairs) over all SMs or over half of them.
+            for (const long long tc : {ntile_c1, (ntile_c1 + 1) / 2})
+                for (int slots : {sms, sms / 2}) {
+                    const long long ns = k2_plan_nsplit(tc * no, nkb, slots);
+                    if (ns > 1)
+                        need = std::max(need, (size_t)(2 * ((ntile_c1 + 1) / 2) * no * ns * TM * TN));
+                }
         }
         if (need > 0) {
             tc_status st = k2_partial_alloc(s, need);

@@ -915,6 +915,242 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2_THREADS, 1)
     }
 }
 
+// The BF16 hi/lo split on persistent CTA pairs. As k2_toeplitz_c2p, each
+// CTA of a pair stages its 128 channels of X (hi and lo) and its 128-output
+// half of T (hi and lo), so a K block costs each SM 32 KB instead of the
+// single-tile kernel's 48 KB; the three products of a K block go into one
+// M = 256 accumulator. As k2_toeplitz<3>, a unit's K blocks are accumulated
+// in TMEM runs of `range` blocks, alternating between two accumulators, and
+// the eight epilogue warps of each CTA drain every finished run into FP32
+// register sums (round-to-nearest adds) under the next run's MMAs. Runs are
+// counted across units, so the MMAs of a unit's first run never wait for the
+// previous unit's last drain.
+constexpr int K2S_BLK = 4 * K2_M * K2_KB * 2;  // one K block per CTA: X hi, X lo, T hi half, T lo half (8 KB each)
+constexpr int K2S_GS = 1;                        // K blocks per pipeline stage
+constexpr int K2S_STAGE = K2S_GS * K2S_BLK;
+constexpr int K2S_NS = 6;
+constexpr int K2S_SMEM = K2S_NS * K2S_STAGE + 1024;
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2_THREADS, 1)
+    k2_toeplitz_c2s(const __grid_constant__ CUtensorMap mx_hi, const __grid_constant__ CUtensorMap mx_lo,
+                    const __grid_constant__ CUtensorMap mt2_hi, const __grid_constant__ CUtensorMap mt2_lo,
+                    const K2Params p, long long units)
+{
+    constexpr int XB = K2_M * K2_KB * 2;  // 8 KB
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full[K2S_NS];
+    __shared__ __align__(8) uint64_t empty[K2S_NS];
+    __shared__ __align__(8) uint64_t accfull[2];
+    __shared__ __align__(8) uint64_t accfree[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int s_fail;
+
+    uint8_t *const smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int lane = tid & 31;
+    const uint32_t rank = cluster_ctarank();
+    const long long cid = blockIdx.x >> 1, ncl = gridDim.x >> 1;
+    const int range = p.range;
+
+    if (tid == 0) {
+        for (int i = 0; i < K2S_NS; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&accfull[i], 1);
+            mbar_init(&accfree[i], 2 * K2_EPI_WARPS);
+        }
+        s_fail = 0;
+        fence_mbar_init();
+    }
+    if (warp == 2)
+        tmem_alloc_pair(&tmem_base, 2 * K2_N);
+    tc_fence_before_sync();
+    cluster_sync();
+    tc_fence_after_sync();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- producer (each CTA loads its own halves), across units ----
+            long long gi = 0;
+            for (long long u = cid; u < units && !s_fail; u += ncl) {
+                const K2Unit w = k2_unit(p, u);
+                const int c0 = w.tile_c * 2 * K2_M + (int)rank * K2_M;
+                const long long xcol0 = p.x_col0 + (long long)w.tile_o * K2_N;
+                for (int g = 0; g * K2S_GS < w.nk; ++g, ++gi) {
+                    const int st = (int)(gi % K2S_NS);
+                    const long long use = gi / K2S_NS;
+                    if (use > 0 &&
+                        !mbar_wait_bounded(&empty[st], (uint32_t)((use - 1) & 1), p.err, ERR_TIMEOUT_TMA)) {
+                        s_fail = 1;
+                        break;
+                    }
+                    const int nb = min(K2S_GS, w.nk - g * K2S_GS);
+                    if (rank == 0)
+                        mbar_arrive_expect_tx(&full[st], (uint32_t)(2 * nb * K2S_BLK));
+                    const uint32_t bar = mapa_shared(smem_u32(&full[st]), 0);
+                    for (int j = 0; j < nb; ++j) {
+                        uint8_t *sb = smem + st * K2S_STAGE + j * K2S_BLK;
+                        const int kb = w.kb0 + g * K2S_GS + j;
+                        const int xc = (int)(xcol0 + (long long)kb * K2_KB);
+                        const int tr = kb * K2_N + (int)rank * (K2_N / 2);
+                        tma_load_2d_pair(sb, &mx_hi, xc, c0, bar);
+                        tma_load_2d_pair(sb + XB, &mx_lo, xc, c0, bar);
+                        tma_load_2d_pair(sb + 2 * XB, &mt2_hi, 0, tr, bar);
+                        tma_load_2d_pair(sb + 3 * XB, &mt2_lo, 0, tr, bar);
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && rank == 0) {
+            // ---- MMA issuer (even CTA): runs of `range` K blocks, across units ----
+            const uint32_t idesc = umma_idesc_bf16(2 * K2_M, K2_N);
+            const uint64_t d0 = umma_desc_sw64(smem_u32(smem));
+            long long gi = 0, run = 0;
+            for (long long u = cid; u < units && !s_fail; u += ncl) {
+                const K2Unit w = k2_unit(p, u);
+                for (int k0 = 0; k0 < w.nk && !s_fail; k0 += range, ++run) {
+                    const int buf = (int)(run & 1);
+                    const long long reuse = run >> 1;
+                    if (reuse > 0 && !mbar_wait_cluster_bounded(&accfree[buf], (uint32_t)((reuse - 1) & 1), p.err,
+                                                                ERR_TIMEOUT_MMA)) {
+                        s_fail = 1;
+                        break;
+                    }
+                    tc_fence_after_sync();
+                    const uint32_t acc = tmem + (uint32_t)(buf * K2_N);
+                    const int k1 = min(w.nk, k0 + range);
+                    // range is a multiple of K2S_GS: the run's stages are the producer's stages.
+                    for (int g = k0 / K2S_GS; g * K2S_GS < k1; ++g, ++gi) {
+                        const int st = (int)(gi % K2S_NS);
+                        if (!mbar_wait_bounded(&full[st], (uint32_t)((gi / K2S_NS) & 1), p.err, ERR_TIMEOUT_MMA)) {
+                            s_fail = 1;
+                            break;
+                        }
+                        tc_fence_after_sync();
+                        const int nb = min(K2S_GS, k1 - g * K2S_GS);
+                        for (int j = 0; j < nb; ++j) {
+                            const uint64_t sd = d0 + (uint64_t)((st * K2S_STAGE + j * K2S_BLK) >> 4);
+#pragma unroll
+                            for (int kk = 0; kk < K2_KB / 16; ++kk) {
+                                const uint64_t xh = sd + (uint64_t)(kk * 2);
+                                const uint64_t xl = sd + (uint64_t)((XB + kk * 32) >> 4);
+                                const uint64_t th = sd + (uint64_t)((2 * XB + kk * 32) >> 4);
+                                const uint64_t tl = sd + (uint64_t)((3 * XB + kk * 32) >> 4);
+                                const bool first = g * K2S_GS + j == k0 && kk == 0;
+                                umma_bf16_pair(acc, xh, th, idesc, first ? 0u : 1u);
+                                umma_bf16_pair(acc, xh, tl, idesc, 1u);
+                                umma_bf16_pair(acc, xl, th, idesc, 1u);
+                            }
+                        }
+                        umma_commit_pair(&empty[st], 0x3);
+                    }
+                    if (s_fail)
+                        break;
+                    umma_commit_pair(&accfull[buf], 0x3);  // the run is complete in both CTAs' TMEM
+                }
+            }
+        }
+    } else if (warp >= K2_ROLE_WARPS) {
+        // ---- epilogue: drain each run into FP32 register sums, across units ----
+        const int ew = warp - K2_ROLE_WARPS;
+        const int q = warp & 3;
+        const int half = ew >> 2;
+        const uint32_t free0 = mapa_shared(smem_u32(&accfree[0]), 0), free1 = mapa_shared(smem_u32(&accfree[1]), 0);
+        const bool fold = p.nsplit > 1 && p.nsplit <= K2_FOLD_MAX && p.ticket != nullptr;
+        long long run = 0;
+        bool ok = true;
+        for (long long u = cid; u < units && ok; u += ncl) {
+            const K2Unit w = k2_unit(p, u);
+            float sum[128];
+#pragma unroll
+            for (int j = 0; j < 128; ++j)
+                sum[j] = 0.f;
+            for (int k0 = 0; k0 < w.nk; k0 += range, ++run) {
+                const int buf = (int)(run & 1);
+                const uint32_t par = (uint32_t)((run >> 1) & 1);
+                bool got = true;
+                if (lane == 0)
+                    got = mbar_wait_limited(&accfull[buf], par, p.err, ERR_TIMEOUT_MMA, kWaitLimitNs, &s_fail);
+                got = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
+                if (!got) {
+                    ok = false;
+                    break;
+                }
+                mbar_try_wait(&accfull[buf], par);
+                tc_fence_after_sync();
+                const uint32_t src = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * K2_N + half * 128);
+#pragma unroll
+                for (int cc = 0; cc < 8; ++cc) {
+                    float v[16];
+                    tmem_ld_32x16(src + cc * 16, v);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        sum[cc * 16 + j] += v[j];
+                }
+                tc_fence_before_sync();
+                __syncwarp();
+                if (lane == 0)
+                    mbar_arrive_cluster(buf ? free1 : free0);  // this accumulator may take the next run
+            }
+            if (!ok)
+                break;
+            const int ch = q * 32 + lane;
+            const int tc1 = w.tile_c * 2 + (int)rank;
+            const int c = tc1 * K2_M + ch;
+            if (c < p.C) {
+                float *dst;
+                long long lim;
+                if (p.nsplit == 1) {
+                    dst = p.y + (long long)c * p.y_pitch + (long long)w.tile_o * K2_N + half * 128;
+                    lim = p.nout - (long long)w.tile_o * K2_N - half * 128;
+                } else {
+                    dst = p.partial +
+                          ((((long long)tc1 * p.ntile_o + w.tile_o) * p.nsplit + w.part) * K2_M + ch) * K2_N +
+                          half * 128;
+                    lim = 128;
+                }
+                if (lim >= 128 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+#pragma unroll
+                    for (int j = 0; j < 128; j += 4)
+                        *reinterpret_cast<float4 *>(dst + j) =
+                            make_float4(sum[j], sum[j + 1], sum[j + 2], sum[j + 3]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 128; ++j)
+                        if (j < lim)
+                            dst[j] = sum[j];
+                }
+            }
+            if (fold) {
+                unsigned *tk = p.ticket + ((long long)tc1 * p.ntile_o + w.tile_o) * K2_EPI_WARPS + ew;
+                __threadfence();  // this lane's part sums before the ticket
+                __syncwarp();
+                unsigned prev = 0;
+                if (lane == 0)
+                    prev = atomicAdd(tk, 1u);
+                prev = __shfl_sync(0xffffffffu, prev, 0);
+                if (prev == (unsigned)(p.nsplit - 1)) {
+                    __threadfence();  // the other parts' sums after their tickets
+                    k2_fold_slice(p, tc1, w.tile_o, q, half, lane);
+                    if (lane == 0)
+                        *tk = 0u;  // zero again for the next launch
+                }
+            }
+        }
+    }
+    tc_fence_before_sync();
+    cluster_sync();
+    if (warp == 2) {
+        tc_fence_after_sync();
+        tmem_dealloc_pair(tmem, 2 * K2_N);
+    }
+}
+
 // Adds the nsplit K-range partials of each (channel, output) by a fixed
 // pairwise tree (adjacent pairs, zero-padded to 64 leaves) and writes y.
 __global__ void k2_reduce(const float *__restrict__ partial, int nsplit, int C, int ntile_o, int nout, float *y,
@@ -1102,6 +1338,44 @@ cudaError_t k2_launch_c2p(const CUtensorMap &mx_hi, const CUtensorMap &mt2_hi, c
         return cudaSuccess;
     const long long ncl = std::min<long long>(units, clusters[dev]);
     k2_toeplitz_c2p<<<(unsigned)(2 * ncl), K2_THREADS, K2C_SMEM, st>>>(mx_hi, mt2_hi, p, units);
+    count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess || p.nsplit == 1 || (p.ticket != nullptr && p.nsplit <= K2_FOLD_MAX))
+        return e;  // no parts, or folded in the kernel
+    const long long work = (long long)p.C * p.nout;
+    k2_reduce<<<grid_for(work), 256, 0, st>>>(p.partial, p.nsplit, p.C, (p.nout + K2_N - 1) / K2_N, p.nout, p.y,
+                                              p.y_pitch);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t k2_launch_c2s(const CUtensorMap &mx_hi, const CUtensorMap &mx_lo, const CUtensorMap &mt2_hi,
+                          const CUtensorMap &mt2_lo, const K2Params &p, cudaStream_t st)
+{
+    static bool attr[64] = {};
+    static int clusters[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    if (dev < 0 || dev >= 64 || p.nsplit < 1 || p.nsplit > 64 || p.range < 1 || p.range % K2S_GS != 0)
+        return cudaErrorInvalidValue;
+    if (!attr[dev]) {
+        e = cudaFuncSetAttribute(k2_toeplitz_c2s, cudaFuncAttributeMaxDynamicSharedMemorySize, K2S_SMEM);
+        if (e != cudaSuccess)
+            return e;
+        int sms = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess)
+            return e;
+        clusters[dev] = std::max(1, sms / 2);
+        attr[dev] = true;
+    }
+    const long long units = (long long)p.ntile_c * p.ntile_o * p.nsplit;  // ntile_c counts tile pairs here
+    if (units <= 0)
+        return cudaSuccess;
+    const long long ncl = std::min<long long>(units, clusters[dev]);
+    k2_toeplitz_c2s<<<(unsigned)(2 * ncl), K2_THREADS, K2S_SMEM, st>>>(mx_hi, mx_lo, mt2_hi, mt2_lo, p, units);
     count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess || p.nsplit == 1 || (p.ticket != nullptr && p.nsplit <= K2_FOLD_MAX))

@@ -344,7 +344,9 @@ extern "C" tc_status tc_convolve_tc(const float *x, size_t N, const float *h, si
     // Scratch: padded fp32 input, its bf16 hi/lo, Toeplitz tiles hi/lo, the
     // row-major output and the K-part partials.
     const long long ntile_c1 = (R + TM - 1) / TM;
-    bool pair = precision == TC_BF16;
+    // Plain BF16 on persistent CTA pairs; the split too when there are two row tiles to pair.
+    const bool spair = precision == TC_BF16_SPLIT && ntile_c1 >= 2;
+    bool pair = precision == TC_BF16 || spair;
     tc::K2Params p{};
     p.C = (int)R;
     p.nout = TN;
@@ -373,7 +375,7 @@ extern "C" tc_status tc_convolve_tc(const float *x, size_t N, const float *h, si
     nsplit = (nkb + kb_per - 1) / kb_per;
     p.nsplit = (int)nsplit;
     p.kb_per = (int)kb_per;
-    if (pair && p.range < p.kb_per) {
+    if (pair && !spair && p.range < p.kb_per) {
         pair = false;
         p.ntile_c = (int)ntile_c1;
     }
@@ -404,7 +406,7 @@ extern "C" tc_status tc_convolve_tc(const float *x, size_t N, const float *h, si
     p.partial = nsplit > 1 ? reinterpret_cast<float *>(mem + o_part) : nullptr;
     p.ticket = fold ? reinterpret_cast<unsigned *>(mem + o_tk) : nullptr;
     p.err = err;
-    CUtensorMap mx_hi{}, mx_lo{}, mt_hi{}, mt_lo{}, mt2_hi{};
+    CUtensorMap mx_hi{}, mx_lo{}, mt_hi{}, mt_lo{}, mt2_hi{}, mt2_lo{};
     int herr = 0;
     // Rows of the X view overlap: row r starts 256 samples after row r - 1.
     e = tc::encode_bf16_2d(&mx_hi, xhi, (unsigned long long)nkb * KB, (unsigned long long)R, (unsigned long long)TN * 2,
@@ -418,6 +420,8 @@ extern "C" tc_status tc_convolve_tc(const float *x, size_t N, const float *h, si
         e = tc::encode_bf16_2d(&mt_lo, tlo, KB, (unsigned long long)nkb * TN, KB * 2, KB, TN);
     if (e == cudaSuccess)
         e = tc::encode_bf16_2d(&mt2_hi, thi, KB, (unsigned long long)nkb * TN, KB * 2, KB, TN / 2);
+    if (e == cudaSuccess)
+        e = tc::encode_bf16_2d(&mt2_lo, tlo, KB, (unsigned long long)nkb * TN, KB * 2, KB, TN / 2);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(err, 0, sizeof(int), cs);
     if (e == cudaSuccess && fold)
@@ -437,7 +441,9 @@ extern "C" tc_status tc_convolve_tc(const float *x, size_t N, const float *h, si
     if (e == cudaSuccess)
         e = tc::k2_tprep_launch(h, (int)Ll, 0, (int)nkb, KB, thi, nprod == 1 ? nullptr : tlo, cs);
     if (e == cudaSuccess)
-        e = pair ? tc::k2_launch_c2p(mx_hi, mt2_hi, p, cs) : tc::k2_launch(mx_hi, mx_lo, mt_hi, mt_lo, p, nprod, cs);
+        e = spair  ? tc::k2_launch_c2s(mx_hi, mx_lo, mt2_hi, mt2_lo, p, cs)
+            : pair ? tc::k2_launch_c2p(mx_hi, mt2_hi, p, cs)
+                   : tc::k2_launch(mx_hi, mx_lo, mt_hi, mt_lo, p, nprod, cs);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(y, ytmp, (size_t)ny * 4, cudaMemcpyDeviceToDevice, cs);
     if (e == cudaSuccess)

@@ -187,6 +187,11 @@ cudaError_t k2_launch_c2(const CUtensorMap &mx_hi, const CUtensorMap &mt2_hi, co
 // The same on persistent CTA pairs (one cluster per SM pair walks the units,
 // two TMEM accumulators: a unit's epilogue overlaps the next unit's MMAs).
 cudaError_t k2_launch_c2p(const CUtensorMap &mx_hi, const CUtensorMap &mt2_hi, const K2Params &p, cudaStream_t st);
+// The BF16 hi/lo split on persistent CTA pairs (TMEM runs of p.range K blocks
+// drained into FP32 register sums, as k2_launch with nprod 3). p.ntile_c
+// counts tile pairs; mt2_hi / mt2_lo: T over [nkb * 256][32], box 32 x 128.
+cudaError_t k2_launch_c2s(const CUtensorMap &mx_hi, const CUtensorMap &mx_lo, const CUtensorMap &mt2_hi,
+                          const CUtensorMap &mt2_lo, const K2Params &p, cudaStream_t st);
 // Encodes a 2-D bf16 tensor map (inner dimension first). Rows of the box of
 // 64 bytes (box0 = 32) take the 64-byte swizzle, rows of 128 bytes (box0 = 64)
 // the 128-byte swizzle.

@@ -133,6 +133,27 @@ def test_k_parts_folded_in_kernel_equal_k2_reduce(prec, pair, nsplit):
     check(ys[1], X, H, [0], B, prec, rows=[0, 31, 32, 127, 128, 255, 256, 299])
 
 
+@pytest.mark.parametrize("nsplit,rng", [(1, 16), (3, 16), (4, 5), (17, 16)])
+def test_split_on_cta_pairs_equals_single_tiles(nsplit, rng):
+    """The BF16 split on persistent CTA pairs (each SM staging half of the
+    operands, runs of `range` K blocks drained into FP32 registers) computes
+    exactly what the one-tile kernel computes with the same K parts and runs:
+    same bits, in pushes and in the flush (odd pitch); and both match the
+    oracle. 300 channels: the second pair is half outside the group. An odd
+    range leaves a short last run in every part."""
+    C, N, L, B = 300, 2600, 20_000, 256
+    X = synth.audio_block(C, N, 9000 + nsplit)
+    H = synth.decayed_ir(L, 0.2 * L, 83)[None]
+    ys = {}
+    for pair in (2, 0):
+        ys[pair], info = run_group(X, H, [0], L, B, "bf16split", 1280,
+                                   tuning=[(capi.TC_TUNE_K2_PAIR, pair), (capi.TC_TUNE_K2_SPLIT, nsplit),
+                                           (capi.TC_TUNE_K2_RANGE, rng)])
+        assert info.tensor_launches > 0 and info.fp32_fallbacks == 0
+    assert np.array_equal(ys[2], ys[0]), np.argwhere(ys[2] != ys[0])[:5]
+    check(ys[2], X, H, [0], B, "bf16split", rows=[0, 31, 127, 128, 255, 256, 299])
+
+
 @pytest.mark.parametrize("prec", ["bf16split", "bf16"])
 def test_short_ir_one_k_part_odd_pitch(prec):
     """A short IR (L = 700: fewer than 32 K blocks, so one K part and the epilogue writes y itself) with

@@ -602,6 +602,13 @@ uint64_t tc_kernel_launches(void);
  *                        persistent CTA pairs and the one-tile kernel);
  *                        0 = by a separate reduction launch. Both add the
  *                        parts by the same tree: the results are identical
+ *   TC_TUNE_K2_ORDER     order in which the persistent CTA pairs take their
+ *                        units (channel tile pair, output tile, K part):
+ *                        0 = K part fastest, then output tile; 1 = output
+ *                        tile fastest, then K part; 2 = output tile, then
+ *                        channel tile, K part slowest (default: the pairs
+ *                        running at a time share one K range of the IR
+ *                        tiles in L2). Changes no result bit
  *   TC_TUNE_ZERO_SKIP    1 = zero gating on the FP32 gather (the zero-skip of
  *                        Sec. 3.2 and 4.2 at block level, threshold 0): a
  *                        staged stretch of input that is all zero skips its
@@ -614,7 +621,8 @@ typedef enum tc_tune_knob {
     TC_TUNE_K2_PAIR = 2,
     TC_TUNE_ZERO_SKIP = 3,
     TC_TUNE_K2_SPLIT = 4,
-    TC_TUNE_K2_FOLD = 5
+    TC_TUNE_K2_FOLD = 5,
+    TC_TUNE_K2_ORDER = 6
 } tc_tune_knob;
 tc_status tc_set_tuning(tc_stream *s, int knob, long long value);
 

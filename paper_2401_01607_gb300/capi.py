@@ -302,7 +302,8 @@ def tc_convolve(x, N: int, h, L: int, y, cuda_stream=None) -> None:
     _call("tc_convolve", _dev_ptr(x), N, _dev_ptr(h), L, _dev_ptr(y), cs)
 
 
-TC_TUNE_K1_CHUNK, TC_TUNE_K2_RANGE, TC_TUNE_K2_PAIR, TC_TUNE_ZERO_SKIP, TC_TUNE_K2_SPLIT, TC_TUNE_K2_FOLD = range(6)
+(TC_TUNE_K1_CHUNK, TC_TUNE_K2_RANGE, TC_TUNE_K2_PAIR, TC_TUNE_ZERO_SKIP, TC_TUNE_K2_SPLIT, TC_TUNE_K2_FOLD,
+ TC_TUNE_K2_ORDER) = range(7)
 
 
 def tc_set_tuning(s: int, knob: int, value: int) -> None:

@@ -168,6 +168,7 @@ struct tc_stream {
     long long k2_range = -1;    // K blocks per tensor-core CTA range (-1: by precision)
     int k2_nsplit = -1;         // K parts per K2 tile (-1: planned from the waves)
     bool k2_fold = true;        // K parts added inside K2 (false: a k2_reduce launch)
+    int k2_order = 2;           // unit order of the persistent CTA pairs (K2Params::order)
     int k2_mode = 2;  // plain BF16: 0 one channel tile per CTA, 1 two per CTA, 2 persistent CTA pairs,
                       // 3 CTA pairs launched per unit (tuning knob)
     bool zero_skip = false;      // K1 zero gating (tuning knob)
@@ -946,6 +947,7 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
         pair = false;
         p.ntile_c = (int)ntile_c1;
     }
+    p.order = s->k2_order;
     p.y = rowview ? s->k2_rows : y;
     p.y_pitch = rowview ? TN : y_pitch;
     p.err = s->d_err;
@@ -1615,6 +1617,11 @@ tc_status tc_set_tuning(tc_stream *s, int knob, long long value)
         if (value != -1 && value != 0 && value != 1)
             return fail(TC_EINVAL, "TC_TUNE_K2_FOLD must be -1, 0 or 1");
         s->k2_fold = value != 0;
+        return TC_OK;
+    case TC_TUNE_K2_ORDER:
+        if (value < -1 || value > 2)
+            return fail(TC_EINVAL, "TC_TUNE_K2_ORDER must be -1, 0, 1 or 2");
+        s->k2_order = value == -1 ? 2 : (int)value;
         return TC_OK;
     case TC_TUNE_ZERO_SKIP:
         if (value != -1 && value != 0 && value != 1)

@@ -711,10 +711,22 @@ struct K2Unit {
 __device__ __forceinline__ K2Unit k2_unit(const K2Params &p, long long u)
 {
     K2Unit w;
-    w.part = (int)(u % p.nsplit);
-    u /= p.nsplit;
-    w.tile_o = (int)(u % p.ntile_o);
-    w.tile_c = (int)(u / p.ntile_o);
+    if (p.order == 1) {  // output tile fastest, then K part
+        w.tile_o = (int)(u % p.ntile_o);
+        u /= p.ntile_o;
+        w.part = (int)(u % p.nsplit);
+        w.tile_c = (int)(u / p.nsplit);
+    } else if (p.order == 2) {  // output tile fastest, then channel tile; K part slowest
+        w.tile_o = (int)(u % p.ntile_o);
+        u /= p.ntile_o;
+        w.tile_c = (int)(u % p.ntile_c);
+        w.part = (int)(u / p.ntile_c);
+    } else {  // K part fastest, then output tile
+        w.part = (int)(u % p.nsplit);
+        u /= p.nsplit;
+        w.tile_o = (int)(u % p.ntile_o);
+        w.tile_c = (int)(u / p.ntile_o);
+    }
     w.kb0 = w.part * p.kb_per;
     w.nk = max(min(w.kb0 + p.kb_per, p.nkb) - w.kb0, 0);
     return w;

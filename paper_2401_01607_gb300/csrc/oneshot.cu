@@ -354,6 +354,7 @@ extern "C" tc_status tc_convolve_tc(const float *x, size_t N, const float *h, si
     p.x_col0 = 0;
     p.nkb = (int)nkb;
     p.range = precision == TC_BF16_SPLIT ? 16 : 4096;
+    p.order = 2;  // persistent pairs: row tiles fastest, K parts slowest
     p.ntile_c = (int)(pair ? (ntile_c1 + 1) / 2 : ntile_c1);
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);

@@ -150,6 +150,8 @@ struct K2Params {
     int nkb;                 // K blocks per output tile
     int nsplit, kb_per;      // K parts per tile (one CTA each) and blocks per part
     int range;               // K blocks per serial TMEM run before the drain to FP32 registers
+    int order;               // persistent CTA pairs: order of the units (0 K part fastest, then output
+                             // tile; 1 output tile fastest, then K part; 2 output tile, channel tile, K part)
     float *y;                // y[c * y_pitch + j], j < nout
     long long y_pitch;
     float *partial;          // [ntile_c][ntile_o][nsplit][128][256] (nsplit > 1)

@@ -154,6 +154,19 @@ def test_split_on_cta_pairs_equals_single_tiles(nsplit, rng):
     check(ys[2], X, H, [0], B, "bf16split", rows=[0, 31, 127, 128, 255, 256, 299])
 
 
+@pytest.mark.parametrize("prec", ["bf16", "bf16split"])
+def test_unit_order_of_cta_pairs_does_not_change_bits(prec):
+    """The persistent CTA pairs take their units in one of three orders; each
+    unit computes the same sums whichever pair takes it, and the K parts are
+    folded by the same tree, so all three give the same bits."""
+    C, N, L, B = 520, 2600, 20_000, 256
+    X = synth.audio_block(C, N, 9500)
+    H = synth.decayed_ir(L, 0.2 * L, 84)[None]
+    ys = [run_group(X, H, [0], L, B, prec, 1280, tuning=[(capi.TC_TUNE_K2_ORDER, o)])[0] for o in (0, 1, 2)]
+    assert np.array_equal(ys[0], ys[1]) and np.array_equal(ys[0], ys[2])
+    check(ys[0], X, H, [0], B, prec, rows=[0, 255, 256, 511, 512, 519])
+
+
 @pytest.mark.parametrize("prec", ["bf16split", "bf16"])
 def test_short_ir_one_k_part_odd_pitch(prec):
     """A short IR (L = 700: fewer than 32 K blocks, so one K part and the epilogue writes y itself) with

@@ -190,8 +190,6 @@ struct tc_stream {
     size_t k2_partial_floats = 0;
     unsigned *k2_ticket = nullptr;  // after the partials in the same allocation: K-part tickets
     size_t k2_ticket_n = 0;
-    float *k2_rows = nullptr;  // mono streams: row-major output of the 256-sample rows
-    size_t k2_rows_floats = 0;
     long long k2_launches = 0, k1_fallbacks = 0;
 
     // BF16 tensor-core path for MIMO (K3): reversed bf16 hi/lo inputs of a
@@ -268,7 +266,6 @@ void free_all(tc_stream *s)
     cudaFree(s->hist_hi);
     cudaFree(s->hist_lo);
     cudaFree(s->k2_partial);
-    cudaFree(s->k2_rows);
     for (auto &arr : s->tsets)
         for (auto &t : arr) {
             cudaFree(t.thi);
@@ -891,8 +888,8 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
     // A mono stream cuts the push's output into rows of 256 samples and runs
     // them as K2's channels: row r's history is the window from w0 + 256 r, so
     // the X tensor map is one strided view of the history (row stride 512
-    // bytes) and 128 rows fill a tile. Outputs go to a row-major staging
-    // buffer first (the last row may run past the push).
+    // bytes) and 128 rows fill a tile. The rows are written straight into y
+    // (row-major, pitch 256), the last one cut at the push's end.
     CUtensorMap mxr_hi{}, mxr_lo{};
     const bool rowview = s->rows == 1 && nout >= TN &&
                          (w0 - s->base) + (ntile_o - 1) * TN + nkb * KB <= s->cap;
@@ -902,15 +899,6 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
                                  (unsigned long long)ntile_o, (unsigned long long)TN * 2, KB, TM));
         TC_CU(tc::encode_bf16_2d(&mxr_lo, static_cast<char *>(s->hist_lo) + col * 2, (unsigned long long)nkb * KB,
                                  (unsigned long long)ntile_o, (unsigned long long)TN * 2, KB, TM));
-        const size_t need_rows = (size_t)ntile_o * TN;
-        if (need_rows > s->k2_rows_floats) {
-            if (s->k2_rows)
-                cudaFreeAsync(s->k2_rows, s->cs);
-            s->k2_rows = nullptr;
-            TC_CU(tc::pool_alloc(reinterpret_cast<void **>(&s->k2_rows), need_rows * sizeof(float), s->cs));
-            TC_ALIGNED(s->k2_rows);
-            s->k2_rows_floats = need_rows;
-        }
         p.C = (int)ntile_o;
         p.nout = TN;
         p.ntile_o = 1;
@@ -948,8 +936,9 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
         p.ntile_c = (int)ntile_c1;
     }
     p.order = s->k2_order;
-    p.y = rowview ? s->k2_rows : y;
+    p.y = y;
     p.y_pitch = rowview ? TN : y_pitch;
+    p.y_total = rowview ? nout : 0;
     p.err = s->d_err;
     if (nsplit > 1) {
         // Partials per 128-channel tile (the pair kernel writes that layout too).
@@ -977,8 +966,6 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
         TC_CU(tc::k2_launch_pair(mxh, t.mt_hi, p, s->cs));
     else
         TC_CU(tc::k2_launch(mxh, mxl, t.mt_hi, t.mt_lo, p, s->prec == TC_BF16 ? 1 : 3, s->cs));
-    if (rowview)
-        TC_CU(cudaMemcpyAsync(y, s->k2_rows, (size_t)nout * sizeof(float), cudaMemcpyDeviceToDevice, s->cs));
     TC_TRY(prof_end(s, t0, nout));
     s->k2_launches++;
     *used = true;

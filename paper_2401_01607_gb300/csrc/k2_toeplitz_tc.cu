@@ -68,6 +68,14 @@ struct K2Cfg {
     static constexpr int SMEM = NS * STAGE + 1024;  // + alignment slack
 };
 
+// Outputs of row c from column col on that may be written: lim, and with a
+// flat destination of y_total elements (a row view writing the caller's
+// output directly) no further than its end.
+__device__ __forceinline__ long long k2_ylim(const K2Params &p, long long lim, long long c, long long col)
+{
+    return p.y_total > 0 ? min(lim, p.y_total - c * p.y_pitch - col) : lim;
+}
+
 // K parts folded inside the kernel (no k2_reduce launch): every epilogue warp
 // owns a slice of its CTA's tile (32 channels x 128 outputs). After a warp has
 // stored its slice of one K part's sums, it takes a ticket for that slice; the
@@ -81,7 +89,7 @@ constexpr int K2_FOLD_MAX = 16;
 
 template <int NL, int RG>
 __device__ __forceinline__ void k2_fold_rows(const K2Params &p, const float *src, float *dst, long long lim,
-                                             int c, int nrow)
+                                             long long col, int c, int nrow)
 {
     const long long part_stride = (long long)K2_M * K2_N;
     for (int r0 = 0; r0 < nrow; r0 += RG) {
@@ -101,18 +109,21 @@ __device__ __forceinline__ void k2_fold_rows(const K2Params &p, const float *src
                 for (int s = 0; s < w; ++s)
                     v[g][s] = make_float4(v[g][2 * s].x + v[g][2 * s + 1].x, v[g][2 * s].y + v[g][2 * s + 1].y,
                                           v[g][2 * s].z + v[g][2 * s + 1].z, v[g][2 * s].w + v[g][2 * s + 1].w);
-            if (r0 + g >= nrow || lim <= 0)
+            if (r0 + g >= nrow)
+                continue;
+            const long long lr = k2_ylim(p, lim, c + r0 + g, col);
+            if (lr <= 0)
                 continue;
             float *d = dst + (long long)(c + r0 + g) * p.y_pitch;
-            if (lim >= 4 && (reinterpret_cast<uintptr_t>(d) & 15) == 0) {
+            if (lr >= 4 && (reinterpret_cast<uintptr_t>(d) & 15) == 0) {
                 *reinterpret_cast<float4 *>(d) = v[g][0];
             } else {
                 d[0] = v[g][0].x;
-                if (lim > 1)
+                if (lr > 1)
                     d[1] = v[g][0].y;
-                if (lim > 2)
+                if (lr > 2)
                     d[2] = v[g][0].z;
-                if (lim > 3)
+                if (lr > 3)
                     d[3] = v[g][0].w;
             }
         }
@@ -129,14 +140,15 @@ __device__ __forceinline__ void k2_fold_slice(const K2Params &p, int tc1, int ti
         return;
     const float *src = p.partial + ((long long)tc1 * p.ntile_o + tile_o) * p.nsplit * K2_M * K2_N +
                        (long long)(q * 32) * K2_N + half * 128 + lane * 4;
-    float *dst = p.y + (long long)tile_o * K2_N + half * 128 + lane * 4;
-    const long long lim = (long long)p.nout - (long long)tile_o * K2_N - half * 128 - lane * 4;
+    const long long col = (long long)tile_o * K2_N + half * 128 + lane * 4;  // this lane's first output
+    float *dst = p.y + col;
+    const long long lim = (long long)p.nout - col;
     if (p.nsplit <= 4)
-        k2_fold_rows<4, 4>(p, src, dst, lim, c, nrow);
+        k2_fold_rows<4, 4>(p, src, dst, lim, col, c, nrow);
     else if (p.nsplit <= 8)
-        k2_fold_rows<8, 2>(p, src, dst, lim, c, nrow);
+        k2_fold_rows<8, 2>(p, src, dst, lim, col, c, nrow);
     else
-        k2_fold_rows<16, 1>(p, src, dst, lim, c, nrow);
+        k2_fold_rows<16, 1>(p, src, dst, lim, col, c, nrow);
 }
 
 template <int NPROD>
@@ -311,7 +323,8 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
             long long lim;
             if (p.nsplit == 1) {
                 dst = p.y + (long long)c * p.y_pitch + (long long)tile_o * K2_N + half * 128;
-                lim = p.nout - (long long)tile_o * K2_N - half * 128;
+                lim = k2_ylim(p, p.nout - (long long)tile_o * K2_N - half * 128, c,
+                              (long long)tile_o * K2_N + half * 128);
             } else {
                 dst = p.partial + ((((long long)tile_c * p.ntile_o + tile_o) * p.nsplit + part) * K2_M + ch) * K2_N +
                       half * 128;
@@ -482,7 +495,8 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
                 long long lim;
                 if (p.nsplit == 1) {
                     dst = p.y + (long long)c * p.y_pitch + (long long)tile_o * K2_N + half * 128;
-                    lim = p.nout - (long long)tile_o * K2_N - half * 128;
+                    lim = k2_ylim(p, p.nout - (long long)tile_o * K2_N - half * 128, c,
+                                  (long long)tile_o * K2_N + half * 128);
                 } else {
                     // Partials are laid out per 128-channel tile, as k2_reduce reads them.
                     const int tc1 = tile_c * 2 + a;
@@ -657,7 +671,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2_THREADS, 1)
             long long lim;
             if (p.nsplit == 1) {
                 dst = p.y + (long long)c * p.y_pitch + (long long)tile_o * K2_N + half * 128;
-                lim = p.nout - (long long)tile_o * K2_N - half * 128;
+                lim = k2_ylim(p, p.nout - (long long)tile_o * K2_N - half * 128, c,
+                              (long long)tile_o * K2_N + half * 128);
             } else {
                 // Partials per 128-channel tile, as k2_reduce reads them.
                 const int tc1 = tile_c * 2 + (int)rank;
@@ -869,7 +884,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2_THREADS, 1)
             long long lim;
             if (p.nsplit == 1) {
                 dst = p.y + (long long)c * p.y_pitch + (long long)w.tile_o * K2_N + half * 128;
-                lim = p.nout - (long long)w.tile_o * K2_N - half * 128;
+                lim = k2_ylim(p, p.nout - (long long)w.tile_o * K2_N - half * 128, c,
+                              (long long)w.tile_o * K2_N + half * 128);
             } else {
                 const int tc1 = w.tile_c * 2 + (int)rank;
                 dst = p.partial +
@@ -1119,7 +1135,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2_THREADS, 1)
                 long long lim;
                 if (p.nsplit == 1) {
                     dst = p.y + (long long)c * p.y_pitch + (long long)w.tile_o * K2_N + half * 128;
-                    lim = p.nout - (long long)w.tile_o * K2_N - half * 128;
+                    lim = k2_ylim(p, p.nout - (long long)w.tile_o * K2_N - half * 128, c,
+                                  (long long)w.tile_o * K2_N + half * 128);
                 } else {
                     dst = p.partial +
                           ((((long long)tc1 * p.ntile_o + w.tile_o) * p.nsplit + w.part) * K2_M + ch) * K2_N +
@@ -1166,7 +1183,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2_THREADS, 1)
 // Adds the nsplit K-range partials of each (channel, output) by a fixed
 // pairwise tree (adjacent pairs, zero-padded to 64 leaves) and writes y.
 __global__ void k2_reduce(const float *__restrict__ partial, int nsplit, int C, int ntile_o, int nout, float *y,
-                          long long y_pitch)
+                          long long y_pitch, long long y_total)
 {
     const long long total = (long long)C * nout;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
@@ -1185,7 +1202,8 @@ __global__ void k2_reduce(const float *__restrict__ partial, int nsplit, int C, 
             for (int s = 0; s < w; ++s)
                 v[s] = v[2 * s] + v[2 * s + 1];
         }
-        y[(long long)c * y_pitch + o] = v[0];
+        if (y_total <= 0 || (long long)c * y_pitch + o < y_total)
+            y[(long long)c * y_pitch + o] = v[0];
     }
 }
 
@@ -1193,56 +1211,126 @@ __global__ void k2_reduce(const float *__restrict__ partial, int nsplit, int C, 
 // K blocks of kbs samples (32 or 64):
 //   T[kb][i][j] = h[L - 1 + delta + i - kbs kb - j]  (0 outside [0, L)),
 // as bf16 hi = bf16(h) and lo = bf16(h - hi), row-major [kb][256][kbs]
-// (tlo may be null: plain BF16).
+// (tlo may be null: plain BF16). One thread writes eight consecutive j of a
+// row (one 16-byte store per tile).
+__device__ __forceinline__ uint32_t k2_pack_bf16(__nv_bfloat16 a, __nv_bfloat16 b)
+{
+    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
 __global__ void k2_tprep(const float *__restrict__ h, int L, int delta, int nkb, int kbs, __nv_bfloat16 *thi,
                          __nv_bfloat16 *tlo)
 {
-    const long long total = (long long)nkb * K2_N * kbs;
+    const int sh = kbs == 64 ? 3 : 2;  // log2 of the groups of eight per row
+    const long long total = ((long long)nkb * K2_N) << sh;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
          q += (long long)gridDim.x * blockDim.x) {
-        const int j = (int)(q % kbs);
-        const long long r = q / kbs;
-        const int i = (int)(r % K2_N);
-        const long long kb = r / K2_N;
-        const long long k = (long long)L - 1 + delta + i - (long long)kbs * kb - j;
-        const float v = (k >= 0 && k < L) ? h[k] : 0.f;
-        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-        thi[q] = hi;
+        const int jg = (int)(q & ((1 << sh) - 1));
+        const long long r = q >> sh;  // kb * 256 + i
+        const int i = (int)(r & (K2_N - 1));
+        const long long kb = r >> 8;
+        const long long k0 = (long long)L - 1 + delta + i - (long long)kbs * kb - 8 * jg;  // tap of j = 8 jg
+        uint32_t hw[4], lw[4];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+            const long long ka = k0 - e, kb2 = k0 - e - 1;
+            const float va = (ka >= 0 && ka < L) ? h[ka] : 0.f;
+            const float vb = (kb2 >= 0 && kb2 < L) ? h[kb2] : 0.f;
+            const __nv_bfloat16 ha = __float2bfloat16_rn(va), hb = __float2bfloat16_rn(vb);
+            hw[e / 2] = k2_pack_bf16(ha, hb);
+            lw[e / 2] = k2_pack_bf16(__float2bfloat16_rn(va - __bfloat162float(ha)),
+                                     __float2bfloat16_rn(vb - __bfloat162float(hb)));
+        }
+        const long long o = r * kbs + 8 * jg;
+        *reinterpret_cast<uint4 *>(thi + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
         if (tlo)  // plain BF16 reads only the hi tiles
-            tlo[q] = __float2bfloat16_rn(v - __bfloat162float(hi));
+            *reinterpret_cast<uint4 *>(tlo + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
     }
+}
+
+// bf16 hi = bf16(v) and lo = bf16(v - hi) of four values, as two 8-byte words.
+__device__ __forceinline__ void k2_split4(const float v[4], uint2 &hi, uint2 &lo)
+{
+    __nv_bfloat16 b[4];
+    float r[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        b[e] = __float2bfloat16_rn(v[e]);
+        r[e] = v[e] - __bfloat162float(b[e]);
+    }
+    hi = make_uint2(k2_pack_bf16(b[0], b[1]), k2_pack_bf16(b[2], b[3]));
+    lo = make_uint2(k2_pack_bf16(__float2bfloat16_rn(r[0]), __float2bfloat16_rn(r[1])),
+                    k2_pack_bf16(__float2bfloat16_rn(r[2]), __float2bfloat16_rn(r[3])));
 }
 
 // Splits new history samples into bf16 hi = bf16(x) and lo = bf16(x - hi):
 // rows r < rows, columns [col0, col0 + n) of pitch-`pitch` histories (hlo
-// may be null: plain BF16).
+// may be null: plain BF16). One thread takes four consecutive elements of the
+// flat history, on a four-element boundary (16-byte loads, 8-byte stores
+// where all four are in the range).
 __global__ void k2_split(const float *__restrict__ hist, long long pitch, int rows, long long col0, long long n,
                          __nv_bfloat16 *hhi, __nv_bfloat16 *hlo)
 {
-    const long long total = (long long)rows * n;
+    const long long lead = col0 & 3;               // elements of the first group before col0 (pitch % 4 == 0)
+    const long long gpr = (lead + n + 3) >> 2;     // groups per row
+    const long long total = (long long)rows * gpr;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
          q += (long long)gridDim.x * blockDim.x) {
-        const long long r = q / n;
-        const long long idx = r * pitch + col0 + q % n;
-        const float v = hist[idx];
-        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-        hhi[idx] = hi;
-        if (hlo)  // plain BF16 reads only the hi history
-            hlo[idx] = __float2bfloat16_rn(v - __bfloat162float(hi));
+        const long long r = q / gpr;
+        const long long c = (col0 - lead) + ((q - r * gpr) << 2);  // first column of the group
+        const long long idx = r * pitch + c;
+        if (c >= col0 && c + 4 <= col0 + n) {
+            const float4 f = *reinterpret_cast<const float4 *>(hist + idx);
+            const float v[4] = {f.x, f.y, f.z, f.w};
+            uint2 hi, lo;
+            k2_split4(v, hi, lo);
+            *reinterpret_cast<uint2 *>(hhi + idx) = hi;
+            if (hlo)  // plain BF16 reads only the hi history
+                *reinterpret_cast<uint2 *>(hlo + idx) = lo;
+        } else {
+            for (int e = 0; e < 4; ++e) {
+                if (c + e < col0 || c + e >= col0 + n)
+                    continue;
+                const float v = hist[idx + e];
+                const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+                hhi[idx + e] = hi;
+                if (hlo)
+                    hlo[idx + e] = __float2bfloat16_rn(v - __bfloat162float(hi));
+            }
+        }
     }
 }
 
 // hhi[dst_off + i] = bf16(src[i]) and hlo[dst_off + i] = bf16(src[i] - hi),
-// i < n (hlo may be null: plain BF16).
+// i < n (hlo may be null: plain BF16). One thread takes four destination
+// elements on a four-element boundary (one 8-byte store each where all four
+// are in the range).
 __global__ void k2_split_shift(const float *__restrict__ src, long long n, long long dst_off, __nv_bfloat16 *hhi,
                                __nv_bfloat16 *hlo)
 {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const float v = src[i];
-        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-        hhi[dst_off + i] = hi;
-        if (hlo)
-            hlo[dst_off + i] = __float2bfloat16_rn(v - __bfloat162float(hi));
+    const long long d0 = dst_off & ~3LL;
+    const long long groups = (dst_off + n - d0 + 3) >> 2;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < groups;
+         g += (long long)gridDim.x * blockDim.x) {
+        const long long d = d0 + (g << 2);
+        if (d >= dst_off && d + 4 <= dst_off + n) {
+            const float v[4] = {src[d - dst_off], src[d - dst_off + 1], src[d - dst_off + 2], src[d - dst_off + 3]};
+            uint2 hi, lo;
+            k2_split4(v, hi, lo);
+            *reinterpret_cast<uint2 *>(hhi + d) = hi;
+            if (hlo)
+                *reinterpret_cast<uint2 *>(hlo + d) = lo;
+        } else {
+            for (int e = 0; e < 4; ++e) {
+                if (d + e < dst_off || d + e >= dst_off + n)
+                    continue;
+                const float v = src[d + e - dst_off];
+                const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+                hhi[d + e] = hi;
+                if (hlo)
+                    hlo[d + e] = __float2bfloat16_rn(v - __bfloat162float(hi));
+            }
+        }
     }
 }
 
@@ -1265,7 +1353,7 @@ cudaError_t k2_tprep_launch(const float *h, int L, int delta, int nkb, int kbs, 
 {
     if (kbs != K2_KB && kbs != K2_KB1)
         return cudaErrorInvalidValue;
-    const long long work = (long long)nkb * K2_N * kbs;
+    const long long work = (long long)nkb * K2_N * (kbs / 8);
     k2_tprep<<<grid_for(work), 256, 0, st>>>(h, L, delta, nkb, kbs, (__nv_bfloat16 *)thi, (__nv_bfloat16 *)tlo);
     count_launch();
     return cudaGetLastError();
@@ -1276,8 +1364,11 @@ cudaError_t k2_split_launch(const float *hist, long long pitch, int rows, long l
 {
     if (n <= 0)
         return cudaSuccess;
-    k2_split<<<grid_for((long long)rows * n), 256, 0, st>>>(hist, pitch, rows, col0, n, (__nv_bfloat16 *)hhi,
-                                                           (__nv_bfloat16 *)hlo);
+    if (pitch % 4 != 0 || (reinterpret_cast<uintptr_t>(hist) & 15) != 0 || (reinterpret_cast<uintptr_t>(hhi) & 7) != 0 ||
+        (reinterpret_cast<uintptr_t>(hlo) & 7) != 0)
+        return cudaErrorInvalidValue;  // the four-element groups need these alignments
+    k2_split<<<grid_for((long long)rows * ((n + 6) / 4)), 256, 0, st>>>(hist, pitch, rows, col0, n,
+                                                                       (__nv_bfloat16 *)hhi, (__nv_bfloat16 *)hlo);
     count_launch();
     return cudaGetLastError();
 }
@@ -1287,7 +1378,10 @@ cudaError_t k2_split_shift_launch(const float *src, long long n, long long dst_o
 {
     if (n <= 0)
         return cudaSuccess;
-    k2_split_shift<<<grid_for(n), 256, 0, st>>>(src, n, dst_off, (__nv_bfloat16 *)hhi, (__nv_bfloat16 *)hlo);
+    if ((reinterpret_cast<uintptr_t>(hhi) & 7) != 0 || (reinterpret_cast<uintptr_t>(hlo) & 7) != 0)
+        return cudaErrorInvalidValue;  // the four-element groups need 8-byte aligned destinations
+    k2_split_shift<<<grid_for((n + 6) / 4), 256, 0, st>>>(src, n, dst_off, (__nv_bfloat16 *)hhi,
+                                                          (__nv_bfloat16 *)hlo);
     count_launch();
     return cudaGetLastError();
 }
@@ -1319,7 +1413,7 @@ cudaError_t k2_launch_pair(const CUtensorMap &mx_hi, const CUtensorMap &mt_hi, c
         return e;
     const long long work = (long long)p.C * p.nout;
     k2_reduce<<<grid_for(work), 256, 0, st>>>(p.partial, p.nsplit, p.C, (p.nout + K2_N - 1) / K2_N, p.nout, p.y,
-                                              p.y_pitch);
+                                              p.y_pitch, p.y_total);
     count_launch();
     return cudaGetLastError();
 }
@@ -1356,7 +1450,7 @@ cudaError_t k2_launch_c2p(const CUtensorMap &mx_hi, const CUtensorMap &mt2_hi, c
         return e;  // no parts, or folded in the kernel
     const long long work = (long long)p.C * p.nout;
     k2_reduce<<<grid_for(work), 256, 0, st>>>(p.partial, p.nsplit, p.C, (p.nout + K2_N - 1) / K2_N, p.nout, p.y,
-                                              p.y_pitch);
+                                              p.y_pitch, p.y_total);
     count_launch();
     return cudaGetLastError();
 }
@@ -1394,7 +1488,7 @@ cudaError_t k2_launch_c2s(const CUtensorMap &mx_hi, const CUtensorMap &mx_lo, co
         return e;  // no parts, or folded in the kernel
     const long long work = (long long)p.C * p.nout;
     k2_reduce<<<grid_for(work), 256, 0, st>>>(p.partial, p.nsplit, p.C, (p.nout + K2_N - 1) / K2_N, p.nout, p.y,
-                                              p.y_pitch);
+                                              p.y_pitch, p.y_total);
     count_launch();
     return cudaGetLastError();
 }
@@ -1426,7 +1520,7 @@ cudaError_t k2_launch_c2(const CUtensorMap &mx_hi, const CUtensorMap &mt2_hi, co
         return e;
     const long long work = (long long)p.C * p.nout;
     k2_reduce<<<grid_for(work), 256, 0, st>>>(p.partial, p.nsplit, p.C, (p.nout + K2_N - 1) / K2_N, p.nout, p.y,
-                                              p.y_pitch);
+                                              p.y_pitch, p.y_total);
     count_launch();
     return cudaGetLastError();
 }
@@ -1463,7 +1557,8 @@ cudaError_t k2_launch(const CUtensorMap &mx_hi, const CUtensorMap &mx_lo, const 
     if (e != cudaSuccess || p.nsplit == 1 || (p.ticket != nullptr && p.nsplit <= K2_FOLD_MAX))
         return e;  // no parts, or folded in the kernel
     const long long work = (long long)p.C * p.nout;
-    k2_reduce<<<grid_for(work), 256, 0, st>>>(p.partial, p.nsplit, p.C, p.ntile_o, p.nout, p.y, p.y_pitch);
+    k2_reduce<<<grid_for(work), 256, 0, st>>>(p.partial, p.nsplit, p.C, p.ntile_o, p.nout, p.y,
+                                              p.y_pitch, p.y_total);
     count_launch();
     return cudaGetLastError();
 }

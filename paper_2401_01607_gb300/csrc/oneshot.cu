@@ -381,14 +381,15 @@ extern "C" tc_status tc_convolve_tc(const float *x, size_t N, const float *h, si
         p.ntile_c = (int)ntile_c1;
     }
     // The bf16 input rows are split straight from x into the padded buffers (zero margins before and after).
+    // Plain BF16 reads only the hi input and tiles; the rows are written straight into y.
     const size_t b_xs = 0, b_xb = (size_t)npad * 2, b_t = (size_t)nkb * TN * KB * 2;
-    const size_t b_y = (size_t)R * TN * 4;
+    const size_t b_xl = nprod == 1 ? 0 : b_xb, b_tl = nprod == 1 ? 0 : b_t;
     const size_t b_part = nsplit > 1 ? (size_t)2 * ((ntile_c1 + 1) / 2) * nsplit * TM * TN * 4 : 0;
     // K-part tickets of the in-kernel fold (one per 128-row tile and warp slice).
     const bool fold = nsplit > 1 && nsplit <= 16;
     const size_t b_tk = fold ? (size_t)2 * ((ntile_c1 + 1) / 2) * 8 * 4 : 0;
-    const size_t o_xs = 0, o_hi = o_xs + ru(b_xs, 256), o_lo = o_hi + ru(b_xb, 256), o_th = o_lo + ru(b_xb, 256);
-    const size_t o_tl = o_th + ru(b_t, 256), o_y = o_tl + ru(b_t, 256), o_part = o_y + ru(b_y, 256);
+    const size_t o_xs = 0, o_hi = o_xs + ru(b_xs, 256), o_lo = o_hi + ru(b_xb, 256), o_th = o_lo + ru(b_xl, 256);
+    const size_t o_tl = o_th + ru(b_t, 256), o_part = o_tl + ru(b_tl, 256);
     const size_t o_tk = o_part + ru(b_part, 256), o_err = o_tk + ru(b_tk, 256), total = o_err + 256;
     char *mem = nullptr;
     cudaError_t e = tc::pool_alloc(reinterpret_cast<void **>(&mem), total, cs);
@@ -400,10 +401,10 @@ extern "C" tc_status tc_convolve_tc(const float *x, size_t N, const float *h, si
         return na_fail(TC_ECUDA, "tc_convolve_tc: the stream-ordered allocation is not 256-byte aligned");
     }
     void *xhi = mem + o_hi, *xlo = mem + o_lo, *thi = mem + o_th, *tlo = mem + o_tl;
-    float *ytmp = reinterpret_cast<float *>(mem + o_y);
     int *err = reinterpret_cast<int *>(mem + o_err);
-    p.y = ytmp;
+    p.y = y;
     p.y_pitch = TN;
+    p.y_total = ny;  // the last row stops at the end of y
     p.partial = nsplit > 1 ? reinterpret_cast<float *>(mem + o_part) : nullptr;
     p.ticket = fold ? reinterpret_cast<unsigned *>(mem + o_tk) : nullptr;
     p.err = err;
@@ -412,16 +413,16 @@ extern "C" tc_status tc_convolve_tc(const float *x, size_t N, const float *h, si
     // Rows of the X view overlap: row r starts 256 samples after row r - 1.
     e = tc::encode_bf16_2d(&mx_hi, xhi, (unsigned long long)nkb * KB, (unsigned long long)R, (unsigned long long)TN * 2,
                            KB, TM);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && nprod == 3)
         e = tc::encode_bf16_2d(&mx_lo, xlo, (unsigned long long)nkb * KB, (unsigned long long)R,
                                (unsigned long long)TN * 2, KB, TM);
     if (e == cudaSuccess)
         e = tc::encode_bf16_2d(&mt_hi, thi, KB, (unsigned long long)nkb * TN, KB * 2, KB, TN);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && nprod == 3)
         e = tc::encode_bf16_2d(&mt_lo, tlo, KB, (unsigned long long)nkb * TN, KB * 2, KB, TN);
     if (e == cudaSuccess)
         e = tc::encode_bf16_2d(&mt2_hi, thi, KB, (unsigned long long)nkb * TN, KB * 2, KB, TN / 2);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && nprod == 3)
         e = tc::encode_bf16_2d(&mt2_lo, tlo, KB, (unsigned long long)nkb * TN, KB * 2, KB, TN / 2);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(err, 0, sizeof(int), cs);
@@ -445,8 +446,6 @@ extern "C" tc_status tc_convolve_tc(const float *x, size_t N, const float *h, si
         e = spair  ? tc::k2_launch_c2s(mx_hi, mx_lo, mt2_hi, mt2_lo, p, cs)
             : pair ? tc::k2_launch_c2p(mx_hi, mt2_hi, p, cs)
                    : tc::k2_launch(mx_hi, mx_lo, mt_hi, mt_lo, p, nprod, cs);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(y, ytmp, (size_t)ny * 4, cudaMemcpyDeviceToDevice, cs);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, cs);
     cudaFreeAsync(mem, cs);

@@ -154,6 +154,7 @@ struct K2Params {
                              // tile; 1 output tile fastest, then K part; 2 output tile, channel tile, K part)
     float *y;                // y[c * y_pitch + j], j < nout
     long long y_pitch;
+    long long y_total;       // > 0: y is flat and writes at c * y_pitch + j >= y_total are dropped
     float *partial;          // [ntile_c][ntile_o][nsplit][128][256] (nsplit > 1)
     unsigned *ticket;        // persistent CTA pairs: [2 ntile_c][ntile_o][8] K-part tickets per warp slice,
                              // zero between launches; null = parts added by k2_reduce

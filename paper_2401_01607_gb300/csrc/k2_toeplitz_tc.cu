@@ -1218,34 +1218,41 @@ __device__ __forceinline__ uint32_t k2_pack_bf16(__nv_bfloat16 a, __nv_bfloat16 
     return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
 
+// Group q (eight consecutive j of one row) of the Toeplitz tiles; sh = log2
+// of the groups per row (kbs / 8).
+__device__ __forceinline__ void k2_tprep_group(const float *__restrict__ h, int L, int delta, int kbs, int sh,
+                                               long long q, __nv_bfloat16 *thi, __nv_bfloat16 *tlo)
+{
+    const int jg = (int)(q & ((1 << sh) - 1));
+    const long long r = q >> sh;  // kb * 256 + i
+    const int i = (int)(r & (K2_N - 1));
+    const long long kb = r >> 8;
+    const long long k0 = (long long)L - 1 + delta + i - (long long)kbs * kb - 8 * jg;  // tap of j = 8 jg
+    uint32_t hw[4], lw[4];
+#pragma unroll
+    for (int e = 0; e < 8; e += 2) {
+        const long long ka = k0 - e, kb2 = k0 - e - 1;
+        const float va = (ka >= 0 && ka < L) ? h[ka] : 0.f;
+        const float vb = (kb2 >= 0 && kb2 < L) ? h[kb2] : 0.f;
+        const __nv_bfloat16 ha = __float2bfloat16_rn(va), hb = __float2bfloat16_rn(vb);
+        hw[e / 2] = k2_pack_bf16(ha, hb);
+        lw[e / 2] = k2_pack_bf16(__float2bfloat16_rn(va - __bfloat162float(ha)),
+                                 __float2bfloat16_rn(vb - __bfloat162float(hb)));
+    }
+    const long long o = r * kbs + 8 * jg;
+    *reinterpret_cast<uint4 *>(thi + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+    if (tlo)  // plain BF16 reads only the hi tiles
+        *reinterpret_cast<uint4 *>(tlo + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+}
+
 __global__ void k2_tprep(const float *__restrict__ h, int L, int delta, int nkb, int kbs, __nv_bfloat16 *thi,
                          __nv_bfloat16 *tlo)
 {
-    const int sh = kbs == 64 ? 3 : 2;  // log2 of the groups of eight per row
+    const int sh = kbs == 64 ? 3 : 2;
     const long long total = ((long long)nkb * K2_N) << sh;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
-         q += (long long)gridDim.x * blockDim.x) {
-        const int jg = (int)(q & ((1 << sh) - 1));
-        const long long r = q >> sh;  // kb * 256 + i
-        const int i = (int)(r & (K2_N - 1));
-        const long long kb = r >> 8;
-        const long long k0 = (long long)L - 1 + delta + i - (long long)kbs * kb - 8 * jg;  // tap of j = 8 jg
-        uint32_t hw[4], lw[4];
-#pragma unroll
-        for (int e = 0; e < 8; e += 2) {
-            const long long ka = k0 - e, kb2 = k0 - e - 1;
-            const float va = (ka >= 0 && ka < L) ? h[ka] : 0.f;
-            const float vb = (kb2 >= 0 && kb2 < L) ? h[kb2] : 0.f;
-            const __nv_bfloat16 ha = __float2bfloat16_rn(va), hb = __float2bfloat16_rn(vb);
-            hw[e / 2] = k2_pack_bf16(ha, hb);
-            lw[e / 2] = k2_pack_bf16(__float2bfloat16_rn(va - __bfloat162float(ha)),
-                                     __float2bfloat16_rn(vb - __bfloat162float(hb)));
-        }
-        const long long o = r * kbs + 8 * jg;
-        *reinterpret_cast<uint4 *>(thi + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-        if (tlo)  // plain BF16 reads only the hi tiles
-            *reinterpret_cast<uint4 *>(tlo + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-    }
+         q += (long long)gridDim.x * blockDim.x)
+        k2_tprep_group(h, L, delta, kbs, sh, q, thi, tlo);
 }
 
 // bf16 hi = bf16(v) and lo = bf16(v - hi) of four values, as two 8-byte words.
@@ -1301,35 +1308,35 @@ __global__ void k2_split(const float *__restrict__ hist, long long pitch, int ro
     }
 }
 
-// hhi[dst_off + i] = bf16(src[i]) and hlo[dst_off + i] = bf16(src[i] - hi),
-// i < n (hlo may be null: plain BF16). One thread takes four destination
-// elements on a four-element boundary (one 8-byte store each where all four
-// are in the range).
-__global__ void k2_split_shift(const float *__restrict__ src, long long n, long long dst_off, __nv_bfloat16 *hhi,
-                               __nv_bfloat16 *hlo)
+// Everything a one-shot call prepares, in one launch: the padded input as
+// bf16 hi (and lo) rows, xs[d] = x[d - off] for d in [off, off + N) and 0 on
+// the rest of [0, npad) (groups of four, 8-byte stores); the Toeplitz tiles
+// of h at shift 0 (as k2_tprep); and nzero zero words (tickets, error word).
+__global__ void k2_oneshot_prep(const float *__restrict__ x, long long N, long long off, long long npad,
+                                __nv_bfloat16 *xhi, __nv_bfloat16 *xlo, const float *__restrict__ h, int L, int nkb,
+                                int kbs, __nv_bfloat16 *thi, __nv_bfloat16 *tlo, unsigned *zero, long long nzero)
 {
-    const long long d0 = dst_off & ~3LL;
-    const long long groups = (dst_off + n - d0 + 3) >> 2;
-    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < groups;
-         g += (long long)gridDim.x * blockDim.x) {
-        const long long d = d0 + (g << 2);
-        if (d >= dst_off && d + 4 <= dst_off + n) {
-            const float v[4] = {src[d - dst_off], src[d - dst_off + 1], src[d - dst_off + 2], src[d - dst_off + 3]};
+    const long long gx = npad >> 2;
+    const int sh = kbs == 64 ? 3 : 2;
+    const long long gt = ((long long)nkb * K2_N) << sh;
+    const long long total = gx + gt + nzero;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        if (q < gx) {
+            const long long d = q << 2;
+            float v[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                v[e] = (d + e >= off && d + e < off + N) ? x[d + e - off] : 0.f;
             uint2 hi, lo;
             k2_split4(v, hi, lo);
-            *reinterpret_cast<uint2 *>(hhi + d) = hi;
-            if (hlo)
-                *reinterpret_cast<uint2 *>(hlo + d) = lo;
+            *reinterpret_cast<uint2 *>(xhi + d) = hi;
+            if (xlo)
+                *reinterpret_cast<uint2 *>(xlo + d) = lo;
+        } else if (q < gx + gt) {
+            k2_tprep_group(h, L, 0, kbs, sh, q - gx, thi, tlo);
         } else {
-            for (int e = 0; e < 4; ++e) {
-                if (d + e < dst_off || d + e >= dst_off + n)
-                    continue;
-                const float v = src[d + e - dst_off];
-                const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-                hhi[d + e] = hi;
-                if (hlo)
-                    hlo[d + e] = __float2bfloat16_rn(v - __bfloat162float(hi));
-            }
+            zero[q - gx - gt] = 0u;
         }
     }
 }
@@ -1373,15 +1380,18 @@ cudaError_t k2_split_launch(const float *hist, long long pitch, int rows, long l
     return cudaGetLastError();
 }
 
-cudaError_t k2_split_shift_launch(const float *src, long long n, long long dst_off, void *hhi, void *hlo,
-                                  cudaStream_t st)
+cudaError_t k2_oneshot_prep_launch(const float *x, long long N, long long off, long long npad, void *xhi, void *xlo,
+                                   const float *h, int L, int nkb, int kbs, void *thi, void *tlo, unsigned *zero,
+                                   long long nzero, cudaStream_t st)
 {
-    if (n <= 0)
-        return cudaSuccess;
-    if ((reinterpret_cast<uintptr_t>(hhi) & 7) != 0 || (reinterpret_cast<uintptr_t>(hlo) & 7) != 0)
-        return cudaErrorInvalidValue;  // the four-element groups need 8-byte aligned destinations
-    k2_split_shift<<<grid_for((n + 6) / 4), 256, 0, st>>>(src, n, dst_off, (__nv_bfloat16 *)hhi,
-                                                          (__nv_bfloat16 *)hlo);
+    if ((kbs != K2_KB && kbs != K2_KB1) || npad % 4 != 0 || (reinterpret_cast<uintptr_t>(xhi) & 7) != 0 ||
+        (reinterpret_cast<uintptr_t>(xlo) & 7) != 0 || (reinterpret_cast<uintptr_t>(thi) & 15) != 0 ||
+        (reinterpret_cast<uintptr_t>(tlo) & 15) != 0)
+        return cudaErrorInvalidValue;
+    const long long work = npad / 4 + (long long)nkb * K2_N * (kbs / 8) + nzero;
+    k2_oneshot_prep<<<grid_for(work), 256, 0, st>>>(x, N, off, npad, (__nv_bfloat16 *)xhi, (__nv_bfloat16 *)xlo, h,
+                                                    L, nkb, kbs, (__nv_bfloat16 *)thi, (__nv_bfloat16 *)tlo, zero,
+                                                    nzero);
     count_launch();
     return cudaGetLastError();
 }

@@ -408,11 +408,18 @@ extern "C" tc_status tc_convolve_tc(const float *x, size_t N, const float *h, si
     p.partial = nsplit > 1 ? reinterpret_cast<float *>(mem + o_part) : nullptr;
     p.ticket = fold ? reinterpret_cast<unsigned *>(mem + o_tk) : nullptr;
     p.err = err;
+    // One launch prepares the bf16 input rows (with their zero margins), the
+    // Toeplitz tiles and the zeroed tickets and error word; the tensor maps
+    // are encoded on the host while it runs.
+    e = tc::k2_oneshot_prep_launch(x, Nl, off, npad, xhi, nprod == 1 ? nullptr : xlo, h, (int)Ll, (int)nkb, KB, thi,
+                                   nprod == 1 ? nullptr : tlo, reinterpret_cast<unsigned *>(mem + o_tk),
+                                   (long long)(total - o_tk) / 4, cs);
     CUtensorMap mx_hi{}, mx_lo{}, mt_hi{}, mt_lo{}, mt2_hi{}, mt2_lo{};
     int herr = 0;
     // Rows of the X view overlap: row r starts 256 samples after row r - 1.
-    e = tc::encode_bf16_2d(&mx_hi, xhi, (unsigned long long)nkb * KB, (unsigned long long)R, (unsigned long long)TN * 2,
-                           KB, TM);
+    if (e == cudaSuccess)
+        e = tc::encode_bf16_2d(&mx_hi, xhi, (unsigned long long)nkb * KB, (unsigned long long)R,
+                               (unsigned long long)TN * 2, KB, TM);
     if (e == cudaSuccess && nprod == 3)
         e = tc::encode_bf16_2d(&mx_lo, xlo, (unsigned long long)nkb * KB, (unsigned long long)R,
                                (unsigned long long)TN * 2, KB, TM);
@@ -424,24 +431,6 @@ extern "C" tc_status tc_convolve_tc(const float *x, size_t N, const float *h, si
         e = tc::encode_bf16_2d(&mt2_hi, thi, KB, (unsigned long long)nkb * TN, KB * 2, KB, TN / 2);
     if (e == cudaSuccess && nprod == 3)
         e = tc::encode_bf16_2d(&mt2_lo, tlo, KB, (unsigned long long)nkb * TN, KB * 2, KB, TN / 2);
-    if (e == cudaSuccess)
-        e = cudaMemsetAsync(err, 0, sizeof(int), cs);
-    if (e == cudaSuccess && fold)
-        e = cudaMemsetAsync(p.ticket, 0, b_tk, cs);
-    // xs[m] = x[m - off] with zeros around it, as bf16 hi (and lo for the split; plain BF16 reads hi only).
-    for (void *xb : {xhi, xlo}) {
-        if (xb == xlo && nprod == 1)
-            continue;
-        char *b = static_cast<char *>(xb);
-        if (e == cudaSuccess)
-            e = cudaMemsetAsync(b, 0, (size_t)off * 2, cs);
-        if (e == cudaSuccess)
-            e = cudaMemsetAsync(b + (size_t)(off + Nl) * 2, 0, (size_t)(npad - off - Nl) * 2, cs);
-    }
-    if (e == cudaSuccess)
-        e = tc::k2_split_shift_launch(x, Nl, off, xhi, nprod == 1 ? nullptr : xlo, cs);
-    if (e == cudaSuccess)
-        e = tc::k2_tprep_launch(h, (int)Ll, 0, (int)nkb, KB, thi, nprod == 1 ? nullptr : tlo, cs);
     if (e == cudaSuccess)
         e = spair  ? tc::k2_launch_c2s(mx_hi, mx_lo, mt2_hi, mt2_lo, p, cs)
             : pair ? tc::k2_launch_c2p(mx_hi, mt2_hi, p, cs)

@@ -168,9 +168,12 @@ size_t k2_smem_bytes(int nprod);
 // Toeplitz tiles of IR h (fp32, L taps) for shift delta: hi/lo bf16 [nkb][256][kbs].
 cudaError_t k2_tprep_launch(const float *h, int L, int delta, int nkb, int kbs, void *thi, void *tlo,
                             cudaStream_t st);
-// bf16 hi/lo split of src[0, n) into hhi/hlo[dst_off, dst_off + n) (hlo may be null).
-cudaError_t k2_split_shift_launch(const float *src, long long n, long long dst_off, void *hhi, void *hlo,
-                                  cudaStream_t st);
+// One-shot preparation in one launch: xhi/xlo[d] = bf16 split of x[d - off] on
+// [off, off + N), 0 elsewhere in [0, npad) (xlo may be null); the Toeplitz
+// tiles of h at shift 0 (as k2_tprep_launch); zero[0, nzero) = 0.
+cudaError_t k2_oneshot_prep_launch(const float *x, long long N, long long off, long long npad, void *xhi, void *xlo,
+                                   const float *h, int L, int nkb, int kbs, void *thi, void *tlo, unsigned *zero,
+                                   long long nzero, cudaStream_t st);
 // bf16 hi/lo split of history columns [col0, col0 + n) of `rows` rows.
 cudaError_t k2_split_launch(const float *hist, long long pitch, int rows, long long col0, long long n, void *hhi,
                             void *hlo, cudaStream_t st);

@@ -83,32 +83,43 @@ __device__ __forceinline__ long long k2_ylim(const K2Params &p, long long lim, l
 // them by the same fixed pairwise tree as k2_reduce (adjacent pairs, zero
 // padded), so the result does not depend on which part finished last, and
 // writes y. Nothing waits: a slice whose tickets are not all taken is simply
-// not folded. Up to K2_FOLD_MAX parts; the loads of NL parts x RG rows are in
-// flight together.
+// not folded. Up to K2_FOLD_MAX parts.
 constexpr int K2_FOLD_MAX = 16;
 
-template <int NL, int RG>
+__device__ __forceinline__ float4 k2_add4(float4 a, float4 b)
+{
+    return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+
+// NS parts of RG = 16 / NS rows at a time (at most 16 loads of 16 bytes in
+// flight per lane). The tree adds adjacent pairs level by level and carries
+// an odd last element up unchanged, which gives the same sums as the zero
+// padded tree of k2_reduce (x + 0 = x).
+template <int NS>
 __device__ __forceinline__ void k2_fold_rows(const K2Params &p, const float *src, float *dst, long long lim,
                                              long long col, int c, int nrow)
 {
+    constexpr int RG = NS >= 16 ? 1 : 16 / NS;
     const long long part_stride = (long long)K2_M * K2_N;
     for (int r0 = 0; r0 < nrow; r0 += RG) {
-        float4 v[RG][NL];
+        float4 v[RG][NS];
 #pragma unroll
         for (int g = 0; g < RG; ++g)
 #pragma unroll
-            for (int s = 0; s < NL; ++s)
-                v[g][s] = (s < p.nsplit && r0 + g < nrow)
+            for (int s = 0; s < NS; ++s)
+                v[g][s] = r0 + g < nrow
                               ? __ldcg(reinterpret_cast<const float4 *>(src + s * part_stride + (r0 + g) * K2_N))
                               : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int g = 0; g < RG; ++g) {
 #pragma unroll
-            for (int w = NL / 2; w >= 1; w >>= 1)
+            for (int n = NS; n > 1; n = (n + 1) / 2) {
 #pragma unroll
-                for (int s = 0; s < w; ++s)
-                    v[g][s] = make_float4(v[g][2 * s].x + v[g][2 * s + 1].x, v[g][2 * s].y + v[g][2 * s + 1].y,
-                                          v[g][2 * s].z + v[g][2 * s + 1].z, v[g][2 * s].w + v[g][2 * s + 1].w);
+                for (int s = 0; s < n / 2; ++s)
+                    v[g][s] = k2_add4(v[g][2 * s], v[g][2 * s + 1]);
+                if (n & 1)
+                    v[g][n / 2] = v[g][n - 1];
+            }
             if (r0 + g >= nrow)
                 continue;
             const long long lr = k2_ylim(p, lim, c + r0 + g, col);
@@ -143,12 +154,18 @@ __device__ __forceinline__ void k2_fold_slice(const K2Params &p, int tc1, int ti
     const long long col = (long long)tile_o * K2_N + half * 128 + lane * 4;  // this lane's first output
     float *dst = p.y + col;
     const long long lim = (long long)p.nout - col;
-    if (p.nsplit <= 4)
-        k2_fold_rows<4, 4>(p, src, dst, lim, col, c, nrow);
-    else if (p.nsplit <= 8)
-        k2_fold_rows<8, 2>(p, src, dst, lim, col, c, nrow);
-    else
-        k2_fold_rows<16, 1>(p, src, dst, lim, col, c, nrow);
+    switch (p.nsplit) {
+#define K2_FOLD_CASE(n)                                    \
+    case n:                                                \
+        k2_fold_rows<n>(p, src, dst, lim, col, c, nrow); \
+        break;
+        K2_FOLD_CASE(2) K2_FOLD_CASE(3) K2_FOLD_CASE(4) K2_FOLD_CASE(5) K2_FOLD_CASE(6) K2_FOLD_CASE(7)
+        K2_FOLD_CASE(8) K2_FOLD_CASE(9) K2_FOLD_CASE(10) K2_FOLD_CASE(11) K2_FOLD_CASE(12) K2_FOLD_CASE(13)
+        K2_FOLD_CASE(14) K2_FOLD_CASE(15) K2_FOLD_CASE(16)
+#undef K2_FOLD_CASE
+    default:
+        break;  // 1 part needs no fold; more than K2_FOLD_MAX parts go to k2_reduce
+    }
 }
 
 template <int NPROD>

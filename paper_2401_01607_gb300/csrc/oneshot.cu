@@ -305,11 +305,13 @@ extern "C" tc_status tc_convolve_noalloc(const float *x, size_t N, const float *
 // samples, each row a "channel" of the shared-IR contraction K2.
 //
 // With xs the input delayed by L - 1 (zeros before and after it), row r of the
-// output is y[256 r + i] = sum_j T[i][j] xs[256 r + j], i < 256, j < 32 nkb,
+// output is y[256 r + i] = sum_j T[i][j] xs[256 r + j], i < 256, j < KB nkb,
 // T[i][j] = h[L - 1 + i - j]: exactly K2's product for a group whose channel
-// r has the history xs[256 r + .]. Those histories overlap, so K2's X tensor
-// map is one strided view of xs: row stride 256 samples (512 bytes), row
-// length 32 nkb. The Toeplitz tiles of h are built once per call.
+// r has the history xs[256 r + .] (K blocks of KB = 64 samples in plain BF16,
+// 32 in the split). Those histories overlap, so K2's X tensor map is one
+// strided view of xs: row stride 256 samples (512 bytes), row length KB nkb.
+// The Toeplitz tiles of h are built once per call; the rows are written
+// straight into y, the last one cut at its end.
 // ---------------------------------------------------------------------------
 extern "C" tc_status tc_convolve_tc(const float *x, size_t N, const float *h, size_t L, float *y, int precision,
                                     void *cuda_stream)
@@ -415,7 +417,27 @@ extern "C" tc_status tc_convolve_tc(const float *x, size_t N, const float *h, si
                                    nprod == 1 ? nullptr : tlo, reinterpret_cast<unsigned *>(mem + o_tk),
                                    (long long)(total - o_tk) / 4, cs);
     CUtensorMap mx_hi{}, mx_lo{}, mt_hi{}, mt_lo{}, mt2_hi{}, mt2_lo{};
-    int herr = 0;
+    // The error word comes back through a pinned word of this thread (a
+    // true asynchronous copy); pageable memory where that cannot be had.
+    struct PinnedWord {
+        int *p = nullptr;
+        PinnedWord()
+        {
+            if (cudaHostAlloc(reinterpret_cast<void **>(&p), sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+                p = nullptr;
+                cudaGetLastError();
+            }
+        }
+        ~PinnedWord()
+        {
+            if (p)
+                cudaFreeHost(p);
+        }
+    };
+    static thread_local PinnedWord pinned;
+    int herr_pageable = 0;
+    int *const herr_p = pinned.p ? pinned.p : &herr_pageable;
+    *herr_p = 0;
     // Rows of the X view overlap: row r starts 256 samples after row r - 1.
     if (e == cudaSuccess)
         e = tc::encode_bf16_2d(&mx_hi, xhi, (unsigned long long)nkb * KB, (unsigned long long)R,
@@ -436,13 +458,13 @@ extern "C" tc_status tc_convolve_tc(const float *x, size_t N, const float *h, si
             : pair ? tc::k2_launch_c2p(mx_hi, mt2_hi, p, cs)
                    : tc::k2_launch(mx_hi, mx_lo, mt_hi, mt_lo, p, nprod, cs);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, cs);
+        e = cudaMemcpyAsync(herr_p, err, sizeof(int), cudaMemcpyDeviceToHost, cs);
     cudaFreeAsync(mem, cs);
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(cs);
     if (e != cudaSuccess)
         return na_fail(TC_ECUDA, std::string("tc_convolve_tc: ") + cudaGetErrorString(e));
-    if (herr)
+    if (*herr_p)
         return na_fail(TC_ETIMEOUT, "tc_convolve_tc: a kernel's bounded wait gave up");
     return TC_OK;
 }

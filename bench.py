@@ -483,7 +483,7 @@ def bench_shared(torch, steps: int, warmup: int, P: int = 8192, C: int = 1024, N
     h_d = torch.from_numpy(np.ascontiguousarray(w.H[0][None])).cuda()
     macs = C * N * L
     peaks = load_peaks()
-    bf16_peak = float(peaks.get("bf16_tflops_sustained", 1690.8))
+    bf16_peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
     out = {"workload": "%d streams x %d samples (%.1f s @ 48 kHz), one shared IR L=96000 tau=19200, "
                        "block 256, pushes of %d" % (C, N, N / FS, P), "tap_macs": macs}
     ts = run.ts
@@ -528,8 +528,9 @@ def bench_shared(torch, steps: int, warmup: int, P: int = 8192, C: int = 1024, N
                              "frac": tflops / bf16_peak,
                              "traffic": traffic_from_profile(K2_SRC, "k2_toeplitz_traffic.txt",
                                                              f"{name}-C{C}-P{P}") if C == 1024 else None,
-                             "traffic_unit": "DRAM bytes per push (K2 + k2_reduce, one ncu capture)",
-                             "kernel": "k2_toeplitz (tcgen05 kind::f16) + k2_reduce",
+                             "traffic_unit": "DRAM bytes per push (the push's K2 launch, one ncu capture)",
+                             "kernel": ("k2_toeplitz_c2p" if name == "bf16" else "k2_toeplitz_c2s") +
+                                       " (tcgen05 cta_group::2 kind::f16, persistent, K parts folded in the kernel)",
                              "peak_basis": "measured cuBLAS bf16, sustained (MEASURED_PEAKS.json)",
                              "flops_counted": f"2 x {nprod} products x useful tap-MACs"}
         else:
@@ -563,7 +564,7 @@ def bench_mimo(torch, P: int = 8192, precisions=("bf16split", "bf16", "fp32"), L
     refs = np.array([sum(eq4_at(w.x[i_], w.H[0, o, i_][None], w.vstart, m) for i_ in range(nin))
                      for o, m in picks])
     peaks = load_peaks()
-    bf16_peak = float(peaks.get("bf16_tflops_sustained", 1690.8))
+    bf16_peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
     out = {"workload": "MIMO 16 x 16, %g s @ 48 kHz (%d samples per input), L=%d tau=%g, block 512, pushes of %d"
                        % (seconds, N, L, 0.2 * L, P), "tap_macs": macs}
     for name in precisions:
@@ -860,7 +861,7 @@ def bench_offline(torch, capi, reps: int = 3) -> dict:
             # The same convolution with the products on the tensor cores (256-sample output rows as K2's
             # channels), against the FP32 result.
             peaks = load_peaks()
-            bf16_peak = float(peaks.get("bf16_tflops", 1690.8))
+            bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
             for pname, pcode, nprod in (("bf16split", capi.TC_BF16_SPLIT, 3), ("bf16", capi.TC_BF16, 1)):
                 yt = torch.empty_like(y)
                 ms_t = timed(lambda: capi.tc_convolve_tc(x, N, h, L, yt, pcode))

@@ -860,15 +860,19 @@ def bench_offline(torch, capi, reps: int = 3) -> dict:
                 r["orientations_rel_l2"] = float(torch.linalg.norm(y - y2) / torch.linalg.norm(y2))
             # The same convolution with the products on the tensor cores (256-sample output rows as K2's
             # channels), against the FP32 result.
+            # Whole synchronous calls back to back: fractions of the burst peak (a call times alone) and,
+            # beside it, of the sustained one.
             peaks = load_peaks()
             bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
+            bf16_sus = float(peaks.get("bf16_tflops_sustained", 1700.0))
             for pname, pcode, nprod in (("bf16split", capi.TC_BF16_SPLIT, 3), ("bf16", capi.TC_BF16, 1)):
                 yt = torch.empty_like(y)
                 ms_t = timed(lambda: capi.tc_convolve_tc(x, N, h, L, yt, pcode))
                 tfl = 2.0 * nprod * N * L / (ms_t / 1e3) / 1e12
                 r["tensor_" + pname] = {"ms": ms_t, "tap_macs_per_s": N * L / (ms_t / 1e3),
                                         "rel_l2_vs_fp32": float(torch.linalg.norm(yt - y) / torch.linalg.norm(y)),
-                                        "tflops_counted": tfl, "frac_of_bf16_peak": tfl / bf16_peak}
+                                        "tflops_counted": tfl, "frac_of_bf16_peak": tfl / bf16_peak,
+                                        "frac_of_bf16_sustained": tfl / bf16_sus}
             nfft = 1 << int(math.ceil(math.log2(N + L - 1)))
 
             def fft_conv():

@@ -921,6 +921,7 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
     // Plain BF16 is limited by its operands, not by the run. K parts per
     // tile: the fewest that fill the GPU's waves to >= 90 %.
     p.range = (int)(s->k2_range > 0 ? s->k2_range : (s->prec == TC_BF16_SPLIT ? 16 : 4096));
+    p.range += p.range & 1;  // the split's CTA pairs run whole pipeline stages of 2 K blocks
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
     long long nsplit = k2_plan_nsplit(tiles, nkb, cta_pair ? sms / 2 : sms);  // a CTA pair takes two SMs

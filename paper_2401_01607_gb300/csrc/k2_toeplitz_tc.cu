@@ -562,16 +562,17 @@ __global__ void __launch_bounds__(K2_THREADS, 1)
 // stage to both CTAs' free barriers, the last one also to both accumulator
 // barriers; each CTA's eight epilogue warps then read its own TMEM (128
 // lanes = its channels, 256 columns = the outputs). One TMEM run per unit.
-// Measured on the 1024-stream shared-IR workload (one box, same run): 1 K
-// block per stage 39 % of the sustained BF16 peak, 2 blocks 58 %, 3 blocks x
-// 4 stages 64 % (4 x 3: 61 %; 7 x 2: 52 %; 1 x 13: 40 %), against 64 % for
-// two 128-channel tiles on one CTA: the cost is per stage (the barrier round
-// trip and commit of each stage), not the shared-memory operand traffic that
-// the pair halves, so the pair only matches the one-CTA form.
+// K blocks of 64 samples: 128-byte rows take half the L2 requests per byte
+// of the 64-byte rows that K blocks of 32 would give. Each pipeline stage
+// has a fixed cost (its barrier round trip and commit), so a stage holds two
+// K blocks (8 MMAs): measured on the 1024-stream shared-IR workload, 2 blocks
+// x 3 stages 75-77 % of the sustained BF16 peak against 72-73 % for 1 x 6 and
+// 1 x 7 (with K blocks of 32 the same trade gave 39 % for 1 x 10 and 64 % for
+// 3 x 4).
 constexpr int K2C_BLK = 2 * K2_XBYTES1;  // one K block per CTA: X (128 x 64) and T half (128 x 64)
-constexpr int K2C_GS = 1;               // K blocks per pipeline stage
+constexpr int K2C_GS = 2;               // K blocks per pipeline stage
 constexpr int K2C_STAGE = K2C_GS * K2C_BLK;
-constexpr int K2C_NS = 6;
+constexpr int K2C_NS = 3;
 constexpr int K2C_SMEM = K2C_NS * K2C_STAGE + 1024;
 
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2_THREADS, 1)
@@ -969,11 +970,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2_THREADS, 1)
 // the eight epilogue warps of each CTA drain every finished run into FP32
 // register sums (round-to-nearest adds) under the next run's MMAs. Runs are
 // counted across units, so the MMAs of a unit's first run never wait for the
-// previous unit's last drain.
+// previous unit's last drain. Two K blocks per stage (runs are whole stages:
+// `range` even).
 constexpr int K2S_BLK = 4 * K2_M * K2_KB * 2;  // one K block per CTA: X hi, X lo, T hi half, T lo half (8 KB each)
-constexpr int K2S_GS = 1;                        // K blocks per pipeline stage
+constexpr int K2S_GS = 2;                        // K blocks per pipeline stage
 constexpr int K2S_STAGE = K2S_GS * K2S_BLK;
-constexpr int K2S_NS = 6;
+constexpr int K2S_NS = 3;
 constexpr int K2S_SMEM = K2S_NS * K2S_STAGE + 1024;
 
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2_THREADS, 1)

@@ -228,3 +228,31 @@ def test_mono_stream_on_the_tensor_cores(prec, P):
     print(f"mono {prec} P={P}: rel_l2={err:.3g}, tensor launches {info.tensor_launches}, fallbacks {info.fp32_fallbacks}")
     assert info.tensor_launches > 0
     assert err <= TOL[prec]
+
+
+def test_tuning_knobs_reject_values_out_of_range():
+    """Every tuning knob of the tensor path takes -1 (default) or its documented range; anything else is
+    TC_EINVAL and leaves the stream usable."""
+    s = capi.tc_open_group(4, 1000, 256, True, capi.TC_BF16, 1024)
+    try:
+        for knob, good, bad in [(capi.TC_TUNE_K2_RANGE, (-1, 1, 4096), (0, 4097)),
+                                (capi.TC_TUNE_K2_PAIR, (-1, 0, 1, 2, 3), (4, -2)),
+                                (capi.TC_TUNE_K2_SPLIT, (-1, 1, 64), (0, 65)),
+                                (capi.TC_TUNE_K2_FOLD, (-1, 0, 1), (2, -2)),
+                                (capi.TC_TUNE_K2_ORDER, (-1, 0, 1, 2), (3, -2)),
+                                (99, (), (0,))]:
+            for v in good:
+                capi.tc_set_tuning(s, knob, v)
+            for v in bad:
+                with pytest.raises(capi.TcError) as e:
+                    capi.tc_set_tuning(s, knob, v)
+                assert e.value.code == "TC_EINVAL", (knob, v)
+        h = synth.decayed_ir(1000, 200.0, 78)
+        capi.tc_set_ir_rows(s, h[None], 1000, 0)
+        X = synth.audio_block(4, 600, 77)
+        y = np.empty((4, 600), np.float32)
+        capi.tc_push(s, np.ascontiguousarray(X), 600, y)  # still usable
+        ref = oracle.buffer(X[1], h[None], np.zeros(1, np.int64), 256)[:600]
+        assert rel_l2(y[1], ref) <= TOL["bf16"]
+    finally:
+        capi.tc_close(s)

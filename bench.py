@@ -1488,7 +1488,7 @@ def _tc_summary(sec: dict | None) -> dict | None:
     return out
 
 
-HEADLINE_MAX = 2500  # bytes: the driver keeps only the tail of the output
+HEADLINE_MAX = 2900  # bytes: the driver keeps only the tail of the output (about 3 KB)
 
 
 def headline(line: dict, sections: dict) -> dict:
@@ -1541,7 +1541,9 @@ def headline(line: dict, sections: dict) -> dict:
                         "one_shot_ms": mono.get("one_shot_ms"),
                         "tc_bf16split_frac": _get(mono, "offline", "long_signal_1s_ir", "tensor_bf16split",
                                                   "frac_of_bf16_peak"),
-                        "tc_bf16_frac": _get(mono, "offline", "long_signal_1s_ir", "tensor_bf16", "frac_of_bf16_peak")}
+                        "tc_bf16_frac": _get(mono, "offline", "long_signal_1s_ir", "tensor_bf16", "frac_of_bf16_peak"),
+                        "tc_bf16_frac_sustained": _get(mono, "offline", "long_signal_1s_ir", "tensor_bf16",
+                                                       "frac_of_bf16_sustained")}
     ext = sections.get("ext")
     if isinstance(ext, dict) and "zero_gating" in ext:
         side["ext"] = {"gating_speedup": ext["zero_gating"]["speedup"],

@@ -314,9 +314,10 @@ tc_status tc_convolve_noalloc(const float *x, size_t N, const float *h, size_t L
  * TC_BF16 (BF16 operands, FP32 accumulation; about 2e-3 relative L2),
  * TC_BF16_SPLIT (hi/lo BF16 split of both operands, three products; about
  * 5e-6) or TC_FP32 (the same as tc_convolve). The shorter operand takes the
- * IR role (Sec. 3.2) unless TC_NO_ROLE_SWAP=1. Working memory (the padded
- * input in FP32 and BF16 hi/lo, the IR's Toeplitz tiles, the row-major
- * output, K-part partials) comes from the library's stream-ordered pool. Runs on
+ * IR role (Sec. 3.2) unless TC_NO_ROLE_SWAP=1. The rows are written straight
+ * into y (the last one stops at y's end). Working memory (the padded input as
+ * BF16 hi and, for the split, lo; the IR's Toeplitz tiles; K-part partials and
+ * their tickets) comes from the library's stream-ordered pool. Runs on
  * cuda_stream and waits for it. Errors: TC_EINVAL (NULL, zero sizes, unknown
  * precision, L > 2^26); TC_ENOMEM; TC_ECUDA; TC_ETIMEOUT. */
 tc_status tc_convolve_tc(const float *x, size_t N, const float *h, size_t L, float *y, int precision,

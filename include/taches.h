@@ -582,7 +582,9 @@ uint64_t tc_kernel_launches(void);
  *                        plain BF16) accumulated serially on the
  *                        tensor cores before the pairwise reduction of
  *                        ranges (default 16 for the BF16 split, 4096 for
- *                        BF16; 1..4096)
+ *                        BF16; 1..4096; rounded up to an even count for
+ *                        the split; MIMO streams: K blocks of 32, rounded
+ *                        up to a multiple of 8)
  *   TC_TUNE_K2_PAIR      2 = pairs of CTAs on two SMs (tcgen05
  *                        cta_group::2) per 256 channels x 256 outputs, each
  *                        SM staging half the operands, persistent (one pair

@@ -1020,7 +1020,7 @@ tc_status launch_k3(tc_stream *s, long long t0, long long nout, float *y, long l
     p.ntile = ntile;
     p.nkbp = nkbp;
     p.range = (int)(s->k2_range > 0 ? s->k2_range : (s->prec == TC_BF16_SPLIT ? 16 : 4096));
-    p.range = (p.range + 3) / 4 * 4;  // K3 runs hold whole groups of K blocks (up to four chains)
+    p.range = (p.range + 7) / 8 * 8;  // K3 runs hold whole stages of K blocks (8 in BF16, 4 in the split)
     // K parts per tile: the fewest (<= 64) that fill the GPU's waves to >= 90 %,
     // each a whole number of A chunks.
     const long long gtot = (long long)s->nin * nkbp;

@@ -25,12 +25,15 @@ def _built():
     capi.load()
 
 
-def run_mimo(X, H, vstart, L, B, prec, max_push):
-    """X [nin, N]; H [nver, nout, nin, L]; returns (y [nout, N + L - 1], info)."""
+def run_mimo(X, H, vstart, L, B, prec, max_push, tuning=()):
+    """X [nin, N]; H [nver, nout, nin, L]; returns (y [nout, N + L - 1], info).
+    tuning: (knob, value) pairs set before the first push."""
     nin, N = X.shape
     nout = H.shape[1]
     s = capi.tc_open_mimo(nin, nout, L, B, PREC[prec], max_push)
     try:
+        for knob, value in tuning:
+            capi.tc_set_tuning(s, knob, value)
         outs, pos, v = [], 0, 0
         while pos < N:
             n = min(max_push, N - pos)
@@ -81,6 +84,19 @@ def test_mimo_16x16_split_k(prec):
         err = rel_l2(y[o], ref)
         print(f"{prec} output {o}: rel_l2 {err:.3g}")
         assert err <= TOL[prec], (o, err)
+
+
+@pytest.mark.parametrize("prec,rng", [("bf16split", 5), ("bf16split", 12), ("bf16", 3), ("bf16", 20)])
+def test_mimo_runs_of_any_length(prec, rng):
+    """TMEM runs of a set length (TC_TUNE_K2_RANGE, rounded up to whole pipeline stages of 8 K blocks in BF16
+    and 4 in the split): every run boundary falls on a stage boundary and the drains match the runs."""
+    nin, nout, N, L, B = 4, 5, 2200, 9000, 512
+    X = synth.audio_block(nin, N, 7300 + rng)
+    H = irs(1, nout, nin, L, 73)
+    y, info = run_mimo(X, H, [0], L, B, prec, 2048, tuning=[(capi.TC_TUNE_K2_RANGE, rng)])
+    assert info.tensor_launches > 0 and info.fp32_fallbacks == 0
+    ref = oracle.mimo(X, H, None, B)
+    assert rel_l2(y, ref) <= TOL[prec], rel_l2(y, ref)
 
 
 def test_mimo_ir_switch_falls_back():

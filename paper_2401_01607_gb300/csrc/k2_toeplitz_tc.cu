@@ -9,8 +9,10 @@
 // delta and on j's block, not on t0. So its tiles are materialised once per IR
 // version (k2_tprep) and shared by every output tile of every push.
 //
-// Tile: M = 128 channels (TMEM lanes) x N = 256 outputs (TMEM columns), K in
-// blocks of 32 samples (64-byte swizzled rows). Warp roles: warp 0 lane 0 issues
+// Tile: M = 128 channels (TMEM lanes) x N = 256 outputs (TMEM columns) per CTA
+// (the default kernels pair two CTAs into M = 256, tcgen05 cta_group::2), K in
+// blocks of 64 samples for plain BF16 (128-byte swizzled rows) and 32 for the
+// split (64-byte swizzled rows). Warp roles: warp 0 lane 0 issues
 // TMA tensor loads of the X tile (bf16 history) and the T tile into a stage
 // ring; warp 1 lane 0 issues tcgen05.mma (kind::f16, BF16 in, FP32 accumulate
 // in TMEM) and commits each stage back to the producer; warp 2 owns the TMEM

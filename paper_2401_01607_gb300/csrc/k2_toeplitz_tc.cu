@@ -808,6 +808,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2_THREADS, 1)
     if (warp == 0) {
         if (lane == 0) {
             // ---- producer (each CTA loads its own halves), across units ----
+            // The IR tiles of a K range are read by every pair working in it: keep them in L2.
+            const uint64_t pol = l2_policy_evict_last();
             long long gi = 0;  // stage fills so far
             for (long long u = cid; u < units && !s_fail; u += ncl) {
                 const K2Unit w = k2_unit(p, u);
@@ -829,7 +831,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2_THREADS, 1)
                         uint8_t *sb = smem + st * K2C_STAGE + j * K2C_BLK;
                         const int kb = w.kb0 + g * K2C_GS + j;
                         tma_load_2d_pair(sb, &mx_hi, (int)(xcol0 + (long long)kb * K2_KB1), c0, bar);
-                        tma_load_2d_pair(sb + K2_XBYTES1, &mt2_hi, 0, kb * K2_N + (int)rank * (K2_N / 2), bar);
+                        tma_load_2d_pair_hint(sb + K2_XBYTES1, &mt2_hi, 0, kb * K2_N + (int)rank * (K2_N / 2), bar,
+                                              pol);
                     }
                 }
             }
@@ -1024,6 +1027,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2_THREADS, 1)
     if (warp == 0) {
         if (lane == 0) {
             // ---- producer (each CTA loads its own halves), across units ----
+            // The IR tiles of a K range are read by every pair working in it: keep them in L2.
+            const uint64_t pol = l2_policy_evict_last();
             long long gi = 0;
             for (long long u = cid; u < units && !s_fail; u += ncl) {
                 const K2Unit w = k2_unit(p, u);
@@ -1048,8 +1053,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2_THREADS, 1)
                         const int tr = kb * K2_N + (int)rank * (K2_N / 2);
                         tma_load_2d_pair(sb, &mx_hi, xc, c0, bar);
                         tma_load_2d_pair(sb + XB, &mx_lo, xc, c0, bar);
-                        tma_load_2d_pair(sb + 2 * XB, &mt2_hi, 0, tr, bar);
-                        tma_load_2d_pair(sb + 3 * XB, &mt2_lo, 0, tr, bar);
+                        tma_load_2d_pair_hint(sb + 2 * XB, &mt2_hi, 0, tr, bar, pol);
+                        tma_load_2d_pair_hint(sb + 3 * XB, &mt2_lo, 0, tr, bar, pol);
                     }
                 }
             }

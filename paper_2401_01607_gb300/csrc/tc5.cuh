@@ -259,6 +259,26 @@ __device__ __forceinline__ void tma_load_2d_pair(void *dst, const CUtensorMap *m
         : "memory");
 }
 
+// L2 policy "evict last" for data that many CTAs read again soon (the IR's
+// Toeplitz tiles): created once per thread and passed as a cache hint.
+__device__ __forceinline__ uint64_t l2_policy_evict_last()
+{
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// tma_load_2d_pair with an L2 cache hint (a policy from createpolicy).
+__device__ __forceinline__ void tma_load_2d_pair_hint(void *dst, const CUtensorMap *map, int c0, int c1,
+                                                      uint32_t bar_cluster, uint64_t pol)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.cta_group::2.L2::cache_hint "
+        "[%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar_cluster), "l"(pol)
+        : "memory");
+}
+
 // ---- Tiled TMA --------------------------------------------------------------
 
 // 2-D tiled load of the box at (c0, c1) of tensor map `map` into dst,

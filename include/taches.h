@@ -588,9 +588,11 @@ uint64_t tc_kernel_launches(void);
  *   TC_TUNE_K2_PAIR      2 = pairs of CTAs on two SMs (tcgen05
  *                        cta_group::2) per 256 channels x 256 outputs, each
  *                        SM staging half the operands, persistent (one pair
- *                        per two SMs walks the units; default; the BF16
- *                        split takes it when it has two 128-channel tiles,
- *                        else one tile per CTA); plain BF16 only: 3 = the
+ *                        per two SMs walks the units; default; a group of
+ *                        at most 128 channels pairs two adjacent output
+ *                        tiles instead, and the BF16 split takes the pairs
+ *                        when it has two tiles of either kind, else one tile
+ *                        per CTA); plain BF16 only: 3 = the
  *                        same pairs launched one per unit; 1 = two
  *                        128-channel tiles per CTA sharing each IR tile;
  *                        0 = one tile per CTA (the split: any value but 2)

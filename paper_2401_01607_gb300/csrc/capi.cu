@@ -907,13 +907,17 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
     // Plain BF16 runs two channel tiles per CTA (one T stage feeds both), as
     // long as a unit's K range fits one TMEM run.
     const long long ntile_c1 = ((long long)p.C + TM - 1) / TM;
-    // The BF16 split runs on persistent CTA pairs when there are two channel
-    // tiles to pair (one tile alone would leave half of each pair idle).
-    const bool spair = s->prec == TC_BF16_SPLIT && s->k2_mode == 2 && ntile_c1 >= 2;
+    // The persistent CTA pairs take two channel tiles of one output tile; a
+    // group of one channel tile pairs two adjacent output tiles instead (the
+    // same IR tile serves both), so that neither SM of a pair computes empty
+    // rows. The BF16 split takes the pairs when it has two tiles of either kind.
+    const bool pair_o = s->k2_mode == 2 && ntile_c1 == 1 && p.ntile_o >= 2;
+    const bool spair = s->prec == TC_BF16_SPLIT && s->k2_mode == 2 && (ntile_c1 >= 2 || pair_o);
     bool pair = (s->prec == TC_BF16 && s->k2_mode != 0) || spair;
     const bool cta_pair = pair && s->k2_mode >= 2;
-    p.ntile_c = (int)(pair ? (ntile_c1 + 1) / 2 : ntile_c1);
-    const long long tiles = (long long)p.ntile_c * p.ntile_o;
+    p.pair_o = pair_o ? 1 : 0;
+    p.ntile_c = (int)(pair && !pair_o ? (ntile_c1 + 1) / 2 : ntile_c1);
+    const long long tiles = (long long)p.ntile_c * (pair_o ? (p.ntile_o + 1) / 2 : p.ntile_o);
     // TMEM runs of `range` K blocks before each drain into FP32 registers.
     // The BF16 split's error grows with the run (measured at L = 96000:
     // 4.4e-6 at 16, 6.2e-6 at 48, 7.4e-6 at 64 relative L2), and draining
@@ -934,6 +938,7 @@ tc_status launch_k2(tc_stream *s, long long t0, long long nout, float *y, long l
     if (pair && !spair && p.range < p.kb_per) {
         // One TMEM run cannot hold this unit's K range: single tiles, same K split.
         pair = false;
+        p.pair_o = 0;
         p.ntile_c = (int)ntile_c1;
     }
     p.order = s->k2_order;
@@ -1258,9 +1263,9 @@ tc_status group_open(size_t channels, size_t L, size_t max_push, int precision, 
         for (long long no = 1; no <= ((long long)max_push + TN - 1) / TN; ++no) {
             // Single tiles over all SMs; tile pairs (plain BF16, and the split on
             // CTA pairs) over all SMs or over half of them.
-            for (const long long tc : {ntile_c1, (ntile_c1 + 1) / 2})
+            for (const long long tcno : {ntile_c1 * no, (ntile_c1 + 1) / 2 * no, ntile_c1 * ((no + 1) / 2)})
                 for (int slots : {sms, sms / 2}) {
-                    const long long ns = k2_plan_nsplit(tc * no, nkb, slots);
+                    const long long ns = k2_plan_nsplit(tcno, nkb, slots);
                     if (ns > 1)
                         need = std::max(need, (size_t)(2 * ((ntile_c1 + 1) / 2) * no * ns * TM * TN));
                 }

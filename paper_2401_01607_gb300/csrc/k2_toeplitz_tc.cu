@@ -743,24 +743,49 @@ struct K2Unit {
     int part, tile_o, tile_c, kb0, nk;
 };
 
+// What one CTA of a pair computes of unit w: its 128-channel tile and its
+// output tile. Two channel tiles of one output tile (the usual pair), or,
+// with pair_o (groups of one channel tile), two adjacent output tiles of the
+// same channels: T does not depend on the output tile, so each CTA stages X
+// from its own window and both multiply it by the shared T tile.
+struct K2Cta {
+    int tc1, ot;
+};
+
+__device__ __forceinline__ K2Cta k2_cta(const K2Params &p, const K2Unit &w, uint32_t rank)
+{
+    K2Cta m;
+    m.tc1 = p.pair_o ? w.tile_c : w.tile_c * 2 + (int)rank;
+    m.ot = p.pair_o ? w.tile_o * 2 + (int)rank : w.tile_o;
+    return m;
+}
+
+// Output tiles of one unit row: all of them, or their pairs when the two
+// CTAs of a pair take two adjacent output tiles of the same channels.
+__device__ __forceinline__ int k2_unit_ntile_o(const K2Params &p)
+{
+    return p.pair_o ? (p.ntile_o + 1) / 2 : p.ntile_o;
+}
+
 __device__ __forceinline__ K2Unit k2_unit(const K2Params &p, long long u)
 {
     K2Unit w;
+    const int nto = k2_unit_ntile_o(p);
     if (p.order == 1) {  // output tile fastest, then K part
-        w.tile_o = (int)(u % p.ntile_o);
-        u /= p.ntile_o;
+        w.tile_o = (int)(u % nto);
+        u /= nto;
         w.part = (int)(u % p.nsplit);
         w.tile_c = (int)(u / p.nsplit);
     } else if (p.order == 2) {  // output tile fastest, then channel tile; K part slowest
-        w.tile_o = (int)(u % p.ntile_o);
-        u /= p.ntile_o;
+        w.tile_o = (int)(u % nto);
+        u /= nto;
         w.tile_c = (int)(u % p.ntile_c);
         w.part = (int)(u / p.ntile_c);
     } else {  // K part fastest, then output tile
         w.part = (int)(u % p.nsplit);
         u /= p.nsplit;
-        w.tile_o = (int)(u % p.ntile_o);
-        w.tile_c = (int)(u / p.ntile_o);
+        w.tile_o = (int)(u % nto);
+        w.tile_c = (int)(u / nto);
     }
     w.kb0 = w.part * p.kb_per;
     w.nk = max(min(w.kb0 + p.kb_per, p.nkb) - w.kb0, 0);
@@ -813,8 +838,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2_THREADS, 1)
             long long gi = 0;  // stage fills so far
             for (long long u = cid; u < units && !s_fail; u += ncl) {
                 const K2Unit w = k2_unit(p, u);
-                const int c0 = w.tile_c * 2 * K2_M + (int)rank * K2_M;
-                const long long xcol0 = p.x_col0 + (long long)w.tile_o * K2_N;
+                const K2Cta m = k2_cta(p, w, rank);
+                const int c0 = m.tc1 * K2_M;
+                const long long xcol0 = p.x_col0 + (long long)m.ot * K2_N;
                 for (int g = 0; g * K2C_GS < w.nk; ++g, ++gi) {
                     const int st = (int)(gi % K2C_NS);
                     const long long use = gi / K2C_NS;
@@ -902,17 +928,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2_THREADS, 1)
             mbar_try_wait(&accfull[buf], par);
             tc_fence_after_sync();
             const int ch = q * 32 + lane;
-            const int c = w.tile_c * 2 * K2_M + (int)rank * K2_M + ch;
+            const K2Cta m = k2_cta(p, w, rank);
+            const bool live = m.ot < p.ntile_o;  // the odd last output tile of a pair_o row has no partner
+            const int c = m.tc1 * K2_M + ch;
             float *dst;
             long long lim;
             if (p.nsplit == 1) {
-                dst = p.y + (long long)c * p.y_pitch + (long long)w.tile_o * K2_N + half * 128;
-                lim = k2_ylim(p, p.nout - (long long)w.tile_o * K2_N - half * 128, c,
-                              (long long)w.tile_o * K2_N + half * 128);
+                dst = p.y + (long long)c * p.y_pitch + (long long)m.ot * K2_N + half * 128;
+                lim = k2_ylim(p, p.nout - (long long)m.ot * K2_N - half * 128, c, (long long)m.ot * K2_N + half * 128);
             } else {
-                const int tc1 = w.tile_c * 2 + (int)rank;
                 dst = p.partial +
-                      ((((long long)tc1 * p.ntile_o + w.tile_o) * p.nsplit + w.part) * K2_M + ch) * K2_N + half * 128;
+                      ((((long long)m.tc1 * p.ntile_o + m.ot) * p.nsplit + w.part) * K2_M + ch) * K2_N + half * 128;
                 lim = 128;
             }
             const uint32_t src = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * K2_N + half * 128);
@@ -920,7 +946,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2_THREADS, 1)
             for (int cc = 0; cc < 8; ++cc) {
                 float v[16];
                 tmem_ld_32x16(src + cc * 16, v);
-                if (c >= p.C)
+                if (c >= p.C || !live)
                     continue;
                 const long long j0 = cc * 16;
                 if (lim >= j0 + 16 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
@@ -938,9 +964,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2_THREADS, 1)
             __syncwarp();
             if (lane == 0)
                 mbar_arrive_cluster(buf ? free1 : free0);  // this buffer may take the next unit's MMAs
-            if (fold) {
-                const int tc1 = w.tile_c * 2 + (int)rank;
-                unsigned *tk = p.ticket + ((long long)tc1 * p.ntile_o + w.tile_o) * K2_EPI_WARPS + ew;
+            if (fold && live) {
+                unsigned *tk = p.ticket + ((long long)m.tc1 * p.ntile_o + m.ot) * K2_EPI_WARPS + ew;
                 __threadfence();  // this lane's part sums before the ticket
                 __syncwarp();
                 unsigned prev = 0;
@@ -949,7 +974,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2_THREADS, 1)
                 prev = __shfl_sync(0xffffffffu, prev, 0);
                 if (prev == (unsigned)(p.nsplit - 1)) {
                     __threadfence();  // the other parts' sums after their tickets
-                    k2_fold_slice(p, tc1, w.tile_o, q, half, lane);
+                    k2_fold_slice(p, m.tc1, m.ot, q, half, lane);
                     if (lane == 0)
                         *tk = 0u;  // every part has its ticket: zero again for the next launch
                 }
@@ -1032,8 +1057,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2_THREADS, 1)
             long long gi = 0;
             for (long long u = cid; u < units && !s_fail; u += ncl) {
                 const K2Unit w = k2_unit(p, u);
-                const int c0 = w.tile_c * 2 * K2_M + (int)rank * K2_M;
-                const long long xcol0 = p.x_col0 + (long long)w.tile_o * K2_N;
+                const K2Cta m = k2_cta(p, w, rank);
+                const int c0 = m.tc1 * K2_M;
+                const long long xcol0 = p.x_col0 + (long long)m.ot * K2_N;
                 for (int g = 0; g * K2S_GS < w.nk; ++g, ++gi) {
                     const int st = (int)(gi % K2S_NS);
                     const long long use = gi / K2S_NS;
@@ -1154,18 +1180,19 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2_THREADS, 1)
             if (!ok)
                 break;
             const int ch = q * 32 + lane;
-            const int tc1 = w.tile_c * 2 + (int)rank;
-            const int c = tc1 * K2_M + ch;
-            if (c < p.C) {
+            const K2Cta m = k2_cta(p, w, rank);
+            const bool live = m.ot < p.ntile_o;  // the odd last output tile of a pair_o row has no partner
+            const int c = m.tc1 * K2_M + ch;
+            if (c < p.C && live) {
                 float *dst;
                 long long lim;
                 if (p.nsplit == 1) {
-                    dst = p.y + (long long)c * p.y_pitch + (long long)w.tile_o * K2_N + half * 128;
-                    lim = k2_ylim(p, p.nout - (long long)w.tile_o * K2_N - half * 128, c,
-                                  (long long)w.tile_o * K2_N + half * 128);
+                    dst = p.y + (long long)c * p.y_pitch + (long long)m.ot * K2_N + half * 128;
+                    lim = k2_ylim(p, p.nout - (long long)m.ot * K2_N - half * 128, c,
+                                  (long long)m.ot * K2_N + half * 128);
                 } else {
                     dst = p.partial +
-                          ((((long long)tc1 * p.ntile_o + w.tile_o) * p.nsplit + w.part) * K2_M + ch) * K2_N +
+                          ((((long long)m.tc1 * p.ntile_o + m.ot) * p.nsplit + w.part) * K2_M + ch) * K2_N +
                           half * 128;
                     lim = 128;
                 }
@@ -1181,8 +1208,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2_THREADS, 1)
                             dst[j] = sum[j];
                 }
             }
-            if (fold) {
-                unsigned *tk = p.ticket + ((long long)tc1 * p.ntile_o + w.tile_o) * K2_EPI_WARPS + ew;
+            if (fold && live) {
+                unsigned *tk = p.ticket + ((long long)m.tc1 * p.ntile_o + m.ot) * K2_EPI_WARPS + ew;
                 __threadfence();  // this lane's part sums before the ticket
                 __syncwarp();
                 unsigned prev = 0;
@@ -1191,7 +1218,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(K2_THREADS, 1)
                 prev = __shfl_sync(0xffffffffu, prev, 0);
                 if (prev == (unsigned)(p.nsplit - 1)) {
                     __threadfence();  // the other parts' sums after their tickets
-                    k2_fold_slice(p, tc1, w.tile_o, q, half, lane);
+                    k2_fold_slice(p, m.tc1, m.ot, q, half, lane);
                     if (lane == 0)
                         *tk = 0u;  // zero again for the next launch
                 }
@@ -1475,7 +1502,9 @@ cudaError_t k2_launch_c2p(const CUtensorMap &mx_hi, const CUtensorMap &mt2_hi, c
         clusters[dev] = std::max(1, sms / 2);  // one CTA per SM, two per cluster
         attr[dev] = true;
     }
-    const long long units = (long long)p.ntile_c * p.ntile_o * p.nsplit;  // ntile_c counts tile pairs here
+    // ntile_c counts tile pairs here (or channel tiles, with pair_o taking output-tile pairs).
+    const long long nto = p.pair_o ? (p.ntile_o + 1) / 2 : p.ntile_o;
+    const long long units = (long long)p.ntile_c * nto * p.nsplit;
     if (units <= 0)
         return cudaSuccess;
     const long long ncl = std::min<long long>(units, clusters[dev]);
@@ -1513,7 +1542,9 @@ cudaError_t k2_launch_c2s(const CUtensorMap &mx_hi, const CUtensorMap &mx_lo, co
         clusters[dev] = std::max(1, sms / 2);
         attr[dev] = true;
     }
-    const long long units = (long long)p.ntile_c * p.ntile_o * p.nsplit;  // ntile_c counts tile pairs here
+    // ntile_c counts tile pairs here (or channel tiles, with pair_o taking output-tile pairs).
+    const long long nto = p.pair_o ? (p.ntile_o + 1) / 2 : p.ntile_o;
+    const long long units = (long long)p.ntile_c * nto * p.nsplit;
     if (units <= 0)
         return cudaSuccess;
     const long long ncl = std::min<long long>(units, clusters[dev]);

@@ -150,6 +150,8 @@ struct K2Params {
     int nkb;                 // K blocks per output tile
     int nsplit, kb_per;      // K parts per tile (one CTA each) and blocks per part
     int range;               // K blocks per serial TMEM run before the drain to FP32 registers
+    int pair_o;              // persistent CTA pairs of a group of one channel tile: the two CTAs take two
+                             // adjacent output tiles of the same channels (ntile_c counts channel tiles)
     int order;               // persistent CTA pairs: order of the units (0 K part fastest, then output
                              // tile; 1 output tile fastest, then K part; 2 output tile, channel tile, K part)
     float *y;                // y[c * y_pitch + j], j < nout

@@ -154,6 +154,28 @@ def test_split_on_cta_pairs_equals_single_tiles(nsplit, rng):
     check(ys[2], X, H, [0], B, "bf16split", rows=[0, 31, 127, 128, 255, 256, 299])
 
 
+@pytest.mark.parametrize("nsplit", [-1, 3, 17])
+@pytest.mark.parametrize("prec", ["bf16", "bf16split"])
+def test_one_channel_tile_pairs_output_tiles(prec, nsplit):
+    """A group of at most 128 channels runs on the persistent CTA pairs with the two CTAs on two adjacent output
+    tiles of the same channels (each multiplies its own X window by the shared IR tile). With the same K parts it
+    gives the same bits as one tile per CTA (TC_TUNE_K2_PAIR 0), in pushes of 5 output tiles (the last pair has one)
+    and in a flush of odd pitch; with the planned K parts (-1) the two forms plan for different unit counts, so
+    there only the oracle decides."""
+    C, N, L, B = 100, 2600, 20_000, 256
+    X = synth.audio_block(C, N, 9700 + max(nsplit, 0))
+    H = synth.decayed_ir(L, 0.2 * L, 85)[None]
+    ys = {}
+    for pair in (2, 0):
+        ys[pair], info = run_group(X, H, [0], L, B, prec, 1280,
+                                   tuning=[(capi.TC_TUNE_K2_PAIR, pair), (capi.TC_TUNE_K2_SPLIT, nsplit)])
+        assert info.tensor_launches > 0 and info.fp32_fallbacks == 0
+    if nsplit > 0:
+        assert np.array_equal(ys[2], ys[0]), np.argwhere(ys[2] != ys[0])[:5]
+    check(ys[2], X, H, [0], B, prec, rows=[0, 31, 32, 63, 99])
+    check(ys[0], X, H, [0], B, prec, rows=[0, 99])
+
+
 @pytest.mark.parametrize("prec", ["bf16", "bf16split"])
 def test_unit_order_of_cta_pairs_does_not_change_bits(prec):
     """The persistent CTA pairs take their units in one of three orders; each

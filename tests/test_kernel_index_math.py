@@ -12,6 +12,11 @@ reasoning that the kernels' bounds and decompositions rest on. Each test restate
     Eq. 4 with per-sample IR versions.
   * K2 (`csrc/k2_toeplitz_tc.cu`, `csrc/oneshot.cu`): the Toeplitz product on an 8-sample grid (shift delta),
     and the row view of one signal (rows of 256 outputs as channels), equal the convolution.
+  * K2 persistent CTA pairs: K blocks of 32 and 64 samples tile every tap once and k2_tprep's threads write
+    every tile element once; the units of every order, with pairs of channel tiles or (one channel tile) of
+    output tiles, cover every (tile, output tile, K part) once inside the allocated partials and tickets; the
+    in-kernel fold adds K parts bit for bit as k2_reduce does; a row view's flat output limit writes every
+    output once.
   * K3 (`csrc/k3_mimo_tc.cu`): the phase reshaping of a MIMO output tile (row r, phase p, output o; A a strided
     view of the reversed input, B the phase-shifted IRs) equals the sum of convolutions.
 """
@@ -323,3 +328,138 @@ def test_k3_phase_reshaping_of_a_mimo_tile():
             t = Tb - 8 * np.arange(128) - p
             ok = (t >= 0) & (t < N + L - 1)
             assert np.abs(D[ok, col] - ref[o, t[ok]]).max() <= 1e-11 * np.abs(ref).max(), (Tb, col)
+
+
+# K2 persistent CTA pairs (k2_toeplitz_tc.cu: k2_unit, k2_cta, k2_fold_*; capi.cu: launch_k2)
+K2_M, K2_N = 128, 256
+
+
+def k2_nkb(L, delta, kbs):
+    return (L - 1 + delta + K2_N + kbs - 1) // kbs
+
+
+def test_k2_toeplitz_tiles_in_k_blocks_of_32_and_64():
+    """k2_tprep: T[kb][i][j] = h[L - 1 + delta + i - kbs kb - j] in K blocks of kbs = 32 (split) or 64 (plain);
+    nkb = k2_nkb(L, delta, kbs) blocks cover every tap of every output of the tile, and one thread's group of eight
+    j (q -> jg = q mod kbs/8, row r = q div kbs/8) writes each element of the tiles exactly once."""
+    rng = np.random.default_rng(17)
+    for kbs in (32, 64):
+        sh = 3 if kbs == 64 else 2
+        for L, delta in [(1, 0), (257, 3), (1000, 7), (4097, 5)]:
+            h = rng.standard_normal(L)
+            nkb = k2_nkb(L, delta, kbs)
+            kb = np.arange(nkb)[:, None, None]
+            i = np.arange(K2_N)[None, :, None]
+            j = np.arange(kbs)[None, None, :]
+            k = L - 1 + delta + i - kbs * kb - j
+            T = np.where((k >= 0) & (k < L), h[np.clip(k, 0, L - 1)], 0.0)
+            # every tap of every output row appears once, in its K block
+            for row in (0, 1, K2_N - 1):
+                taps = k[:, row, :].reshape(-1)
+                taps = taps[(taps >= 0) & (taps < L)]
+                assert np.array_equal(np.sort(taps), np.arange(L)), (kbs, L, delta, row)
+            # the thread decomposition of k2_tprep_group writes each element once
+            total = (nkb * K2_N) << sh
+            q = np.arange(total)
+            jg = q & ((1 << sh) - 1)
+            r = q >> sh
+            o = (r * kbs + 8 * jg)[:, None] + np.arange(8)[None, :]
+            assert np.array_equal(np.sort(o.reshape(-1)), np.arange(nkb * K2_N * kbs))
+            flat = T.reshape(-1)
+            assert flat.shape[0] == nkb * K2_N * kbs
+
+
+def k2_units(ntile_c, ntile_o, nsplit, order, pair_o):
+    """(unit, rank) -> (tc1, ot, part) as k2_unit and k2_cta compute them."""
+    nto = (ntile_o + 1) // 2 if pair_o else ntile_o
+    out = []
+    for u0 in range(ntile_c * nto * nsplit):
+        u = u0
+        if order == 1:
+            tile_o = u % nto; u //= nto; part = u % nsplit; tile_c = u // nsplit
+        elif order == 2:
+            tile_o = u % nto; u //= nto; tile_c = u % ntile_c; part = u // ntile_c
+        else:
+            part = u % nsplit; u //= nsplit; tile_o = u % nto; tile_c = u // nto
+        for rank in (0, 1):
+            tc1 = tile_c if pair_o else tile_c * 2 + rank
+            ot = tile_o * 2 + rank if pair_o else tile_o
+            out.append((tc1, ot, part))
+    return out
+
+
+def test_k2_pair_units_cover_every_tile_and_part_once():
+    """The persistent CTA pairs: over all units and both CTAs, every (128-channel tile, output tile, K part) is
+    computed once by a CTA whose output tile exists (live), in every unit order, with pairs of channel tiles or,
+    for a group of one channel tile, pairs of output tiles (the odd last one's partner is not live); the partial
+    and ticket indices of the live CTAs stay inside what launch_k2 allocates
+    (2 ceil(tiles / 2) x ntile_o x nsplit tiles of 128 x 256 floats, 8 tickets per tile)."""
+    for C in (1, 100, 128, 129, 300, 1024):
+        ntile_c1 = -(-C // K2_M)
+        for ntile_o in (1, 2, 5, 32):
+            for nsplit in (1, 3, 4, 17):
+                pair_o = ntile_c1 == 1 and ntile_o >= 2
+                ntile_c = ntile_c1 if pair_o else (ntile_c1 + 1) // 2
+                alloc_tiles = 2 * ((ntile_c1 + 1) // 2) * ntile_o
+                for order in (0, 1, 2):
+                    cover = {}
+                    for tc1, ot, part in k2_units(ntile_c, ntile_o, nsplit, order, pair_o):
+                        if ot >= ntile_o:
+                            assert pair_o and ntile_o % 2 == 1 and ot == ntile_o  # only the odd tile's partner
+                            continue
+                        if tc1 * K2_M >= C:
+                            continue  # rows past the group: computed, never stored
+                        key = (tc1, ot, part)
+                        cover[key] = cover.get(key, 0) + 1
+                        tile = tc1 * ntile_o + ot
+                        assert (tile * nsplit + part) < alloc_tiles * nsplit
+                        assert tile * 8 + 7 < alloc_tiles * 8
+                    want = {(t, o, p) for t in range(ntile_c1) for o in range(ntile_o) for p in range(nsplit)}
+                    assert set(cover) == want and all(v == 1 for v in cover.values()), (C, ntile_o, nsplit, order)
+
+
+def fold_carry(v):
+    """k2_fold_rows: adjacent pairs level by level, an odd last element carried up (float32)."""
+    v = list(v)
+    while len(v) > 1:
+        n = len(v)
+        nxt = [np.float32(v[2 * s] + v[2 * s + 1]) for s in range(n // 2)]
+        if n & 1:
+            nxt.append(v[n - 1])
+        v = nxt
+    return v[0]
+
+
+def fold_padded(v):
+    """k2_reduce: zero-padded to 64 leaves, adjacent pairs level by level (float32)."""
+    w = [np.float32(x) for x in v] + [np.float32(0.0)] * (64 - len(v))
+    while len(w) > 1:
+        w = [np.float32(w[2 * s] + w[2 * s + 1]) for s in range(len(w) // 2)]
+    return w[0]
+
+
+def test_k2_fold_tree_equals_the_zero_padded_reduce_tree():
+    """The in-kernel fold of 2..16 K parts adds them as k2_reduce does, bit for bit in float32: carrying an odd
+    element up unchanged is the zero-padded tree, since x + 0 = x (only the sign of a zero may differ)."""
+    rng = np.random.default_rng(18)
+    for n in range(1, 17):
+        for _ in range(200):
+            v = (rng.standard_normal(n) * 10.0 ** rng.integers(-3, 4, n)).astype(np.float32)
+            a, b = fold_carry(v), fold_padded(v)
+            assert a == b and np.float32(a).tobytes() in (np.float32(b).tobytes(), np.float32(-b).tobytes()), (n, v)
+
+
+def test_k2_row_view_writes_each_output_once_up_to_y_total():
+    """k2_ylim with a flat destination (row pitch 256): over the rows and column halves of every tile, the kept
+    writes cover [0, y_total) exactly once (the last row cut at the end of y)."""
+    for y_total in (256, 257, 1000, 32768, 40001):
+        rows = -(-y_total // 256)
+        hits = np.zeros(rows * 256, np.int64)
+        for c in range(rows):
+            for half in (0, 1):
+                col = half * 128
+                lim = min(256 - col, y_total - c * 256 - col)  # nout = 256 per row, tile_o = 0
+                if lim > 0:
+                    start = c * 256 + col
+                    hits[start:start + min(lim, 128)] += 1
+        assert np.array_equal(hits[:y_total], np.ones(y_total, np.int64)) and not hits[y_total:].any(), y_total
